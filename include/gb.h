@@ -1,0 +1,229 @@
+/*
+ * gb.h -- C ABI of the B300 F4 library (sm_103a).
+ *
+ * Problem (Sec. 1): R = F_p[x1..xn] with a term order, I = <f1..fm>; compute a Groebner basis of I.
+ * The library runs the data-parallel hot path of the F4 method on one GPU:
+ *   - symbolic preprocessing SP : batch -> (T, R, Pi) (Def. 5.2), realised as the two-pass FBSP
+ *     pipeline of Algorithm 1 with the one-step reduction closure (Rem. 3.3, Def. 11.2);
+ *   - exact structured elimination of the Macaulay matrix A (Def. 3.1) over F_p: pivot / non-pivot
+ *     split, sparse row reduction, reduced echelon form of the remaining block (Sec. 9.2), with
+ *     Barrett / Montgomery modular arithmetic (Sec. 8);
+ *   - reconstruction of new basis elements and the basis update (Sec. 4.2).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns gb_status.  Outputs are written only on GB_OK (or GB_DONE).  Nothing
+ *     throws across this boundary.  gb_last_error() gives a human-readable detail for the calling
+ *     thread's last failure.
+ *   - Pointers in argument lists are HOST pointers unless the name says otherwise.  Input arrays
+ *     are owned by the caller and copied during the call.
+ *   - Handles (gb_ctx, gb_system, gb_macaulay, gb_echelon, gb_server) are owned by the library and
+ *     released by the matching *_destroy call.
+ *   - Exports use a two-call pattern: call with NULL array pointers to learn the sizes (the size
+ *     fields are filled), then call again with caller-allocated arrays of at least those sizes.
+ *   - Coefficients cross the boundary as standard residues in [0, p).
+ *   - Term order: grevlex with x1 > x2 > ... > xn (x^a > x^b iff deg a > deg b, or equal degrees
+ *     and the last nonzero entry of a - b is negative).  Monomials are exponent vectors of n bytes.
+ *   - p must be an odd prime below 2^31 (GB_EINVAL otherwise), 1 <= n <= 16.
+ *   - A context and everything created from it is used by one host thread at a time, except the
+ *     server, whose submit/poll calls may come from any thread.
+ */
+#ifndef GB_H
+#define GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GB_OK = 0,
+    GB_DONE = 1,           /* gb_f4_step: no critical pairs remain */
+    GB_EINVAL = -1,        /* bad argument (null handle, bad prime, n out of range, ...) */
+    GB_ENOMEM = -2,        /* device arena or host memory exhausted */
+    GB_EOVERFLOW = -3,     /* an exponent above 255 or a monomial space too large for the keys */
+    GB_ETIMEOUT = -4,      /* a bounded device wait gave up */
+    GB_EDEVICE = -5,       /* a CUDA error */
+    GB_EUNSUPPORTED = -6,  /* valid but outside what this build handles */
+    GB_EBUSY = -7          /* server: the ticket is still running */
+} gb_status;
+
+typedef enum { GB_GREVLEX = 0 } gb_order;
+
+typedef struct gb_ctx gb_ctx;
+typedef struct gb_system gb_system;
+typedef struct gb_macaulay gb_macaulay;
+typedef struct gb_echelon gb_echelon;
+typedef struct gb_server gb_server;
+
+/* Context options.  All fields may be zero. */
+typedef struct {
+    void *stream;        /* cudaStream_t to run on; NULL: the context creates its own stream */
+    void *arena;         /* DEVICE memory the caller owns (e.g. a torch tensor), or NULL */
+    size_t arena_bytes;  /* size of `arena`; when arena is NULL, bytes the context allocates
+                            with cudaMalloc at creation (0: 2 GiB) */
+    uint32_t flags;      /* GB_CTX_KEEP_STEP: keep the last F4 step's matrix and echelon form
+                            of each system for gb_system_last_step (costs memory) */
+    uint32_t reserved;
+} gb_ctx_opts;
+
+#define GB_CTX_KEEP_STEP 1u
+
+/* A polynomial system on the host: polynomial i has the terms [poly_off[i], poly_off[i+1]). */
+typedef struct {
+    uint32_t npolys;
+    const uint32_t *poly_off; /* npolys + 1 */
+    const uint8_t *exps;      /* poly_off[npolys] * nvars, row-major */
+    const uint32_t *coeffs;   /* poly_off[npolys]; reduced mod p on input */
+} gb_polys;
+
+/* Host export of polynomials (two-call pattern on npolys / nterms). */
+typedef struct {
+    uint32_t npolys;
+    uint64_t nterms;
+    uint32_t *poly_off; /* npolys + 1 */
+    uint8_t *exps;      /* nterms * nvars */
+    uint32_t *coeffs;   /* nterms */
+} gb_polys_host;
+
+/* Host export of Pi = (row_ptr, col_ind, val, dict_keys, row_meta) (Def. 5.2). */
+typedef struct {
+    uint32_t nvars, nrows, ndict, npivot;
+    uint64_t nnz;
+    uint32_t *row_ptr;  /* nrows + 1 */
+    uint32_t *col_ind;  /* nnz, 0-based dictionary columns, ascending within a row */
+    uint32_t *val;      /* nnz */
+    uint8_t *dict_exps; /* ndict * nvars, monomials in descending order (column 0 = largest) */
+    uint8_t *row_t;     /* nrows * nvars: the shift t_i of row i */
+    uint32_t *row_k;    /* nrows: the basis index k_i of row i */
+    uint8_t *row_flags; /* nrows: bit 0 pivot row, bit 1 added by the closure (reducer row) */
+} gb_macaulay_host;
+
+/* Host export of the elimination: D' and its reduced row echelon form (Sec. 9.2). */
+typedef struct {
+    uint32_t nC, nb, rank;
+    uint32_t *nonpiv;   /* nb: dictionary columns of D', ascending */
+    uint32_t *dprime;   /* nC * nb: the non-pivot rows after reduction by the pivot rows */
+    uint32_t *rref_piv; /* rank: pivot positions in [0, nb), ascending */
+    uint32_t *rref;     /* rank * nb: RREF(D') */
+} gb_echelon_host;
+
+typedef struct {
+    uint32_t step, degree, npairs, nrows, ndict, npivot, nC, nb, rank, nbasis;
+    uint32_t closure_rounds, reserved;
+    uint64_t nnz;
+    uint64_t axpy_rows;  /* pivot rows applied by the sparse reduction (eq. 8.1 row updates) */
+    uint64_t axpy_fma;   /* modular multiply-adds a <- a + b c of the sparse reduction */
+    float ms_sp;       /* device time: symbolic preprocessing (DictBuild + RowAssemble) */
+    float ms_reduce;   /* device time: sparse reduction of the non-pivot rows */
+    float ms_rref;     /* device time: reduced echelon form of D' */
+    float ms_update;   /* device time: reconstruction of the new elements */
+    double ms_wall;    /* host wall time of the step */
+} gb_step_stats;
+
+typedef struct {
+    uint32_t steps, nbasis;
+    uint64_t nnz_total;
+    uint64_t axpy_rows, axpy_fma;
+    double ms_sp, ms_reduce, ms_rref, ms_update, ms_wall;
+} gb_run_stats;
+
+/* ---- context -------------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  opts may be NULL. */
+gb_status gb_ctx_create(int device, const gb_ctx_opts *opts, gb_ctx **out);
+gb_status gb_ctx_destroy(gb_ctx *ctx);
+/* Device bytes currently allocated from the context's arena, and its size. */
+gb_status gb_ctx_memory(const gb_ctx *ctx, size_t *used, size_t *capacity);
+
+/* ---- systems -------------------------------------------------------------------------------- */
+
+/* Create a system <f1..fm> in F_p[x1..xn] (Sec. 1).  The inputs are normalised: equal monomials
+   merged mod p, zero terms and zero polynomials dropped, each polynomial made monic, terms sorted
+   descending.  The normalised inputs become the first basis elements, inserted in input order with
+   the Gebauer-Moeller pair update.  GB_EOVERFLOW: an exponent above 255. */
+gb_status gb_system_create(gb_ctx *ctx, uint32_t nvars, uint32_t p, gb_order order,
+                           const gb_polys *F, gb_system **out);
+gb_status gb_system_destroy(gb_system *sys);
+
+/* ---- the hot path --------------------------------------------------------------------------- */
+
+/* Symbolic preprocessing (Def. 5.2, Algorithm 1) of the r shifted rows (t_i, g_{k_i}) of the
+   system's current basis.  t_exps: r * nvars host bytes; k: r basis indices.  Equal (t, k) rows
+   collapse.  closure != 0 adds, for every dictionary monomial m that is not the leading monomial of
+   a given row and is divisible by the leading monomial of a non-redundant basis element, the
+   reducer row (m / LM(g), g) for the oldest such g, until closed (Rem. 3.3).  Row order: pivot rows
+   (one per leading column; reducer rows, else the given row of smallest k) by leading column,
+   then the other rows by (leading column, k).  The result lives on the device. */
+gb_status gb_symbolic_preprocess(gb_system *sys, uint32_t r, const uint8_t *t_exps,
+                                 const uint32_t *k, int closure, gb_macaulay **out);
+gb_status gb_macaulay_export(const gb_macaulay *mac, gb_macaulay_host *inout);
+gb_status gb_macaulay_destroy(gb_macaulay *mac);
+
+/* Structured elimination of Pi (Sec. 9.2): each non-pivot row is reduced by the pivot rows
+   (pivot columns in ascending order) to D', zero on every pivot column, then D' is brought to its
+   reduced row echelon form.  Both are unique. */
+gb_status gb_reduce_macaulay(gb_macaulay *mac, gb_echelon **out);
+gb_status gb_echelon_export(const gb_echelon *ech, gb_echelon_host *inout);
+gb_status gb_echelon_destroy(gb_echelon *ech);
+
+/* One F4 step (Sec. 4.2): select every critical pair of minimal lcm degree, build the rows of both
+   halves of each pair, run symbolic preprocessing with closure and the elimination, append the
+   echelon rows as new basis elements and update the pairs.  GB_DONE when no pair remains (nothing
+   is changed).  stats may be NULL. */
+gb_status gb_f4_step(gb_system *sys, gb_step_stats *stats);
+
+/* F4 steps until no pair remains, then the reduced Groebner basis: redundant elements dropped,
+   tails fully reduced, monic, sorted by leading monomial descending.  stats may be NULL. */
+gb_status gb_groebner(gb_system *sys, gb_run_stats *stats);
+
+/* The reduced basis after gb_groebner (reduced != 0), or the running basis in insertion order,
+   redundant elements included (reduced == 0). */
+gb_status gb_basis_export(const gb_system *sys, int reduced, gb_polys_host *inout);
+/* Redundancy flags of the running basis (one byte per element; two-call pattern on *count). */
+gb_status gb_basis_redundant(const gb_system *sys, uint32_t *count, uint8_t *flags);
+
+/* With GB_CTX_KEEP_STEP: borrowed handles to the last step's matrix and echelon form (valid until
+   the next step or the system's destruction). */
+gb_status gb_system_last_step(const gb_system *sys, const gb_macaulay **mac,
+                              const gb_echelon **ech);
+
+/* ---- batching and serving ------------------------------------------------------------------- */
+
+/* Run gb_groebner on `count` independent systems of one context, overlapping their device work
+   (each system on its own stream, host control on worker threads).  per_system may be NULL. */
+gb_status gb_batch_groebner(gb_ctx *ctx, uint32_t count, gb_system *const *systems,
+                            gb_run_stats *per_system);
+
+typedef struct {
+    size_t hbm_cap_bytes;  /* admission cap on the summed device footprint of admitted systems */
+    uint32_t max_slots;    /* systems running at once (0: 64) */
+    uint32_t reserved;
+} gb_server_opts;
+
+/* A continuous-batching server: submitted systems are admitted into free slots while their
+   estimated device footprint fits under the cap; each runs gb_groebner on its own stream while
+   others run.  Ownership of a submitted system moves to the server until it is returned by poll. */
+gb_status gb_server_create(gb_ctx *ctx, const gb_server_opts *opts, gb_server **out);
+gb_status gb_server_submit(gb_server *srv, gb_system *sys, uint64_t *ticket);
+/* GB_OK and *done = the system when finished (ownership returns to the caller, with its status in
+   *result); GB_EBUSY while it is queued or running. */
+gb_status gb_server_poll(gb_server *srv, uint64_t ticket, gb_system **done, gb_status *result);
+gb_status gb_server_destroy(gb_server *srv);
+
+/* ---- diagnostics ---------------------------------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched in this process so far (all contexts). */
+uint64_t gb_kernel_launches(void);
+
+/* ---- errors --------------------------------------------------------------------------------- */
+
+const char *gb_status_str(gb_status s);
+const char *gb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB_H */

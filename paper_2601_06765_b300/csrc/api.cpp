@@ -1,0 +1,427 @@
+// api.cpp -- the extern "C" entry points of include/gb.h: argument checks, handle lifetime,
+// exports to host arrays, error mapping, and the device arena.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+
+#include "internal.hpp"
+
+namespace gb {
+gb_status f4_step(gb_system *S, gb_step_stats *stats);
+gb_status groebner(gb_system *S, gb_run_stats *stats);
+void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F);
+std::vector<RowSpec> order_rows(const gb_system *S, std::vector<std::pair<Mono, uint32_t>> tk);
+
+static thread_local std::string t_last_error;
+std::atomic<unsigned long long> g_launches{0};
+
+void set_last_error(const std::string &msg) { t_last_error = msg; }
+
+void fail(gb_status s, const std::string &msg) { throw Error(s, msg); }
+
+void cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        throw Error(GB_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    throw Error(GB_EDEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---- arena ------------------------------------------------------------------------------------
+
+void Arena::init(void *base, size_t bytes, bool owned) {
+    std::lock_guard<std::mutex> g(mu_);
+    base_ = static_cast<char *>(base);
+    cap_ = bytes & ~size_t(255);
+    owned_ = owned;
+    used_ = 0;
+    free_.clear();
+    live_.clear();
+    pending_.clear();
+    if (cap_) free_[0] = cap_;
+}
+
+void Arena::release() {
+    std::lock_guard<std::mutex> g(mu_);
+    if (owned_ && base_) cudaFree(base_);
+    base_ = nullptr;
+    cap_ = used_ = 0;
+    free_.clear();
+    live_.clear();
+    pending_.clear();
+}
+
+void *Arena::alloc(size_t bytes) {
+    const size_t need = (std::max<size_t>(bytes, 1) + 255) & ~size_t(255);
+    std::lock_guard<std::mutex> g(mu_);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+        if (it->second < need) continue;
+        const size_t off = it->first, sz = it->second;
+        free_.erase(it);
+        if (sz > need) free_[off + need] = sz - need;
+        live_[off] = need;
+        used_ += need;
+        return base_ + off;
+    }
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "device arena exhausted: %zu bytes requested, %zu of %zu in use",
+                  need, used_, cap_);
+    throw Error(GB_ENOMEM, msg);
+}
+
+void Arena::free_locked(size_t off) {
+    auto it = live_.find(off);
+    if (it == live_.end()) return;
+    size_t sz = it->second;
+    live_.erase(it);
+    used_ -= sz;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && off + sz == nx->first) {
+        sz += nx->second;
+        nx = free_.erase(nx);
+    }
+    if (nx != free_.begin()) {
+        auto pv = std::prev(nx);
+        if (pv->first + pv->second == off) {
+            pv->second += sz;
+            return;
+        }
+    }
+    free_[off] = sz;
+}
+
+void Arena::defer_free(void *p, cudaStream_t s) {
+    if (!p || !base_) return;
+    std::lock_guard<std::mutex> g(mu_);
+    pending_.emplace(s, (size_t)(static_cast<char *>(p) - base_));
+}
+
+void Arena::flush(cudaStream_t s) {
+    std::lock_guard<std::mutex> g(mu_);
+    auto range = pending_.equal_range(s);
+    for (auto it = range.first; it != range.second; ++it) free_locked(it->second);
+    pending_.erase(range.first, range.second);
+}
+
+}  // namespace gb
+
+using namespace gb;
+
+#define GB_API_BEGIN try {
+#define GB_API_END                                      \
+    }                                                   \
+    catch (const gb::Error &e) {                        \
+        set_last_error(e.what());                       \
+        return e.st;                                    \
+    }                                                   \
+    catch (const std::bad_alloc &) {                    \
+        set_last_error("host allocation failed");       \
+        return GB_ENOMEM;                               \
+    }                                                   \
+    catch (const std::exception &e) {                   \
+        set_last_error(e.what());                       \
+        return GB_EDEVICE;                              \
+    }
+
+static void use_device(const gb_ctx *ctx) { GB_CUDA(cudaSetDevice(ctx->device)); }
+
+// order the system's work after whatever the caller queued on the context's stream
+static void enter(gb_system *S) {
+    use_device(S->ctx);
+    if (S->ctx->stream && S->stream != S->ctx->stream && !S->ctx->own_stream) {
+        GB_CUDA(cudaEventRecord(S->ev[7], S->ctx->stream));
+        GB_CUDA(cudaStreamWaitEvent(S->stream, S->ev[7], 0));
+    }
+}
+
+extern "C" {
+
+const char *gb_status_str(gb_status s) {
+    switch (s) {
+        case GB_OK: return "GB_OK";
+        case GB_DONE: return "GB_DONE";
+        case GB_EINVAL: return "GB_EINVAL";
+        case GB_ENOMEM: return "GB_ENOMEM";
+        case GB_EOVERFLOW: return "GB_EOVERFLOW";
+        case GB_ETIMEOUT: return "GB_ETIMEOUT";
+        case GB_EDEVICE: return "GB_EDEVICE";
+        case GB_EUNSUPPORTED: return "GB_EUNSUPPORTED";
+        case GB_EBUSY: return "GB_EBUSY";
+    }
+    return "unknown gb_status";
+}
+
+const char *gb_last_error(void) { return t_last_error.c_str(); }
+
+uint64_t gb_kernel_launches(void) { return g_launches.load(); }
+
+gb_status gb_ctx_create(int device, const gb_ctx_opts *opts, gb_ctx **out) {
+    GB_API_BEGIN
+    if (!out) fail(GB_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    GB_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) fail(GB_EINVAL, "no such CUDA device");
+    auto ctx = std::make_unique<gb_ctx>();
+    ctx->device = device;
+    GB_CUDA(cudaSetDevice(device));
+    gb_ctx_opts o{};
+    if (opts) o = *opts;
+    ctx->flags = o.flags;
+    if (o.stream) {
+        ctx->stream = static_cast<cudaStream_t>(o.stream);
+        ctx->own_stream = false;
+    } else {
+        GB_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    if (o.arena) {
+        if (!o.arena_bytes) fail(GB_EINVAL, "arena given without arena_bytes");
+        ctx->arena.init(o.arena, o.arena_bytes, false);
+    } else {
+        const size_t bytes = o.arena_bytes ? o.arena_bytes : (size_t(2) << 30);
+        void *p = nullptr;
+        GB_CUDA(cudaMalloc(&p, bytes));
+        ctx->arena.init(p, bytes, true);
+    }
+    *out = ctx.release();
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_ctx_destroy(gb_ctx *ctx) {
+    GB_API_BEGIN
+    if (!ctx) return GB_EINVAL;
+    use_device(ctx);
+    cudaDeviceSynchronize();
+    ctx->arena.release();
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_ctx_memory(const gb_ctx *ctx, size_t *used, size_t *capacity) {
+    if (!ctx) return GB_EINVAL;
+    if (used) *used = ctx->arena.used();
+    if (capacity) *capacity = ctx->arena.capacity();
+    return GB_OK;
+}
+
+gb_status gb_system_create(gb_ctx *ctx, uint32_t nvars, uint32_t p, gb_order order,
+                           const gb_polys *F, gb_system **out) {
+    GB_API_BEGIN
+    if (!ctx || !out) fail(GB_EINVAL, "null context or out");
+    *out = nullptr;
+    if (order != GB_GREVLEX) fail(GB_EUNSUPPORTED, "only grevlex is implemented");
+    if (F && F->npolys && (!F->poly_off || ((!F->exps || !F->coeffs) && F->poly_off[F->npolys])))
+        fail(GB_EINVAL, "null arrays in the input system");
+    use_device(ctx);
+    auto S = std::make_unique<gb_system>();
+    S->ctx = ctx;
+    GB_CUDA(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
+    S->own_stream = true;
+    for (auto &e : S->ev) GB_CUDA(cudaEventCreate(&e));
+    if (ctx->stream && !ctx->own_stream) {
+        GB_CUDA(cudaEventRecord(S->ev[7], ctx->stream));
+        GB_CUDA(cudaStreamWaitEvent(S->stream, S->ev[7], 0));
+    }
+    system_init(S.get(), nvars, p, F);
+    *out = S.release();
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_system_destroy(gb_system *S) {
+    GB_API_BEGIN
+    if (!S) return GB_EINVAL;
+    use_device(S->ctx);
+    cudaStreamSynchronize(S->stream);
+    S->last_ech.reset();
+    S->last_mac.reset();
+    S->bmon.reset();
+    S->bcf.reset();
+    S->boff.reset();
+    S->blen.reset();
+    S->ctx->arena.flush(S->stream);
+    if (S->pinned) cudaFreeHost(S->pinned);
+    for (auto &e : S->ev) cudaEventDestroy(e);
+    if (S->own_stream) cudaStreamDestroy(S->stream);
+    delete S;
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_symbolic_preprocess(gb_system *S, uint32_t r, const uint8_t *t_exps, const uint32_t *k,
+                                 int closure, gb_macaulay **out) {
+    GB_API_BEGIN
+    if (!S || !out || (r && (!t_exps || !k))) fail(GB_EINVAL, "null argument");
+    *out = nullptr;
+    enter(S);
+    std::vector<std::pair<Mono, uint32_t>> tk(r);
+    for (uint32_t i = 0; i < r; ++i) {
+        Mono t{};
+        std::memcpy(t.e, t_exps + (size_t)i * S->n, S->n);
+        tk[i] = {t, k[i]};
+    }
+    std::vector<RowSpec> rows = order_rows(S, std::move(tk));
+    std::vector<uint32_t> nonred;
+    for (uint32_t g = 0; g < S->redundant.size(); ++g)
+        if (!S->redundant[g]) nonred.push_back(g);
+    *out = symbolic_preprocess(S, rows, closure != 0, nonred).release();
+    return GB_OK;
+    GB_API_END
+}
+
+static void d2h(gb_system *S, void *dst, const void *src, size_t bytes) {
+    if (bytes) GB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, S->stream));
+}
+
+gb_status gb_macaulay_export(const gb_macaulay *M, gb_macaulay_host *h) {
+    GB_API_BEGIN
+    if (!M || !h) fail(GB_EINVAL, "null argument");
+    gb_system *S = M->sys;
+    use_device(S->ctx);
+    h->nvars = M->n;
+    h->nrows = M->nrows;
+    h->ndict = M->ndict;
+    h->npivot = M->nA;
+    h->nnz = M->nnz;
+    const uint32_t n = M->n;
+    if (h->row_ptr) d2h(S, h->row_ptr, M->row_ptr.p, 4ull * (M->nrows + 1));
+    if (h->col_ind) d2h(S, h->col_ind, M->col.p, 4ull * M->nnz);
+    if (h->val) d2h(S, h->val, M->val.p, 4ull * M->nnz);
+    if (h->row_k) d2h(S, h->row_k, M->row_k.p, 4ull * M->nrows);
+    std::vector<uint4> dict, rt;
+    std::vector<uint8_t> fl;
+    if (h->dict_exps) { dict.resize(M->ndict); d2h(S, dict.data(), M->dict.p, 16ull * M->ndict); }
+    if (h->row_t) { rt.resize(M->nrows); d2h(S, rt.data(), M->row_t.p, 16ull * M->nrows); }
+    if (h->row_flags) { fl.resize(M->nrows); d2h(S, fl.data(), M->row_flags.p, M->nrows); }
+    sync(S);
+    for (uint32_t i = 0; h->dict_exps && i < M->ndict; ++i)
+        std::memcpy(h->dict_exps + (size_t)i * n, &dict[i], n);
+    for (uint32_t i = 0; h->row_t && i < M->nrows; ++i) std::memcpy(h->row_t + (size_t)i * n, &rt[i], n);
+    for (uint32_t i = 0; h->row_flags && i < M->nrows; ++i) h->row_flags[i] = fl[i] & 3u;
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_macaulay_destroy(gb_macaulay *M) {
+    GB_API_BEGIN
+    if (!M) return GB_EINVAL;
+    delete M;
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_reduce_macaulay(gb_macaulay *M, gb_echelon **out) {
+    GB_API_BEGIN
+    if (!M || !out) fail(GB_EINVAL, "null argument");
+    *out = nullptr;
+    enter(M->sys);
+    *out = reduce_rows(M, true).release();
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_echelon_export(const gb_echelon *E, gb_echelon_host *h) {
+    GB_API_BEGIN
+    if (!E || !h) fail(GB_EINVAL, "null argument");
+    gb_system *S = E->mac->sys;
+    use_device(S->ctx);
+    h->nC = E->nC;
+    h->nb = E->nb;
+    h->rank = E->rank;
+    if (h->nonpiv) d2h(S, h->nonpiv, E->mac->nonpiv.p, 4ull * E->nb);
+    if (h->dprime) d2h(S, h->dprime, E->dprime.p, 4ull * E->nC * E->nb);
+    if (h->rref_piv) d2h(S, h->rref_piv, E->rpiv.p, 4ull * E->rank);
+    if (h->rref) d2h(S, h->rref, E->rref.p, 4ull * E->rank * E->nb);
+    sync(S);
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_echelon_destroy(gb_echelon *E) {
+    GB_API_BEGIN
+    if (!E) return GB_EINVAL;
+    delete E;
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_f4_step(gb_system *S, gb_step_stats *stats) {
+    GB_API_BEGIN
+    if (!S) fail(GB_EINVAL, "null system");
+    if (S->finished) return GB_DONE;
+    enter(S);
+    return f4_step(S, stats);
+    GB_API_END
+}
+
+gb_status gb_groebner(gb_system *S, gb_run_stats *stats) {
+    GB_API_BEGIN
+    if (!S) fail(GB_EINVAL, "null system");
+    enter(S);
+    return groebner(S, stats);
+    GB_API_END
+}
+
+gb_status gb_basis_export(const gb_system *S, int reduced, gb_polys_host *h) {
+    GB_API_BEGIN
+    if (!S || !h) fail(GB_EINVAL, "null argument");
+    const uint32_t n = S->n;
+    if (reduced) {
+        if (!S->finished) fail(GB_EINVAL, "the reduced basis exists after gb_groebner");
+        h->npolys = (uint32_t)S->fin_off.size() - 1;
+        h->nterms = S->fin_cf.size();
+        if (h->poly_off) std::memcpy(h->poly_off, S->fin_off.data(), 4 * S->fin_off.size());
+        if (h->exps) std::memcpy(h->exps, S->fin_exps.data(), S->fin_exps.size());
+        if (h->coeffs) std::memcpy(h->coeffs, S->fin_cf.data(), 4 * S->fin_cf.size());
+        return GB_OK;
+    }
+    gb_system *Sm = const_cast<gb_system *>(S);
+    use_device(S->ctx);
+    const uint32_t ng = (uint32_t)S->lm.size();
+    uint64_t T = 0;
+    for (uint32_t l : S->len) T += l;
+    h->npolys = ng;
+    h->nterms = T;
+    if (!h->poly_off && !h->exps && !h->coeffs) return GB_OK;
+    std::vector<uint4> mon(S->nterms);
+    std::vector<uint32_t> cf(S->nterms);
+    d2h(Sm, mon.data(), S->bmon.p, 16ull * S->nterms);
+    d2h(Sm, cf.data(), S->bcf.p, 4ull * S->nterms);
+    sync(Sm);
+    uint64_t o = 0;
+    for (uint32_t g = 0; g < ng; ++g) {
+        if (h->poly_off) h->poly_off[g] = (uint32_t)o;
+        for (uint32_t j = 0; j < S->len[g]; ++j, ++o) {
+            if (h->exps) std::memcpy(h->exps + o * n, &mon[S->off[g] + j], n);
+            if (h->coeffs) h->coeffs[o] = cf[S->off[g] + j];
+        }
+    }
+    if (h->poly_off) h->poly_off[ng] = (uint32_t)o;
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_basis_redundant(const gb_system *S, uint32_t *count, uint8_t *flags) {
+    if (!S || !count) return GB_EINVAL;
+    *count = (uint32_t)S->redundant.size();
+    if (flags) std::memcpy(flags, S->redundant.data(), S->redundant.size());
+    return GB_OK;
+}
+
+gb_status gb_system_last_step(const gb_system *S, const gb_macaulay **mac, const gb_echelon **ech) {
+    if (!S) return GB_EINVAL;
+    if (!S->last_mac || !S->last_ech) {
+        set_last_error("no step kept: create the context with GB_CTX_KEEP_STEP and run a step");
+        return GB_EINVAL;
+    }
+    if (mac) *mac = S->last_mac.get();
+    if (ech) *ech = S->last_ech.get();
+    return GB_OK;
+}
+
+}  // extern "C"

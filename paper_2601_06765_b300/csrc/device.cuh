@@ -1,0 +1,135 @@
+// device.cuh -- register-level primitives shared by the kernels: F_p arithmetic (Sec. 8) and
+// packed monomials with an injective, order-refining key (Sec. 7.3, Assumption 11.1).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gb {
+
+// ---------------------------------------------------------------------------------------------
+// F_p arithmetic.  Residues are standard representatives in [0, p), p odd, p < 2^31.
+//
+// Barrett (Sec. 8.3) with k = 64: mu = floor(2^64 / p).  For any x < 2^64,
+// q = floor(x * mu / 2^64) satisfies floor(x/p) - 1 <= q <= floor(x/p), so r = x - q p lies in
+// [0, 2p) and one predicated subtraction finishes.  This reduces lazily accumulated sums
+// (the lazy window of Rem. 8.1) and single products.
+//
+// Montgomery (Sec. 8.4) with R = 2^32 and p' = -p^{-1} mod R: redc(t) = (t + ((t mod R) p' mod R) p)
+// / R is congruent to t R^{-1} and lies in [0, 2p) for t < p R.  The sparse row update multiplies
+// every entry of a pivot row by one scalar f; with f converted once to f R mod p, redc(fR * v) is
+// f v mod p (up to one p) for a standard v, so the entries never leave standard form.
+// ---------------------------------------------------------------------------------------------
+struct Fp {
+    uint32_t p;
+    uint32_t pinv_neg;  // -p^{-1} mod 2^32
+    uint64_t mu;        // floor(2^64 / p)
+    uint32_t r2;        // R^2 mod p
+    uint32_t small;     // 1 when p < 2^16: products of residues fit in 32 bits
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fp_reduce(uint64_t x, const Fp &f) {
+    uint64_t q = __umul64hi(x, f.mu);
+    uint64_t r = x - q * (uint64_t)f.p;
+    return (uint32_t)(r >= f.p ? r - f.p : r);
+}
+
+__device__ __forceinline__ uint32_t fp_mul(uint32_t a, uint32_t b, const Fp &f) {
+    return fp_reduce((uint64_t)a * b, f);
+}
+
+__device__ __forceinline__ uint32_t fp_add(uint32_t a, uint32_t b, const Fp &f) {
+    uint32_t s = a + b;
+    return s >= f.p ? s - f.p : s;
+}
+
+__device__ __forceinline__ uint32_t fp_sub(uint32_t a, uint32_t b, const Fp &f) {
+    return a >= b ? a - b : a + f.p - b;
+}
+
+// t R^{-1} mod p, in [0, 2p), for t < p * 2^32
+__device__ __forceinline__ uint32_t fp_redc(uint64_t t, const Fp &f) {
+    uint32_t m = (uint32_t)t * f.pinv_neg;
+    return (uint32_t)((t + (uint64_t)m * f.p) >> 32);
+}
+
+// a R mod p in [0, p)
+__device__ __forceinline__ uint32_t fp_to_mont(uint32_t a, const Fp &f) {
+    uint32_t r = fp_redc((uint64_t)a * f.r2, f);
+    return r >= f.p ? r - f.p : r;
+}
+
+// a^{-1} mod p by the extended Euclidean algorithm (a != 0)
+__device__ __forceinline__ uint32_t fp_inv(uint32_t a, const Fp &f) {
+    int64_t r0 = f.p, r1 = a, s0 = 0, s1 = 1;
+    while (r1) {
+        int64_t q = r0 / r1, t;
+        t = r0 - q * r1; r0 = r1; r1 = t;
+        t = s0 - q * s1; s0 = s1; s1 = t;
+    }
+    if (s0 < 0) s0 += f.p;
+    return (uint32_t)s0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Monomials: n <= 16 exponents of 8 bits packed little-endian in a uint4 (byte i = exponent of
+// x_{i+1}).  Multiplication is a bytewise add; the library keeps every exponent and degree below
+// 256, so the four 32-bit adds never carry across bytes.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 mono_mul(uint4 a, uint4 b) {
+    return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ __forceinline__ uint4 mono_div(uint4 b, uint4 a) {  // requires a | b
+    return make_uint4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+}
+
+__device__ __forceinline__ bool mono_divides(uint4 a, uint4 b) {  // a | b: every byte a_i <= b_i
+    return (__vcmpleu4(a.x, b.x) & __vcmpleu4(a.y, b.y) & __vcmpleu4(a.z, b.z) &
+            __vcmpleu4(a.w, b.w)) == 0xFFFFFFFFu;
+}
+
+__device__ __forceinline__ uint32_t byte_of(uint4 m, int i) {
+    uint32_t w = i < 4 ? m.x : i < 8 ? m.y : i < 12 ? m.z : m.w;
+    return (w >> (8 * (i & 3))) & 0xFFu;
+}
+
+// Dense grevlex rank: the position of x^a among all monomials in n variables, ascending in grevlex
+// with x1 > ... > xn.  With S_j = a_1 + ... + a_j and d = S_n:
+//     rank(a) = C(n + d - 1, n) + sum_{j=1}^{n-1} C(S_j + j - 1, j).
+// C(n + d - 1, n) counts the monomials of degree < d.  Within degree d, a monomial b is smaller
+// than a iff at the last index where they differ b has the larger exponent; fixing b_n..b_{j+2} to
+// a's and letting b_{j+1} exceed a_{j+1} leaves the first j variables to share a total below S_j,
+// which C(S_j + j - 1, j) counts.  The rank is injective and order-preserving (Assumption 11.1),
+// so it serves as MonKey, and as a bitmap index in [0, C(n + D, n)) for degrees <= D.
+//
+// tab (shared memory): tab[d] = C(n + d - 1, n) for d in [0, D], then for j = 1..n-1 the row
+// tab[(D+1) * j + s] = C(s + j - 1, j) for s in [0, D].
+__device__ __forceinline__ uint32_t mono_rank(uint4 m, const uint32_t *tab, int n, int D1) {
+    uint32_t r = 0, s = 0;
+    uint32_t w[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (i >= n) break;
+        if (i >= 1) r += tab[D1 * i + s];
+        s += (w[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+    }
+    return r + tab[s];
+}
+
+__device__ __forceinline__ uint32_t mono_deg(uint4 m) {
+    return __dp4a(m.x, 0x01010101u, 0u) + __dp4a(m.y, 0x01010101u, 0u) +
+           __dp4a(m.z, 0x01010101u, 0u) + __dp4a(m.w, 0x01010101u, 0u);
+}
+
+// column of a monomial in the dictionary: the dictionary is the set bits of `bits` (indexed by
+// rank) in descending order, word_prefix[w] = set bits in words [0, w)
+__device__ __forceinline__ uint32_t rank_to_col(uint32_t r, const uint32_t *bits,
+                                                const uint32_t *word_prefix, uint32_t N) {
+    uint32_t w = r >> 5, below = bits[w] & ((1u << (r & 31)) - 1u);
+    return N - 1u - (word_prefix[w] + __popc(below));
+}
+
+#endif  // __CUDACC__
+
+}  // namespace gb

@@ -1,0 +1,233 @@
+// internal.hpp -- host-side structures of the library behind include/gb.h.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/gb.h"
+#include "device.cuh"
+
+namespace gb {
+
+// ---- errors ---------------------------------------------------------------------------------
+struct Error : std::runtime_error {
+    gb_status st;
+    Error(gb_status s, const std::string &m) : std::runtime_error(m), st(s) {}
+};
+[[noreturn]] void fail(gb_status s, const std::string &msg);
+void cuda_check(cudaError_t e, const char *what);
+#define GB_CUDA(x) ::gb::cuda_check((x), #x)
+void set_last_error(const std::string &msg);
+
+// every kernel launch site calls counted() right after its <<<...>>>
+extern std::atomic<unsigned long long> g_launches;
+inline void counted(unsigned k = 1) {
+    g_launches.fetch_add(k, std::memory_order_relaxed);
+    GB_CUDA(cudaGetLastError());
+}
+
+// ---- device memory: a first-fit arena over one device allocation ------------------------------
+// The arena is either caller-owned device memory (for instance a torch tensor) or one cudaMalloc
+// made when the context is created.  Blocks are 256-byte aligned.  Thread-safe.
+// A block is only ever used by work on the stream that allocated it.  Freeing is deferred: a
+// block freed on stream s becomes reusable after flush(s), which callers invoke right after
+// synchronising s, so no kernel still queued on s can touch a block handed out again.
+class Arena {
+  public:
+    void init(void *base, size_t bytes, bool owned);
+    void release();
+    void *alloc(size_t bytes);  // throws Error(GB_ENOMEM)
+    void defer_free(void *p, cudaStream_t s);
+    void flush(cudaStream_t s);  // s has been synchronised: its deferred blocks are free again
+    size_t used() const { return used_; }
+    size_t capacity() const { return cap_; }
+
+  private:
+    void free_locked(size_t off);
+    char *base_ = nullptr;
+    size_t cap_ = 0, used_ = 0;
+    bool owned_ = false;
+    std::map<size_t, size_t> free_;  // offset -> size
+    std::map<size_t, size_t> live_;  // offset -> size
+    std::multimap<cudaStream_t, size_t> pending_;
+    std::mutex mu_;
+};
+
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    Arena *a = nullptr;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept { *this = std::move(o); }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) {
+            reset();
+            p = o.p; n = o.n; a = o.a; s = o.s;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { reset(); }
+    void alloc(Arena &ar, size_t count, cudaStream_t stream) {
+        reset();
+        a = &ar;
+        s = stream;
+        n = count;
+        p = static_cast<T *>(ar.alloc(sizeof(T) * (count ? count : 1)));
+    }
+    // grow to at least `count` elements, keeping the first `keep` elements (stream-ordered copy)
+    void grow(Arena &ar, size_t count, size_t keep, cudaStream_t stream) {
+        if (count <= n && p) return;
+        DBuf<T> nb;
+        nb.alloc(ar, count, stream);
+        if (keep && p)
+            GB_CUDA(cudaMemcpyAsync(nb.p, p, sizeof(T) * keep, cudaMemcpyDeviceToDevice, stream));
+        *this = std::move(nb);
+    }
+    void reset() {
+        if (p && a) a->defer_free(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return sizeof(T) * n; }
+};
+
+// ---- host monomials (same packing as the device: byte i = exponent of x_{i+1}) ---------------
+struct Mono {
+    uint8_t e[16];
+};
+inline bool operator==(const Mono &a, const Mono &b) { return std::memcmp(a.e, b.e, 16) == 0; }
+int mono_deg(const Mono &a, int n);
+int mono_cmp(const Mono &a, const Mono &b, int n);  // grevlex: +1 a > b, -1 a < b, 0 equal
+Mono mono_mul(const Mono &a, const Mono &b, int n);
+Mono mono_div(const Mono &b, const Mono &a, int n);
+Mono mono_lcm(const Mono &a, const Mono &b, int n);
+bool mono_divides(const Mono &a, const Mono &b, int n);
+bool mono_coprime(const Mono &a, const Mono &b, int n);
+inline uint4 to_u4(const Mono &m) {
+    uint4 r;
+    std::memcpy(&r, m.e, 16);
+    return r;
+}
+
+Fp make_fp(uint32_t p);
+uint32_t host_inv(uint32_t a, uint32_t p);
+
+// ---- rows handed to symbolic preprocessing -------------------------------------------------
+struct RowSpec {
+    Mono t;
+    uint32_t k;
+    uint8_t pivot;  // chosen pivot among given rows sharing a leading monomial
+    uint8_t skip;   // 1: the first term of g_k is left out (tail rows of the final reduction)
+};
+
+struct Pair {
+    uint32_t i, j;
+};
+
+}  // namespace gb
+
+// ---- handles ---------------------------------------------------------------------------------
+struct gb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint32_t flags = 0;
+    gb::Arena arena;
+};
+
+// The materialised plan Pi of one batch (Def. 5.2) on the device.
+struct gb_macaulay {
+    gb_system *sys = nullptr;
+    uint32_t n = 0, degree = 0, nrows = 0, ndict = 0, nA = 0, nC = 0, nb = 0;
+    uint32_t closure_rounds = 0;
+    uint64_t nnz = 0;
+    gb::DBuf<uint32_t> row_ptr, col, val;  // CSR, val in [0, p)
+    gb::DBuf<uint4> dict;                  // descending monomials
+    gb::DBuf<uint4> row_t;
+    gb::DBuf<uint32_t> row_k;
+    gb::DBuf<uint8_t> row_flags;           // bit0 pivot, bit1 reducer, bit2 tail row
+    gb::DBuf<uint32_t> pcols;              // nA pivot columns ascending (pivot row i has lm pcols[i])
+    gb::DBuf<uint32_t> nonpiv;             // nb non-pivot columns ascending
+    gb::DBuf<uint32_t> colpos;             // ndict: position of a column among pivots / non-pivots
+    float ms_sp = 0.f;
+};
+
+// D' and RREF(D') on the device.
+struct gb_echelon {
+    gb_macaulay *mac = nullptr;
+    uint32_t nC = 0, nb = 0, rank = 0;
+    gb::DBuf<uint32_t> dprime;  // nC x nb
+    gb::DBuf<uint32_t> rref;    // rank x nb, rows in pivot order
+    gb::DBuf<uint32_t> rpiv;    // rank pivot positions (ascending)
+    uint64_t work[2] = {0, 0};  // pivot-row applications, mod-p multiply-adds of the reduction
+    float ms_reduce = 0.f, ms_rref = 0.f;
+};
+
+struct gb_system {
+    gb_ctx *ctx = nullptr;
+    uint32_t n = 0, p = 0;
+    gb::Fp fp{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev[8] = {};
+    // host mirror of the basis metadata
+    std::vector<gb::Mono> lm;
+    std::vector<uint32_t> off, len;
+    std::vector<uint8_t> redundant;
+    std::vector<gb::Pair> pairs;
+    // device basis: terms of element k are [off[k], off[k] + len[k]) of bmon / bcf
+    gb::DBuf<uint4> bmon;
+    gb::DBuf<uint32_t> bcf;
+    gb::DBuf<uint32_t> boff, blen;
+    uint64_t nterms = 0;
+    // pinned staging for small transfers
+    void *pinned = nullptr;
+    size_t pinned_bytes = 0;
+    // kept objects of the last step (GB_CTX_KEEP_STEP)
+    std::unique_ptr<gb_macaulay> last_mac;
+    std::unique_ptr<gb_echelon> last_ech;
+    // progress
+    uint32_t steps = 0;
+    bool unit = false;       // a constant input or element: the ideal is R
+    bool finished = false;
+    gb_run_stats run{};
+    // the reduced basis after gb_groebner
+    std::vector<uint32_t> fin_off;
+    std::vector<uint8_t> fin_exps;
+    std::vector<uint32_t> fin_cf;
+    // estimate of the device footprint (server admission)
+    size_t footprint = 0;
+};
+
+namespace gb {
+// pipeline stages (sp.cu, reduce.cu)
+std::unique_ptr<gb_macaulay> symbolic_preprocess(gb_system *S, const std::vector<RowSpec> &rows,
+                                                 bool closure, const std::vector<uint32_t> &nonred);
+std::unique_ptr<gb_echelon> reduce_rows(gb_macaulay *M, bool echelon);
+// append the echelon rows as new basis elements on the device; returns their LMs and lengths
+void append_echelon(gb_system *S, gb_echelon *E, std::vector<Mono> &lms, std::vector<uint32_t> &lens);
+// tails of the final reduction: new coefficient arrays for the given elements
+void replace_tails(gb_system *S, gb_echelon *E, const std::vector<uint32_t> &elems,
+                   std::vector<uint32_t> &off, std::vector<uint8_t> &exps, std::vector<uint32_t> &cf);
+void *pinned(gb_system *S, size_t bytes);
+// cudaStreamSynchronize on the system's stream, then release its deferred arena blocks
+void sync(gb_system *S);
+// exclusive scan of n u32 values on the stream; out has n + 1 entries (out[n] = total)
+void exclusive_scan(Arena &ar, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t s);
+}  // namespace gb
