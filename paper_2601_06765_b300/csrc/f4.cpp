@@ -198,10 +198,14 @@ static void append_host_poly(gb_system *S, const std::vector<Mono> &mon, const s
     const uint32_t len = (uint32_t)mon.size();
     const uint64_t base = S->nterms;
     const size_t ng0 = S->off.size();
-    S->bmon.grow(ar, std::max<size_t>(base + len, std::max<size_t>(1024, 2 * S->bmon.n)), base, st);
-    S->bcf.grow(ar, std::max<size_t>(base + len, std::max<size_t>(1024, 2 * S->bcf.n)), base, st);
-    S->boff.grow(ar, std::max<size_t>(ng0 + 1, std::max<size_t>(64, 2 * S->boff.n)), ng0, st);
-    S->blen.grow(ar, std::max<size_t>(ng0 + 1, std::max<size_t>(64, 2 * S->blen.n)), ng0, st);
+    if (base + len > S->bmon.n) {
+        S->bmon.grow(ar, std::max<size_t>(base + len, std::max<size_t>(1024, 2 * S->bmon.n)), base, st);
+        S->bcf.grow(ar, std::max<size_t>(base + len, std::max<size_t>(1024, 2 * S->bcf.n)), base, st);
+    }
+    if (ng0 + 1 > S->boff.n) {
+        S->boff.grow(ar, std::max<size_t>(ng0 + 1, std::max<size_t>(64, 2 * S->boff.n)), ng0, st);
+        S->blen.grow(ar, std::max<size_t>(ng0 + 1, std::max<size_t>(64, 2 * S->blen.n)), ng0, st);
+    }
     char *h = static_cast<char *>(pinned(S, 20ull * len + 64));
     sync(S);  // earlier uploads from the staging buffer have landed
     std::vector<uint4> m4(len);

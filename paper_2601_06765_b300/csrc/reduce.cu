@@ -181,9 +181,11 @@ __global__ void __launch_bounds__(PT) k_panel_solve(uint32_t *__restrict__ R, ui
     if (threadIdx.x == 0) X.state[1] = nnew;
 }
 
-// E_e -= sum_k E_e[newpiv_k] * New_k for the rows that existed before this panel
+// E_e -= sum_k E_e[newpiv_k] * New_k for the rows that existed before this panel.  One block
+// owns a whole row: the multipliers are entries of the row being rewritten, so they are read
+// before any thread of the block writes it.
 __global__ void k_panel_merge(Ech X, Fp fp) {
-    extern __shared__ uint32_t m[];
+    __shared__ uint32_t m[64];
     const uint32_t e = blockIdx.x, nb = X.nb;
     const uint32_t rho = X.state[0], nnew = X.state[1];
     if (e >= rho || nnew == 0) return;
@@ -191,12 +193,12 @@ __global__ void k_panel_merge(Ech X, Fp fp) {
     const uint32_t *New = X.E + (size_t)rho * nb;
     for (uint32_t k = threadIdx.x; k < nnew; k += blockDim.x) m[k] = row[X.epiv[rho + k]];
     __syncthreads();
-    const uint32_t j = blockIdx.y * blockDim.x + threadIdx.x;
-    if (j >= nb) return;
-    uint64_t acc = row[j];
-    for (uint32_t k = 0; k < nnew; ++k)
-        if (m[k]) acc += fp_mul(fp.p - m[k], New[(size_t)k * nb + j], fp);
-    row[j] = fp_reduce(acc, fp);
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+        uint64_t acc = row[j];
+        for (uint32_t k = 0; k < nnew; ++k)
+            if (m[k]) acc += fp_mul(fp.p - m[k], New[(size_t)k * nb + j], fp);
+        row[j] = fp_reduce(acc, fp);
+    }
 }
 
 __global__ void k_panel_commit(Ech X) { X.state[0] += X.state[1]; }
@@ -335,7 +337,7 @@ std::unique_ptr<gb_echelon> reduce_rows(gb_macaulay *Mac, bool echelon) {
             counted();
             k_panel_solve<<<1, PT, 0, st>>>(R.p, rows, X, S->fp);
             counted();
-            k_panel_merge<<<dim3(cap, blocks(nb, 256)), 256, sizeof(uint32_t) * 64, st>>>(X, S->fp);
+            k_panel_merge<<<cap, 256, 0, st>>>(X, S->fp);
             counted();
             k_panel_commit<<<1, 1, 0, st>>>(X);
             counted();
@@ -403,10 +405,14 @@ void append_echelon(gb_system *S, gb_echelon *E, std::vector<Mono> &lms, std::ve
         noff[e] = (uint32_t)(base + hoff[e]);
         nlen[e] = hoff[e + 1] - hoff[e];
     }
-    S->bmon.grow(ar, std::max<size_t>(base + add, 2 * S->bmon.n), base, st);
-    S->bcf.grow(ar, std::max<size_t>(base + add, 2 * S->bcf.n), base, st);
-    S->boff.grow(ar, std::max<size_t>(ng0 + rank, 2 * S->boff.n), ng0, st);
-    S->blen.grow(ar, std::max<size_t>(ng0 + rank, 2 * S->blen.n), ng0, st);
+    if (base + add > S->bmon.n) {
+        S->bmon.grow(ar, std::max<size_t>(base + add, 2 * S->bmon.n), base, st);
+        S->bcf.grow(ar, std::max<size_t>(base + add, 2 * S->bcf.n), base, st);
+    }
+    if (ng0 + rank > S->boff.n) {
+        S->boff.grow(ar, std::max<size_t>(ng0 + rank, 2 * S->boff.n), ng0, st);
+        S->blen.grow(ar, std::max<size_t>(ng0 + rank, 2 * S->blen.n), ng0, st);
+    }
     uint32_t *hb = reinterpret_cast<uint32_t *>(h);  // the read-back above is complete
     std::memcpy(hb, noff.data(), 4ull * rank);
     std::memcpy(hb + rank, nlen.data(), 4ull * rank);
