@@ -193,7 +193,8 @@ def run_ours(args) -> None:
                 "traffic": profile_traffic("k_reduce_config2")}
 
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
-             for k in ("ms_sp", "ms_reduce", "ms_rref", "ms_update", "ms_wall")}
+             for k in ("ms_sp", "ms_reduce", "ms_rref", "ms_update", "ms_pairs", "ms_select",
+                       "ms_wall")}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(system)

@@ -118,7 +118,9 @@ typedef struct {
     float ms_sp;       /* device time: symbolic preprocessing (DictBuild + RowAssemble) */
     float ms_reduce;   /* device time: sparse reduction of the non-pivot rows */
     float ms_rref;     /* device time: reduced echelon form of D' */
-    float ms_update;   /* device time: reconstruction of the new elements */
+    float ms_update;   /* wall time: reconstruction of the new elements on the device */
+    float ms_pairs;    /* host time: critical-pair update (Gebauer-Moeller) for the new elements */
+    float ms_select;   /* host time: pair selection and ordering of the step's rows */
     double ms_wall;    /* host wall time of the step */
 } gb_step_stats;
 
@@ -126,7 +128,7 @@ typedef struct {
     uint32_t steps, nbasis;
     uint64_t nnz_total;
     uint64_t axpy_rows, axpy_fma;
-    double ms_sp, ms_reduce, ms_rref, ms_update, ms_wall;
+    double ms_sp, ms_reduce, ms_rref, ms_update, ms_pairs, ms_select, ms_wall;
 } gb_run_stats;
 
 /* ---- context -------------------------------------------------------------------------------- */

@@ -25,6 +25,8 @@ struct Fp {
     uint64_t mu;        // floor(2^64 / p)
     uint32_t r2;        // R^2 mod p
     uint32_t small;     // 1 when p < 2^16: products of residues fit in 32 bits
+    uint32_t mu32;      // floor(2^32 / p), for the 32-bit Barrett reduction (p < 2^16)
+    uint32_t pad;
 };
 
 #ifdef __CUDACC__
@@ -32,6 +34,13 @@ __device__ __forceinline__ uint32_t fp_reduce(uint64_t x, const Fp &f) {
     uint64_t q = __umul64hi(x, f.mu);
     uint64_t r = x - q * (uint64_t)f.p;
     return (uint32_t)(r >= f.p ? r - f.p : r);
+}
+
+// x mod p for x < 2^32 and p < 2^16: Barrett with k = 32 (same argument as above, one correction)
+__device__ __forceinline__ uint32_t fp_reduce32(uint32_t x, const Fp &f) {
+    const uint32_t q = __umulhi(x, f.mu32);
+    const uint32_t r = x - q * f.p;
+    return r >= f.p ? r - f.p : r;
 }
 
 __device__ __forceinline__ uint32_t fp_mul(uint32_t a, uint32_t b, const Fp &f) {
@@ -59,16 +68,31 @@ __device__ __forceinline__ uint32_t fp_to_mont(uint32_t a, const Fp &f) {
     return r >= f.p ? r - f.p : r;
 }
 
-// a^{-1} mod p by the extended Euclidean algorithm (a != 0)
+// a^{-1} mod p (0 < a < p, p odd) by the binary extended Euclidean algorithm (Menezes, van
+// Oorschot, Vanstone, Handbook of Applied Cryptography, Alg. 14.61 in its modular-inverse form):
+// shifts and subtractions on 32-bit values only, about 2 log2(p) iterations, no division.
+// Invariants: x1 a = u and x2 a = v (mod p); the loop ends when u or v reaches 1.
 __device__ __forceinline__ uint32_t fp_inv(uint32_t a, const Fp &f) {
-    int64_t r0 = f.p, r1 = a, s0 = 0, s1 = 1;
-    while (r1) {
-        int64_t q = r0 / r1, t;
-        t = r0 - q * r1; r0 = r1; r1 = t;
-        t = s0 - q * s1; s0 = s1; s1 = t;
+    const uint32_t p = f.p;
+    uint32_t u = a, v = p, x1 = 1, x2 = 0;
+    while (u != 1 && v != 1) {
+        while (!(u & 1)) {
+            u >>= 1;
+            x1 = (x1 & 1) ? (uint32_t)(((uint64_t)x1 + p) >> 1) : x1 >> 1;
+        }
+        while (!(v & 1)) {
+            v >>= 1;
+            x2 = (x2 & 1) ? (uint32_t)(((uint64_t)x2 + p) >> 1) : x2 >> 1;
+        }
+        if (u >= v) {
+            u -= v;
+            x1 = x1 >= x2 ? x1 - x2 : x1 + p - x2;
+        } else {
+            v -= u;
+            x2 = x2 >= x1 ? x2 - x1 : x2 + p - x1;
+        }
     }
-    if (s0 < 0) s0 += f.p;
-    return (uint32_t)s0;
+    return u == 1 ? x1 : x2;
 }
 
 // ---------------------------------------------------------------------------------------------

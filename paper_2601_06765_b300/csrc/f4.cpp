@@ -27,10 +27,16 @@ int mono_deg(const Mono &a, int n) {
 }
 
 int mono_cmp(const Mono &a, const Mono &b, int n) {
-    const int da = mono_deg(a, n), db = mono_deg(b, n);
+    // equal degrees: the last differing exponent decides, the smaller one giving the larger
+    // monomial.  With byte i = exponent of x_{i+1} (bytes >= n zero), the last differing byte is
+    // the most significant differing byte of the 128-bit little-endian word, so the words compare
+    // in reverse.
+    const M16 x = m16(a), y = m16(b);
+    const uint32_t da = deg16(x), db = deg16(y);
+    (void)n;
     if (da != db) return da > db ? 1 : -1;
-    for (int i = n - 1; i >= 0; --i)  // the last differing exponent decides: smaller is larger
-        if (a.e[i] != b.e[i]) return a.e[i] < b.e[i] ? 1 : -1;
+    if (x.hi != y.hi) return x.hi < y.hi ? 1 : -1;
+    if (x.lo != y.lo) return x.lo < y.lo ? 1 : -1;
     return 0;
 }
 
@@ -80,6 +86,7 @@ Fp make_fp(uint32_t p) {
     const unsigned __int128 R = (unsigned __int128)1 << 64;
     f.r2 = (uint32_t)(R % p);
     f.small = p < 65536u ? 1u : 0u;
+    f.mu32 = (uint32_t)(0xFFFFFFFFu / p);  // = floor(2^32 / p) since p does not divide 2^32
     return f;
 }
 
@@ -103,7 +110,8 @@ void *pinned(gb_system *S, size_t bytes) {
             GB_CUDA(cudaFreeHost(S->pinned));
             S->pinned = nullptr;
         }
-        const size_t sz = std::max<size_t>(bytes, 2 * S->pinned_bytes);
+        // page-locked allocations cost about a millisecond each: start at 1 MiB, grow 4x
+        const size_t sz = std::max<size_t>({bytes, 4 * S->pinned_bytes, size_t(1) << 20});
         GB_CUDA(cudaHostAlloc(&S->pinned, sz, cudaHostAllocDefault));
         S->pinned_bytes = sz;
     }
@@ -116,43 +124,88 @@ void sync(gb_system *S) {
 }
 
 // ---- critical pairs: UPDATE of Becker and Weispfenning (Gebauer-Moeller criteria) --------------
+//
+// Leading monomials are compared as SWAR words (internal.hpp) while every exponent is below 128;
+// beyond that the bytewise routines above are used.  Pair lcms are cached with the pair.
+
+namespace {
+struct MonoOps {
+    int n;
+    bool swar;
+    bool divides(const M16 &a, const M16 &b, const Mono &ma, const Mono &mb) const {
+        return swar ? divides16(a, b) : mono_divides(ma, mb, n);
+    }
+};
+}  // namespace
 
 static void gm_update(gb_system *S, uint32_t h) {
     const int n = (int)S->n;
     const Mono &lh = S->lm[h];
+    const M16 lh16 = S->lm16[h];
+    const bool swar = S->swar;
+    auto lcm_of = [&](uint32_t a, uint32_t b) -> M16 {
+        if (swar) return lcm16(S->lm16[a], S->lm16[b]);
+        return m16(mono_lcm(S->lm[a], S->lm[b], n));
+    };
+    auto divides = [&](const M16 &a, const M16 &b) -> bool {
+        if (swar) return divides16(a, b);
+        Mono x, y;
+        std::memcpy(x.e, &a, 16);
+        std::memcpy(y.e, &b, 16);
+        return mono_divides(x, y, n);
+    };
+    auto coprime = [&](uint32_t a) -> bool {
+        return swar ? coprime16(lh16, S->lm16[a]) : mono_coprime(lh, S->lm[a], n);
+    };
     std::vector<uint32_t> C;
+    C.reserve(h);
     for (uint32_t g = 0; g < h; ++g)
         if (!S->redundant[g]) C.push_back(g);
-    std::vector<Mono> L(C.size());
-    for (size_t a = 0; a < C.size(); ++a) L[a] = mono_lcm(lh, S->lm[C[a]], n);
+    std::vector<M16> L(C.size());
+    for (size_t a = 0; a < C.size(); ++a) L[a] = lcm_of(h, C[a]);
     // pairs (h, g), oldest g first: keep one when its leading monomials are coprime, or when no
     // pair still waiting or already kept has an lcm dividing its lcm
-    std::vector<char> kept(C.size(), 0);
+    std::vector<char> kept(C.size(), 0), cop(C.size(), 0);
     for (size_t a = 0; a < C.size(); ++a) {
+        cop[a] = coprime(C[a]);
         bool keep = true;
-        if (!mono_coprime(lh, S->lm[C[a]], n)) {
+        if (!cop[a]) {
             for (size_t b = a + 1; b < C.size() && keep; ++b)
-                if (mono_divides(L[b], L[a], n)) keep = false;
+                if (divides(L[b], L[a])) keep = false;
             for (size_t b = 0; b < a && keep; ++b)
-                if (kept[b] && mono_divides(L[b], L[a], n)) keep = false;
+                if (kept[b] && divides(L[b], L[a])) keep = false;
         }
         kept[a] = keep;
     }
     // old pairs whose lcm LM(h) divides, with both lcm(g1, h) and lcm(g2, h) different, go
-    std::vector<Pair> nb;
-    nb.reserve(S->pairs.size() + C.size());
-    for (const Pair &q : S->pairs) {
-        const Mono l12 = mono_lcm(S->lm[q.i], S->lm[q.j], n);
-        const bool drop = mono_divides(lh, l12, n) && !(mono_lcm(S->lm[q.i], lh, n) == l12) &&
-                          !(mono_lcm(S->lm[q.j], lh, n) == l12);
-        if (!drop) nb.push_back(q);
+    size_t w = 0;
+    for (size_t q = 0; q < S->pairs.size(); ++q) {
+        const PairL &pr = S->pairs[q];
+        bool drop = divides(lh16, pr.lcm);
+        if (drop) drop = !(lcm_of(pr.i, h) == pr.lcm) && !(lcm_of(pr.j, h) == pr.lcm);
+        if (!drop) S->pairs[w++] = pr;
     }
+    S->pairs.resize(w);
     // kept new pairs, except those with coprime leading monomials (Buchberger's product criterion)
     for (size_t a = 0; a < C.size(); ++a)
-        if (kept[a] && !mono_coprime(lh, S->lm[C[a]], n)) nb.push_back(Pair{C[a], h});
-    S->pairs.swap(nb);
+        if (kept[a] && !cop[a]) {
+            PairL pr{C[a], h, 0, 0, L[a]};
+            Mono l;
+            std::memcpy(l.e, &L[a], 16);
+            pr.deg = (uint32_t)mono_deg(l, n);
+            S->pairs.push_back(pr);
+        }
     for (uint32_t g = 0; g < h; ++g)
-        if (!S->redundant[g] && mono_divides(lh, S->lm[g], n)) S->redundant[g] = 1;
+        if (!S->redundant[g] && divides(lh16, S->lm16[g])) S->redundant[g] = 1;
+}
+
+// record a new leading monomial (SWAR form, and whether the fast comparisons still apply)
+static void push_lm(gb_system *S, const Mono &m) {
+    S->lm.push_back(m);
+    S->lm16.push_back(m16(m));
+    for (uint32_t i = 0; i < S->n; ++i)
+        if (m.e[i] >= 128) S->swar = false;
+    S->redundant.push_back(0);
 }
 
 static std::vector<uint32_t> nonredundant(const gb_system *S) {
@@ -223,8 +276,7 @@ static void append_host_poly(gb_system *S, const std::vector<Mono> &mon, const s
     S->nterms = base + len;
     S->off.push_back((uint32_t)base);
     S->len.push_back(len);
-    S->lm.push_back(mon[0]);
-    S->redundant.push_back(0);
+    push_lm(S, mon[0]);
     if (mono_deg(mon[0], (int)S->n) == 0) S->unit = true;
     gm_update(S, (uint32_t)(S->lm.size() - 1));
 }
@@ -303,30 +355,32 @@ gb_status f4_step(gb_system *S, gb_step_stats *stats) {
     if (S->pairs.empty()) return GB_DONE;
     const int n = (int)S->n;
     // normal strategy: every pair of minimal lcm degree
-    int dmin = 1 << 30;
-    for (const Pair &q : S->pairs) dmin = std::min(dmin, mono_deg(mono_lcm(S->lm[q.i], S->lm[q.j], n), n));
+    uint32_t dmin = UINT32_MAX;
+    for (const PairL &q : S->pairs) dmin = std::min(dmin, q.deg);
     if (dmin > 255) fail(GB_EOVERFLOW, "step degree above 255");
     std::vector<std::pair<Mono, uint32_t>> tk;
-    std::vector<Pair> rest;
+    std::vector<PairL> rest;
     uint32_t npairs = 0;
-    for (const Pair &q : S->pairs) {
-        const Mono l = mono_lcm(S->lm[q.i], S->lm[q.j], n);
-        if (mono_deg(l, n) != dmin) { rest.push_back(q); continue; }
+    for (const PairL &q : S->pairs) {
+        if (q.deg != dmin) { rest.push_back(q); continue; }
         ++npairs;
+        Mono l;
+        std::memcpy(l.e, &q.lcm, 16);
         tk.emplace_back(mono_div(l, S->lm[q.i], n), q.i);
         tk.emplace_back(mono_div(l, S->lm[q.j], n), q.j);
     }
     S->pairs.swap(rest);
     std::vector<RowSpec> rows = order_rows(S, std::move(tk));
+    const auto ts = std::chrono::steady_clock::now();
     auto mac = symbolic_preprocess(S, rows, true, nonredundant(S));
     auto ech = reduce_rows(mac.get(), true);
     const auto t1 = std::chrono::steady_clock::now();
     std::vector<Mono> lms;
     std::vector<uint32_t> lens;
     append_echelon(S, ech.get(), lms, lens);
+    const auto tp = std::chrono::steady_clock::now();
     for (size_t e = 0; e < lms.size(); ++e) {
-        S->lm.push_back(lms[e]);
-        S->redundant.push_back(0);
+        push_lm(S, lms[e]);
         if (mono_deg(lms[e], n) == 0) S->unit = true;
         gm_update(S, (uint32_t)(S->lm.size() - 1));
     }
@@ -350,7 +404,9 @@ gb_status f4_step(gb_system *S, gb_step_stats *stats) {
     st.ms_sp = mac->ms_sp;
     st.ms_reduce = ech->ms_reduce;
     st.ms_rref = ech->ms_rref;
-    st.ms_update = (float)std::chrono::duration<double, std::milli>(t2 - t1).count();
+    st.ms_update = (float)std::chrono::duration<double, std::milli>(tp - t1).count();
+    st.ms_pairs = (float)std::chrono::duration<double, std::milli>(t2 - tp).count();
+    st.ms_select = (float)std::chrono::duration<double, std::milli>(ts - t0).count();
     st.ms_wall = std::chrono::duration<double, std::milli>(t2 - t0).count();
     S->run.steps = S->steps;
     S->run.nnz_total += st.nnz;
@@ -360,6 +416,8 @@ gb_status f4_step(gb_system *S, gb_step_stats *stats) {
     S->run.ms_reduce += st.ms_reduce;
     S->run.ms_rref += st.ms_rref;
     S->run.ms_update += st.ms_update;
+    S->run.ms_pairs += st.ms_pairs;
+    S->run.ms_select += st.ms_select;
     S->run.ms_wall += st.ms_wall;
     if (stats) *stats = st;
     if (S->ctx->flags & GB_CTX_KEEP_STEP) {
@@ -385,6 +443,8 @@ void finish(gb_system *S) {
         }
         if (!drop) keep.push_back(i);
     }
+    // final order: leading monomials descending
+    std::sort(keep.begin(), keep.end(), [&](uint32_t a, uint32_t b) { return mono_cmp(S->lm[a], S->lm[b], n) > 0; });
     std::vector<uint32_t> off{0};
     std::vector<uint8_t> exps;
     std::vector<uint32_t> cf;
@@ -403,20 +463,11 @@ void finish(gb_system *S) {
         S->run.axpy_rows += ech->work[0];
         S->run.axpy_fma += ech->work[1];
     }
-    // sort by leading monomial descending
-    std::vector<uint32_t> ord(keep.size());
-    std::iota(ord.begin(), ord.end(), 0u);
-    std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) { return mono_cmp(S->lm[keep[a]], S->lm[keep[b]], n) > 0; });
-    S->fin_off.assign(1, 0);
-    S->fin_exps.clear();
-    S->fin_cf.clear();
-    for (uint32_t o : ord) {
-        S->fin_exps.insert(S->fin_exps.end(), exps.begin() + (size_t)off[o] * n, exps.begin() + (size_t)off[o + 1] * n);
-        S->fin_cf.insert(S->fin_cf.end(), cf.begin() + off[o], cf.begin() + off[o + 1]);
-        S->fin_off.push_back((uint32_t)S->fin_cf.size());
-    }
+    S->fin_off.swap(off);
+    S->fin_exps.swap(exps);
+    S->fin_cf.swap(cf);
     S->finished = true;
-    S->run.nbasis = (uint32_t)ord.size();
+    S->run.nbasis = (uint32_t)keep.size();
     S->run.ms_wall += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 

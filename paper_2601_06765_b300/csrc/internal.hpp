@@ -140,6 +140,43 @@ struct Pair {
     uint32_t i, j;
 };
 
+// Monomials as two 64-bit words of eight 8-bit exponents.  While every exponent is below 128,
+// bytewise comparisons run without carries between bytes (SWAR):
+//   (b | H) - a has the high bit of byte i set  iff  b_i >= a_i   (no borrow leaves a byte)
+struct M16 {
+    uint64_t lo, hi;
+};
+inline M16 m16(const Mono &m) {
+    M16 r;
+    std::memcpy(&r, m.e, 16);
+    return r;
+}
+inline bool operator==(const M16 &a, const M16 &b) { return a.lo == b.lo && a.hi == b.hi; }
+constexpr uint64_t SWAR_H = 0x8080808080808080ull, SWAR_L = 0x7F7F7F7F7F7F7F7Full;
+inline bool ge_all(uint64_t b, uint64_t a) { return (((b | SWAR_H) - a) & SWAR_H) == SWAR_H; }
+inline bool divides16(const M16 &a, const M16 &b) { return ge_all(b.lo, a.lo) && ge_all(b.hi, a.hi); }
+inline uint64_t max8(uint64_t a, uint64_t b) {
+    const uint64_t ge = ((a | SWAR_H) - b) & SWAR_H;  // bytes where a >= b
+    const uint64_t mask = (ge >> 7) * 0xFFull;
+    return (a & mask) | (b & ~mask);
+}
+inline M16 lcm16(const M16 &a, const M16 &b) { return M16{max8(a.lo, b.lo), max8(a.hi, b.hi)}; }
+inline uint64_t nonzero8(uint64_t x) { return (((x & SWAR_L) + SWAR_L) | x) & SWAR_H; }
+inline bool coprime16(const M16 &a, const M16 &b) {
+    return !(nonzero8(a.lo) & nonzero8(b.lo)) && !(nonzero8(a.hi) & nonzero8(b.hi));
+}
+inline uint32_t deg16(const M16 &a) {
+    uint64_t s = (a.lo & 0x00FF00FF00FF00FFull) + ((a.lo >> 8) & 0x00FF00FF00FF00FFull) +
+                 (a.hi & 0x00FF00FF00FF00FFull) + ((a.hi >> 8) & 0x00FF00FF00FF00FFull);
+    s = (s & 0x0000FFFF0000FFFFull) + ((s >> 16) & 0x0000FFFF0000FFFFull);
+    return (uint32_t)((s & 0xFFFFFFFFull) + (s >> 32));
+}
+
+struct PairL {  // a critical pair with its lcm cached
+    uint32_t i, j, deg, pad;
+    M16 lcm;
+};
+
 }  // namespace gb
 
 // ---- handles ---------------------------------------------------------------------------------
@@ -164,7 +201,8 @@ struct gb_macaulay {
     gb::DBuf<uint8_t> row_flags;           // bit0 pivot, bit1 reducer, bit2 tail row
     gb::DBuf<uint32_t> pcols;              // nA pivot columns ascending (pivot row i has lm pcols[i])
     gb::DBuf<uint32_t> nonpiv;             // nb non-pivot columns ascending
-    gb::DBuf<uint32_t> colpos;             // ndict: position of a column among pivots / non-pivots
+    gb::DBuf<uint32_t> colpos;             // ndict: pivot index | 0x80000000 for a pivot column,
+                                           // else the position among the non-pivot columns
     float ms_sp = 0.f;
 };
 
@@ -190,7 +228,9 @@ struct gb_system {
     std::vector<gb::Mono> lm;
     std::vector<uint32_t> off, len;
     std::vector<uint8_t> redundant;
-    std::vector<gb::Pair> pairs;
+    std::vector<gb::PairL> pairs;
+    std::vector<gb::M16> lm16;     // leading monomials, SWAR form
+    bool swar = true;              // every exponent so far below 128
     // device basis: terms of element k are [off[k], off[k] + len[k]) of bmon / bcf
     gb::DBuf<uint4> bmon;
     gb::DBuf<uint32_t> bcf;

@@ -16,6 +16,7 @@
 //   append     echelon rows become new basis elements (Sec. 4.2 step 4), written to the device
 //              basis in standard form.
 #include <algorithm>
+#include <cstdlib>
 
 #include "internal.hpp"
 
@@ -27,196 +28,433 @@ constexpr int RT = 256;  // threads per block of the row-reduction kernel
 
 inline unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 
-template <bool SMALLP, bool SMEM>
-__global__ void __launch_bounds__(RT) k_reduce(uint32_t nA, uint32_t N,
+// ---- sparse reduction of the non-pivot rows (PSGE trailing update, Sec. 9.2) -------------------
+//
+// The pivot columns are taken in chunks of CW = 32 consecutive pivots (pivot rows k..k+31, one
+// contiguous CSR segment).  For a non-pivot row v the multipliers of a chunk are the solution of a
+// 32 x 32 unit upper-triangular system: f_i = v[c_i] - sum_{j<i} f_j U[j][i], where U[j][i] is the
+// entry of pivot row j at pivot column c_i.  One warp per row solves it with shuffles from a shared
+// copy of U (prefetched by the other warps while the previous chunk's system is solved); then
+// every warp of the block applies v <- v - sum_i f_i (pivot row i) to the accumulators with
+// shared-memory atomics (each pivot row's own leading entry included, which leaves v[c_i] = 0).
+// A block reduces R non-pivot rows together, so each pivot-row entry read from L2 serves R rows,
+// and it synchronises twice per chunk instead of once per pivot column.
+//
+// Accumulators are lazy (Rem. 8.1), in one of three modes:
+//   A32: p < 2^16, each product (p - f) v < 2^32 is Barrett-reduced to [0, p) and added to a 32-bit
+//        sum (exact while a column takes fewer than 2^16 updates: the host requires nA < 2^16);
+//   A64: p < 2^16, the raw products are added to a 64-bit sum (no reduction per update);
+//   M64: p < 2^31, the Montgomery product redc(fR * v) in [0, 2p) is added to a 64-bit sum.
+// A32 halves the shared memory per row, which lets more blocks share an SM.  Entries are reduced
+// (Barrett) when read.
+constexpr int CW = 32;
+enum AccMode { A32 = 0, A64 = 1, M64 = 2 };
+template <int MODE>
+struct AccOf { using type = unsigned long long; };
+template <>
+struct AccOf<A32> { using type = uint32_t; };
+
+// U[chunk][j][i] for j < i: entry of pivot row chunk*32+j at pivot column pcols[chunk*32+i]
+__global__ void k_build_chunk_tri(uint32_t nA, const uint32_t *__restrict__ row_ptr,
+                                  const uint32_t *__restrict__ col, const uint32_t *__restrict__ val,
+                                  const uint32_t *__restrict__ pcols,
+                                  const uint32_t *__restrict__ colpos, uint32_t *__restrict__ U) {
+    const uint32_t k = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (k >= nA) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t chunk = k / CW, j = k % CW;
+    const uint32_t last = pcols[min(chunk * CW + CW, nA) - 1];
+    uint32_t *Uc = U + (size_t)chunk * CW * CW + (size_t)j * CW;
+    const uint32_t a = row_ptr[k] + 1, b = row_ptr[k + 1];
+    for (uint32_t q0 = a; q0 < b; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        bool past = true;
+        if (q < b) {
+            const uint32_t c = col[q];
+            past = c > last;
+            if (!past) {
+                const uint32_t cp = colpos[c];
+                if ((cp & 0x80000000u) && (cp & 0x7FFFFFFFu) / CW == chunk) Uc[(cp & 0x7FFFFFFFu) % CW] = val[q];
+            }
+        }
+        if (__all_sync(0xffffffffu, past)) break;  // columns ascend: the rest lies past the chunk
+    }
+}
+
+template <int R, int MODE, bool SMEM>
+__global__ void __launch_bounds__(RT) k_reduce(uint32_t nA, uint32_t nC, uint32_t N,
                                               const uint32_t *__restrict__ row_ptr,
                                               const uint32_t *__restrict__ col,
                                               const uint32_t *__restrict__ val,
                                               const uint32_t *__restrict__ pcols,
+                                              const uint32_t *__restrict__ U,
                                               const uint32_t *__restrict__ nonpiv, uint32_t nb,
-                                              Fp fp, unsigned long long *__restrict__ gacc,
+                                              Fp fp, typename AccOf<MODE>::type *__restrict__ gacc,
                                               uint32_t *__restrict__ dprime,
                                               unsigned long long *__restrict__ work) {
-    extern __shared__ unsigned long long sacc[];
-    uint32_t applied = 0, fmas = 0;  // pivot rows applied and mod-p multiply-adds (thread 0)
-    const uint32_t i = blockIdx.x, row = nA + i;
-    const uint32_t a = row_ptr[row], b = row_ptr[row + 1];
-    const uint32_t lm = a < b ? col[a] : N;
-    const uint32_t width = N - lm;
-    unsigned long long *acc = SMEM ? sacc : gacc + (size_t)i * N;
-    for (uint32_t j = threadIdx.x; j < width; j += RT) acc[j] = 0ull;
+    using Acc = typename AccOf<MODE>::type;
+    constexpr bool SMALLP = MODE != M64;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t fsh[R][CW];
+    __shared__ uint32_t Us[2][CW * CW];
+    __shared__ uint32_t rp[CW + 1];
+    __shared__ uint32_t s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t r0 = blockIdx.x * R;
+    const int nr = (int)min((uint32_t)R, nC - r0);
+    // base column = smallest leading column of the block's rows
+    if (threadIdx.x == 0) {
+        uint32_t b = N;
+        for (int r = 0; r < nr; ++r) {
+            const uint32_t a = row_ptr[nA + r0 + r];
+            if (a < row_ptr[nA + r0 + r + 1]) b = min(b, col[a]);
+        }
+        s_base = b;
+    }
     __syncthreads();
-    for (uint32_t q = a + threadIdx.x; q < b; q += RT) acc[col[q] - lm] = val[q];
-    // first pivot column at or right of lm
+    const uint32_t base = s_base, width = N - base;
+    Acc *acc = SMEM ? reinterpret_cast<Acc *>(smem_raw) : gacc + (size_t)blockIdx.x * R * N;
+    for (uint32_t j = threadIdx.x; j < (uint32_t)R * width; j += RT) acc[j] = 0;
+    __syncthreads();
+    for (int r = 0; r < nr; ++r) {
+        const uint32_t a = row_ptr[nA + r0 + r], b = row_ptr[nA + r0 + r + 1];
+        for (uint32_t q = a + threadIdx.x; q < b; q += RT) acc[(size_t)r * width + col[q] - base] = val[q];
+    }
+    // first chunk holding a pivot column >= base
     uint32_t lo = 0, hi = nA;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (pcols[mid] < lm) lo = mid + 1; else hi = mid;
+        if (pcols[mid] < base) lo = mid + 1; else hi = mid;
     }
-    for (uint32_t k = lo; k < nA; ++k) {
-        const uint32_t c = pcols[k];
-        __syncthreads();
-        const uint32_t f = fp_reduce(acc[c - lm], fp);
-        if (f == 0) continue;  // uniform: every thread read the same entry
-        const uint32_t neg = fp.p - f;
-        const uint32_t mult = SMALLP ? neg : fp_to_mont(neg, fp);
-        const uint32_t pa = row_ptr[k] + 1, pb = row_ptr[k + 1];
-        if (threadIdx.x == 0) {
-            ++applied;
-            fmas += pb - pa;
+    const uint32_t k0 = (lo / CW) * CW;
+    if (k0 < nA)
+        for (uint32_t t = threadIdx.x; t < CW * CW; t += RT) Us[0][t] = U[(size_t)(k0 / CW) * CW * CW + t];
+    unsigned long long applied = 0, fmas = 0;
+    for (uint32_t kc = k0, buf = 0; kc < nA; kc += CW, buf ^= 1) {
+        const uint32_t cnt = min((uint32_t)CW, nA - kc);
+        __syncthreads();  // the previous chunk's updates (and this chunk's U) are visible
+        if (warp < nr) {
+            // phase A: multipliers of the chunk for row `warp`
+            const Acc *a = acc + (size_t)warp * width;
+            uint32_t x = 0;
+            if ((uint32_t)lane < cnt) {
+                const uint32_t c = pcols[kc + lane];
+                if (c >= base) x = MODE == A32 ? fp_reduce32((uint32_t)a[c - base], fp) : fp_reduce(a[c - base], fp);
+            }
+            const uint32_t *Uc = Us[buf];
+            for (uint32_t i = 0; i + 1 < cnt; ++i) {
+                const uint32_t fi = __shfl_sync(0xffffffffu, x, i);
+                if (fi && (uint32_t)lane > i && (uint32_t)lane < cnt) {
+                    const uint32_t u = Uc[i * CW + lane];
+                    if (u) x = fp_sub(x, SMALLP ? fp_reduce32(fi * u, fp) : fp_mul(fi, u, fp), fp);
+                }
+            }
+            fsh[warp][lane] = (uint32_t)lane < cnt ? x : 0u;
+        } else {
+            if (warp < R) fsh[warp][lane] = 0u;
+            // the other warps prefetch the next chunk's triangle
+            const uint32_t kn = kc + CW;
+            if (kn < nA)
+                for (uint32_t t = threadIdx.x - 32u * (uint32_t)nr; t < CW * CW; t += RT - 32u * (uint32_t)nr)
+                    Us[buf ^ 1][t] = U[(size_t)(kn / CW) * CW * CW + t];
         }
-        for (uint32_t q = pa + threadIdx.x; q < pb; q += RT) {
-            const uint64_t prod = (uint64_t)mult * val[q];
-            acc[col[q] - lm] += SMALLP ? prod : (uint64_t)fp_redc(prod, fp);
+        if (threadIdx.x <= cnt) rp[threadIdx.x] = row_ptr[kc + threadIdx.x];
+        __syncthreads();
+        // phase B: warp w applies pivot rows w, w + 8, ... of the chunk
+        for (uint32_t i = warp; i < cnt; i += RT / 32) {
+            uint32_t m[R];
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t f = fsh[r][i];
+                m[r] = f ? (SMALLP ? fp.p - f : fp_to_mont(fp.p - f, fp)) : 0u;
+                any |= f != 0;
+            }
+            if (!any) continue;
+            const uint32_t a = rp[i], b = rp[i + 1];
+            if (lane == 0) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (m[r]) { ++applied; fmas += b - a; }
+            }
+            for (uint32_t q = a + lane; q < b; q += 64) {
+                // two entries per lane in flight
+                const bool two = q + 32 < b;
+                const uint32_t c0 = col[q] - base, v0 = val[q];
+                const uint32_t c1 = two ? col[q + 32] - base : 0u, v1 = two ? val[q + 32] : 0u;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (!m[r]) continue;
+                    Acc *ar = acc + (size_t)r * width;
+                    if (MODE == A32) {
+                        atomicAdd(reinterpret_cast<uint32_t *>(ar + c0), fp_reduce32(m[r] * v0, fp));
+                        if (two) atomicAdd(reinterpret_cast<uint32_t *>(ar + c1), fp_reduce32(m[r] * v1, fp));
+                    } else if (MODE == A64) {
+                        atomicAdd(reinterpret_cast<unsigned long long *>(ar + c0), (unsigned long long)(m[r] * v0));
+                        if (two) atomicAdd(reinterpret_cast<unsigned long long *>(ar + c1), (unsigned long long)(m[r] * v1));
+                    } else {
+                        atomicAdd(reinterpret_cast<unsigned long long *>(ar + c0),
+                                  (unsigned long long)fp_redc((uint64_t)m[r] * v0, fp));
+                        if (two)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(ar + c1),
+                                      (unsigned long long)fp_redc((uint64_t)m[r] * v1, fp));
+                    }
+                }
+            }
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&work[0], (unsigned long long)applied);
-        atomicAdd(&work[1], (unsigned long long)fmas);
+    if (lane == 0 && (applied || fmas)) {
+        atomicAdd(&work[0], applied);
+        atomicAdd(&work[1], fmas);
     }
-    uint32_t *out = dprime + (size_t)i * nb;
-    for (uint32_t jj = threadIdx.x; jj < nb; jj += RT) {
-        const uint32_t c = nonpiv[jj];
-        out[jj] = c >= lm ? fp_reduce(acc[c - lm], fp) : 0u;
+    for (int r = 0; r < nr; ++r) {
+        uint32_t *out = dprime + (size_t)(r0 + r) * nb;
+        const Acc *a = acc + (size_t)r * width;
+        for (uint32_t jj = threadIdx.x; jj < nb; jj += RT) {
+            const uint32_t c = nonpiv[jj];
+            out[jj] = c < base ? 0u : MODE == A32 ? fp_reduce32((uint32_t)a[c - base], fp) : fp_reduce(a[c - base], fp);
+        }
     }
 }
 
-// ---- RREF(D') by row panels ------------------------------------------------------------------
+// ---- RREF(D'): right-looking Gauss-Jordan by panels of K rows --------------------------------
+//
+// M starts as a copy of D'.  Each round picks up to K non-zero rows that are not pivots yet, brings
+// them to reduced echelon form among themselves in one block (pivots at their leading columns),
+// then eliminates the new pivot columns from every other row of M in parallel (a GEMM-shaped
+// update), which also keeps the earlier pivot rows reduced.  A pivot row's leading column never
+// moves: it is zero left of its pivot, and later pivot rows are zero at it.  When no non-zero
+// non-pivot row is left, the pivot rows sorted by pivot column are RREF(D'), which is unique.
+constexpr uint32_t KP = 32;       // panel rows
+constexpr uint32_t NOLEAD = 0xFFFFFFFFu;
 
-struct Ech {
-    uint32_t *E;      // rho_cap x nb echelon rows (RREF among themselves), unordered
-    uint32_t *epiv;   // their pivot positions
-    uint32_t *state;  // [0] rho, [1] nnew of the current panel
-    uint32_t nb, cap;
+struct Rref {
+    uint32_t *M;       // nC x nb working matrix
+    uint32_t *lead;    // nC: first non-zero column, NOLEAD for a zero row
+    uint32_t *pcol;    // nC: pivot column of a pivot row, NOLEAD otherwise
+    uint32_t *order;   // rank: pivot rows in discovery order
+    uint32_t *state;   // [0] pivots so far, [1] panel rows, [2] new pivots, [3] rows left
+    uint32_t *panel;   // KP panel row ids, then KP new pivot row ids, then KP new pivot columns
+    uint32_t nC, nb;
 };
 
-// R[r] = D'[i0 + r] - sum_e D'[i0 + r][epiv_e] * E_e   (the E rows are zero on each other's pivots)
-__global__ void k_panel_reduce(const uint32_t *__restrict__ Dp, uint32_t i0, Ech X, Fp fp,
-                               uint32_t *__restrict__ R) {
-    extern __shared__ uint32_t m[];
-    const uint32_t r = blockIdx.x, nb = X.nb;
-    const uint32_t rho = X.state[0];
-    const uint32_t *src = Dp + (size_t)(i0 + r) * nb;
-    for (uint32_t e = threadIdx.x; e < rho; e += blockDim.x) m[e] = src[X.epiv[e]];
+__device__ __forceinline__ uint32_t block_min(uint32_t v, uint32_t *red) {
+    for (int d = 16; d; d >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, d));
     __syncthreads();
-    const uint32_t j = blockIdx.y * blockDim.x + threadIdx.x;
-    if (j >= nb) return;
-    uint64_t acc = src[j];
-    if (fp.small) {
-        for (uint32_t e = 0; e < rho; ++e)
-            if (m[e]) acc += (uint64_t)(fp.p - m[e]) * X.E[(size_t)e * nb + j];
-        R[(size_t)r * nb + j] = fp_reduce(acc, fp);
-    } else {
-        for (uint32_t e = 0; e < rho; ++e)
-            if (m[e]) acc += fp_mul(fp.p - m[e], X.E[(size_t)e * nb + j], fp);
-        R[(size_t)r * nb + j] = fp_reduce(acc, fp);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : NOLEAD;
+    if (threadIdx.x < 32)
+        for (int d = 16; d; d >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, d));
+    if (threadIdx.x == 0) red[0] = v;
+    __syncthreads();
+    return red[0];
+}
+
+// leading columns of every row of M
+__global__ void k_leads(Rref X) {
+    __shared__ uint32_t red[32];
+    const uint32_t r = blockIdx.x;
+    const uint32_t *row = X.M + (size_t)r * X.nb;
+    uint32_t c = NOLEAD;
+    for (uint32_t j = threadIdx.x; j < X.nb; j += blockDim.x)
+        if (row[j]) { c = j; break; }
+    c = block_min(c, red);
+    if (threadIdx.x == 0) {
+        X.lead[r] = c;
+        X.pcol[r] = NOLEAD;
     }
 }
 
-// one block: Gauss-Jordan over the P reduced panel rows; new rows go to E[rho..rho+nnew)
-constexpr int PT = 1024;
-__global__ void __launch_bounds__(PT) k_panel_solve(uint32_t *__restrict__ R, uint32_t P, Ech X,
-                                                   Fp fp) {
-    __shared__ uint32_t mult[64];
-    __shared__ uint32_t newpiv[64];
-    __shared__ uint32_t red[PT / 32];
-    __shared__ uint32_t s_c, s_inv;
-    const uint32_t nb = X.nb, rho = X.state[0];
-    uint32_t nnew = 0;
-    uint32_t *NewRows = X.E + (size_t)rho * nb;
-    for (uint32_t r = 0; r < P; ++r) {
-        uint32_t *row = R + (size_t)r * nb;
-        // reduce by the panel's new rows (zero on each other's pivots)
-        if (threadIdx.x < nnew) mult[threadIdx.x] = row[newpiv[threadIdx.x]];
+// choose the next panel: the first KP non-zero rows that are not pivots (one block)
+__global__ void k_pick_panel(Rref X) {
+    __shared__ uint32_t wcnt[32];
+    __shared__ uint32_t s_taken;
+    if (threadIdx.x == 0) s_taken = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x / 32;
+    uint32_t left = 0;
+    for (uint32_t r0 = 0; r0 < X.nC; r0 += blockDim.x) {
+        const uint32_t r = r0 + threadIdx.x;
+        const bool want = r < X.nC && X.lead[r] != NOLEAD && X.pcol[r] == NOLEAD;
+        left += want;
+        const unsigned mask = __ballot_sync(0xffffffffu, want);
+        if (lane == 0) wcnt[warp] = __popc(mask);
         __syncthreads();
-        if (nnew) {
-            for (uint32_t j = threadIdx.x; j < nb; j += PT) {
-                uint64_t acc = row[j];
-                for (uint32_t k = 0; k < nnew; ++k)
-                    if (mult[k]) acc += fp_mul(fp.p - mult[k], NewRows[(size_t)k * nb + j], fp);
-                row[j] = fp_reduce(acc, fp);
-            }
-        }
+        uint32_t before = s_taken;
+        for (int w = 0; w < warp; ++w) before += wcnt[w];
+        before += __popc(mask & ((1u << lane) - 1u));
+        if (want && before < KP) X.panel[before] = r;
         __syncthreads();
-        // first nonzero column
-        uint32_t c = 0xFFFFFFFFu;
-        for (uint32_t j = threadIdx.x; j < nb; j += PT)
-            if (row[j]) { c = j; break; }
-        for (int d = 16; d; d >>= 1) c = min(c, __shfl_xor_sync(0xffffffffu, c, d));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            uint32_t v = red[threadIdx.x];
-            for (int d = 16; d; d >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, d));
-            if (threadIdx.x == 0) {
-                s_c = v;
-                if (v != 0xFFFFFFFFu) s_inv = fp_inv(row[v], fp);
-            }
-        }
-        __syncthreads();
-        c = s_c;
-        if (c == 0xFFFFFFFFu) continue;
-        if (nnew == 64 || rho + nnew >= X.cap) break;  // cannot happen: P <= 64, rank <= cap
-        const uint32_t inv = s_inv;
-        for (uint32_t j = threadIdx.x; j < nb; j += PT) row[j] = fp_mul(row[j], inv, fp);
-        if (threadIdx.x < nnew) mult[threadIdx.x] = NewRows[(size_t)threadIdx.x * nb + c];
-        __syncthreads();
-        // clear column c from the earlier new rows, then append the row
-        for (uint32_t idx = threadIdx.x; idx < nnew * nb; idx += PT) {
-            const uint32_t k = idx / nb, j = idx - k * nb;
-            if (mult[k]) {
-                uint32_t *x = NewRows + (size_t)k * nb + j;
-                *x = fp_sub(*x, fp_mul(mult[k], row[j], fp), fp);
-            }
-        }
-        for (uint32_t j = threadIdx.x; j < nb; j += PT) NewRows[(size_t)nnew * nb + j] = row[j];
         if (threadIdx.x == 0) {
-            newpiv[nnew] = c;
-            X.epiv[rho + nnew] = c;
+            uint32_t t = s_taken;
+            for (int w = 0; w < nw; ++w) t += wcnt[w];
+            s_taken = t;
+        }
+        __syncthreads();
+    }
+    for (int d = 16; d; d >>= 1) left += __shfl_xor_sync(0xffffffffu, left, d);
+    if (lane == 0) wcnt[warp] = left;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < nw; ++w) t += wcnt[w];
+        X.state[3] = t;
+        X.state[1] = min(s_taken, KP);
+        X.state[2] = 0;
+    }
+}
+
+// reduced echelon form of the panel rows among themselves (one block).  With SMEM the panel is
+// copied to shared memory, reduced there and written back.
+constexpr int PT = 1024;
+template <bool SMEM>
+__global__ void __launch_bounds__(PT) k_panel_rref(Rref X, Fp fp) {
+    extern __shared__ __align__(16) uint32_t pan[];
+    __shared__ uint32_t mult[KP], prow[KP], pslot[KP], pc[KP], red[32];
+    __shared__ uint32_t s_inv;
+    const uint32_t P = X.state[1], nb = X.nb;
+    auto rowp = [&](uint32_t t) -> uint32_t * {
+        return SMEM ? pan + (size_t)t * nb : X.M + (size_t)X.panel[t] * nb;
+    };
+    if (SMEM) {
+        for (uint32_t t = 0; t < P; ++t) {
+            const uint32_t *src = X.M + (size_t)X.panel[t] * nb;
+            for (uint32_t j = threadIdx.x; j < nb; j += PT) pan[(size_t)t * nb + j] = src[j];
+        }
+        __syncthreads();
+    }
+    uint32_t nnew = 0;
+    for (uint32_t t = 0; t < P; ++t) {
+        const uint32_t r = X.panel[t];
+        uint32_t *row = rowp(t);
+        // multipliers: entries at the panel's earlier pivots, negated (pivot rows are RREF
+        // among themselves, so each multiplier is read from the unreduced row)
+        if (threadIdx.x < nnew) {
+            const uint32_t v = row[pc[threadIdx.x]];
+            mult[threadIdx.x] = v ? fp.p - v : 0u;
+        }
+        __syncthreads();
+        uint32_t c = NOLEAD;
+        for (uint32_t j = threadIdx.x; j < nb; j += PT) {
+            uint64_t acc = row[j];
+            if (fp.small) {  // raw products < 2^32, at most 32 of them: one reduction per entry
+                for (uint32_t k = 0; k < nnew; ++k) acc += (uint64_t)(mult[k] * rowp(pslot[k])[j]);
+            } else {
+                for (uint32_t k = 0; k < nnew; ++k)
+                    if (mult[k]) acc += fp_mul(mult[k], rowp(pslot[k])[j], fp);
+            }
+            const uint32_t x = nnew ? fp_reduce(acc, fp) : (uint32_t)acc;
+            if (nnew) row[j] = x;
+            if (x && c == NOLEAD) c = j;
+        }
+        c = block_min(c, red);
+        if (c == NOLEAD) {
+            if (threadIdx.x == 0) X.lead[r] = NOLEAD;
+            continue;
+        }
+        if (threadIdx.x == 0) s_inv = fp_inv(row[c], fp);
+        __syncthreads();
+        const uint32_t inv = s_inv;
+        for (uint32_t j = c + threadIdx.x; j < nb; j += PT) row[j] = fp_mul(row[j], inv, fp);
+        if (threadIdx.x < nnew) {
+            const uint32_t v = rowp(pslot[threadIdx.x])[c];
+            mult[threadIdx.x] = v ? fp.p - v : 0u;
+        }
+        __syncthreads();
+        // clear column c from the earlier new rows
+        for (uint32_t k = 0; k < nnew; ++k) {
+            const uint32_t mk = mult[k];
+            if (!mk) continue;
+            uint32_t *dst = rowp(pslot[k]);
+            for (uint32_t j = c + threadIdx.x; j < nb; j += PT) {
+                const uint32_t y = row[j];
+                if (y) dst[j] = fp_reduce((uint64_t)dst[j] + (uint64_t)mk * y, fp);
+            }
+        }
+        if (threadIdx.x == 0) {
+            prow[nnew] = r;
+            pslot[nnew] = t;
+            pc[nnew] = c;
+            X.lead[r] = c;
+            X.pcol[r] = c;
         }
         __syncthreads();
         ++nnew;
     }
-    if (threadIdx.x == 0) X.state[1] = nnew;
-}
-
-// E_e -= sum_k E_e[newpiv_k] * New_k for the rows that existed before this panel.  One block
-// owns a whole row: the multipliers are entries of the row being rewritten, so they are read
-// before any thread of the block writes it.
-__global__ void k_panel_merge(Ech X, Fp fp) {
-    __shared__ uint32_t m[64];
-    const uint32_t e = blockIdx.x, nb = X.nb;
-    const uint32_t rho = X.state[0], nnew = X.state[1];
-    if (e >= rho || nnew == 0) return;
-    uint32_t *row = X.E + (size_t)e * nb;
-    const uint32_t *New = X.E + (size_t)rho * nb;
-    for (uint32_t k = threadIdx.x; k < nnew; k += blockDim.x) m[k] = row[X.epiv[rho + k]];
+    if (SMEM) {  // write the panel back (pivot rows reduced, the others now zero)
+        for (uint32_t t = 0; t < P; ++t) {
+            uint32_t *dst = X.M + (size_t)X.panel[t] * nb;
+            for (uint32_t j = threadIdx.x; j < nb; j += PT) dst[j] = pan[(size_t)t * nb + j];
+        }
+    }
+    if (threadIdx.x < nnew) {
+        X.panel[KP + threadIdx.x] = prow[threadIdx.x];
+        X.panel[2 * KP + threadIdx.x] = pc[threadIdx.x];
+        X.order[X.state[0] + threadIdx.x] = prow[threadIdx.x];
+    }
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
-        uint64_t acc = row[j];
-        for (uint32_t k = 0; k < nnew; ++k)
-            if (m[k]) acc += fp_mul(fp.p - m[k], New[(size_t)k * nb + j], fp);
-        row[j] = fp_reduce(acc, fp);
+    if (threadIdx.x == 0) {
+        X.state[2] = nnew;
+        X.state[0] += nnew;
     }
 }
 
-__global__ void k_panel_commit(Ech X) { X.state[0] += X.state[1]; }
+// every other row: r <- r - sum_k r[pc_k] * Q_k over the panel's new pivot rows Q_k; one block per
+// row, so a row's multipliers are read before any thread writes the row
+__global__ void k_eliminate(Rref X, Fp fp) {
+    __shared__ uint32_t m[KP], q[KP], red[32];
+    __shared__ int s_any;
+    const uint32_t r = blockIdx.x, nb = X.nb, nnew = X.state[2];
+    if (nnew == 0 || X.lead[r] == NOLEAD) return;
+    const uint32_t pr = X.pcol[r];
+    uint32_t *row = X.M + (size_t)r * nb;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    if (threadIdx.x < nnew) {
+        q[threadIdx.x] = X.panel[KP + threadIdx.x];
+        const uint32_t v = q[threadIdx.x] == r ? 0u : row[X.panel[2 * KP + threadIdx.x]];
+        m[threadIdx.x] = v;
+        if (v) s_any = 1;
+    }
+    __syncthreads();
+    if (!s_any) return;
+    uint32_t c = NOLEAD;
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+        uint64_t acc = row[j];
+        if (fp.small) {  // at most KP raw products below 2^32 each
+            for (uint32_t k = 0; k < nnew; ++k)
+                if (m[k]) acc += (uint64_t)((fp.p - m[k]) * X.M[(size_t)q[k] * nb + j]);
+        } else {
+            for (uint32_t k = 0; k < nnew; ++k)
+                if (m[k]) acc += fp_mul(fp.p - m[k], X.M[(size_t)q[k] * nb + j], fp);
+        }
+        const uint32_t x = fp_reduce(acc, fp);
+        row[j] = x;
+        if (x && c == NOLEAD) c = j;
+    }
+    if (pr == NOLEAD) {  // a pivot row keeps its leading column; other rows may move or vanish
+        c = block_min(c, red);
+        if (threadIdx.x == 0) X.lead[r] = c;
+    }
+}
 
-// order the echelon rows by pivot position
-__global__ void k_sort_rows(Ech X, uint32_t *__restrict__ out, uint32_t *__restrict__ opiv) {
-    const uint32_t e = blockIdx.x, nb = X.nb, rho = X.state[0];
-    if (e >= rho) return;
+// the pivot rows in pivot-column order
+__global__ void k_gather_rref(Rref X, uint32_t rank, uint32_t *__restrict__ out,
+                              uint32_t *__restrict__ opiv) {
+    const uint32_t e = blockIdx.x, nb = X.nb;
     __shared__ uint32_t pos;
+    const uint32_t r = X.order[e], c = X.pcol[r];
     if (threadIdx.x == 0) {
-        uint32_t c = 0;
-        for (uint32_t f = 0; f < rho; ++f) c += X.epiv[f] < X.epiv[e];
-        pos = c;
-        opiv[c] = X.epiv[e];
+        uint32_t n = 0;
+        for (uint32_t f = 0; f < rank; ++f) n += X.pcol[X.order[f]] < c;
+        pos = n;
+        opiv[n] = c;
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
-        out[(size_t)pos * nb + j] = X.E[(size_t)e * nb + j];
+        out[(size_t)pos * nb + j] = X.M[(size_t)r * nb + j];
 }
 
 // ---- reconstruction --------------------------------------------------------------------------
@@ -273,6 +511,64 @@ __global__ void k_write_rows(const uint32_t *__restrict__ M, uint32_t rows, uint
     }
 }
 
+// nonzeros of row r of M (rows < mrows; rows beyond are empty), plus one for the leading term
+__global__ void k_count_rows_plus(const uint32_t *__restrict__ M, uint32_t rows, uint32_t mrows,
+                                  uint32_t nb, uint32_t *__restrict__ cnt) {
+    const uint32_t r = blockIdx.x;
+    uint32_t c = 0;
+    if (r < mrows)
+        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) c += M[(size_t)r * nb + j] != 0;
+    for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+    __shared__ uint32_t s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 1;
+        for (uint32_t w = 0; w < blockDim.x / 32; ++w) t += s[w];
+        cnt[r] = t;
+    }
+}
+
+// leading term (coefficient 1) then the nonzeros of row r in column order, exponents as n bytes
+__global__ void k_pack_rows(const uint32_t *__restrict__ M, uint32_t rows, uint32_t mrows, uint32_t nb,
+                            const uint32_t *__restrict__ nonpiv, const uint4 *__restrict__ dict,
+                            const uint4 *__restrict__ lead, const uint32_t *__restrict__ out_off,
+                            uint32_t n, uint8_t *__restrict__ oexp, uint32_t *__restrict__ ocf) {
+    const uint32_t r = blockIdx.x;
+    __shared__ uint32_t base;
+    __shared__ uint32_t wsum[32];
+    auto put = [&](uint32_t pos, uint4 m, uint32_t c) {
+        const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+        for (uint32_t i = 0; i < n; ++i) oexp[(size_t)pos * n + i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+        ocf[pos] = c;
+    };
+    if (threadIdx.x == 0) {
+        base = out_off[r];
+        put(base, lead[r], 1u);
+        base += 1;
+    }
+    __syncthreads();
+    if (r >= mrows) return;
+    const uint32_t *src = M + (size_t)r * nb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x / 32;
+    for (uint32_t j0 = 0; j0 < nb; j0 += blockDim.x) {
+        const uint32_t j = j0 + threadIdx.x;
+        const uint32_t v = j < nb ? src[j] : 0u;
+        const unsigned mask = __ballot_sync(0xffffffffu, v != 0);
+        if (lane == 0) wsum[warp] = __popc(mask);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < warp) before += wsum[w];
+            total += wsum[w];
+        }
+        if (v) put(base + before + __popc(mask & ((1u << lane) - 1u)), dict[nonpiv[j]], v);
+        __syncthreads();
+        if (threadIdx.x == 0) base += total;
+        __syncthreads();
+    }
+}
+
 __global__ void k_gather_lms(uint32_t rank, const uint32_t *__restrict__ rpiv,
                              const uint32_t *__restrict__ nonpiv, const uint4 *__restrict__ dict,
                              uint4 *__restrict__ out) {
@@ -297,65 +593,113 @@ std::unique_ptr<gb_echelon> reduce_rows(gb_macaulay *Mac, bool echelon) {
     work.alloc(ar, 2, st);
     GB_CUDA(cudaMemsetAsync(work.p, 0, 16, st));
     if (nC && nb) {
-        const size_t smem = sizeof(unsigned long long) * N;
         const bool small = S->fp.small != 0;
-        const bool use_smem = smem <= 200 * 1024;
-        DBuf<unsigned long long> gacc;
-        if (use_smem) {
-            auto kern = small ? k_reduce<true, true> : k_reduce<false, true>;
-            GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<nC, RT, smem, st>>>(nA, N, Mac->row_ptr.p, Mac->col.p, Mac->val.p, Mac->pcols.p,
-                                       Mac->nonpiv.p, nb, S->fp, nullptr, E->dprime.p, work.p);
-            counted();
-        } else {
-            gacc.alloc(ar, (size_t)nC * N, st);
-            auto kern = small ? k_reduce<true, false> : k_reduce<false, false>;
-            kern<<<nC, RT, 0, st>>>(nA, N, Mac->row_ptr.p, Mac->col.p, Mac->val.p, Mac->pcols.p,
-                                    Mac->nonpiv.p, nb, S->fp, gacc.p, E->dprime.p, work.p);
+        const uint32_t nchunks = (nA + CW - 1) / CW;
+        DBuf<uint32_t> U;
+        U.alloc(ar, (size_t)std::max(nchunks, 1u) * CW * CW, st);
+        GB_CUDA(cudaMemsetAsync(U.p, 0, 4ull * std::max(nchunks, 1u) * CW * CW, st));
+        if (nA) {
+            k_build_chunk_tri<<<blocks(nA, 8), 256, 0, st>>>(nA, Mac->row_ptr.p, Mac->col.p, Mac->val.p,
+                                                            Mac->pcols.p, Mac->colpos.p, U.p);
             counted();
         }
-        GB_CUDA(cudaGetLastError());
+        // accumulator mode and rows per block: the largest R whose blocks all fit in one wave
+        const int mode = !small ? M64 : (nA < 65536u ? A32 : A64);
+        const size_t accb = mode == A32 ? 4 : 8;
+        // rows per block.  Measured on the n=10 dense workload, one row per block (more resident
+        // warps) beats sharing each streamed pivot row between 2 or 4 rows; GB_REDUCE_R=2|4
+        // selects the shared variants for tuning.
+        static const int forced_r = [] {
+            const char *e = std::getenv("GB_REDUCE_R");
+            return e ? std::atoi(e) : 0;
+        }();
+        int R = (forced_r == 2 || forced_r == 4) ? forced_r : 1;
+        if ((size_t)R * N * accb > 200 * 1024) R = 1;
+        const bool use_smem = (size_t)R * N * accb <= 200 * 1024;
+        const unsigned grid = (nC + R - 1) / R;
+        const size_t smem = use_smem ? (size_t)R * N * accb : 0;
+        DBuf<unsigned long long> gacc;
+        if (!use_smem) gacc.alloc(ar, (size_t)grid * R * N + 1, st);
+        auto launch = [&](auto kern, auto *gp) {
+            // static + dynamic shared memory above 48 KB needs the opt-in, whatever the split
+            GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<grid, RT, smem, st>>>(nA, nC, N, Mac->row_ptr.p, Mac->col.p, Mac->val.p, Mac->pcols.p,
+                                         U.p, Mac->nonpiv.p, nb, S->fp, gp, E->dprime.p, work.p);
+            counted();
+        };
+        uint32_t *g32 = reinterpret_cast<uint32_t *>(gacc.p);
+        unsigned long long *g64 = gacc.p;
+#define GB_REDUCE_CASE(RR)                                                                   \
+    if (R == RR) {                                                                           \
+        if (mode == A32) {                                                                   \
+            if (use_smem) launch(k_reduce<RR, A32, true>, g32);                              \
+            else launch(k_reduce<RR, A32, false>, g32);                                      \
+        } else if (mode == A64) {                                                            \
+            if (use_smem) launch(k_reduce<RR, A64, true>, g64);                              \
+            else launch(k_reduce<RR, A64, false>, g64);                                      \
+        } else {                                                                             \
+            if (use_smem) launch(k_reduce<RR, M64, true>, g64);                              \
+            else launch(k_reduce<RR, M64, false>, g64);                                      \
+        }                                                                                    \
+    }
+        GB_REDUCE_CASE(1)
+        GB_REDUCE_CASE(2)
+        GB_REDUCE_CASE(4)
+#undef GB_REDUCE_CASE
     }
     GB_CUDA(cudaEventRecord(S->ev[3], st));
     if (echelon && nC && nb) {
-        const uint32_t cap = std::min(nC, nb);
-        const uint32_t P = 64;
-        DBuf<uint32_t> Ebuf, epiv, state, R;
-        Ebuf.alloc(ar, (size_t)cap * nb, st);
-        epiv.alloc(ar, cap, st);
-        state.alloc(ar, 2, st);
-        R.alloc(ar, (size_t)P * nb, st);
-        GB_CUDA(cudaMemsetAsync(state.p, 0, 8, st));
-        Ech X{Ebuf.p, epiv.p, state.p, nb, cap};
-        const size_t msm = sizeof(uint32_t) * std::max<uint32_t>(cap, 1);
-        if (msm > 48 * 1024) {
-            GB_CUDA(cudaFuncSetAttribute(k_panel_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
-        }
-        for (uint32_t i0 = 0; i0 < nC; i0 += P) {
-            const uint32_t rows = std::min(P, nC - i0);
-            k_panel_reduce<<<dim3(rows, blocks(nb, 256)), 256, msm, st>>>(E->dprime.p, i0, X, S->fp, R.p);
-            counted();
-            k_panel_solve<<<1, PT, 0, st>>>(R.p, rows, X, S->fp);
-            counted();
-            k_panel_merge<<<cap, 256, 0, st>>>(X, S->fp);
-            counted();
-            k_panel_commit<<<1, 1, 0, st>>>(X);
-            counted();
-            GB_CUDA(cudaGetLastError());
-        }
+        DBuf<uint32_t> Mw, lead, pcol, order, state, panel;
+        Mw.alloc(ar, (size_t)nC * nb, st);
+        lead.alloc(ar, nC, st);
+        pcol.alloc(ar, nC, st);
+        order.alloc(ar, std::min(nC, nb), st);
+        state.alloc(ar, 4, st);
+        panel.alloc(ar, 3 * KP, st);
+        GB_CUDA(cudaMemcpyAsync(Mw.p, E->dprime.p, 4ull * nC * nb, cudaMemcpyDeviceToDevice, st));
+        GB_CUDA(cudaMemsetAsync(state.p, 0, 16, st));
+        Rref X{Mw.p, lead.p, pcol.p, order.p, state.p, panel.p, nC, nb};
+        k_leads<<<nC, 256, 0, st>>>(X);
+        counted();
         uint32_t *h = static_cast<uint32_t *>(pinned(S, 64));
-        GB_CUDA(cudaMemcpyAsync(h, state.p, 4, cudaMemcpyDeviceToHost, st));
-        GB_CUDA(cudaMemcpyAsync(h + 2, work.p, 16, cudaMemcpyDeviceToHost, st));
+        const size_t pan_bytes = 4ull * KP * nb;
+        const bool pan_smem = pan_bytes <= 200 * 1024;
+        if (pan_smem)
+            GB_CUDA(cudaFuncSetAttribute(k_panel_rref<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pan_bytes));
+        // rounds are launched in groups; a group's rounds after the last pivot do nothing
+        // every round turns each of its rows into a pivot row or a zero row
+        const uint32_t maxrounds = (nC + KP - 1) / KP + 1;
+        uint32_t rounds = 0;
+        for (;;) {
+            const uint32_t group = rounds == 0 ? 2 : 4;
+            for (uint32_t g = 0; g < group; ++g) {
+                k_pick_panel<<<1, 1024, 0, st>>>(X);
+                if (pan_smem) k_panel_rref<true><<<1, PT, pan_bytes, st>>>(X, S->fp);
+                else k_panel_rref<false><<<1, PT, 0, st>>>(X, S->fp);
+                k_eliminate<<<nC, 256, 0, st>>>(X, S->fp);
+                counted(3);
+            }
+            rounds += group;
+            GB_CUDA(cudaMemcpyAsync(h, state.p, 16, cudaMemcpyDeviceToHost, st));
+            sync(S);
+            if (h[1] == 0 || h[3] <= h[1] || rounds >= maxrounds) break;
+        }
+        // one more pick confirms that no non-zero non-pivot row is left
+        k_pick_panel<<<1, 1024, 0, st>>>(X);
+        counted();
+        GB_CUDA(cudaMemcpyAsync(h, state.p, 16, cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaMemcpyAsync(h + 4, work.p, 16, cudaMemcpyDeviceToHost, st));
         sync(S);
+        if (h[1] != 0) fail(GB_EDEVICE, "RREF: rows left after the last round");
         E->rank = h[0];
-        std::memcpy(E->work, h + 2, 16);
+        std::memcpy(E->work, h + 4, 16);
         E->rref.alloc(ar, (size_t)E->rank * nb, st);
         E->rpiv.alloc(ar, E->rank, st);
         if (E->rank) {
-            k_sort_rows<<<E->rank, 256, 0, st>>>(X, E->rref.p, E->rpiv.p);
+            k_gather_rref<<<E->rank, 256, 0, st>>>(X, E->rank, E->rref.p, E->rpiv.p);
             counted();
         }
-        GB_CUDA(cudaGetLastError());
     }
     GB_CUDA(cudaEventRecord(S->ev[4], st));
     if (!echelon) {
@@ -433,34 +777,45 @@ void append_echelon(gb_system *S, gb_echelon *E, std::vector<Mono> &lms, std::ve
 
 void replace_tails(gb_system *S, gb_echelon *E, const std::vector<uint32_t> &elems,
                    std::vector<uint32_t> &off, std::vector<uint8_t> &exps, std::vector<uint32_t> &cf) {
-    // the reduced tail of element elems[i] is row i of D'; its leading monomial is kept
+    // element elems[i] becomes LM(elems[i]) + (row i of D'), compacted on the device
+    Arena &ar = S->ctx->arena;
     cudaStream_t st = S->stream;
-    const uint32_t nC = E->nC, nb = E->nb, n = S->n;
+    const uint32_t rows = (uint32_t)elems.size(), nb = E->nb, n = S->n;
     gb_macaulay *Mac = E->mac;
-    std::vector<uint32_t> D((size_t)nC * nb);
-    std::vector<uint32_t> npcols(nb);
-    std::vector<uint4> dict(Mac->ndict);
-    if (nC && nb) GB_CUDA(cudaMemcpyAsync(D.data(), E->dprime.p, 4ull * nC * nb, cudaMemcpyDeviceToHost, st));
-    if (nb) GB_CUDA(cudaMemcpyAsync(npcols.data(), Mac->nonpiv.p, 4ull * nb, cudaMemcpyDeviceToHost, st));
-    if (Mac->ndict) GB_CUDA(cudaMemcpyAsync(dict.data(), Mac->dict.p, 16ull * Mac->ndict, cudaMemcpyDeviceToHost, st));
-    sync(S);
     off.assign(1, 0);
     exps.clear();
     cf.clear();
-    for (uint32_t i = 0; i < elems.size(); ++i) {
-        const Mono &l = S->lm[elems[i]];
-        exps.insert(exps.end(), l.e, l.e + n);
-        cf.push_back(1);
-        if (i < nC)
-            for (uint32_t j = 0; j < nb; ++j) {
-                const uint32_t v = D[(size_t)i * nb + j];
-                if (!v) continue;
-                const uint8_t *e = reinterpret_cast<const uint8_t *>(&dict[npcols[j]]);
-                exps.insert(exps.end(), e, e + n);
-                cf.push_back(v);
-            }
-        off.push_back((uint32_t)cf.size());
-    }
+    if (!rows) return;
+    DBuf<uint32_t> cnt, doff;
+    DBuf<uint4> lead;
+    cnt.alloc(ar, rows, st);
+    doff.alloc(ar, (size_t)rows + 1, st);
+    lead.alloc(ar, rows, st);
+    std::vector<uint4> hl(rows);
+    for (uint32_t i = 0; i < rows; ++i) hl[i] = to_u4(S->lm[elems[i]]);
+    char *h = static_cast<char *>(pinned(S, 20ull * rows + 64));
+    std::memcpy(h, hl.data(), 16ull * rows);
+    GB_CUDA(cudaMemcpyAsync(lead.p, h, 16ull * rows, cudaMemcpyHostToDevice, st));
+    k_count_rows_plus<<<rows, 256, 0, st>>>(E->dprime.p, rows, E->nC, nb, cnt.p);
+    counted();
+    exclusive_scan(ar, cnt.p, doff.p, rows, st);
+    uint32_t *ho = reinterpret_cast<uint32_t *>(h + 16ull * rows);
+    GB_CUDA(cudaMemcpyAsync(ho, doff.p, 4ull * (rows + 1), cudaMemcpyDeviceToHost, st));
+    sync(S);
+    off.assign(ho, ho + rows + 1);
+    const uint64_t T = off[rows];
+    DBuf<uint8_t> dex;
+    DBuf<uint32_t> dcf;
+    dex.alloc(ar, T * n, st);
+    dcf.alloc(ar, T, st);
+    k_pack_rows<<<rows, 256, 0, st>>>(E->dprime.p, rows, E->nC, nb, Mac->nonpiv.p, Mac->dict.p, lead.p,
+                                      doff.p, n, dex.p, dcf.p);
+    counted();
+    exps.resize(T * n);
+    cf.resize(T);
+    GB_CUDA(cudaMemcpyAsync(exps.data(), dex.p, T * n, cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(cf.data(), dcf.p, 4 * T, cudaMemcpyDeviceToHost, st));
+    sync(S);
 }
 
 }  // namespace gb

@@ -255,7 +255,7 @@ __global__ void k_place_pivots(uint32_t N, const uint32_t *__restrict__ is_piv,
             O.flags[r] = (uint8_t)(FLAG_PIVOT | FLAG_REDUCER);
         }
         O.pcols[r] = c;
-        O.colpos[c] = r;
+        O.colpos[c] = r | 0x80000000u;
     } else {
         const uint32_t q = c - pidx[c];
         if (q >= O.nb) { atomicOr(O.err, 16u); return; }
