@@ -4,7 +4,8 @@
  * Problem (Sec. 1): R = F_p[x1..xn] with a term order, I = <f1..fm>; compute a Groebner basis of I.
  * The library runs the data-parallel hot path of the F4 method on one GPU:
  *   - symbolic preprocessing SP : batch -> (T, R, Pi) (Def. 5.2), realised as the two-pass FBSP
- *     pipeline of Algorithm 1 with the one-step reduction closure (Rem. 3.3, Def. 11.2);
+ *     pipeline of the FBSP algorithm (Sec. 10) with the one-step reduction closure (Rem. 3.3;
+ *     the support-closure definition of Sec. 11);
  *   - exact structured elimination of the Macaulay matrix A (Def. 3.1) over F_p: pivot / non-pivot
  *     split, sparse row reduction, reduced echelon form of the remaining block (Sec. 9.2), with
  *     Barrett / Montgomery modular arithmetic (Sec. 8);
@@ -151,7 +152,7 @@ gb_status gb_system_destroy(gb_system *sys);
 
 /* ---- the hot path --------------------------------------------------------------------------- */
 
-/* Symbolic preprocessing (Def. 5.2, Algorithm 1) of the r shifted rows (t_i, g_{k_i}) of the
+/* Symbolic preprocessing (Def. 5.2, the FBSP algorithm (Sec. 10)) of the r shifted rows (t_i, g_{k_i}) of the
    system's current basis.  t_exps: r * nvars host bytes; k: r basis indices.  Equal (t, k) rows
    collapse.  closure != 0 adds, for every dictionary monomial m that is not the leading monomial of
    a given row and is divisible by the leading monomial of a non-redundant basis element, the

@@ -9,8 +9,9 @@
  * It follows the paper step by step, in the paper's notation:
  *   - batch reduction by a Macaulay matrix whose rows are shifted reducers t*g (Sec. 2.3, Def. 3.1);
  *   - symbolic preprocessing SP : batch -> (T, R, Pi) with the one-step reduction closure
- *     (Def. 5.2, Rem. 3.3, Def. 11.2) and the dictionary T = Sort(Set(M(R))) (Sec. 5.1);
- *   - CSR layout Pi = (row_ptr, col_ind, val, dict_keys, row_meta) (Def. 5.2, Algorithm 1);
+ *     (Def. 5.2, Rem. 3.3, the support-closure definition of Sec. 11) and the dictionary
+ *     T = Sort(Set(M(R))) (Sec. 5.1);
+ *   - CSR layout Pi = (row_ptr, col_ind, val, dict_keys, row_meta) (Def. 5.2, the FBSP algorithm (Sec. 10));
  *   - structured elimination: pivot / non-pivot split, row reduction of the non-pivot rows by the
  *     pivot rows, then reduced echelon form of the remaining block (Sec. 9.2);
  *   - reconstruction of new basis elements and the basis update (Sec. 4.2, step 4).
@@ -358,7 +359,7 @@ static int dict_index(const dict_ctx *D, const omono *m) { /* binary search, des
         if (c == 0) return mid;
         if (c > 0) hi = mid - 1; else lo = mid + 1;
     }
-    abort(); /* every row monomial is in T (Thm. 11.4) */
+    abort(); /* every row monomial is in T (the dictionary-correctness theorem of Sec. 11) */
 }
 
 static int row_cmp_final(const void *x, const void *y) {
@@ -430,7 +431,7 @@ int or_step(osys *S) {
         if (u == 0 || rows[u - 1].k != rows[a].k || !m_eq(&rows[u - 1].t, &rows[a].t, n)) rows[u++] = rows[a];
     nr = u;
 
-    /* Symbolic preprocessing with the one-step reduction closure (Rem. 3.3, Def. 11.2):
+    /* Symbolic preprocessing with the one-step reduction closure (Rem. 3.3, the support-closure definition of Sec. 11):
        T = supports of the rows, Done = LMs of the pair rows; every m in T \ Done gets the
        reducer row (m / LM(g), g) of R5, whose support joins T. */
     oset T, Done;
@@ -500,7 +501,7 @@ int or_step(osys *S) {
     while (nA < nr && rows[nA].pivot) ++nA;
     int nC = nr - nA;
 
-    /* CSR in the row order: Pass 1 lengths and exclusive prefix sums, Pass 2 fill (Algorithm 1) */
+    /* CSR in the row order: Pass 1 lengths and exclusive prefix sums, Pass 2 fill (the FBSP algorithm (Sec. 10)) */
     uint32_t *row_ptr = (uint32_t *)xrealloc(NULL, sizeof(uint32_t) * (size_t)(nr + 1));
     row_ptr[0] = 0;
     for (int a = 0; a < nr; ++a) row_ptr[a + 1] = row_ptr[a] + (uint32_t)S->g[rows[a].k].len;

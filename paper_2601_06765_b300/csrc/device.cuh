@@ -1,5 +1,5 @@
 // device.cuh -- register-level primitives shared by the kernels: F_p arithmetic (Sec. 8) and
-// packed monomials with an injective, order-refining key (Sec. 7.3, Assumption 11.1).
+// packed monomials with an injective, order-refining key (Sec. 7.3; the key assumption of Sec. 11).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -124,7 +124,8 @@ __device__ __forceinline__ uint32_t byte_of(uint4 m, int i) {
 // C(n + d - 1, n) counts the monomials of degree < d.  Within degree d, a monomial b is smaller
 // than a iff at the last index where they differ b has the larger exponent; fixing b_n..b_{j+2} to
 // a's and letting b_{j+1} exceed a_{j+1} leaves the first j variables to share a total below S_j,
-// which C(S_j + j - 1, j) counts.  The rank is injective and order-preserving (Assumption 11.1),
+// which C(S_j + j - 1, j) counts.  The rank is injective and order-preserving (the key assumption
+// of Sec. 11),
 // so it serves as MonKey, and as a bitmap index in [0, C(n + D, n)) for degrees <= D.
 //
 // tab (shared memory): tab[d] = C(n + d - 1, n) for d in [0, D], then for j = 1..n-1 the row

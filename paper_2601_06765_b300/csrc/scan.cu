@@ -1,6 +1,7 @@
 // scan.cu -- exclusive prefix sums of u32 arrays: the "plan" step of count -> plan -> fill
-// (Sec. 7.1, Algorithm 1).  Tiles of 2048 values per 256-thread block: per-thread serial sums,
-// a warp-shuffle scan of the thread sums, then tile offsets from a recursive scan of tile totals.
+// (Sec. 7.1; the FBSP algorithm of Sec. 10).  Tiles of 2048 values per 256-thread block:
+// per-thread serial sums, a warp-shuffle scan of the thread sums, then tile offsets from a
+// recursive scan of tile totals.
 #include "internal.hpp"
 
 namespace gb {

@@ -1,6 +1,6 @@
 // sp.cu -- symbolic preprocessing SP : batch -> (T, R, Pi) (Def. 5.2) as the two-pass FBSP
-// pipeline of Algorithm 1, with the one-step reduction closure of Rem. 3.3 run as bulk frontier
-// rounds (Sec. 7.2).
+// pipeline (the algorithm of Sec. 10), with the one-step reduction closure of Rem. 3.3 run as
+// bulk frontier rounds (Sec. 7.2).
 //
 // Keys.  Every monomial of the batch has degree <= D (the step degree), so its dense grevlex rank
 // (device.cuh) lies in [0, C(n + D, n)).  Setification + ordering of T (Sec. 5.1) is then a
@@ -17,7 +17,7 @@
 //   4. dictionary: popcount scan, columns, dictionary monomials scattered to their columns
 //   5. row order: pivot rows by leading column (a scan over the pivot-column flags), then the
 //      non-pivot given rows in the order the host fixed
-//   6. CSR: count (row lengths) -> exclusive scan (row_ptr) -> fill (col_ind, val) (Thm. 11.1:
+//   6. CSR: count (row lengths) -> exclusive scan (row_ptr) -> fill (col_ind, val) (the race-freedom theorem of Sec. 11:
 //      every row writes its own segment [row_ptr[i], row_ptr[i+1]))
 #include <algorithm>
 

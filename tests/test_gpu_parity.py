@@ -1,8 +1,9 @@
 """Parity of the CUDA path with the CPU oracle, bit for bit (integer work: no tolerance).
 
-Every F4 step is compared: the dictionary T (Thm. 11.4), the row metadata and the CSR plan Pi
-(Thm. 11.5), the reduced non-pivot block D' and RREF(D') (Sec. 9.2), the redundancy flags, the new
-basis elements, and finally the reduced Groebner basis.  All calls go through the C ABI."""
+Every F4 step is compared: the dictionary T (the dictionary-correctness theorem of Sec. 11), the
+row metadata and the CSR plan Pi (the matrix-materialisation theorem of Sec. 11), the reduced
+non-pivot block D' and RREF(D') (Sec. 9.2), the redundancy flags, the new basis elements, and
+finally the reduced Groebner basis.  All calls go through the C ABI."""
 from __future__ import annotations
 
 import numpy as np
@@ -137,7 +138,8 @@ def test_standalone_sp_and_reduce_match_oracle_steps(ctx):
 
 
 def test_sp_without_closure(ctx):
-    """closure = 0: T is exactly the union of the given rows' supports (Def. 11.2), no reducer rows."""
+    """closure = 0: T is exactly the union of the given rows' supports (the support-closure
+    definition of Sec. 11), no reducer rows."""
     system = synth.dense_system(4, 4, 65521, 77)
     with gb.System(ctx, system) as S:
         t = np.zeros((4, 4), np.uint8)
@@ -155,8 +157,8 @@ def test_sp_without_closure(ctx):
 
 
 def test_dictionary_order_is_grevlex_exhaustive(ctx):
-    """Assumption 11.1 on the device keys: one polynomial holding every monomial of degree <= 6 in
-    4 variables; its dictionary must list all C(10, 4) = 210 monomials in sympy's grevlex order."""
+    """The key assumption of Sec. 11 (injective, order-refining keys) on the device keys: one
+    polynomial holding every monomial of degree <= 6 in 4 variables; its dictionary must list all C(10, 4) = 210 monomials in sympy's grevlex order."""
     from sympy.polys.orderings import grevlex
     n, D = 4, 6
     mons = synth.monomials_upto(n, D)
@@ -170,7 +172,7 @@ def test_dictionary_order_is_grevlex_exhaustive(ctx):
 
 
 def test_determinism(ctx):
-    """Thm. 11.3: the same batch gives byte-identical plans on repeated runs."""
+    """the determinism theorem of Sec. 11: the same batch gives byte-identical plans on repeated runs."""
     system = synth.config1(2)
     dumps = []
     for _ in range(2):

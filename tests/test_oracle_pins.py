@@ -126,9 +126,9 @@ def test_dictionary_matrix_and_closure(system):
 
 
 def check_dictionary_matrix_closure(system, lib=None, limit=100):
-    """Thm. 11.4: T is exactly the union of the row supports, in descending order (sympy's grevlex
-    key).  Thm. 11.5: row i of the CSR is t_i * g_{k_i}, nnz = M = sum |supp g_k|.  Thm. 11.1: the
-    row segments partition [0, M).  Def. 11.2 / Rem. 3.3: every dictionary monomial divisible by a
+    """the dictionary-correctness theorem of Sec. 11: T is exactly the union of the row supports, in descending order (sympy's grevlex
+    key).  the matrix-materialisation theorem of Sec. 11: row i of the CSR is t_i * g_{k_i}, nnz = M = sum |supp g_k|.  the race-freedom theorem of Sec. 11: the
+    row segments partition [0, M).  the support-closure definition of Sec. 11 / Rem. 3.3: every dictionary monomial divisible by a
     non-redundant leading monomial is the leading monomial of a row, and reducer rows use the
     oldest such element."""
     for basis, d in _steps(system, limit=limit, lib=lib):
@@ -197,7 +197,7 @@ def test_reduction_and_echelon_against_library_rref(system):
 
 
 def check_reduction_and_echelon(system, lib=None, limit=6):
-    """Sec. 9.2 / Thm. 11.7: D' spans, with the pivot rows, the row space of A and vanishes on the
+    """Sec. 9.2 / the row-operations theorem of Sec. 11: D' spans, with the pivot rows, the row space of A and vanishes on the
     pivot columns (so it is the unique such reduction), and RREF(D') equals the rows of the full
     reduced echelon form of A whose leading column is a non-pivot column (sympy DomainMatrix over
     GF(p) as the library reference)."""
