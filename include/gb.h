@@ -215,6 +215,36 @@ gb_status gb_server_submit(gb_server *srv, gb_system *sys, uint64_t *ticket);
 gb_status gb_server_poll(gb_server *srv, uint64_t ticket, gb_system **done, gb_status *result);
 gb_status gb_server_destroy(gb_server *srv);
 
+/* ---- sparse reduction without device allocation --------------------------------------------- */
+
+/* Limits of gb_reduce_rows_noalloc: its scratch is a fixed array compiled into the library. */
+#define GB_NOALLOC_MAX_DICT 51200u    /* ndict for p < 2^16 (25600 for larger p) */
+#define GB_NOALLOC_MAX_PIVOTS 16384u  /* pivot rows */
+
+/* The sparse row reduction of gb_reduce_macaulay (D' only, no echelon form), for callers that
+   cannot allocate device memory: code recorded into a CUDA graph by stream capture, or a process
+   whose device memory belongs to another allocator that must not see new allocations between its
+   own calls.  This entry point allocates nothing: it works on the caller's buffers plus one
+   scratch array of about 2.3 MB that is part of the library image (each GPU that loads the
+   library holds it until the process exits).  It has no counterpart in the paper.
+   All pointers are DEVICE pointers on the current device:
+     row_ptr[npivot + nnonpivot + 1], col_ind, val: CSR of the matrix, the npivot pivot rows first
+       (row i monic with leading column pivot_cols[i], pivot_cols ascending), then the non-pivot
+       rows; columns ascending within a row, values in [0, p);
+     nonpivot_cols[nb]: the columns that are no pivot's leading column, ascending;
+     dprime[nnonpivot * nb] (output): the non-pivot rows reduced by the pivot rows, restricted to
+       nonpivot_cols -- the D' of gb_echelon_export.
+   stream: a cudaStream_t of the current device (NULL: the legacy default stream).  The call only
+   enqueues work; it returns before the work finishes.
+   The first call on each device looks up the scratch array's device address (no allocation); make
+   that first call before any stream capture.  Every call uses the same scratch array, so calls
+   whose work overlaps on the GPU (several streams, several host threads) race: serialise them.
+   GB_EINVAL: p not an odd prime below 2^31, or a size above the limits above. */
+gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, uint32_t nnonpivot,
+                                 uint32_t nb, const uint32_t *row_ptr, const uint32_t *col_ind,
+                                 const uint32_t *val, const uint32_t *pivot_cols,
+                                 const uint32_t *nonpivot_cols, uint32_t *dprime, void *stream);
+
 /* ---- diagnostics ---------------------------------------------------------------------------- */
 
 /* Number of CUDA kernels this library has launched in this process so far (all contexts). */

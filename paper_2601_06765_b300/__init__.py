@@ -114,6 +114,7 @@ _SIGS = {
     "gb_server_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)],
     "gb_server_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)],
     "gb_server_destroy": [_vp],
+    "gb_reduce_rows_noalloc": [ctypes.c_uint32] * 5 + [_vp] * 7,
 }
 
 
@@ -330,6 +331,16 @@ def gb_server_poll(srv: int, ticket: int) -> tuple[int | None, int]:
 
 def gb_server_destroy(srv: int) -> None:
     check(lib().gb_server_destroy(srv), "gb_server_destroy")
+
+
+def gb_reduce_rows_noalloc(p: int, ndict: int, npivot: int, nnonpivot: int, nb: int, row_ptr: int,
+                           col_ind: int, val: int, pivot_cols: int, nonpivot_cols: int, dprime: int,
+                           stream: int | None = None) -> None:
+    """The sparse reduction on caller-owned device buffers (integer device addresses); no device
+    memory is allocated.  See include/gb.h for the layout and the limits."""
+    check(lib().gb_reduce_rows_noalloc(p, ndict, npivot, nnonpivot, nb, row_ptr, col_ind, val,
+                                       pivot_cols, nonpivot_cols, dprime, stream or None),
+          "gb_reduce_rows_noalloc")
 
 
 # ---- convenience wrappers -----------------------------------------------------------------------

@@ -7,6 +7,10 @@
 #include "internal.hpp"
 
 namespace gb {
+void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint32_t nb,
+                         const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
+                         const uint32_t *pcols, const uint32_t *nonpiv, uint32_t *dprime,
+                         cudaStream_t st);
 gb_status f4_step(gb_system *S, gb_step_stats *stats);
 gb_status groebner(gb_system *S, gb_run_stats *stats);
 void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F);
@@ -411,6 +415,17 @@ gb_status gb_basis_redundant(const gb_system *S, uint32_t *count, uint8_t *flags
     *count = (uint32_t)S->redundant.size();
     if (flags) std::memcpy(flags, S->redundant.data(), S->redundant.size());
     return GB_OK;
+}
+
+gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, uint32_t nnonpivot,
+                                 uint32_t nb, const uint32_t *row_ptr, const uint32_t *col_ind,
+                                 const uint32_t *val, const uint32_t *pivot_cols,
+                                 const uint32_t *nonpivot_cols, uint32_t *dprime, void *stream) {
+    GB_API_BEGIN
+    reduce_rows_noalloc(p, ndict, npivot, nnonpivot, nb, row_ptr, col_ind, val, pivot_cols, nonpivot_cols,
+                        dprime, static_cast<cudaStream_t>(stream));
+    return GB_OK;
+    GB_API_END
 }
 
 gb_status gb_system_last_step(const gb_system *S, const gb_macaulay **mac, const gb_echelon **ech) {

@@ -281,7 +281,7 @@ static void append_host_poly(gb_system *S, const std::vector<Mono> &mon, const s
     gm_update(S, (uint32_t)(S->lm.size() - 1));
 }
 
-static bool is_prime32(uint32_t q) {
+bool is_prime32(uint32_t q) {
     if (q < 2) return false;
     for (uint32_t d : {2u, 3u, 5u, 7u, 11u, 13u})
         if (q % d == 0) return q == d;

@@ -127,6 +127,7 @@ inline uint4 to_u4(const Mono &m) {
 
 Fp make_fp(uint32_t p);
 uint32_t host_inv(uint32_t a, uint32_t p);
+bool is_prime32(uint32_t q);
 
 // ---- rows handed to symbolic preprocessing -------------------------------------------------
 struct RowSpec {

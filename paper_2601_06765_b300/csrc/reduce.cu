@@ -818,4 +818,81 @@ void replace_tails(gb_system *S, gb_echelon *E, const std::vector<uint32_t> &ele
     sync(S);
 }
 
+// ---- the sparse reduction without device allocation --------------------------------------------
+//
+// Scratch of gb_reduce_rows_noalloc: pivot-column flags (one word per dictionary column), the
+// 32 x 32 chunk triangles (one per 32 pivot rows) and the two work counters of k_reduce, carved
+// out of one fixed array that is part of the library image.  Host code reaches it only through
+// the address cudaGetSymbolAddress returns for the current device.
+constexpr uint32_t NA_COLPOS = 0;
+constexpr uint32_t NA_TRI = GB_NOALLOC_MAX_DICT;
+constexpr uint32_t NA_WORK = NA_TRI + GB_NOALLOC_MAX_PIVOTS * CW;  // even: 8-byte aligned
+constexpr uint32_t NA_WORDS = NA_WORK + 4;
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
+
+namespace {
+__global__ void k_mark_pivot_cols(uint32_t nA, const uint32_t *__restrict__ pcols,
+                                  uint32_t *__restrict__ colpos) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nA) colpos[pcols[k]] = k | 0x80000000u;
+}
+
+uint32_t *noalloc_scratch_for_current_device() {
+    static std::mutex mu;
+    static uint32_t *addr[64] = {};
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(GB_EUNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[dev]) {
+        void *ptr = nullptr;
+        GB_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        addr[dev] = static_cast<uint32_t *>(ptr);
+    }
+    return addr[dev];
+}
+}  // namespace
+
+void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint32_t nb,
+                         const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
+                         const uint32_t *pcols, const uint32_t *nonpiv, uint32_t *dprime,
+                         cudaStream_t st) {
+    if (p < 3 || p >= (1u << 31) || !is_prime32(p)) fail(GB_EINVAL, "p must be an odd prime below 2^31");
+    const Fp fp = make_fp(p);
+    const int mode = fp.small ? A32 : M64;
+    const uint32_t max_dict = fp.small ? GB_NOALLOC_MAX_DICT : GB_NOALLOC_MAX_DICT / 2;
+    if (N > max_dict || nA > GB_NOALLOC_MAX_PIVOTS)
+        fail(GB_EINVAL, "gb_reduce_rows_noalloc: ndict above " + std::to_string(max_dict) +
+                            " or npivot above " + std::to_string(GB_NOALLOC_MAX_PIVOTS));
+    if (nb > N || nA > N) fail(GB_EINVAL, "gb_reduce_rows_noalloc: more pivots or non-pivot columns than columns");
+    if (!nC || !nb) return;
+    if (!row_ptr || !col || !val || (nA && !pcols) || !nonpiv || !dprime)
+        fail(GB_EINVAL, "gb_reduce_rows_noalloc: null device pointer");
+    uint32_t *scr = noalloc_scratch_for_current_device();
+    uint32_t *colpos = scr + NA_COLPOS, *tri = scr + NA_TRI;
+    unsigned long long *work = reinterpret_cast<unsigned long long *>(scr + NA_WORK);
+    const uint32_t nchunks = (nA + CW - 1) / CW;
+    // the array keeps the previous call's contents: clear what the kernels expect at zero
+    GB_CUDA(cudaMemsetAsync(colpos, 0, 4ull * N, st));
+    if (nchunks) GB_CUDA(cudaMemsetAsync(tri, 0, 4ull * nchunks * CW * CW, st));
+    GB_CUDA(cudaMemsetAsync(work, 0, 16, st));
+    if (nA) {
+        k_mark_pivot_cols<<<blocks(nA, 256), 256, 0, st>>>(nA, pcols, colpos);
+        counted();
+        k_build_chunk_tri<<<blocks(nA, 8), 256, 0, st>>>(nA, row_ptr, col, val, pcols, colpos, tri);
+        counted();
+    }
+    const size_t smem = (size_t)N * (mode == A32 ? 4 : 8);
+    if (mode == A32) {
+        GB_CUDA(cudaFuncSetAttribute(k_reduce<1, A32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_reduce<1, A32, true><<<nC, RT, smem, st>>>(nA, nC, N, row_ptr, col, val, pcols, tri, nonpiv, nb, fp,
+                                                     nullptr, dprime, work);
+    } else {
+        GB_CUDA(cudaFuncSetAttribute(k_reduce<1, M64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_reduce<1, M64, true><<<nC, RT, smem, st>>>(nA, nC, N, row_ptr, col, val, pcols, tri, nonpiv, nb, fp,
+                                                     nullptr, dprime, work);
+    }
+    counted();
+}
+
 }  // namespace gb
