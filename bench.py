@@ -118,7 +118,7 @@ def run_ours(args) -> None:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     system = synth.config2(0)
-    ctx = gb.Context(device=local, arena_bytes=8 << 30)
+    ctx = gb.Context(device=local, arena_bytes=32 << 30)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 126 MB L2
 
     def barrier():
@@ -192,6 +192,8 @@ def run_ours(args) -> None:
                 "peak_source": f"{pk['source']} HBM copy bandwidth",
                 "traffic": profile_traffic("k_reduce_config2")}
 
+    batched = measure_batched(gb, synth, ctx) if rank == 0 and not args.no_batch else None
+    served = measure_served(gb, synth, ctx) if rank == 0 and not args.no_batch else None
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
              for k in ("ms_sp", "ms_reduce", "ms_rref", "ms_update", "ms_pairs", "ms_select",
                        "ms_wall")}
@@ -211,6 +213,8 @@ def run_ours(args) -> None:
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": statistics.median(e2e_ms),
                     "h2d_bytes_per_step": input_bytes(system), "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
+            "batched": batched,
+            "served": served,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -220,6 +224,66 @@ def run_ours(args) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def measure_batched(gb, synth, ctx) -> dict:
+    """The multi-prime batch: one n=8 dense quadratic system modulo the 128 largest primes below
+    2^31, run one system after another (plain) and as one gb_batch_groebner call (batched)."""
+    systems = synth.multi_prime_system(synth.largest_primes_below(2 ** 31, 128))
+    out = {"workload": "n=8 dense quadratic system modulo the 128 largest primes below 2^31 "
+                       "(128 independent F4 runs)", "systems": len(systems)}
+    for mode in ("plain", "batched"):
+        hs = [gb.gb_system_create(ctx.h, s) for s in systems]
+        t0 = time.perf_counter()
+        if mode == "plain":
+            stats = [gb.gb_groebner(h) for h in hs]
+        else:
+            stats = gb.gb_batch_groebner(ctx.h, hs)
+        dt = time.perf_counter() - t0
+        for h in hs:
+            gb.gb_system_destroy(h)
+        nnz = sum(st["nnz_total"] for st in stats)
+        out[f"{mode}_ms"] = dt * 1e3
+        out[f"{mode}_nnz_per_s"] = nnz / dt
+    out["speedup"] = out["plain_ms"] / out["batched_ms"]
+    return out
+
+
+def measure_served(gb, synth, ctx, count: int = 300) -> dict:
+    """Poisson stream of served requests (n ~ U{5..11}, 20-66 terms, p = 65521 or 2^31-1) at 0.8x
+    the batched saturation rate; latency = completion - arrival, through gb_server_*."""
+    import numpy as _np
+    reqs = [synth.served_request(i) for i in range(count)]
+    hs = [gb.gb_system_create(ctx.h, s) for s in reqs[:64]]
+    t0 = time.perf_counter()
+    gb.gb_batch_groebner(ctx.h, hs)
+    sat = len(hs) / (time.perf_counter() - t0)
+    for h in hs:
+        gb.gb_system_destroy(h)
+    rate = 0.8 * sat
+    arrivals = synth.poisson_arrivals(count, rate)
+    srv = gb.gb_server_create(ctx.h, 150 << 30, 32)
+    pending, lat = {}, []
+    start = time.perf_counter()
+    nxt = 0
+    while nxt < count or pending:
+        now = time.perf_counter() - start
+        while nxt < count and arrivals[nxt] <= now:
+            pending[gb.gb_server_submit(srv, gb.gb_system_create(ctx.h, reqs[nxt]))] = arrivals[nxt]
+            nxt += 1
+        for t in list(pending):
+            h, st = gb.gb_server_poll(srv, t)
+            if h is not None:
+                lat.append(time.perf_counter() - start - pending.pop(t))
+                gb.gb_system_destroy(h)
+        time.sleep(0.0005)
+    wall = time.perf_counter() - start
+    gb.gb_server_destroy(srv)
+    lat_ms = _np.array(lat) * 1e3
+    return {"workload": f"{count} Poisson requests, n ~ U{{5..11}}, 20-66 terms, p in {{65521, 2^31-1}}",
+            "rate_per_s": rate, "saturation_per_s": sat, "systems_per_s": count / wall,
+            "p50_ms": float(_np.percentile(lat_ms, 50)), "p99_ms": float(_np.percentile(lat_ms, 99)),
+            "hbm_cap_bytes": 150 << 30, "slots": 32}
 
 
 def cpu_baseline(system: dict) -> dict:
@@ -278,6 +342,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and served lines")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

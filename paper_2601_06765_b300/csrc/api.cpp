@@ -11,8 +11,8 @@ void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint3
                          const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
                          const uint32_t *pcols, const uint32_t *nonpiv, uint32_t *dprime,
                          cudaStream_t st);
-gb_status f4_step(gb_system *S, gb_step_stats *stats);
-gb_status groebner(gb_system *S, gb_run_stats *stats);
+void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *stats);
+void groebner_batch(const std::vector<gb_system *> &Ss);
 void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F);
 std::vector<RowSpec> order_rows(const gb_system *S, std::vector<std::pair<Mono, uint32_t>> tk);
 
@@ -30,6 +30,51 @@ void cuda_check(cudaError_t e, const char *what) {
         throw Error(GB_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
     }
     throw Error(GB_EDEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void opt_in_smem(const void *kernel) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, bool> done;
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    if (done.count({dev, kernel})) return;
+    int optin = 0;
+    GB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    GB_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    GB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes));
+    done[{dev, kernel}] = true;
+}
+
+// ---- page-locked staging of the batch in flight --------------------------------------------------
+
+void *ctx_pinned(gb_ctx *ctx, size_t bytes) {
+    if (bytes > ctx->stage_bytes) {
+        if (ctx->stage) {
+            ctx_sync(ctx);  // copies in flight may still use the old area
+            GB_CUDA(cudaFreeHost(ctx->stage));
+            ctx->stage = nullptr;
+        }
+        const size_t sz = std::max<size_t>({bytes, 2 * ctx->stage_bytes, size_t(4) << 20});
+        GB_CUDA(cudaHostAlloc(&ctx->stage, sz, cudaHostAllocDefault));
+        ctx->stage_bytes = sz;
+    }
+    return ctx->stage;
+}
+
+void ctx_sync(gb_ctx *ctx) {
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->arena.flush(ctx->stream);
+}
+
+void Stage::upload(gb_ctx *ctx, DBuf<char> &d) {
+    d.alloc(ctx->arena, h.size() + 16, ctx->stream);
+    char *hp = static_cast<char *>(ctx_pinned(ctx, h.size() + 16));
+    std::memcpy(hp, h.data(), h.size());
+    GB_CUDA(cudaMemcpyAsync(d.p, hp, h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    ctx_sync(ctx);
 }
 
 // ---- arena ------------------------------------------------------------------------------------
@@ -130,14 +175,14 @@ using namespace gb;
 
 static void use_device(const gb_ctx *ctx) { GB_CUDA(cudaSetDevice(ctx->device)); }
 
-// order the system's work after whatever the caller queued on the context's stream
-static void enter(gb_system *S) {
-    use_device(S->ctx);
-    if (S->ctx->stream && S->stream != S->ctx->stream && !S->ctx->own_stream) {
-        GB_CUDA(cudaEventRecord(S->ev[7], S->ctx->stream));
-        GB_CUDA(cudaStreamWaitEvent(S->stream, S->ev[7], 0));
-    }
-}
+// Systems run on their context's stream, so work the caller queued there comes first.  Every
+// call that touches the stream holds the context's lock for its duration.
+namespace {
+struct Enter {
+    std::lock_guard<std::recursive_mutex> g;
+    explicit Enter(gb_ctx *ctx) : g(ctx->mu) { use_device(ctx); }
+};
+}  // namespace
 
 extern "C" {
 
@@ -189,6 +234,7 @@ gb_status gb_ctx_create(int device, const gb_ctx_opts *opts, gb_ctx **out) {
         GB_CUDA(cudaMalloc(&p, bytes));
         ctx->arena.init(p, bytes, true);
     }
+    for (auto &e : ctx->ev) GB_CUDA(cudaEventCreate(&e));
     *out = ctx.release();
     return GB_OK;
     GB_API_END
@@ -200,6 +246,9 @@ gb_status gb_ctx_destroy(gb_ctx *ctx) {
     use_device(ctx);
     cudaDeviceSynchronize();
     ctx->arena.release();
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return GB_OK;
@@ -221,16 +270,10 @@ gb_status gb_system_create(gb_ctx *ctx, uint32_t nvars, uint32_t p, gb_order ord
     if (order != GB_GREVLEX) fail(GB_EUNSUPPORTED, "only grevlex is implemented");
     if (F && F->npolys && (!F->poly_off || ((!F->exps || !F->coeffs) && F->poly_off[F->npolys])))
         fail(GB_EINVAL, "null arrays in the input system");
-    use_device(ctx);
+    Enter entered(ctx);
     auto S = std::make_unique<gb_system>();
     S->ctx = ctx;
-    GB_CUDA(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
-    S->own_stream = true;
-    for (auto &e : S->ev) GB_CUDA(cudaEventCreate(&e));
-    if (ctx->stream && !ctx->own_stream) {
-        GB_CUDA(cudaEventRecord(S->ev[7], ctx->stream));
-        GB_CUDA(cudaStreamWaitEvent(S->stream, S->ev[7], 0));
-    }
+    S->stream = ctx->stream;
     system_init(S.get(), nvars, p, F);
     *out = S.release();
     return GB_OK;
@@ -240,7 +283,7 @@ gb_status gb_system_create(gb_ctx *ctx, uint32_t nvars, uint32_t p, gb_order ord
 gb_status gb_system_destroy(gb_system *S) {
     GB_API_BEGIN
     if (!S) return GB_EINVAL;
-    use_device(S->ctx);
+    Enter entered(S->ctx);
     cudaStreamSynchronize(S->stream);
     S->last_ech.reset();
     S->last_mac.reset();
@@ -249,9 +292,6 @@ gb_status gb_system_destroy(gb_system *S) {
     S->boff.reset();
     S->blen.reset();
     S->ctx->arena.flush(S->stream);
-    if (S->pinned) cudaFreeHost(S->pinned);
-    for (auto &e : S->ev) cudaEventDestroy(e);
-    if (S->own_stream) cudaStreamDestroy(S->stream);
     delete S;
     return GB_OK;
     GB_API_END
@@ -262,18 +302,21 @@ gb_status gb_symbolic_preprocess(gb_system *S, uint32_t r, const uint8_t *t_exps
     GB_API_BEGIN
     if (!S || !out || (r && (!t_exps || !k))) fail(GB_EINVAL, "null argument");
     *out = nullptr;
-    enter(S);
+    Enter entered(S->ctx);
     std::vector<std::pair<Mono, uint32_t>> tk(r);
     for (uint32_t i = 0; i < r; ++i) {
         Mono t{};
         std::memcpy(t.e, t_exps + (size_t)i * S->n, S->n);
         tk[i] = {t, k[i]};
     }
-    std::vector<RowSpec> rows = order_rows(S, std::move(tk));
-    std::vector<uint32_t> nonred;
+    std::vector<SpTask> tasks(1);
+    tasks[0].S = S;
+    tasks[0].rows = order_rows(S, std::move(tk));
+    tasks[0].closure = closure != 0;
     for (uint32_t g = 0; g < S->redundant.size(); ++g)
-        if (!S->redundant[g]) nonred.push_back(g);
-    *out = symbolic_preprocess(S, rows, closure != 0, nonred).release();
+        if (!S->redundant[g]) tasks[0].nonred.push_back(g);
+    symbolic_preprocess(tasks);
+    *out = tasks[0].out.release();
     return GB_OK;
     GB_API_END
 }
@@ -286,7 +329,7 @@ gb_status gb_macaulay_export(const gb_macaulay *M, gb_macaulay_host *h) {
     GB_API_BEGIN
     if (!M || !h) fail(GB_EINVAL, "null argument");
     gb_system *S = M->sys;
-    use_device(S->ctx);
+    Enter entered(S->ctx);
     h->nvars = M->n;
     h->nrows = M->nrows;
     h->ndict = M->ndict;
@@ -302,7 +345,7 @@ gb_status gb_macaulay_export(const gb_macaulay *M, gb_macaulay_host *h) {
     if (h->dict_exps) { dict.resize(M->ndict); d2h(S, dict.data(), M->dict.p, 16ull * M->ndict); }
     if (h->row_t) { rt.resize(M->nrows); d2h(S, rt.data(), M->row_t.p, 16ull * M->nrows); }
     if (h->row_flags) { fl.resize(M->nrows); d2h(S, fl.data(), M->row_flags.p, M->nrows); }
-    sync(S);
+    ctx_sync(S->ctx);
     for (uint32_t i = 0; h->dict_exps && i < M->ndict; ++i)
         std::memcpy(h->dict_exps + (size_t)i * n, &dict[i], n);
     for (uint32_t i = 0; h->row_t && i < M->nrows; ++i) std::memcpy(h->row_t + (size_t)i * n, &rt[i], n);
@@ -323,8 +366,9 @@ gb_status gb_reduce_macaulay(gb_macaulay *M, gb_echelon **out) {
     GB_API_BEGIN
     if (!M || !out) fail(GB_EINVAL, "null argument");
     *out = nullptr;
-    enter(M->sys);
-    *out = reduce_rows(M, true).release();
+    Enter entered(M->sys->ctx);
+    auto Es = reduce_rows({M}, true);
+    *out = Es[0].release();
     return GB_OK;
     GB_API_END
 }
@@ -333,7 +377,7 @@ gb_status gb_echelon_export(const gb_echelon *E, gb_echelon_host *h) {
     GB_API_BEGIN
     if (!E || !h) fail(GB_EINVAL, "null argument");
     gb_system *S = E->mac->sys;
-    use_device(S->ctx);
+    Enter entered(S->ctx);
     h->nC = E->nC;
     h->nb = E->nb;
     h->rank = E->rank;
@@ -341,7 +385,7 @@ gb_status gb_echelon_export(const gb_echelon *E, gb_echelon_host *h) {
     if (h->dprime) d2h(S, h->dprime, E->dprime.p, 4ull * E->nC * E->nb);
     if (h->rref_piv) d2h(S, h->rref_piv, E->rpiv.p, 4ull * E->rank);
     if (h->rref) d2h(S, h->rref, E->rref.p, 4ull * E->rank * E->nb);
-    sync(S);
+    ctx_sync(S->ctx);
     return GB_OK;
     GB_API_END
 }
@@ -357,17 +401,22 @@ gb_status gb_echelon_destroy(gb_echelon *E) {
 gb_status gb_f4_step(gb_system *S, gb_step_stats *stats) {
     GB_API_BEGIN
     if (!S) fail(GB_EINVAL, "null system");
-    if (S->finished) return GB_DONE;
-    enter(S);
-    return f4_step(S, stats);
+    if (S->finished || S->pairs.empty()) return GB_DONE;
+    Enter entered(S->ctx);
+    std::vector<gb_step_stats> st;
+    f4_steps({S}, &st);
+    if (stats) *stats = st[0];
+    return GB_OK;
     GB_API_END
 }
 
 gb_status gb_groebner(gb_system *S, gb_run_stats *stats) {
     GB_API_BEGIN
     if (!S) fail(GB_EINVAL, "null system");
-    enter(S);
-    return groebner(S, stats);
+    Enter entered(S->ctx);
+    groebner_batch({S});
+    if (stats) *stats = S->run;
+    return GB_OK;
     GB_API_END
 }
 
@@ -385,7 +434,7 @@ gb_status gb_basis_export(const gb_system *S, int reduced, gb_polys_host *h) {
         return GB_OK;
     }
     gb_system *Sm = const_cast<gb_system *>(S);
-    use_device(S->ctx);
+    Enter entered(S->ctx);
     const uint32_t ng = (uint32_t)S->lm.size();
     uint64_t T = 0;
     for (uint32_t l : S->len) T += l;
@@ -396,7 +445,7 @@ gb_status gb_basis_export(const gb_system *S, int reduced, gb_polys_host *h) {
     std::vector<uint32_t> cf(S->nterms);
     d2h(Sm, mon.data(), S->bmon.p, 16ull * S->nterms);
     d2h(Sm, cf.data(), S->bcf.p, 4ull * S->nterms);
-    sync(Sm);
+    ctx_sync(Sm->ctx);
     uint64_t o = 0;
     for (uint32_t g = 0; g < ng; ++g) {
         if (h->poly_off) h->poly_off[g] = (uint32_t)o;

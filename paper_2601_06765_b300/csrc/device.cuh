@@ -155,6 +155,17 @@ __device__ __forceinline__ uint32_t rank_to_col(uint32_t r, const uint32_t *bits
     return N - 1u - (word_prefix[w] + __popc(below));
 }
 
+// block -> job of a grouped launch: bstart[j] is the first block of job j (non-decreasing, nj
+// entries); the largest j with bstart[j] <= blockIdx.x (jobs without blocks are skipped)
+__device__ __forceinline__ int job_of_block(const uint32_t *__restrict__ bstart, int nj) {
+    int lo = 0, hi = nj - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bstart[mid] <= blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 #endif  // __CUDACC__
 
 }  // namespace gb

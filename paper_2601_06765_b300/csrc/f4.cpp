@@ -12,6 +12,7 @@
 //   reduced, sorted by leading monomial descending.
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
 #include <numeric>
 
 #include "internal.hpp"
@@ -101,26 +102,89 @@ uint32_t host_inv(uint32_t a, uint32_t p) {
     return (uint32_t)(s0 < 0 ? s0 + p : s0);
 }
 
-// ---- small host helpers -----------------------------------------------------------------------
+// ---- host workers ----------------------------------------------------------------------------
+//
+// The per-system host control of a batch (pair updates, selection, minimalisation) is independent
+// across systems, so it runs on a small persistent pool; the calling thread takes part.
 
-void *pinned(gb_system *S, size_t bytes) {
-    if (bytes > S->pinned_bytes) {
-        if (S->pinned) {
-            sync(S);
-            GB_CUDA(cudaFreeHost(S->pinned));
-            S->pinned = nullptr;
-        }
-        // page-locked allocations cost about a millisecond each: start at 1 MiB, grow 4x
-        const size_t sz = std::max<size_t>({bytes, 4 * S->pinned_bytes, size_t(1) << 20});
-        GB_CUDA(cudaHostAlloc(&S->pinned, sz, cudaHostAllocDefault));
-        S->pinned_bytes = sz;
+struct HostPool {
+    explicit HostPool(unsigned nthreads) {
+        for (unsigned t = 0; t < nthreads; ++t) th.emplace_back([this] { loop(); });
     }
-    return S->pinned;
-}
+    ~HostPool() {
+        {
+            std::lock_guard<std::mutex> g(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (auto &t : th) t.join();
+    }
+    void run(size_t n, const std::function<void(size_t)> &f) {
+        {
+            std::lock_guard<std::mutex> g(mu);
+            fn = &f;
+            count = n;
+            next = 0;
+            err = nullptr;
+            pending = (unsigned)th.size();
+            ++gen;
+        }
+        cv.notify_all();
+        work();
+        std::unique_lock<std::mutex> lk(mu);
+        done_cv.wait(lk, [&] { return pending == 0; });
+        fn = nullptr;
+        if (err) std::rethrow_exception(err);
+    }
 
-void sync(gb_system *S) {
-    GB_CUDA(cudaStreamSynchronize(S->stream));
-    S->ctx->arena.flush(S->stream);
+   private:
+    void work() {
+        for (size_t i; (i = next.fetch_add(1)) < count;) {
+            try {
+                (*fn)(i);
+            } catch (...) {
+                std::lock_guard<std::mutex> g(mu);
+                if (!err) err = std::current_exception();
+            }
+        }
+    }
+    void loop() {
+        uint64_t seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return stop || gen != seen; });
+                if (stop) return;
+                seen = gen;
+            }
+            work();
+            std::lock_guard<std::mutex> g(mu);
+            if (--pending == 0) done_cv.notify_all();
+        }
+    }
+    std::vector<std::thread> th;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    const std::function<void(size_t)> *fn = nullptr;
+    size_t count = 0;
+    std::atomic<size_t> next{0};
+    uint64_t gen = 0;
+    unsigned pending = 0;
+    bool stop = false;
+    std::exception_ptr err;
+};
+
+void parallel_for(gb_ctx *ctx, size_t n, const std::function<void(size_t)> &fn) {
+    if (n <= 1) {
+        for (size_t i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    if (!ctx->pool) {
+        unsigned hw = std::thread::hardware_concurrency();
+        if (!hw) hw = 4;
+        ctx->pool = std::make_unique<HostPool>(std::min(hw, 16u) - 1);
+    }
+    ctx->pool->run(n, fn);
 }
 
 // ---- critical pairs: UPDATE of Becker and Weispfenning (Gebauer-Moeller criteria) --------------
@@ -244,40 +308,14 @@ std::vector<RowSpec> order_rows(const gb_system *S, std::vector<std::pair<Mono, 
     return out;
 }
 
-// upload one normalised polynomial (host terms) as a new basis element and run UPDATE
-static void append_host_poly(gb_system *S, const std::vector<Mono> &mon, const std::vector<uint32_t> &cf) {
-    Arena &ar = S->ctx->arena;
-    cudaStream_t st = S->stream;
-    const uint32_t len = (uint32_t)mon.size();
-    const uint64_t base = S->nterms;
-    const size_t ng0 = S->off.size();
-    if (base + len > S->bmon.n) {
-        S->bmon.grow(ar, std::max<size_t>(base + len, std::max<size_t>(1024, 2 * S->bmon.n)), base, st);
-        S->bcf.grow(ar, std::max<size_t>(base + len, std::max<size_t>(1024, 2 * S->bcf.n)), base, st);
-    }
-    if (ng0 + 1 > S->boff.n) {
-        S->boff.grow(ar, std::max<size_t>(ng0 + 1, std::max<size_t>(64, 2 * S->boff.n)), ng0, st);
-        S->blen.grow(ar, std::max<size_t>(ng0 + 1, std::max<size_t>(64, 2 * S->blen.n)), ng0, st);
-    }
-    char *h = static_cast<char *>(pinned(S, 20ull * len + 64));
-    sync(S);  // earlier uploads from the staging buffer have landed
-    std::vector<uint4> m4(len);
-    for (uint32_t j = 0; j < len; ++j) m4[j] = to_u4(mon[j]);
-    std::memcpy(h, m4.data(), 16ull * len);
-    std::memcpy(h + 16ull * len, cf.data(), 4ull * len);
-    uint32_t *ol = reinterpret_cast<uint32_t *>(h + 20ull * len);
-    ol[0] = (uint32_t)base;
-    ol[1] = len;
-    GB_CUDA(cudaMemcpyAsync(S->bmon.p + base, h, 16ull * len, cudaMemcpyHostToDevice, st));
-    GB_CUDA(cudaMemcpyAsync(S->bcf.p + base, h + 16ull * len, 4ull * len, cudaMemcpyHostToDevice, st));
-    GB_CUDA(cudaMemcpyAsync(S->boff.p + ng0, ol, 4, cudaMemcpyHostToDevice, st));
-    GB_CUDA(cudaMemcpyAsync(S->blen.p + ng0, ol + 1, 4, cudaMemcpyHostToDevice, st));
-    sync(S);
-    S->nterms = base + len;
-    S->off.push_back((uint32_t)base);
+// register one normalised polynomial as a new basis element (its terms already sit at the end of
+// the device basis) and run UPDATE
+static void append_host_poly(gb_system *S, const Mono &lm, uint32_t len) {
+    S->off.push_back((uint32_t)S->nterms);
     S->len.push_back(len);
-    push_lm(S, mon[0]);
-    if (mono_deg(mon[0], (int)S->n) == 0) S->unit = true;
+    S->nterms += len;
+    push_lm(S, lm);
+    if (mono_deg(lm, (int)S->n) == 0) S->unit = true;
     gm_update(S, (uint32_t)(S->lm.size() - 1));
 }
 
@@ -313,6 +351,9 @@ void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F) {
     S->p = p;
     S->fp = make_fp(p);
     const int n = (int)nvars;
+    std::vector<std::vector<Mono>> mons;
+    std::vector<std::vector<uint32_t>> cfs;
+    uint64_t total = 0;
     for (uint32_t i = 0; F && i < F->npolys; ++i) {
         const uint32_t a = F->poly_off[i], b = F->poly_off[i + 1];
         if (b < a) fail(GB_EINVAL, "poly_off must be non-decreasing");
@@ -335,8 +376,43 @@ void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F) {
         if (mon.empty()) continue;
         const uint32_t inv = host_inv(cf[0], p);
         for (auto &c : cf) c = (uint32_t)((uint64_t)c * inv % p);
-        append_host_poly(S, mon, cf);
+        total += mon.size();
+        mons.push_back(std::move(mon));
+        cfs.push_back(std::move(cf));
     }
+    if (total >= (1ull << 32)) fail(GB_EUNSUPPORTED, "input above 2^32 terms");
+    // the whole input in one upload: terms, coefficients, offsets, lengths
+    const uint32_t ng = (uint32_t)mons.size();
+    if (ng) {
+        gb_ctx *ctx = S->ctx;
+        Arena &ar = ctx->arena;
+        cudaStream_t st = S->stream;
+        S->bmon.alloc(ar, std::max<uint64_t>(total, 1024), st);
+        S->bcf.alloc(ar, std::max<uint64_t>(total, 1024), st);
+        S->boff.alloc(ar, std::max<uint32_t>(ng, 64), st);
+        S->blen.alloc(ar, std::max<uint32_t>(ng, 64), st);
+        Stage sg;
+        std::vector<uint4> m4;
+        std::vector<uint32_t> c4, o4, l4;
+        m4.reserve(total);
+        c4.reserve(total);
+        for (uint32_t g = 0; g < ng; ++g) {
+            o4.push_back((uint32_t)m4.size());
+            l4.push_back((uint32_t)mons[g].size());
+            for (const Mono &m : mons[g]) m4.push_back(to_u4(m));
+            c4.insert(c4.end(), cfs[g].begin(), cfs[g].end());
+        }
+        const size_t om = sg.put(m4.data(), 16ull * total), oc = sg.put(c4.data(), 4ull * total);
+        const size_t oo = sg.put(o4.data(), 4ull * ng), ol = sg.put(l4.data(), 4ull * ng);
+        DBuf<char> d;
+        sg.upload(ctx, d);
+        GB_CUDA(cudaMemcpyAsync(S->bmon.p, d.p + om, 16ull * total, cudaMemcpyDeviceToDevice, st));
+        GB_CUDA(cudaMemcpyAsync(S->bcf.p, d.p + oc, 4ull * total, cudaMemcpyDeviceToDevice, st));
+        GB_CUDA(cudaMemcpyAsync(S->boff.p, d.p + oo, 4ull * ng, cudaMemcpyDeviceToDevice, st));
+        GB_CUDA(cudaMemcpyAsync(S->blen.p, d.p + ol, 4ull * ng, cudaMemcpyDeviceToDevice, st));
+        ctx_sync(ctx);  // the staging block goes back to the arena
+    }
+    for (uint32_t g = 0; g < ng; ++g) append_host_poly(S, mons[g][0], (uint32_t)mons[g].size());
     // footprint estimate for admission control: the basis plus a few dense step matrices
     uint64_t terms = 0;
     for (uint32_t l : S->len) terms += l;
@@ -348,137 +424,213 @@ void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F) {
     S->footprint = (size_t)(64ull << 20) + (size_t)(terms * 20 * 64) + (size_t)(N * N / 4);
 }
 
-// ---- one F4 step ------------------------------------------------------------------------------
+// ---- lockstep F4 steps of many systems ------------------------------------------------------------
+//
+// One step of every system: each selects its pairs of minimal degree (normal strategy) on the host
+// workers, then one symbolic preprocessing, one sparse reduction and one RREF run over all of the
+// systems' matrices together (each kernel launch covers every system's rows), and the new basis
+// elements go through UPDATE on the host workers again.
 
-gb_status f4_step(gb_system *S, gb_step_stats *stats) {
-    const auto t0 = std::chrono::steady_clock::now();
-    if (S->pairs.empty()) return GB_DONE;
-    const int n = (int)S->n;
-    // normal strategy: every pair of minimal lcm degree
-    uint32_t dmin = UINT32_MAX;
-    for (const PairL &q : S->pairs) dmin = std::min(dmin, q.deg);
-    if (dmin > 255) fail(GB_EOVERFLOW, "step degree above 255");
-    std::vector<std::pair<Mono, uint32_t>> tk;
-    std::vector<PairL> rest;
-    uint32_t npairs = 0;
-    for (const PairL &q : S->pairs) {
-        if (q.deg != dmin) { rest.push_back(q); continue; }
-        ++npairs;
-        Mono l;
-        std::memcpy(l.e, &q.lcm, 16);
-        tk.emplace_back(mono_div(l, S->lm[q.i], n), q.i);
-        tk.emplace_back(mono_div(l, S->lm[q.j], n), q.j);
+namespace {
+using Clock = std::chrono::steady_clock;
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+}  // namespace
+
+void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *stats) {
+    const size_t nj = Ss.size();
+    if (stats) stats->assign(nj, gb_step_stats{});
+    if (!nj) return;
+    gb_ctx *ctx = Ss[0]->ctx;
+    const auto t0 = Clock::now();
+    std::vector<SpTask> tasks(nj);
+    std::vector<uint32_t> dmin(nj, UINT32_MAX), npairs(nj, 0);
+    parallel_for(ctx, nj, [&](size_t j) {
+        gb_system *S = Ss[j];
+        const int n = (int)S->n;
+        for (const PairL &q : S->pairs) dmin[j] = std::min(dmin[j], q.deg);
+        if (dmin[j] > 255) fail(GB_EOVERFLOW, "step degree above 255");
+        std::vector<std::pair<Mono, uint32_t>> tk;
+        std::vector<PairL> rest;
+        for (const PairL &q : S->pairs) {
+            if (q.deg != dmin[j]) { rest.push_back(q); continue; }
+            ++npairs[j];
+            Mono l;
+            std::memcpy(l.e, &q.lcm, 16);
+            tk.emplace_back(mono_div(l, S->lm[q.i], n), q.i);
+            tk.emplace_back(mono_div(l, S->lm[q.j], n), q.j);
+        }
+        S->pairs.swap(rest);
+        tasks[j].S = S;
+        tasks[j].rows = order_rows(S, std::move(tk));
+        tasks[j].closure = true;
+        tasks[j].nonred = nonredundant(S);
+    });
+    const auto ts = Clock::now();
+    symbolic_preprocess(tasks);
+    std::vector<gb_macaulay *> Ms(nj);
+    for (size_t j = 0; j < nj; ++j) Ms[j] = tasks[j].out.get();
+    auto Es = reduce_rows(Ms, true);
+    const auto t1 = Clock::now();
+    std::vector<gb_echelon *> Ep(nj);
+    for (size_t j = 0; j < nj; ++j) Ep[j] = Es[j].get();
+    std::vector<std::vector<Mono>> lms;
+    append_echelon(Ep, lms);
+    const auto tp = Clock::now();
+    parallel_for(ctx, nj, [&](size_t j) {
+        gb_system *S = Ss[j];
+        for (const Mono &m : lms[j]) {
+            push_lm(S, m);
+            if (mono_deg(m, (int)S->n) == 0) S->unit = true;
+            gm_update(S, (uint32_t)(S->lm.size() - 1));
+        }
+    });
+    const auto t2 = Clock::now();
+    for (size_t j = 0; j < nj; ++j) {
+        gb_system *S = Ss[j];
+        gb_macaulay *mac = Ms[j];
+        gb_echelon *ech = Ep[j];
+        S->steps++;
+        gb_step_stats st{};
+        st.step = S->steps;
+        st.degree = dmin[j];
+        st.npairs = npairs[j];
+        st.nrows = mac->nrows;
+        st.ndict = mac->ndict;
+        st.npivot = mac->nA;
+        st.nC = mac->nC;
+        st.nb = mac->nb;
+        st.rank = ech->rank;
+        st.nbasis = (uint32_t)S->lm.size();
+        st.closure_rounds = mac->closure_rounds;
+        st.nnz = mac->nnz;
+        st.axpy_rows = ech->work[0];
+        st.axpy_fma = ech->work[1];
+        // device stages are timed once for the whole batch
+        st.ms_sp = mac->ms_sp;
+        st.ms_reduce = ech->ms_reduce;
+        st.ms_rref = ech->ms_rref;
+        st.ms_update = (float)ms_between(t1, tp);
+        st.ms_pairs = (float)ms_between(tp, t2);
+        st.ms_select = (float)ms_between(t0, ts);
+        st.ms_wall = ms_between(t0, t2);
+        S->run.steps = S->steps;
+        S->run.nnz_total += st.nnz;
+        S->run.axpy_rows += st.axpy_rows;
+        S->run.axpy_fma += st.axpy_fma;
+        S->run.ms_sp += st.ms_sp;
+        S->run.ms_reduce += st.ms_reduce;
+        S->run.ms_rref += st.ms_rref;
+        S->run.ms_update += st.ms_update;
+        S->run.ms_pairs += st.ms_pairs;
+        S->run.ms_select += st.ms_select;
+        S->run.ms_wall += st.ms_wall;
+        if (stats) (*stats)[j] = st;
+        if (ctx->flags & GB_CTX_KEEP_STEP) {
+            S->last_ech = std::move(Es[j]);
+            S->last_mac = std::move(tasks[j].out);
+        }
     }
-    S->pairs.swap(rest);
-    std::vector<RowSpec> rows = order_rows(S, std::move(tk));
-    const auto ts = std::chrono::steady_clock::now();
-    auto mac = symbolic_preprocess(S, rows, true, nonredundant(S));
-    auto ech = reduce_rows(mac.get(), true);
-    const auto t1 = std::chrono::steady_clock::now();
-    std::vector<Mono> lms;
-    std::vector<uint32_t> lens;
-    append_echelon(S, ech.get(), lms, lens);
-    const auto tp = std::chrono::steady_clock::now();
-    for (size_t e = 0; e < lms.size(); ++e) {
-        push_lm(S, lms[e]);
-        if (mono_deg(lms[e], n) == 0) S->unit = true;
-        gm_update(S, (uint32_t)(S->lm.size() - 1));
-    }
-    const auto t2 = std::chrono::steady_clock::now();
-    S->steps++;
-    gb_step_stats st{};
-    st.step = S->steps;
-    st.degree = (uint32_t)dmin;
-    st.npairs = npairs;
-    st.nrows = mac->nrows;
-    st.ndict = mac->ndict;
-    st.npivot = mac->nA;
-    st.nC = mac->nC;
-    st.nb = mac->nb;
-    st.rank = ech->rank;
-    st.nbasis = (uint32_t)S->lm.size();
-    st.closure_rounds = mac->closure_rounds;
-    st.nnz = mac->nnz;
-    st.axpy_rows = ech->work[0];
-    st.axpy_fma = ech->work[1];
-    st.ms_sp = mac->ms_sp;
-    st.ms_reduce = ech->ms_reduce;
-    st.ms_rref = ech->ms_rref;
-    st.ms_update = (float)std::chrono::duration<double, std::milli>(tp - t1).count();
-    st.ms_pairs = (float)std::chrono::duration<double, std::milli>(t2 - tp).count();
-    st.ms_select = (float)std::chrono::duration<double, std::milli>(ts - t0).count();
-    st.ms_wall = std::chrono::duration<double, std::milli>(t2 - t0).count();
-    S->run.steps = S->steps;
-    S->run.nnz_total += st.nnz;
-    S->run.axpy_rows += st.axpy_rows;
-    S->run.axpy_fma += st.axpy_fma;
-    S->run.ms_sp += st.ms_sp;
-    S->run.ms_reduce += st.ms_reduce;
-    S->run.ms_rref += st.ms_rref;
-    S->run.ms_update += st.ms_update;
-    S->run.ms_pairs += st.ms_pairs;
-    S->run.ms_select += st.ms_select;
-    S->run.ms_wall += st.ms_wall;
-    if (stats) *stats = st;
-    if (S->ctx->flags & GB_CTX_KEEP_STEP) {
-        S->last_ech = std::move(ech);
-        S->last_mac = std::move(mac);
-    }
-    return GB_OK;
 }
 
 // ---- the reduced basis ------------------------------------------------------------------------
 
-void finish(gb_system *S) {
-    const auto t0 = std::chrono::steady_clock::now();
-    const int n = (int)S->n;
-    const uint32_t ng = (uint32_t)S->lm.size();
-    std::vector<uint32_t> keep;
-    for (uint32_t i = 0; i < ng; ++i) {
-        if (S->redundant[i]) continue;
-        bool drop = false;
-        for (uint32_t j = 0; j < ng && !drop; ++j) {
-            if (j == i || S->redundant[j]) continue;
-            if (mono_divides(S->lm[j], S->lm[i], n) && (!(S->lm[j] == S->lm[i]) || j < i)) drop = true;
+void finish_batch(const std::vector<gb_system *> &Ss) {
+    const size_t nj = Ss.size();
+    if (!nj) return;
+    gb_ctx *ctx = Ss[0]->ctx;
+    const auto t0 = Clock::now();
+    // minimalisation: an element goes when another one's leading monomial divides its own (the
+    // older one staying on equality); the rest in leading-monomial order, descending
+    std::vector<std::vector<uint32_t>> keep(nj);
+    parallel_for(ctx, nj, [&](size_t j) {
+        gb_system *S = Ss[j];
+        const int n = (int)S->n;
+        const uint32_t ng = (uint32_t)S->lm.size();
+        for (uint32_t i = 0; i < ng; ++i) {
+            if (S->redundant[i]) continue;
+            bool drop = false;
+            for (uint32_t g = 0; g < ng && !drop; ++g) {
+                if (g == i || S->redundant[g]) continue;
+                if (mono_divides(S->lm[g], S->lm[i], n) && (!(S->lm[g] == S->lm[i]) || g < i)) drop = true;
+            }
+            if (!drop) keep[j].push_back(i);
         }
-        if (!drop) keep.push_back(i);
+        std::sort(keep[j].begin(), keep[j].end(),
+                  [&](uint32_t a, uint32_t b) { return mono_cmp(S->lm[a], S->lm[b], n) > 0; });
+    });
+    // the tails t(g) = g - LM(g), reduced by the minimal basis with the same pipeline: the closure
+    // supplies reducer rows for every tail monomial a leading monomial divides, and the sparse
+    // reduction leaves each tail with non-pivot (standard) monomials only
+    std::vector<SpTask> tasks;
+    std::vector<std::vector<uint32_t>> elems;
+    std::vector<gb_system *> owners;
+    for (size_t j = 0; j < nj; ++j) {
+        gb_system *S = Ss[j];
+        if (keep[j].empty()) {
+            S->fin_off.assign(1, 0);
+            S->fin_exps.clear();
+            S->fin_cf.clear();
+            continue;
+        }
+        SpTask t;
+        t.S = S;
+        for (uint32_t g : keep[j]) t.rows.push_back(RowSpec{Mono{}, g, 0, 1});
+        t.closure = true;
+        t.nonred = keep[j];
+        tasks.push_back(std::move(t));
+        elems.push_back(keep[j]);
+        owners.push_back(S);
     }
-    // final order: leading monomials descending
-    std::sort(keep.begin(), keep.end(), [&](uint32_t a, uint32_t b) { return mono_cmp(S->lm[a], S->lm[b], n) > 0; });
-    std::vector<uint32_t> off{0};
-    std::vector<uint8_t> exps;
-    std::vector<uint32_t> cf;
-    if (!keep.empty()) {
-        // the tails t(g) = g - LM(g), reduced by the minimal basis with the same pipeline: the
-        // closure supplies reducer rows for every tail monomial a leading monomial divides, and the
-        // sparse reduction leaves each tail with non-pivot (standard) monomials only
-        std::vector<RowSpec> rows;
-        for (uint32_t g : keep) rows.push_back(RowSpec{Mono{}, g, 0, 1});
-        auto mac = symbolic_preprocess(S, rows, true, keep);
-        auto ech = reduce_rows(mac.get(), false);
-        replace_tails(S, ech.get(), keep, off, exps, cf);
-        S->run.ms_sp += mac->ms_sp;
-        S->run.ms_reduce += ech->ms_reduce;
-        S->run.nnz_total += mac->nnz;
-        S->run.axpy_rows += ech->work[0];
-        S->run.axpy_fma += ech->work[1];
+    if (!tasks.empty()) {
+        symbolic_preprocess(tasks);
+        std::vector<gb_macaulay *> Ms;
+        for (auto &t : tasks) Ms.push_back(t.out.get());
+        auto Es = reduce_rows(Ms, false);
+        std::vector<gb_echelon *> Ep;
+        for (auto &e : Es) Ep.push_back(e.get());
+        replace_tails(Ep, elems);
+        for (size_t k = 0; k < owners.size(); ++k) {
+            gb_system *S = owners[k];
+            S->run.ms_sp += Ms[k]->ms_sp;
+            S->run.ms_reduce += Ep[k]->ms_reduce;
+            S->run.nnz_total += Ms[k]->nnz;
+            S->run.axpy_rows += Ep[k]->work[0];
+            S->run.axpy_fma += Ep[k]->work[1];
+        }
     }
-    S->fin_off.swap(off);
-    S->fin_exps.swap(exps);
-    S->fin_cf.swap(cf);
-    S->finished = true;
-    S->run.nbasis = (uint32_t)keep.size();
-    S->run.ms_wall += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const double ms = ms_between(t0, Clock::now());
+    for (size_t j = 0; j < nj; ++j) {
+        gb_system *S = Ss[j];
+        S->finished = true;
+        S->run.nbasis = (uint32_t)keep[j].size();
+        S->run.ms_wall += ms;
+    }
 }
 
-gb_status groebner(gb_system *S, gb_run_stats *stats) {
-    if (!S->finished) {
-        while (f4_step(S, nullptr) == GB_OK) {
-        }
-        finish(S);
+// One lockstep iteration over a set of running systems: those without pairs left get their reduced
+// basis, the others take one F4 step together.
+void advance(const std::vector<gb_system *> &Ss) {
+    std::vector<gb_system *> step, fin;
+    for (gb_system *S : Ss) {
+        if (S->finished) continue;
+        (S->pairs.empty() ? fin : step).push_back(S);
     }
-    if (stats) *stats = S->run;
-    return GB_OK;
+    if (!fin.empty()) finish_batch(fin);
+    if (!step.empty()) f4_steps(step, nullptr);
+}
+
+void groebner_batch(const std::vector<gb_system *> &Ss) {
+    for (;;) {
+        bool any = false;
+        for (gb_system *S : Ss) any = any || !S->finished;
+        if (!any) return;
+        advance(Ss);
+    }
 }
 
 }  // namespace gb
+
+gb_ctx::gb_ctx() = default;
+gb_ctx::~gb_ctx() = default;

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -29,6 +30,11 @@ struct Error : std::runtime_error {
 void cuda_check(cudaError_t e, const char *what);
 #define GB_CUDA(x) ::gb::cuda_check((x), #x)
 void set_last_error(const std::string &msg);
+
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum, once per kernel and
+// device.  The limit is a per-kernel attribute shared by every thread of the process, so it is
+// only ever raised: a thread lowering it while another launches with more would fail the launch.
+void opt_in_smem(const void *kernel);
 
 // every kernel launch site calls counted() right after its <<<...>>>
 extern std::atomic<unsigned long long> g_launches;
@@ -181,12 +187,26 @@ struct PairL {  // a critical pair with its lcm cached
 }  // namespace gb
 
 // ---- handles ---------------------------------------------------------------------------------
+namespace gb {
+struct HostPool;
+}
+
 struct gb_ctx {
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // every system of the context runs on this stream
     bool own_stream = false;
     uint32_t flags = 0;
     gb::Arena arena;
+    cudaEvent_t ev[8] = {};         // stage timing of the batch in flight
+    void *stage = nullptr;          // page-locked staging of the batch in flight
+    size_t stage_bytes = 0;
+    // host worker threads for per-system host control of a batch (pair updates, selection)
+    std::unique_ptr<gb::HostPool> pool;
+    // held by every call that queues work on the stream or uses the staging area, so that a
+    // server's scheduler thread and the caller's own calls on the same context do not interleave
+    std::recursive_mutex mu;
+    gb_ctx();
+    ~gb_ctx();
 };
 
 // The materialised plan Pi of one batch (Def. 5.2) on the device.
@@ -222,9 +242,7 @@ struct gb_system {
     gb_ctx *ctx = nullptr;
     uint32_t n = 0, p = 0;
     gb::Fp fp{};
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    cudaEvent_t ev[8] = {};
+    cudaStream_t stream = nullptr;  // the context's stream
     // host mirror of the basis metadata
     std::vector<gb::Mono> lm;
     std::vector<uint32_t> off, len;
@@ -237,9 +255,6 @@ struct gb_system {
     gb::DBuf<uint32_t> bcf;
     gb::DBuf<uint32_t> boff, blen;
     uint64_t nterms = 0;
-    // pinned staging for small transfers
-    void *pinned = nullptr;
-    size_t pinned_bytes = 0;
     // kept objects of the last step (GB_CTX_KEEP_STEP)
     std::unique_ptr<gb_macaulay> last_mac;
     std::unique_ptr<gb_echelon> last_ech;
@@ -257,18 +272,48 @@ struct gb_system {
 };
 
 namespace gb {
-// pipeline stages (sp.cu, reduce.cu)
-std::unique_ptr<gb_macaulay> symbolic_preprocess(gb_system *S, const std::vector<RowSpec> &rows,
-                                                 bool closure, const std::vector<uint32_t> &nonred);
-std::unique_ptr<gb_echelon> reduce_rows(gb_macaulay *M, bool echelon);
-// append the echelon rows as new basis elements on the device; returns their LMs and lengths
-void append_echelon(gb_system *S, gb_echelon *E, std::vector<Mono> &lms, std::vector<uint32_t> &lens);
-// tails of the final reduction: new coefficient arrays for the given elements
-void replace_tails(gb_system *S, gb_echelon *E, const std::vector<uint32_t> &elems,
-                   std::vector<uint32_t> &off, std::vector<uint8_t> &exps, std::vector<uint32_t> &cf);
-void *pinned(gb_system *S, size_t bytes);
-// cudaStreamSynchronize on the system's stream, then release its deferred arena blocks
-void sync(gb_system *S);
+
+// many small host arrays staged for one host-to-device copy through the context's pinned area
+struct Stage {
+    std::vector<char> h;
+    size_t put(const void *src, size_t bytes) {
+        const size_t at = (h.size() + 15) & ~size_t(15);
+        h.resize(at + bytes);
+        if (bytes && src) std::memcpy(h.data() + at, src, bytes);
+        return at;
+    }
+    void upload(gb_ctx *ctx, DBuf<char> &d);  // synchronises: the pinned area is reused next
+};
+
+// prefix table of per-job block counts appended to a stage; returns the total
+inline uint32_t plan(Stage &sg, const std::vector<uint32_t> &per_job, size_t &at) {
+    std::vector<uint32_t> pre(per_job.size() + 1, 0);
+    for (size_t j = 0; j < per_job.size(); ++j) pre[j + 1] = pre[j] + per_job[j];
+    at = sg.put(pre.data(), 4 * pre.size());
+    return pre.back();
+}
+
+// one job of symbolic preprocessing: the rows of one system's batch
+struct SpTask {
+    gb_system *S = nullptr;
+    std::vector<RowSpec> rows;
+    bool closure = true;
+    std::vector<uint32_t> nonred;  // non-redundant basis indices, ascending
+    uint64_t cap = 0;              // frontier capacity (0: estimate)
+    std::unique_ptr<gb_macaulay> out;
+};
+
+// pipeline stages for many systems of one context at once (sp.cu, reduce.cu)
+void symbolic_preprocess(std::vector<SpTask> &tasks);
+std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaulay *> &Ms, bool echelon);
+// append each job's echelon rows as new basis elements on the device; returns their LMs
+void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector<Mono>> &lms);
+// final reduction: element elems[j][i] of job j becomes LM + row i of its D' (writes fin_*)
+void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::vector<uint32_t>> &elems);
+void *ctx_pinned(gb_ctx *ctx, size_t bytes);  // the context's page-locked staging area
+void ctx_sync(gb_ctx *ctx);                     // synchronise the stream, release deferred blocks
+// run fn(i) for i in [0, n) on the context's host workers and the calling thread
+void parallel_for(gb_ctx *ctx, size_t n, const std::function<void(size_t)> &fn);
 // exclusive scan of n u32 values on the stream; out has n + 1 entries (out[n] = total)
 void exclusive_scan(Arena &ar, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t s);
 }  // namespace gb

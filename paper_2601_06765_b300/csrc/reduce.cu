@@ -1,20 +1,15 @@
-// reduce.cu -- the numeric phase (Sec. 9.2): structured elimination of the Macaulay matrix.
+// reduce.cu -- the numeric phase (Sec. 9.2): structured elimination of Macaulay matrices, for
+// many independent jobs (systems) at once.
 //
 // Rows of Pi come as nA pivot rows (distinct leading columns pcols[0..nA), ascending, every row
-// monic) followed by nC non-pivot rows.  The result is unique (the pivot rows have distinct
+// monic) followed by nC non-pivot rows.  The results are unique (the pivot rows have distinct
 // leading columns), so any schedule on the device gives the same bits as the CPU oracle.
 //
-//   k_reduce   each non-pivot row is loaded into a dense accumulator (shared memory, or global
-//              memory for wide dictionaries); the pivot columns at or right of its leading column
-//              are swept in ascending order and every nonzero entry c is cleared with
-//              v <- v - v[c] * (pivot row of c), a sparse row AXPY (eq. 8.1).  Accumulation is lazy
-//              (Rem. 8.1): 64-bit sums of products (p < 2^16) or of Montgomery products (p < 2^31)
-//              are reduced with Barrett only when an entry is read.  Output: D' (nC x nb, dense).
-//   rref_*     RREF(D') by row panels: reduce a panel by the current echelon rows (a GEMM-shaped
-//              update), echelonise what is left in one block, then clear the new pivot columns
-//              from the older rows and append.
-//   append     echelon rows become new basis elements (Sec. 4.2 step 4), written to the device
-//              basis in standard form.
+//   k_reduce   each non-pivot row is reduced by the pivot rows into a dense accumulator -> D'
+//   rref_*     RREF(D') by right-looking panels of KP rows
+//   append     echelon rows become new basis elements in the device basis (Sec. 4.2 step 4)
+//   tails      the final reduction's rows become the reduced basis, packed on the device
+// Every kernel serves all jobs of a launch: a prefix table maps a block to its job.
 #include <algorithm>
 #include <cstdlib>
 
@@ -33,20 +28,19 @@ inline unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t
 // The pivot columns are taken in chunks of CW = 32 consecutive pivots (pivot rows k..k+31, one
 // contiguous CSR segment).  For a non-pivot row v the multipliers of a chunk are the solution of a
 // 32 x 32 unit upper-triangular system: f_i = v[c_i] - sum_{j<i} f_j U[j][i], where U[j][i] is the
-// entry of pivot row j at pivot column c_i.  One warp per row solves it with shuffles from a shared
-// copy of U (prefetched by the other warps while the previous chunk's system is solved); then
-// every warp of the block applies v <- v - sum_i f_i (pivot row i) to the accumulators with
-// shared-memory atomics (each pivot row's own leading entry included, which leaves v[c_i] = 0).
-// A block reduces R non-pivot rows together, so each pivot-row entry read from L2 serves R rows,
-// and it synchronises twice per chunk instead of once per pivot column.
+// entry of pivot row j at pivot column c_i.  Warp 0 solves it with shuffles from a shared copy of
+// U (prefetched by the other warps while the previous chunk's system is solved); then every warp
+// applies v <- v - sum_i f_i (pivot row i) to the row's accumulator with shared-memory atomics
+// (each pivot row's own leading entry included, which leaves v[c_i] = 0).  Two block barriers per
+// 32 pivot columns instead of one per column.
 //
 // Accumulators are lazy (Rem. 8.1), in one of three modes:
 //   A32: p < 2^16, each product (p - f) v < 2^32 is Barrett-reduced to [0, p) and added to a 32-bit
 //        sum (exact while a column takes fewer than 2^16 updates: the host requires nA < 2^16);
 //   A64: p < 2^16, the raw products are added to a 64-bit sum (no reduction per update);
-//   M64: p < 2^31, the Montgomery product redc(fR * v) in [0, 2p) is added to a 64-bit sum.
-// A32 halves the shared memory per row, which lets more blocks share an SM.  Entries are reduced
-// (Barrett) when read.
+//   M64: p < 2^31, the Montgomery product redc(fR * v) in [0, 2p) is added to a 64-bit sum; only
+//        the multiplier is converted (once per pivot row), the entries stay in standard form.
+// Entries are reduced (Barrett) when read.
 constexpr int CW = 32;
 enum AccMode { A32 = 0, A64 = 1, M64 = 2 };
 template <int MODE>
@@ -54,189 +48,165 @@ struct AccOf { using type = unsigned long long; };
 template <>
 struct AccOf<A32> { using type = uint32_t; };
 
+struct RedJob {
+    const uint32_t *row_ptr, *col, *val, *pcols, *colpos, *nonpiv;
+    uint32_t *U, *dprime;
+    void *gacc;                // global accumulators, one row of N per block, when shared memory is short
+    unsigned long long *work;  // [0] pivot rows applied, [1] modular multiply-adds
+    uint32_t nA, nC, N, nb;
+    Fp fp;
+};
+
 // U[chunk][j][i] for j < i: entry of pivot row chunk*32+j at pivot column pcols[chunk*32+i]
-__global__ void k_build_chunk_tri(uint32_t nA, const uint32_t *__restrict__ row_ptr,
-                                  const uint32_t *__restrict__ col, const uint32_t *__restrict__ val,
-                                  const uint32_t *__restrict__ pcols,
-                                  const uint32_t *__restrict__ colpos, uint32_t *__restrict__ U) {
-    const uint32_t k = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (k >= nA) return;
+// (warp per pivot row, 8 per block)
+__global__ void k_build_chunk_tri(const RedJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    const int jb = job_of_block(bstart, nj);
+    const RedJob &J = jobs[jb];
+    const uint32_t k = (blockIdx.x - bstart[jb]) * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (k >= J.nA) return;
     const int lane = threadIdx.x & 31;
     const uint32_t chunk = k / CW, j = k % CW;
-    const uint32_t last = pcols[min(chunk * CW + CW, nA) - 1];
-    uint32_t *Uc = U + (size_t)chunk * CW * CW + (size_t)j * CW;
-    const uint32_t a = row_ptr[k] + 1, b = row_ptr[k + 1];
+    const uint32_t last = J.pcols[min(chunk * CW + CW, J.nA) - 1];
+    uint32_t *Uc = J.U + (size_t)chunk * CW * CW + (size_t)j * CW;
+    const uint32_t a = J.row_ptr[k] + 1, b = J.row_ptr[k + 1];
     for (uint32_t q0 = a; q0 < b; q0 += 32) {
         const uint32_t q = q0 + lane;
         bool past = true;
         if (q < b) {
-            const uint32_t c = col[q];
+            const uint32_t c = J.col[q];
             past = c > last;
             if (!past) {
-                const uint32_t cp = colpos[c];
-                if ((cp & 0x80000000u) && (cp & 0x7FFFFFFFu) / CW == chunk) Uc[(cp & 0x7FFFFFFFu) % CW] = val[q];
+                const uint32_t cp = J.colpos[c];
+                if ((cp & 0x80000000u) && (cp & 0x7FFFFFFFu) / CW == chunk) Uc[(cp & 0x7FFFFFFFu) % CW] = J.val[q];
             }
         }
         if (__all_sync(0xffffffffu, past)) break;  // columns ascend: the rest lies past the chunk
     }
 }
 
-template <int R, int MODE, bool SMEM>
-__global__ void __launch_bounds__(RT) k_reduce(uint32_t nA, uint32_t nC, uint32_t N,
-                                              const uint32_t *__restrict__ row_ptr,
-                                              const uint32_t *__restrict__ col,
-                                              const uint32_t *__restrict__ val,
-                                              const uint32_t *__restrict__ pcols,
-                                              const uint32_t *__restrict__ U,
-                                              const uint32_t *__restrict__ nonpiv, uint32_t nb,
-                                              Fp fp, typename AccOf<MODE>::type *__restrict__ gacc,
-                                              uint32_t *__restrict__ dprime,
-                                              unsigned long long *__restrict__ work) {
+// block per non-pivot row of some job
+template <int MODE, bool SMEM>
+__global__ void __launch_bounds__(RT) k_reduce(const RedJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     using Acc = typename AccOf<MODE>::type;
     constexpr bool SMALLP = MODE != M64;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint32_t fsh[R][CW];
+    __shared__ uint32_t fsh[CW];
     __shared__ uint32_t Us[2][CW * CW];
     __shared__ uint32_t rp[CW + 1];
-    __shared__ uint32_t s_base;
+    const int jb = job_of_block(bstart, nj);
+    const RedJob &J = jobs[jb];
+    const Fp fp = J.fp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t r0 = blockIdx.x * R;
-    const int nr = (int)min((uint32_t)R, nC - r0);
-    // base column = smallest leading column of the block's rows
-    if (threadIdx.x == 0) {
-        uint32_t b = N;
-        for (int r = 0; r < nr; ++r) {
-            const uint32_t a = row_ptr[nA + r0 + r];
-            if (a < row_ptr[nA + r0 + r + 1]) b = min(b, col[a]);
-        }
-        s_base = b;
-    }
+    const uint32_t i = blockIdx.x - bstart[jb], row = J.nA + i;
+    const uint32_t a0 = J.row_ptr[row], b0 = J.row_ptr[row + 1];
+    const uint32_t base = a0 < b0 ? J.col[a0] : J.N, width = J.N - base;
+    Acc *acc = SMEM ? reinterpret_cast<Acc *>(smem_raw)
+                    : reinterpret_cast<Acc *>(J.gacc) + (size_t)i * J.N;
+    for (uint32_t j = threadIdx.x; j < width; j += RT) acc[j] = 0;
     __syncthreads();
-    const uint32_t base = s_base, width = N - base;
-    Acc *acc = SMEM ? reinterpret_cast<Acc *>(smem_raw) : gacc + (size_t)blockIdx.x * R * N;
-    for (uint32_t j = threadIdx.x; j < (uint32_t)R * width; j += RT) acc[j] = 0;
-    __syncthreads();
-    for (int r = 0; r < nr; ++r) {
-        const uint32_t a = row_ptr[nA + r0 + r], b = row_ptr[nA + r0 + r + 1];
-        for (uint32_t q = a + threadIdx.x; q < b; q += RT) acc[(size_t)r * width + col[q] - base] = val[q];
-    }
+    for (uint32_t q = a0 + threadIdx.x; q < b0; q += RT) acc[J.col[q] - base] = J.val[q];
     // first chunk holding a pivot column >= base
-    uint32_t lo = 0, hi = nA;
+    uint32_t lo = 0, hi = J.nA;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (pcols[mid] < base) lo = mid + 1; else hi = mid;
+        if (J.pcols[mid] < base) lo = mid + 1; else hi = mid;
     }
     const uint32_t k0 = (lo / CW) * CW;
-    if (k0 < nA)
-        for (uint32_t t = threadIdx.x; t < CW * CW; t += RT) Us[0][t] = U[(size_t)(k0 / CW) * CW * CW + t];
+    if (k0 < J.nA)
+        for (uint32_t t = threadIdx.x; t < CW * CW; t += RT) Us[0][t] = J.U[(size_t)(k0 / CW) * CW * CW + t];
     unsigned long long applied = 0, fmas = 0;
-    for (uint32_t kc = k0, buf = 0; kc < nA; kc += CW, buf ^= 1) {
-        const uint32_t cnt = min((uint32_t)CW, nA - kc);
+    for (uint32_t kc = k0, buf = 0; kc < J.nA; kc += CW, buf ^= 1) {
+        const uint32_t cnt = min((uint32_t)CW, J.nA - kc);
         __syncthreads();  // the previous chunk's updates (and this chunk's U) are visible
-        if (warp < nr) {
-            // phase A: multipliers of the chunk for row `warp`
-            const Acc *a = acc + (size_t)warp * width;
+        if (warp == 0) {
+            // phase A: the chunk's multipliers
             uint32_t x = 0;
             if ((uint32_t)lane < cnt) {
-                const uint32_t c = pcols[kc + lane];
-                if (c >= base) x = MODE == A32 ? fp_reduce32((uint32_t)a[c - base], fp) : fp_reduce(a[c - base], fp);
+                const uint32_t c = J.pcols[kc + lane];
+                if (c >= base) x = MODE == A32 ? fp_reduce32((uint32_t)acc[c - base], fp) : fp_reduce(acc[c - base], fp);
             }
             const uint32_t *Uc = Us[buf];
-            for (uint32_t i = 0; i + 1 < cnt; ++i) {
-                const uint32_t fi = __shfl_sync(0xffffffffu, x, i);
-                if (fi && (uint32_t)lane > i && (uint32_t)lane < cnt) {
-                    const uint32_t u = Uc[i * CW + lane];
-                    if (u) x = fp_sub(x, SMALLP ? fp_reduce32(fi * u, fp) : fp_mul(fi, u, fp), fp);
+            for (uint32_t t = 0; t + 1 < cnt; ++t) {
+                const uint32_t ft = __shfl_sync(0xffffffffu, x, t);
+                if (ft && (uint32_t)lane > t && (uint32_t)lane < cnt) {
+                    const uint32_t u = Uc[t * CW + lane];
+                    if (u) x = fp_sub(x, SMALLP ? fp_reduce32(ft * u, fp) : fp_mul(ft, u, fp), fp);
                 }
             }
-            fsh[warp][lane] = (uint32_t)lane < cnt ? x : 0u;
+            fsh[lane] = (uint32_t)lane < cnt ? x : 0u;
         } else {
-            if (warp < R) fsh[warp][lane] = 0u;
             // the other warps prefetch the next chunk's triangle
             const uint32_t kn = kc + CW;
-            if (kn < nA)
-                for (uint32_t t = threadIdx.x - 32u * (uint32_t)nr; t < CW * CW; t += RT - 32u * (uint32_t)nr)
-                    Us[buf ^ 1][t] = U[(size_t)(kn / CW) * CW * CW + t];
+            if (kn < J.nA)
+                for (uint32_t t = threadIdx.x - 32u; t < CW * CW; t += RT - 32u)
+                    Us[buf ^ 1][t] = J.U[(size_t)(kn / CW) * CW * CW + t];
         }
-        if (threadIdx.x <= cnt) rp[threadIdx.x] = row_ptr[kc + threadIdx.x];
+        if (threadIdx.x <= cnt) rp[threadIdx.x] = J.row_ptr[kc + threadIdx.x];
         __syncthreads();
         // phase B: warp w applies pivot rows w, w + 8, ... of the chunk
-        for (uint32_t i = warp; i < cnt; i += RT / 32) {
-            uint32_t m[R];
-            bool any = false;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint32_t f = fsh[r][i];
-                m[r] = f ? (SMALLP ? fp.p - f : fp_to_mont(fp.p - f, fp)) : 0u;
-                any |= f != 0;
-            }
-            if (!any) continue;
-            const uint32_t a = rp[i], b = rp[i + 1];
+        for (uint32_t t = warp; t < cnt; t += RT / 32) {
+            const uint32_t f = fsh[t];
+            if (!f) continue;
+            const uint32_t m = SMALLP ? fp.p - f : fp_to_mont(fp.p - f, fp);
+            const uint32_t a = rp[t], b = rp[t + 1];
             if (lane == 0) {
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (m[r]) { ++applied; fmas += b - a; }
+                ++applied;
+                fmas += b - a;
             }
-            for (uint32_t q = a + lane; q < b; q += 64) {
-                // two entries per lane in flight
+            for (uint32_t q = a + lane; q < b; q += 64) {  // two entries per lane in flight
                 const bool two = q + 32 < b;
-                const uint32_t c0 = col[q] - base, v0 = val[q];
-                const uint32_t c1 = two ? col[q + 32] - base : 0u, v1 = two ? val[q + 32] : 0u;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (!m[r]) continue;
-                    Acc *ar = acc + (size_t)r * width;
-                    if (MODE == A32) {
-                        atomicAdd(reinterpret_cast<uint32_t *>(ar + c0), fp_reduce32(m[r] * v0, fp));
-                        if (two) atomicAdd(reinterpret_cast<uint32_t *>(ar + c1), fp_reduce32(m[r] * v1, fp));
-                    } else if (MODE == A64) {
-                        atomicAdd(reinterpret_cast<unsigned long long *>(ar + c0), (unsigned long long)(m[r] * v0));
-                        if (two) atomicAdd(reinterpret_cast<unsigned long long *>(ar + c1), (unsigned long long)(m[r] * v1));
-                    } else {
-                        atomicAdd(reinterpret_cast<unsigned long long *>(ar + c0),
-                                  (unsigned long long)fp_redc((uint64_t)m[r] * v0, fp));
-                        if (two)
-                            atomicAdd(reinterpret_cast<unsigned long long *>(ar + c1),
-                                      (unsigned long long)fp_redc((uint64_t)m[r] * v1, fp));
-                    }
+                const uint32_t c0 = J.col[q] - base, v0 = J.val[q];
+                const uint32_t c1 = two ? J.col[q + 32] - base : 0u, v1 = two ? J.val[q + 32] : 0u;
+                if (MODE == A32) {
+                    atomicAdd(reinterpret_cast<uint32_t *>(acc + c0), fp_reduce32(m * v0, fp));
+                    if (two) atomicAdd(reinterpret_cast<uint32_t *>(acc + c1), fp_reduce32(m * v1, fp));
+                } else if (MODE == A64) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(acc + c0), (unsigned long long)(m * v0));
+                    if (two) atomicAdd(reinterpret_cast<unsigned long long *>(acc + c1), (unsigned long long)(m * v1));
+                } else {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(acc + c0),
+                              (unsigned long long)fp_redc((uint64_t)m * v0, fp));
+                    if (two)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(acc + c1),
+                                  (unsigned long long)fp_redc((uint64_t)m * v1, fp));
                 }
             }
         }
     }
     __syncthreads();
     if (lane == 0 && (applied || fmas)) {
-        atomicAdd(&work[0], applied);
-        atomicAdd(&work[1], fmas);
+        atomicAdd(&J.work[0], applied);
+        atomicAdd(&J.work[1], fmas);
     }
-    for (int r = 0; r < nr; ++r) {
-        uint32_t *out = dprime + (size_t)(r0 + r) * nb;
-        const Acc *a = acc + (size_t)r * width;
-        for (uint32_t jj = threadIdx.x; jj < nb; jj += RT) {
-            const uint32_t c = nonpiv[jj];
-            out[jj] = c < base ? 0u : MODE == A32 ? fp_reduce32((uint32_t)a[c - base], fp) : fp_reduce(a[c - base], fp);
-        }
+    uint32_t *out = J.dprime + (size_t)i * J.nb;
+    for (uint32_t jj = threadIdx.x; jj < J.nb; jj += RT) {
+        const uint32_t c = J.nonpiv[jj];
+        out[jj] = c < base ? 0u : MODE == A32 ? fp_reduce32((uint32_t)acc[c - base], fp) : fp_reduce(acc[c - base], fp);
     }
 }
 
-// ---- RREF(D'): right-looking Gauss-Jordan by panels of K rows --------------------------------
+// ---- RREF(D'): right-looking Gauss-Jordan by panels of KP rows --------------------------------
 //
-// M starts as a copy of D'.  Each round picks up to K non-zero rows that are not pivots yet, brings
-// them to reduced echelon form among themselves in one block (pivots at their leading columns),
-// then eliminates the new pivot columns from every other row of M in parallel (a GEMM-shaped
-// update), which also keeps the earlier pivot rows reduced.  A pivot row's leading column never
-// moves: it is zero left of its pivot, and later pivot rows are zero at it.  When no non-zero
-// non-pivot row is left, the pivot rows sorted by pivot column are RREF(D'), which is unique.
-constexpr uint32_t KP = 32;       // panel rows
+// M starts as a copy of D'.  Each round picks up to KP non-zero rows that are not pivots yet,
+// brings them to reduced echelon form among themselves in one block (pivots at their leading
+// columns), then eliminates the new pivot columns from every other row of M in parallel, which
+// also keeps the earlier pivot rows reduced.  A pivot row's leading column never moves: it is zero
+// left of its pivot, and later pivot rows are zero at it.  When no non-zero non-pivot row is left,
+// the pivot rows sorted by pivot column are RREF(D'), which is unique.  The panel solves of
+// different jobs run side by side, one block each.
+constexpr uint32_t KP = 32;
 constexpr uint32_t NOLEAD = 0xFFFFFFFFu;
 
-struct Rref {
-    uint32_t *M;       // nC x nb working matrix
-    uint32_t *lead;    // nC: first non-zero column, NOLEAD for a zero row
-    uint32_t *pcol;    // nC: pivot column of a pivot row, NOLEAD otherwise
-    uint32_t *order;   // rank: pivot rows in discovery order
-    uint32_t *state;   // [0] pivots so far, [1] panel rows, [2] new pivots, [3] rows left
-    uint32_t *panel;   // KP panel row ids, then KP new pivot row ids, then KP new pivot columns
-    uint32_t nC, nb;
+struct RrefJob {
+    uint32_t *M;      // nC x nb working matrix
+    uint32_t *lead;   // nC: first non-zero column, NOLEAD for a zero row
+    uint32_t *pcol;   // nC: pivot column of a pivot row, NOLEAD otherwise
+    uint32_t *order;  // pivot rows in discovery order
+    uint32_t *state;  // [0] pivots so far, [1] panel rows, [2] new pivots, [3] rows left
+    uint32_t *panel;  // KP panel row ids, then KP new pivot row ids, then KP new pivot columns
+    uint32_t *out, *opiv;
+    uint32_t nC, nb, rank;
+    Fp fp;
 };
 
 __device__ __forceinline__ uint32_t block_min(uint32_t v, uint32_t *red) {
@@ -252,10 +222,12 @@ __device__ __forceinline__ uint32_t block_min(uint32_t v, uint32_t *red) {
     return red[0];
 }
 
-// leading columns of every row of M
-__global__ void k_leads(Rref X) {
+// leading columns of every row (block per row)
+__global__ void k_leads(const RrefJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     __shared__ uint32_t red[32];
-    const uint32_t r = blockIdx.x;
+    const int jb = job_of_block(bstart, nj);
+    const RrefJob &X = jobs[jb];
+    const uint32_t r = blockIdx.x - bstart[jb];
     const uint32_t *row = X.M + (size_t)r * X.nb;
     uint32_t c = NOLEAD;
     for (uint32_t j = threadIdx.x; j < X.nb; j += blockDim.x)
@@ -267,10 +239,12 @@ __global__ void k_leads(Rref X) {
     }
 }
 
-// choose the next panel: the first KP non-zero rows that are not pivots (one block)
-__global__ void k_pick_panel(Rref X) {
+// the next panel of each job: its first KP non-zero rows that are not pivots (block per job)
+__global__ void k_pick_panel(const RrefJob *__restrict__ jobs) {
     __shared__ uint32_t wcnt[32];
     __shared__ uint32_t s_taken;
+    const RrefJob &X = jobs[blockIdx.x];
+    if (!X.state) return;  // a job without a D' block
     if (threadIdx.x == 0) s_taken = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x / 32;
@@ -306,14 +280,16 @@ __global__ void k_pick_panel(Rref X) {
     }
 }
 
-// reduced echelon form of the panel rows among themselves (one block).  With SMEM the panel is
-// copied to shared memory, reduced there and written back.
+// reduced echelon form of each job's panel rows among themselves (block per job of `list`).
+// With SMEM the panel is copied to shared memory, reduced there and written back.
 constexpr int PT = 1024;
 template <bool SMEM>
-__global__ void __launch_bounds__(PT) k_panel_rref(Rref X, Fp fp) {
+__global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ jobs, const int *__restrict__ list) {
     extern __shared__ __align__(16) uint32_t pan[];
     __shared__ uint32_t mult[KP], prow[KP], pslot[KP], pc[KP], red[32];
     __shared__ uint32_t s_inv;
+    const RrefJob &X = jobs[list[blockIdx.x]];
+    const Fp fp = X.fp;
     const uint32_t P = X.state[1], nb = X.nb;
     auto rowp = [&](uint32_t t) -> uint32_t * {
         return SMEM ? pan + (size_t)t * nb : X.M + (size_t)X.panel[t] * nb;
@@ -329,7 +305,7 @@ __global__ void __launch_bounds__(PT) k_panel_rref(Rref X, Fp fp) {
     for (uint32_t t = 0; t < P; ++t) {
         const uint32_t r = X.panel[t];
         uint32_t *row = rowp(t);
-        // multipliers: entries at the panel's earlier pivots, negated (pivot rows are RREF
+        // multipliers: entries at the panel's earlier pivots, negated (those pivot rows are RREF
         // among themselves, so each multiplier is read from the unreduced row)
         if (threadIdx.x < nnew) {
             const uint32_t v = row[pc[threadIdx.x]];
@@ -403,10 +379,13 @@ __global__ void __launch_bounds__(PT) k_panel_rref(Rref X, Fp fp) {
 
 // every other row: r <- r - sum_k r[pc_k] * Q_k over the panel's new pivot rows Q_k; one block per
 // row, so a row's multipliers are read before any thread writes the row
-__global__ void k_eliminate(Rref X, Fp fp) {
+__global__ void k_eliminate(const RrefJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     __shared__ uint32_t m[KP], q[KP], red[32];
     __shared__ int s_any;
-    const uint32_t r = blockIdx.x, nb = X.nb, nnew = X.state[2];
+    const int jb = job_of_block(bstart, nj);
+    const RrefJob &X = jobs[jb];
+    const Fp fp = X.fp;
+    const uint32_t r = blockIdx.x - bstart[jb], nb = X.nb, nnew = X.state[2];
     if (nnew == 0 || X.lead[r] == NOLEAD) return;
     const uint32_t pr = X.pcol[r];
     uint32_t *row = X.M + (size_t)r * nb;
@@ -440,120 +419,91 @@ __global__ void k_eliminate(Rref X, Fp fp) {
     }
 }
 
-// the pivot rows in pivot-column order
-__global__ void k_gather_rref(Rref X, uint32_t rank, uint32_t *__restrict__ out,
-                              uint32_t *__restrict__ opiv) {
-    const uint32_t e = blockIdx.x, nb = X.nb;
+// the pivot rows in pivot-column order (block per pivot row)
+__global__ void k_gather_rref(const RrefJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     __shared__ uint32_t pos;
+    const int jb = job_of_block(bstart, nj);
+    const RrefJob &X = jobs[jb];
+    const uint32_t e = blockIdx.x - bstart[jb], nb = X.nb;
     const uint32_t r = X.order[e], c = X.pcol[r];
     if (threadIdx.x == 0) {
         uint32_t n = 0;
-        for (uint32_t f = 0; f < rank; ++f) n += X.pcol[X.order[f]] < c;
+        for (uint32_t f = 0; f < X.rank; ++f) n += X.pcol[X.order[f]] < c;
         pos = n;
-        opiv[n] = c;
+        X.opiv[n] = c;
     }
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x)
-        out[(size_t)pos * nb + j] = X.M[(size_t)r * nb + j];
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) X.out[(size_t)pos * nb + j] = X.M[(size_t)r * nb + j];
 }
 
-// ---- reconstruction --------------------------------------------------------------------------
+// ---- reconstruction and the final tails ------------------------------------------------------
 
-__global__ void k_count_rows(const uint32_t *__restrict__ M, uint32_t rows, uint32_t nb,
-                             uint32_t *__restrict__ cnt) {
-    const uint32_t r = blockIdx.x;
-    if (r >= rows) return;
+struct RowsJob {
+    const uint32_t *M;      // rows x nb (rows >= mrows are empty)
+    const uint32_t *rpiv;   // echelon pivots (append) or null
+    const uint32_t *nonpiv;
+    const uint4 *dict;
+    const uint4 *lead;      // leading monomial written first (tails) or null
+    uint32_t rows, mrows, nb, n, plus;
+    uint32_t *cnt;          // this job's range of the concatenated counts
+    const uint32_t *oscan;  // range of their exclusive scan (subtract oscan[0])
+    uint4 *lm;              // leading monomials of the rows (append)
+    const uint32_t *dst_off;  // absolute output offsets (append: the new elements' boff)
+    uint4 *omon;            // append: basis monomials
+    uint32_t *ocf;
+    uint8_t *oexp;          // tails: n-byte exponent vectors
+};
+
+// nonzeros of each row (+ plus for the leading term) (block per row)
+__global__ void k_count_rows(const RowsJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    const int jb = job_of_block(bstart, nj);
+    const RowsJob &J = jobs[jb];
+    const uint32_t r = blockIdx.x - bstart[jb];
     uint32_t c = 0;
-    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) c += M[(size_t)r * nb + j] != 0;
+    if (r < J.mrows)
+        for (uint32_t j = threadIdx.x; j < J.nb; j += blockDim.x) c += J.M[(size_t)r * J.nb + j] != 0;
     for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
     __shared__ uint32_t s[32];
     if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t t = 0;
+        uint32_t t = J.plus;
         for (uint32_t w = 0; w < blockDim.x / 32; ++w) t += s[w];
-        cnt[r] = t;
+        J.cnt[r] = t;
+        if (J.rpiv) J.lm[r] = J.dict[J.nonpiv[J.rpiv[r]]];
     }
 }
 
-// write the nonzeros of row r (ascending columns = descending monomials) at out_off[r]
-__global__ void k_write_rows(const uint32_t *__restrict__ M, uint32_t rows, uint32_t nb,
-                             const uint32_t *__restrict__ nonpiv, const uint4 *__restrict__ dict,
-                             const uint32_t *__restrict__ out_off, uint4 *__restrict__ omon,
-                             uint32_t *__restrict__ ocf) {
-    const uint32_t r = blockIdx.x;
-    if (r >= rows) return;
-    __shared__ uint32_t base;
-    __shared__ uint32_t wsum[32];
-    if (threadIdx.x == 0) base = out_off[r];
-    __syncthreads();
-    const uint32_t *src = M + (size_t)r * nb;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x / 32;
-    for (uint32_t j0 = 0; j0 < nb; j0 += blockDim.x) {
-        const uint32_t j = j0 + threadIdx.x;
-        const uint32_t v = j < nb ? src[j] : 0u;
-        const unsigned mask = __ballot_sync(0xffffffffu, v != 0);
-        if (lane == 0) wsum[warp] = __popc(mask);
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int w = 0; w < nw; ++w) {
-            if (w < warp) before += wsum[w];
-            total += wsum[w];
-        }
-        if (v) {
-            const uint32_t pos = base + before + __popc(mask & ((1u << lane) - 1u));
-            omon[pos] = dict[nonpiv[j]];
-            ocf[pos] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) base += total;
-        __syncthreads();
-    }
-}
-
-// nonzeros of row r of M (rows < mrows; rows beyond are empty), plus one for the leading term
-__global__ void k_count_rows_plus(const uint32_t *__restrict__ M, uint32_t rows, uint32_t mrows,
-                                  uint32_t nb, uint32_t *__restrict__ cnt) {
-    const uint32_t r = blockIdx.x;
-    uint32_t c = 0;
-    if (r < mrows)
-        for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) c += M[(size_t)r * nb + j] != 0;
-    for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
-    __shared__ uint32_t s[32];
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 1;
-        for (uint32_t w = 0; w < blockDim.x / 32; ++w) t += s[w];
-        cnt[r] = t;
-    }
-}
-
-// leading term (coefficient 1) then the nonzeros of row r in column order, exponents as n bytes
-__global__ void k_pack_rows(const uint32_t *__restrict__ M, uint32_t rows, uint32_t mrows, uint32_t nb,
-                            const uint32_t *__restrict__ nonpiv, const uint4 *__restrict__ dict,
-                            const uint4 *__restrict__ lead, const uint32_t *__restrict__ out_off,
-                            uint32_t n, uint8_t *__restrict__ oexp, uint32_t *__restrict__ ocf) {
-    const uint32_t r = blockIdx.x;
+// write each row's terms in column order (descending monomials) at its offset (block per row)
+__global__ void k_write_rows(const RowsJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    const int jb = job_of_block(bstart, nj);
+    const RowsJob &J = jobs[jb];
+    const uint32_t r = blockIdx.x - bstart[jb];
     __shared__ uint32_t base;
     __shared__ uint32_t wsum[32];
     auto put = [&](uint32_t pos, uint4 m, uint32_t c) {
-        const uint32_t w[4] = {m.x, m.y, m.z, m.w};
-        for (uint32_t i = 0; i < n; ++i) oexp[(size_t)pos * n + i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
-        ocf[pos] = c;
+        if (J.omon) {
+            J.omon[pos] = m;
+        } else {
+            const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+            for (uint32_t i = 0; i < J.n; ++i) J.oexp[(size_t)pos * J.n + i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+        }
+        J.ocf[pos] = c;
     };
     if (threadIdx.x == 0) {
-        base = out_off[r];
-        put(base, lead[r], 1u);
-        base += 1;
+        base = J.dst_off ? J.dst_off[r] : J.oscan[r] - J.oscan[0];
+        if (J.lead) {
+            put(base, J.lead[r], 1u);
+            base += 1;
+        }
     }
     __syncthreads();
-    if (r >= mrows) return;
-    const uint32_t *src = M + (size_t)r * nb;
+    if (r >= J.mrows) return;
+    const uint32_t *src = J.M + (size_t)r * J.nb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x / 32;
-    for (uint32_t j0 = 0; j0 < nb; j0 += blockDim.x) {
+    for (uint32_t j0 = 0; j0 < J.nb; j0 += blockDim.x) {
         const uint32_t j = j0 + threadIdx.x;
-        const uint32_t v = j < nb ? src[j] : 0u;
+        const uint32_t v = j < J.nb ? src[j] : 0u;
         const unsigned mask = __ballot_sync(0xffffffffu, v != 0);
         if (lane == 0) wsum[warp] = __popc(mask);
         __syncthreads();
@@ -562,281 +512,451 @@ __global__ void k_pack_rows(const uint32_t *__restrict__ M, uint32_t rows, uint3
             if (w < warp) before += wsum[w];
             total += wsum[w];
         }
-        if (v) put(base + before + __popc(mask & ((1u << lane) - 1u)), dict[nonpiv[j]], v);
+        if (v) put(base + before + __popc(mask & ((1u << lane) - 1u)), J.dict[J.nonpiv[j]], v);
         __syncthreads();
         if (threadIdx.x == 0) base += total;
         __syncthreads();
     }
 }
 
-__global__ void k_gather_lms(uint32_t rank, const uint32_t *__restrict__ rpiv,
-                             const uint32_t *__restrict__ nonpiv, const uint4 *__restrict__ dict,
-                             uint4 *__restrict__ out) {
-    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < rank) out[e] = dict[nonpiv[rpiv[e]]];
+__global__ void k_mark_pivot_cols(uint32_t nA, const uint32_t *__restrict__ pcols, uint32_t *__restrict__ colpos) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nA) colpos[pcols[k]] = k | 0x80000000u;
 }
+
+// launch a grouped row kernel: `per_job` blocks per job, plan staged and uploaded with the jobs
+template <class JobT>
+struct Grouped {
+    DBuf<char> d;
+    const JobT *jobs = nullptr;
+    std::vector<const uint32_t *> plans;
+    std::vector<uint32_t> totals;
+    void build(gb_ctx *ctx, const std::vector<JobT> &J, const std::vector<std::vector<uint32_t>> &per_job) {
+        Stage sg;
+        std::vector<size_t> at(per_job.size());
+        totals.resize(per_job.size());
+        for (size_t k = 0; k < per_job.size(); ++k) totals[k] = plan(sg, per_job[k], at[k]);
+        const size_t oj = sg.put(J.data(), sizeof(JobT) * J.size());
+        sg.upload(ctx, d);
+        jobs = reinterpret_cast<const JobT *>(d.p + oj);
+        plans.resize(per_job.size());
+        for (size_t k = 0; k < per_job.size(); ++k) plans[k] = reinterpret_cast<const uint32_t *>(d.p + at[k]);
+    }
+};
 
 }  // namespace
 
-std::unique_ptr<gb_echelon> reduce_rows(gb_macaulay *Mac, bool echelon) {
-    gb_system *S = Mac->sys;
-    Arena &ar = S->ctx->arena;
-    cudaStream_t st = S->stream;
-    auto E = std::make_unique<gb_echelon>();
-    E->mac = Mac;
-    E->nC = Mac->nC;
-    E->nb = Mac->nb;
-    const uint32_t nC = Mac->nC, nb = Mac->nb, N = Mac->ndict, nA = Mac->nA;
-    E->dprime.alloc(ar, (size_t)nC * nb, st);
-    GB_CUDA(cudaEventRecord(S->ev[2], st));
+std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaulay *> &Ms, bool echelon) {
+    std::vector<std::unique_ptr<gb_echelon>> Es;
+    if (Ms.empty()) return Es;
+    gb_ctx *ctx = Ms[0]->sys->ctx;
+    Arena &ar = ctx->arena;
+    cudaStream_t st = ctx->stream;
+    const int nj = (int)Ms.size();
+    GB_CUDA(cudaEventRecord(ctx->ev[2], st));
     DBuf<unsigned long long> work;
-    work.alloc(ar, 2, st);
-    GB_CUDA(cudaMemsetAsync(work.p, 0, 16, st));
-    if (nC && nb) {
-        const bool small = S->fp.small != 0;
-        const uint32_t nchunks = (nA + CW - 1) / CW;
-        DBuf<uint32_t> U;
-        U.alloc(ar, (size_t)std::max(nchunks, 1u) * CW * CW, st);
-        GB_CUDA(cudaMemsetAsync(U.p, 0, 4ull * std::max(nchunks, 1u) * CW * CW, st));
-        if (nA) {
-            k_build_chunk_tri<<<blocks(nA, 8), 256, 0, st>>>(nA, Mac->row_ptr.p, Mac->col.p, Mac->val.p,
-                                                            Mac->pcols.p, Mac->colpos.p, U.p);
+    work.alloc(ar, 2ull * nj, st);
+    GB_CUDA(cudaMemsetAsync(work.p, 0, 16ull * nj, st));
+    std::vector<RedJob> R(nj);
+    std::vector<DBuf<uint32_t>> Ubuf(nj);
+    std::vector<int> mode(nj, A32);
+    for (int j = 0; j < nj; ++j) {
+        gb_macaulay *Mac = Ms[j];
+        gb_system *S = Mac->sys;
+        auto E = std::make_unique<gb_echelon>();
+        E->mac = Mac;
+        E->nC = Mac->nC;
+        E->nb = Mac->nb;
+        E->dprime.alloc(ar, (size_t)Mac->nC * Mac->nb, st);
+        const uint32_t nchunks = std::max<uint32_t>((Mac->nA + CW - 1) / CW, 1);
+        Ubuf[j].alloc(ar, (size_t)nchunks * CW * CW, st);
+        GB_CUDA(cudaMemsetAsync(Ubuf[j].p, 0, 4ull * nchunks * CW * CW, st));
+        RedJob &J = R[j];
+        J = RedJob{Mac->row_ptr.p, Mac->col.p, Mac->val.p, Mac->pcols.p, Mac->colpos.p, Mac->nonpiv.p,
+                   Ubuf[j].p, E->dprime.p, nullptr, work.p + 2 * j, Mac->nA, Mac->nC, Mac->ndict, Mac->nb, S->fp};
+        mode[j] = !S->fp.small ? M64 : (Mac->nA < 65536u ? A32 : A64);
+        Es.push_back(std::move(E));
+    }
+    // accumulators: shared memory per block when N fits, else one global row per block; launch
+    // groups by mode and by the shared-memory size class (powers of two)
+    std::vector<DBuf<unsigned char>> gbuf(nj);
+    std::map<std::pair<int, int>, std::vector<int>> groups;  // (mode, size class or -1) -> jobs
+    for (int j = 0; j < nj; ++j) {
+        if (!R[j].nC || !R[j].nb) continue;
+        const size_t accb = mode[j] == A32 ? 4 : 8;
+        const size_t bytes = (size_t)R[j].N * accb;
+        int cls = -1;
+        if (bytes <= 200 * 1024) {
+            cls = 0;
+            while (((size_t)1024 << cls) < bytes) ++cls;
+        } else {
+            gbuf[j].alloc(ar, (size_t)R[j].nC * bytes, st);
+            R[j].gacc = gbuf[j].p;
+        }
+        groups[{mode[j], cls}].push_back(j);
+    }
+    {
+        std::vector<uint32_t> tri(nj);
+        for (int j = 0; j < nj; ++j) tri[j] = blocks(R[j].nA, 8);
+        std::vector<std::vector<uint32_t>> per{tri};
+        for (auto &g : groups) {
+            std::vector<uint32_t> rows(nj, 0);
+            for (int j : g.second) rows[j] = R[j].nC;
+            per.push_back(rows);
+        }
+        Grouped<RedJob> G;
+        G.build(ctx, R, per);
+        if (G.totals[0]) {
+            k_build_chunk_tri<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
             counted();
         }
-        // accumulator mode and rows per block: the largest R whose blocks all fit in one wave
-        const int mode = !small ? M64 : (nA < 65536u ? A32 : A64);
-        const size_t accb = mode == A32 ? 4 : 8;
-        // rows per block.  Measured on the n=10 dense workload, one row per block (more resident
-        // warps) beats sharing each streamed pivot row between 2 or 4 rows; GB_REDUCE_R=2|4
-        // selects the shared variants for tuning.
-        static const int forced_r = [] {
-            const char *e = std::getenv("GB_REDUCE_R");
-            return e ? std::atoi(e) : 0;
-        }();
-        int R = (forced_r == 2 || forced_r == 4) ? forced_r : 1;
-        if ((size_t)R * N * accb > 200 * 1024) R = 1;
-        const bool use_smem = (size_t)R * N * accb <= 200 * 1024;
-        const unsigned grid = (nC + R - 1) / R;
-        const size_t smem = use_smem ? (size_t)R * N * accb : 0;
-        DBuf<unsigned long long> gacc;
-        if (!use_smem) gacc.alloc(ar, (size_t)grid * R * N + 1, st);
-        auto launch = [&](auto kern, auto *gp) {
-            // static + dynamic shared memory above 48 KB needs the opt-in, whatever the split
-            GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<grid, RT, smem, st>>>(nA, nC, N, Mac->row_ptr.p, Mac->col.p, Mac->val.p, Mac->pcols.p,
-                                         U.p, Mac->nonpiv.p, nb, S->fp, gp, E->dprime.p, work.p);
-            counted();
-        };
-        uint32_t *g32 = reinterpret_cast<uint32_t *>(gacc.p);
-        unsigned long long *g64 = gacc.p;
-#define GB_REDUCE_CASE(RR)                                                                   \
-    if (R == RR) {                                                                           \
-        if (mode == A32) {                                                                   \
-            if (use_smem) launch(k_reduce<RR, A32, true>, g32);                              \
-            else launch(k_reduce<RR, A32, false>, g32);                                      \
-        } else if (mode == A64) {                                                            \
-            if (use_smem) launch(k_reduce<RR, A64, true>, g64);                              \
-            else launch(k_reduce<RR, A64, false>, g64);                                      \
-        } else {                                                                             \
-            if (use_smem) launch(k_reduce<RR, M64, true>, g64);                              \
-            else launch(k_reduce<RR, M64, false>, g64);                                      \
-        }                                                                                    \
+        size_t gi = 1;
+        for (auto &g : groups) {
+            const int md = g.first.first, cls = g.first.second;
+            const bool smem = cls >= 0;
+            size_t dyn = 0;
+            if (smem)
+                for (int j : g.second) dyn = std::max<size_t>(dyn, (size_t)R[j].N * (md == A32 ? 4 : 8));
+            auto go = [&](auto kern) {
+                if (smem) opt_in_smem(reinterpret_cast<const void *>(kern));
+                kern<<<G.totals[gi], RT, dyn, st>>>(G.jobs, G.plans[gi], nj);
+                counted();
+            };
+            if (md == A32) { if (smem) go(k_reduce<A32, true>); else go(k_reduce<A32, false>); }
+            else if (md == A64) { if (smem) go(k_reduce<A64, true>); else go(k_reduce<A64, false>); }
+            else { if (smem) go(k_reduce<M64, true>); else go(k_reduce<M64, false>); }
+            ++gi;
+        }
     }
-        GB_REDUCE_CASE(1)
-        GB_REDUCE_CASE(2)
-        GB_REDUCE_CASE(4)
-#undef GB_REDUCE_CASE
-    }
-    GB_CUDA(cudaEventRecord(S->ev[3], st));
-    if (echelon && nC && nb) {
-        DBuf<uint32_t> Mw, lead, pcol, order, state, panel;
-        Mw.alloc(ar, (size_t)nC * nb, st);
-        lead.alloc(ar, nC, st);
-        pcol.alloc(ar, nC, st);
-        order.alloc(ar, std::min(nC, nb), st);
-        state.alloc(ar, 4, st);
-        panel.alloc(ar, 3 * KP, st);
-        GB_CUDA(cudaMemcpyAsync(Mw.p, E->dprime.p, 4ull * nC * nb, cudaMemcpyDeviceToDevice, st));
-        GB_CUDA(cudaMemsetAsync(state.p, 0, 16, st));
-        Rref X{Mw.p, lead.p, pcol.p, order.p, state.p, panel.p, nC, nb};
-        k_leads<<<nC, 256, 0, st>>>(X);
-        counted();
-        uint32_t *h = static_cast<uint32_t *>(pinned(S, 64));
-        const size_t pan_bytes = 4ull * KP * nb;
-        const bool pan_smem = pan_bytes <= 200 * 1024;
-        if (pan_smem)
-            GB_CUDA(cudaFuncSetAttribute(k_panel_rref<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pan_bytes));
-        // rounds are launched in groups; a group's rounds after the last pivot do nothing
-        // every round turns each of its rows into a pivot row or a zero row
-        const uint32_t maxrounds = (nC + KP - 1) / KP + 1;
-        uint32_t rounds = 0;
-        for (;;) {
-            const uint32_t group = rounds == 0 ? 2 : 4;
-            for (uint32_t g = 0; g < group; ++g) {
-                k_pick_panel<<<1, 1024, 0, st>>>(X);
-                if (pan_smem) k_panel_rref<true><<<1, PT, pan_bytes, st>>>(X, S->fp);
-                else k_panel_rref<false><<<1, PT, 0, st>>>(X, S->fp);
-                k_eliminate<<<nC, 256, 0, st>>>(X, S->fp);
-                counted(3);
+    GB_CUDA(cudaEventRecord(ctx->ev[3], st));
+
+    std::vector<uint32_t> rank(nj, 0);
+    if (echelon) {
+        // per-job working state, one allocation each
+        std::vector<RrefJob> X(nj);
+        std::vector<DBuf<uint32_t>> Mw(nj), lead(nj), pcol(nj), order(nj), panel(nj);
+        DBuf<uint32_t> states;  // 4 words per job, read back in one copy
+        states.alloc(ar, 4ull * nj, st);
+        GB_CUDA(cudaMemsetAsync(states.p, 0, 16ull * nj, st));
+        std::vector<int> live, smem_jobs, glob_jobs;
+        for (int j = 0; j < nj; ++j) {
+            const uint32_t nC = R[j].nC, nb = R[j].nb;
+            X[j] = RrefJob{};
+            X[j].nC = nC;
+            X[j].nb = nb;
+            X[j].fp = R[j].fp;
+            if (!nC || !nb) continue;
+            Mw[j].alloc(ar, (size_t)nC * nb, st);
+            lead[j].alloc(ar, nC, st);
+            pcol[j].alloc(ar, nC, st);
+            order[j].alloc(ar, std::min(nC, nb), st);
+            panel[j].alloc(ar, 3 * KP, st);
+            GB_CUDA(cudaMemcpyAsync(Mw[j].p, Es[j]->dprime.p, 4ull * nC * nb, cudaMemcpyDeviceToDevice, st));
+            X[j].M = Mw[j].p;
+            X[j].lead = lead[j].p;
+            X[j].pcol = pcol[j].p;
+            X[j].order = order[j].p;
+            X[j].state = states.p + 4 * j;
+            X[j].panel = panel[j].p;
+            live.push_back(j);
+            (4ull * KP * nb <= 200 * 1024 ? smem_jobs : glob_jobs).push_back(j);
+        }
+        if (!live.empty()) {
+            std::vector<uint32_t> rows(nj, 0);
+            for (int j : live) rows[j] = X[j].nC;
+            Grouped<RrefJob> G;
+            G.build(ctx, X, {rows});
+            DBuf<int> lists;
+            lists.alloc(ar, (size_t)nj + 1, st);
+            {
+                std::vector<int> l(smem_jobs);
+                l.insert(l.end(), glob_jobs.begin(), glob_jobs.end());
+                int *hl = static_cast<int *>(ctx_pinned(ctx, 4ull * (l.size() + 1)));
+                std::memcpy(hl, l.data(), 4 * l.size());
+                GB_CUDA(cudaMemcpyAsync(lists.p, hl, 4 * l.size(), cudaMemcpyHostToDevice, st));
+                ctx_sync(ctx);
             }
-            rounds += group;
-            GB_CUDA(cudaMemcpyAsync(h, state.p, 16, cudaMemcpyDeviceToHost, st));
-            sync(S);
-            if (h[1] == 0 || h[3] <= h[1] || rounds >= maxrounds) break;
-        }
-        // one more pick confirms that no non-zero non-pivot row is left
-        k_pick_panel<<<1, 1024, 0, st>>>(X);
-        counted();
-        GB_CUDA(cudaMemcpyAsync(h, state.p, 16, cudaMemcpyDeviceToHost, st));
-        GB_CUDA(cudaMemcpyAsync(h + 4, work.p, 16, cudaMemcpyDeviceToHost, st));
-        sync(S);
-        if (h[1] != 0) fail(GB_EDEVICE, "RREF: rows left after the last round");
-        E->rank = h[0];
-        std::memcpy(E->work, h + 4, 16);
-        E->rref.alloc(ar, (size_t)E->rank * nb, st);
-        E->rpiv.alloc(ar, E->rank, st);
-        if (E->rank) {
-            k_gather_rref<<<E->rank, 256, 0, st>>>(X, E->rank, E->rref.p, E->rpiv.p);
+            size_t pan_bytes = 0;
+            for (int j : smem_jobs) pan_bytes = std::max<size_t>(pan_bytes, 4ull * KP * X[j].nb);
+            if (!smem_jobs.empty()) opt_in_smem(reinterpret_cast<const void *>(k_panel_rref<true>));
+            // jobs are packed in the job table at their own index; k_pick_panel runs on all of them
+            // (a job without rows has no blocks elsewhere and its state stays zero)
+            k_leads<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
             counted();
+            // every round turns each of its rows into a pivot row or a zero row
+            uint32_t maxrounds = 1;
+            for (int j : live) maxrounds = std::max<uint32_t>(maxrounds, (X[j].nC + KP - 1) / KP + 1);
+            uint32_t rounds = 0;
+            for (;;) {
+                const uint32_t group = rounds == 0 ? 2 : 4;
+                for (uint32_t g = 0; g < group; ++g) {
+                    k_pick_panel<<<nj, 1024, 0, st>>>(G.jobs);
+                    if (!smem_jobs.empty())
+                        k_panel_rref<true><<<(unsigned)smem_jobs.size(), PT, pan_bytes, st>>>(G.jobs, lists.p);
+                    if (!glob_jobs.empty())
+                        k_panel_rref<false><<<(unsigned)glob_jobs.size(), PT, 0, st>>>(G.jobs, lists.p + smem_jobs.size());
+                    k_eliminate<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
+                    counted(2 + (smem_jobs.empty() ? 0 : 1) + (glob_jobs.empty() ? 0 : 1));
+                }
+                rounds += group;
+                uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj));
+                GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
+                ctx_sync(ctx);
+                bool more = false;
+                for (int j : live) {
+                    const uint32_t *s = h + 4 * j;
+                    if (s[1] != 0 && s[3] > s[1]) more = true;
+                }
+                if (!more || rounds >= maxrounds) break;
+            }
+            // one more pick confirms that no non-zero non-pivot row is left
+            k_pick_panel<<<nj, 1024, 0, st>>>(G.jobs);
+            counted();
+            uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj));
+            GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
+            ctx_sync(ctx);
+            for (int j : live) {
+                if (h[4 * j + 1] != 0) fail(GB_EDEVICE, "RREF: rows left after the last round");
+                rank[j] = h[4 * j];
+            }
+            // gather the pivot rows in order
+            std::vector<uint32_t> prow(nj, 0);
+            for (int j : live) {
+                Es[j]->rank = rank[j];
+                Es[j]->rref.alloc(ar, (size_t)rank[j] * X[j].nb, st);
+                Es[j]->rpiv.alloc(ar, rank[j], st);
+                X[j].out = Es[j]->rref.p;
+                X[j].opiv = Es[j]->rpiv.p;
+                X[j].rank = rank[j];
+                prow[j] = rank[j];
+            }
+            Grouped<RrefJob> G2;
+            G2.build(ctx, X, {prow});
+            if (G2.totals[0]) {
+                k_gather_rref<<<G2.totals[0], 256, 0, st>>>(G2.jobs, G2.plans[0], nj);
+                counted();
+            }
         }
     }
-    GB_CUDA(cudaEventRecord(S->ev[4], st));
-    if (!echelon) {
-        uint64_t *h = static_cast<uint64_t *>(pinned(S, 64));
-        GB_CUDA(cudaMemcpyAsync(h, work.p, 16, cudaMemcpyDeviceToHost, st));
-        sync(S);
-        std::memcpy(E->work, h, 16);
+    GB_CUDA(cudaEventRecord(ctx->ev[4], st));
+    uint64_t *hw = static_cast<uint64_t *>(ctx_pinned(ctx, 16ull * nj));
+    GB_CUDA(cudaMemcpyAsync(hw, work.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
+    ctx_sync(ctx);
+    float ms_red = 0.f, ms_rref = 0.f;
+    GB_CUDA(cudaEventElapsedTime(&ms_red, ctx->ev[2], ctx->ev[3]));
+    GB_CUDA(cudaEventElapsedTime(&ms_rref, ctx->ev[3], ctx->ev[4]));
+    for (int j = 0; j < nj; ++j) {
+        Es[j]->work[0] = hw[2 * j];
+        Es[j]->work[1] = hw[2 * j + 1];
+        Es[j]->ms_reduce = ms_red;
+        Es[j]->ms_rref = ms_rref;
     }
-    sync(S);
-    GB_CUDA(cudaEventElapsedTime(&E->ms_reduce, S->ev[2], S->ev[3]));
-    GB_CUDA(cudaEventElapsedTime(&E->ms_rref, S->ev[3], S->ev[4]));
-    return E;
+    return Es;
 }
 
-void append_echelon(gb_system *S, gb_echelon *E, std::vector<Mono> &lms, std::vector<uint32_t> &lens) {
-    Arena &ar = S->ctx->arena;
-    cudaStream_t st = S->stream;
-    const uint32_t rank = E->rank, nb = E->nb;
-    lms.clear();
-    lens.clear();
-    if (!rank) return;
-    gb_macaulay *Mac = E->mac;
-    DBuf<uint32_t> cnt, off;
+void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector<Mono>> &lms) {
+    lms.assign(Es.size(), {});
+    if (Es.empty()) return;
+    gb_ctx *ctx = Es[0]->mac->sys->ctx;
+    Arena &ar = ctx->arena;
+    cudaStream_t st = ctx->stream;
+    const int nj = (int)Es.size();
+    uint64_t tot = 0;
+    std::vector<uint64_t> roff(nj);
+    for (int j = 0; j < nj; ++j) {
+        roff[j] = tot;
+        tot += Es[j]->rank;
+    }
+    if (!tot) return;
+    DBuf<uint32_t> cnt, scan;
     DBuf<uint4> lmd;
-    cnt.alloc(ar, rank, st);
-    off.alloc(ar, (size_t)rank + 1, st);
-    lmd.alloc(ar, rank, st);
-    k_count_rows<<<rank, 256, 0, st>>>(E->rref.p, rank, nb, cnt.p);
+    cnt.alloc(ar, tot, st);
+    scan.alloc(ar, tot + 1, st);
+    lmd.alloc(ar, tot, st);
+    std::vector<RowsJob> J(nj);
+    std::vector<uint32_t> rows(nj);
+    for (int j = 0; j < nj; ++j) {
+        gb_echelon *E = Es[j];
+        J[j] = RowsJob{E->rref.p, E->rpiv.p, E->mac->nonpiv.p, E->mac->dict.p, nullptr, E->rank, E->rank, E->nb,
+                       E->mac->n, 0, cnt.p + roff[j], scan.p + roff[j], lmd.p + roff[j], nullptr, nullptr,
+                       nullptr, nullptr};
+        rows[j] = E->rank;
+    }
+    {
+        Grouped<RowsJob> G;
+        G.build(ctx, J, {rows});
+        k_count_rows<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
+        counted();
+    }
+    exclusive_scan(ar, cnt.p, scan.p, tot, st);
+    char *h = static_cast<char *>(ctx_pinned(ctx, 4ull * (tot + 1) + 16ull * tot + 64));
+    uint32_t *hs = reinterpret_cast<uint32_t *>(h);
+    Mono *hl = reinterpret_cast<Mono *>(h + ((4ull * (tot + 1) + 15) & ~15ull));
+    GB_CUDA(cudaMemcpyAsync(hs, scan.p, 4ull * (tot + 1), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(hl, lmd.p, 16ull * tot, cudaMemcpyDeviceToHost, st));
+    ctx_sync(ctx);
+    // room in every basis, and the new elements' offsets and lengths
+    std::vector<uint32_t> hoff_all(tot + 1);
+    std::memcpy(hoff_all.data(), hs, 4ull * (tot + 1));
+    Stage offs;
+    std::vector<size_t> at(nj), at_len(nj);
+    for (int j = 0; j < nj; ++j) {
+        gb_system *S = Es[j]->mac->sys;
+        const uint32_t rank = Es[j]->rank;
+        lms[j].assign(hl + roff[j], hl + roff[j] + rank);
+        if (!rank) continue;
+        const uint32_t b0 = hoff_all[roff[j]];
+        const uint64_t add = hoff_all[roff[j] + rank] - b0;
+        const uint64_t base = S->nterms;
+        if (base + add >= (1ull << 32)) fail(GB_EUNSUPPORTED, "basis above 2^32 terms");
+        const size_t ng0 = S->off.size();
+        if (base + add > S->bmon.n) {
+            S->bmon.grow(ar, std::max<size_t>(base + add, 2 * S->bmon.n), base, st);
+            S->bcf.grow(ar, std::max<size_t>(base + add, 2 * S->bcf.n), base, st);
+        }
+        if (ng0 + rank > S->boff.n) {
+            S->boff.grow(ar, std::max<size_t>(ng0 + rank, 2 * S->boff.n), ng0, st);
+            S->blen.grow(ar, std::max<size_t>(ng0 + rank, 2 * S->blen.n), ng0, st);
+        }
+        std::vector<uint32_t> noff(rank), nlen(rank);
+        for (uint32_t e = 0; e < rank; ++e) {
+            noff[e] = (uint32_t)(base + hoff_all[roff[j] + e] - b0);
+            nlen[e] = hoff_all[roff[j] + e + 1] - hoff_all[roff[j] + e];
+        }
+        at[j] = offs.put(noff.data(), 4ull * rank);
+        at_len[j] = offs.put(nlen.data(), 4ull * rank);
+        S->nterms = base + add;
+        for (uint32_t e = 0; e < rank; ++e) {
+            S->off.push_back(noff[e]);
+            S->len.push_back(nlen[e]);
+        }
+    }
+    DBuf<char> d;
+    offs.upload(ctx, d);
+    for (int j = 0; j < nj; ++j) {
+        gb_system *S = Es[j]->mac->sys;
+        const uint32_t rank = Es[j]->rank;
+        if (!rank) continue;
+        const size_t ng0 = S->off.size() - rank;
+        GB_CUDA(cudaMemcpyAsync(S->boff.p + ng0, d.p + at[j], 4ull * rank, cudaMemcpyDeviceToDevice, st));
+        GB_CUDA(cudaMemcpyAsync(S->blen.p + ng0, d.p + at_len[j], 4ull * rank, cudaMemcpyDeviceToDevice, st));
+        J[j].dst_off = S->boff.p + ng0;
+        J[j].omon = S->bmon.p;
+        J[j].ocf = S->bcf.p;
+    }
+    Grouped<RowsJob> G;
+    G.build(ctx, J, {rows});
+    k_write_rows<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
     counted();
-    exclusive_scan(ar, cnt.p, off.p, rank, st);
-    k_gather_lms<<<blocks(rank, 128), 128, 0, st>>>(rank, E->rpiv.p, Mac->nonpiv.p, Mac->dict.p, lmd.p);
-    counted();
-    GB_CUDA(cudaGetLastError());
-    char *h = static_cast<char *>(pinned(S, 32ull * rank + 256));
-    uint32_t *hoff = reinterpret_cast<uint32_t *>(h);
-    Mono *hlm = reinterpret_cast<Mono *>(h + ((4ull * (rank + 1) + 15) & ~15ull));
-    GB_CUDA(cudaMemcpyAsync(hoff, off.p, 4ull * (rank + 1), cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaMemcpyAsync(hlm, lmd.p, 16ull * rank, cudaMemcpyDeviceToHost, st));
-    sync(S);
-    lms.assign(hlm, hlm + rank);
-    const uint64_t add = hoff[rank];
-    const uint64_t base = S->nterms;
-    if (base + add >= (1ull << 32)) fail(GB_EUNSUPPORTED, "basis above 2^32 terms");
-    const size_t ng0 = S->off.size();
-    std::vector<uint32_t> noff(rank), nlen(rank);
-    for (uint32_t e = 0; e < rank; ++e) {
-        noff[e] = (uint32_t)(base + hoff[e]);
-        nlen[e] = hoff[e + 1] - hoff[e];
-    }
-    if (base + add > S->bmon.n) {
-        S->bmon.grow(ar, std::max<size_t>(base + add, 2 * S->bmon.n), base, st);
-        S->bcf.grow(ar, std::max<size_t>(base + add, 2 * S->bcf.n), base, st);
-    }
-    if (ng0 + rank > S->boff.n) {
-        S->boff.grow(ar, std::max<size_t>(ng0 + rank, 2 * S->boff.n), ng0, st);
-        S->blen.grow(ar, std::max<size_t>(ng0 + rank, 2 * S->blen.n), ng0, st);
-    }
-    uint32_t *hb = reinterpret_cast<uint32_t *>(h);  // the read-back above is complete
-    std::memcpy(hb, noff.data(), 4ull * rank);
-    std::memcpy(hb + rank, nlen.data(), 4ull * rank);
-    GB_CUDA(cudaMemcpyAsync(S->boff.p + ng0, hb, 4ull * rank, cudaMemcpyHostToDevice, st));
-    GB_CUDA(cudaMemcpyAsync(S->blen.p + ng0, hb + rank, 4ull * rank, cudaMemcpyHostToDevice, st));
-    k_write_rows<<<rank, 256, 0, st>>>(E->rref.p, rank, nb, Mac->nonpiv.p, Mac->dict.p,
-                                       S->boff.p + ng0, S->bmon.p, S->bcf.p);
-    counted();
-    GB_CUDA(cudaGetLastError());
-    sync(S);  // the staging buffer is reused by the next step
-    S->nterms = base + add;
-    lens = nlen;
-    for (uint32_t e = 0; e < rank; ++e) {
-        S->off.push_back(noff[e]);
-        S->len.push_back(nlen[e]);
-    }
+    ctx_sync(ctx);
 }
 
-void replace_tails(gb_system *S, gb_echelon *E, const std::vector<uint32_t> &elems,
-                   std::vector<uint32_t> &off, std::vector<uint8_t> &exps, std::vector<uint32_t> &cf) {
-    // element elems[i] becomes LM(elems[i]) + (row i of D'), compacted on the device
-    Arena &ar = S->ctx->arena;
-    cudaStream_t st = S->stream;
-    const uint32_t rows = (uint32_t)elems.size(), nb = E->nb, n = S->n;
-    gb_macaulay *Mac = E->mac;
-    off.assign(1, 0);
-    exps.clear();
-    cf.clear();
-    if (!rows) return;
-    DBuf<uint32_t> cnt, doff;
+void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::vector<uint32_t>> &elems) {
+    if (Es.empty()) return;
+    gb_ctx *ctx = Es[0]->mac->sys->ctx;
+    Arena &ar = ctx->arena;
+    cudaStream_t st = ctx->stream;
+    const int nj = (int)Es.size();
+    // element elems[j][i] becomes LM + (row i of job j's D'), compacted on the device
+    uint64_t tot = 0;
+    std::vector<uint64_t> roff(nj);
+    for (int j = 0; j < nj; ++j) {
+        roff[j] = tot;
+        tot += elems[j].size();
+    }
+    if (!tot) {
+        for (int j = 0; j < nj; ++j) {
+            gb_system *S = Es[j]->mac->sys;
+            S->fin_off.assign(1, 0);
+            S->fin_exps.clear();
+            S->fin_cf.clear();
+        }
+        return;
+    }
+    DBuf<uint32_t> cnt, scan;
     DBuf<uint4> lead;
-    cnt.alloc(ar, rows, st);
-    doff.alloc(ar, (size_t)rows + 1, st);
-    lead.alloc(ar, rows, st);
-    std::vector<uint4> hl(rows);
-    for (uint32_t i = 0; i < rows; ++i) hl[i] = to_u4(S->lm[elems[i]]);
-    char *h = static_cast<char *>(pinned(S, 20ull * rows + 64));
-    std::memcpy(h, hl.data(), 16ull * rows);
-    GB_CUDA(cudaMemcpyAsync(lead.p, h, 16ull * rows, cudaMemcpyHostToDevice, st));
-    k_count_rows_plus<<<rows, 256, 0, st>>>(E->dprime.p, rows, E->nC, nb, cnt.p);
-    counted();
-    exclusive_scan(ar, cnt.p, doff.p, rows, st);
-    uint32_t *ho = reinterpret_cast<uint32_t *>(h + 16ull * rows);
-    GB_CUDA(cudaMemcpyAsync(ho, doff.p, 4ull * (rows + 1), cudaMemcpyDeviceToHost, st));
-    sync(S);
-    off.assign(ho, ho + rows + 1);
-    const uint64_t T = off[rows];
+    cnt.alloc(ar, tot, st);
+    scan.alloc(ar, tot + 1, st);
+    lead.alloc(ar, tot, st);
+    std::vector<uint4> hl(tot);
+    for (int j = 0; j < nj; ++j)
+        for (size_t i = 0; i < elems[j].size(); ++i) hl[roff[j] + i] = to_u4(Es[j]->mac->sys->lm[elems[j][i]]);
+    {
+        Stage s;
+        const size_t o = s.put(hl.data(), 16ull * tot);
+        DBuf<char> d;
+        s.upload(ctx, d);
+        GB_CUDA(cudaMemcpyAsync(lead.p, d.p + o, 16ull * tot, cudaMemcpyDeviceToDevice, st));
+    }
+    std::vector<RowsJob> J(nj);
+    std::vector<uint32_t> rows(nj);
+    for (int j = 0; j < nj; ++j) {
+        gb_echelon *E = Es[j];
+        J[j] = RowsJob{E->dprime.p, nullptr, E->mac->nonpiv.p, E->mac->dict.p, lead.p + roff[j],
+                       (uint32_t)elems[j].size(), E->nC, E->nb, E->mac->n, 1, cnt.p + roff[j], scan.p + roff[j],
+                       nullptr, nullptr, nullptr, nullptr, nullptr};
+        rows[j] = (uint32_t)elems[j].size();
+    }
+    {
+        Grouped<RowsJob> G;
+        G.build(ctx, J, {rows});
+        k_count_rows<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
+        counted();
+    }
+    exclusive_scan(ar, cnt.p, scan.p, tot, st);
+    std::vector<uint32_t> hs(tot + 1);
+    GB_CUDA(cudaMemcpyAsync(hs.data(), scan.p, 4ull * (tot + 1), cudaMemcpyDeviceToHost, st));
+    ctx_sync(ctx);
+    uint64_t bytes = 0;
+    std::vector<uint64_t> eoff(nj);
+    for (int j = 0; j < nj; ++j) {
+        eoff[j] = bytes;
+        bytes += (uint64_t)(hs[roff[j] + elems[j].size()] - hs[roff[j]]) * Es[j]->mac->n;
+    }
     DBuf<uint8_t> dex;
     DBuf<uint32_t> dcf;
-    dex.alloc(ar, T * n, st);
-    dcf.alloc(ar, T, st);
-    k_pack_rows<<<rows, 256, 0, st>>>(E->dprime.p, rows, E->nC, nb, Mac->nonpiv.p, Mac->dict.p, lead.p,
-                                      doff.p, n, dex.p, dcf.p);
-    counted();
-    exps.resize(T * n);
-    cf.resize(T);
-    GB_CUDA(cudaMemcpyAsync(exps.data(), dex.p, T * n, cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaMemcpyAsync(cf.data(), dcf.p, 4 * T, cudaMemcpyDeviceToHost, st));
-    sync(S);
+    dex.alloc(ar, bytes, st);
+    dcf.alloc(ar, hs[tot], st);
+    for (int j = 0; j < nj; ++j) {
+        // a job's terms start at its own offset of the concatenated output
+        J[j].ocf = dcf.p + hs[roff[j]];
+        J[j].oexp = dex.p + eoff[j];
+    }
+    {
+        Grouped<RowsJob> G;
+        G.build(ctx, J, {rows});
+        k_write_rows<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
+        counted();
+    }
+    std::vector<uint8_t> allx(bytes);
+    std::vector<uint32_t> allc(hs[tot]);
+    GB_CUDA(cudaMemcpyAsync(allx.data(), dex.p, bytes, cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(allc.data(), dcf.p, 4ull * hs[tot], cudaMemcpyDeviceToHost, st));
+    ctx_sync(ctx);
+    for (int j = 0; j < nj; ++j) {
+        gb_system *S = Es[j]->mac->sys;
+        const uint32_t b = hs[roff[j]], e = hs[roff[j] + elems[j].size()], n = S->n;
+        S->fin_off.resize(elems[j].size() + 1);
+        for (size_t i = 0; i <= elems[j].size(); ++i) S->fin_off[i] = hs[roff[j] + i] - b;
+        S->fin_cf.assign(allc.begin() + b, allc.begin() + e);
+        S->fin_exps.assign(allx.begin() + eoff[j], allx.begin() + eoff[j] + (size_t)(e - b) * n);
+    }
 }
 
 // ---- the sparse reduction without device allocation --------------------------------------------
 //
 // Scratch of gb_reduce_rows_noalloc: pivot-column flags (one word per dictionary column), the
-// 32 x 32 chunk triangles (one per 32 pivot rows) and the two work counters of k_reduce, carved
-// out of one fixed array that is part of the library image.  Host code reaches it only through
-// the address cudaGetSymbolAddress returns for the current device.
+// 32 x 32 chunk triangles (one per 32 pivot rows), the two work counters of k_reduce and its
+// one-job table, carved out of one fixed array that is part of the library image.  Host code
+// reaches it only through the address cudaGetSymbolAddress returns for the current device.
 constexpr uint32_t NA_COLPOS = 0;
 constexpr uint32_t NA_TRI = GB_NOALLOC_MAX_DICT;
 constexpr uint32_t NA_WORK = NA_TRI + GB_NOALLOC_MAX_PIVOTS * CW;  // even: 8-byte aligned
-constexpr uint32_t NA_WORDS = NA_WORK + 4;
+constexpr uint32_t NA_TABLE = NA_WORK + 4;                           // 16-byte aligned
+constexpr uint32_t NA_WORDS = NA_TABLE + (uint32_t)((sizeof(RedJob) + 15) / 4) + 4;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
 
 namespace {
-__global__ void k_mark_pivot_cols(uint32_t nA, const uint32_t *__restrict__ pcols,
-                                  uint32_t *__restrict__ colpos) {
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nA) colpos[pcols[k]] = k | 0x80000000u;
-}
-
 uint32_t *noalloc_scratch_for_current_device() {
     static std::mutex mu;
     static uint32_t *addr[64] = {};
@@ -876,23 +996,34 @@ void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint3
     GB_CUDA(cudaMemsetAsync(colpos, 0, 4ull * N, st));
     if (nchunks) GB_CUDA(cudaMemsetAsync(tri, 0, 4ull * nchunks * CW * CW, st));
     GB_CUDA(cudaMemsetAsync(work, 0, 16, st));
+    // the one-job table: job, then the two block-start tables {0, blocks}
+    struct Table {
+        RedJob job;
+        uint32_t tri_start[2], red_start[2];
+    } tb{};
+    tb.job = RedJob{row_ptr, col, val, pcols, colpos, nonpiv, tri, dprime, nullptr, work, nA, nC, N, nb, fp};
+    tb.tri_start[1] = blocks(nA, 8);
+    tb.red_start[1] = nC;
+    static_assert(sizeof(Table) <= 4 * (NA_WORDS - NA_TABLE), "scratch too small for the job table");
+    Table *dtb = reinterpret_cast<Table *>(scr + NA_TABLE);
+    GB_CUDA(cudaMemcpyAsync(dtb, &tb, sizeof(Table), cudaMemcpyHostToDevice, st));
     if (nA) {
         k_mark_pivot_cols<<<blocks(nA, 256), 256, 0, st>>>(nA, pcols, colpos);
         counted();
-        k_build_chunk_tri<<<blocks(nA, 8), 256, 0, st>>>(nA, row_ptr, col, val, pcols, colpos, tri);
+        k_build_chunk_tri<<<tb.tri_start[1], 256, 0, st>>>(&dtb->job, dtb->tri_start, 1);
         counted();
     }
     const size_t smem = (size_t)N * (mode == A32 ? 4 : 8);
     if (mode == A32) {
-        GB_CUDA(cudaFuncSetAttribute(k_reduce<1, A32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_reduce<1, A32, true><<<nC, RT, smem, st>>>(nA, nC, N, row_ptr, col, val, pcols, tri, nonpiv, nb, fp,
-                                                     nullptr, dprime, work);
+        opt_in_smem(reinterpret_cast<const void *>(k_reduce<A32, true>));
+        k_reduce<A32, true><<<nC, RT, smem, st>>>(&dtb->job, dtb->red_start, 1);
     } else {
-        GB_CUDA(cudaFuncSetAttribute(k_reduce<1, M64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_reduce<1, M64, true><<<nC, RT, smem, st>>>(nA, nC, N, row_ptr, col, val, pcols, tri, nonpiv, nb, fp,
-                                                     nullptr, dprime, work);
+        opt_in_smem(reinterpret_cast<const void *>(k_reduce<M64, true>));
+        k_reduce<M64, true><<<nC, RT, smem, st>>>(&dtb->job, dtb->red_start, 1);
     }
     counted();
+    // the table's host-to-device copy came from pageable memory, so the runtime staged it before
+    // returning: this stack frame may go away while the kernels run
 }
 
 }  // namespace gb

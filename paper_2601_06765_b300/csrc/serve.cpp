@@ -1,10 +1,12 @@
 // serve.cpp -- batching and continuous-batching serving of independent systems on one GPU.
 //
-// Every system owns a CUDA stream, so the device work of different systems overlaps whenever
-// their host control runs concurrently.  gb_batch_groebner drives a fixed set of systems with a
-// pool of host workers.  gb_server admits submitted systems into slots while the summed device
-// footprint estimate of the admitted systems stays under the cap; a slot that finishes frees its
-// footprint and the next queued system is admitted at once, while the others keep running.
+// Both run systems in lockstep: one iteration takes one F4 step of every running system with
+// pairs left (one launch of each pipeline kernel covers all of their rows) and builds the reduced
+// basis of every running system without pairs.  gb_batch_groebner iterates over a fixed set until
+// all are finished.  gb_server's scheduler thread admits queued systems between iterations while
+// a slot is free and the summed device footprint estimate of the running systems stays under the
+// cap, so a request that arrives joins the very next iteration and one that finishes leaves at
+// once (iteration-level continuous batching).
 #include <algorithm>
 #include <condition_variable>
 #include <unordered_map>
@@ -12,102 +14,123 @@
 #include "internal.hpp"
 
 namespace gb {
-gb_status groebner(gb_system *S, gb_run_stats *stats);
-}
+void advance(const std::vector<gb_system *> &Ss);
+void groebner_batch(const std::vector<gb_system *> &Ss);
+}  // namespace gb
 
 using namespace gb;
-
-namespace {
-
-gb_status run_one(gb_system *S, gb_run_stats *st) {
-    try {
-        GB_CUDA(cudaSetDevice(S->ctx->device));
-        return groebner(S, st);
-    } catch (const gb::Error &e) {
-        set_last_error(e.what());
-        return e.st;
-    } catch (const std::exception &e) {
-        set_last_error(e.what());
-        return GB_EDEVICE;
-    }
-}
-
-unsigned default_workers(uint32_t count) {
-    unsigned hw = std::thread::hardware_concurrency();
-    if (!hw) hw = 4;
-    return std::max(1u, std::min<unsigned>(count, std::min(hw, 32u)));
-}
-
-}  // namespace
 
 struct gb_server {
     gb_ctx *ctx = nullptr;
     gb_server_opts opts{};
     std::mutex mu;
-    std::condition_variable cv, done_cv;
+    std::condition_variable cv;
     std::deque<std::pair<uint64_t, gb_system *>> queue;
     std::unordered_map<uint64_t, std::pair<gb_system *, gb_status>> done;
     std::unordered_map<uint64_t, bool> known;
-    size_t admitted_bytes = 0;
-    uint32_t running = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
-    std::vector<std::thread> workers;
+    std::thread scheduler;
 };
 
-static void server_worker(gb_server *srv) {
-    for (;;) {
-        std::pair<uint64_t, gb_system *> job;
-        {
-            std::unique_lock<std::mutex> lk(srv->mu);
-            // admission: a slot is free and the head of the queue fits under the cap (a system
-            // larger than the whole cap is still admitted when nothing else runs)
-            srv->cv.wait(lk, [&] {
-                if (srv->stop) return true;
-                if (srv->queue.empty()) return false;
-                const size_t need = srv->queue.front().second->footprint;
-                return srv->running == 0 || srv->admitted_bytes + need <= srv->opts.hbm_cap_bytes;
-            });
-            if (srv->stop && srv->queue.empty()) return;
-            if (srv->queue.empty()) continue;
-            job = srv->queue.front();
-            srv->queue.pop_front();
-            srv->admitted_bytes += job.second->footprint;
-            srv->running++;
-        }
-        const gb_status st = run_one(job.second, nullptr);
-        {
-            std::lock_guard<std::mutex> lk(srv->mu);
-            srv->admitted_bytes -= job.second->footprint;
-            srv->running--;
-            srv->done[job.first] = {job.second, st};
-        }
-        srv->cv.notify_all();
-        srv->done_cv.notify_all();
+namespace {
+
+struct Running {
+    uint64_t ticket;
+    gb_system *sys;
+};
+
+// take queued systems while a slot is free and the footprint fits (a system larger than the whole
+// cap is still admitted when nothing else runs); called with srv->mu held
+void admit(gb_server *srv, std::vector<Running> &run, size_t &bytes) {
+    while (!srv->queue.empty() && run.size() < srv->opts.max_slots) {
+        gb_system *S = srv->queue.front().second;
+        if (!run.empty() && bytes + S->footprint > srv->opts.hbm_cap_bytes) break;
+        run.push_back(Running{srv->queue.front().first, S});
+        bytes += S->footprint;
+        srv->queue.pop_front();
     }
 }
+
+void scheduler_loop(gb_server *srv) {
+    std::vector<Running> run;
+    size_t bytes = 0;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            if (run.empty()) srv->cv.wait(lk, [&] { return srv->stop || !srv->queue.empty(); });
+            if (srv->stop) {  // running and queued systems are destroyed with the server
+                for (auto &r : run) srv->done[r.ticket] = {r.sys, GB_EBUSY};
+                return;
+            }
+            admit(srv, run, bytes);
+        }
+        std::vector<gb_system *> Ss;
+        for (auto &r : run) Ss.push_back(r.sys);
+        gb_status st = GB_OK;
+        try {
+            std::lock_guard<std::recursive_mutex> g(srv->ctx->mu);
+            GB_CUDA(cudaSetDevice(srv->ctx->device));
+            advance(Ss);
+        } catch (const gb::Error &e) {
+            set_last_error(e.what());
+            st = e.st;
+        } catch (const std::bad_alloc &) {
+            st = GB_ENOMEM;
+        } catch (const std::exception &e) {
+            set_last_error(e.what());
+            st = GB_EDEVICE;
+        }
+        // a failed iteration leaves its systems in an undefined state: all of them finish with the
+        // error (the pipeline runs them together, so the failing one is not singled out)
+        std::lock_guard<std::mutex> lk(srv->mu);
+        size_t w = 0;
+        for (auto &r : run) {
+            if (st != GB_OK || r.sys->finished) {
+                srv->done[r.ticket] = {r.sys, st};
+                bytes -= r.sys->footprint;
+            } else {
+                run[w++] = r;
+            }
+        }
+        run.resize(w);
+    }
+}
+
+}  // namespace
 
 extern "C" {
 
 gb_status gb_batch_groebner(gb_ctx *ctx, uint32_t count, gb_system *const *systems,
                             gb_run_stats *per_system) {
-    if (!ctx || (count && !systems)) return GB_EINVAL;
-    for (uint32_t i = 0; i < count; ++i)
-        if (!systems[i] || systems[i]->ctx != ctx) return GB_EINVAL;
-    std::atomic<uint32_t> next{0};
-    std::vector<gb_status> st(count, GB_OK);
-    auto work = [&] {
-        for (uint32_t i; (i = next.fetch_add(1)) < count;)
-            st[i] = run_one(systems[i], per_system ? &per_system[i] : nullptr);
-    };
-    std::vector<std::thread> pool;
-    const unsigned w = default_workers(count);
-    for (unsigned t = 1; t < w; ++t) pool.emplace_back(work);
-    work();
-    for (auto &t : pool) t.join();
-    for (uint32_t i = 0; i < count; ++i)
-        if (st[i] != GB_OK) return st[i];
-    return GB_OK;
+    try {
+        if (!ctx || (count && !systems)) return GB_EINVAL;
+        std::vector<gb_system *> Ss;
+        for (uint32_t i = 0; i < count; ++i) {
+            if (!systems[i] || systems[i]->ctx != ctx) return GB_EINVAL;
+            if (std::find(Ss.begin(), Ss.end(), systems[i]) != Ss.end()) {
+                set_last_error("a system appears twice in the batch");
+                return GB_EINVAL;
+            }
+            Ss.push_back(systems[i]);
+        }
+        {
+            std::lock_guard<std::recursive_mutex> g(ctx->mu);
+            GB_CUDA(cudaSetDevice(ctx->device));
+            groebner_batch(Ss);
+        }
+        for (uint32_t i = 0; per_system && i < count; ++i) per_system[i] = Ss[i]->run;
+        return GB_OK;
+    } catch (const gb::Error &e) {
+        set_last_error(e.what());
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return GB_ENOMEM;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return GB_EDEVICE;
+    }
 }
 
 gb_status gb_server_create(gb_ctx *ctx, const gb_server_opts *opts, gb_server **out) {
@@ -118,7 +141,13 @@ gb_status gb_server_create(gb_ctx *ctx, const gb_server_opts *opts, gb_server **
     if (opts) srv->opts = *opts;
     if (!srv->opts.max_slots) srv->opts.max_slots = 64;
     if (!srv->opts.hbm_cap_bytes) srv->opts.hbm_cap_bytes = ctx->arena.capacity();
-    for (uint32_t i = 0; i < srv->opts.max_slots; ++i) srv->workers.emplace_back(server_worker, srv);
+    try {
+        srv->scheduler = std::thread(scheduler_loop, srv);
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        delete srv;
+        return GB_EDEVICE;
+    }
     *out = srv;
     return GB_OK;
 }
@@ -156,11 +185,13 @@ gb_status gb_server_destroy(gb_server *srv) {
         srv->stop = true;
     }
     srv->cv.notify_all();
-    for (auto &t : srv->workers) t.join();
-    // systems still queued or finished but never polled are destroyed with the server
-    for (auto &q : srv->queue) gb_system_destroy(q.second);
-    for (auto &d : srv->done) gb_system_destroy(d.second.first);
+    if (srv->scheduler.joinable()) srv->scheduler.join();
+    // systems that were submitted and never polled (queued, running or finished) go with the server
+    std::vector<gb_system *> owned;
+    for (auto &q : srv->queue) owned.push_back(q.second);
+    for (auto &d : srv->done) owned.push_back(d.second.first);
     delete srv;
+    for (gb_system *S : owned) gb_system_destroy(S);
     return GB_OK;
 }
 

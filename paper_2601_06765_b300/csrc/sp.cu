@@ -1,24 +1,26 @@
 // sp.cu -- symbolic preprocessing SP : batch -> (T, R, Pi) (Def. 5.2) as the two-pass FBSP
 // pipeline (the algorithm of Sec. 10), with the one-step reduction closure of Rem. 3.3 run as
-// bulk frontier rounds (Sec. 7.2).
+// bulk frontier rounds (Sec. 7.2), for many independent jobs (systems) at once.
 //
-// Keys.  Every monomial of the batch has degree <= D (the step degree), so its dense grevlex rank
-// (device.cuh) lies in [0, C(n + D, n)).  Setification + ordering of T (Sec. 5.1) is then a
-// single-pass counting sort: a bitmap over the rank space (L2-resident, a few MB at most for the
-// sizes this library admits) is marked with atomicOr, and the dictionary column of a rank is the
-// number of marked ranks above it (word popcounts + one exclusive scan).  A newly set bit is also
-// the "new monomial" test of the frontier: the atomicOr that flips it pushes the monomial once.
+// Keys.  Every monomial of a job has degree <= D (its step degree), so its dense grevlex rank
+// (device.cuh) lies in [0, C(n + D, n)).  Setification + ordering of T (Sec. 5.1) is a counting
+// sort: a bitmap over the rank space (L2-resident) is marked with atomicOr, and the dictionary
+// column of a rank is the number of marked ranks above it (word popcounts + one exclusive scan).
+// The atomicOr that flips a bit is also the "new monomial" test of the closure frontier.
 //
-// Passes.
+// Passes (each one launch for all jobs; a job's blocks are found through a prefix table):
 //   1. mark the leading monomials of the given rows (they start in Done: no reducer rows for them)
 //   2. expand the given rows: every term t*m is marked; unmarked ones join the frontier queue
 //   3. closure rounds: for each frontier monomial, the oldest non-redundant g with LM(g) | m gives
-//      the reducer row (m / LM(g), g), whose tail is expanded into the next frontier
+//      the reducer row (m / LM(g), g), whose tail is expanded into the next frontier; one
+//      read-back of every job's counters per round
 //   4. dictionary: popcount scan, columns, dictionary monomials scattered to their columns
 //   5. row order: pivot rows by leading column (a scan over the pivot-column flags), then the
 //      non-pivot given rows in the order the host fixed
-//   6. CSR: count (row lengths) -> exclusive scan (row_ptr) -> fill (col_ind, val) (the race-freedom theorem of Sec. 11:
-//      every row writes its own segment [row_ptr[i], row_ptr[i+1]))
+//   6. CSR: count (row lengths) -> exclusive scan (row_ptr) -> fill (col_ind, val); every row
+//      writes its own segment [row_ptr[i], row_ptr[i+1]) (the race-freedom theorem of Sec. 11)
+// Scans run once over the concatenation of all jobs' arrays; a job reads its prefixes relative
+// to the first entry of its own range.
 #include <algorithm>
 
 #include "internal.hpp"
@@ -30,26 +32,7 @@ namespace {
 constexpr uint32_t FLAG_PIVOT = 1u, FLAG_REDUCER = 2u, FLAG_TAIL = 4u;
 constexpr int WPB = 8;  // warps per block in the warp-per-row kernels
 
-struct Basis {
-    const uint4 *mon;
-    const uint32_t *cf;
-    const uint32_t *off;
-    const uint32_t *len;
-};
-
-struct Keys {
-    uint32_t *bits;        // rank bitmap
-    const uint32_t *tab;   // rank table (global; copied to shared memory per block)
-    int n, D1, tabsz;
-};
-
-struct Queue {
-    uint4 *mon;
-    uint32_t *rank;
-    uint32_t cap;
-};
-
-struct Counters {  // device-side counters read back after each round
+struct Counters {  // device-side counters of one job, read back after each round
     uint32_t q;    // frontier monomials pushed (all rounds)
     uint32_t red;  // reducer rows
     unsigned long long red_nnz;
@@ -57,9 +40,52 @@ struct Counters {  // device-side counters read back after each round
     uint32_t pad;
 };
 
-__device__ __forceinline__ void load_tab(uint32_t *sm, const Keys &K) {
-    for (int i = threadIdx.x; i < K.tabsz; i += blockDim.x) sm[i] = K.tab[i];
+struct Job {
+    // basis of the job's system
+    const uint4 *bmon;
+    const uint32_t *bcf, *boff, *blen;
+    // given rows
+    const uint4 *gt;
+    const uint32_t *gk, *gnp;
+    const uint8_t *gf;
+    uint32_t ng;
+    // keys
+    uint32_t *bits;
+    const uint32_t *tab;
+    int n, D1, tabsz;
+    uint32_t W;
+    // closure
+    const uint32_t *nr_idx;
+    const uint4 *nr_lm;
+    uint32_t nnr;
+    uint4 *qmon;
+    uint32_t *qrank;
+    uint32_t cap;
+    uint4 *red_t;
+    uint32_t *red_k, *red_rank, *lm_rank;
+    Counters *cnt;
+    // dictionary, rows and CSR (filled in once the counts are known)
+    uint32_t N, nA, nrows, nq, nred, nnz;
+    uint32_t *wcnt;        // this job's range of the concatenated word counts
+    const uint32_t *wpre;  // its range of their exclusive scan (subtract wpre[0])
+    uint32_t *is_piv, *src;
+    const uint32_t *pidx;  // range of the scan of is_piv (subtract pidx[0])
+    uint4 *dict, *row_t;
+    uint32_t *row_k, *pcols, *nonpiv, *colpos;
+    uint8_t *row_flags;
+    uint32_t *lens;
+    const uint32_t *lscan;  // range of the scan of lens (subtract lscan[0])
+    uint32_t *row_ptr, *col, *val;
+};
+
+__device__ __forceinline__ void load_tab(uint32_t *sm, const Job &J) {
+    for (int i = threadIdx.x; i < J.tabsz; i += blockDim.x) sm[i] = J.tab[i];
     __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t col_of(const Job &J, uint32_t r) {
+    const uint32_t w = r >> 5, below = J.bits[w] & ((1u << (r & 31)) - 1u);
+    return J.N - 1u - (J.wpre[w] - J.wpre[0] + __popc(below));
 }
 
 // mark rank r; true if this call flipped the bit (the monomial is new)
@@ -69,28 +95,26 @@ __device__ __forceinline__ bool test_and_set(uint32_t *bits, uint32_t r) {
     return !(atomicOr(&bits[w], b) & b);
 }
 
-// warp-aggregated append of the lanes' new monomials to the frontier queue
-__device__ __forceinline__ void push_new(bool isnew, uint4 m, uint32_t r, const Queue &Q,
-                                         Counters *C) {
+// warp-aggregated append of the lanes' new monomials to the job's frontier queue
+__device__ __forceinline__ void push_new(bool isnew, uint4 m, uint32_t r, const Job &J) {
     const unsigned mask = __ballot_sync(0xffffffffu, isnew);
     if (!mask) return;
     const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
     uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(&C->q, (uint32_t)__popc(mask));
+    if (lane == leader) base = atomicAdd(&J.cnt->q, (uint32_t)__popc(mask));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (isnew) {
         const uint32_t pos = base + __popc(mask & ((1u << lane) - 1u));
-        if (pos < Q.cap) {
-            Q.mon[pos] = m;
-            Q.rank[pos] = r;
+        if (pos < J.cap) {
+            J.qmon[pos] = m;
+            J.qrank[pos] = r;
         }
     }
 }
 
 // expand terms [j0, len) of t*g into the bitmap / queue; called by a whole warp
 __device__ __forceinline__ void expand_terms(uint4 t, uint32_t off, uint32_t j0, uint32_t len,
-                                             const Basis &B, const Keys &K, const uint32_t *tab,
-                                             const Queue &Q, Counters *C) {
+                                             const Job &J, const uint32_t *tab) {
     const int lane = threadIdx.x & 31;
     for (uint32_t jb = j0; jb < len; jb += 32) {
         const uint32_t j = jb + lane;
@@ -98,218 +122,207 @@ __device__ __forceinline__ void expand_terms(uint4 t, uint32_t off, uint32_t j0,
         uint4 m = make_uint4(0, 0, 0, 0);
         uint32_t r = 0;
         if (j < len) {
-            m = mono_mul(t, B.mon[off + j]);
-            r = mono_rank(m, tab, K.n, K.D1);
-            isnew = test_and_set(K.bits, r);
+            m = mono_mul(t, J.bmon[off + j]);
+            r = mono_rank(m, tab, J.n, J.D1);
+            isnew = test_and_set(J.bits, r);
         }
-        push_new(isnew, m, r, Q, C);
+        push_new(isnew, m, r, J);
     }
 }
 
-// Pass 1: leading monomials of the given rows (tail rows have none)
-__global__ void k_mark_given(uint32_t nrows, const uint4 *__restrict__ rt,
-                             const uint32_t *__restrict__ rk, const uint8_t *__restrict__ rflags,
-                             Basis B, Keys K, uint32_t *__restrict__ lm_rank) {
+// Pass 1: leading monomials of the given rows (tail rows have none); 256 rows per block
+__global__ void k_mark_given(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     extern __shared__ uint32_t tab[];
-    load_tab(tab, K);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrows) return;
-    if (rflags[i] & FLAG_TAIL) {
-        lm_rank[i] = 0xFFFFFFFFu;
+    const int jb = job_of_block(bstart, nj);
+    const Job &J = jobs[jb];
+    load_tab(tab, J);
+    const uint32_t i = (blockIdx.x - bstart[jb]) * blockDim.x + threadIdx.x;
+    if (i >= J.ng) return;
+    if (J.gf[i] & FLAG_TAIL) {
+        J.lm_rank[i] = 0xFFFFFFFFu;
         return;
     }
-    const uint4 m = mono_mul(rt[i], B.mon[B.off[rk[i]]]);
-    const uint32_t r = mono_rank(m, tab, K.n, K.D1);
-    atomicOr(&K.bits[r >> 5], 1u << (r & 31));
-    lm_rank[i] = r;
+    const uint4 m = mono_mul(J.gt[i], J.bmon[J.boff[J.gk[i]]]);
+    const uint32_t r = mono_rank(m, tab, J.n, J.D1);
+    atomicOr(&J.bits[r >> 5], 1u << (r & 31));
+    J.lm_rank[i] = r;
 }
 
 // Pass 2: expand the given rows (warp per row)
-__global__ void k_expand_given(uint32_t nrows, const uint4 *__restrict__ rt,
-                               const uint32_t *__restrict__ rk, const uint8_t *__restrict__ rflags,
-                               Basis B, Keys K, Queue Q, Counters *C) {
+__global__ void k_expand_given(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     extern __shared__ uint32_t tab[];
-    load_tab(tab, K);
-    const uint32_t row = blockIdx.x * WPB + (threadIdx.x >> 5);
-    if (row >= nrows) return;  // whole warp leaves together
-    const uint32_t k = rk[row];
-    const uint32_t j0 = (rflags[row] & FLAG_TAIL) ? 1u : 0u;
-    expand_terms(rt[row], B.off[k], j0, B.len[k], B, K, tab, Q, C);
+    const int jb = job_of_block(bstart, nj);
+    const Job &J = jobs[jb];
+    load_tab(tab, J);
+    const uint32_t row = (blockIdx.x - bstart[jb]) * WPB + (threadIdx.x >> 5);
+    if (row >= J.ng) return;  // whole warp leaves together
+    const uint32_t k = J.gk[row];
+    const uint32_t j0 = (J.gf[row] & FLAG_TAIL) ? 1u : 0u;
+    expand_terms(J.gt[row], J.boff[k], j0, J.blen[k], J, tab);
 }
 
-// Pass 3: one closure round over frontier items [f0, f1) (warp per item)
-__global__ void k_closure(uint32_t f0, uint32_t f1, Basis B, Keys K, Queue Q, Counters *C,
-                          const uint32_t *__restrict__ nr_idx, const uint4 *__restrict__ nr_lm,
-                          uint32_t nnr, uint4 *__restrict__ red_t, uint32_t *__restrict__ red_k,
-                          uint32_t *__restrict__ red_rank, uint32_t red_cap) {
+// Pass 3: one closure round over each job's frontier items [range[2j], range[2j+1]) (warp per item)
+__global__ void k_closure(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj,
+                          const uint32_t *__restrict__ range) {
     extern __shared__ uint32_t tab[];
-    load_tab(tab, K);
-    const uint32_t item = f0 + blockIdx.x * WPB + (threadIdx.x >> 5);
-    if (item >= f1) return;
+    const int jb = job_of_block(bstart, nj);
+    const Job &J = jobs[jb];
+    load_tab(tab, J);
+    const uint32_t item = range[2 * jb] + (blockIdx.x - bstart[jb]) * WPB + (threadIdx.x >> 5);
+    if (item >= range[2 * jb + 1]) return;
     const int lane = threadIdx.x & 31;
-    const uint4 m = Q.mon[item];
+    const uint4 m = J.qmon[item];
     // oldest non-redundant element whose leading monomial divides m (nr_idx ascending)
     int g = -1;
     uint4 lmg = make_uint4(0, 0, 0, 0);
-    for (uint32_t cb = 0; cb < nnr; cb += 32) {
+    for (uint32_t cb = 0; cb < J.nnr; cb += 32) {
         const uint32_t idx = cb + lane;
-        const bool ok = idx < nnr && mono_divides(nr_lm[idx], m);
+        const bool ok = idx < J.nnr && mono_divides(J.nr_lm[idx], m);
         const unsigned mask = __ballot_sync(0xffffffffu, ok);
         if (mask) {
             const uint32_t hit = cb + __ffs(mask) - 1;
-            g = (int)nr_idx[hit];
-            lmg = nr_lm[hit];
+            g = (int)J.nr_idx[hit];
+            lmg = J.nr_lm[hit];
             break;
         }
     }
     if (g < 0) return;
     const uint4 t = mono_div(m, lmg);
-    const uint32_t len = B.len[g];
+    const uint32_t len = J.blen[g];
     if (lane == 0) {
-        const uint32_t pos = atomicAdd(&C->red, 1u);
-        if (pos < red_cap) {
-            red_t[pos] = t;
-            red_k[pos] = (uint32_t)g;
-            red_rank[pos] = Q.rank[item];
+        const uint32_t pos = atomicAdd(&J.cnt->red, 1u);
+        if (pos < J.cap) {
+            J.red_t[pos] = t;
+            J.red_k[pos] = (uint32_t)g;
+            J.red_rank[pos] = J.qrank[item];
         }
-        atomicAdd(&C->red_nnz, (unsigned long long)len);
+        atomicAdd(&J.cnt->red_nnz, (unsigned long long)len);
     }
-    expand_terms(t, B.off[g], 1u, len, B, K, tab, Q, C);
+    expand_terms(t, J.boff[g], 1u, len, J, tab);
 }
 
-__global__ void k_popc(const uint32_t *__restrict__ bits, uint32_t *__restrict__ cnt, uint32_t W) {
-    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w < W) cnt[w] = __popc(bits[w]);
-}
+// thread-per-item kernels: 256 items per block, block -> (job, local index i)
+#define GB_JOB_ITEM(limit)                                                   \
+    const int jb = job_of_block(bstart, nj);                                \
+    const Job &J = jobs[jb];                                                \
+    const uint32_t i = (blockIdx.x - bstart[jb]) * blockDim.x + threadIdx.x; \
+    if (i >= (limit)) return;
 
-struct Dict {
-    const uint32_t *bits;
-    const uint32_t *wpre;
-    uint32_t N;
-};
+__global__ void k_popc(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    GB_JOB_ITEM(J.W)
+    J.wcnt[i] = __popc(J.bits[i]);
+}
 
 // Pass 4: dictionary monomials to their columns (queue entries, then the given rows' LMs)
-__global__ void k_dict_queue(uint32_t q, const uint4 *__restrict__ qmon,
-                             const uint32_t *__restrict__ qrank, Dict Dd, uint4 *__restrict__ dict,
-                             uint32_t *err) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= q) return;
-    const uint32_t c = rank_to_col(qrank[i], Dd.bits, Dd.wpre, Dd.N);
-    if (c >= Dd.N) { atomicOr(err, 1u); return; }
-    dict[c] = qmon[i];
+__global__ void k_dict_queue(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    GB_JOB_ITEM(J.nq)
+    const uint32_t c = col_of(J, J.qrank[i]);
+    if (c >= J.N) { atomicOr(&J.cnt->err, 1u); return; }
+    J.dict[c] = J.qmon[i];
 }
 
-__global__ void k_dict_given(uint32_t nrows, const uint4 *__restrict__ rt,
-                             const uint32_t *__restrict__ rk, const uint8_t *__restrict__ rflags,
-                             const uint32_t *__restrict__ lm_rank, Basis B, Dict Dd,
-                             uint4 *__restrict__ dict, uint32_t *__restrict__ is_piv,
-                             uint32_t *__restrict__ src, uint32_t *err) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrows || !(rflags[i] & FLAG_PIVOT)) return;
-    const uint32_t c = rank_to_col(lm_rank[i], Dd.bits, Dd.wpre, Dd.N);
-    if (c >= Dd.N) { atomicOr(err, 2u); return; }
-    dict[c] = mono_mul(rt[i], B.mon[B.off[rk[i]]]);
-    is_piv[c] = 1u;
-    src[c] = 0x80000000u | i;
+__global__ void k_dict_given(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    GB_JOB_ITEM(J.ng)
+    if (!(J.gf[i] & FLAG_PIVOT)) return;
+    const uint32_t c = col_of(J, J.lm_rank[i]);
+    if (c >= J.N) { atomicOr(&J.cnt->err, 2u); return; }
+    J.dict[c] = mono_mul(J.gt[i], J.bmon[J.boff[J.gk[i]]]);
+    J.is_piv[c] = 1u;
+    J.src[c] = 0x80000000u | i;
 }
 
-__global__ void k_piv_reducers(uint32_t nred, const uint32_t *__restrict__ red_rank, Dict Dd,
-                               uint32_t *__restrict__ is_piv, uint32_t *__restrict__ src,
-                               uint32_t *err) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nred) return;
-    const uint32_t c = rank_to_col(red_rank[i], Dd.bits, Dd.wpre, Dd.N);
-    if (c >= Dd.N) { atomicOr(err, 4u); return; }
-    is_piv[c] = 1u;
-    src[c] = i;
+__global__ void k_piv_reducers(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    GB_JOB_ITEM(J.nred)
+    const uint32_t c = col_of(J, J.red_rank[i]);
+    if (c >= J.N) { atomicOr(&J.cnt->err, 4u); return; }
+    J.is_piv[c] = 1u;
+    J.src[c] = i;
 }
-
-struct RowsOut {
-    uint4 *t;
-    uint32_t *k;
-    uint8_t *flags;
-    uint32_t *pcols, *nonpiv, *colpos;
-    uint32_t nA, nb;  // allocated pivot rows / non-pivot columns
-    uint32_t *err;
-};
 
 // Pass 5a: pivot rows by leading column, and the column maps
-__global__ void k_place_pivots(uint32_t N, const uint32_t *__restrict__ is_piv,
-                               const uint32_t *__restrict__ pidx, const uint32_t *__restrict__ src,
-                               const uint4 *__restrict__ gt, const uint32_t *__restrict__ gk,
-                               const uint8_t *__restrict__ gflags, const uint4 *__restrict__ red_t,
-                               const uint32_t *__restrict__ red_k, RowsOut O) {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    if (is_piv[c]) {
-        const uint32_t r = pidx[c], s = src[c];
-        if (r >= O.nA) { atomicOr(O.err, 8u); return; }
+__global__ void k_place_pivots(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    GB_JOB_ITEM(J.N)
+    const uint32_t c = i;
+    const uint32_t pc = J.pidx[c] - J.pidx[0];
+    if (J.is_piv[c]) {
+        const uint32_t r = pc, s = J.src[c];
+        if (r >= J.nA) { atomicOr(&J.cnt->err, 8u); return; }
         if (s & 0x80000000u) {
-            const uint32_t i = s & 0x7FFFFFFFu;
-            O.t[r] = gt[i];
-            O.k[r] = gk[i];
-            O.flags[r] = (uint8_t)(gflags[i] & (FLAG_PIVOT | FLAG_TAIL));
+            const uint32_t g = s & 0x7FFFFFFFu;
+            J.row_t[r] = J.gt[g];
+            J.row_k[r] = J.gk[g];
+            J.row_flags[r] = (uint8_t)(J.gf[g] & (FLAG_PIVOT | FLAG_TAIL));
         } else {
-            O.t[r] = red_t[s];
-            O.k[r] = red_k[s];
-            O.flags[r] = (uint8_t)(FLAG_PIVOT | FLAG_REDUCER);
+            J.row_t[r] = J.red_t[s];
+            J.row_k[r] = J.red_k[s];
+            J.row_flags[r] = (uint8_t)(FLAG_PIVOT | FLAG_REDUCER);
         }
-        O.pcols[r] = c;
-        O.colpos[c] = r | 0x80000000u;
+        J.pcols[r] = c;
+        J.colpos[c] = r | 0x80000000u;
     } else {
-        const uint32_t q = c - pidx[c];
-        if (q >= O.nb) { atomicOr(O.err, 16u); return; }
-        O.nonpiv[q] = c;
-        O.colpos[c] = q;
+        const uint32_t q = c - pc;
+        if (q >= J.N - J.nA) { atomicOr(&J.cnt->err, 16u); return; }
+        J.nonpiv[q] = c;
+        J.colpos[c] = q;
     }
 }
 
 // Pass 5b: non-pivot given rows after the nA pivot rows, in the host's order
-__global__ void k_place_nonpivots(uint32_t nrows, uint32_t nA, const uint4 *__restrict__ gt,
-                                  const uint32_t *__restrict__ gk,
-                                  const uint8_t *__restrict__ gflags,
-                                  const uint32_t *__restrict__ np_index, RowsOut O) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrows || np_index[i] == 0xFFFFFFFFu) return;
-    const uint32_t r = nA + np_index[i];
-    O.t[r] = gt[i];
-    O.k[r] = gk[i];
-    O.flags[r] = (uint8_t)(gflags[i] & FLAG_TAIL);
+__global__ void k_place_nonpivots(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    GB_JOB_ITEM(J.ng)
+    if (J.gnp[i] == 0xFFFFFFFFu) return;
+    const uint32_t r = J.nA + J.gnp[i];
+    J.row_t[r] = J.gt[i];
+    J.row_k[r] = J.gk[i];
+    J.row_flags[r] = (uint8_t)(J.gf[i] & FLAG_TAIL);
 }
 
-// Pass 6: count
-__global__ void k_row_len(uint32_t nrows, const uint32_t *__restrict__ row_k,
-                          const uint8_t *__restrict__ flags, const uint32_t *__restrict__ blen,
-                          uint32_t *__restrict__ out) {
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < nrows) out[r] = blen[row_k[r]] - ((flags[r] & FLAG_TAIL) ? 1u : 0u);
+// Pass 6: count, then the job's own row_ptr from the concatenated scan
+__global__ void k_row_len(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    GB_JOB_ITEM(J.nrows)
+    J.lens[i] = J.blen[J.row_k[i]] - ((J.row_flags[i] & FLAG_TAIL) ? 1u : 0u);
+}
+
+__global__ void k_row_ptr(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    GB_JOB_ITEM(J.nrows + 1)
+    J.row_ptr[i] = J.lscan[i] - J.lscan[0];
 }
 
 // Pass 6: fill (warp per row)
-__global__ void k_fill(uint32_t nrows, const uint4 *__restrict__ row_t,
-                       const uint32_t *__restrict__ row_k, const uint8_t *__restrict__ flags,
-                       const uint32_t *__restrict__ row_ptr, Basis B, Keys K, Dict Dd,
-                       uint32_t *__restrict__ col, uint32_t *__restrict__ val, uint32_t nnz,
-                       uint32_t *err) {
+__global__ void k_fill(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     extern __shared__ uint32_t tab[];
-    load_tab(tab, K);
-    const uint32_t row = blockIdx.x * WPB + (threadIdx.x >> 5);
-    if (row >= nrows) return;
+    const int jb = job_of_block(bstart, nj);
+    const Job &J = jobs[jb];
+    load_tab(tab, J);
+    const uint32_t row = (blockIdx.x - bstart[jb]) * WPB + (threadIdx.x >> 5);
+    if (row >= J.nrows) return;
     const int lane = threadIdx.x & 31;
-    const uint32_t k = row_k[row];
-    const uint32_t skip = (flags[row] & FLAG_TAIL) ? 1u : 0u;
-    const uint32_t off = B.off[k] + skip, len = B.len[k] - skip, s = row_ptr[row];
-    const uint4 t = row_t[row];
-    if (s + len > nnz) {
-        if (lane == 0) atomicOr(err, 32u);
+    const uint32_t k = J.row_k[row];
+    const uint32_t skip = (J.row_flags[row] & FLAG_TAIL) ? 1u : 0u;
+    const uint32_t off = J.boff[k] + skip, len = J.blen[k] - skip, s = J.row_ptr[row];
+    const uint4 t = J.row_t[row];
+    if (s + len > J.nnz) {
+        if (lane == 0) atomicOr(&J.cnt->err, 32u);
         return;
     }
     for (uint32_t j = lane; j < len; j += 32) {
-        const uint4 m = mono_mul(t, B.mon[off + j]);
-        const uint32_t r = mono_rank(m, tab, K.n, K.D1);
-        col[s + j] = rank_to_col(r, Dd.bits, Dd.wpre, Dd.N);
-        val[s + j] = B.cf[off + j];
+        const uint4 m = mono_mul(t, J.bmon[off + j]);
+        const uint32_t r = mono_rank(m, tab, J.n, J.D1);
+        J.col[s + j] = col_of(J, r);
+        J.val[s + j] = J.bcf[off + j];
     }
+}
+
+// plan checks: dictionary size, pivot count, nnz and error flags of every job
+__global__ void k_check(const Job *__restrict__ jobs, int nj, const uint8_t *__restrict__ live,
+                        uint32_t *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nj || !live[j]) return;
+    const Job &J = jobs[j];
+    out[4 * j + 0] = J.wpre[J.W] - J.wpre[0];
+    out[4 * j + 1] = J.pidx[J.N] - J.pidx[0];
+    out[4 * j + 2] = J.row_ptr[J.nrows];
+    out[4 * j + 3] = J.cnt->err;
 }
 
 inline unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
@@ -322,230 +335,343 @@ uint64_t binom(uint32_t a, uint32_t b) {
     return r > (unsigned __int128)UINT64_MAX ? UINT64_MAX : (uint64_t)r;
 }
 
-}  // namespace
-
-std::unique_ptr<gb_macaulay> symbolic_preprocess(gb_system *S, const std::vector<RowSpec> &rows,
-                                                 bool closure, const std::vector<uint32_t> &nonred) {
-    Arena &ar = S->ctx->arena;
-    cudaStream_t st = S->stream;
-    const int n = (int)S->n;
-    const uint32_t ng = (uint32_t)rows.size();
-    auto M = std::make_unique<gb_macaulay>();
-    M->sys = S;
-    M->n = S->n;
-    GB_CUDA(cudaEventRecord(S->ev[0], st));
-
-    // step degree, rank space and the rank table
-    uint32_t D = 0;
-    for (const RowSpec &r : rows)
-        D = std::max<uint32_t>(D, (uint32_t)(mono_deg(r.t, n) + mono_deg(S->lm[r.k], n)));
-    M->degree = D;
-    const uint64_t space = binom((uint32_t)n + D, (uint32_t)n);
-    if (space >= (1ull << 32) - 64)
-        fail(GB_EUNSUPPORTED, "monomial space C(n+D, n) above 2^32 for the dense grevlex keys");
-    const uint32_t D1 = D + 1, W = (uint32_t)((space + 31) / 32);
-    std::vector<uint32_t> tab((size_t)D1 * n);
-    for (uint32_t d = 0; d <= D; ++d) tab[d] = (uint32_t)(d ? binom(n + d - 1, n) : 0);
-    for (int j = 1; j < n; ++j)
-        for (uint32_t s = 0; s <= D; ++s) tab[(size_t)D1 * j + s] = (uint32_t)binom(s + j - 1, j);
-    const int tabsz = (int)tab.size();
-    const size_t tab_smem = sizeof(uint32_t) * tabsz;
-
-    // given rows and the non-redundant list, staged through pinned memory
-    std::vector<uint32_t> np_index(ng, 0xFFFFFFFFu);
-    uint32_t npiv_given = 0, nnp = 0;
-    uint64_t nnz_given = 0;
-    for (uint32_t i = 0; i < ng; ++i) {
-        if (rows[i].pivot) ++npiv_given;
-        else np_index[i] = nnp++;
-        nnz_given += S->len[rows[i].k] - rows[i].skip;
-    }
-    const uint32_t nnr = (uint32_t)nonred.size();
-    const size_t stage = sizeof(uint4) * ng + 4 * ng + ng + 4 * ng + 4 * (size_t)tabsz +
-                         4 * nnr + sizeof(uint4) * nnr + 256 * 8;
-    char *h = static_cast<char *>(pinned(S, stage));
-    size_t o = 0;
-    auto put = [&](const void *src, size_t bytes) {
-        o = (o + 15) & ~size_t(15);
-        std::memcpy(h + o, src, bytes);
-        size_t at = o;
-        o += bytes;
-        return at;
-    };
-    std::vector<uint4> gt(ng);
-    std::vector<uint32_t> gk(ng);
-    std::vector<uint8_t> gf(ng);
-    std::vector<uint4> nlm(nnr);
-    for (uint32_t i = 0; i < ng; ++i) {
-        gt[i] = to_u4(rows[i].t);
-        gk[i] = rows[i].k;
-        gf[i] = (uint8_t)((rows[i].pivot ? FLAG_PIVOT : 0u) | (rows[i].skip ? FLAG_TAIL : 0u));
-    }
-    for (uint32_t i = 0; i < nnr; ++i) nlm[i] = to_u4(S->lm[nonred[i]]);
-    const size_t o_gt = put(gt.data(), sizeof(uint4) * ng), o_gk = put(gk.data(), 4 * ng),
-                 o_gf = put(gf.data(), ng), o_np = put(np_index.data(), 4 * ng),
-                 o_tab = put(tab.data(), 4 * (size_t)tabsz), o_nri = put(nonred.data(), 4 * nnr),
-                 o_nrl = put(nlm.data(), sizeof(uint4) * nnr);
-    DBuf<char> dstage;
-    dstage.alloc(ar, o, st);
-    GB_CUDA(cudaMemcpyAsync(dstage.p, h, o, cudaMemcpyHostToDevice, st));
-    const uint4 *d_gt = reinterpret_cast<const uint4 *>(dstage.p + o_gt);
-    const uint32_t *d_gk = reinterpret_cast<const uint32_t *>(dstage.p + o_gk);
-    const uint8_t *d_gf = reinterpret_cast<const uint8_t *>(dstage.p + o_gf);
-    const uint32_t *d_np = reinterpret_cast<const uint32_t *>(dstage.p + o_np);
-    const uint32_t *d_tab = reinterpret_cast<const uint32_t *>(dstage.p + o_tab);
-    const uint32_t *d_nri = reinterpret_cast<const uint32_t *>(dstage.p + o_nri);
-    const uint4 *d_nrl = reinterpret_cast<const uint4 *>(dstage.p + o_nrl);
-
-    Basis B{S->bmon.p, S->bcf.p, S->boff.p, S->blen.p};
-    DBuf<uint32_t> bits, lm_rank;
-    bits.alloc(ar, W, st);
-    lm_rank.alloc(ar, ng, st);
-    DBuf<Counters> cnt;
-    cnt.alloc(ar, 1, st);
-    Keys K{bits.p, d_tab, n, (int)D1, tabsz};
-
-    // queue and reducer-row capacity: start from an estimate, restart larger on overflow
-    uint64_t cap = std::min<uint64_t>(space, std::max<uint64_t>(1u << 16, 8ull * nnz_given / 4));
+// host part of one job
+struct SpHost {
+    uint32_t D = 0, D1 = 0, W = 0, ng = 0, npiv_given = 0, nnp = 0, tabsz = 0;
+    uint64_t space = 0, nnz_given = 0, cap = 0;
+    std::vector<uint32_t> tab, np_index;
+    std::vector<uint4> gt, nlm;
+    std::vector<uint32_t> gk;
+    std::vector<uint8_t> gf;
+    size_t o_gt = 0, o_gk = 0, o_gf = 0, o_np = 0, o_tab = 0, o_nri = 0, o_nrl = 0;
+    DBuf<uint32_t> bits, lm_rank, qrank, red_k, red_rank;
     DBuf<uint4> qmon, red_t;
-    DBuf<uint32_t> qrank, red_k, red_rank;
     Counters hc{};
     uint32_t rounds = 0;
-    for (int attempt = 0;; ++attempt) {
-        qmon.alloc(ar, cap, st);
-        qrank.alloc(ar, cap, st);
-        red_t.alloc(ar, cap, st);
-        red_k.alloc(ar, cap, st);
-        red_rank.alloc(ar, cap, st);
-        Queue Q{qmon.p, qrank.p, (uint32_t)cap};
-        GB_CUDA(cudaMemsetAsync(bits.p, 0, 4ull * W, st));
-        GB_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(Counters), st));
-        if (ng) {
-            k_mark_given<<<blocks(ng, 256), 256, tab_smem, st>>>(ng, d_gt, d_gk, d_gf, B, K, lm_rank.p);
-            counted();
-            k_expand_given<<<blocks(ng, WPB), 32 * WPB, tab_smem, st>>>(ng, d_gt, d_gk, d_gf, B, K, Q, cnt.p);
-            counted();
-            GB_CUDA(cudaGetLastError());
+    bool overflow = false;
+};
+
+}  // namespace
+
+void symbolic_preprocess(std::vector<SpTask> &tasks) {
+    if (tasks.empty()) return;
+    gb_ctx *ctx = tasks[0].S->ctx;
+    Arena &ar = ctx->arena;
+    cudaStream_t st = ctx->stream;
+    const int nj = (int)tasks.size();
+    GB_CUDA(cudaEventRecord(ctx->ev[0], st));
+
+    std::vector<SpHost> H(nj);
+    Stage sg;
+    for (int j = 0; j < nj; ++j) {
+        SpTask &T = tasks[j];
+        gb_system *S = T.S;
+        SpHost &h = H[j];
+        const int n = (int)S->n;
+        h.ng = (uint32_t)T.rows.size();
+        for (const RowSpec &r : T.rows)
+            h.D = std::max<uint32_t>(h.D, (uint32_t)(mono_deg(r.t, n) + mono_deg(S->lm[r.k], n)));
+        if (h.D > 255) fail(GB_EOVERFLOW, "step degree above 255");
+        h.space = binom((uint32_t)n + h.D, (uint32_t)n);
+        if (h.space >= (1ull << 32) - 64)
+            fail(GB_EUNSUPPORTED, "monomial space C(n+D, n) above 2^32 for the dense grevlex keys");
+        h.D1 = h.D + 1;
+        h.W = (uint32_t)((h.space + 31) / 32);
+        h.tab.assign((size_t)h.D1 * n, 0);
+        for (uint32_t d = 0; d <= h.D; ++d) h.tab[d] = (uint32_t)(d ? binom(n + d - 1, n) : 0);
+        for (int i = 1; i < n; ++i)
+            for (uint32_t s = 0; s <= h.D; ++s) h.tab[(size_t)h.D1 * i + s] = (uint32_t)binom(s + i - 1, i);
+        h.tabsz = (uint32_t)h.tab.size();
+        h.np_index.assign(h.ng, 0xFFFFFFFFu);
+        h.gt.resize(h.ng);
+        h.gk.resize(h.ng);
+        h.gf.resize(h.ng);
+        for (uint32_t i = 0; i < h.ng; ++i) {
+            const RowSpec &r = T.rows[i];
+            if (r.pivot) ++h.npiv_given;
+            else h.np_index[i] = h.nnp++;
+            h.nnz_given += S->len[r.k] - r.skip;
+            h.gt[i] = to_u4(r.t);
+            h.gk[i] = r.k;
+            h.gf[i] = (uint8_t)((r.pivot ? FLAG_PIVOT : 0u) | (r.skip ? FLAG_TAIL : 0u));
         }
-        uint32_t f0 = 0;
-        rounds = 0;
-        Counters *hcp = reinterpret_cast<Counters *>(h + ((o + 255) & ~size_t(255)));
-        bool overflow = false;
-        for (;;) {
-            GB_CUDA(cudaMemcpyAsync(hcp, cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-            sync(S);
-            hc = *hcp;
-            if (hc.q > cap || hc.red > cap) { overflow = true; break; }
-            if (!closure || hc.q == f0 || nnr == 0) break;
-            const uint32_t f1 = hc.q;
-            k_closure<<<blocks(f1 - f0, WPB), 32 * WPB, tab_smem, st>>>(
-                f0, f1, B, K, Q, cnt.p, d_nri, d_nrl, nnr, red_t.p, red_k.p, red_rank.p, (uint32_t)cap);
-            counted();
-            GB_CUDA(cudaGetLastError());
-            ++rounds;
-            f0 = f1;
+        h.nlm.resize(T.nonred.size());
+        for (size_t i = 0; i < T.nonred.size(); ++i) h.nlm[i] = to_u4(S->lm[T.nonred[i]]);
+        h.o_gt = sg.put(h.gt.data(), 16ull * h.ng);
+        h.o_gk = sg.put(h.gk.data(), 4ull * h.ng);
+        h.o_gf = sg.put(h.gf.data(), h.ng);
+        h.o_np = sg.put(h.np_index.data(), 4ull * h.ng);
+        h.o_tab = sg.put(h.tab.data(), 4ull * h.tabsz);
+        h.o_nri = sg.put(T.nonred.data(), 4ull * T.nonred.size());
+        h.o_nrl = sg.put(h.nlm.data(), 16ull * h.nlm.size());
+        h.cap = T.cap ? T.cap : std::min<uint64_t>(h.space, std::max<uint64_t>(1u << 14, 2ull * h.nnz_given));
+        h.bits.alloc(ar, h.W, st);
+        h.lm_rank.alloc(ar, h.ng, st);
+        h.qmon.alloc(ar, h.cap, st);
+        h.qrank.alloc(ar, h.cap, st);
+        h.red_t.alloc(ar, h.cap, st);
+        h.red_k.alloc(ar, h.cap, st);
+        h.red_rank.alloc(ar, h.cap, st);
+        GB_CUDA(cudaMemsetAsync(h.bits.p, 0, 4ull * h.W, st));
+    }
+    std::vector<uint32_t> bm(nj), be(nj);
+    int max_tab = 1;
+    for (int j = 0; j < nj; ++j) {
+        bm[j] = blocks(H[j].ng, 256);
+        be[j] = blocks(H[j].ng, WPB);
+        max_tab = std::max<int>(max_tab, (int)H[j].tabsz);
+    }
+    size_t o_bm, o_be;
+    const uint32_t tbm = plan(sg, bm, o_bm), tbe = plan(sg, be, o_be);
+    const size_t o_jobs = sg.put(nullptr, sizeof(Job) * nj);
+    DBuf<Counters> cnt;
+    cnt.alloc(ar, nj, st);
+    GB_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(Counters) * nj, st));
+    // the device staging buffer holds the job table, so its address is needed first
+    DBuf<char> dstage;
+    dstage.alloc(ar, sg.h.size() + 16, st);
+    auto dptr = [&](size_t off) { return dstage.p + off; };
+    std::vector<Job> jobs(nj);
+    for (int j = 0; j < nj; ++j) {
+        SpTask &T = tasks[j];
+        gb_system *S = T.S;
+        SpHost &h = H[j];
+        Job &J = jobs[j];
+        J = Job{};
+        J.bmon = S->bmon.p;
+        J.bcf = S->bcf.p;
+        J.boff = S->boff.p;
+        J.blen = S->blen.p;
+        J.gt = reinterpret_cast<const uint4 *>(dptr(h.o_gt));
+        J.gk = reinterpret_cast<const uint32_t *>(dptr(h.o_gk));
+        J.gf = reinterpret_cast<const uint8_t *>(dptr(h.o_gf));
+        J.gnp = reinterpret_cast<const uint32_t *>(dptr(h.o_np));
+        J.ng = h.ng;
+        J.bits = h.bits.p;
+        J.tab = reinterpret_cast<const uint32_t *>(dptr(h.o_tab));
+        J.n = (int)S->n;
+        J.D1 = (int)h.D1;
+        J.tabsz = (int)h.tabsz;
+        J.W = h.W;
+        J.nr_idx = reinterpret_cast<const uint32_t *>(dptr(h.o_nri));
+        J.nr_lm = reinterpret_cast<const uint4 *>(dptr(h.o_nrl));
+        J.nnr = (uint32_t)T.nonred.size();
+        J.qmon = h.qmon.p;
+        J.qrank = h.qrank.p;
+        J.cap = (uint32_t)h.cap;
+        J.red_t = h.red_t.p;
+        J.red_k = h.red_k.p;
+        J.red_rank = h.red_rank.p;
+        J.lm_rank = h.lm_rank.p;
+        J.cnt = cnt.p + j;
+    }
+    std::memcpy(sg.h.data() + o_jobs, jobs.data(), sizeof(Job) * nj);
+    {
+        char *hp = static_cast<char *>(ctx_pinned(ctx, sg.h.size() + 16));
+        std::memcpy(hp, sg.h.data(), sg.h.size());
+        GB_CUDA(cudaMemcpyAsync(dstage.p, hp, sg.h.size(), cudaMemcpyHostToDevice, st));
+    }
+    const Job *djobs = reinterpret_cast<const Job *>(dptr(o_jobs));
+    const size_t tab_smem = 4ull * max_tab;
+    if (tbm) {
+        k_mark_given<<<tbm, 256, tab_smem, st>>>(djobs, reinterpret_cast<const uint32_t *>(dptr(o_bm)), nj);
+        counted();
+        k_expand_given<<<tbe, 32 * WPB, tab_smem, st>>>(djobs, reinterpret_cast<const uint32_t *>(dptr(o_be)), nj);
+        counted();
+    }
+
+    // closure rounds: every job's counters come back in one copy per round
+    DBuf<uint32_t> dround;  // [2 nj] ranges, then nj + 1 block starts
+    dround.alloc(ar, 3ull * nj + 1, st);
+    std::vector<uint32_t> f0(nj, 0);
+    for (;;) {
+        Counters *hc = static_cast<Counters *>(ctx_pinned(ctx, sizeof(Counters) * nj + 16ull * nj + 64));
+        GB_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof(Counters) * nj, cudaMemcpyDeviceToHost, st));
+        ctx_sync(ctx);
+        std::vector<uint32_t> buf(3ull * nj + 1, 0);
+        uint32_t total = 0;
+        for (int j = 0; j < nj; ++j) {
+            SpHost &h = H[j];
+            h.hc = hc[j];
+            if (h.hc.q > h.cap || h.hc.red > h.cap) h.overflow = true;
+            const bool more = tasks[j].closure && !h.overflow && h.hc.q > f0[j] && jobs[j].nnr > 0;
+            buf[2 * j] = f0[j];
+            buf[2 * j + 1] = more ? h.hc.q : f0[j];
+            buf[2 * nj + j] = total;
+            if (more) {
+                total += blocks(h.hc.q - f0[j], WPB);
+                ++h.rounds;
+                f0[j] = h.hc.q;
+            }
         }
-        if (!overflow) break;
-        if (cap >= space) fail(GB_EDEVICE, "frontier queue overflow beyond the monomial space");
-        cap = std::min<uint64_t>(space, 2ull * std::max<uint64_t>(hc.q, hc.red));
+        buf[3 * nj] = total;
+        if (!total) break;
+        uint32_t *hb = reinterpret_cast<uint32_t *>(hc);  // the counters have been consumed
+        std::memcpy(hb, buf.data(), 4 * buf.size());
+        GB_CUDA(cudaMemcpyAsync(dround.p, hb, 4 * buf.size(), cudaMemcpyHostToDevice, st));
+        k_closure<<<total, 32 * WPB, tab_smem, st>>>(djobs, dround.p + 2 * nj, nj, dround.p);
+        counted();
     }
-    M->closure_rounds = rounds;
 
-    const uint32_t nq = hc.q, nred = hc.red;
-    const uint32_t N = npiv_given + nq;
-    const uint32_t nA = nred + npiv_given, nrows = ng + nred;
-    const uint64_t nnz = nnz_given + hc.red_nnz;
-    if (nnz >= (1ull << 32)) fail(GB_EUNSUPPORTED, "more than 2^32 nonzeros in one matrix");
-    M->ndict = N;
-    M->nA = nA;
-    M->nC = nnp;
-    M->nb = N - nA;
-    M->nrows = nrows;
-    M->nnz = nnz;
+    // jobs whose queue overflowed start again with room for what they found
+    std::vector<SpTask> retry;
+    std::vector<int> retry_of;
+    for (int j = 0; j < nj; ++j) {
+        if (!H[j].overflow) continue;
+        if (H[j].cap >= H[j].space) fail(GB_EDEVICE, "frontier queue overflow beyond the monomial space");
+        SpTask t;
+        t.S = tasks[j].S;
+        t.rows = tasks[j].rows;
+        t.closure = tasks[j].closure;
+        t.nonred = tasks[j].nonred;
+        t.cap = std::min<uint64_t>(H[j].space, 4ull * std::max<uint64_t>(H[j].hc.q, H[j].hc.red));
+        retry.push_back(std::move(t));
+        retry_of.push_back(j);
+    }
 
-    // dictionary
-    DBuf<uint32_t> wcnt, wpre;
-    wcnt.alloc(ar, W, st);
-    wpre.alloc(ar, (size_t)W + 1, st);
-    k_popc<<<blocks(W, 256), 256, 0, st>>>(bits.p, wcnt.p, W);
-    counted();
-    exclusive_scan(ar, wcnt.p, wpre.p, W, st);
-    Dict Dd{bits.p, wpre.p, N};
-    M->dict.alloc(ar, N, st);
-    DBuf<uint32_t> is_piv, src, pidx;
-    is_piv.alloc(ar, N, st);
-    src.alloc(ar, N, st);
-    pidx.alloc(ar, (size_t)N + 1, st);
-    GB_CUDA(cudaMemsetAsync(is_piv.p, 0, 4ull * N, st));
-    uint32_t *derr = &cnt.p->err;
-    if (nq) {
-        k_dict_queue<<<blocks(nq, 256), 256, 0, st>>>(nq, qmon.p, qrank.p, Dd, M->dict.p, derr);
-        counted();
+    // sizes of the plans that did not overflow
+    std::vector<int> live;
+    std::vector<uint8_t> live_flag(nj, 0);
+    uint64_t tw = 0, tN = 0, tr = 0;
+    std::vector<uint64_t> woff(nj, 0), noff(nj, 0), roff(nj, 0);
+    for (int j = 0; j < nj; ++j) {
+        if (H[j].overflow) continue;
+        live.push_back(j);
+        live_flag[j] = 1;
+        SpHost &h = H[j];
+        Job &J = jobs[j];
+        J.nq = h.hc.q;
+        J.nred = h.hc.red;
+        J.N = h.npiv_given + J.nq;
+        J.nA = J.nred + h.npiv_given;
+        J.nrows = h.ng + J.nred;
+        const uint64_t nnz = h.nnz_given + h.hc.red_nnz;
+        if (nnz >= (1ull << 32)) fail(GB_EUNSUPPORTED, "more than 2^32 nonzeros in one matrix");
+        J.nnz = (uint32_t)nnz;
+        woff[j] = tw;
+        tw += h.W;
+        noff[j] = tN;
+        tN += J.N;
+        roff[j] = tr;
+        tr += J.nrows;
     }
-    if (ng) {
-        k_dict_given<<<blocks(ng, 256), 256, 0, st>>>(ng, d_gt, d_gk, d_gf, lm_rank.p, B, Dd,
-                                                      M->dict.p, is_piv.p, src.p, derr);
-        counted();
+    DBuf<uint32_t> wcnt, wpre, ispiv, src, pidx, lens, lscan;
+    wcnt.alloc(ar, tw, st);
+    wpre.alloc(ar, tw + 1, st);
+    ispiv.alloc(ar, tN, st);
+    src.alloc(ar, tN, st);
+    pidx.alloc(ar, tN + 1, st);
+    lens.alloc(ar, tr, st);
+    lscan.alloc(ar, tr + 1, st);
+    GB_CUDA(cudaMemsetAsync(ispiv.p, 0, 4 * tN, st));
+    for (int j : live) {
+        SpTask &T = tasks[j];
+        Job &J = jobs[j];
+        auto M = std::make_unique<gb_macaulay>();
+        M->sys = T.S;
+        M->n = T.S->n;
+        M->degree = H[j].D;
+        M->ndict = J.N;
+        M->nA = J.nA;
+        M->nC = H[j].nnp;
+        M->nb = J.N - J.nA;
+        M->nrows = J.nrows;
+        M->nnz = J.nnz;
+        M->closure_rounds = H[j].rounds;
+        M->dict.alloc(ar, J.N, st);
+        M->row_t.alloc(ar, J.nrows, st);
+        M->row_k.alloc(ar, J.nrows, st);
+        M->row_flags.alloc(ar, J.nrows, st);
+        M->pcols.alloc(ar, J.nA, st);
+        M->nonpiv.alloc(ar, M->nb, st);
+        M->colpos.alloc(ar, J.N, st);
+        M->row_ptr.alloc(ar, (size_t)J.nrows + 1, st);
+        M->col.alloc(ar, J.nnz, st);
+        M->val.alloc(ar, J.nnz, st);
+        J.wcnt = wcnt.p + woff[j];
+        J.wpre = wpre.p + woff[j];
+        J.is_piv = ispiv.p + noff[j];
+        J.src = src.p + noff[j];
+        J.pidx = pidx.p + noff[j];
+        J.dict = M->dict.p;
+        J.row_t = M->row_t.p;
+        J.row_k = M->row_k.p;
+        J.row_flags = M->row_flags.p;
+        J.pcols = M->pcols.p;
+        J.nonpiv = M->nonpiv.p;
+        J.colpos = M->colpos.p;
+        J.lens = lens.p + roff[j];
+        J.lscan = lscan.p + roff[j];
+        J.row_ptr = M->row_ptr.p;
+        J.col = M->col.p;
+        J.val = M->val.p;
+        T.out = std::move(M);
     }
-    if (nred) {
-        k_piv_reducers<<<blocks(nred, 256), 256, 0, st>>>(nred, red_rank.p, Dd, is_piv.p, src.p, derr);
+    if (!live.empty()) {
+        // second-stage job table and plans (jobs that overflowed get no blocks)
+        Stage s2;
+        std::vector<uint32_t> b_w(nj, 0), b_q(nj, 0), b_g(nj, 0), b_r(nj, 0), b_N(nj, 0), b_rows(nj, 0),
+            b_rp(nj, 0), b_fill(nj, 0);
+        for (int j : live) {
+            const Job &J = jobs[j];
+            b_w[j] = blocks(J.W, 256);
+            b_q[j] = blocks(J.nq, 256);
+            b_g[j] = blocks(J.ng, 256);
+            b_r[j] = blocks(J.nred, 256);
+            b_N[j] = blocks(J.N, 256);
+            b_rows[j] = blocks(J.nrows, 256);
+            b_rp[j] = blocks((size_t)J.nrows + 1, 256);
+            b_fill[j] = blocks(J.nrows, WPB);
+        }
+        size_t o_w, o_q, o_g, o_r, o_N, o_rows, o_rp, o_fill;
+        const uint32_t t_w = plan(s2, b_w, o_w), t_q = plan(s2, b_q, o_q), t_g = plan(s2, b_g, o_g),
+                       t_r = plan(s2, b_r, o_r), t_N = plan(s2, b_N, o_N), t_rows = plan(s2, b_rows, o_rows),
+                       t_rp = plan(s2, b_rp, o_rp), t_fill = plan(s2, b_fill, o_fill);
+        const size_t o_j2 = s2.put(jobs.data(), sizeof(Job) * nj);
+        const size_t o_live = s2.put(live_flag.data(), nj);
+        DBuf<char> d2;
+        s2.upload(ctx, d2);
+        const Job *dj = reinterpret_cast<const Job *>(d2.p + o_j2);
+        auto P = [&](size_t o) { return reinterpret_cast<const uint32_t *>(d2.p + o); };
+        if (t_w) { k_popc<<<t_w, 256, 0, st>>>(dj, P(o_w), nj); counted(); }
+        exclusive_scan(ar, wcnt.p, wpre.p, tw, st);
+        if (t_q) { k_dict_queue<<<t_q, 256, 0, st>>>(dj, P(o_q), nj); counted(); }
+        if (t_g) { k_dict_given<<<t_g, 256, 0, st>>>(dj, P(o_g), nj); counted(); }
+        if (t_r) { k_piv_reducers<<<t_r, 256, 0, st>>>(dj, P(o_r), nj); counted(); }
+        exclusive_scan(ar, ispiv.p, pidx.p, tN, st);
+        if (t_N) { k_place_pivots<<<t_N, 256, 0, st>>>(dj, P(o_N), nj); counted(); }
+        if (t_g) { k_place_nonpivots<<<t_g, 256, 0, st>>>(dj, P(o_g), nj); counted(); }
+        if (t_rows) { k_row_len<<<t_rows, 256, 0, st>>>(dj, P(o_rows), nj); counted(); }
+        exclusive_scan(ar, lens.p, lscan.p, tr, st);
+        if (t_rp) { k_row_ptr<<<t_rp, 256, 0, st>>>(dj, P(o_rp), nj); counted(); }
+        if (t_fill) { k_fill<<<t_fill, 32 * WPB, tab_smem, st>>>(dj, P(o_fill), nj); counted(); }
+        GB_CUDA(cudaEventRecord(ctx->ev[1], st));
+        // consistency of every plan with the host's counts (one small read-back)
+        DBuf<uint32_t> chk;
+        chk.alloc(ar, 4ull * nj, st);
+        k_check<<<blocks(nj, 128), 128, 0, st>>>(dj, nj, reinterpret_cast<const uint8_t *>(d2.p + o_live), chk.p);
         counted();
+        uint32_t *hchk = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj + 16));
+        GB_CUDA(cudaMemcpyAsync(hchk, chk.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
+        ctx_sync(ctx);
+        float ms = 0.f;
+        GB_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        for (int j : live) {
+            const Job &J = jobs[j];
+            const uint32_t *c = hchk + 4 * j;
+            if (c[0] != J.N || c[1] != J.nA || c[2] != J.nnz || c[3])
+                fail(GB_EDEVICE, "symbolic preprocessing: device counts disagree with the plan: columns " +
+                                     std::to_string(c[0]) + "/" + std::to_string(J.N) + ", pivots " +
+                                     std::to_string(c[1]) + "/" + std::to_string(J.nA) + ", nnz " +
+                                     std::to_string(c[2]) + "/" + std::to_string(J.nnz) + ", flags " +
+                                     std::to_string(c[3]));
+            tasks[j].out->ms_sp = ms;
+        }
     }
-    GB_CUDA(cudaGetLastError());
-    exclusive_scan(ar, is_piv.p, pidx.p, N, st);
-
-    // rows
-    M->row_t.alloc(ar, nrows, st);
-    M->row_k.alloc(ar, nrows, st);
-    M->row_flags.alloc(ar, nrows, st);
-    M->pcols.alloc(ar, nA, st);
-    M->nonpiv.alloc(ar, M->nb, st);
-    M->colpos.alloc(ar, N, st);
-    RowsOut O{M->row_t.p, M->row_k.p, M->row_flags.p, M->pcols.p, M->nonpiv.p, M->colpos.p,
-              nA, M->nb, derr};
-    if (N) {
-        k_place_pivots<<<blocks(N, 256), 256, 0, st>>>(N, is_piv.p, pidx.p, src.p, d_gt, d_gk, d_gf,
-                                                       red_t.p, red_k.p, O);
-        counted();
+    if (!retry.empty()) {
+        symbolic_preprocess(retry);
+        for (size_t i = 0; i < retry.size(); ++i) tasks[retry_of[i]].out = std::move(retry[i].out);
     }
-    if (ng) {
-        k_place_nonpivots<<<blocks(ng, 256), 256, 0, st>>>(ng, nA, d_gt, d_gk, d_gf, d_np, O);
-        counted();
-    }
-    GB_CUDA(cudaGetLastError());
-
-    // CSR: count -> scan -> fill
-    DBuf<uint32_t> lens;
-    lens.alloc(ar, nrows, st);
-    M->row_ptr.alloc(ar, (size_t)nrows + 1, st);
-    M->col.alloc(ar, nnz, st);
-    M->val.alloc(ar, nnz, st);
-    if (nrows) {
-        k_row_len<<<blocks(nrows, 256), 256, 0, st>>>(nrows, M->row_k.p, M->row_flags.p, S->blen.p, lens.p);
-        counted();
-    }
-    exclusive_scan(ar, lens.p, M->row_ptr.p, nrows, st);
-    if (nrows) {
-        k_fill<<<blocks(nrows, WPB), 32 * WPB, tab_smem, st>>>(nrows, M->row_t.p, M->row_k.p,
-                                                               M->row_flags.p, M->row_ptr.p, B, K, Dd,
-                                                               M->col.p, M->val.p, (uint32_t)nnz, derr);
-        counted();
-    }
-    GB_CUDA(cudaGetLastError());
-    GB_CUDA(cudaEventRecord(S->ev[1], st));
-
-    // consistency of the plan with the host's counts (one small read-back)
-    uint32_t *chk = reinterpret_cast<uint32_t *>(h + ((o + 255) & ~size_t(255)) + 256);
-    GB_CUDA(cudaMemcpyAsync(chk, wpre.p + W, 4, cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaMemcpyAsync(chk + 1, pidx.p + N, 4, cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaMemcpyAsync(chk + 2, M->row_ptr.p + nrows, 4, cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaMemcpyAsync(chk + 3, derr, 4, cudaMemcpyDeviceToHost, st));
-    sync(S);
-    if (chk[0] != N || chk[1] != nA || chk[2] != (uint32_t)nnz || chk[3])
-        fail(GB_EDEVICE, "symbolic preprocessing: device counts disagree with the plan (flags " +
-                             std::to_string(chk[3]) + ")");
-    GB_CUDA(cudaEventElapsedTime(&M->ms_sp, S->ev[0], S->ev[1]));
-    return M;
 }
 
 }  // namespace gb
