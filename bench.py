@@ -118,7 +118,7 @@ def run_ours(args) -> None:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     system = synth.config2(0)
-    ctx = gb.Context(device=local, arena_bytes=32 << 30)
+    ctx = gb.Context(device=local, arena_bytes=args.arena_gb << 30)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 126 MB L2
 
     def barrier():
@@ -179,12 +179,14 @@ def run_ours(args) -> None:
         d2h = off.nbytes + ex.nbytes + cf.nbytes
     e2e_value = (nnz / len(runs) * (world if world > 1 else 1)) / (statistics.median(e2e_ms) / 1e3)
 
-    # roofline of the sparse row reduction (the dominant stage, see profiles/): algorithmic bytes
-    # = 8 B per modular multiply-add (col_ind + val of a pivot-row entry read) + 4 B per D' entry
+    # roofline of the sparse row reduction kernel (the dominant kernel, see profiles/): algorithmic
+    # bytes = 8 B per modular multiply-add (col_ind + val of a pivot-row entry read); time = the
+    # device time of its launches alone (CUDA events around them on the context's stream), summed
+    # over the timed runs
     r0 = runs[0]
     pk = peaks()
-    red_ms = r0["ms_reduce"]
-    alg_bytes = 8.0 * r0["axpy_fma"]
+    red_ms = sum(r["ms_reduce_kernel"] for r in runs)
+    alg_bytes = 8.0 * sum(r["axpy_fma"] for r in runs)
     achieved = alg_bytes / (red_ms / 1e3) / 1e9 if red_ms > 0 else 0.0
     roofline = {"kernel": "k_reduce (sparse row AXPY reduction, per F4 run)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -195,7 +197,7 @@ def run_ours(args) -> None:
     batched = measure_batched(gb, synth, ctx) if rank == 0 and not args.no_batch else None
     served = measure_served(gb, synth, ctx) if rank == 0 and not args.no_batch else None
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
-             for k in ("ms_sp", "ms_reduce", "ms_rref", "ms_update", "ms_pairs", "ms_select",
+             for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_rref", "ms_update", "ms_pairs", "ms_select",
                        "ms_wall")}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -226,12 +228,10 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
-def measure_batched(gb, synth, ctx) -> dict:
-    """The multi-prime batch: one n=8 dense quadratic system modulo the 128 largest primes below
-    2^31, run one system after another (plain) and as one gb_batch_groebner call (batched)."""
-    systems = synth.multi_prime_system(synth.largest_primes_below(2 ** 31, 128))
-    out = {"workload": "n=8 dense quadratic system modulo the 128 largest primes below 2^31 "
-                       "(128 independent F4 runs)", "systems": len(systems)}
+def _plain_vs_batched(gb, ctx, systems) -> dict:
+    """The same systems run one after another through gb_groebner (plain) and as one
+    gb_batch_groebner call (batched, lockstep); wall clock of each, nnz rate of each."""
+    out = {"systems": len(systems)}
     for mode in ("plain", "batched"):
         hs = [gb.gb_system_create(ctx.h, s) for s in systems]
         t0 = time.perf_counter()
@@ -243,47 +243,81 @@ def measure_batched(gb, synth, ctx) -> dict:
         for h in hs:
             gb.gb_system_destroy(h)
         nnz = sum(st["nnz_total"] for st in stats)
-        out[f"{mode}_ms"] = dt * 1e3
+        out[f"{mode}_ms"] = round(dt * 1e3, 2)
         out[f"{mode}_nnz_per_s"] = nnz / dt
-    out["speedup"] = out["plain_ms"] / out["batched_ms"]
+        out[f"{mode}_systems_per_s"] = len(systems) / dt
+    out["speedup"] = round(out["plain_ms"] / out["batched_ms"], 3)
     return out
 
 
-def measure_served(gb, synth, ctx, count: int = 300) -> dict:
-    """Poisson stream of served requests (n ~ U{5..11}, 20-66 terms, p = 65521 or 2^31-1) at 0.8x
-    the batched saturation rate; latency = completion - arrival, through gb_server_*."""
+def _max_degree(s: dict) -> int:
+    return int(s["exps"].reshape(-1, s["n"]).sum(axis=1).max())
+
+
+def measure_batched(gb, synth, ctx) -> list:
+    """Two batches, each run plain and batched: the n=8 dense quadratic system modulo the 128
+    largest primes below 2^31, and the 256-system mixed batch without its cubic members in 8 or 9
+    variables (those alone run for seconds to minutes each, beyond a bench line's budget)."""
+    primes = synth.multi_prime_system(synth.largest_primes_below(2 ** 31, 128))
+    mixed = [s for s in synth.mixed_batch(256) if not (_max_degree(s) == 3 and s["n"] >= 8)]
+    a = _plain_vs_batched(gb, ctx, primes)
+    a["workload"] = "n=8 dense quadratic system modulo the 128 largest primes below 2^31"
+    b = _plain_vs_batched(gb, ctx, mixed)
+    b["workload"] = (f"{len(mixed)} of the 256 mixed systems (n ~ U{{5..9}}, degree 2 or 3, 10-40 terms, "
+                     "p=65521): all but the cubic ones with n >= 8")
+    return [a, b]
+
+
+def measure_served(gb, synth, ctx, count: int = 300, slots: int = 64,
+                   loads=(0.5, 0.8, 0.95)) -> dict:
+    """Poisson streams of served requests (n ~ U{5..11}, 20-66 terms, p = 65521 or 2^31-1) through
+    gb_server_* at fractions of the batched saturation rate; latency = completion - arrival.  The
+    plain rate is the same requests run one at a time through gb_groebner."""
     import numpy as _np
     reqs = [synth.served_request(i) for i in range(count)]
-    hs = [gb.gb_system_create(ctx.h, s) for s in reqs[:64]]
+    # plain: one system at a time
+    t0 = time.perf_counter()
+    for s in reqs:
+        h = gb.gb_system_create(ctx.h, s)
+        gb.gb_groebner(h)
+        gb.gb_system_destroy(h)
+    plain = count / (time.perf_counter() - t0)
+    # saturation: a lockstep batch of as many requests as the server has slots
+    hs = [gb.gb_system_create(ctx.h, s) for s in reqs[:slots]]
     t0 = time.perf_counter()
     gb.gb_batch_groebner(ctx.h, hs)
     sat = len(hs) / (time.perf_counter() - t0)
     for h in hs:
         gb.gb_system_destroy(h)
-    rate = 0.8 * sat
-    arrivals = synth.poisson_arrivals(count, rate)
-    srv = gb.gb_server_create(ctx.h, 150 << 30, 32)
-    pending, lat = {}, []
-    start = time.perf_counter()
-    nxt = 0
-    while nxt < count or pending:
-        now = time.perf_counter() - start
-        while nxt < count and arrivals[nxt] <= now:
-            pending[gb.gb_server_submit(srv, gb.gb_system_create(ctx.h, reqs[nxt]))] = arrivals[nxt]
-            nxt += 1
-        for t in list(pending):
-            h, st = gb.gb_server_poll(srv, t)
-            if h is not None:
-                lat.append(time.perf_counter() - start - pending.pop(t))
-                gb.gb_system_destroy(h)
-        time.sleep(0.0005)
-    wall = time.perf_counter() - start
-    gb.gb_server_destroy(srv)
-    lat_ms = _np.array(lat) * 1e3
-    return {"workload": f"{count} Poisson requests, n ~ U{{5..11}}, 20-66 terms, p in {{65521, 2^31-1}}",
-            "rate_per_s": rate, "saturation_per_s": sat, "systems_per_s": count / wall,
-            "p50_ms": float(_np.percentile(lat_ms, 50)), "p99_ms": float(_np.percentile(lat_ms, 99)),
-            "hbm_cap_bytes": 150 << 30, "slots": 32}
+    runs = []
+    for load in loads:
+        rate = load * sat
+        arrivals = synth.poisson_arrivals(count, rate)
+        srv = gb.gb_server_create(ctx.h, 150 << 30, slots)
+        pending, lat = {}, []
+        start = time.perf_counter()
+        nxt = 0
+        while nxt < count or pending:
+            now = time.perf_counter() - start
+            while nxt < count and arrivals[nxt] <= now:
+                pending[gb.gb_server_submit(srv, gb.gb_system_create(ctx.h, reqs[nxt]))] = arrivals[nxt]
+                nxt += 1
+            for t in list(pending):
+                h, st = gb.gb_server_poll(srv, t)
+                if h is not None:
+                    lat.append(time.perf_counter() - start - pending.pop(t))
+                    gb.gb_system_destroy(h)
+            time.sleep(0.0005)
+        wall = time.perf_counter() - start
+        gb.gb_server_destroy(srv)
+        lat_ms = _np.array(lat) * 1e3
+        runs.append({"load": load, "rate_per_s": round(rate, 2), "systems_per_s": round(count / wall, 2),
+                     "p50_ms": round(float(_np.percentile(lat_ms, 50)), 2),
+                     "p99_ms": round(float(_np.percentile(lat_ms, 99)), 2)})
+    return {"workload": f"{count} Poisson requests per load, n ~ U{{5..11}}, 20-66 terms, "
+                        "p in {65521, 2^31-1}",
+            "plain_systems_per_s": round(plain, 2), "saturation_systems_per_s": round(sat, 2),
+            "hbm_cap_bytes": 150 << 30, "slots": slots, "loads": runs}
 
 
 def cpu_baseline(system: dict) -> dict:
@@ -343,6 +377,7 @@ def main() -> None:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and served lines")
+    ap.add_argument("--arena-gb", type=int, default=32, help="device arena of the context (GiB)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

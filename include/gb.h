@@ -122,6 +122,8 @@ typedef struct {
     float ms_update;   /* wall time: reconstruction of the new elements on the device */
     float ms_pairs;    /* host time: critical-pair update (Gebauer-Moeller) for the new elements */
     float ms_select;   /* host time: pair selection and ordering of the step's rows */
+    float ms_reduce_kernel; /* device time of the row-reduction kernel launches alone (a part of
+                               ms_reduce, which also covers their setup) */
     double ms_wall;    /* host wall time of the step */
 } gb_step_stats;
 
@@ -130,6 +132,8 @@ typedef struct {
     uint64_t nnz_total;
     uint64_t axpy_rows, axpy_fma;
     double ms_sp, ms_reduce, ms_rref, ms_update, ms_pairs, ms_select, ms_wall;
+    double ms_reduce_kernel;
+    double ms_finish;  /* wall time of the final minimalisation and tail reduction */
 } gb_run_stats;
 
 /* ---- context -------------------------------------------------------------------------------- */

@@ -63,7 +63,8 @@ class gb_step_stats(ctypes.Structure):
                [("nnz", ctypes.c_uint64), ("axpy_rows", ctypes.c_uint64), ("axpy_fma", ctypes.c_uint64),
                 ("ms_sp", ctypes.c_float), ("ms_reduce", ctypes.c_float),
                 ("ms_rref", ctypes.c_float), ("ms_update", ctypes.c_float), ("ms_pairs", ctypes.c_float),
-                ("ms_select", ctypes.c_float), ("ms_wall", ctypes.c_double)]
+                ("ms_select", ctypes.c_float), ("ms_reduce_kernel", ctypes.c_float),
+                ("ms_wall", ctypes.c_double)]
 
 
 class gb_run_stats(ctypes.Structure):
@@ -71,7 +72,8 @@ class gb_run_stats(ctypes.Structure):
                 ("axpy_rows", ctypes.c_uint64), ("axpy_fma", ctypes.c_uint64),
                 ("ms_sp", ctypes.c_double), ("ms_reduce", ctypes.c_double), ("ms_rref", ctypes.c_double),
                 ("ms_update", ctypes.c_double), ("ms_pairs", ctypes.c_double),
-                ("ms_select", ctypes.c_double), ("ms_wall", ctypes.c_double)]
+                ("ms_select", ctypes.c_double), ("ms_wall", ctypes.c_double),
+                ("ms_reduce_kernel", ctypes.c_double), ("ms_finish", ctypes.c_double)]
 
 
 class gb_server_opts(ctypes.Structure):

@@ -14,6 +14,7 @@ void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint3
 void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *stats);
 void groebner_batch(const std::vector<gb_system *> &Ss);
 void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F);
+void make_resident(const std::vector<gb_system *> &Ss);
 std::vector<RowSpec> order_rows(const gb_system *S, std::vector<std::pair<Mono, uint32_t>> tk);
 
 static thread_local std::string t_last_error;
@@ -50,23 +51,30 @@ void opt_in_smem(const void *kernel) {
 
 // ---- page-locked staging of the batch in flight --------------------------------------------------
 
+// A bump allocator over one page-locked area: a region stays valid until the next ctx_sync, which
+// (after the stream has drained, so no copy still reads or writes the area) starts over at zero.
 void *ctx_pinned(gb_ctx *ctx, size_t bytes) {
-    if (bytes > ctx->stage_bytes) {
-        if (ctx->stage) {
-            ctx_sync(ctx);  // copies in flight may still use the old area
-            GB_CUDA(cudaFreeHost(ctx->stage));
+    const size_t need = (std::max<size_t>(bytes, 1) + 255) & ~size_t(255);
+    if (ctx->stage_off + need > ctx->stage_bytes) {
+        ctx_sync(ctx);
+        if (need > ctx->stage_bytes) {
+            if (ctx->stage) GB_CUDA(cudaFreeHost(ctx->stage));
             ctx->stage = nullptr;
+            ctx->stage_bytes = 0;
+            const size_t sz = std::max<size_t>({need, 2 * ctx->stage_bytes, size_t(8) << 20});
+            GB_CUDA(cudaHostAlloc(&ctx->stage, sz, cudaHostAllocDefault));
+            ctx->stage_bytes = sz;
         }
-        const size_t sz = std::max<size_t>({bytes, 2 * ctx->stage_bytes, size_t(4) << 20});
-        GB_CUDA(cudaHostAlloc(&ctx->stage, sz, cudaHostAllocDefault));
-        ctx->stage_bytes = sz;
     }
-    return ctx->stage;
+    void *p = static_cast<char *>(ctx->stage) + ctx->stage_off;
+    ctx->stage_off += need;
+    return p;
 }
 
 void ctx_sync(gb_ctx *ctx) {
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->arena.flush(ctx->stream);
+    ctx->stage_off = 0;
 }
 
 void Stage::upload(gb_ctx *ctx, DBuf<char> &d) {
@@ -74,7 +82,6 @@ void Stage::upload(gb_ctx *ctx, DBuf<char> &d) {
     char *hp = static_cast<char *>(ctx_pinned(ctx, h.size() + 16));
     std::memcpy(hp, h.data(), h.size());
     GB_CUDA(cudaMemcpyAsync(d.p, hp, h.size(), cudaMemcpyHostToDevice, ctx->stream));
-    ctx_sync(ctx);
 }
 
 // ---- arena ------------------------------------------------------------------------------------
@@ -270,7 +277,7 @@ gb_status gb_system_create(gb_ctx *ctx, uint32_t nvars, uint32_t p, gb_order ord
     if (order != GB_GREVLEX) fail(GB_EUNSUPPORTED, "only grevlex is implemented");
     if (F && F->npolys && (!F->poly_off || ((!F->exps || !F->coeffs) && F->poly_off[F->npolys])))
         fail(GB_EINVAL, "null arrays in the input system");
-    Enter entered(ctx);
+    // host work only: the input reaches the device with the system's first step
     auto S = std::make_unique<gb_system>();
     S->ctx = ctx;
     S->stream = ctx->stream;
@@ -283,16 +290,17 @@ gb_status gb_system_create(gb_ctx *ctx, uint32_t nvars, uint32_t p, gb_order ord
 gb_status gb_system_destroy(gb_system *S) {
     GB_API_BEGIN
     if (!S) return GB_EINVAL;
-    Enter entered(S->ctx);
-    cudaStreamSynchronize(S->stream);
-    S->last_ech.reset();
-    S->last_mac.reset();
-    S->bmon.reset();
-    S->bcf.reset();
-    S->boff.reset();
-    S->blen.reset();
-    S->ctx->arena.flush(S->stream);
+    // The system's device blocks go to the arena's deferred list (no work that is still queued uses
+    // them: a system is destroyed only when no step of it runs).  They are reclaimed at the
+    // context's next synchronisation; done here at once unless another thread is using the
+    // context, so a destroy never waits for a server's iteration.
+    gb_ctx *ctx = S->ctx;
     delete S;
+    std::unique_lock<std::recursive_mutex> lk(ctx->mu, std::try_to_lock);
+    if (lk.owns_lock()) {
+        GB_CUDA(cudaSetDevice(ctx->device));
+        ctx_sync(ctx);
+    }
     return GB_OK;
     GB_API_END
 }
@@ -303,6 +311,7 @@ gb_status gb_symbolic_preprocess(gb_system *S, uint32_t r, const uint8_t *t_exps
     if (!S || !out || (r && (!t_exps || !k))) fail(GB_EINVAL, "null argument");
     *out = nullptr;
     Enter entered(S->ctx);
+    make_resident({S});
     std::vector<std::pair<Mono, uint32_t>> tk(r);
     for (uint32_t i = 0; i < r; ++i) {
         Mono t{};
@@ -435,6 +444,7 @@ gb_status gb_basis_export(const gb_system *S, int reduced, gb_polys_host *h) {
     }
     gb_system *Sm = const_cast<gb_system *>(S);
     Enter entered(S->ctx);
+    make_resident({Sm});
     const uint32_t ng = (uint32_t)S->lm.size();
     uint64_t T = 0;
     for (uint32_t l : S->len) T += l;

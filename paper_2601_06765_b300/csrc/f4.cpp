@@ -381,36 +381,12 @@ void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F) {
         cfs.push_back(std::move(cf));
     }
     if (total >= (1ull << 32)) fail(GB_EUNSUPPORTED, "input above 2^32 terms");
-    // the whole input in one upload: terms, coefficients, offsets, lengths
     const uint32_t ng = (uint32_t)mons.size();
-    if (ng) {
-        gb_ctx *ctx = S->ctx;
-        Arena &ar = ctx->arena;
-        cudaStream_t st = S->stream;
-        S->bmon.alloc(ar, std::max<uint64_t>(total, 1024), st);
-        S->bcf.alloc(ar, std::max<uint64_t>(total, 1024), st);
-        S->boff.alloc(ar, std::max<uint32_t>(ng, 64), st);
-        S->blen.alloc(ar, std::max<uint32_t>(ng, 64), st);
-        Stage sg;
-        std::vector<uint4> m4;
-        std::vector<uint32_t> c4, o4, l4;
-        m4.reserve(total);
-        c4.reserve(total);
-        for (uint32_t g = 0; g < ng; ++g) {
-            o4.push_back((uint32_t)m4.size());
-            l4.push_back((uint32_t)mons[g].size());
-            for (const Mono &m : mons[g]) m4.push_back(to_u4(m));
-            c4.insert(c4.end(), cfs[g].begin(), cfs[g].end());
-        }
-        const size_t om = sg.put(m4.data(), 16ull * total), oc = sg.put(c4.data(), 4ull * total);
-        const size_t oo = sg.put(o4.data(), 4ull * ng), ol = sg.put(l4.data(), 4ull * ng);
-        DBuf<char> d;
-        sg.upload(ctx, d);
-        GB_CUDA(cudaMemcpyAsync(S->bmon.p, d.p + om, 16ull * total, cudaMemcpyDeviceToDevice, st));
-        GB_CUDA(cudaMemcpyAsync(S->bcf.p, d.p + oc, 4ull * total, cudaMemcpyDeviceToDevice, st));
-        GB_CUDA(cudaMemcpyAsync(S->boff.p, d.p + oo, 4ull * ng, cudaMemcpyDeviceToDevice, st));
-        GB_CUDA(cudaMemcpyAsync(S->blen.p, d.p + ol, 4ull * ng, cudaMemcpyDeviceToDevice, st));
-        ctx_sync(ctx);  // the staging block goes back to the arena
+    S->in_mon.reserve(total);
+    S->in_cf.reserve(total);
+    for (uint32_t g = 0; g < ng; ++g) {
+        for (const Mono &m : mons[g]) S->in_mon.push_back(to_u4(m));
+        S->in_cf.insert(S->in_cf.end(), cfs[g].begin(), cfs[g].end());
     }
     for (uint32_t g = 0; g < ng; ++g) append_host_poly(S, mons[g][0], (uint32_t)mons[g].size());
     // footprint estimate for admission control: the basis plus a few dense step matrices
@@ -422,6 +398,50 @@ void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F) {
         return r;
     }();
     S->footprint = (size_t)(64ull << 20) + (size_t)(terms * 20 * 64) + (size_t)(N * N / 4);
+}
+
+// the inputs of systems not yet on the device, in one staged copy: terms, coefficients, offsets
+// and lengths (no step has run yet, so the host mirrors off / len describe exactly the input)
+void make_resident(const std::vector<gb_system *> &Ss) {
+    std::vector<gb_system *> todo;
+    for (gb_system *S : Ss)
+        if (!S->resident) todo.push_back(S);
+    if (todo.empty()) return;
+    gb_ctx *ctx = todo[0]->ctx;
+    Arena &ar = ctx->arena;
+    cudaStream_t st = ctx->stream;
+    Stage sg;
+    struct At { size_t m, c, o, l; };
+    std::vector<At> at(todo.size());
+    for (size_t j = 0; j < todo.size(); ++j) {
+        gb_system *S = todo[j];
+        const uint64_t T = S->nterms;
+        const size_t ng = S->off.size();
+        S->bmon.alloc(ar, std::max<uint64_t>(T, 1024), st);
+        S->bcf.alloc(ar, std::max<uint64_t>(T, 1024), st);
+        S->boff.alloc(ar, std::max<size_t>(ng, 64), st);
+        S->blen.alloc(ar, std::max<size_t>(ng, 64), st);
+        at[j] = At{sg.put(S->in_mon.data(), 16ull * T), sg.put(S->in_cf.data(), 4ull * T),
+                   sg.put(S->off.data(), 4ull * ng), sg.put(S->len.data(), 4ull * ng)};
+    }
+    DBuf<char> d;
+    sg.upload(ctx, d);
+    for (size_t j = 0; j < todo.size(); ++j) {
+        gb_system *S = todo[j];
+        const uint64_t T = S->nterms;
+        const size_t ng = S->off.size();
+        if (T) {
+            GB_CUDA(cudaMemcpyAsync(S->bmon.p, d.p + at[j].m, 16ull * T, cudaMemcpyDeviceToDevice, st));
+            GB_CUDA(cudaMemcpyAsync(S->bcf.p, d.p + at[j].c, 4ull * T, cudaMemcpyDeviceToDevice, st));
+        }
+        if (ng) {
+            GB_CUDA(cudaMemcpyAsync(S->boff.p, d.p + at[j].o, 4ull * ng, cudaMemcpyDeviceToDevice, st));
+            GB_CUDA(cudaMemcpyAsync(S->blen.p, d.p + at[j].l, 4ull * ng, cudaMemcpyDeviceToDevice, st));
+        }
+        S->resident = true;
+        std::vector<uint4>().swap(S->in_mon);
+        std::vector<uint32_t>().swap(S->in_cf);
+    }
 }
 
 // ---- lockstep F4 steps of many systems ------------------------------------------------------------
@@ -444,6 +464,7 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
     if (!nj) return;
     gb_ctx *ctx = Ss[0]->ctx;
     const auto t0 = Clock::now();
+    make_resident(Ss);
     std::vector<SpTask> tasks(nj);
     std::vector<uint32_t> dmin(nj, UINT32_MAX), npairs(nj, 0);
     parallel_for(ctx, nj, [&](size_t j) {
@@ -511,6 +532,7 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
         st.ms_sp = mac->ms_sp;
         st.ms_reduce = ech->ms_reduce;
         st.ms_rref = ech->ms_rref;
+        st.ms_reduce_kernel = ech->ms_reduce_kernel;
         st.ms_update = (float)ms_between(t1, tp);
         st.ms_pairs = (float)ms_between(tp, t2);
         st.ms_select = (float)ms_between(t0, ts);
@@ -522,6 +544,7 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
         S->run.ms_sp += st.ms_sp;
         S->run.ms_reduce += st.ms_reduce;
         S->run.ms_rref += st.ms_rref;
+        S->run.ms_reduce_kernel += st.ms_reduce_kernel;
         S->run.ms_update += st.ms_update;
         S->run.ms_pairs += st.ms_pairs;
         S->run.ms_select += st.ms_select;
@@ -541,6 +564,7 @@ void finish_batch(const std::vector<gb_system *> &Ss) {
     if (!nj) return;
     gb_ctx *ctx = Ss[0]->ctx;
     const auto t0 = Clock::now();
+    make_resident(Ss);
     // minimalisation: an element goes when another one's leading monomial divides its own (the
     // older one staying on equality); the rest in leading-monomial order, descending
     std::vector<std::vector<uint32_t>> keep(nj);
@@ -548,12 +572,15 @@ void finish_batch(const std::vector<gb_system *> &Ss) {
         gb_system *S = Ss[j];
         const int n = (int)S->n;
         const uint32_t ng = (uint32_t)S->lm.size();
-        for (uint32_t i = 0; i < ng; ++i) {
-            if (S->redundant[i]) continue;
+        std::vector<uint32_t> live;
+        for (uint32_t i = 0; i < ng; ++i)
+            if (!S->redundant[i]) live.push_back(i);
+        for (uint32_t i : live) {
             bool drop = false;
-            for (uint32_t g = 0; g < ng && !drop; ++g) {
-                if (g == i || S->redundant[g]) continue;
-                if (mono_divides(S->lm[g], S->lm[i], n) && (!(S->lm[g] == S->lm[i]) || g < i)) drop = true;
+            for (uint32_t g : live) {
+                if (g == i) continue;
+                const bool div = S->swar ? divides16(S->lm16[g], S->lm16[i]) : mono_divides(S->lm[g], S->lm[i], n);
+                if (div && (!(S->lm[g] == S->lm[i]) || g < i)) { drop = true; break; }
             }
             if (!drop) keep[j].push_back(i);
         }
@@ -595,6 +622,7 @@ void finish_batch(const std::vector<gb_system *> &Ss) {
             gb_system *S = owners[k];
             S->run.ms_sp += Ms[k]->ms_sp;
             S->run.ms_reduce += Ep[k]->ms_reduce;
+            S->run.ms_reduce_kernel += Ep[k]->ms_reduce_kernel;
             S->run.nnz_total += Ms[k]->nnz;
             S->run.axpy_rows += Ep[k]->work[0];
             S->run.axpy_fma += Ep[k]->work[1];
@@ -606,6 +634,7 @@ void finish_batch(const std::vector<gb_system *> &Ss) {
         S->finished = true;
         S->run.nbasis = (uint32_t)keep[j].size();
         S->run.ms_wall += ms;
+        S->run.ms_finish += ms;
     }
 }
 

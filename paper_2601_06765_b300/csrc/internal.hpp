@@ -200,6 +200,7 @@ struct gb_ctx {
     cudaEvent_t ev[8] = {};         // stage timing of the batch in flight
     void *stage = nullptr;          // page-locked staging of the batch in flight
     size_t stage_bytes = 0;
+    size_t stage_off = 0;           // bump offset, back to 0 at every ctx_sync
     // host worker threads for per-system host control of a batch (pair updates, selection)
     std::unique_ptr<gb::HostPool> pool;
     // held by every call that queues work on the stream or uses the staging area, so that a
@@ -235,7 +236,7 @@ struct gb_echelon {
     gb::DBuf<uint32_t> rref;    // rank x nb, rows in pivot order
     gb::DBuf<uint32_t> rpiv;    // rank pivot positions (ascending)
     uint64_t work[2] = {0, 0};  // pivot-row applications, mod-p multiply-adds of the reduction
-    float ms_reduce = 0.f, ms_rref = 0.f;
+    float ms_reduce = 0.f, ms_rref = 0.f, ms_reduce_kernel = 0.f;
 };
 
 struct gb_system {
@@ -255,6 +256,10 @@ struct gb_system {
     gb::DBuf<uint32_t> bcf;
     gb::DBuf<uint32_t> boff, blen;
     uint64_t nterms = 0;
+    // the normalised input until its upload with the first step (SWAR monomials, coefficients)
+    bool resident = false;
+    std::vector<uint4> in_mon;
+    std::vector<uint32_t> in_cf;
     // kept objects of the last step (GB_CTX_KEEP_STEP)
     std::unique_ptr<gb_macaulay> last_mac;
     std::unique_ptr<gb_echelon> last_ech;
@@ -282,7 +287,8 @@ struct Stage {
         if (bytes && src) std::memcpy(h.data() + at, src, bytes);
         return at;
     }
-    void upload(gb_ctx *ctx, DBuf<char> &d);  // synchronises: the pinned area is reused next
+    // stream-ordered copy into a new device block d (no synchronisation)
+    void upload(gb_ctx *ctx, DBuf<char> &d);
 };
 
 // prefix table of per-job block counts appended to a stage; returns the total
@@ -310,7 +316,8 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
 void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector<Mono>> &lms);
 // final reduction: element elems[j][i] of job j becomes LM + row i of its D' (writes fin_*)
 void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::vector<uint32_t>> &elems);
-void *ctx_pinned(gb_ctx *ctx, size_t bytes);  // the context's page-locked staging area
+// a region of the context's page-locked staging area, valid until the next ctx_sync
+void *ctx_pinned(gb_ctx *ctx, size_t bytes);
 void ctx_sync(gb_ctx *ctx);                     // synchronise the stream, release deferred blocks
 // run fn(i) for i in [0, n) on the context's host workers and the calling thread
 void parallel_for(gb_ctx *ctx, size_t n, const std::function<void(size_t)> &fn);

@@ -610,6 +610,7 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             k_build_chunk_tri<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
             counted();
         }
+        GB_CUDA(cudaEventRecord(ctx->ev[5], st));
         size_t gi = 1;
         for (auto &g : groups) {
             const int md = g.first.first, cls = g.first.second;
@@ -674,7 +675,6 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
                 int *hl = static_cast<int *>(ctx_pinned(ctx, 4ull * (l.size() + 1)));
                 std::memcpy(hl, l.data(), 4 * l.size());
                 GB_CUDA(cudaMemcpyAsync(lists.p, hl, 4 * l.size(), cudaMemcpyHostToDevice, st));
-                ctx_sync(ctx);
             }
             size_t pan_bytes = 0;
             for (int j : smem_jobs) pan_bytes = std::max<size_t>(pan_bytes, 4ull * KP * X[j].nb);
@@ -742,14 +742,16 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
     uint64_t *hw = static_cast<uint64_t *>(ctx_pinned(ctx, 16ull * nj));
     GB_CUDA(cudaMemcpyAsync(hw, work.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
     ctx_sync(ctx);
-    float ms_red = 0.f, ms_rref = 0.f;
+    float ms_red = 0.f, ms_rref = 0.f, ms_kern = 0.f;
     GB_CUDA(cudaEventElapsedTime(&ms_red, ctx->ev[2], ctx->ev[3]));
+    GB_CUDA(cudaEventElapsedTime(&ms_kern, ctx->ev[5], ctx->ev[3]));
     GB_CUDA(cudaEventElapsedTime(&ms_rref, ctx->ev[3], ctx->ev[4]));
     for (int j = 0; j < nj; ++j) {
         Es[j]->work[0] = hw[2 * j];
         Es[j]->work[1] = hw[2 * j + 1];
         Es[j]->ms_reduce = ms_red;
         Es[j]->ms_rref = ms_rref;
+        Es[j]->ms_reduce_kernel = ms_kern;
     }
     return Es;
 }
@@ -848,7 +850,6 @@ void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector
     G.build(ctx, J, {rows});
     k_write_rows<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
     counted();
-    ctx_sync(ctx);
 }
 
 void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::vector<uint32_t>> &elems) {
