@@ -143,6 +143,8 @@ gb_status gb_ctx_create(int device, const gb_ctx_opts *opts, gb_ctx **out);
 gb_status gb_ctx_destroy(gb_ctx *ctx);
 /* Device bytes currently allocated from the context's arena, and its size. */
 gb_status gb_ctx_memory(const gb_ctx *ctx, size_t *used, size_t *capacity);
+/* High-water mark of the arena's allocated bytes; reset != 0 restarts it at the current use. */
+gb_status gb_ctx_memory_peak(gb_ctx *ctx, size_t *peak, int reset);
 
 /* ---- systems -------------------------------------------------------------------------------- */
 
@@ -198,8 +200,12 @@ gb_status gb_system_last_step(const gb_system *sys, const gb_macaulay **mac,
 
 /* ---- batching and serving ------------------------------------------------------------------- */
 
-/* Run gb_groebner on `count` independent systems of one context, overlapping their device work
-   (each system on its own stream, host control on worker threads).  per_system may be NULL. */
+/* Run gb_groebner on `count` independent systems of one context in lockstep: each iteration takes
+   one F4 step of every system with pairs left (each pipeline kernel is launched once for all of
+   their matrices) and builds the reduced basis of every system without pairs; per-system host
+   control runs on the context's worker threads.  The results are those of gb_groebner on each
+   system alone.  A failing iteration fails the whole call (the systems are left unusable).
+   per_system may be NULL. */
 gb_status gb_batch_groebner(gb_ctx *ctx, uint32_t count, gb_system *const *systems,
                             gb_run_stats *per_system);
 
@@ -209,15 +215,30 @@ typedef struct {
     uint32_t reserved;
 } gb_server_opts;
 
-/* A continuous-batching server: submitted systems are admitted into free slots while their
-   estimated device footprint fits under the cap; each runs gb_groebner on its own stream while
-   others run.  Ownership of a submitted system moves to the server until it is returned by poll. */
+/* A continuous-batching server: one scheduler thread runs lockstep iterations (as in
+   gb_batch_groebner) over the admitted systems, and between iterations admits queued systems into
+   free slots while their summed device footprint estimate fits under the cap.  A submitted system
+   thus joins the next iteration and a finished one leaves at once.  Ownership of a submitted
+   system moves to the server until it is returned by poll.  An iteration that fails finishes all
+   of its systems with its error status. */
 gb_status gb_server_create(gb_ctx *ctx, const gb_server_opts *opts, gb_server **out);
 gb_status gb_server_submit(gb_server *srv, gb_system *sys, uint64_t *ticket);
 /* GB_OK and *done = the system when finished (ownership returns to the caller, with its status in
    *result); GB_EBUSY while it is queued or running. */
 gb_status gb_server_poll(gb_server *srv, uint64_t ticket, gb_system **done, gb_status *result);
 gb_status gb_server_destroy(gb_server *srv);
+
+typedef struct {
+    uint64_t iterations;    /* lockstep iterations run */
+    uint64_t system_steps;  /* sum over iterations of the systems in the iteration */
+    uint64_t admitted, finished;
+    double busy_ms;         /* wall time inside iterations */
+    uint32_t max_running;   /* most systems in one iteration */
+    uint32_t queued;        /* systems waiting for admission now */
+} gb_server_stats;
+
+/* Counters of the server since its creation. */
+gb_status gb_server_stats_get(gb_server *srv, gb_server_stats *out);
 
 /* ---- sparse reduction without device allocation --------------------------------------------- */
 

@@ -76,6 +76,12 @@ class gb_run_stats(ctypes.Structure):
                 ("ms_reduce_kernel", ctypes.c_double), ("ms_finish", ctypes.c_double)]
 
 
+class gb_server_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_uint64), ("system_steps", ctypes.c_uint64),
+                ("admitted", ctypes.c_uint64), ("finished", ctypes.c_uint64), ("busy_ms", ctypes.c_double),
+                ("max_running", ctypes.c_uint32), ("queued", ctypes.c_uint32)]
+
+
 class gb_server_opts(ctypes.Structure):
     _fields_ = [("hbm_cap_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
@@ -97,6 +103,7 @@ _SIGS = {
     "gb_ctx_create": [ctypes.c_int, ctypes.POINTER(gb_ctx_opts), ctypes.POINTER(_vp)],
     "gb_ctx_destroy": [_vp],
     "gb_ctx_memory": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
+    "gb_ctx_memory_peak": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.c_int],
     "gb_system_create": [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(gb_polys),
                          ctypes.POINTER(_vp)],
     "gb_system_destroy": [_vp],
@@ -116,6 +123,7 @@ _SIGS = {
     "gb_server_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)],
     "gb_server_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)],
     "gb_server_destroy": [_vp],
+    "gb_server_stats_get": [_vp, ctypes.POINTER(gb_server_stats)],
     "gb_reduce_rows_noalloc": [ctypes.c_uint32] * 5 + [_vp] * 7,
 }
 
@@ -331,6 +339,12 @@ def gb_server_poll(srv: int, ticket: int) -> tuple[int | None, int]:
     return d.value, r.value
 
 
+def gb_server_stats_get(srv: int) -> dict:
+    st = gb_server_stats()
+    check(lib().gb_server_stats_get(srv, ctypes.byref(st)), "gb_server_stats_get")
+    return _struct_dict(st)
+
+
 def gb_server_destroy(srv: int) -> None:
     check(lib().gb_server_destroy(srv), "gb_server_destroy")
 
@@ -369,6 +383,11 @@ class Context:
         u, c = ctypes.c_size_t(), ctypes.c_size_t()
         check(lib().gb_ctx_memory(self.h, ctypes.byref(u), ctypes.byref(c)), "gb_ctx_memory")
         return u.value, c.value
+
+    def memory_peak(self, reset: bool = False) -> int:
+        pk = ctypes.c_size_t()
+        check(lib().gb_ctx_memory_peak(self.h, ctypes.byref(pk), int(reset)), "gb_ctx_memory_peak")
+        return pk.value
 
     def close(self):
         if self.h:

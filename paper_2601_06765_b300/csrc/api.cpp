@@ -118,6 +118,7 @@ void *Arena::alloc(size_t bytes) {
         if (sz > need) free_[off + need] = sz - need;
         live_[off] = need;
         used_ += need;
+        peak_ = std::max(peak_, used_);
         return base_ + off;
     }
     char msg[160];
@@ -266,6 +267,13 @@ gb_status gb_ctx_memory(const gb_ctx *ctx, size_t *used, size_t *capacity) {
     if (!ctx) return GB_EINVAL;
     if (used) *used = ctx->arena.used();
     if (capacity) *capacity = ctx->arena.capacity();
+    return GB_OK;
+}
+
+gb_status gb_ctx_memory_peak(gb_ctx *ctx, size_t *peak, int reset) {
+    if (!ctx || !peak) return GB_EINVAL;
+    *peak = ctx->arena.peak();
+    if (reset) ctx->arena.reset_peak();
     return GB_OK;
 }
 

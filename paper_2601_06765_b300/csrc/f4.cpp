@@ -11,6 +11,7 @@
 //   one's leading monomial divides its own, the older one staying on equality), tails fully
 //   reduced, sorted by leading monomial descending.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <numeric>
@@ -225,22 +226,68 @@ static void gm_update(gb_system *S, uint32_t h) {
     C.reserve(h);
     for (uint32_t g = 0; g < h; ++g)
         if (!S->redundant[g]) C.push_back(g);
-    std::vector<M16> L(C.size());
-    for (size_t a = 0; a < C.size(); ++a) L[a] = lcm_of(h, C[a]);
-    // pairs (h, g), oldest g first: keep one when its leading monomials are coprime, or when no
-    // pair still waiting or already kept has an lcm dividing its lcm
-    std::vector<char> kept(C.size(), 0), cop(C.size(), 0);
-    for (size_t a = 0; a < C.size(); ++a) {
+    const size_t c = C.size();
+    std::vector<M16> L(c);
+    std::vector<uint32_t> Ld(c);
+    std::vector<char> kept(c, 0), cop(c, 0), dom(c, 0);
+    for (size_t a = 0; a < c; ++a) {
+        L[a] = lcm_of(h, C[a]);
+        Ld[a] = deg16(L[a]);
         cop[a] = coprime(C[a]);
-        bool keep = true;
-        if (!cop[a]) {
-            for (size_t b = a + 1; b < C.size() && keep; ++b)
-                if (divides(L[b], L[a])) keep = false;
-            for (size_t b = 0; b < a && keep; ++b)
-                if (kept[b] && divides(L[b], L[a])) keep = false;
-        }
-        kept[a] = keep;
     }
+    // The new pairs (h, g) are taken oldest g first: one is kept when its leading monomials are
+    // coprime, or when no pair still waiting and no pair already kept has an lcm dividing its lcm.
+    // That sequential rule has a closed form (by induction over the order, following a chain of
+    // divisors down to a minimal lcm): a non-coprime pair is kept iff no new pair's lcm strictly
+    // divides its lcm, no later pair has the same lcm, and no coprime pair has the same lcm.  A
+    // strict divisor has lower degree, and when there is one, one of the minimal lcms of lower
+    // degree divides too; so the pairs are visited by degree against the minimal lcms found so far.
+    std::vector<uint32_t> ord(c);
+    std::iota(ord.begin(), ord.end(), 0u);
+    std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return Ld[x] < Ld[y]; });
+    std::vector<M16> mins;
+    for (size_t s0 = 0; s0 < c;) {
+        size_t e = s0;
+        while (e < c && Ld[ord[e]] == Ld[ord[s0]]) ++e;
+        for (size_t q = s0; q < e; ++q)
+            for (const M16 &m : mins)
+                if (divides(m, L[ord[q]])) {
+                    dom[ord[q]] = 1;
+                    break;
+                }
+        for (size_t q = s0; q < e; ++q) {
+            if (dom[ord[q]]) continue;
+            bool have = false;
+            for (size_t t = mins.size(); t-- > 0 && Ld[ord[q]] == deg16(mins[t]);)
+                if (mins[t] == L[ord[q]]) {
+                    have = true;
+                    break;
+                }
+            if (!have) mins.push_back(L[ord[q]]);
+        }
+        s0 = e;
+    }
+    // equal lcms among the undominated pairs: sort by lcm, then index
+    std::vector<uint32_t> und;
+    for (uint32_t a = 0; a < c; ++a)
+        if (!dom[a]) und.push_back(a);
+    std::sort(und.begin(), und.end(), [&](uint32_t x, uint32_t y) {
+        if (L[x].hi != L[y].hi) return L[x].hi < L[y].hi;
+        if (L[x].lo != L[y].lo) return L[x].lo < L[y].lo;
+        return x < y;
+    });
+    for (size_t s0 = 0; s0 < und.size();) {
+        size_t e = s0;
+        bool anycop = false;
+        while (e < und.size() && L[und[e]] == L[und[s0]]) anycop = anycop || cop[und[e++]];
+        for (size_t q = s0; q < e; ++q) {
+            const uint32_t a = und[q];
+            kept[a] = cop[a] || (q + 1 == e && !anycop);
+        }
+        s0 = e;
+    }
+    for (uint32_t a = 0; a < c; ++a)
+        if (cop[a]) kept[a] = 1;
     // old pairs whose lcm LM(h) divides, with both lcm(g1, h) and lcm(g2, h) different, go
     size_t w = 0;
     for (size_t q = 0; q < S->pairs.size(); ++q) {
@@ -389,15 +436,16 @@ void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F) {
         S->in_cf.insert(S->in_cf.end(), cfs[g].begin(), cfs[g].end());
     }
     for (uint32_t g = 0; g < ng; ++g) append_host_poly(S, mons[g][0], (uint32_t)mons[g].size());
-    // footprint estimate for admission control: the basis plus a few dense step matrices
-    uint64_t terms = 0;
-    for (uint32_t l : S->len) terms += l;
-    const uint64_t N = [&] {
-        uint64_t r = 1;
-        for (uint32_t i = 1; i <= nvars; ++i) r = r * (nvars + 2 + i) / i;  // C(n + 3, n)
-        return r;
-    }();
-    S->footprint = (size_t)(64ull << 20) + (size_t)(terms * 20 * 64) + (size_t)(N * N / 4);
+    // Device footprint estimate for admission control.  The peak arena use of a whole run grows
+    // geometrically with n, faster for higher input degree: measured high-water marks of systems
+    // run alone (n = 5..11, degree 2 and 3, 10-66 terms per polynomial) follow
+    // log2(peak / MiB) ~ 1.7 (d - 1) n - 8.5 - 3.5 (d - 1) for input degree d, within a factor
+    // of about 1.5.  The estimate is twice that, plus 8 MiB.
+    uint32_t dmax = 1;
+    for (const Mono &m : S->lm) dmax = std::max<uint32_t>(dmax, (uint32_t)mono_deg(m, n));
+    const double d1 = (double)std::max<uint32_t>(dmax, 2) - 1.0;
+    const double log2_mib = std::min(40.0, 1.7 * d1 * nvars - 8.5 - 3.5 * d1);
+    S->footprint = (size_t)((8.0 + 2.0 * std::exp2(log2_mib)) * 1048576.0);
 }
 
 // the inputs of systems not yet on the device, in one staged copy: terms, coefficients, offsets

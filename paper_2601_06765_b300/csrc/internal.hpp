@@ -58,11 +58,16 @@ class Arena {
     void flush(cudaStream_t s);  // s has been synchronised: its deferred blocks are free again
     size_t used() const { return used_; }
     size_t capacity() const { return cap_; }
+    size_t peak() const { return peak_; }
+    void reset_peak() {
+        std::lock_guard<std::mutex> g(mu_);
+        peak_ = used_;
+    }
 
   private:
     void free_locked(size_t off);
     char *base_ = nullptr;
-    size_t cap_ = 0, used_ = 0;
+    size_t cap_ = 0, used_ = 0, peak_ = 0;
     bool owned_ = false;
     std::map<size_t, size_t> free_;  // offset -> size
     std::map<size_t, size_t> live_;  // offset -> size

@@ -27,12 +27,14 @@ inline unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t
 //
 // The pivot columns are taken in chunks of CW = 32 consecutive pivots (pivot rows k..k+31, one
 // contiguous CSR segment).  For a non-pivot row v the multipliers of a chunk are the solution of a
-// 32 x 32 unit upper-triangular system: f_i = v[c_i] - sum_{j<i} f_j U[j][i], where U[j][i] is the
-// entry of pivot row j at pivot column c_i.  Warp 0 solves it with shuffles from a shared copy of
-// U (prefetched by the other warps while the previous chunk's system is solved); then every warp
-// applies v <- v - sum_i f_i (pivot row i) to the row's accumulator with shared-memory atomics
-// (each pivot row's own leading entry included, which leaves v[c_i] = 0).  Two block barriers per
-// 32 pivot columns instead of one per column.
+// 32 x 32 unit upper-triangular system f U = v_c, i.e. f_i = v[c_i] - sum_{j<i} f_j U[j][i], where
+// U[j][i] is the entry of pivot row j at pivot column c_i.  U^{-1} is computed once per chunk
+// (k_invert_chunk_tri), so the solve is the product f = v_c U^{-1}: every lane forms one
+// multiplier from 32 independent products instead of a 32-step dependent chain.  Warp 0 does it
+// from a shared copy of U^{-1} (prefetched by the other warps during the previous chunk); then
+// every warp applies v <- v - sum_i f_i (pivot row i) to the row's accumulator with shared-memory
+// atomics (each pivot row's own leading entry included, which leaves v[c_i] = 0).  Two block
+// barriers per 32 pivot columns instead of one per column.
 //
 // Accumulators are lazy (Rem. 8.1), in one of three modes:
 //   A32: p < 2^16, each product (p - f) v < 2^32 is Barrett-reduced to [0, p) and added to a 32-bit
@@ -84,15 +86,56 @@ __global__ void k_build_chunk_tri(const RedJob *__restrict__ jobs, const uint32_
     }
 }
 
+// U^{-1} of every chunk triangle, in place (warp per chunk, IW per block).  With W = U^{-1} (unit
+// upper triangular): W[j][i] = -sum_{k=j}^{i-1} W[j][k] U[k][i] for j < i, a column at a time.
+// Stored row-major with W[i][i] = 1 and zeros below the diagonal; in Montgomery form (W R mod p)
+// when p >= 2^16, so that k_reduce can add redc(v W') terms, each below 2p, in 64 bits.
+constexpr int IW = 4;
+constexpr int TS = CW + 1;  // padded shared-memory row stride
+__global__ void __launch_bounds__(IW * 32) k_invert_chunk_tri(const RedJob *__restrict__ jobs,
+                                                             const uint32_t *__restrict__ bstart, int nj) {
+    __shared__ uint32_t Us[IW][CW * TS], Ws[IW][CW * TS];
+    const int jb = job_of_block(bstart, nj);
+    const RedJob &J = jobs[jb];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t chunk = (blockIdx.x - bstart[jb]) * IW + warp;
+    if (chunk >= (J.nA + CW - 1) / CW) return;  // whole warp leaves together
+    const Fp fp = J.fp;
+    uint32_t *Ug = J.U + (size_t)chunk * CW * CW;
+    uint32_t *U = Us[warp], *W = Ws[warp];
+    for (int r = 0; r < CW; ++r) {
+        U[r * TS + lane] = Ug[r * CW + lane];
+        W[r * TS + lane] = r == lane ? 1u : 0u;
+    }
+    __syncwarp();
+    for (int i = 1; i < CW; ++i) {
+        if (lane < i) {
+            uint32_t acc = 0;
+            for (int k = lane; k < i; ++k) {
+                const uint32_t u = U[k * TS + i];
+                if (u) acc = fp_add(acc, fp_mul(W[lane * TS + k], u, fp), fp);
+            }
+            W[lane * TS + i] = acc ? fp.p - acc : 0u;
+        }
+        __syncwarp();
+    }
+    for (int r = 0; r < CW; ++r) {
+        const uint32_t w = W[r * TS + lane];
+        Ug[r * CW + lane] = fp.small ? w : fp_to_mont(w, fp);
+    }
+}
+
 // block per non-pivot row of some job
 template <int MODE, bool SMEM>
-__global__ void __launch_bounds__(RT) k_reduce(const RedJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+__global__ void __launch_bounds__(RT, 6) k_reduce(const RedJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     using Acc = typename AccOf<MODE>::type;
     constexpr bool SMALLP = MODE != M64;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint32_t fsh[CW];
     __shared__ uint32_t Us[2][CW * CW];
-    __shared__ uint32_t rp[CW + 1];
+    // the chunk's pivot rows with a non-zero multiplier, as segments of its CSR range: first entry,
+    // multiplier (Montgomery form for p >= 2^16) and the exclusive prefix of the segment lengths
+    __shared__ uint32_t seg_q[CW], seg_m[CW], seg_pre[CW + 1];
+    __shared__ uint32_t s_nseg;
     const int jb = job_of_block(bstart, nj);
     const RedJob &J = jobs[jb];
     const Fp fp = J.fp;
@@ -119,21 +162,48 @@ __global__ void __launch_bounds__(RT) k_reduce(const RedJob *__restrict__ jobs, 
         const uint32_t cnt = min((uint32_t)CW, J.nA - kc);
         __syncthreads();  // the previous chunk's updates (and this chunk's U) are visible
         if (warp == 0) {
-            // phase A: the chunk's multipliers
+            // phase A: the chunk's multipliers f = v_c U^{-1}.  Lanes past cnt hold v = 0, and a
+            // pivot column left of base has v = 0 as do all columns before it, so its f is 0.
             uint32_t x = 0;
             if ((uint32_t)lane < cnt) {
                 const uint32_t c = J.pcols[kc + lane];
                 if (c >= base) x = MODE == A32 ? fp_reduce32((uint32_t)acc[c - base], fp) : fp_reduce(acc[c - base], fp);
             }
-            const uint32_t *Uc = Us[buf];
-            for (uint32_t t = 0; t + 1 < cnt; ++t) {
-                const uint32_t ft = __shfl_sync(0xffffffffu, x, t);
-                if (ft && (uint32_t)lane > t && (uint32_t)lane < cnt) {
-                    const uint32_t u = Uc[t * CW + lane];
-                    if (u) x = fp_sub(x, SMALLP ? fp_reduce32(ft * u, fp) : fp_mul(ft, u, fp), fp);
-                }
+            const uint32_t *Wc = Us[buf];
+            unsigned long long s = 0;  // < 32 * 2^32 (p < 2^16) or < 32 * 2p (Montgomery terms)
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+                const uint32_t vj = __shfl_sync(0xffffffffu, x, j);
+                const uint32_t w = Wc[j * CW + lane];
+                if (SMALLP) s += (unsigned long long)(vj * w);
+                else s += fp_redc((uint64_t)vj * w, fp);
             }
-            fsh[lane] = (uint32_t)lane < cnt ? x : 0u;
+            const uint32_t f = (uint32_t)lane < cnt ? fp_reduce(s, fp) : 0u;
+            const unsigned nzmask = __ballot_sync(0xffffffffu, f != 0u);
+            uint32_t q0 = 0, len = 0;
+            if (f) {
+                q0 = J.row_ptr[kc + lane];
+                len = J.row_ptr[kc + lane + 1] - q0;
+            }
+            uint32_t end = len;  // inclusive prefix of the lengths over the lanes
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, end, d);
+                if (lane >= d) end += y;
+            }
+            if (f) {
+                const uint32_t pos = __popc(nzmask & ((1u << lane) - 1u));
+                seg_q[pos] = q0;
+                seg_m[pos] = SMALLP ? fp.p - f : fp_to_mont(fp.p - f, fp);
+                seg_pre[pos + 1] = end;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, end, 31);
+            if (lane == 0) {
+                seg_pre[0] = 0;
+                s_nseg = __popc(nzmask);
+                applied += __popc(nzmask);
+                fmas += total;
+            }
         } else {
             // the other warps prefetch the next chunk's triangle
             const uint32_t kn = kc + CW;
@@ -141,35 +211,56 @@ __global__ void __launch_bounds__(RT) k_reduce(const RedJob *__restrict__ jobs, 
                 for (uint32_t t = threadIdx.x - 32u; t < CW * CW; t += RT - 32u)
                     Us[buf ^ 1][t] = J.U[(size_t)(kn / CW) * CW * CW + t];
         }
-        if (threadIdx.x <= cnt) rp[threadIdx.x] = J.row_ptr[kc + threadIdx.x];
         __syncthreads();
-        // phase B: warp w applies pivot rows w, w + 8, ... of the chunk
-        for (uint32_t t = warp; t < cnt; t += RT / 32) {
-            const uint32_t f = fsh[t];
-            if (!f) continue;
-            const uint32_t m = SMALLP ? fp.p - f : fp_to_mont(fp.p - f, fp);
-            const uint32_t a = rp[t], b = rp[t + 1];
-            if (lane == 0) {
-                ++applied;
-                fmas += b - a;
+        // phase B: the segments' entries, flattened, split evenly over the warps (a multiple of 32
+        // entries each), four entries per lane in flight.  A lane finds the segment of its first
+        // entry by binary search and then only moves forward; the current segment's end, CSR offset
+        // and multiplier stay in registers, so the common case costs one compare.
+        const uint32_t nseg = s_nseg, total = seg_pre[nseg];
+        const uint32_t per = (total + RT - 1) / RT * 32;
+        const uint32_t w0 = min(warp * per, total), w1 = min(w0 + per, total);
+        uint32_t sg = 0, send = 0, soff = 0, smul = 0;
+        if (w0 + lane < w1) {
+            uint32_t lo = 0, hi = nseg - 1;  // last segment starting at or before w0 + lane
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (seg_pre[mid] <= w0 + lane) lo = mid; else hi = mid - 1;
             }
-            for (uint32_t q = a + lane; q < b; q += 64) {  // two entries per lane in flight
-                const bool two = q + 32 < b;
-                const uint32_t c0 = J.col[q] - base, v0 = J.val[q];
-                const uint32_t c1 = two ? J.col[q + 32] - base : 0u, v1 = two ? J.val[q + 32] : 0u;
-                if (MODE == A32) {
-                    atomicAdd(reinterpret_cast<uint32_t *>(acc + c0), fp_reduce32(m * v0, fp));
-                    if (two) atomicAdd(reinterpret_cast<uint32_t *>(acc + c1), fp_reduce32(m * v1, fp));
-                } else if (MODE == A64) {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(acc + c0), (unsigned long long)(m * v0));
-                    if (two) atomicAdd(reinterpret_cast<unsigned long long *>(acc + c1), (unsigned long long)(m * v1));
-                } else {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(acc + c0),
-                              (unsigned long long)fp_redc((uint64_t)m * v0, fp));
-                    if (two)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(acc + c1),
-                                  (unsigned long long)fp_redc((uint64_t)m * v1, fp));
+            sg = lo;
+            send = seg_pre[sg + 1];
+            soff = seg_q[sg] - seg_pre[sg];
+            smul = seg_m[sg];
+        }
+        for (uint32_t x0 = w0; x0 < w1; x0 += 4 * 32) {
+            uint32_t cc[4], vv[4], mm[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t x = x0 + 32u * u + lane;
+                cc[u] = 0xFFFFFFFFu;
+                vv[u] = mm[u] = 0u;
+                if (x < w1) {
+                    while (x >= send) {  // stops below nseg: x < seg_pre[nseg]
+                        ++sg;
+                        send = seg_pre[sg + 1];
+                        soff = seg_q[sg] - seg_pre[sg];
+                        smul = seg_m[sg];
+                    }
+                    cc[u] = J.col[soff + x];
+                    vv[u] = J.val[soff + x];
+                    mm[u] = smul;
                 }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (cc[u] == 0xFFFFFFFFu) continue;
+                Acc *dst = acc + (cc[u] - base);
+                if (MODE == A32)
+                    atomicAdd(reinterpret_cast<uint32_t *>(dst), fp_reduce32(mm[u] * vv[u], fp));
+                else if (MODE == A64)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)(mm[u] * vv[u]));
+                else
+                    atomicAdd(reinterpret_cast<unsigned long long *>(dst),
+                              (unsigned long long)fp_redc((uint64_t)mm[u] * vv[u], fp));
             }
         }
     }
@@ -596,9 +687,12 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         groups[{mode[j], cls}].push_back(j);
     }
     {
-        std::vector<uint32_t> tri(nj);
-        for (int j = 0; j < nj; ++j) tri[j] = blocks(R[j].nA, 8);
-        std::vector<std::vector<uint32_t>> per{tri};
+        std::vector<uint32_t> tri(nj), inv(nj);
+        for (int j = 0; j < nj; ++j) {
+            tri[j] = blocks(R[j].nA, 8);
+            inv[j] = blocks(((size_t)R[j].nA + CW - 1) / CW, IW);
+        }
+        std::vector<std::vector<uint32_t>> per{tri, inv};
         for (auto &g : groups) {
             std::vector<uint32_t> rows(nj, 0);
             for (int j : g.second) rows[j] = R[j].nC;
@@ -608,10 +702,11 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         G.build(ctx, R, per);
         if (G.totals[0]) {
             k_build_chunk_tri<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
-            counted();
+            k_invert_chunk_tri<<<G.totals[1], IW * 32, 0, st>>>(G.jobs, G.plans[1], nj);
+            counted(2);
         }
         GB_CUDA(cudaEventRecord(ctx->ev[5], st));
-        size_t gi = 1;
+        size_t gi = 2;
         for (auto &g : groups) {
             const int md = g.first.first, cls = g.first.second;
             const bool smem = cls >= 0;
@@ -954,7 +1049,7 @@ constexpr uint32_t NA_COLPOS = 0;
 constexpr uint32_t NA_TRI = GB_NOALLOC_MAX_DICT;
 constexpr uint32_t NA_WORK = NA_TRI + GB_NOALLOC_MAX_PIVOTS * CW;  // even: 8-byte aligned
 constexpr uint32_t NA_TABLE = NA_WORK + 4;                           // 16-byte aligned
-constexpr uint32_t NA_WORDS = NA_TABLE + (uint32_t)((sizeof(RedJob) + 15) / 4) + 4;
+constexpr uint32_t NA_WORDS = NA_TABLE + (uint32_t)((sizeof(RedJob) + 15) / 4) + 8;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
 
 namespace {
@@ -1000,10 +1095,11 @@ void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint3
     // the one-job table: job, then the two block-start tables {0, blocks}
     struct Table {
         RedJob job;
-        uint32_t tri_start[2], red_start[2];
+        uint32_t tri_start[2], inv_start[2], red_start[2];
     } tb{};
     tb.job = RedJob{row_ptr, col, val, pcols, colpos, nonpiv, tri, dprime, nullptr, work, nA, nC, N, nb, fp};
     tb.tri_start[1] = blocks(nA, 8);
+    tb.inv_start[1] = blocks(nchunks, IW);
     tb.red_start[1] = nC;
     static_assert(sizeof(Table) <= 4 * (NA_WORDS - NA_TABLE), "scratch too small for the job table");
     Table *dtb = reinterpret_cast<Table *>(scr + NA_TABLE);
@@ -1012,7 +1108,8 @@ void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint3
         k_mark_pivot_cols<<<blocks(nA, 256), 256, 0, st>>>(nA, pcols, colpos);
         counted();
         k_build_chunk_tri<<<tb.tri_start[1], 256, 0, st>>>(&dtb->job, dtb->tri_start, 1);
-        counted();
+        k_invert_chunk_tri<<<tb.inv_start[1], IW * 32, 0, st>>>(&dtb->job, dtb->inv_start, 1);
+        counted(2);
     }
     const size_t smem = (size_t)N * (mode == A32 ? 4 : 8);
     if (mode == A32) {

@@ -8,6 +8,7 @@
 // cap, so a request that arrives joins the very next iteration and one that finishes leaves at
 // once (iteration-level continuous batching).
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <unordered_map>
 
@@ -31,6 +32,7 @@ struct gb_server {
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread scheduler;
+    gb_server_stats stats{};
 };
 
 namespace {
@@ -49,6 +51,7 @@ void admit(gb_server *srv, std::vector<Running> &run, size_t &bytes) {
         run.push_back(Running{srv->queue.front().first, S});
         bytes += S->footprint;
         srv->queue.pop_front();
+        srv->stats.admitted++;
     }
 }
 
@@ -68,6 +71,7 @@ void scheduler_loop(gb_server *srv) {
         std::vector<gb_system *> Ss;
         for (auto &r : run) Ss.push_back(r.sys);
         gb_status st = GB_OK;
+        const auto t0 = std::chrono::steady_clock::now();
         try {
             std::lock_guard<std::recursive_mutex> g(srv->ctx->mu);
             GB_CUDA(cudaSetDevice(srv->ctx->device));
@@ -83,12 +87,18 @@ void scheduler_loop(gb_server *srv) {
         }
         // a failed iteration leaves its systems in an undefined state: all of them finish with the
         // error (the pipeline runs them together, so the failing one is not singled out)
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stats.iterations++;
+        srv->stats.system_steps += Ss.size();
+        srv->stats.busy_ms += ms;
+        srv->stats.max_running = std::max<uint32_t>(srv->stats.max_running, (uint32_t)Ss.size());
         size_t w = 0;
         for (auto &r : run) {
             if (st != GB_OK || r.sys->finished) {
                 srv->done[r.ticket] = {r.sys, st};
                 bytes -= r.sys->footprint;
+                srv->stats.finished++;
             } else {
                 run[w++] = r;
             }
@@ -175,6 +185,14 @@ gb_status gb_server_poll(gb_server *srv, uint64_t ticket, gb_system **done, gb_s
     if (result) *result = it->second.second;
     srv->done.erase(it);
     srv->known.erase(ticket);
+    return GB_OK;
+}
+
+gb_status gb_server_stats_get(gb_server *srv, gb_server_stats *out) {
+    if (!srv || !out) return GB_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *out = srv->stats;
+    out->queued = (uint32_t)srv->queue.size();
     return GB_OK;
 }
 
