@@ -240,6 +240,25 @@ typedef struct {
 /* Counters of the server since its creation. */
 gb_status gb_server_stats_get(gb_server *srv, gb_server_stats *out);
 
+/* ---- dense update over F_p on the tensor cores ------------------------------------------------ */
+
+/* C <- C - A B (subtract != 0) or C <- C + A B (subtract == 0), mod p, exactly: the GEMM-like
+   block update of the panel-structured elimination (Sec. 9.2), with the modular multiply-add of
+   Sec. 8 taken out of the inner loop.  The product runs on the tensor cores: each residue is split
+   into balanced base-256 digits (two for p < 2^16, four for p < 2^31), the digit products are
+   accumulated in FP32 (exact: every partial sum is an integer below 2^24 in magnitude) and the
+   digit sums are recombined mod p.
+   All matrix pointers are DEVICE pointers on the context's device, row-major with the given row
+   pitches (in elements): A is m x k, B is k x n, C is m x n; entries in [0, p).  A and B are
+   read, C is updated in place.  The work runs on the context's stream and the call returns when
+   it is done.  Scratch (the digit planes) comes from the context's arena.
+   GB_EINVAL: null handle or pointer, p not an odd prime below 2^31, a pitch below the width.
+   GB_ENOMEM: the arena cannot hold the digit planes (2 (m + n) k digits of 2 bytes, times 2 for
+   p >= 2^16).  GB_ETIMEOUT: a bounded device wait gave up. */
+gb_status gb_matmul_modp(gb_ctx *ctx, uint32_t p, uint32_t m, uint32_t n, uint32_t k, const uint32_t *A,
+                         uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
+                         int subtract);
+
 /* ---- sparse reduction without device allocation --------------------------------------------- */
 
 /* Limits of gb_reduce_rows_noalloc: its scratch is a fixed array compiled into the library. */

@@ -125,6 +125,8 @@ _SIGS = {
     "gb_server_destroy": [_vp],
     "gb_server_stats_get": [_vp, ctypes.POINTER(gb_server_stats)],
     "gb_reduce_rows_noalloc": [ctypes.c_uint32] * 5 + [_vp] * 7,
+    "gb_matmul_modp": [_vp] + [ctypes.c_uint32] * 4 + [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp,
+                                                       ctypes.c_uint64, ctypes.c_int],
 }
 
 
@@ -357,6 +359,14 @@ def gb_reduce_rows_noalloc(p: int, ndict: int, npivot: int, nnonpivot: int, nb: 
     check(lib().gb_reduce_rows_noalloc(p, ndict, npivot, nnonpivot, nb, row_ptr, col_ind, val,
                                        pivot_cols, nonpivot_cols, dprime, stream or None),
           "gb_reduce_rows_noalloc")
+
+
+def gb_matmul_modp(ctx: int, p: int, m: int, n: int, k: int, A: int, lda: int, B: int, ldb: int, C: int,
+                   ldc: int, subtract: bool = True) -> None:
+    """C <- C -/+ A B mod p on the tensor cores; A, B, C are integer device addresses of row-major
+    u32 matrices (m x k, k x n, m x n) with the given row pitches.  See include/gb.h."""
+    check(lib().gb_matmul_modp(ctx, p, m, n, k, A, lda, B, ldb, C, ldc, 1 if subtract else 0),
+          "gb_matmul_modp")
 
 
 # ---- convenience wrappers -----------------------------------------------------------------------

@@ -495,6 +495,40 @@ gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, ui
     GB_API_END
 }
 
+gb_status gb_matmul_modp(gb_ctx *ctx, uint32_t p, uint32_t m, uint32_t n, uint32_t k, const uint32_t *A,
+                         uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
+                         int subtract) {
+    GB_API_BEGIN
+    if (!ctx) fail(GB_EINVAL, "null context");
+    if (p < 3 || p >= (1u << 31) || !is_prime32(p)) fail(GB_EINVAL, "p must be an odd prime below 2^31");
+    if (!m || !n) return GB_OK;
+    if (!C || (k && (!A || !B))) fail(GB_EINVAL, "null device pointer");
+    if (lda < k || ldb < n || ldc < n) fail(GB_EINVAL, "row pitch below the matrix width");
+    if (!k) return GB_OK;
+    Enter entered(ctx);
+    Arena &ar = ctx->arena;
+    cudaStream_t st = ctx->stream;
+    const Fp fp = make_fp(p);
+    const uint32_t L = digits_for(p);
+    DigitPlanes DA, DB;
+    DA.alloc(ar, L, m, k, st);
+    DB.alloc(ar, L, n, k, st);
+    to_digits(A, lda, 1, DA, p, st);
+    to_digits(B, 1, ldb, DB, p, st);  // B^T: row j holds column j of B
+    DBuf<uint32_t> err;
+    err.alloc(ar, 1, st);
+    GB_CUDA(cudaMemsetAsync(err.p, 0, 4, st));
+    const uint32_t kmax = mm_kmax(p);
+    for (uint32_t k0 = 0; k0 < k; k0 += kmax)
+        mm_update(DA, k0, 0, DB, k0, 0, m, n, std::min(kmax, k - k0), C, ldc, fp, subtract != 0, err.p, st);
+    uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16));
+    GB_CUDA(cudaMemcpyAsync(h, err.p, 4, cudaMemcpyDeviceToHost, st));
+    ctx_sync(ctx);
+    if (*h) fail(GB_ETIMEOUT, "gb_matmul_modp: a bounded wait in the tensor-core kernel gave up");
+    return GB_OK;
+    GB_API_END
+}
+
 gb_status gb_system_last_step(const gb_system *S, const gb_macaulay **mac, const gb_echelon **ech) {
     if (!S) return GB_EINVAL;
     if (!S->last_mac || !S->last_ech) {

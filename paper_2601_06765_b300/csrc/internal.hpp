@@ -328,4 +328,24 @@ void ctx_sync(gb_ctx *ctx);                     // synchronise the stream, relea
 void parallel_for(gb_ctx *ctx, size_t n, const std::function<void(size_t)> &fn);
 // exclusive scan of n u32 values on the stream; out has n + 1 entries (out[n] = total)
 void exclusive_scan(Arena &ar, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t s);
+
+// ---- exact dense update over F_p on the tensor cores (mm.cu) --------------------------------
+// Digit planes of a matrix: [L][rows][kpad] BF16 bit patterns of the balanced base-256 digits of
+// its residues (L = 2 for p < 2^16, 4 for p < 2^31), K-major: row r holds the K values of one
+// row of A, or of one column of B (B^T).
+struct DigitPlanes {
+    uint32_t L = 0;
+    uint64_t rows = 0, K = 0, kpad = 0;
+    uint16_t *p = nullptr;
+    DBuf<uint16_t> buf;
+    void alloc(Arena &ar, uint32_t L, uint64_t rows, uint64_t K, cudaStream_t st);
+};
+uint32_t digits_for(uint32_t p);
+uint32_t mm_kmax(uint32_t p);  // longest K one exact tensor-core accumulation covers
+// digit planes of the R x K matrix whose element (r, k) is src[r * rs + k * ks]
+void to_digits(const uint32_t *src, uint64_t rs, uint64_t ks, const DigitPlanes &D, uint32_t p, cudaStream_t st);
+// C[M x N] <- C -/+ A B mod p over K <= mm_kmax(p) (see mm.cu); err collects device error flags
+void mm_update(const DigitPlanes &A, uint32_t ax, uint32_t ay, const DigitPlanes &B, uint32_t bx, uint32_t by,
+               uint32_t M, uint32_t N, uint32_t K, uint32_t *C, uint64_t ldc, const Fp &fp, bool sub,
+               uint32_t *err, cudaStream_t st);
 }  // namespace gb
