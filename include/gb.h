@@ -65,11 +65,17 @@ typedef struct {
     size_t arena_bytes;  /* size of `arena`; when arena is NULL, bytes the context allocates
                             with cudaMalloc at creation (0: 2 GiB) */
     uint32_t flags;      /* GB_CTX_KEEP_STEP: keep the last F4 step's matrix and echelon form
-                            of each system for gb_system_last_step (costs memory) */
+                            of each system for gb_system_last_step (costs memory);
+                            GB_CTX_REDUCE_SPARSE / GB_CTX_REDUCE_DENSE: reduce every matrix
+                            row by row (sparse), or by dense blocked elimination on the tensor
+                            cores whenever the arena has room; neither: chosen per matrix by
+                            its shape.  Both give the same (unique) D'. */
     uint32_t reserved;
 } gb_ctx_opts;
 
 #define GB_CTX_KEEP_STEP 1u
+#define GB_CTX_REDUCE_SPARSE 2u
+#define GB_CTX_REDUCE_DENSE 4u
 
 /* A polynomial system on the host: polynomial i has the terms [poly_off[i], poly_off[i+1]). */
 typedef struct {

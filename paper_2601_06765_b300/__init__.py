@@ -24,6 +24,8 @@ GB_OK, GB_DONE = 0, 1
 STATUS = {0: "GB_OK", 1: "GB_DONE", -1: "GB_EINVAL", -2: "GB_ENOMEM", -3: "GB_EOVERFLOW",
           -4: "GB_ETIMEOUT", -5: "GB_EDEVICE", -6: "GB_EUNSUPPORTED", -7: "GB_EBUSY"}
 GB_CTX_KEEP_STEP = 1
+GB_CTX_REDUCE_SPARSE = 2
+GB_CTX_REDUCE_DENSE = 4
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -379,15 +381,17 @@ def basis_terms(off: np.ndarray, ex: np.ndarray, cf: np.ndarray) -> list[list[tu
 class Context:
     """A library context whose device arena is a torch tensor on `device`."""
 
-    def __init__(self, device: int = 0, arena_bytes: int = 2 << 30, keep_step: bool = False):
+    def __init__(self, device: int = 0, arena_bytes: int = 2 << 30, keep_step: bool = False,
+                 reduce: str = "auto"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: this library has no CPU path")
         self.device = device
         self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=f"cuda:{device}")
         torch.cuda.synchronize(device)
-        self.h = gb_ctx_create(device, None, self.arena.data_ptr(), arena_bytes,
-                               GB_CTX_KEEP_STEP if keep_step else 0)
+        flags = (GB_CTX_KEEP_STEP if keep_step else 0) | {"auto": 0, "sparse": GB_CTX_REDUCE_SPARSE,
+                                                            "dense": GB_CTX_REDUCE_DENSE}[reduce]
+        self.h = gb_ctx_create(device, None, self.arena.data_ptr(), arena_bytes, flags)
 
     def memory(self) -> tuple[int, int]:
         u, c = ctypes.c_size_t(), ctypes.c_size_t()

@@ -1,0 +1,211 @@
+// dense.cu -- the reduction of the non-pivot rows by the pivot rows (the PSGE trailing update of
+// Sec. 9.2) as dense blocked elimination on the tensor cores, for steps whose non-pivot rows fill
+// in.
+//
+// Columns are renumbered q(c): the pivot columns first in pivot order (pivot row i has leading
+// column q = i), zero columns up to nAp = nA rounded up to 64, then the non-pivot columns in
+// order.  With W the pivot rows (nA x N', unit upper triangular on its first nA columns) and M the
+// non-pivot rows (nC x N'), the reduction is
+//     F W[:, :nA] = M[:, :nA],    D' = M[:, nAp:] - F W[:, nAp:],
+// and F is found block by block (right-looking, blocks of BS pivots):
+//     F_J = M[:, J] U_J^{-1}                  (U_J = W[J, J], CUDA cores: k_trsm_block)
+//     M[:, j1:] <- M[:, j1:] - F_J W[J, j1:]  (tensor cores: mm_update)
+// D' is unique (the pivot rows have distinct leading columns), so this schedule gives the same
+// bits as the row-by-row sparse reduction.  BS = 512 / L (L digits per residue) is the longest K
+// one exact tensor-core accumulation covers.
+//
+// Inside a block, the solve runs 32 pivots at a time with the 32 x 32 inverses of the chunk
+// triangles that the sparse path also uses (Montgomery form for p >= 2^16): a warp owns one row,
+// lane j holds the row's entries at columns j, j + 32, ... of the block; the chunk's multipliers
+// are f = v_c U_c^{-1} (32 independent products per lane), then the later chunks of the block are
+// updated with the rows of U_J held densely in Ub.
+#include "internal.hpp"
+
+namespace gb {
+
+namespace {
+
+constexpr int DW = 4;  // warps (rows) per block of the row kernels
+
+__device__ __forceinline__ uint32_t qcol(uint32_t cp, uint32_t nAp) {
+    return (cp & 0x80000000u) ? (cp & 0x7FFFFFFFu) : nAp + cp;
+}
+
+// balanced base-256 digits of a residue x as BF16 bits, digit l at dst[l * plane]
+template <int L>
+__device__ __forceinline__ void put_digits(uint32_t x, uint32_t p, uint16_t *dst, uint64_t plane) {
+    const uint32_t T = L == 2 ? 32639u : 2139062143u;  // 127 (1 + 256 + ... + 256^{L-1})
+    int v = x <= T ? (int)x : (int)(x - p);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const int a = l + 1 < L ? (int)(((uint32_t)v & 0xFFu) ^ 0x80u) - 0x80 : v;
+        if (l + 1 < L) v = (v - a) >> 8;
+        dst[(size_t)l * plane] = (uint16_t)(__float_as_uint((float)a) >> 16);
+    }
+}
+
+// pivot row i: entries right of its block go to the digit planes of W^T (row q, K index i), the
+// entries inside its own block (right of the diagonal) to the dense block Ub
+template <int L>
+__global__ void k_scatter_pivots(DenseJob J) {
+    const uint32_t i = blockIdx.x * DW + (threadIdx.x >> 5);
+    if (i >= J.nA) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t j0 = i / J.bs * J.bs, j1 = min(j0 + J.bs, J.nAp);
+    const uint64_t plane = (uint64_t)J.Np * J.wkpad;
+    uint32_t *ub = J.Ub + (size_t)(i / J.bs) * J.bs * J.bs + (size_t)(i - j0) * J.bs;
+    for (uint32_t e = J.row_ptr[i] + lane; e < J.row_ptr[i + 1]; e += 32) {
+        const uint32_t q = qcol(J.colpos[J.col[e]], J.nAp), v = J.val[e];
+        if (q >= j1) put_digits<L>(v, J.fp.p, J.WT + (size_t)q * J.wkpad + i, plane);
+        else if (q > i) ub[q - j0] = v;
+    }
+}
+
+// non-pivot row r into the dense M
+__global__ void k_scatter_rows(DenseJob J) {
+    const uint32_t r = blockIdx.x * DW + (threadIdx.x >> 5);
+    if (r >= J.nC) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t *row = J.M + (size_t)r * J.ldm;
+    for (uint32_t e = J.row_ptr[J.nA + r] + lane; e < J.row_ptr[J.nA + r + 1]; e += 32)
+        row[qcol(J.colpos[J.col[e]], J.nAp)] = J.val[e];
+}
+
+// F_J = M[:, j0:j0+jn] U_J^{-1}, written as digit planes (row r, K index k) -- warp per row
+template <int L>
+__global__ void __launch_bounds__(DW * 32) k_trsm_block(DenseJob J, uint32_t j0) {
+    constexpr int NS = 512 / L / 32;  // 32-pivot chunks per block
+    constexpr bool SMALLP = L == 2;
+    const uint32_t r = blockIdx.x * DW + (threadIdx.x >> 5);
+    if (r >= J.nC) return;
+    const int lane = threadIdx.x & 31;
+    const Fp fp = J.fp;
+    const uint32_t jn = min(J.bs, J.nA - j0);  // pivots of the block (the rest is padding)
+    const uint32_t *row = J.M + (size_t)r * J.ldm + j0;
+    const uint32_t *Ub = J.Ub + (size_t)(j0 / J.bs) * J.bs * J.bs;
+    const uint32_t *Winv = J.Uinv + (size_t)(j0 / 32) * 32 * 32;
+    const uint64_t fplane = (uint64_t)J.nC * J.fkpad;
+    uint16_t *frow = J.F + (size_t)r * J.fkpad;
+    uint32_t v[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+        const uint32_t k = 32u * t + lane;
+        v[t] = k < jn ? row[k] : 0u;
+    }
+#pragma unroll
+    for (int c = 0; c < NS; ++c) {
+        if (32u * c >= jn) break;  // uniform across the warp
+        // multipliers of chunk c: f_lane = sum_j v_c[j] W[j][lane]
+        const uint32_t x = v[c];
+        const uint32_t *W = Winv + (size_t)c * 32 * 32;
+        unsigned long long s = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t xj = __shfl_sync(0xffffffffu, x, j);
+            const uint32_t w = W[j * 32 + lane];
+            if (SMALLP) s += (unsigned long long)(xj * w);
+            else s += fp_redc((uint64_t)xj * w, fp);
+        }
+        const uint32_t k = 32u * c + lane;
+        const uint32_t f = k < jn ? fp_reduce(s, fp) : 0u;
+        if (k < jn) put_digits<L>(f, fp.p, frow + k, fplane);
+        const uint32_t fm = f ? (SMALLP ? fp.p - f : fp_to_mont(fp.p - f, fp)) : 0u;
+        // later chunks of the block: v_t <- v_t - f U[chunk c rows][chunk t columns]; each
+        // multiplier is broadcast once and feeds every later chunk (independent accumulators)
+        unsigned long long a[NS];
+#pragma unroll
+        for (int t = 0; t < NS; ++t) a[t] = v[t];
+        const uint32_t *U = Ub + (size_t)(32 * c) * J.bs + lane;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+            const uint32_t fi = __shfl_sync(0xffffffffu, fm, i);
+            const uint32_t *Ui = U + (size_t)i * J.bs;
+#pragma unroll
+            for (int t = c + 1; t < NS; ++t) {
+                const uint32_t u = Ui[32 * t];
+                if (SMALLP) a[t] += (unsigned long long)(fi * u);
+                else a[t] += fp_redc((uint64_t)fi * u, fp);
+            }
+        }
+#pragma unroll
+        for (int t = c + 1; t < NS; ++t) v[t] = fp_reduce(a[t], fp);
+    }
+}
+
+__global__ void k_dense_work(DenseJob J, unsigned long long macs) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        J.work[0] += J.nA;
+        J.work[1] += macs;
+    }
+}
+
+inline unsigned blocks_of(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// The dense schedule pays once the non-pivot rows are many enough to fill in and the pivot
+// block is wide enough for whole tensor-core blocks; below that the sparse row-by-row reduction,
+// whose work follows the nonzeros, is faster.
+bool dense_pays(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC) {
+    // measured on B300: dense wins from about 4k pivots and 1k non-pivot rows (31-bit p, where
+    // the sparse path's Montgomery updates run in 64 bits), and at any row count past 16k pivots
+    // (where the sparse path has too few rows to fill the GPU)
+    (void)N;
+    if (p < 65536u) return nA >= 8192 && nC >= 1024;
+    return nA >= 4096 && (nC >= 1024 || nA >= 16384);
+}
+
+size_t dense_bytes(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC) {
+    const uint64_t L = digits_for(p), bs = mm_kmax(p);
+    const uint64_t nAp = (nA + 63) / 64 * 64, Np = nAp + (N - nA), ldm = (Np + 3) / 4 * 4;
+    const uint64_t nblk = (nAp + bs - 1) / bs;
+    return 2 * L * Np * nAp + 4 * nC * ldm + 4 * nblk * bs * bs + 2 * L * nC * bs + 4096;
+}
+
+void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaStream_t st) {
+    const uint32_t L = digits_for(J.fp.p);
+    J.bs = mm_kmax(J.fp.p);
+    J.nAp = (J.nA + 63) / 64 * 64;
+    J.Np = J.nAp + J.nb;
+    J.ldm = (J.Np + 3) / 4 * 4;
+    const uint32_t nblk = (J.nAp + J.bs - 1) / J.bs;
+    DBuf<uint32_t> M, Ub;
+    DigitPlanes WT, F;
+    M.alloc(ar, (size_t)J.nC * J.ldm, st);
+    Ub.alloc(ar, (size_t)nblk * J.bs * J.bs, st);
+    WT.alloc(ar, L, J.Np, J.nAp, st);
+    F.alloc(ar, L, J.nC, J.bs, st);
+    GB_CUDA(cudaMemsetAsync(M.p, 0, M.bytes(), st));
+    GB_CUDA(cudaMemsetAsync(Ub.p, 0, Ub.bytes(), st));
+    GB_CUDA(cudaMemsetAsync(WT.p, 0, WT.buf.bytes(), st));
+    GB_CUDA(cudaMemsetAsync(F.p, 0, F.buf.bytes(), st));  // digits past a short last block stay finite
+    J.M = M.p;
+    J.Ub = Ub.p;
+    J.WT = WT.p;
+    J.wkpad = WT.kpad;
+    J.F = F.p;
+    J.fkpad = F.kpad;
+    if (L == 2) k_scatter_pivots<2><<<blocks_of(J.nA, DW), DW * 32, 0, st>>>(J);
+    else k_scatter_pivots<4><<<blocks_of(J.nA, DW), DW * 32, 0, st>>>(J);
+    k_scatter_rows<<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J);
+    counted(2);
+    unsigned long long macs = 0;
+    const MmPlan plan(F, WT, J.M, J.ldm, J.nC, J.Np, J.fp);
+    for (uint32_t b = 0; b < nblk; ++b) {
+        const uint32_t j0 = b * J.bs, j1 = std::min(j0 + J.bs, J.nAp);
+        if (L == 2) k_trsm_block<2><<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J, j0);
+        else k_trsm_block<4><<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J, j0);
+        counted();
+        // columns j1.. of M, K = the block's pivots (a multiple of 64: padding pivots are zero)
+        plan.update(0, 0, j0, j1, j1, 0, J.nC, J.Np - j1, j1 - j0, true, err, st);
+        macs += (unsigned long long)J.nC * (j1 - j0) * (J.Np - j1);
+    }
+    k_dense_work<<<1, 32, 0, st>>>(J, macs);
+    counted();
+    // D' = M[:, nAp:]
+    if (J.nb)
+        GB_CUDA(cudaMemcpy2DAsync(dprime, 4ull * J.nb, J.M + J.nAp, 4ull * J.ldm, 4ull * J.nb, J.nC,
+                                  cudaMemcpyDeviceToDevice, st));
+}
+
+}  // namespace gb

@@ -344,8 +344,44 @@ uint32_t digits_for(uint32_t p);
 uint32_t mm_kmax(uint32_t p);  // longest K one exact tensor-core accumulation covers
 // digit planes of the R x K matrix whose element (r, k) is src[r * rs + k * ks]
 void to_digits(const uint32_t *src, uint64_t rs, uint64_t ks, const DigitPlanes &D, uint32_t p, cudaStream_t st);
-// C[M x N] <- C -/+ A B mod p over K <= mm_kmax(p) (see mm.cu); err collects device error flags
-void mm_update(const DigitPlanes &A, uint32_t ax, uint32_t ay, const DigitPlanes &B, uint32_t bx, uint32_t by,
-               uint32_t M, uint32_t N, uint32_t K, uint32_t *C, uint64_t ldc, const Fp &fp, bool sub,
-               uint32_t *err, cudaStream_t st);
+// Updates C[cy + m][cx + n] <- C -/+ (A B)[m][n] mod p (m < M, n < N, K <= mm_kmax(p)) on the
+// tensor cores (mm.cu), with A and B^T given by digit planes and C (crows x ccols, row pitch ldc,
+// 16-byte aligned, ldc a multiple of 4) by TMA.  The tensor maps are encoded once per plan; each
+// update's region ends the C tensor on the right and bottom.  err collects device error flags.
+struct MmPlan {
+    MmPlan(const DigitPlanes &A, const DigitPlanes &B, uint32_t *C, uint64_t ldc, uint32_t crows, uint32_t ccols,
+           const Fp &fp);
+    ~MmPlan();
+    MmPlan(const MmPlan &) = delete;
+    MmPlan &operator=(const MmPlan &) = delete;
+    void update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t cx, uint32_t cy, uint32_t M, uint32_t N,
+                uint32_t K, bool sub, uint32_t *err, cudaStream_t st) const;
+    const DigitPlanes *A, *B;
+    uint32_t *C;
+    uint64_t ldc;
+    uint32_t rows, cols;
+    Fp fp;
+    struct Maps;
+    Maps *maps;
+};
+
+// ---- dense blocked reduction of the non-pivot rows (dense.cu) --------------------------------
+struct DenseJob {
+    const uint32_t *row_ptr, *col, *val, *colpos;  // CSR (pivot rows first) and column map
+    const uint32_t *Uinv;                          // 32 x 32 chunk-triangle inverses
+    uint32_t N, nA, nC, nb;
+    Fp fp;
+    unsigned long long *work;                      // [0] pivot rows, [1] dense multiply-adds
+    // set by reduce_dense: block size, pivots padded to 64, padded width, row pitches
+    uint32_t bs, nAp, Np;
+    uint64_t ldm, wkpad, fkpad;
+    uint32_t *M, *Ub;
+    uint16_t *WT, *F;
+};
+// whether the dense schedule is expected to beat the sparse one for a matrix of this shape
+bool dense_pays(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC);
+// device bytes reduce_dense takes from the arena for one matrix
+size_t dense_bytes(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC);
+// D' (nC x nb) of one matrix by dense blocked elimination (the chunk inverses must be ready)
+void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaStream_t st);
 }  // namespace gb

@@ -16,18 +16,22 @@
 // digit), which equals (A B)[m][n] mod p.  One launch covers K <= 512 / L; longer products are
 // split by the host into launches that each update C.
 //
-// Kernel (one 128 x 64 tile of C per CTA, 6 warps):
-//   warp 0, lane 0   TMA producer: digit planes of A (128 x 64 per digit) and B^T (64 x 64 per
-//                    digit) for each 64-wide K block into a ring of shared-memory stages
-//                    (128-byte swizzle), mbarrier with transaction count
+// Kernel: persistent, one CTA per SM, each CTA takes a contiguous run of the 128 x 32 output
+// tiles in row-major tile order.  10 warps:
+//   warp 0, lane 0   TMA producer: the digit planes of A for the CTA's current 128-row tile
+//                    (all of K, kept in shared memory while the row tile lasts), then per output
+//                    tile the digit planes of B^T (32 rows) and the C tile, double-buffered
+//                    (128-byte swizzle; mbarriers with transaction counts)
 //   warp 1           allocates the tensor memory; lane 0 issues tcgen05.mma (kind::f16, BF16
-//                    operands, FP32 accumulators, M = 128, N = 64, K = 16) for every digit pair
-//                    into the accumulator of its diagonal, and commits to the stage's "empty"
-//                    barrier and finally to the "accumulators full" barrier
-//   warps 2-5        epilogue: tcgen05.ld of the thread's row of every diagonal, exact
-//                    conversion, Horner mod p, read-modify-write of C
-// Every wait is bounded; a wait that gives up sets an error flag that the host turns into
-// GB_ETIMEOUT, and the CTA still releases its tensor memory.
+//                    operands, FP32 accumulators, M = 128, N = 32, K = 16) for every digit pair
+//                    into the accumulator of its diagonal, in one of two accumulator sets
+//   warps 2-9        epilogue (two warps per tensor-memory lane quarter, 16 columns each):
+//                    tcgen05.ld of the thread's row of every diagonal, exact conversion and
+//                    recombination mod p, read-modify-write of the C tile in shared memory, TMA
+//                    store of the tile
+// so the next tile's products run while the epilogue finishes the previous one.  Every wait is
+// bounded; a wait that gives up sets an error flag that the host turns into GB_ETIMEOUT, and
+// the CTA still releases its tensor memory.
 #include <cuda.h>
 
 #include <algorithm>
@@ -39,28 +43,33 @@ namespace gb {
 
 namespace {
 
-constexpr int MM_BM = 128, MM_BN = 64, MM_BK = 64;  // tile of C, K block (64 BF16 = 128 bytes)
-constexpr int MM_THREADS = 192;
+constexpr int MM_BM = 128, MM_BN = 32, MM_BK = 64;  // C tile, K block (64 BF16 = 128 bytes)
+constexpr int MM_EPI = 8;                          // epilogue warps: two per tensor-memory lane quarter
+constexpr int MM_THREADS = 32 * (2 + MM_EPI);
 constexpr uint32_t MM_SPIN = 1u << 22;               // bounded mbarrier waits
 
 template <int L>
 struct MmCfg {
-    static constexpr int DIAG = 2 * L - 1;                              // digit diagonals
-    static constexpr uint32_t A_TILE = MM_BM * MM_BK * 2;               // bytes per digit
-    static constexpr uint32_t B_TILE = MM_BN * MM_BK * 2;
-    static constexpr uint32_t STAGE = L * (A_TILE + B_TILE);
-    static constexpr int STAGES = L == 2 ? 4 : 2;
-    static constexpr uint32_t TMEM_COLS = DIAG * MM_BN <= 256 ? 256 : 512;
-    static constexpr uint32_t SMEM = STAGES * STAGE + 1024 + 256;       // + alignment + barriers
+    static constexpr int DIAG = 2 * L - 1;            // digit diagonals
+    static constexpr int KB = 512 / L / MM_BK;        // K blocks of the longest exact K
+    static constexpr uint32_t A_BLK = MM_BM * 128;    // bytes of one digit x K block of A
+    static constexpr uint32_t B_BLK = MM_BN * 128;
+    static constexpr uint32_t A_BYTES = L * KB * A_BLK;
+    static constexpr uint32_t B_BYTES = L * KB * B_BLK;
+    static constexpr uint32_t C_BYTES = MM_BM * MM_BN * 4;
+    static constexpr uint32_t SMEM_DATA = A_BYTES + 2 * (B_BYTES + C_BYTES);
+    static constexpr uint32_t SMEM = SMEM_DATA + 1024 + 256;  // + alignment + barriers
+    static constexpr uint32_t TMEM_COLS = 2 * DIAG * MM_BN <= 256 ? 256 : 512;
 };
 
 struct MmParams {
-    uint32_t M, N, K;       // C is M x N; the product runs over K
-    int ax, ay, bx, by;     // TMA coordinates of the first K block of A (k, m) and of B^T (k, n)
-    uint32_t *C;            // element (m, n) at C[m * ldc + n]
-    uint64_t ldc;
+    uint32_t M, N, K;       // the update covers C[cy + m][cx + n], m < M, n < N; K <= 512 / L
+    int ax, ay, bx, by;     // TMA coordinates of A (k, m) and of B^T (k, n) at the origin
+    int cx, cy;             // TMA coordinates of the update region in C
+    uint32_t ntn, items;    // tiles per tile row, tiles in all
     Fp fp;
-    uint64_t big;           // a multiple of p above 2^48, added before each Barrett reduction
+    uint64_t big;           // a multiple of p above 2^58, added before the Barrett reduction
+    uint32_t rd[7];         // 256^d mod p
     int sub;                // 1: C -= A B, 0: C += A B
     uint32_t *err;          // bit 0: a bounded wait gave up
 };
@@ -74,6 +83,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -98,6 +110,23 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
         : "memory");
 }
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * MM_EPI) : "memory"); }
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols) : "memory");
 }
@@ -133,46 +162,70 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle: rows of 128 bytes,
 // 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1, layout type 2.
 // The tile base is 1024-byte aligned; a K offset inside the 128-byte row moves the start address.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
+// Low word: start address >> 4 (bits 0-13), leading byte offset 16 >> 4 (bits 16-29); adding a
+// 16-byte-unit offset to it moves the start address (shared addresses stay below 2^18, so the
+// 14-bit field never carries).  High word: stride byte offset 1024 >> 4, version, swizzle mode.
+__device__ __forceinline__ uint32_t sdesc_lo(uint32_t addr) { return ((addr & 0x3FFFFu) >> 4) | (1u << 16); }
+constexpr uint32_t SDESC_HI = (1024u >> 4) | (1u << 14) | (2u << 29);
+__device__ __forceinline__ uint64_t sdesc_of(uint32_t lo) { return ((uint64_t)SDESC_HI << 32) | lo; }
 
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9,
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MM_BN >> 3) << 17) |
                            ((uint32_t)(MM_BM >> 4) << 24);
 
-// signed value (|x| < 2^62 - big) mod p
-__device__ __forceinline__ uint32_t mod_signed(long long x, const MmParams &P) {
-    return fp_reduce((uint64_t)(x + (long long)P.big), P.fp);
-}
+__device__ __forceinline__ int acc_int(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
 
 template <int L>
 __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CUtensorMap ta,
-                                                     const __grid_constant__ CUtensorMap tb, const MmParams P) {
+                                                     const __grid_constant__ CUtensorMap tb,
+                                                     const __grid_constant__ CUtensorMap tc, const MmParams P) {
     using Cfg = MmCfg<L>;
     extern __shared__ unsigned char mm_smem_raw[];
     const uint32_t raw = smem_u32(mm_smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;  // stage buffers, 1024-byte aligned
+    const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned
     unsigned char *gbase = mm_smem_raw + (base - raw);
-    const uint32_t bars = base + Cfg::STAGES * Cfg::STAGE;  // full[S], empty[S], accfull, tmem slot
-    auto full = [&](int s) { return bars + 8u * s; };
-    auto empty = [&](int s) { return bars + 8u * (Cfg::STAGES + s); };
-    const uint32_t accfull = bars + 8u * (2 * Cfg::STAGES);
-    const uint32_t tslot = accfull + 8u;
+    // layout: A | B[2] | C[2] | barriers
+    const uint32_t sA = base, sB = base + Cfg::A_BYTES, sC = sB + 2 * Cfg::B_BYTES;
+    const uint32_t bars = base + Cfg::SMEM_DATA;
+    const uint32_t a_full = bars, a_empty = bars + 8;
+    auto b_full = [&](int s) { return bars + 16 + 8u * s; };
+    auto b_empty = [&](int s) { return bars + 32 + 8u * s; };
+    auto c_full = [&](int s) { return bars + 48 + 8u * s; };
+    auto c_empty = [&](int s) { return bars + 64 + 8u * s; };
+    auto t_full = [&](int s) { return bars + 80 + 8u * s; };
+    auto t_empty = [&](int s) { return bars + 96 + 8u * s; };
+    const uint32_t tslot = bars + 112;
     uint32_t *tslot_g = reinterpret_cast<uint32_t *>(gbase + (tslot - base));
+    // set when a bounded wait gives up: from then on every wait returns at once and no new copy,
+    // product or store is issued, but every role still runs its whole loop, so the epilogue warps
+    // keep meeting at their named barrier and the CTA reaches its teardown
+    volatile uint32_t *abort_flag = reinterpret_cast<volatile uint32_t *>(gbase + (tslot + 4 - base));
+    auto wait = [&](uint32_t bar, uint32_t parity) -> bool {
+        if (*abort_flag) return false;
+        if (mbar_wait(bar, parity)) return true;
+        *abort_flag = 1u;
+        atomicOr(P.err, 1u);
+        return false;
+    };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t m0 = blockIdx.y * MM_BM, n0 = blockIdx.x * MM_BN;
+    const uint32_t w0 = (uint32_t)((unsigned long long)blockIdx.x * P.items / gridDim.x);
+    const uint32_t w1 = (uint32_t)((unsigned long long)(blockIdx.x + 1) * P.items / gridDim.x);
     const int nkb = (int)((P.K + MM_BK - 1) / MM_BK);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < Cfg::STAGES; ++s) {
-            mbar_init(full(s), 1);
-            mbar_init(empty(s), 1);
+        *abort_flag = 0u;
+        mbar_init(a_full, 1);
+        mbar_init(a_empty, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(b_full(s), 1);
+            mbar_init(b_empty(s), 1);
+            mbar_init(c_full(s), 1);
+            mbar_init(c_empty(s), 1);
+            mbar_init(t_full(s), 1);
+            mbar_init(t_empty(s), MM_EPI);  // one arrival per epilogue warp
         }
-        mbar_init(accfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -185,90 +238,154 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot_g);
 
     if (warp == 0 && lane == 0) {
-        // producer
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % Cfg::STAGES;
-            const uint32_t ph = (uint32_t)(kb / Cfg::STAGES) & 1u;
-            if (!mbar_wait(empty(s), ph ^ 1u)) {
-                atomicOr(P.err, 1u);
-                break;
+        // ---- producer
+        int arow = -1;
+        uint32_t a_loads = 0;
+        for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
+            const int mt = (int)(w / P.ntn), nt = (int)(w % P.ntn);
+            if (mt != arow) {
+                if (!a_loads || wait(a_empty, (a_loads - 1) & 1u)) {
+                    mbar_expect_tx(a_full, (uint32_t)(L * nkb) * Cfg::A_BLK);
+                    for (int l = 0; l < L; ++l)
+                        for (int kb = 0; kb < nkb; ++kb)
+                            tma_load_3d(sA + (uint32_t)(l * Cfg::KB + kb) * Cfg::A_BLK, &ta, a_full,
+                                        P.ax + kb * MM_BK, P.ay + mt * MM_BM, l);
+                }
+                ++a_loads;
+                arow = mt;
             }
-            const uint32_t st = base + s * Cfg::STAGE;
-            mbar_expect_tx(full(s), Cfg::STAGE);
-            for (int l = 0; l < L; ++l) {
-                tma_load_3d(st + l * Cfg::A_TILE, &ta, full(s), P.ax + kb * MM_BK, P.ay + (int)m0, l);
-                tma_load_3d(st + L * Cfg::A_TILE + l * Cfg::B_TILE, &tb, full(s), P.bx + kb * MM_BK, P.by + (int)n0, l);
+            const int s = (int)(it & 1u);
+            const uint32_t ph = (it >> 1) & 1u;
+            if (wait(b_empty(s), ph ^ 1u)) {
+                mbar_expect_tx(b_full(s), (uint32_t)(L * nkb) * Cfg::B_BLK);
+                for (int l = 0; l < L; ++l)
+                    for (int kb = 0; kb < nkb; ++kb)
+                        tma_load_3d(sB + s * Cfg::B_BYTES + (uint32_t)(l * Cfg::KB + kb) * Cfg::B_BLK, &tb, b_full(s),
+                                    P.bx + kb * MM_BK, P.by + nt * MM_BN, l);
+            }
+            if (wait(c_empty(s), ph ^ 1u)) {
+                mbar_expect_tx(c_full(s), Cfg::C_BYTES);
+                tma_load_2d(sC + s * Cfg::C_BYTES, &tc, c_full(s), P.cx + nt * MM_BN, P.cy + mt * MM_BM);
             }
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        uint32_t started = 0;  // diagonals written at least once
-        bool ok = true;
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int s = kb % Cfg::STAGES;
-            const uint32_t ph = (uint32_t)(kb / Cfg::STAGES) & 1u;
-            if (!mbar_wait(full(s), ph)) {
-                atomicOr(P.err, 1u);
-                ok = false;
-                break;
+    } else if (warp == 1) {
+        // ---- MMA issuer: the whole warp runs the loop (warp-uniform descriptors), lane 0 issues
+        int arow = -1;
+        uint32_t a_loads = 0;
+        const uint32_t a_lo = sdesc_lo(sA), b_lo0 = sdesc_lo(sB);
+        for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
+            const int mt = (int)(w / P.ntn);
+            if (mt != arow) {
+                if (a_loads && lane == 0) mma_commit(a_empty);  // A is free once the earlier products are done
+                wait(a_full, a_loads & 1u);
+                ++a_loads;
+                arow = mt;
             }
+            const int s = (int)(it & 1u);
+            const uint32_t ph = (it >> 1) & 1u;
+            const bool ready = wait(b_full(s), ph) && wait(t_empty(s), ph ^ 1u);
             tc_fence_after();
-            const uint32_t st = base + s * Cfg::STAGE;
+            const bool go = __all_sync(0xffffffffu, ready) && !*abort_flag;
+            if (go && lane == 0) {
+                const uint32_t tacc = tmem + (uint32_t)(s * Cfg::DIAG * MM_BN);
+                const uint32_t b_lo = b_lo0 + ((uint32_t)s * Cfg::B_BYTES >> 4);
+                // descriptor start addresses move in 16-byte units; every offset below is a
+                // compile-time constant except the stage, so each product is one add and the MMA
 #pragma unroll
-            for (int kk = 0; kk < MM_BK / 16; ++kk) {
+                for (int kb = 0; kb < Cfg::KB; ++kb) {
+                    if (kb < nkb) {
 #pragma unroll
-                for (int i = 0; i < L; ++i) {
+                        for (int kk = 0; kk < MM_BK / 16; ++kk) {
 #pragma unroll
-                    for (int j = 0; j < L; ++j) {
-                        const int d = i + j;
-                        const uint64_t ad = sdesc(st + i * Cfg::A_TILE + kk * 32);
-                        const uint64_t bd = sdesc(st + L * Cfg::A_TILE + j * Cfg::B_TILE + kk * 32);
-                        mma_bf16(tmem + (uint32_t)(d * MM_BN), ad, bd, IDESC, (started >> d) & 1u);
-                        started |= 1u << d;
+                            for (int i = 0; i < L; ++i) {
+#pragma unroll
+                                for (int j = 0; j < L; ++j) {
+                                    const int d = i + j;
+                                    // the first product into diagonal d overwrites it
+                                    const bool first = kb == 0 && kk == 0 && (i == 0 || j == L - 1);
+                                    const uint32_t ao = ((uint32_t)(i * Cfg::KB + kb) * Cfg::A_BLK + kk * 32) >> 4;
+                                    const uint32_t bo = ((uint32_t)(j * Cfg::KB + kb) * Cfg::B_BLK + kk * 32) >> 4;
+                                    mma_bf16(tacc + (uint32_t)(d * MM_BN), sdesc_of(a_lo + ao), sdesc_of(b_lo + bo), IDESC,
+                                             first ? 0u : 1u);
+                                }
+                            }
+                        }
                     }
                 }
             }
-            mma_commit(empty(s));  // the stage is free once these products are done
+            __syncwarp();
+            if (lane == 0) {
+                mma_commit(b_empty(s));  // the B stage is free once these products are done
+                mma_commit(t_full(s));   // and the accumulators are ready
+            }
+            __syncwarp();
         }
-        mma_commit(accfull);
     } else if (warp >= 2) {
-        // epilogue: row r of the tile is tensor-memory lane r
-        const int sub = warp & 3;
-        const uint32_t r = (uint32_t)(32 * sub + lane);
-        const uint32_t m = m0 + r;
-        const bool ok = mbar_wait(accfull, 0);
-        if (!ok && lane == 0) atomicOr(P.err, 1u);
-        tc_fence_after();
-        const uint32_t trow = tmem + ((uint32_t)(32 * sub) << 16);
-#pragma unroll 1
-        for (int g = 0; g < MM_BN / 16; ++g) {
-            uint32_t acc[16];
-            uint32_t v[16];
-            // Horner over the diagonals, highest first
-            tmem_ld16(trow + (uint32_t)((Cfg::DIAG - 1) * MM_BN + 16 * g), v);
+        // ---- epilogue: row r of the tile is tensor-memory lane r; warps 2..9 cover the four lane
+        // quarters twice, the first four taking columns 0..15 of the tile and the others 16..31
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        const uint32_t r = (uint32_t)(32 * quarter + lane);
+        const uint32_t trow_off = ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * half);
+        const bool storer = warp == 2 && lane == 0;
+        uint32_t it = 0;
+        for (uint32_t w = w0; w < w1; ++w, ++it) {
+            const int mt = (int)(w / P.ntn), nt = (int)(w % P.ntn);
+            const int s = (int)(it & 1u);
+            const uint32_t ph = (it >> 1) & 1u;
+            wait(t_full(s), ph);
+            tc_fence_after();
+            const uint32_t tacc = tmem + trow_off + (uint32_t)(s * Cfg::DIAG * MM_BN);
+            // value = sum_d D_d 256^d = sum_d D_d rd[d] (mod p); |sum| < 7 2^23 2^31 < 2^57
+            long long acc[16];
+            uint32_t va[16], vb[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0;
+            tmem_ld16(tacc, va);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = mod_signed((long long)__float2int_rn(__uint_as_float(v[j])), P);
-#pragma unroll 1
-            for (int d = Cfg::DIAG - 2; d >= 0; --d) {
-                tmem_ld16(trow + (uint32_t)(d * MM_BN + 16 * g), v);
-                tmem_wait_ld();
+            for (int d = 0; d < Cfg::DIAG; ++d) {
+                uint32_t(&cur)[16] = (d & 1) ? vb : va;
+                uint32_t(&nxt)[16] = (d & 1) ? va : vb;
+                if (d + 1 < Cfg::DIAG) tmem_ld16(tacc + (uint32_t)((d + 1) * MM_BN), nxt);  // in flight meanwhile
+                const long long rdd = (long long)P.rd[d];
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    acc[j] = mod_signed(((long long)acc[j] << 8) + (long long)__float2int_rn(__uint_as_float(v[j])), P);
+                for (int j = 0; j < 16; ++j) acc[j] += acc_int(cur[j]) * rdd;
+                if (d + 1 < Cfg::DIAG) tmem_wait_ld();
             }
-            if (ok && m < P.M) {
-                uint32_t *crow = P.C + (size_t)m * P.ldc;
+            uint32_t res[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const uint32_t n = n0 + 16 * g + j;
-                    if (n < P.N) {
-                        const uint32_t c = crow[n], s = acc[j];
-                        crow[n] = P.sub ? (c >= s ? c - s : c + P.fp.p - s) : fp_add(c, s, P.fp);
+            for (int j = 0; j < 16; ++j) res[j] = fp_reduce((uint64_t)(acc[j] + (long long)P.big), P.fp);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(t_empty(s));  // the accumulators may be overwritten
+            const bool have_c = wait(c_full(s), ph);
+            // C tile row r: 128 bytes, 16-byte chunk j at chunk position j ^ (r mod 8)
+            unsigned char *crow = gbase + (sC - base) + s * Cfg::C_BYTES + r * 128u;
+            if (have_c) {
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const uint32_t j = (uint32_t)(4 * half + jj);
+                    uint4 *q = reinterpret_cast<uint4 *>(crow + 16u * (j ^ (r & 7u)));
+                    uint4 c = *q;
+                    uint32_t *cw = reinterpret_cast<uint32_t *>(&c);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const uint32_t x = res[4 * jj + e];
+                        cw[e] = P.sub ? (cw[e] >= x ? cw[e] - x : cw[e] + P.fp.p - x) : fp_add(cw[e], x, P.fp);
                     }
+                    *q = c;
                 }
             }
+            fence_async_smem();
+            epi_sync();
+            if (storer) {
+                if (!*abort_flag) tma_store_2d(&tc, sC + s * Cfg::C_BYTES, P.cx + nt * MM_BN, P.cy + mt * MM_BM);
+                bulk_commit();
+                bulk_wait_read0();  // the store has read the buffer: the next C tile may land there
+                mbar_arrive(c_empty(s));
+            }
         }
+        if (storer) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
@@ -314,27 +431,41 @@ EncodeTiled encode_tiled() {
     return fn;
 }
 
-}  // namespace
+void encode(CUtensorMap *m, CUtensorMapDataType t, cuuint32_t rank, void *base, const cuuint64_t *dims,
+            const cuuint64_t *strides, const cuuint32_t *box) {
+    std::memset(m, 0, sizeof(*m));
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = encode_tiled()(m, t, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(GB_EDEVICE, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
 
-uint32_t digits_for(uint32_t p) { return p < 65536u ? 2u : 4u; }
-uint32_t mm_kmax(uint32_t p) { return 512u / digits_for(p); }
-
-// Tensor map of digit planes [L][rows][kpad] (BF16), box of 64 K values x box_rows rows x 1 digit.
+// digit planes [L][rows][kpad] (BF16), box of 64 K values x box_rows rows x 1 digit
 CUtensorMap digit_map(const DigitPlanes &D, uint32_t box_rows) {
     if (D.kpad % 8 || (reinterpret_cast<uintptr_t>(D.p) & 15))
         fail(GB_EDEVICE, "digit planes: row pitch or base not 16-byte aligned");
     CUtensorMap m;
-    std::memset(&m, 0, sizeof(m));
     const cuuint64_t dims[3] = {D.K, D.rows, D.L};
     const cuuint64_t strides[2] = {2ull * D.kpad, 2ull * D.kpad * D.rows};
     const cuuint32_t box[3] = {(cuuint32_t)MM_BK, box_rows, 1};
-    const cuuint32_t es[3] = {1, 1, 1};
-    const CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, D.p, dims, strides, box, es,
-                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) fail(GB_EDEVICE, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, D.p, dims, strides, box);
     return m;
 }
+
+int sm_count() {
+    static int n[64] = {};
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(GB_EUNSUPPORTED, "device ordinal above 63");
+    if (!n[dev]) GB_CUDA(cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev));
+    return n[dev];
+}
+
+}  // namespace
+
+uint32_t digits_for(uint32_t p) { return p < 65536u ? 2u : 4u; }
+uint32_t mm_kmax(uint32_t p) { return 512u / digits_for(p); }
 
 void DigitPlanes::alloc(Arena &ar, uint32_t L_, uint64_t rows_, uint64_t K_, cudaStream_t st) {
     L = L_;
@@ -354,23 +485,43 @@ void to_digits(const uint32_t *src, uint64_t rs, uint64_t ks, const DigitPlanes 
     counted();
 }
 
-// C[M x N] (row pitch ldc) <- C -/+ A B mod p, A given by digit planes of A (rows m, K-major,
-// starting at row ay and K offset ax), B by digit planes of B^T (rows n, K-major, starting at row
-// by and K offset bx); K <= mm_kmax(p).  err: a device word that collects the error flags.
-void mm_update(const DigitPlanes &A, uint32_t ax, uint32_t ay, const DigitPlanes &B, uint32_t bx, uint32_t by,
-               uint32_t M, uint32_t N, uint32_t K, uint32_t *C, uint64_t ldc, const Fp &fp, bool sub, uint32_t *err,
-               cudaStream_t st) {
-    if (!M || !N || !K) return;
+// Tensor maps of one operand set (A digit planes, B^T digit planes, C) for any number of
+// updates over sub-ranges of them: the maps are encoded once, each launch passes its offsets.
+struct MmPlan::Maps {
+    CUtensorMap ta, tb, tc;
+};
+
+MmPlan::MmPlan(const DigitPlanes &A_, const DigitPlanes &B_, uint32_t *C_, uint64_t ldc_, uint32_t crows,
+               uint32_t ccols, const Fp &fp_)
+    : A(&A_), B(&B_), C(C_), ldc(ldc_), rows(crows), cols(ccols), fp(fp_), maps(new Maps) {
     const uint32_t L = digits_for(fp.p);
-    if (A.L != L || B.L != L) fail(GB_EDEVICE, "mm_update: digit count does not match p");
+    if (A->L != L || B->L != L) fail(GB_EDEVICE, "mm plan: digit count does not match p");
+    if (ldc % 4 || (reinterpret_cast<uintptr_t>(C) & 15)) fail(GB_EDEVICE, "mm plan: C rows not 16-byte aligned");
+    maps->ta = digit_map(*A, MM_BM);
+    maps->tb = digit_map(*B, MM_BN);
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {4ull * ldc};
+    const cuuint32_t box[2] = {(cuuint32_t)MM_BN, (cuuint32_t)MM_BM};
+    encode(&maps->tc, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, C, dims, strides, box);
+}
+
+MmPlan::~MmPlan() { delete maps; }
+
+// C[cy + m][cx + n] <- C -/+ sum_k A[ay + m][ax + k] B^T[by + n][bx + k] mod p for m < M, n < N,
+// k < K <= mm_kmax(p).  The update region must end the C tensor of the plan on the right and
+// bottom (the stores of ragged tiles are clipped there) and cx must be a multiple of 4.
+void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t cx, uint32_t cy, uint32_t M,
+                    uint32_t N, uint32_t K, bool sub, uint32_t *err, cudaStream_t st) const {
+    if (!M || !N || !K) return;
     if (K > mm_kmax(fp.p)) fail(GB_EDEVICE, "mm_update: K above the exact accumulation bound");
     if (ax % 8 || bx % 8) fail(GB_EDEVICE, "mm_update: K offsets must be multiples of 8 (16-byte TMA rule)");
-    // the kernel reads whole 64-wide K blocks: a ragged K must end where the planes end (the TMA
-    // then fills the rest of the block with zeros)
-    if (K % MM_BK && (ax + K != A.K || bx + K != B.K)) fail(GB_EDEVICE, "mm_update: ragged K inside the planes");
-    if (ax + K > A.K || bx + K > B.K || ay + M > A.rows || by + N > B.rows)
+    // the kernel reads whole 64-wide K blocks: a ragged K must end where one operand's planes end
+    // (the TMA fills the rest of that operand's block with zeros, so the other operand's extra
+    // values, which must be finite, multiply zeros)
+    if (K % MM_BK && ax + K != A->K && bx + K != B->K) fail(GB_EDEVICE, "mm_update: ragged K inside both planes");
+    if (ax + K > A->K || bx + K > B->K || ay + M > A->rows || by + N > B->rows)
         fail(GB_EDEVICE, "mm_update: operand range outside the digit planes");
-    const CUtensorMap ta = digit_map(A, MM_BM), tb = digit_map(B, MM_BN);
+    if (cx % 4 || cx + N != cols || cy + M != rows) fail(GB_EDEVICE, "mm_update: C region does not end the tensor");
     MmParams P{};
     P.M = M;
     P.N = N;
@@ -379,20 +530,24 @@ void mm_update(const DigitPlanes &A, uint32_t ax, uint32_t ay, const DigitPlanes
     P.ay = (int)ay;
     P.bx = (int)bx;
     P.by = (int)by;
-    P.C = C;
-    P.ldc = ldc;
+    P.cx = (int)cx;
+    P.cy = (int)cy;
+    P.ntn = (N + MM_BN - 1) / MM_BN;
+    const uint64_t items = (uint64_t)((M + MM_BM - 1) / MM_BM) * P.ntn;
+    if (items >= (1ull << 31)) fail(GB_EUNSUPPORTED, "mm_update: too many tiles for one launch");
+    P.items = (uint32_t)items;
     P.fp = fp;
-    P.big = ((1ull << 50) / fp.p + 1) * fp.p;
+    P.big = ((1ull << 58) / fp.p + 1) * fp.p;
+    for (uint32_t d = 0, x = 1; d < 7; ++d, x = (uint32_t)((uint64_t)x * 256 % fp.p)) P.rd[d] = x;
     P.sub = sub ? 1 : 0;
     P.err = err;
-    const dim3 grid((N + MM_BN - 1) / MM_BN, (M + MM_BM - 1) / MM_BM);
-    if (grid.y > 65535u) fail(GB_EUNSUPPORTED, "mm_update: M too large for one launch");
-    if (L == 2) {
+    const unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)sm_count());
+    if (A->L == 2) {
         opt_in_smem(reinterpret_cast<const void *>(k_mm<2>));
-        k_mm<2><<<grid, MM_THREADS, MmCfg<2>::SMEM, st>>>(ta, tb, P);
+        k_mm<2><<<grid, MM_THREADS, MmCfg<2>::SMEM, st>>>(maps->ta, maps->tb, maps->tc, P);
     } else {
         opt_in_smem(reinterpret_cast<const void *>(k_mm<4>));
-        k_mm<4><<<grid, MM_THREADS, MmCfg<4>::SMEM, st>>>(ta, tb, P);
+        k_mm<4><<<grid, MM_THREADS, MmCfg<4>::SMEM, st>>>(maps->ta, maps->tb, maps->tc, P);
     }
     counted();
 }

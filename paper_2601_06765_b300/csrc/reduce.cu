@@ -668,12 +668,31 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         mode[j] = !S->fp.small ? M64 : (Mac->nA < 65536u ? A32 : A64);
         Es.push_back(std::move(E));
     }
+    // path of each matrix: dense blocked elimination on the tensor cores (dense.cu) or the sparse
+    // row-by-row reduction below
+    std::vector<uint8_t> dense(nj, 0);
+    {
+        size_t room = ar.capacity() > ar.used() ? ar.capacity() - ar.used() : 0;
+        for (int j = 0; j < nj; ++j) {
+            const RedJob &J = R[j];
+            if (!J.nC || !J.nb || !J.nA || (ctx->flags & GB_CTX_REDUCE_SPARSE)) continue;
+            const bool want = (ctx->flags & GB_CTX_REDUCE_DENSE) || dense_pays(J.fp.p, J.N, J.nA, J.nC);
+            const size_t need = dense_bytes(J.fp.p, J.N, J.nA, J.nC);
+            if (want && need + (64u << 20) < room) {
+                dense[j] = 1;
+                room -= need;
+            }
+        }
+    }
+    DBuf<uint32_t> derr;
+    derr.alloc(ar, 1, st);
+    GB_CUDA(cudaMemsetAsync(derr.p, 0, 4, st));
     // accumulators: shared memory per block when N fits, else one global row per block; launch
     // groups by mode and by the shared-memory size class (powers of two)
     std::vector<DBuf<unsigned char>> gbuf(nj);
     std::map<std::pair<int, int>, std::vector<int>> groups;  // (mode, size class or -1) -> jobs
     for (int j = 0; j < nj; ++j) {
-        if (!R[j].nC || !R[j].nb) continue;
+        if (!R[j].nC || !R[j].nb || dense[j]) continue;
         const size_t accb = mode[j] == A32 ? 4 : 8;
         const size_t bytes = (size_t)R[j].N * accb;
         int cls = -1;
@@ -706,6 +725,23 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             counted(2);
         }
         GB_CUDA(cudaEventRecord(ctx->ev[5], st));
+        for (int j = 0; j < nj; ++j) {
+            if (!dense[j]) continue;
+            const RedJob &J = R[j];
+            DenseJob D{};
+            D.row_ptr = J.row_ptr;
+            D.col = J.col;
+            D.val = J.val;
+            D.colpos = J.colpos;
+            D.Uinv = J.U;
+            D.N = J.N;
+            D.nA = J.nA;
+            D.nC = J.nC;
+            D.nb = J.nb;
+            D.fp = J.fp;
+            D.work = J.work;
+            reduce_dense(D, J.dprime, ar, derr.p, st);
+        }
         size_t gi = 2;
         for (auto &g : groups) {
             const int md = g.first.first, cls = g.first.second;
@@ -834,9 +870,12 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         }
     }
     GB_CUDA(cudaEventRecord(ctx->ev[4], st));
-    uint64_t *hw = static_cast<uint64_t *>(ctx_pinned(ctx, 16ull * nj));
+    uint64_t *hw = static_cast<uint64_t *>(ctx_pinned(ctx, 16ull * nj + 16));
     GB_CUDA(cudaMemcpyAsync(hw, work.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(hw + 2 * nj, derr.p, 4, cudaMemcpyDeviceToHost, st));
     ctx_sync(ctx);
+    if (*reinterpret_cast<const uint32_t *>(hw + 2 * nj))
+        fail(GB_ETIMEOUT, "dense reduction: a bounded wait in the tensor-core kernel gave up");
     float ms_red = 0.f, ms_rref = 0.f, ms_kern = 0.f;
     GB_CUDA(cudaEventElapsedTime(&ms_red, ctx->ev[2], ctx->ev[3]));
     GB_CUDA(cudaEventElapsedTime(&ms_kern, ctx->ev[5], ctx->ev[3]));

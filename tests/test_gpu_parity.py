@@ -16,9 +16,11 @@ from paper_2601_06765_b300 import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
-    c = gb.Context(arena_bytes=6 << 30, keep_step=True)
+@pytest.fixture(scope="module", params=["sparse", "dense"])
+def ctx(request):
+    """Every case runs with each reduction schedule forced: the sparse row-by-row reduction and
+    the dense blocked elimination on the tensor cores must both reproduce the unique D'."""
+    c = gb.Context(arena_bytes=6 << 30, keep_step=True, reduce=request.param)
     yield c
     c.close()
 
