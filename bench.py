@@ -196,6 +196,8 @@ def run_ours(args) -> None:
 
     batched = measure_batched(gb, synth, ctx) if rank == 0 and not args.no_batch else None
     served = measure_served(gb, synth, ctx) if rank == 0 and not args.no_batch else None
+    tensor = measure_tensor_core(gb, local) if rank == 0 and not args.no_batch else None
+    big = measure_config3(gb, synth, local, pk) if rank == 0 and not args.no_batch else None
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
              for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_rref", "ms_update", "ms_pairs", "ms_select",
                        "ms_wall")}
@@ -217,6 +219,8 @@ def run_ours(args) -> None:
             "gpu_launches": launches,
             "batched": batched,
             "served": served,
+            "tensor_core": tensor,
+            "config3": big,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -318,6 +322,84 @@ def measure_served(gb, synth, ctx, count: int = 300, slots: int = 64,
                         "p in {65521, 2^31-1}",
             "plain_systems_per_s": round(plain, 2), "saturation_systems_per_s": round(sat, 2),
             "hbm_cap_bytes": 150 << 30, "slots": slots, "loads": runs}
+
+
+def measure_tensor_core(gb, local: int) -> list:
+    """The exact mod-p update C <- C - A B on the tensor cores (gb_matmul_modp), device time by
+    CUDA events on the context's stream, against the measured BF16 dense peak.  Each modular
+    multiply-add costs L^2 BF16 digit products (L = 2 digits for p < 2^16, 4 for p < 2^31)."""
+    import torch
+    out = []
+    stream = torch.cuda.Stream(device=f"cuda:{local}")
+    peak = None
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    with torch.cuda.stream(stream):
+        ctx = gb.Context(device=local, arena_bytes=2 << 30, stream=stream)
+        for p, L, (m, n, k) in ((65521, 2, (4096, 8192, 1024)), (2147483647, 4, (4096, 8192, 512))):
+            g = torch.Generator(device=f"cuda:{local}").manual_seed(7)
+            A = torch.randint(0, p, (m, k), device=f"cuda:{local}", dtype=torch.int64, generator=g).to(torch.int32)
+            B = torch.randint(0, p, (k, n), device=f"cuda:{local}", dtype=torch.int64, generator=g).to(torch.int32)
+            C = torch.randint(0, p, (m, n), device=f"cuda:{local}", dtype=torch.int64, generator=g).to(torch.int32)
+            args = (ctx.h, p, m, n, k, A.data_ptr(), k, B.data_ptr(), n, C.data_ptr(), n, True)
+            gb.gb_matmul_modp(*args)  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record(stream)
+            for _ in range(reps):
+                gb.gb_matmul_modp(*args)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            macs = m * n * k
+            tflops = 2.0 * macs * L * L / (ms / 1e3) / 1e12
+            out.append({"p": p, "digits": L, "shape_mnk": [m, n, k], "ms": round(ms, 3),
+                        "modp_mac_per_s": macs / (ms / 1e3),
+                        "digit_product_tflops": round(tflops, 1),
+                        "frac_of_bf16_peak": round(tflops / peak, 4) if peak else None,
+                        "note": "device time of the whole call: digit planes of A and B, then "
+                                "ceil(k / (512 / L)) persistent tcgen05 launches"})
+        ctx.close()
+    return out
+
+
+def measure_config3(gb, synth, local: int, pk: dict) -> dict:
+    """One F4 run of the n=13 sparse 31-bit system (the large-matrix workload) with the reduction
+    chosen per matrix (dense tensor-core blocks for the large steps) and with the sparse reduction
+    only; and the symbolic preprocessing bandwidth of its largest step (algorithmic bytes: col_ind +
+    val written per nonzero, row_ptr, and the dictionary monomials)."""
+    system = synth.config3(0)
+    res = {"workload": "n=13, m=13 quadratics with 30 of the 105 monomials of degree <= 2, p=2^31-1, grevlex, "
+                       "SplitMix64 seed 20260765; one full F4 run"}
+    for mode in ("auto", "sparse"):
+        ctx = gb.Context(device=local, arena_bytes=48 << 30, reduce=mode)
+        S = gb.System(ctx, system)
+        t0 = time.perf_counter()
+        steps = []
+        while True:
+            st, stats = S.step()
+            if st != gb.GB_OK:
+                break
+            steps.append(stats)
+        S.groebner()
+        wall = time.perf_counter() - t0
+        S.close()
+        ctx.close()
+        nnz = sum(x["nnz"] for x in steps)
+        res[mode] = {"ms": round(wall * 1e3, 1), "nnz_per_s": nnz / wall,
+                     "ms_reduce": round(sum(x["ms_reduce"] for x in steps), 1),
+                     "ms_rref": round(sum(x["ms_rref"] for x in steps), 1)}
+        if mode == "auto":
+            top = max(steps, key=lambda x: x["nnz"])
+            alg = 8.0 * top["nnz"] + 4.0 * (top["nrows"] + 1) + 16.0 * top["ndict"]
+            gbs = alg / (top["ms_sp"] / 1e3) / 1e9
+            res["sp_largest_step"] = {"step": top["step"], "nnz": top["nnz"], "ms_sp": round(top["ms_sp"], 3),
+                                      "algorithmic_bytes": alg, "achieved_gbs": round(gbs, 1),
+                                      "peak_gbs": pk["hbm_gbs"], "frac": round(gbs / pk["hbm_gbs"], 4)}
+    res["speedup_auto_vs_sparse"] = round(res["sparse"]["ms"] / res["auto"]["ms"], 3)
+    return res
 
 
 def cpu_baseline(system: dict) -> dict:

@@ -382,7 +382,9 @@ class Context:
     """A library context whose device arena is a torch tensor on `device`."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 2 << 30, keep_step: bool = False,
-                 reduce: str = "auto"):
+                 reduce: str = "auto", stream=None):
+        """reduce: "auto" (per matrix by shape), "sparse" or "dense" (see GB_CTX_REDUCE_*).
+        stream: a torch.cuda.Stream the context runs on (default: a stream of its own)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: this library has no CPU path")
@@ -391,7 +393,9 @@ class Context:
         torch.cuda.synchronize(device)
         flags = (GB_CTX_KEEP_STEP if keep_step else 0) | {"auto": 0, "sparse": GB_CTX_REDUCE_SPARSE,
                                                             "dense": GB_CTX_REDUCE_DENSE}[reduce]
-        self.h = gb_ctx_create(device, None, self.arena.data_ptr(), arena_bytes, flags)
+        self.stream = stream
+        self.h = gb_ctx_create(device, stream.cuda_stream if stream is not None else None,
+                               self.arena.data_ptr(), arena_bytes, flags)
 
     def memory(self) -> tuple[int, int]:
         u, c = ctypes.c_size_t(), ctypes.c_size_t()

@@ -676,7 +676,10 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         for (int j = 0; j < nj; ++j) {
             const RedJob &J = R[j];
             if (!J.nC || !J.nb || !J.nA || (ctx->flags & GB_CTX_REDUCE_SPARSE)) continue;
-            const bool want = (ctx->flags & GB_CTX_REDUCE_DENSE) || dense_pays(J.fp.p, J.N, J.nA, J.nC);
+            // a dense matrix runs its own launch sequence, while the sparse kernels cover every
+            // matrix of a batch in one launch: inside a batch only very large matrices go dense
+            const bool want = (ctx->flags & GB_CTX_REDUCE_DENSE) ||
+                              (dense_pays(J.fp.p, J.N, J.nA, J.nC) && (nj == 1 || J.nA >= 16384));
             const size_t need = dense_bytes(J.fp.p, J.N, J.nA, J.nC);
             if (want && need + (64u << 20) < room) {
                 dense[j] = 1;
