@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <cmath>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <numeric>
 
@@ -607,6 +609,15 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
 
 // ---- the reduced basis ------------------------------------------------------------------------
 
+// GB_TRACE=1 in the environment: per-stage wall times of the final reduction on stderr
+static bool trace_on() {
+    static const bool on = [] {
+        const char *e = std::getenv("GB_TRACE");
+        return e && *e && *e != '0';
+    }();
+    return on;
+}
+
 void finish_batch(const std::vector<gb_system *> &Ss) {
     const size_t nj = Ss.size();
     if (!nj) return;
@@ -658,14 +669,20 @@ void finish_batch(const std::vector<gb_system *> &Ss) {
         elems.push_back(keep[j]);
         owners.push_back(S);
     }
+    const auto tm = Clock::now();
     if (!tasks.empty()) {
         symbolic_preprocess(tasks);
+        const auto ts = Clock::now();
         std::vector<gb_macaulay *> Ms;
         for (auto &t : tasks) Ms.push_back(t.out.get());
         auto Es = reduce_rows(Ms, false);
+        const auto tr = Clock::now();
         std::vector<gb_echelon *> Ep;
         for (auto &e : Es) Ep.push_back(e.get());
         replace_tails(Ep, elems);
+        if (trace_on())
+            std::fprintf(stderr, "[gb] finish: %zu systems, minimalise %.3f ms, SP %.3f ms, reduce %.3f ms, tails %.3f ms\n",
+                         nj, ms_between(t0, tm), ms_between(tm, ts), ms_between(ts, tr), ms_between(tr, Clock::now()));
         for (size_t k = 0; k < owners.size(); ++k) {
             gb_system *S = owners[k];
             S->run.ms_sp += Ms[k]->ms_sp;

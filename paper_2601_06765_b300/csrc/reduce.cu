@@ -1043,8 +1043,12 @@ void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::v
     }
     exclusive_scan(ar, cnt.p, scan.p, tot, st);
     std::vector<uint32_t> hs(tot + 1);
-    GB_CUDA(cudaMemcpyAsync(hs.data(), scan.p, 4ull * (tot + 1), cudaMemcpyDeviceToHost, st));
-    ctx_sync(ctx);
+    {
+        uint32_t *hp = static_cast<uint32_t *>(ctx_pinned(ctx, 4ull * (tot + 1)));
+        GB_CUDA(cudaMemcpyAsync(hp, scan.p, 4ull * (tot + 1), cudaMemcpyDeviceToHost, st));
+        ctx_sync(ctx);
+        std::memcpy(hs.data(), hp, 4ull * (tot + 1));
+    }
     uint64_t bytes = 0;
     std::vector<uint64_t> eoff(nj);
     for (int j = 0; j < nj; ++j) {
@@ -1066,18 +1070,22 @@ void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::v
         k_write_rows<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
         counted();
     }
-    std::vector<uint8_t> allx(bytes);
-    std::vector<uint32_t> allc(hs[tot]);
-    GB_CUDA(cudaMemcpyAsync(allx.data(), dex.p, bytes, cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaMemcpyAsync(allc.data(), dcf.p, 4ull * hs[tot], cudaMemcpyDeviceToHost, st));
+    // the terms come back through the page-locked staging area (one DMA, no pageable bounce) and
+    // are copied once into each system's result
+    const size_t cbytes = (4ull * hs[tot] + 255) & ~size_t(255);
+    char *hp = static_cast<char *>(ctx_pinned(ctx, cbytes + bytes + 16));
+    const uint32_t *allc = reinterpret_cast<const uint32_t *>(hp);
+    const uint8_t *allx = reinterpret_cast<const uint8_t *>(hp + cbytes);
+    GB_CUDA(cudaMemcpyAsync(hp, dcf.p, 4ull * hs[tot], cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(hp + cbytes, dex.p, bytes, cudaMemcpyDeviceToHost, st));
     ctx_sync(ctx);
     for (int j = 0; j < nj; ++j) {
         gb_system *S = Es[j]->mac->sys;
         const uint32_t b = hs[roff[j]], e = hs[roff[j] + elems[j].size()], n = S->n;
         S->fin_off.resize(elems[j].size() + 1);
         for (size_t i = 0; i <= elems[j].size(); ++i) S->fin_off[i] = hs[roff[j] + i] - b;
-        S->fin_cf.assign(allc.begin() + b, allc.begin() + e);
-        S->fin_exps.assign(allx.begin() + eoff[j], allx.begin() + eoff[j] + (size_t)(e - b) * n);
+        S->fin_cf.assign(allc + b, allc + e);
+        S->fin_exps.assign(allx + eoff[j], allx + eoff[j] + (size_t)(e - b) * n);
     }
 }
 
