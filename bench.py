@@ -460,9 +460,20 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and served lines")
     ap.add_argument("--arena-gb", type=int, default=32, help="device arena of the context (GiB)")
+    ap.add_argument("--only", choices=["tensor", "config3"], default=None,
+                    help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
-    if args.impl == "reference":
+    if args.only:
+        import torch
+        import paper_2601_06765_b300 as gb
+        from paper_2601_06765_b300 import synth
+        torch.cuda.set_device(0)
+        if args.only == "tensor":
+            print(json.dumps({"tensor_core": measure_tensor_core(gb, 0)}))
+        else:
+            print(json.dumps({"config3": measure_config3(gb, synth, 0, peaks())}))
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(RT, 6) k_reduce(const RedJob *__restrict__ job
 // left of its pivot, and later pivot rows are zero at it.  When no non-zero non-pivot row is left,
 // the pivot rows sorted by pivot column are RREF(D'), which is unique.  The panel solves of
 // different jobs run side by side, one block each.
-constexpr uint32_t KP = 32;
+constexpr uint32_t KP = 16;
 constexpr uint32_t NOLEAD = 0xFFFFFFFFu;
 
 struct RrefJob {
