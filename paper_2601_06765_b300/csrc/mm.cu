@@ -16,22 +16,25 @@
 // digit), which equals (A B)[m][n] mod p.  One launch covers K <= 512 / L; longer products are
 // split by the host into launches that each update C.
 //
-// Kernel: persistent, one CTA per SM, each CTA takes a contiguous run of the 128 x 32 output
+// Kernel: persistent, one CTA per SM, each CTA takes a contiguous run of the 128 x 64 output
 // tiles in row-major tile order.  10 warps:
 //   warp 0, lane 0   TMA producer: the digit planes of A for the CTA's current 128-row tile
-//                    (all of K, kept in shared memory while the row tile lasts), then per output
-//                    tile the digit planes of B^T (32 rows) and the C tile, double-buffered
-//                    (128-byte swizzle; mbarriers with transaction counts)
+//                    (all of K, resident in shared memory while the row tile lasts), then per
+//                    output tile the digit planes of B^T, one buffer per 64-wide K block so that a
+//                    block is refilled for the next tile as soon as its products are done, and the
+//                    C tile (128-byte swizzle; mbarriers with transaction counts)
 //   warp 1           allocates the tensor memory; lane 0 issues tcgen05.mma (kind::f16, BF16
-//                    operands, FP32 accumulators, M = 128, N = 32, K = 16) for every digit pair
-//                    into the accumulator of its diagonal, in one of two accumulator sets
-//   warps 2-9        epilogue (two warps per tensor-memory lane quarter, 16 columns each):
-//                    tcgen05.ld of the thread's row of every diagonal, exact conversion and
-//                    recombination mod p, read-modify-write of the C tile in shared memory, TMA
-//                    store of the tile
-// so the next tile's products run while the epilogue finishes the previous one.  Every wait is
-// bounded; a wait that gives up sets an error flag that the host turns into GB_ETIMEOUT, and
-// the CTA still releases its tensor memory.
+//                    operands, FP32 accumulators, M = 128, N = 64, K = 16) for every digit pair
+//                    into the accumulator of its diagonal.  Tensor memory holds two regions: for
+//                    p >= 2^16 diagonals 0-3 and 4-6 of the same tile (7 x 64 columns), for
+//                    p < 2^16 all 3 diagonals of alternate tiles
+//   warps 2-9        epilogue (two warps per tensor-memory lane quarter, 32 columns each): drains
+//                    a region as soon as its products are done (tcgen05.ld, exact conversion,
+//                    sum_s D_s (256^s mod p)), hands it back, then one Barrett reduction,
+//                    read-modify-write of the C tile in shared memory and a TMA store
+// so that one region's products run while the other is drained.  Every wait is bounded; a wait that
+// gives up sets an error flag that the host turns into GB_ETIMEOUT, and the CTA still releases its
+// tensor memory.
 #include <cuda.h>
 
 #include <algorithm>
@@ -43,7 +46,7 @@ namespace gb {
 
 namespace {
 
-constexpr int MM_BM = 128, MM_BN = 32, MM_BK = 64;  // C tile, K block (64 BF16 = 128 bytes)
+constexpr int MM_BM = 128, MM_BN = 64, MM_BK = 64;  // C tile, K block (64 BF16 = 128 bytes)
 constexpr int MM_EPI = 8;                          // epilogue warps: two per tensor-memory lane quarter
 constexpr int MM_THREADS = 32 * (2 + MM_EPI);
 constexpr uint32_t MM_SPIN = 1u << 22;               // bounded mbarrier waits
@@ -53,13 +56,21 @@ struct MmCfg {
     static constexpr int DIAG = 2 * L - 1;            // digit diagonals
     static constexpr int KB = 512 / L / MM_BK;        // K blocks of the longest exact K
     static constexpr uint32_t A_BLK = MM_BM * 128;    // bytes of one digit x K block of A
-    static constexpr uint32_t B_BLK = MM_BN * 128;
+    static constexpr uint32_t B_BLK = MM_BN * 128;    // bytes of one digit x K block of B^T
     static constexpr uint32_t A_BYTES = L * KB * A_BLK;
-    static constexpr uint32_t B_BYTES = L * KB * B_BLK;
-    static constexpr uint32_t C_BYTES = MM_BM * MM_BN * 4;
-    static constexpr uint32_t SMEM_DATA = A_BYTES + 2 * (B_BYTES + C_BYTES);
+    static constexpr uint32_t B_KB = L * B_BLK;       // one K block of B^T, all digits
+    static constexpr uint32_t B_BYTES = KB * B_KB;
+    static constexpr uint32_t C_HALF = MM_BM * 32 * 4;  // one 32-column TMA box of the C tile
+    static constexpr uint32_t C_BYTES = 2 * C_HALF;
+    static constexpr uint32_t SMEM_DATA = A_BYTES + B_BYTES + C_BYTES;
     static constexpr uint32_t SMEM = SMEM_DATA + 1024 + 256;  // + alignment + barriers
-    static constexpr uint32_t TMEM_COLS = 2 * DIAG * MM_BN <= 256 ? 256 : 512;
+    // tensor-memory regions: SPLIT (L = 4): region 0 = diagonals 0-3, region 1 = diagonals 4-6 of
+    // every tile; otherwise each region holds all diagonals of alternate tiles
+    static constexpr bool SPLIT = L == 4;
+    static constexpr int R0_DIAG = SPLIT ? 4 : DIAG;
+    static constexpr uint32_t R1_COL = (uint32_t)R0_DIAG * MM_BN;
+    static constexpr uint32_t TMEM_COLS = 512;
+    static_assert(R1_COL + (uint32_t)(SPLIT ? DIAG - R0_DIAG : DIAG) * MM_BN <= TMEM_COLS, "tensor memory");
 };
 
 struct MmParams {
@@ -176,6 +187,18 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MM_B
 
 __device__ __forceinline__ int acc_int(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
 
+// region of diagonal d and its first tensor-memory column within the region
+template <int L>
+__host__ __device__ constexpr int region_of(int d) { return MmCfg<L>::SPLIT ? (d < MmCfg<L>::R0_DIAG ? 0 : 1) : 0; }
+template <int L>
+__host__ __device__ constexpr uint32_t dcol(int d) {
+    return MmCfg<L>::SPLIT ? (d < MmCfg<L>::R0_DIAG ? (uint32_t)d * MM_BN : MmCfg<L>::R1_COL + (uint32_t)(d - MmCfg<L>::R0_DIAG) * MM_BN)
+                           : (uint32_t)d * MM_BN;
+}
+// is (i, j) the first digit pair of its diagonal in the issue order (i outer, j inner)?
+template <int L>
+__host__ __device__ constexpr bool first_pair(int i, int j) { return i == 0 || j == L - 1; }
+
 template <int L>
 __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CUtensorMap ta,
                                                      const __grid_constant__ CUtensorMap tb,
@@ -185,17 +208,15 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
     const uint32_t raw = smem_u32(mm_smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned
     unsigned char *gbase = mm_smem_raw + (base - raw);
-    // layout: A | B[2] | C[2] | barriers
-    const uint32_t sA = base, sB = base + Cfg::A_BYTES, sC = sB + 2 * Cfg::B_BYTES;
+    // layout: A | B (per K block: all digits) | C (two 32-column halves) | barriers
+    const uint32_t sA = base, sB = base + Cfg::A_BYTES, sC = sB + Cfg::B_BYTES;
     const uint32_t bars = base + Cfg::SMEM_DATA;
-    const uint32_t a_full = bars, a_empty = bars + 8;
-    auto b_full = [&](int s) { return bars + 16 + 8u * s; };
-    auto b_empty = [&](int s) { return bars + 32 + 8u * s; };
-    auto c_full = [&](int s) { return bars + 48 + 8u * s; };
-    auto c_empty = [&](int s) { return bars + 64 + 8u * s; };
-    auto t_full = [&](int s) { return bars + 80 + 8u * s; };
-    auto t_empty = [&](int s) { return bars + 96 + 8u * s; };
-    const uint32_t tslot = bars + 112;
+    const uint32_t a_full = bars, a_empty = bars + 8, c_full = bars + 16, c_empty = bars + 24;
+    auto r_full = [&](int r) { return bars + 32 + 8u * r; };
+    auto r_empty = [&](int r) { return bars + 48 + 8u * r; };
+    auto b_full = [&](int kb) { return bars + 64 + 8u * kb; };
+    auto b_empty = [&](int kb) { return bars + 96 + 8u * kb; };
+    const uint32_t tslot = bars + 128;
     uint32_t *tslot_g = reinterpret_cast<uint32_t *>(gbase + (tslot - base));
     // set when a bounded wait gives up: from then on every wait returns at once and no new copy,
     // product or store is issued, but every role still runs its whole loop, so the epilogue warps
@@ -218,13 +239,15 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
         *abort_flag = 0u;
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(b_full(s), 1);
-            mbar_init(b_empty(s), 1);
-            mbar_init(c_full(s), 1);
-            mbar_init(c_empty(s), 1);
-            mbar_init(t_full(s), 1);
-            mbar_init(t_empty(s), MM_EPI);  // one arrival per epilogue warp
+        mbar_init(c_full, 1);
+        mbar_init(c_empty, 1);
+        for (int r = 0; r < 2; ++r) {
+            mbar_init(r_full(r), 1);
+            mbar_init(r_empty(r), MM_EPI);  // one arrival per epilogue warp
+        }
+        for (int kb = 0; kb < Cfg::KB; ++kb) {
+            mbar_init(b_full(kb), 1);
+            mbar_init(b_empty(kb), 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -254,25 +277,29 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 ++a_loads;
                 arow = mt;
             }
-            const int s = (int)(it & 1u);
-            const uint32_t ph = (it >> 1) & 1u;
-            if (wait(b_empty(s), ph ^ 1u)) {
-                mbar_expect_tx(b_full(s), (uint32_t)(L * nkb) * Cfg::B_BLK);
-                for (int l = 0; l < L; ++l)
-                    for (int kb = 0; kb < nkb; ++kb)
-                        tma_load_3d(sB + s * Cfg::B_BYTES + (uint32_t)(l * Cfg::KB + kb) * Cfg::B_BLK, &tb, b_full(s),
+            const uint32_t ph = it & 1u;
+            for (int kb = 0; kb < nkb; ++kb) {
+                if (wait(b_empty(kb), ph ^ 1u)) {
+                    mbar_expect_tx(b_full(kb), Cfg::B_KB);
+                    for (int l = 0; l < L; ++l)
+                        tma_load_3d(sB + (uint32_t)kb * Cfg::B_KB + (uint32_t)l * Cfg::B_BLK, &tb, b_full(kb),
                                     P.bx + kb * MM_BK, P.by + nt * MM_BN, l);
+                }
             }
-            if (wait(c_empty(s), ph ^ 1u)) {
-                mbar_expect_tx(c_full(s), Cfg::C_BYTES);
-                tma_load_2d(sC + s * Cfg::C_BYTES, &tc, c_full(s), P.cx + nt * MM_BN, P.cy + mt * MM_BM);
+            // the tile's second 32-column half lies wholly past N on a ragged last tile: not moved
+            const int halves = P.N - (uint32_t)nt * MM_BN > 32u ? 2 : 1;
+            if (wait(c_empty, ph ^ 1u)) {
+                mbar_expect_tx(c_full, (uint32_t)halves * Cfg::C_HALF);
+                for (int h = 0; h < halves; ++h)
+                    tma_load_2d(sC + (uint32_t)h * Cfg::C_HALF, &tc, c_full, P.cx + nt * MM_BN + 32 * h,
+                                P.cy + mt * MM_BM);
             }
         }
     } else if (warp == 1) {
         // ---- MMA issuer: the whole warp runs the loop (warp-uniform descriptors), lane 0 issues
         int arow = -1;
         uint32_t a_loads = 0;
-        const uint32_t a_lo = sdesc_lo(sA), b_lo0 = sdesc_lo(sB);
+        const uint32_t a_lo = sdesc_lo(sA), b_lo = sdesc_lo(sB);
         for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
             const int mt = (int)(w / P.ntn);
             if (mt != arow) {
@@ -281,19 +308,22 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 ++a_loads;
                 arow = mt;
             }
-            const int s = (int)(it & 1u);
-            const uint32_t ph = (it >> 1) & 1u;
-            const bool ready = wait(b_full(s), ph) && wait(t_empty(s), ph ^ 1u);
+            const uint32_t ph = it & 1u;
+            // regions of this tile and the parity of their previous use
+            const int reg0 = Cfg::SPLIT ? 0 : (int)(it & 1u);
+            const uint32_t use0 = Cfg::SPLIT ? it : (it >> 1);
+            bool ok = __all_sync(0xffffffffu, wait(r_empty(reg0), (use0 & 1u) ^ 1u));
+            if (Cfg::SPLIT) ok = __all_sync(0xffffffffu, wait(r_empty(1), (it & 1u) ^ 1u)) && ok;
             tc_fence_after();
-            const bool go = __all_sync(0xffffffffu, ready) && !*abort_flag;
-            if (go && lane == 0) {
-                const uint32_t tacc = tmem + (uint32_t)(s * Cfg::DIAG * MM_BN);
-                const uint32_t b_lo = b_lo0 + ((uint32_t)s * Cfg::B_BYTES >> 4);
-                // descriptor start addresses move in 16-byte units; every offset below is a
-                // compile-time constant except the stage, so each product is one add and the MMA
+            const uint32_t tbase = tmem + (Cfg::SPLIT ? 0u : (uint32_t)reg0 * Cfg::R1_COL);
 #pragma unroll
-                for (int kb = 0; kb < Cfg::KB; ++kb) {
-                    if (kb < nkb) {
+            for (int kb = 0; kb < Cfg::KB; ++kb) {
+                if (kb < nkb) {
+                    const bool have = __all_sync(0xffffffffu, wait(b_full(kb), ph)) && ok;
+                    tc_fence_after();
+                    if (have && !*abort_flag && lane == 0) {
+                        // descriptor start addresses move in 16-byte units; every offset below is a
+                        // compile-time constant, so each product is one add and the MMA
 #pragma unroll
                         for (int kk = 0; kk < MM_BK / 16; ++kk) {
 #pragma unroll
@@ -301,76 +331,95 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
 #pragma unroll
                                 for (int j = 0; j < L; ++j) {
                                     const int d = i + j;
-                                    // the first product into diagonal d overwrites it
-                                    const bool first = kb == 0 && kk == 0 && (i == 0 || j == L - 1);
+                                    const bool first = kb == 0 && kk == 0 && first_pair<L>(i, j);
                                     const uint32_t ao = ((uint32_t)(i * Cfg::KB + kb) * Cfg::A_BLK + kk * 32) >> 4;
-                                    const uint32_t bo = ((uint32_t)(j * Cfg::KB + kb) * Cfg::B_BLK + kk * 32) >> 4;
-                                    mma_bf16(tacc + (uint32_t)(d * MM_BN), sdesc_of(a_lo + ao), sdesc_of(b_lo + bo), IDESC,
+                                    const uint32_t bo = ((uint32_t)kb * Cfg::B_KB + (uint32_t)j * Cfg::B_BLK + kk * 32) >> 4;
+                                    mma_bf16(tbase + dcol<L>(d), sdesc_of(a_lo + ao), sdesc_of(b_lo + bo), IDESC,
                                              first ? 0u : 1u);
                                 }
                             }
                         }
                     }
+                    __syncwarp();
+                    if (lane == 0) mma_commit(b_empty(kb));  // this K block of B^T may be refilled
                 }
             }
             __syncwarp();
             if (lane == 0) {
-                mma_commit(b_empty(s));  // the B stage is free once these products are done
-                mma_commit(t_full(s));   // and the accumulators are ready
+                mma_commit(r_full(reg0));  // the tile's accumulators are ready
+                if (Cfg::SPLIT) mma_commit(r_full(1));
             }
             __syncwarp();
         }
     } else if (warp >= 2) {
         // ---- epilogue: row r of the tile is tensor-memory lane r; warps 2..9 cover the four lane
-        // quarters twice, the first four taking columns 0..15 of the tile and the others 16..31
+        // quarters twice, the first four taking columns 0..31 of the tile and the others 32..63
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         const uint32_t r = (uint32_t)(32 * quarter + lane);
-        const uint32_t trow_off = ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * half);
+        const uint32_t trow_off = ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * half);
         const bool storer = warp == 2 && lane == 0;
-        uint32_t it = 0;
-        for (uint32_t w = w0; w < w1; ++w, ++it) {
+        for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
             const int mt = (int)(w / P.ntn), nt = (int)(w % P.ntn);
-            const int s = (int)(it & 1u);
-            const uint32_t ph = (it >> 1) & 1u;
-            wait(t_full(s), ph);
-            tc_fence_after();
-            const uint32_t tacc = tmem + trow_off + (uint32_t)(s * Cfg::DIAG * MM_BN);
+            const uint32_t ph = it & 1u;
             // value = sum_d D_d 256^d = sum_d D_d rd[d] (mod p); |sum| < 7 2^23 2^31 < 2^57
-            long long acc[16];
-            uint32_t va[16], vb[16];
+            long long acc[32];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0;
-            tmem_ld16(tacc, va);
-            tmem_wait_ld();
+            for (int j = 0; j < 32; ++j) acc[j] = 0;
+            const int nreg = Cfg::SPLIT ? 2 : 1;
 #pragma unroll
-            for (int d = 0; d < Cfg::DIAG; ++d) {
-                uint32_t(&cur)[16] = (d & 1) ? vb : va;
-                uint32_t(&nxt)[16] = (d & 1) ? va : vb;
-                if (d + 1 < Cfg::DIAG) tmem_ld16(tacc + (uint32_t)((d + 1) * MM_BN), nxt);  // in flight meanwhile
-                const long long rdd = (long long)P.rd[d];
+            for (int rr = 0; rr < nreg; ++rr) {
+                const int reg = Cfg::SPLIT ? rr : (int)(it & 1u);
+                const uint32_t use = Cfg::SPLIT ? it : (it >> 1);
+                wait(r_full(reg), use & 1u);
+                tc_fence_after();
+                const uint32_t tb = tmem + trow_off + (Cfg::SPLIT ? 0u : (uint32_t)reg * Cfg::R1_COL);
+                const int d0 = Cfg::SPLIT ? (rr == 0 ? 0 : Cfg::R0_DIAG) : 0;
+                const int d1 = Cfg::SPLIT ? (rr == 0 ? Cfg::R0_DIAG : Cfg::DIAG) : Cfg::DIAG;
+                // two 16-column loads per diagonal, one pair in flight while the previous is summed
+                uint32_t va[16], vb[16], vc[16], vd[16];
+                tmem_ld16(tb + dcol<L>(d0), va);
+                tmem_ld16(tb + dcol<L>(d0) + 16, vb);
+                tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[j] += acc_int(cur[j]) * rdd;
-                if (d + 1 < Cfg::DIAG) tmem_wait_ld();
+                for (int d = 0; d < Cfg::DIAG; ++d) {
+                    if (d < d0 || d >= d1) continue;
+                    const bool odd = ((d - d0) & 1) != 0;
+                    uint32_t(&c0)[16] = odd ? vc : va;
+                    uint32_t(&c1)[16] = odd ? vd : vb;
+                    uint32_t(&n0)[16] = odd ? va : vc;
+                    uint32_t(&n1)[16] = odd ? vb : vd;
+                    if (d + 1 < d1) {  // in flight meanwhile
+                        tmem_ld16(tb + dcol<L>(d + 1), n0);
+                        tmem_ld16(tb + dcol<L>(d + 1) + 16, n1);
+                    }
+                    const long long rdd = (long long)P.rd[d];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        acc[j] += acc_int(c0[j]) * rdd;
+                        acc[16 + j] += acc_int(c1[j]) * rdd;
+                    }
+                    if (d + 1 < d1) tmem_wait_ld();
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(r_empty(reg));  // the region may be overwritten
             }
-            uint32_t res[16];
+            uint32_t res[32];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) res[j] = fp_reduce((uint64_t)(acc[j] + (long long)P.big), P.fp);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(t_empty(s));  // the accumulators may be overwritten
-            const bool have_c = wait(c_full(s), ph);
-            // C tile row r: 128 bytes, 16-byte chunk j at chunk position j ^ (r mod 8)
-            unsigned char *crow = gbase + (sC - base) + s * Cfg::C_BYTES + r * 128u;
+            for (int j = 0; j < 32; ++j) res[j] = fp_reduce((uint64_t)(acc[j] + (long long)P.big), P.fp);
+            const bool have_c = wait(c_full, ph);
+            // the thread's 32 columns are the C half `half`, row r: 128 bytes, 16-byte chunk j at
+            // chunk position j ^ (r mod 8)
+            unsigned char *crow = gbase + (sC - base) + (uint32_t)half * Cfg::C_HALF + r * 128u;
             if (have_c) {
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const uint32_t j = (uint32_t)(4 * half + jj);
-                    uint4 *q = reinterpret_cast<uint4 *>(crow + 16u * (j ^ (r & 7u)));
+                for (int j = 0; j < 8; ++j) {
+                    uint4 *q = reinterpret_cast<uint4 *>(crow + 16u * ((uint32_t)j ^ (r & 7u)));
                     uint4 c = *q;
                     uint32_t *cw = reinterpret_cast<uint32_t *>(&c);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const uint32_t x = res[4 * jj + e];
+                        const uint32_t x = res[4 * j + e];
                         cw[e] = P.sub ? (cw[e] >= x ? cw[e] - x : cw[e] + P.fp.p - x) : fp_add(cw[e], x, P.fp);
                     }
                     *q = c;
@@ -379,10 +428,13 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
             fence_async_smem();
             epi_sync();
             if (storer) {
-                if (!*abort_flag) tma_store_2d(&tc, sC + s * Cfg::C_BYTES, P.cx + nt * MM_BN, P.cy + mt * MM_BM);
+                const int halves = P.N - (uint32_t)nt * MM_BN > 32u ? 2 : 1;
+                if (!*abort_flag)
+                    for (int h = 0; h < halves; ++h)
+                        tma_store_2d(&tc, sC + (uint32_t)h * Cfg::C_HALF, P.cx + nt * MM_BN + 32 * h, P.cy + mt * MM_BM);
                 bulk_commit();
                 bulk_wait_read0();  // the store has read the buffer: the next C tile may land there
-                mbar_arrive(c_empty(s));
+                mbar_arrive(c_empty);
             }
         }
         if (storer) bulk_wait_all();
@@ -501,7 +553,7 @@ MmPlan::MmPlan(const DigitPlanes &A_, const DigitPlanes &B_, uint32_t *C_, uint6
     maps->tb = digit_map(*B, MM_BN);
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {4ull * ldc};
-    const cuuint32_t box[2] = {(cuuint32_t)MM_BN, (cuuint32_t)MM_BM};
+    const cuuint32_t box[2] = {32u, (cuuint32_t)MM_BM};  // 128 bytes: the 128-byte swizzle span
     encode(&maps->tc, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, C, dims, strides, box);
 }
 
