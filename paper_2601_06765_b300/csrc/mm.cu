@@ -17,7 +17,7 @@
 // split by the host into launches that each update C.
 //
 // Kernel: persistent, one CTA per SM, each CTA takes a contiguous run of the 128 x 64 output
-// tiles in row-major tile order.  10 warps:
+// tiles in row-major tile order.  18 warps:
 //   warp 0, lane 0   TMA producer: the digit planes of A for the CTA's current 128-row tile
 //                    (all of K, resident in shared memory while the row tile lasts), then per
 //                    output tile the digit planes of B^T, one buffer per 64-wide K block so that a
@@ -28,7 +28,7 @@
 //                    into the accumulator of its diagonal.  Tensor memory holds two regions: for
 //                    p >= 2^16 diagonals 0-3 and 4-6 of the same tile (7 x 64 columns), for
 //                    p < 2^16 all 3 diagonals of alternate tiles
-//   warps 2-9        epilogue (two warps per tensor-memory lane quarter, 32 columns each): drains
+//   warps 2-17       epilogue (four warps per tensor-memory lane quarter, 16 columns each): drains
 //                    a region as soon as its products are done (tcgen05.ld, exact conversion,
 //                    sum_s D_s (256^s mod p)), hands it back, then one Barrett reduction,
 //                    read-modify-write of the C tile in shared memory and a TMA store
@@ -47,7 +47,7 @@ namespace gb {
 namespace {
 
 constexpr int MM_BM = 128, MM_BN = 64, MM_BK = 64;  // C tile, K block (64 BF16 = 128 bytes)
-constexpr int MM_EPI = 8;                          // epilogue warps: two per tensor-memory lane quarter
+constexpr int MM_EPI = 16;                         // epilogue warps: four per tensor-memory lane quarter
 constexpr int MM_THREADS = 32 * (2 + MM_EPI);
 constexpr uint32_t MM_SPIN = 1u << 22;               // bounded mbarrier waits
 
@@ -309,65 +309,73 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 arow = mt;
             }
             const uint32_t ph = it & 1u;
-            // regions of this tile and the parity of their previous use
-            const int reg0 = Cfg::SPLIT ? 0 : (int)(it & 1u);
-            const uint32_t use0 = Cfg::SPLIT ? it : (it >> 1);
-            bool ok = __all_sync(0xffffffffu, wait(r_empty(reg0), (use0 & 1u) ^ 1u));
-            if (Cfg::SPLIT) ok = __all_sync(0xffffffffu, wait(r_empty(1), (it & 1u) ^ 1u)) && ok;
-            tc_fence_after();
-            const uint32_t tbase = tmem + (Cfg::SPLIT ? 0u : (uint32_t)reg0 * Cfg::R1_COL);
+            // 31-bit: region 0 (diagonals 0-3) over all of K, then region 1 (diagonals 4-6), so the
+            // epilogue drains one region while the other's products run.  16-bit: one region,
+            // alternating between tiles.
+            constexpr int NPH = Cfg::SPLIT ? 2 : 1;
 #pragma unroll
-            for (int kb = 0; kb < Cfg::KB; ++kb) {
-                if (kb < nkb) {
-                    const bool have = __all_sync(0xffffffffu, wait(b_full(kb), ph)) && ok;
-                    tc_fence_after();
-                    if (have && !*abort_flag && lane == 0) {
-                        // descriptor start addresses move in 16-byte units; every offset below is a
-                        // compile-time constant, so each product is one add and the MMA
+            for (int phs = 0; phs < NPH; ++phs) {
+                const int reg = Cfg::SPLIT ? phs : (int)(it & 1u);
+                const uint32_t use = Cfg::SPLIT ? it : (it >> 1);
+                const bool ok = __all_sync(0xffffffffu, wait(r_empty(reg), (use & 1u) ^ 1u));
+                tc_fence_after();
+                const uint32_t tbase = tmem + (Cfg::SPLIT ? 0u : (uint32_t)reg * Cfg::R1_COL);
 #pragma unroll
-                        for (int kk = 0; kk < MM_BK / 16; ++kk) {
+                for (int kb = 0; kb < Cfg::KB; ++kb) {
+                    if (kb < nkb) {
+                        bool have = ok;
+                        if (phs == 0) {  // the K block arrives once per tile
+                            have = __all_sync(0xffffffffu, wait(b_full(kb), ph)) && ok;
+                            tc_fence_after();
+                        }
+                        if (have && !*abort_flag && lane == 0) {
+                            // descriptor start addresses move in 16-byte units; every offset below
+                            // is a compile-time constant, so each product is one add and the MMA
 #pragma unroll
-                            for (int i = 0; i < L; ++i) {
+                            for (int kk = 0; kk < MM_BK / 16; ++kk) {
 #pragma unroll
-                                for (int j = 0; j < L; ++j) {
-                                    const int d = i + j;
-                                    const bool first = kb == 0 && kk == 0 && first_pair<L>(i, j);
-                                    const uint32_t ao = ((uint32_t)(i * Cfg::KB + kb) * Cfg::A_BLK + kk * 32) >> 4;
-                                    const uint32_t bo = ((uint32_t)kb * Cfg::B_KB + (uint32_t)j * Cfg::B_BLK + kk * 32) >> 4;
-                                    mma_bf16(tbase + dcol<L>(d), sdesc_of(a_lo + ao), sdesc_of(b_lo + bo), IDESC,
-                                             first ? 0u : 1u);
+                                for (int i = 0; i < L; ++i) {
+#pragma unroll
+                                    for (int j = 0; j < L; ++j) {
+                                        const int d = i + j;
+                                        if (region_of<L>(d) != phs) continue;
+                                        const bool first = kb == 0 && kk == 0 && first_pair<L>(i, j);
+                                        const uint32_t ao = ((uint32_t)(i * Cfg::KB + kb) * Cfg::A_BLK + kk * 32) >> 4;
+                                        const uint32_t bo =
+                                            ((uint32_t)kb * Cfg::B_KB + (uint32_t)j * Cfg::B_BLK + kk * 32) >> 4;
+                                        mma_bf16(tbase + dcol<L>(d), sdesc_of(a_lo + ao), sdesc_of(b_lo + bo), IDESC,
+                                                 first ? 0u : 1u);
+                                    }
                                 }
                             }
                         }
+                        __syncwarp();
+                        // this K block of B^T may be refilled after its last use in the tile
+                        if (phs == NPH - 1 && lane == 0) mma_commit(b_empty(kb));
                     }
-                    __syncwarp();
-                    if (lane == 0) mma_commit(b_empty(kb));  // this K block of B^T may be refilled
                 }
+                __syncwarp();
+                if (lane == 0) mma_commit(r_full(reg));  // the region's accumulators are ready
+                __syncwarp();
             }
-            __syncwarp();
-            if (lane == 0) {
-                mma_commit(r_full(reg0));  // the tile's accumulators are ready
-                if (Cfg::SPLIT) mma_commit(r_full(1));
-            }
-            __syncwarp();
         }
     } else if (warp >= 2) {
-        // ---- epilogue: row r of the tile is tensor-memory lane r; warps 2..9 cover the four lane
-        // quarters twice, the first four taking columns 0..31 of the tile and the others 32..63
-        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        // ---- epilogue: row r of the tile is tensor-memory lane r; warps 2..17 cover the four lane
+        // quarters four times, warp group g taking columns 16 g .. 16 g + 15 of the tile
+        const int quarter = warp & 3, grp = (warp - 2) >> 2;
         const uint32_t r = (uint32_t)(32 * quarter + lane);
-        const uint32_t trow_off = ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * half);
+        const uint32_t trow_off = ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * grp);
         const bool storer = warp == 2 && lane == 0;
         for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
             const int mt = (int)(w / P.ntn), nt = (int)(w % P.ntn);
             const uint32_t ph = it & 1u;
             // value = sum_d D_d 256^d = sum_d D_d rd[d] (mod p); |sum| < 7 2^23 2^31 < 2^57
-            long long acc[32];
+            long long acc[16];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] = 0;
-            const int nreg = Cfg::SPLIT ? 2 : 1;
+            for (int j = 0; j < 16; ++j) acc[j] = 0;
+            constexpr int NRG = Cfg::SPLIT ? 2 : 1;
 #pragma unroll
-            for (int rr = 0; rr < nreg; ++rr) {
+            for (int rr = 0; rr < NRG; ++rr) {
                 const int reg = Cfg::SPLIT ? rr : (int)(it & 1u);
                 const uint32_t use = Cfg::SPLIT ? it : (it >> 1);
                 wait(r_full(reg), use & 1u);
@@ -375,51 +383,43 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 const uint32_t tb = tmem + trow_off + (Cfg::SPLIT ? 0u : (uint32_t)reg * Cfg::R1_COL);
                 const int d0 = Cfg::SPLIT ? (rr == 0 ? 0 : Cfg::R0_DIAG) : 0;
                 const int d1 = Cfg::SPLIT ? (rr == 0 ? Cfg::R0_DIAG : Cfg::DIAG) : Cfg::DIAG;
-                // two 16-column loads per diagonal, one pair in flight while the previous is summed
-                uint32_t va[16], vb[16], vc[16], vd[16];
+                // one 16-column load per diagonal, the next in flight while one is summed
+                uint32_t va[16], vb[16];
                 tmem_ld16(tb + dcol<L>(d0), va);
-                tmem_ld16(tb + dcol<L>(d0) + 16, vb);
                 tmem_wait_ld();
 #pragma unroll
                 for (int d = 0; d < Cfg::DIAG; ++d) {
                     if (d < d0 || d >= d1) continue;
                     const bool odd = ((d - d0) & 1) != 0;
-                    uint32_t(&c0)[16] = odd ? vc : va;
-                    uint32_t(&c1)[16] = odd ? vd : vb;
-                    uint32_t(&n0)[16] = odd ? va : vc;
-                    uint32_t(&n1)[16] = odd ? vb : vd;
-                    if (d + 1 < d1) {  // in flight meanwhile
-                        tmem_ld16(tb + dcol<L>(d + 1), n0);
-                        tmem_ld16(tb + dcol<L>(d + 1) + 16, n1);
-                    }
+                    uint32_t(&cur)[16] = odd ? vb : va;
+                    uint32_t(&nxt)[16] = odd ? va : vb;
+                    if (d + 1 < d1) tmem_ld16(tb + dcol<L>(d + 1), nxt);  // in flight meanwhile
                     const long long rdd = (long long)P.rd[d];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        acc[j] += acc_int(c0[j]) * rdd;
-                        acc[16 + j] += acc_int(c1[j]) * rdd;
-                    }
+                    for (int j = 0; j < 16; ++j) acc[j] += acc_int(cur[j]) * rdd;
                     if (d + 1 < d1) tmem_wait_ld();
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(r_empty(reg));  // the region may be overwritten
             }
-            uint32_t res[32];
+            uint32_t res[16];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) res[j] = fp_reduce((uint64_t)(acc[j] + (long long)P.big), P.fp);
+            for (int j = 0; j < 16; ++j) res[j] = fp_reduce((uint64_t)(acc[j] + (long long)P.big), P.fp);
             const bool have_c = wait(c_full, ph);
-            // the thread's 32 columns are the C half `half`, row r: 128 bytes, 16-byte chunk j at
-            // chunk position j ^ (r mod 8)
-            unsigned char *crow = gbase + (sC - base) + (uint32_t)half * Cfg::C_HALF + r * 128u;
+            // columns 16 grp .. 16 grp + 15 are chunks 4 (grp & 1) .. + 3 of C half grp >> 1, row r:
+            // 128 bytes, 16-byte chunk j at chunk position j ^ (r mod 8)
+            unsigned char *crow = gbase + (sC - base) + (uint32_t)(grp >> 1) * Cfg::C_HALF + r * 128u;
             if (have_c) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    uint4 *q = reinterpret_cast<uint4 *>(crow + 16u * ((uint32_t)j ^ (r & 7u)));
+                for (int jj = 0; jj < 4; ++jj) {
+                    const uint32_t j = (uint32_t)(4 * (grp & 1) + jj);
+                    uint4 *q = reinterpret_cast<uint4 *>(crow + 16u * (j ^ (r & 7u)));
                     uint4 c = *q;
                     uint32_t *cw = reinterpret_cast<uint32_t *>(&c);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const uint32_t x = res[4 * j + e];
+                        const uint32_t x = res[4 * jj + e];
                         cw[e] = P.sub ? (cw[e] >= x ? cw[e] - x : cw[e] + P.fp.p - x) : fp_add(cw[e], x, P.fp);
                     }
                     *q = c;
