@@ -468,6 +468,34 @@ __global__ void k_digits(const uint32_t *__restrict__ src, uint64_t rs, uint64_t
     }
 }
 
+// The same planes when the source is row-major in K (src[k * ks + r], the columns of B as rows of
+// B^T): 32 x 32 tiles through shared memory, so that both the reads and the writes are coalesced.
+template <int L>
+__global__ void k_digits_t(const uint32_t *__restrict__ src, uint64_t ks, uint32_t R, uint32_t K,
+                           uint16_t *__restrict__ dst, uint64_t kpad, uint64_t plane, uint32_t p) {
+    __shared__ uint32_t tile[32][33];
+    const uint32_t r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    const uint32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (uint32_t kk = ty; kk < 32; kk += 8) {
+        const uint32_t k = k0 + kk, r = r0 + tx;
+        tile[kk][tx] = (k < K && r < R) ? src[(size_t)k * ks + r] : 0u;
+    }
+    __syncthreads();
+    const uint32_t T = L == 2 ? 32639u : 2139062143u;  // 127 (1 + 256 + ... + 256^{L-1})
+    for (uint32_t rr = ty; rr < 32; rr += 8) {
+        const uint32_t r = r0 + rr, k = k0 + tx;
+        if (r >= R || k >= K) continue;
+        const uint32_t x = tile[tx][rr];
+        int v = x <= T ? (int)x : (int)(x - p);
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const int a = l + 1 < L ? (int)(((uint32_t)v & 0xFFu) ^ 0x80u) - 0x80 : v;
+            if (l + 1 < L) v = (v - a) >> 8;
+            dst[(size_t)l * plane + (size_t)r * kpad + k] = (uint16_t)(__float_as_uint((float)a) >> 16);
+        }
+    }
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -530,6 +558,15 @@ void DigitPlanes::alloc(Arena &ar, uint32_t L_, uint64_t rows_, uint64_t K_, cud
 
 void to_digits(const uint32_t *src, uint64_t rs, uint64_t ks, const DigitPlanes &D, uint32_t p, cudaStream_t st) {
     if (!D.rows || !D.K) return;
+    if (rs == 1 && ks != 1) {  // K-strided source: transpose through shared memory
+        if ((D.K + 31) / 32 > 65535u) fail(GB_EUNSUPPORTED, "digit planes: K too large for one launch");
+        const dim3 grid((unsigned)((D.rows + 31) / 32), (unsigned)((D.K + 31) / 32));
+        const uint64_t plane = D.rows * D.kpad;
+        if (D.L == 2) k_digits_t<2><<<grid, 256, 0, st>>>(src, ks, (uint32_t)D.rows, (uint32_t)D.K, D.p, D.kpad, plane, p);
+        else k_digits_t<4><<<grid, 256, 0, st>>>(src, ks, (uint32_t)D.rows, (uint32_t)D.K, D.p, D.kpad, plane, p);
+        counted();
+        return;
+    }
     const dim3 grid((unsigned)((D.K + 255) / 256), (unsigned)std::min<uint64_t>(D.rows, 65535));
     const uint64_t plane = D.rows * D.kpad;
     if (D.L == 2) k_digits<2><<<grid, 256, 0, st>>>(src, rs, ks, (uint32_t)D.rows, (uint32_t)D.K, D.p, D.kpad, plane, p);
