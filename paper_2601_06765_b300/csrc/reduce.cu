@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include <cooperative_groups.h>
+
 #include "internal.hpp"
 
 namespace gb {
@@ -54,6 +56,7 @@ struct RedJob {
     const uint32_t *row_ptr, *col, *val, *pcols, *colpos, *nonpiv;
     uint32_t *U, *dprime;
     void *gacc;                // global accumulators, one row of N per block, when shared memory is short
+    uint32_t *split;           // k_reduce_cl: per pivot row, the first entry of each block's column range
     unsigned long long *work;  // [0] pivot rows applied, [1] modular multiply-adds
     uint32_t nA, nC, N, nb;
     Fp fp;
@@ -274,6 +277,225 @@ __global__ void __launch_bounds__(RT, 6) k_reduce(const RedJob *__restrict__ job
         const uint32_t c = J.nonpiv[jj];
         out[jj] = c < base ? 0u : MODE == A32 ? fp_reduce32((uint32_t)acc[c - base], fp) : fp_reduce(acc[c - base], fp);
     }
+}
+
+// ---- the same reduction with each row split over a thread-block cluster ------------------------
+//
+// When there are few non-pivot rows, one block per row leaves most SMs idle while each row sweeps
+// its chunks one after another.  Here a row is spread over a cluster of CS blocks: block q owns the
+// columns [q S, (q + 1) S) (S = ceil(N / CS)) in its shared memory, and split[k][q] gives the first
+// entry of pivot row k at or right of q S (computed once per matrix).  Per chunk, the owners of the
+// chunk's pivot columns publish their values into block 0's shared memory (distributed shared
+// memory), one cluster barrier makes them visible, every block forms the same 32 multipliers and
+// applies the part of each pivot row that falls in its own columns.  One cluster barrier per chunk.
+constexpr int CS = 8;  // blocks per row
+
+// split[k][q] = first entry of pivot row k with column >= q S, q = 0..CS (warp per pivot row)
+__global__ void k_split(const RedJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    const int jb = job_of_block(bstart, nj);
+    const RedJob &J = jobs[jb];
+    const uint32_t k = (blockIdx.x - bstart[jb]) * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= J.nA || lane > CS) return;
+    const uint32_t S = (J.N + CS - 1) / CS, x = lane * S;
+    uint32_t lo = J.row_ptr[k], hi = J.row_ptr[k + 1];
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (J.col[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    J.split[(size_t)k * (CS + 1) + lane] = lo;
+}
+
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *__restrict__ a, uint32_t lo, uint32_t hi,
+                                                    uint32_t x) {
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int job_of(const uint32_t *__restrict__ bstart, int nj, uint32_t b) {
+    int lo = 0, hi = nj - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bstart[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MODE>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(RT)
+    k_reduce_cl(const RedJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    using Acc = typename AccOf<MODE>::type;
+    constexpr bool SMALLP = MODE != M64;
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t Us[2][CW * CW];
+    __shared__ uint32_t xs[2][CW];  // block 0's copy: the chunk's pivot-column values
+    __shared__ uint32_t seg_q[CW], seg_m[CW], seg_pre[CW + 1];
+    __shared__ uint32_t s_nseg;
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t q = cl.block_rank();
+    uint32_t *xs0 = cl.map_shared_rank(&xs[0][0], 0);
+    const uint32_t rb = blockIdx.x / CS;  // the row's cluster
+    const int jb = job_of(bstart, nj, rb);
+    const RedJob &J = jobs[jb];
+    const Fp fp = J.fp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t i = rb - bstart[jb], row = J.nA + i;
+    const uint32_t a0 = J.row_ptr[row], b0 = J.row_ptr[row + 1];
+    const uint32_t base = a0 < b0 ? J.col[a0] : J.N, span = (J.N + CS - 1) / CS;
+    const uint32_t lo = min(q * span, J.N), hi = min(lo + span, J.N), width = hi - lo;
+    Acc *acc = reinterpret_cast<Acc *>(smem_raw);  // column c at acc[c - lo]
+    for (uint32_t j = threadIdx.x; j < width; j += RT) acc[j] = 0;
+    __syncthreads();
+    {
+        const uint32_t ea = lower_bound_u32(J.col, a0, b0, lo), eb = lower_bound_u32(J.col, ea, b0, hi);
+        for (uint32_t e = ea + threadIdx.x; e < eb; e += RT) acc[J.col[e] - lo] = J.val[e];
+    }
+    // first chunk holding a pivot column >= base (the same in every block of the cluster)
+    const uint32_t k0 = (lower_bound_u32(J.pcols, 0, J.nA, base) / CW) * CW;
+    if (k0 < J.nA)
+        for (uint32_t t = threadIdx.x; t < CW * CW; t += RT) Us[0][t] = J.U[(size_t)(k0 / CW) * CW * CW + t];
+    unsigned long long applied = 0, fmas = 0;
+    for (uint32_t kc = k0, buf = 0; kc < J.nA; kc += CW, buf ^= 1) {
+        const uint32_t cnt = min((uint32_t)CW, J.nA - kc);
+        __syncthreads();  // this block's updates of the previous chunk (and this chunk's U) are done
+        if (warp == 0) {
+            // publish the values this block owns (a column left of the row's leading column holds
+            // zero: no pivot row with a nonzero multiplier reaches it); block 0 writes the zeros of
+            // lanes past the chunk
+            uint32_t v = 0;
+            bool mine = q == 0;
+            if ((uint32_t)lane < cnt) {
+                const uint32_t c = J.pcols[kc + lane];
+                mine = c >= lo && c < hi;
+                if (mine) {
+                    const Acc a = acc[c - lo];
+                    v = MODE == A32 ? fp_reduce32((uint32_t)a, fp) : fp_reduce((unsigned long long)a, fp);
+                }
+            }
+            if (mine) xs0[buf * CW + lane] = v;
+        }
+        cl.sync();  // every block's values of this chunk are in block 0
+        if (warp == 0) {
+            // the chunk's multipliers f = x U^{-1} (the same in every block), then this block's part
+            // of each pivot row with f != 0 as a segment of its CSR range
+            const uint32_t x = xs0[buf * CW + lane];
+            const uint32_t *Wc = Us[buf];
+            unsigned long long sacc = 0;
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+                const uint32_t vj = __shfl_sync(0xffffffffu, x, j);
+                const uint32_t w = Wc[j * CW + lane];
+                if (SMALLP) sacc += (unsigned long long)(vj * w);
+                else sacc += fp_redc((uint64_t)vj * w, fp);
+            }
+            const uint32_t f = (uint32_t)lane < cnt ? fp_reduce(sacc, fp) : 0u;
+            uint32_t ea = 0, len = 0;
+            if (f) {
+                const uint32_t *sp = J.split + (size_t)(kc + lane) * (CS + 1) + q;
+                ea = sp[0];
+                len = sp[1] - ea;
+            }
+            const unsigned segmask = __ballot_sync(0xffffffffu, len != 0u);
+            uint32_t end = len;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, end, d);
+                if (lane >= d) end += y;
+            }
+            if (len) {
+                // segments in lane order; the prefix over all lanes counts only those with entries
+                const uint32_t pos = __popc(segmask & ((1u << lane) - 1u));
+                seg_q[pos] = ea;
+                seg_m[pos] = SMALLP ? fp.p - f : fp_to_mont(fp.p - f, fp);
+                seg_pre[pos + 1] = end;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, end, 31);
+            const unsigned fmask = __ballot_sync(0xffffffffu, f != 0u);
+            if (lane == 0) {
+                seg_pre[0] = 0;
+                s_nseg = __popc(segmask);
+                if (q == 0) applied += __popc(fmask);  // pivot rows used: counted once per row
+                fmas += total;                          // multiply-adds: each block its own part
+            }
+        } else {
+            const uint32_t kn = kc + CW;
+            if (kn < J.nA)
+                for (uint32_t t = threadIdx.x - 32u; t < CW * CW; t += RT - 32u)
+                    Us[buf ^ 1][t] = J.U[(size_t)(kn / CW) * CW * CW + t];
+        }
+        __syncthreads();
+        // apply this block's segments: entries flattened and split evenly over the warps
+        const uint32_t nseg = s_nseg, total = seg_pre[nseg];
+        const uint32_t per = (total + RT - 1) / RT * 32;
+        const uint32_t w0 = min(warp * per, total), w1 = min(w0 + per, total);
+        uint32_t sg = 0, send = 0, soff = 0, smul = 0;
+        if (w0 + lane < w1) {
+            uint32_t a = 0, b = nseg - 1;
+            while (a < b) {
+                const uint32_t mid = (a + b + 1) >> 1;
+                if (seg_pre[mid] <= w0 + lane) a = mid; else b = mid - 1;
+            }
+            sg = a;
+            send = seg_pre[sg + 1];
+            soff = seg_q[sg] - seg_pre[sg];
+            smul = seg_m[sg];
+        }
+        for (uint32_t x0 = w0; x0 < w1; x0 += 4 * 32) {
+            uint32_t cc[4], vv[4], mm[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t x = x0 + 32u * u + lane;
+                cc[u] = 0xFFFFFFFFu;
+                vv[u] = mm[u] = 0u;
+                if (x < w1) {
+                    while (x >= send) {
+                        ++sg;
+                        send = seg_pre[sg + 1];
+                        soff = seg_q[sg] - seg_pre[sg];
+                        smul = seg_m[sg];
+                    }
+                    cc[u] = J.col[soff + x];
+                    vv[u] = J.val[soff + x];
+                    mm[u] = smul;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (cc[u] == 0xFFFFFFFFu) continue;
+                Acc *dst = acc + (cc[u] - lo);
+                if (MODE == A32)
+                    atomicAdd(reinterpret_cast<uint32_t *>(dst), fp_reduce32(mm[u] * vv[u], fp));
+                else if (MODE == A64)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)(mm[u] * vv[u]));
+                else
+                    atomicAdd(reinterpret_cast<unsigned long long *>(dst),
+                              (unsigned long long)fp_redc((uint64_t)mm[u] * vv[u], fp));
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (applied || fmas)) {
+        atomicAdd(&J.work[0], applied);
+        atomicAdd(&J.work[1], fmas);
+    }
+    // this block's columns of D' (zero left of the row's leading column)
+    uint32_t *out = J.dprime + (size_t)i * J.nb;
+    const uint32_t jlo = lower_bound_u32(J.nonpiv, 0, J.nb, lo);
+    const uint32_t jhi = lower_bound_u32(J.nonpiv, jlo, J.nb, hi);
+    for (uint32_t jj = jlo + threadIdx.x; jj < jhi; jj += RT) {
+        const uint32_t c = J.nonpiv[jj];
+        if (c < base) {
+            out[jj] = 0u;
+        } else {
+            const Acc a = acc[c - lo];
+            out[jj] = MODE == A32 ? fp_reduce32((uint32_t)a, fp) : fp_reduce((unsigned long long)a, fp);
+        }
+    }
+    cl.sync();  // block 0's shared memory stays valid until every block has read its last chunk
 }
 
 // ---- RREF(D'): right-looking Gauss-Jordan by panels of KP rows --------------------------------
@@ -635,6 +857,15 @@ struct Grouped {
     }
 };
 
+// Rows split over clusters when the per-row sweep, not the GPU's width, bounds the time: measured
+// on B300 (n=10 workload), 1.8x faster at 9 rows and 1.5x at 81, slower from about 300 rows (a
+// cluster barrier per chunk and the multipliers formed in every block), and slower on short sweeps
+// (fewer than 2048 pivots).  `rows` counts the non-pivot rows of all sparse matrices of the launch.
+bool use_cluster(const RedJob &J, size_t accb, uint64_t rows) {
+    const size_t per_block = (size_t)((J.N + CS - 1) / CS) * accb;
+    return per_block <= 48 * 1024 && rows <= 160 && J.nA >= 2048;
+}
+
 }  // namespace
 
 std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaulay *> &Ms, bool echelon) {
@@ -664,7 +895,8 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         GB_CUDA(cudaMemsetAsync(Ubuf[j].p, 0, 4ull * nchunks * CW * CW, st));
         RedJob &J = R[j];
         J = RedJob{Mac->row_ptr.p, Mac->col.p, Mac->val.p, Mac->pcols.p, Mac->colpos.p, Mac->nonpiv.p,
-                   Ubuf[j].p, E->dprime.p, nullptr, work.p + 2 * j, Mac->nA, Mac->nC, Mac->ndict, Mac->nb, S->fp};
+                   Ubuf[j].p, E->dprime.p, nullptr, nullptr, work.p + 2 * j, Mac->nA, Mac->nC, Mac->ndict, Mac->nb,
+                   S->fp};
         mode[j] = !S->fp.small ? M64 : (Mac->nA < 65536u ? A32 : A64);
         Es.push_back(std::move(E));
     }
@@ -693,13 +925,21 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
     // accumulators: shared memory per block when N fits, else one global row per block; launch
     // groups by mode and by the shared-memory size class (powers of two)
     std::vector<DBuf<unsigned char>> gbuf(nj);
+    std::vector<DBuf<uint32_t>> sbuf(nj);
+    uint64_t sparse_rows = 0;
+    for (int j = 0; j < nj; ++j)
+        if (R[j].nC && R[j].nb && !dense[j]) sparse_rows += R[j].nC;
     std::map<std::pair<int, int>, std::vector<int>> groups;  // (mode, size class or -1) -> jobs
     for (int j = 0; j < nj; ++j) {
         if (!R[j].nC || !R[j].nb || dense[j]) continue;
         const size_t accb = mode[j] == A32 ? 4 : 8;
         const size_t bytes = (size_t)R[j].N * accb;
         int cls = -1;
-        if (bytes <= 200 * 1024) {
+        if (use_cluster(R[j], accb, sparse_rows)) {
+            cls = -2;  // rows split over clusters of CS blocks (k_reduce_cl)
+            sbuf[j].alloc(ar, (size_t)std::max<uint32_t>(R[j].nA, 1) * (CS + 1), st);
+            R[j].split = sbuf[j].p;
+        } else if (bytes <= 200 * 1024) {
             cls = 0;
             while (((size_t)1024 << cls) < bytes) ++cls;
         } else {
@@ -709,15 +949,16 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         groups[{mode[j], cls}].push_back(j);
     }
     {
-        std::vector<uint32_t> tri(nj), inv(nj);
+        std::vector<uint32_t> tri(nj), inv(nj), spl(nj, 0);
         for (int j = 0; j < nj; ++j) {
             tri[j] = blocks(R[j].nA, 8);
             inv[j] = blocks(((size_t)R[j].nA + CW - 1) / CW, IW);
+            if (R[j].split) spl[j] = blocks(R[j].nA, 8);
         }
-        std::vector<std::vector<uint32_t>> per{tri, inv};
+        std::vector<std::vector<uint32_t>> per{tri, inv, spl};
         for (auto &g : groups) {
             std::vector<uint32_t> rows(nj, 0);
-            for (int j : g.second) rows[j] = R[j].nC;
+            for (int j : g.second) rows[j] = R[j].nC;  // blocks, or clusters of CS blocks for class -2
             per.push_back(rows);
         }
         Grouped<RedJob> G;
@@ -726,6 +967,10 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             k_build_chunk_tri<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
             k_invert_chunk_tri<<<G.totals[1], IW * 32, 0, st>>>(G.jobs, G.plans[1], nj);
             counted(2);
+        }
+        if (G.totals[2]) {
+            k_split<<<G.totals[2], 256, 0, st>>>(G.jobs, G.plans[2], nj);
+            counted();
         }
         GB_CUDA(cudaEventRecord(ctx->ev[5], st));
         for (int j = 0; j < nj; ++j) {
@@ -745,9 +990,24 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             D.work = J.work;
             reduce_dense(D, J.dprime, ar, derr.p, st);
         }
-        size_t gi = 2;
+        size_t gi = 3;
         for (auto &g : groups) {
             const int md = g.first.first, cls = g.first.second;
+            if (cls == -2) {
+                size_t dyn = 0;
+                for (int j : g.second)
+                    dyn = std::max<size_t>(dyn, (size_t)((R[j].N + CS - 1) / CS) * (md == A32 ? 4 : 8));
+                auto goc = [&](auto kern) {
+                    opt_in_smem(reinterpret_cast<const void *>(kern));
+                    kern<<<G.totals[gi] * CS, RT, dyn, st>>>(G.jobs, G.plans[gi], nj);
+                    counted();
+                };
+                if (md == A32) goc(k_reduce_cl<A32>);
+                else if (md == A64) goc(k_reduce_cl<A64>);
+                else goc(k_reduce_cl<M64>);
+                ++gi;
+                continue;
+            }
             const bool smem = cls >= 0;
             size_t dyn = 0;
             if (smem)
@@ -1147,7 +1407,7 @@ void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint3
         RedJob job;
         uint32_t tri_start[2], inv_start[2], red_start[2];
     } tb{};
-    tb.job = RedJob{row_ptr, col, val, pcols, colpos, nonpiv, tri, dprime, nullptr, work, nA, nC, N, nb, fp};
+    tb.job = RedJob{row_ptr, col, val, pcols, colpos, nonpiv, tri, dprime, nullptr, nullptr, work, nA, nC, N, nb, fp};
     tb.tri_start[1] = blocks(nA, 8);
     tb.inv_start[1] = blocks(nchunks, IW);
     tb.red_start[1] = nC;
