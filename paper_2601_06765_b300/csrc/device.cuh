@@ -128,18 +128,27 @@ __device__ __forceinline__ uint32_t byte_of(uint4 m, int i) {
 // of Sec. 11),
 // so it serves as MonKey, and as a bitmap index in [0, C(n + D, n)) for degrees <= D.
 //
-// tab (shared memory): tab[d] = C(n + d - 1, n) for d in [0, D], then for j = 1..n-1 the row
-// tab[(D+1) * j + s] = C(s + j - 1, j) for s in [0, D].
-__device__ __forceinline__ uint32_t mono_rank(uint4 m, const uint32_t *tab, int n, int D1) {
-    uint32_t r = 0, s = 0;
-    uint32_t w[4] = {m.x, m.y, m.z, m.w};
+// tab (shared memory), rows of 2^sh entries: row 0 holds tab[d] = C(n + d - 1, n) for d in [0, D],
+// row j = 1..n-1 holds tab[(j << sh) + s] = C(s + j - 1, j) for s in [0, D] (2^sh > D).
+// The prefix sums S_j come four at a time from one multiply: byte k of w * 0x01010101 is the sum of
+// bytes 0..k of w (no byte carries: every S_j <= D <= 255), and the running total is added to every
+// byte of the next word the same way.
+__device__ __forceinline__ uint32_t mono_rank(uint4 m, const uint32_t *tab, int n, int sh) {
+    const uint32_t p0 = m.x * 0x01010101u;
+    const uint32_t p1 = m.y * 0x01010101u + (p0 >> 24) * 0x01010101u;
+    const uint32_t p2 = m.z * 0x01010101u + (p1 >> 24) * 0x01010101u;
+    const uint32_t p3 = m.w * 0x01010101u + (p2 >> 24) * 0x01010101u;
+    uint32_t r = 0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        if (i >= n) break;
-        if (i >= 1) r += tab[D1 * i + s];
-        s += (w[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+    for (int j = 1; j < 16; ++j) {
+        if (j >= n) break;
+        const uint32_t w = j <= 4 ? p0 : j <= 8 ? p1 : j <= 12 ? p2 : p3;  // S_j is byte j - 1
+        const uint32_t sj = (w >> (8 * ((j - 1) & 3))) & 0xFFu;
+        r += tab[(j << sh) + sj];
     }
-    return r + tab[s];
+    const uint32_t d = __dp4a(m.x, 0x01010101u, 0u) + __dp4a(m.y, 0x01010101u, 0u) +
+                       __dp4a(m.z, 0x01010101u, 0u) + __dp4a(m.w, 0x01010101u, 0u);
+    return r + tab[d];
 }
 
 __device__ __forceinline__ uint32_t mono_deg(uint4 m) {

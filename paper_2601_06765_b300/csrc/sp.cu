@@ -52,7 +52,7 @@ struct Job {
     // keys
     uint32_t *bits;
     const uint32_t *tab;
-    int n, D1, tabsz;
+    int n, sh, tabsz;  // table rows of 2^sh entries
     uint32_t W;
     // closure
     const uint32_t *nr_idx;
@@ -123,7 +123,7 @@ __device__ __forceinline__ void expand_terms(uint4 t, uint32_t off, uint32_t j0,
         uint32_t r = 0;
         if (j < len) {
             m = mono_mul(t, J.bmon[off + j]);
-            r = mono_rank(m, tab, J.n, J.D1);
+            r = mono_rank(m, tab, J.n, J.sh);
             isnew = test_and_set(J.bits, r);
         }
         push_new(isnew, m, r, J);
@@ -143,7 +143,7 @@ __global__ void k_mark_given(const Job *__restrict__ jobs, const uint32_t *__res
         return;
     }
     const uint4 m = mono_mul(J.gt[i], J.bmon[J.boff[J.gk[i]]]);
-    const uint32_t r = mono_rank(m, tab, J.n, J.D1);
+    const uint32_t r = mono_rank(m, tab, J.n, J.sh);
     atomicOr(&J.bits[r >> 5], 1u << (r & 31));
     J.lm_rank[i] = r;
 }
@@ -305,11 +305,25 @@ __global__ void k_fill(const Job *__restrict__ jobs, const uint32_t *__restrict_
         if (lane == 0) atomicOr(&J.cnt->err, 32u);
         return;
     }
-    for (uint32_t j = lane; j < len; j += 32) {
-        const uint4 m = mono_mul(t, J.bmon[off + j]);
-        const uint32_t r = mono_rank(m, tab, J.n, J.D1);
-        J.col[s + j] = col_of(J, r);
-        J.val[s + j] = J.bcf[off + j];
+    // four terms per lane in flight: their ranks and dictionary lookups are independent
+    for (uint32_t j0 = lane; j0 < len; j0 += 4 * 32) {
+        uint32_t r[4], v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = j0 + 32u * u;
+            if (j < len) {
+                r[u] = mono_rank(mono_mul(t, J.bmon[off + j]), tab, J.n, J.sh);
+                v[u] = J.bcf[off + j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = j0 + 32u * u;
+            if (j < len) {
+                J.col[s + j] = col_of(J, r[u]);
+                J.val[s + j] = v[u];
+            }
+        }
     }
 }
 
@@ -337,7 +351,7 @@ uint64_t binom(uint32_t a, uint32_t b) {
 
 // host part of one job
 struct SpHost {
-    uint32_t D = 0, D1 = 0, W = 0, ng = 0, npiv_given = 0, nnp = 0, tabsz = 0;
+    uint32_t D = 0, D1 = 0, sh = 0, W = 0, ng = 0, npiv_given = 0, nnp = 0, tabsz = 0;
     uint64_t space = 0, nnz_given = 0, cap = 0;
     std::vector<uint32_t> tab, np_index;
     std::vector<uint4> gt, nlm;
@@ -376,11 +390,13 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         if (h.space >= (1ull << 32) - 64)
             fail(GB_EUNSUPPORTED, "monomial space C(n+D, n) above 2^32 for the dense grevlex keys");
         h.D1 = h.D + 1;
+        h.sh = 0;
+        while ((1u << h.sh) < h.D1) ++h.sh;
         h.W = (uint32_t)((h.space + 31) / 32);
-        h.tab.assign((size_t)h.D1 * n, 0);
+        h.tab.assign((size_t)n << h.sh, 0);
         for (uint32_t d = 0; d <= h.D; ++d) h.tab[d] = (uint32_t)(d ? binom(n + d - 1, n) : 0);
         for (int i = 1; i < n; ++i)
-            for (uint32_t s = 0; s <= h.D; ++s) h.tab[(size_t)h.D1 * i + s] = (uint32_t)binom(s + i - 1, i);
+            for (uint32_t s = 0; s <= h.D; ++s) h.tab[((size_t)i << h.sh) + s] = (uint32_t)binom(s + i - 1, i);
         h.tabsz = (uint32_t)h.tab.size();
         h.np_index.assign(h.ng, 0xFFFFFFFFu);
         h.gt.resize(h.ng);
@@ -450,7 +466,7 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         J.bits = h.bits.p;
         J.tab = reinterpret_cast<const uint32_t *>(dptr(h.o_tab));
         J.n = (int)S->n;
-        J.D1 = (int)h.D1;
+        J.sh = (int)h.sh;
         J.tabsz = (int)h.tabsz;
         J.W = h.W;
         J.nr_idx = reinterpret_cast<const uint32_t *>(dptr(h.o_nri));
