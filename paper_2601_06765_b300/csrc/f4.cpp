@@ -224,17 +224,31 @@ static void gm_update(gb_system *S, uint32_t h) {
     auto coprime = [&](uint32_t a) -> bool {
         return swar ? coprime16(lh16, S->lm16[a]) : mono_coprime(lh, S->lm[a], n);
     };
-    std::vector<uint32_t> C;
-    C.reserve(h);
+    // per-thread scratch, reused across calls (the batch runs systems on several host threads)
+    struct Scratch {
+        std::vector<uint32_t> C, Ld, ord, cnt, und, slot;
+        std::vector<M16> L, mins;
+        std::vector<char> kept, cop, dom;
+    };
+    static thread_local Scratch z;
+    std::vector<uint32_t> &C = z.C;
+    C.clear();
     for (uint32_t g = 0; g < h; ++g)
         if (!S->redundant[g]) C.push_back(g);
     const size_t c = C.size();
-    std::vector<M16> L(c);
-    std::vector<uint32_t> Ld(c);
-    std::vector<char> kept(c, 0), cop(c, 0), dom(c, 0);
+    z.L.resize(c);
+    z.Ld.resize(c);
+    z.kept.assign(c, 0);
+    z.cop.assign(c, 0);
+    z.dom.assign(c, 0);
+    std::vector<M16> &L = z.L;
+    std::vector<uint32_t> &Ld = z.Ld;
+    std::vector<char> &kept = z.kept, &cop = z.cop, &dom = z.dom;
+    uint32_t dmax = 0;
     for (size_t a = 0; a < c; ++a) {
         L[a] = lcm_of(h, C[a]);
         Ld[a] = deg16(L[a]);
+        dmax = std::max(dmax, Ld[a]);
         cop[a] = coprime(C[a]);
     }
     // The new pairs (h, g) are taken oldest g first: one is kept when its leading monomials are
@@ -244,10 +258,15 @@ static void gm_update(gb_system *S, uint32_t h) {
     // divides its lcm, no later pair has the same lcm, and no coprime pair has the same lcm.  A
     // strict divisor has lower degree, and when there is one, one of the minimal lcms of lower
     // degree divides too; so the pairs are visited by degree against the minimal lcms found so far.
-    std::vector<uint32_t> ord(c);
-    std::iota(ord.begin(), ord.end(), 0u);
-    std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return Ld[x] < Ld[y]; });
-    std::vector<M16> mins;
+    // Visit order: by degree, then index (a counting sort: degrees are small).
+    std::vector<uint32_t> &ord = z.ord, &cnt = z.cnt;
+    cnt.assign(dmax + 2, 0);
+    for (size_t a = 0; a < c; ++a) ++cnt[Ld[a] + 1];
+    for (uint32_t d = 0; d <= dmax; ++d) cnt[d + 1] += cnt[d];
+    ord.resize(c);
+    for (uint32_t a = 0; a < c; ++a) ord[cnt[Ld[a]]++] = a;
+    std::vector<M16> &mins = z.mins;
+    mins.clear();
     for (size_t s0 = 0; s0 < c;) {
         size_t e = s0;
         while (e < c && Ld[ord[e]] == Ld[ord[s0]]) ++e;
@@ -269,25 +288,33 @@ static void gm_update(gb_system *S, uint32_t h) {
         }
         s0 = e;
     }
-    // equal lcms among the undominated pairs: sort by lcm, then index
-    std::vector<uint32_t> und;
+    // equal lcms among the undominated pairs: an open-addressing table keyed by the lcm keeps, per
+    // lcm, its largest index and whether a coprime pair has it
+    std::vector<uint32_t> &und = z.und, &slot = z.slot;
+    und.clear();
     for (uint32_t a = 0; a < c; ++a)
         if (!dom[a]) und.push_back(a);
-    std::sort(und.begin(), und.end(), [&](uint32_t x, uint32_t y) {
-        if (L[x].hi != L[y].hi) return L[x].hi < L[y].hi;
-        if (L[x].lo != L[y].lo) return L[x].lo < L[y].lo;
-        return x < y;
-    });
-    for (size_t s0 = 0; s0 < und.size();) {
-        size_t e = s0;
-        bool anycop = false;
-        while (e < und.size() && L[und[e]] == L[und[s0]]) anycop = anycop || cop[und[e++]];
-        for (size_t q = s0; q < e; ++q) {
-            const uint32_t a = und[q];
-            kept[a] = cop[a] || (q + 1 == e && !anycop);
+    size_t cap = 16;
+    while (cap < 2 * und.size()) cap <<= 1;
+    slot.assign(cap, UINT32_MAX);  // index of the group's largest member (flags in cop/kept below)
+    std::vector<char> &anyc = dom;   // reused: dom is no longer needed for undominated indices
+    for (uint32_t a : und) anyc[a] = 0;
+    for (uint32_t a : und) {
+        const uint64_t hsh = (L[a].lo * 0x9E3779B97F4A7C15ull) ^ (L[a].hi * 0xC2B2AE3D27D4EB4Full);
+        size_t k = (size_t)(hsh >> 20) & (cap - 1);
+        while (slot[k] != UINT32_MAX && !(L[slot[k]] == L[a])) k = (k + 1) & (cap - 1);
+        if (slot[k] == UINT32_MAX) {
+            slot[k] = a;
+            anyc[a] = cop[a];
+        } else {
+            const uint32_t b0 = slot[k];
+            const char any = anyc[b0] || cop[a];
+            slot[k] = std::max(b0, a);
+            anyc[slot[k]] = any;
         }
-        s0 = e;
     }
+    for (size_t k = 0; k < cap; ++k)
+        if (slot[k] != UINT32_MAX && !anyc[slot[k]]) kept[slot[k]] = 1;  // the last of its lcm
     for (uint32_t a = 0; a < c; ++a)
         if (cop[a]) kept[a] = 1;
     // old pairs whose lcm LM(h) divides, with both lcm(g1, h) and lcm(g2, h) different, go
@@ -300,14 +327,8 @@ static void gm_update(gb_system *S, uint32_t h) {
     }
     S->pairs.resize(w);
     // kept new pairs, except those with coprime leading monomials (Buchberger's product criterion)
-    for (size_t a = 0; a < C.size(); ++a)
-        if (kept[a] && !cop[a]) {
-            PairL pr{C[a], h, 0, 0, L[a]};
-            Mono l;
-            std::memcpy(l.e, &L[a], 16);
-            pr.deg = (uint32_t)mono_deg(l, n);
-            S->pairs.push_back(pr);
-        }
+    for (size_t a = 0; a < c; ++a)
+        if (kept[a] && !cop[a]) S->pairs.push_back(PairL{C[a], h, Ld[a], 0, L[a]});
     for (uint32_t g = 0; g < h; ++g)
         if (!S->redundant[g] && divides(lh16, S->lm16[g])) S->redundant[g] = 1;
 }
