@@ -68,8 +68,10 @@ typedef struct {
                             of each system for gb_system_last_step (costs memory);
                             GB_CTX_REDUCE_SPARSE / GB_CTX_REDUCE_DENSE: reduce every matrix
                             row by row (sparse), or by dense blocked elimination on the tensor
-                            cores whenever the arena has room; neither: chosen per matrix by
-                            its shape.  Both give the same (unique) D'. */
+                            cores whenever the arena has room (DENSE also runs every panel
+                            update of the echelon form of D' on the tensor cores); neither:
+                            chosen per matrix by its shape.  All give the same (unique) D' and
+                            RREF(D'). */
     uint32_t reserved;
 } gb_ctx_opts;
 

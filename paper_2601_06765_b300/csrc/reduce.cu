@@ -520,6 +520,10 @@ struct RrefJob {
     uint32_t *out, *opiv;
     uint32_t nC, nb, rank;
     Fp fp;
+    uint64_t ldm;         // row pitch of M (nb rounded up to 4: rows start on 16-byte boundaries)
+    uint32_t tc;          // 1: the trailing update of this job runs on the tensor cores (k_mm)
+    uint16_t *fa, *fb;    // tc: digit planes of the multipliers (nC x KP) and of the pivot rows (nb x KP)
+    uint64_t fkp;         // tc: their row pitch (KP rounded up to 64)
 };
 
 __device__ __forceinline__ uint32_t block_min(uint32_t v, uint32_t *red) {
@@ -541,7 +545,7 @@ __global__ void k_leads(const RrefJob *__restrict__ jobs, const uint32_t *__rest
     const int jb = job_of_block(bstart, nj);
     const RrefJob &X = jobs[jb];
     const uint32_t r = blockIdx.x - bstart[jb];
-    const uint32_t *row = X.M + (size_t)r * X.nb;
+    const uint32_t *row = X.M + (size_t)r * X.ldm;
     uint32_t c = NOLEAD;
     for (uint32_t j = threadIdx.x; j < X.nb; j += blockDim.x)
         if (row[j]) { c = j; break; }
@@ -605,11 +609,11 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
     const Fp fp = X.fp;
     const uint32_t P = X.state[1], nb = X.nb;
     auto rowp = [&](uint32_t t) -> uint32_t * {
-        return SMEM ? pan + (size_t)t * nb : X.M + (size_t)X.panel[t] * nb;
+        return SMEM ? pan + (size_t)t * nb : X.M + (size_t)X.panel[t] * X.ldm;
     };
     if (SMEM) {
         for (uint32_t t = 0; t < P; ++t) {
-            const uint32_t *src = X.M + (size_t)X.panel[t] * nb;
+            const uint32_t *src = X.M + (size_t)X.panel[t] * X.ldm;
             for (uint32_t j = threadIdx.x; j < nb; j += PT) pan[(size_t)t * nb + j] = src[j];
         }
         __syncthreads();
@@ -674,7 +678,7 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
     }
     if (SMEM) {  // write the panel back (pivot rows reduced, the others now zero)
         for (uint32_t t = 0; t < P; ++t) {
-            uint32_t *dst = X.M + (size_t)X.panel[t] * nb;
+            uint32_t *dst = X.M + (size_t)X.panel[t] * X.ldm;
             for (uint32_t j = threadIdx.x; j < nb; j += PT) dst[j] = pan[(size_t)t * nb + j];
         }
     }
@@ -699,9 +703,9 @@ __global__ void k_eliminate(const RrefJob *__restrict__ jobs, const uint32_t *__
     const RrefJob &X = jobs[jb];
     const Fp fp = X.fp;
     const uint32_t r = blockIdx.x - bstart[jb], nb = X.nb, nnew = X.state[2];
-    if (nnew == 0 || X.lead[r] == NOLEAD) return;
+    if (X.tc || nnew == 0 || X.lead[r] == NOLEAD) return;
     const uint32_t pr = X.pcol[r];
-    uint32_t *row = X.M + (size_t)r * nb;
+    uint32_t *row = X.M + (size_t)r * X.ldm;
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
     if (threadIdx.x < nnew) {
@@ -717,10 +721,10 @@ __global__ void k_eliminate(const RrefJob *__restrict__ jobs, const uint32_t *__
         uint64_t acc = row[j];
         if (fp.small) {  // at most KP raw products below 2^32 each
             for (uint32_t k = 0; k < nnew; ++k)
-                if (m[k]) acc += (uint64_t)((fp.p - m[k]) * X.M[(size_t)q[k] * nb + j]);
+                if (m[k]) acc += (uint64_t)((fp.p - m[k]) * X.M[(size_t)q[k] * X.ldm + j]);
         } else {
             for (uint32_t k = 0; k < nnew; ++k)
-                if (m[k]) acc += fp_mul(fp.p - m[k], X.M[(size_t)q[k] * nb + j], fp);
+                if (m[k]) acc += fp_mul(fp.p - m[k], X.M[(size_t)q[k] * X.ldm + j], fp);
         }
         const uint32_t x = fp_reduce(acc, fp);
         row[j] = x;
@@ -730,6 +734,50 @@ __global__ void k_eliminate(const RrefJob *__restrict__ jobs, const uint32_t *__
         c = block_min(c, red);
         if (threadIdx.x == 0) X.lead[r] = c;
     }
+}
+
+// The same trailing update on the tensor cores for large D': M <- M - F Q with F[r][k] = M[r][pc_k]
+// (zero on the panel's own pivot rows and for k past the new pivots) and Q the new pivot rows.
+// Digit planes of F (row r, K index k) and of Q^T (row j, K index k); KP K values, zero past nnew.
+template <int L>
+__global__ void k_elim_digits(const RrefJob *__restrict__ jobs, int jb) {
+    const RrefJob &X = jobs[jb];
+    const uint32_t nnew = X.state[2];
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t T = L == 2 ? 32639u : 2139062143u;  // 127 (1 + 256 + ... + 256^{L-1})
+    auto put = [&](uint32_t x, uint16_t *dst, uint64_t plane) {
+        int v = x <= T ? (int)x : (int)(x - X.fp.p);
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const int a = l + 1 < L ? (int)(((uint32_t)v & 0xFFu) ^ 0x80u) - 0x80 : v;
+            if (l + 1 < L) v = (v - a) >> 8;
+            dst[(size_t)l * plane] = (uint16_t)(__float_as_uint((float)a) >> 16);
+        }
+    };
+    if (t < X.nC * KP) {  // F: row r, column k
+        const uint32_t r = t / KP, k = t % KP;
+        uint32_t x = 0;
+        if (k < nnew && X.panel[KP + k] != r) x = X.M[(size_t)r * X.ldm + X.panel[2 * KP + k]];
+        put(x, X.fa + (size_t)r * X.fkp + k, (uint64_t)X.nC * X.fkp);
+    } else if (t < X.nC * KP + X.nb * KP) {  // Q^T: row j, column k
+        const uint32_t u = t - X.nC * KP, j = u / KP, k = u % KP;
+        const uint32_t x = k < nnew ? X.M[(size_t)X.panel[KP + k] * X.ldm + j] : 0u;
+        put(x, X.fb + (size_t)j * X.fkp + k, (uint64_t)X.nb * X.fkp);
+    }
+}
+
+// leading columns of the rows that are not pivots, after a tensor-core update (block per row)
+__global__ void k_leads_np(const RrefJob *__restrict__ jobs, int jb) {
+    __shared__ uint32_t red[32];
+    const RrefJob &X = jobs[jb];
+    const uint32_t r = blockIdx.x;
+    if (X.state[2] == 0 || X.lead[r] == NOLEAD || X.pcol[r] != NOLEAD) return;  // uniform per block
+    const uint32_t *row = X.M + (size_t)r * X.ldm;
+    uint32_t c = NOLEAD;
+    for (uint32_t j = threadIdx.x; j < X.nb; j += blockDim.x)
+        if (row[j]) { c = j; break; }
+    c = block_min(c, red);
+    if (threadIdx.x == 0) X.lead[r] = c;
 }
 
 // the pivot rows in pivot-column order (block per pivot row)
@@ -746,7 +794,7 @@ __global__ void k_gather_rref(const RrefJob *__restrict__ jobs, const uint32_t *
         X.opiv[n] = c;
     }
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) X.out[(size_t)pos * nb + j] = X.M[(size_t)r * nb + j];
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) X.out[(size_t)pos * nb + j] = X.M[(size_t)r * X.ldm + j];
 }
 
 // ---- reconstruction and the final tails ------------------------------------------------------
@@ -1033,7 +1081,9 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         DBuf<uint32_t> states;  // 4 words per job, read back in one copy
         states.alloc(ar, 4ull * nj, st);
         GB_CUDA(cudaMemsetAsync(states.p, 0, 16ull * nj, st));
-        std::vector<int> live, smem_jobs, glob_jobs;
+        std::vector<int> live, smem_jobs, glob_jobs, tc_jobs;
+        std::vector<DigitPlanes> FA(nj), FB(nj);
+        std::vector<std::unique_ptr<MmPlan>> plans(nj);
         for (int j = 0; j < nj; ++j) {
             const uint32_t nC = R[j].nC, nb = R[j].nb;
             X[j] = RrefJob{};
@@ -1041,12 +1091,28 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             X[j].nb = nb;
             X[j].fp = R[j].fp;
             if (!nC || !nb) continue;
-            Mw[j].alloc(ar, (size_t)nC * nb, st);
+            X[j].ldm = (nb + 3) / 4 * 4;
+            Mw[j].alloc(ar, (size_t)nC * X[j].ldm, st);
             lead[j].alloc(ar, nC, st);
             pcol[j].alloc(ar, nC, st);
             order[j].alloc(ar, std::min(nC, nb), st);
             panel[j].alloc(ar, 3 * KP, st);
-            GB_CUDA(cudaMemcpyAsync(Mw[j].p, Es[j]->dprime.p, 4ull * nC * nb, cudaMemcpyDeviceToDevice, st));
+            GB_CUDA(cudaMemcpy2DAsync(Mw[j].p, 4ull * X[j].ldm, Es[j]->dprime.p, 4ull * nb, 4ull * nb, nC,
+                                      cudaMemcpyDeviceToDevice, st));
+            // large D': the trailing update of each panel on the tensor cores
+            if ((uint64_t)nC * nb >= (1ull << 22) || (ctx->flags & GB_CTX_REDUCE_DENSE)) {
+                const uint32_t L = digits_for(R[j].fp.p);
+                FA[j].alloc(ar, L, nC, KP, st);
+                FB[j].alloc(ar, L, nb, KP, st);
+                GB_CUDA(cudaMemsetAsync(FA[j].p, 0, FA[j].buf.bytes(), st));
+                GB_CUDA(cudaMemsetAsync(FB[j].p, 0, FB[j].buf.bytes(), st));
+                X[j].tc = 1;
+                X[j].fa = FA[j].p;
+                X[j].fb = FB[j].p;
+                X[j].fkp = FA[j].kpad;
+                plans[j] = std::make_unique<MmPlan>(FA[j], FB[j], Mw[j].p, X[j].ldm, nC, nb, R[j].fp);
+                tc_jobs.push_back(j);
+            }
             X[j].M = Mw[j].p;
             X[j].lead = lead[j].p;
             X[j].pcol = pcol[j].p;
@@ -1091,6 +1157,15 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
                         k_panel_rref<false><<<(unsigned)glob_jobs.size(), PT, 0, st>>>(G.jobs, lists.p + smem_jobs.size());
                     k_eliminate<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
                     counted(2 + (smem_jobs.empty() ? 0 : 1) + (glob_jobs.empty() ? 0 : 1));
+                    for (int j : tc_jobs) {
+                        const unsigned nt = (unsigned)(((size_t)X[j].nC + X[j].nb) * KP);
+                        if (FA[j].L == 2) k_elim_digits<2><<<(nt + 255) / 256, 256, 0, st>>>(G.jobs, j);
+                        else k_elim_digits<4><<<(nt + 255) / 256, 256, 0, st>>>(G.jobs, j);
+                        counted();
+                        plans[j]->update(0, 0, 0, 0, 0, 0, X[j].nC, X[j].nb, KP, true, derr.p, st);
+                        k_leads_np<<<X[j].nC, 256, 0, st>>>(G.jobs, j);
+                        counted();
+                    }
                 }
                 rounds += group;
                 uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj));
