@@ -71,13 +71,17 @@ typedef struct {
                             cores whenever the arena has room (DENSE also runs every panel
                             update of the echelon form of D' on the tensor cores); neither:
                             chosen per matrix by its shape.  All give the same (unique) D' and
-                            RREF(D'). */
+                            RREF(D');
+                            GB_CTX_NO_GRAPHS: launch the rounds of the echelon form of D' one
+                            by one from the host instead of as one CUDA graph whose loop runs
+                            on the device (same results). */
     uint32_t reserved;
 } gb_ctx_opts;
 
 #define GB_CTX_KEEP_STEP 1u
 #define GB_CTX_REDUCE_SPARSE 2u
 #define GB_CTX_REDUCE_DENSE 4u
+#define GB_CTX_NO_GRAPHS 8u
 
 /* A polynomial system on the host: polynomial i has the terms [poly_off[i], poly_off[i+1]). */
 typedef struct {
@@ -297,10 +301,50 @@ gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, ui
                                  const uint32_t *val, const uint32_t *pivot_cols,
                                  const uint32_t *nonpivot_cols, uint32_t *dprime, void *stream);
 
+/* ---- autotuning ----------------------------------------------------------------------------- */
+
+/* The reduction of a Macaulay matrix has interchangeable schedules that give the same D' and
+   RREF(D') (Sec. 9.2): the sparse row-by-row reduction or the dense blocked elimination on the
+   tensor cores; the panel updates of RREF(D') on CUDA cores or on the tensor cores; the RREF
+   rounds launched one by one from the host or as one CUDA graph whose loop runs on the device.
+   Without tuning a context chooses by fixed shape rules.
+
+   gb_autotune runs copies of the given systems to completion once per candidate schedule
+   (three runs), times every step's reduction and RREF on the device, and keeps, per shape
+   bucket, the schedule with the least total time.  A reduction's bucket is the prime's class
+   (below 2^16 or not) and floor(log2(x + 1)) of its pivots, non-pivot rows and non-pivot columns;
+   an RREF's bucket is the class and the same of D''s rows and columns.  From then on every
+   single-system reduction of the context (gb_f4_step, gb_groebner, gb_reduce_macaulay) whose
+   bucket the table holds takes the tuned schedule; other buckets, and the matrices of a batch,
+   keep the rules.  GB_CTX_REDUCE_SPARSE, GB_CTX_REDUCE_DENSE and GB_CTX_NO_GRAPHS still take
+   precedence.  Tuning adds to the context's table; a bucket measured again is replaced.
+   The systems must belong to ctx and have run no step; they are not modified.  Do not tune a
+   context that a server is using.
+   GB_EINVAL: null ctx, a null or foreign system, or a system that has run a step. */
+typedef struct {
+    uint32_t runs;            /* complete runs of all systems (one per candidate schedule) */
+    uint32_t steps;           /* F4 steps timed, over all runs */
+    uint32_t buckets_reduce;  /* reduction buckets in the context's table */
+    uint32_t buckets_rref;    /* RREF buckets in the context's table */
+    uint32_t dense_buckets;   /* reduction buckets where the tensor-core schedule won */
+    uint32_t reserved;
+    double ms_wall;           /* host wall time of the tuning */
+} gb_tune_report;
+
+gb_status gb_autotune(gb_ctx *ctx, uint32_t count, gb_system *const *systems, gb_tune_report *report);
+/* Write the context's table to a text file (one bucket per line, with the measured times), or
+   add the buckets of such a file to the table.  GB_EINVAL: the file cannot be opened or a line
+   is malformed (nothing is added then). */
+gb_status gb_tune_save(const gb_ctx *ctx, const char *path);
+gb_status gb_tune_load(gb_ctx *ctx, const char *path);
+
 /* ---- diagnostics ---------------------------------------------------------------------------- */
 
-/* Number of CUDA kernels this library has launched in this process so far (all contexts). */
+/* Number of CUDA kernels this library has launched in this process so far (all contexts); a
+   kernel inside a CUDA graph counts once per execution. */
 uint64_t gb_kernel_launches(void);
+/* Number of CUDA graphs this library has launched in this process so far (all contexts). */
+uint64_t gb_graph_launches(void);
 
 /* ---- errors --------------------------------------------------------------------------------- */
 

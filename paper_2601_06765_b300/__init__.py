@@ -26,6 +26,7 @@ STATUS = {0: "GB_OK", 1: "GB_DONE", -1: "GB_EINVAL", -2: "GB_ENOMEM", -3: "GB_EO
 GB_CTX_KEEP_STEP = 1
 GB_CTX_REDUCE_SPARSE = 2
 GB_CTX_REDUCE_DENSE = 4
+GB_CTX_NO_GRAPHS = 8
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -84,6 +85,12 @@ class gb_server_stats(ctypes.Structure):
                 ("max_running", ctypes.c_uint32), ("queued", ctypes.c_uint32)]
 
 
+class gb_tune_report(ctypes.Structure):
+    _fields_ = [("runs", ctypes.c_uint32), ("steps", ctypes.c_uint32), ("buckets_reduce", ctypes.c_uint32),
+                ("buckets_rref", ctypes.c_uint32), ("dense_buckets", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("ms_wall", ctypes.c_double)]
+
+
 class gb_server_opts(ctypes.Structure):
     _fields_ = [("hbm_cap_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
@@ -121,6 +128,9 @@ _SIGS = {
     "gb_basis_redundant": [_vp, _u32p, _u8p],
     "gb_system_last_step": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
     "gb_batch_groebner": [_vp, ctypes.c_uint32, ctypes.POINTER(_vp), ctypes.POINTER(gb_run_stats)],
+    "gb_autotune": [_vp, ctypes.c_uint32, ctypes.POINTER(_vp), ctypes.POINTER(gb_tune_report)],
+    "gb_tune_save": [_vp, ctypes.c_char_p],
+    "gb_tune_load": [_vp, ctypes.c_char_p],
     "gb_server_create": [_vp, ctypes.POINTER(gb_server_opts), ctypes.POINTER(_vp)],
     "gb_server_submit": [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)],
     "gb_server_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)],
@@ -149,6 +159,8 @@ def lib():
         L.gb_last_error.restype = ctypes.c_char_p
         L.gb_kernel_launches.argtypes = []
         L.gb_kernel_launches.restype = ctypes.c_uint64
+        L.gb_graph_launches.argtypes = []
+        L.gb_graph_launches.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -161,6 +173,10 @@ def check(status: int, where: str) -> int:
 
 def gb_kernel_launches() -> int:
     return int(lib().gb_kernel_launches())
+
+
+def gb_graph_launches() -> int:
+    return int(lib().gb_graph_launches())
 
 
 def _p(a: np.ndarray | None, ct):
@@ -319,6 +335,23 @@ def gb_batch_groebner(ctx: int, systems: list[int]) -> list[dict]:
     return [_struct_dict(st[i]) for i in range(len(systems))]
 
 
+def gb_autotune(ctx: int, systems: list[int]) -> dict:
+    """Time the reduction schedules on copies of `systems` (fresh system handles of ctx) and keep
+    the fastest per shape bucket in the context's table; returns the tuning report."""
+    arr = (_vp * max(len(systems), 1))(*systems)
+    rep = gb_tune_report()
+    check(lib().gb_autotune(ctx, len(systems), arr, ctypes.byref(rep)), "gb_autotune")
+    return _struct_dict(rep)
+
+
+def gb_tune_save(ctx: int, path: str) -> None:
+    check(lib().gb_tune_save(ctx, os.fsencode(path)), "gb_tune_save")
+
+
+def gb_tune_load(ctx: int, path: str) -> None:
+    check(lib().gb_tune_load(ctx, os.fsencode(path)), "gb_tune_load")
+
+
 def gb_server_create(ctx: int, hbm_cap_bytes: int, max_slots: int = 0) -> int:
     o = gb_server_opts(hbm_cap_bytes, max_slots, 0)
     h = _vp()
@@ -382,9 +415,10 @@ class Context:
     """A library context whose device arena is a torch tensor on `device`."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 2 << 30, keep_step: bool = False,
-                 reduce: str = "auto", stream=None):
+                 reduce: str = "auto", stream=None, graphs: bool = True):
         """reduce: "auto" (per matrix by shape), "sparse" or "dense" (see GB_CTX_REDUCE_*).
-        stream: a torch.cuda.Stream the context runs on (default: a stream of its own)."""
+        stream: a torch.cuda.Stream the context runs on (default: a stream of its own).
+        graphs: False launches the echelon-form rounds one by one (GB_CTX_NO_GRAPHS)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: this library has no CPU path")
@@ -393,6 +427,8 @@ class Context:
         torch.cuda.synchronize(device)
         flags = (GB_CTX_KEEP_STEP if keep_step else 0) | {"auto": 0, "sparse": GB_CTX_REDUCE_SPARSE,
                                                             "dense": GB_CTX_REDUCE_DENSE}[reduce]
+        if not graphs:
+            flags |= GB_CTX_NO_GRAPHS
         self.stream = stream
         self.h = gb_ctx_create(device, stream.cuda_stream if stream is not None else None,
                                self.arena.data_ptr(), arena_bytes, flags)

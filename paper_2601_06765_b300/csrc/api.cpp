@@ -15,10 +15,16 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
 void groebner_batch(const std::vector<gb_system *> &Ss);
 void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F);
 void make_resident(const std::vector<gb_system *> &Ss);
+void autotune(gb_ctx *ctx, const std::vector<gb_system *> &Ss, gb_tune_report *rep);
+void tune_save(const gb_ctx *ctx, const char *path);
+void tune_load(gb_ctx *ctx, const char *path);
 std::vector<RowSpec> order_rows(const gb_system *S, std::vector<std::pair<Mono, uint32_t>> tk);
 
 static thread_local std::string t_last_error;
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<unsigned long long> g_graph_launches{0};
+thread_local bool t_capturing = false;
+thread_local unsigned t_captured = 0;
 
 void set_last_error(const std::string &msg) { t_last_error = msg; }
 
@@ -213,6 +219,8 @@ const char *gb_last_error(void) { return t_last_error.c_str(); }
 
 uint64_t gb_kernel_launches(void) { return g_launches.load(); }
 
+uint64_t gb_graph_launches(void) { return g_graph_launches.load(); }
+
 gb_status gb_ctx_create(int device, const gb_ctx_opts *opts, gb_ctx **out) {
     GB_API_BEGIN
     if (!out) fail(GB_EINVAL, "out is NULL");
@@ -258,6 +266,7 @@ gb_status gb_ctx_destroy(gb_ctx *ctx) {
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->capture) cudaStreamDestroy(ctx->capture);
     delete ctx;
     return GB_OK;
     GB_API_END
@@ -433,6 +442,32 @@ gb_status gb_groebner(gb_system *S, gb_run_stats *stats) {
     Enter entered(S->ctx);
     groebner_batch({S});
     if (stats) *stats = S->run;
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_autotune(gb_ctx *ctx, uint32_t count, gb_system *const *systems, gb_tune_report *report) {
+    GB_API_BEGIN
+    if (!ctx || (count && !systems)) fail(GB_EINVAL, "null context or systems");
+    Enter entered(ctx);
+    autotune(ctx, std::vector<gb_system *>(systems, systems + count), report);
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_tune_save(const gb_ctx *ctx, const char *path) {
+    GB_API_BEGIN
+    if (!ctx || !path) fail(GB_EINVAL, "null context or path");
+    tune_save(ctx, path);
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_tune_load(gb_ctx *ctx, const char *path) {
+    GB_API_BEGIN
+    if (!ctx || !path) fail(GB_EINVAL, "null context or path");
+    std::lock_guard<std::recursive_mutex> g(ctx->mu);
+    tune_load(ctx, path);
     return GB_OK;
     GB_API_END
 }

@@ -471,6 +471,33 @@ void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F) {
     S->footprint = (size_t)((8.0 + 2.0 * std::exp2(log2_mib)) * 1048576.0);
 }
 
+// A new system with the same normalised input as S, which must not have run a step: its input
+// polynomials are then in_mon / in_cf, element g holding len[g] terms in order.
+gb_system *system_clone_fresh(const gb_system *S) {
+    if (S->steps || S->resident) fail(GB_EINVAL, "the system has already run a step");
+    const uint32_t n = S->n, ng = (uint32_t)S->len.size();
+    std::vector<uint32_t> po(ng + 1, 0);
+    for (uint32_t g = 0; g < ng; ++g) po[g + 1] = po[g] + S->len[g];
+    if (po[ng] != S->in_mon.size() || S->in_cf.size() != S->in_mon.size())
+        fail(GB_EDEVICE, "system copy: input arrays do not match the element lengths");
+    std::vector<uint8_t> ex((size_t)po[ng] * n);
+    for (size_t q = 0; q < S->in_mon.size(); ++q) {
+        Mono m{};
+        std::memcpy(m.e, &S->in_mon[q], 16);
+        std::memcpy(ex.data() + q * n, m.e, n);
+    }
+    gb_polys F{};
+    F.npolys = ng;
+    F.poly_off = po.data();
+    F.exps = ex.data();
+    F.coeffs = S->in_cf.data();
+    auto C = std::make_unique<gb_system>();
+    C->ctx = S->ctx;
+    C->stream = S->stream;
+    system_init(C.get(), n, S->p, &F);
+    return C.release();
+}
+
 // the inputs of systems not yet on the device, in one staged copy: terms, coefficients, offsets
 // and lengths (no step has run yet, so the host mirrors off / len describe exactly the input)
 void make_resident(const std::vector<gb_system *> &Ss) {

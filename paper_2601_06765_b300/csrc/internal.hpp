@@ -36,10 +36,16 @@ void set_last_error(const std::string &msg);
 // only ever raised: a thread lowering it while another launches with more would fail the launch.
 void opt_in_smem(const void *kernel);
 
-// every kernel launch site calls counted() right after its <<<...>>>
+// every kernel launch site calls counted() right after its <<<...>>>.  While this thread records
+// a CUDA graph (t_capturing), the launches only become graph nodes: they are tallied in
+// t_captured, and the code that launches the graph counts them once per execution.
 extern std::atomic<unsigned long long> g_launches;
+extern std::atomic<unsigned long long> g_graph_launches;
+extern thread_local bool t_capturing;
+extern thread_local unsigned t_captured;
 inline void counted(unsigned k = 1) {
-    g_launches.fetch_add(k, std::memory_order_relaxed);
+    if (t_capturing) t_captured += k;
+    else g_launches.fetch_add(k, std::memory_order_relaxed);
     GB_CUDA(cudaGetLastError());
 }
 
@@ -194,12 +200,32 @@ struct PairL {  // a critical pair with its lcm cached
 // ---- handles ---------------------------------------------------------------------------------
 namespace gb {
 struct HostPool;
+
+// Autotuning of the interchangeable schedules of the reduction (tune.cpp).  All of them give the
+// same D' and RREF(D'):
+//   reduction (TUNE_REDUCE): 0 sparse row-by-row, 1 dense blocked elimination on the tensor cores;
+//   RREF (TUNE_RREF): 0 panel updates on CUDA cores, rounds launched from the host;
+//                     1 the same rounds as one CUDA graph with the loop on the device;
+//                     2 panel updates on the tensor cores, rounds as one graph.
+constexpr uint32_t TUNE_REDUCE = 0, TUNE_RREF = 1;
+struct TuneEntry {
+    uint8_t choice = 0;
+    float ms[3] = {-1.f, -1.f, -1.f};  // measured total per schedule, -1 where not measured
+};
+struct TuneState {
+    int force_reduce = -1, force_rref = -1;  // >= 0: every matrix takes this schedule (tuning runs)
+    std::map<uint64_t, TuneEntry> table;     // bucket key -> the fastest schedule measured
+};
+// bucket of a shape: the kind, the prime's class (below 2^16 or not) and floor(log2(x + 1)) of
+// up to three sizes (reduction: pivots, non-pivot rows, non-pivot columns; RREF: rows, columns)
+uint64_t tune_key(uint32_t kind, uint32_t p, uint32_t a, uint32_t b, uint32_t c);
 }
 
 struct gb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;  // every system of the context runs on this stream
     bool own_stream = false;
+    cudaStream_t capture = nullptr;  // private stream that CUDA graphs are recorded on (lazily created)
     uint32_t flags = 0;
     gb::Arena arena;
     cudaEvent_t ev[8] = {};         // stage timing of the batch in flight
@@ -211,6 +237,7 @@ struct gb_ctx {
     // held by every call that queues work on the stream or uses the staging area, so that a
     // server's scheduler thread and the caller's own calls on the same context do not interleave
     std::recursive_mutex mu;
+    gb::TuneState tune;
     gb_ctx();
     ~gb_ctx();
 };

@@ -592,6 +592,8 @@ MmPlan::MmPlan(const DigitPlanes &A_, const DigitPlanes &B_, uint32_t *C_, uint6
     const cuuint64_t strides[1] = {4ull * ldc};
     const cuuint32_t box[2] = {32u, (cuuint32_t)MM_BM};  // 128 bytes: the 128-byte swizzle span
     encode(&maps->tc, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, C, dims, strides, box);
+    // raised here, before any launch, so that launches recorded into a graph find it set
+    opt_in_smem(L == 2 ? reinterpret_cast<const void *>(k_mm<2>) : reinterpret_cast<const void *>(k_mm<4>));
 }
 
 MmPlan::~MmPlan() { delete maps; }

@@ -780,6 +780,93 @@ __global__ void k_leads_np(const RrefJob *__restrict__ jobs, int jb) {
     if (threadIdx.x == 0) X.lead[r] = c;
 }
 
+// The condition of the round loop, evaluated on the device after each round (one warp): another
+// round is needed while some job's last pick left more non-pivot rows than its panel took, and
+// fewer than maxrounds rounds have run (every round settles at least one panel of KP rows).
+__global__ void k_rref_more(const RrefJob *__restrict__ jobs, int nj, uint32_t *rounds, uint32_t maxrounds,
+                            cudaGraphConditionalHandle more_h) {
+    bool more = false;
+    for (int j = threadIdx.x; j < nj; j += 32) {
+        const uint32_t *st = jobs[j].state;
+        if (st && st[1] != 0 && st[3] > st[1]) more = true;
+    }
+    more = __any_sync(0xffffffffu, more);
+    if (threadIdx.x == 0) {
+        const uint32_t r = *rounds + 1;
+        *rounds = r;
+        cudaGraphSetConditional(more_h, more && r < maxrounds ? 1u : 0u);
+    }
+}
+
+// An executable graph and its template; the executable may be destroyed while it is still in
+// flight (CUDA then frees it when the launch completes).
+struct RoundGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    RoundGraph() = default;
+    RoundGraph(const RoundGraph &) = delete;
+    RoundGraph(RoundGraph &&o) noexcept {
+        std::swap(g, o.g);
+        std::swap(exec, o.exec);
+    }
+    RoundGraph &operator=(const RoundGraph &) = delete;
+    RoundGraph &operator=(RoundGraph &&o) noexcept {
+        reset();
+        std::swap(g, o.g);
+        std::swap(exec, o.exec);
+        return *this;
+    }
+    ~RoundGraph() { reset(); }
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (g) cudaGraphDestroy(g);
+        exec = nullptr;
+        g = nullptr;
+    }
+};
+
+// Loops below this many rounds stay on host launches: recording and instantiating the graph
+// costs about as much as launching a few rounds directly.
+constexpr uint32_t GRAPH_MIN_ROUNDS = 3;
+
+// Records `body` (which launches one round on the stream it is given and then sets the loop
+// condition from the device) as the body of a while-node and instantiates the graph.  The node's
+// condition starts at 1 on every launch, so the body runs at least once.  `nodes` receives the
+// number of kernels in one round.
+template <class F>
+RoundGraph record_round_loop(gb_ctx *ctx, F &&body, unsigned &nodes) {
+    if (!ctx->capture) GB_CUDA(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+    RoundGraph R;
+    GB_CUDA(cudaGraphCreate(&R.g, 0));
+    cudaGraphConditionalHandle h{};
+    GB_CUDA(cudaGraphConditionalHandleCreate(&h, R.g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node{};
+    GB_CUDA(cudaGraphAddNode(&node, R.g, nullptr, nullptr, 0, &np));
+    GB_CUDA(cudaStreamBeginCaptureToGraph(ctx->capture, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    t_capturing = true;
+    t_captured = 0;
+    try {
+        body(ctx->capture, h);
+    } catch (...) {
+        t_capturing = false;
+        cudaGraph_t x = nullptr;
+        cudaStreamEndCapture(ctx->capture, &x);
+        throw;
+    }
+    t_capturing = false;
+    nodes = t_captured;
+    cudaGraph_t x = nullptr;
+    GB_CUDA(cudaStreamEndCapture(ctx->capture, &x));
+    GB_CUDA(cudaGraphInstantiate(&R.exec, R.g, 0));
+    return R;
+}
+
 // the pivot rows in pivot-column order (block per pivot row)
 __global__ void k_gather_rref(const RrefJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     __shared__ uint32_t pos;
@@ -916,6 +1003,19 @@ bool use_cluster(const RedJob &J, size_t accb, uint64_t rows) {
 
 }  // namespace
 
+// the tuned schedule of a bucket, or -1 (the shape rules decide)
+static int tuned_choice(const gb_ctx *ctx, uint64_t key) {
+    const auto it = ctx->tune.table.find(key);
+    return it == ctx->tune.table.end() ? -1 : it->second.choice;
+}
+
+// the RREF schedule forced by a tuning run or found in the tuned table (single matrices only),
+// else -1: 0 CUDA cores with host rounds, 1 CUDA cores in a graph, 2 tensor cores in a graph
+static int rref_schedule(const gb_ctx *ctx, uint32_t p, uint32_t nC, uint32_t nb, int nj) {
+    if (ctx->tune.force_rref >= 0) return ctx->tune.force_rref;
+    return nj == 1 ? tuned_choice(ctx, tune_key(TUNE_RREF, p, nC, nb, 0)) : -1;
+}
+
 std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaulay *> &Ms, bool echelon) {
     std::vector<std::unique_ptr<gb_echelon>> Es;
     if (Ms.empty()) return Es;
@@ -958,8 +1058,11 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             if (!J.nC || !J.nb || !J.nA || (ctx->flags & GB_CTX_REDUCE_SPARSE)) continue;
             // a dense matrix runs its own launch sequence, while the sparse kernels cover every
             // matrix of a batch in one launch: inside a batch only very large matrices go dense
-            const bool want = (ctx->flags & GB_CTX_REDUCE_DENSE) ||
-                              (dense_pays(J.fp.p, J.N, J.nA, J.nC) && (nj == 1 || J.nA >= 16384));
+            bool want = dense_pays(J.fp.p, J.N, J.nA, J.nC) && (nj == 1 || J.nA >= 16384);
+            const int tuned = nj == 1 ? tuned_choice(ctx, tune_key(TUNE_REDUCE, J.fp.p, J.nA, J.nC, J.nb)) : -1;
+            if (ctx->flags & GB_CTX_REDUCE_DENSE) want = true;
+            else if (ctx->tune.force_reduce >= 0) want = ctx->tune.force_reduce == 1;
+            else if (tuned >= 0) want = tuned == 1;
             const size_t need = dense_bytes(J.fp.p, J.N, J.nA, J.nC);
             if (want && need + (64u << 20) < room) {
                 dense[j] = 1;
@@ -1078,9 +1181,11 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         // per-job working state, one allocation each
         std::vector<RrefJob> X(nj);
         std::vector<DBuf<uint32_t>> Mw(nj), lead(nj), pcol(nj), order(nj), panel(nj);
-        DBuf<uint32_t> states;  // 4 words per job, read back in one copy
-        states.alloc(ar, 4ull * nj, st);
-        GB_CUDA(cudaMemsetAsync(states.p, 0, 16ull * nj, st));
+        DBuf<uint32_t> states;  // 4 words per job, then the graph's round count; read back in one copy
+        states.alloc(ar, 4ull * nj + 4, st);
+        GB_CUDA(cudaMemsetAsync(states.p, 0, 16ull * nj + 16, st));
+        RoundGraph graph;
+        unsigned graph_nodes = 0;
         std::vector<int> live, smem_jobs, glob_jobs, tc_jobs;
         std::vector<DigitPlanes> FA(nj), FB(nj);
         std::vector<std::unique_ptr<MmPlan>> plans(nj);
@@ -1100,7 +1205,8 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             GB_CUDA(cudaMemcpy2DAsync(Mw[j].p, 4ull * X[j].ldm, Es[j]->dprime.p, 4ull * nb, 4ull * nb, nC,
                                       cudaMemcpyDeviceToDevice, st));
             // large D': the trailing update of each panel on the tensor cores
-            if ((uint64_t)nC * nb >= (1ull << 22) || (ctx->flags & GB_CTX_REDUCE_DENSE)) {
+            const int sched = rref_schedule(ctx, R[j].fp.p, nC, nb, nj);
+            if ((ctx->flags & GB_CTX_REDUCE_DENSE) || (sched >= 0 ? sched == 2 : (uint64_t)nC * nb >= (1ull << 22))) {
                 const uint32_t L = digits_for(R[j].fp.p);
                 FA[j].alloc(ar, L, nC, KP, st);
                 FB[j].alloc(ar, L, nb, KP, st);
@@ -1146,44 +1252,65 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             // every round turns each of its rows into a pivot row or a zero row
             uint32_t maxrounds = 1;
             for (int j : live) maxrounds = std::max<uint32_t>(maxrounds, (X[j].nC + KP - 1) / KP + 1);
-            uint32_t rounds = 0;
-            for (;;) {
-                const uint32_t group = rounds == 0 ? 2 : 4;
-                for (uint32_t g = 0; g < group; ++g) {
-                    k_pick_panel<<<nj, 1024, 0, st>>>(G.jobs);
-                    if (!smem_jobs.empty())
-                        k_panel_rref<true><<<(unsigned)smem_jobs.size(), PT, pan_bytes, st>>>(G.jobs, lists.p);
-                    if (!glob_jobs.empty())
-                        k_panel_rref<false><<<(unsigned)glob_jobs.size(), PT, 0, st>>>(G.jobs, lists.p + smem_jobs.size());
-                    k_eliminate<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
-                    counted(2 + (smem_jobs.empty() ? 0 : 1) + (glob_jobs.empty() ? 0 : 1));
-                    for (int j : tc_jobs) {
-                        const unsigned nt = (unsigned)(((size_t)X[j].nC + X[j].nb) * KP);
-                        if (FA[j].L == 2) k_elim_digits<2><<<(nt + 255) / 256, 256, 0, st>>>(G.jobs, j);
-                        else k_elim_digits<4><<<(nt + 255) / 256, 256, 0, st>>>(G.jobs, j);
-                        counted();
-                        plans[j]->update(0, 0, 0, 0, 0, 0, X[j].nC, X[j].nb, KP, true, derr.p, st);
-                        k_leads_np<<<X[j].nC, 256, 0, st>>>(G.jobs, j);
-                        counted();
+            // one round: each job picks its next panel, reduces it, and eliminates the panel's
+            // pivot columns from all its other rows
+            auto round = [&](cudaStream_t s) {
+                k_pick_panel<<<nj, 1024, 0, s>>>(G.jobs);
+                if (!smem_jobs.empty())
+                    k_panel_rref<true><<<(unsigned)smem_jobs.size(), PT, pan_bytes, s>>>(G.jobs, lists.p);
+                if (!glob_jobs.empty())
+                    k_panel_rref<false><<<(unsigned)glob_jobs.size(), PT, 0, s>>>(G.jobs, lists.p + smem_jobs.size());
+                k_eliminate<<<G.totals[0], 256, 0, s>>>(G.jobs, G.plans[0], nj);
+                counted(2 + (smem_jobs.empty() ? 0 : 1) + (glob_jobs.empty() ? 0 : 1));
+                for (int j : tc_jobs) {
+                    const unsigned nt = (unsigned)(((size_t)X[j].nC + X[j].nb) * KP);
+                    if (FA[j].L == 2) k_elim_digits<2><<<(nt + 255) / 256, 256, 0, s>>>(G.jobs, j);
+                    else k_elim_digits<4><<<(nt + 255) / 256, 256, 0, s>>>(G.jobs, j);
+                    counted();
+                    plans[j]->update(0, 0, 0, 0, 0, 0, X[j].nC, X[j].nb, KP, true, derr.p, s);
+                    k_leads_np<<<X[j].nC, 256, 0, s>>>(G.jobs, j);
+                    counted();
+                }
+            };
+            int sched = -1;
+            for (int j : live) sched = std::max(sched, rref_schedule(ctx, R[j].fp.p, X[j].nC, X[j].nb, nj));
+            if (!(ctx->flags & GB_CTX_NO_GRAPHS) && (sched >= 0 ? sched >= 1 : maxrounds >= GRAPH_MIN_ROUNDS)) {
+                // the whole loop as one graph: the rounds repeat on the device until no job has
+                // rows left, with no host round trip between them
+                unsigned per_round = 0;
+                graph = record_round_loop(ctx, [&](cudaStream_t s, cudaGraphConditionalHandle more) {
+                    round(s);
+                    k_rref_more<<<1, 32, 0, s>>>(G.jobs, nj, states.p + 4 * nj, maxrounds, more);
+                    counted();
+                }, per_round);
+                GB_CUDA(cudaGraphLaunch(graph.exec, st));
+                g_graph_launches.fetch_add(1, std::memory_order_relaxed);
+                graph_nodes = per_round;
+            } else {
+                uint32_t rounds = 0;
+                for (;;) {
+                    const uint32_t group = rounds == 0 ? 2 : 4;
+                    for (uint32_t g = 0; g < group; ++g) round(st);
+                    rounds += group;
+                    uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj));
+                    GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
+                    ctx_sync(ctx);
+                    bool more = false;
+                    for (int j : live) {
+                        const uint32_t *s = h + 4 * j;
+                        if (s[1] != 0 && s[3] > s[1]) more = true;
                     }
+                    if (!more || rounds >= maxrounds) break;
                 }
-                rounds += group;
-                uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj));
-                GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
-                ctx_sync(ctx);
-                bool more = false;
-                for (int j : live) {
-                    const uint32_t *s = h + 4 * j;
-                    if (s[1] != 0 && s[3] > s[1]) more = true;
-                }
-                if (!more || rounds >= maxrounds) break;
             }
             // one more pick confirms that no non-zero non-pivot row is left
             k_pick_panel<<<nj, 1024, 0, st>>>(G.jobs);
             counted();
-            uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj));
-            GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
+            uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj + 16));
+            GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj + 16, cudaMemcpyDeviceToHost, st));
             ctx_sync(ctx);
+            if (graph.exec) counted(graph_nodes * h[4 * nj]);  // rounds the graph ran
+            graph.reset();
             for (int j : live) {
                 if (h[4 * j + 1] != 0) fail(GB_EDEVICE, "RREF: rows left after the last round");
                 rank[j] = h[4 * j];
