@@ -46,38 +46,46 @@ namespace gb {
 
 namespace {
 
-constexpr int MM_BM = 128, MM_BN = 64, MM_BK = 64;  // C tile, K block (64 BF16 = 128 bytes)
-constexpr int MM_EPI = 16;                         // epilogue warps: four per tensor-memory lane quarter
+constexpr int MM_BM = 128, MM_BK = 64;  // rows of a C tile, K block (64 BF16 = 128 bytes)
+constexpr int MM_MMA_N = 128;           // N of every tcgen05.mma: the L digits of B^T side by side
+constexpr int MM_EPI = 16;              // epilogue warps: four per tensor-memory lane quarter
 constexpr int MM_THREADS = 32 * (2 + MM_EPI);
-constexpr uint32_t MM_SPIN = 1u << 22;               // bounded mbarrier waits
+constexpr uint32_t MM_SPIN = 1u << 22;  // bounded mbarrier waits
 
 template <int L>
 struct MmCfg {
-    static constexpr int DIAG = 2 * L - 1;            // digit diagonals
-    static constexpr int KB = 512 / L / MM_BK;        // K blocks of the longest exact K
-    static constexpr uint32_t A_BLK = MM_BM * 128;    // bytes of one digit x K block of A
-    static constexpr uint32_t B_BLK = MM_BN * 128;    // bytes of one digit x K block of B^T
+    static constexpr int DIAG = 2 * L - 1;             // digit diagonals
+    static constexpr int BN = MM_MMA_N / L;            // columns of a C tile: 32 (L = 4), 64 (L = 2)
+    static constexpr int KB = 512 / L / MM_BK;         // K blocks of the longest exact K
+    static constexpr int CPT = BN / 4;                 // columns of each epilogue thread
+    static constexpr uint32_t A_BLK = MM_BM * 128;     // bytes of one digit x K block of A
     static constexpr uint32_t A_BYTES = L * KB * A_BLK;
-    static constexpr uint32_t B_KB = L * B_BLK;       // one K block of B^T, all digits
-    static constexpr uint32_t B_BYTES = KB * B_KB;
-    static constexpr uint32_t C_HALF = MM_BM * 32 * 4;  // one 32-column TMA box of the C tile
-    static constexpr uint32_t C_BYTES = 2 * C_HALF;
-    static constexpr uint32_t SMEM_DATA = A_BYTES + B_BYTES + C_BYTES;
-    static constexpr uint32_t SMEM = SMEM_DATA + 1024 + 256;  // + alignment + barriers
-    // tensor-memory regions: SPLIT (L = 4): region 0 = diagonals 0-3, region 1 = diagonals 4-6 of
-    // every tile; otherwise each region holds all diagonals of alternate tiles
-    static constexpr bool SPLIT = L == 4;
-    static constexpr int R0_DIAG = SPLIT ? 4 : DIAG;
-    static constexpr uint32_t R1_COL = (uint32_t)R0_DIAG * MM_BN;
+    static constexpr uint32_t B_BLK = MM_MMA_N * 128;  // one K block of B^T: L digits x BN rows
+    static constexpr uint32_t C_BOX = MM_BM * 32 * 4;  // one 32-column TMA box of C
+    static constexpr int C_BOXES = BN / 32;
+    static constexpr uint32_t C_TILE = C_BOXES * C_BOX;
+    static constexpr int NCBUF = C_TILE <= 16384u ? 2 : 1;  // C tiles in flight
+    static constexpr uint32_t C_BYTES = NCBUF * C_TILE;
+    // B^T streams through a ring of K-block slots: as many as fit beside A and C
+    static constexpr uint32_t SMEM_MAX = 227u * 1024u;
+    static constexpr uint32_t OVERHEAD = 1024 + 512;  // alignment + barriers
+    static constexpr int NSLOT = (int)((SMEM_MAX - OVERHEAD - A_BYTES - C_BYTES) / B_BLK);
+    static constexpr uint32_t B_BYTES = (uint32_t)NSLOT * B_BLK;
+    static constexpr uint32_t SMEM_DATA = A_BYTES + C_BYTES + B_BYTES;
+    static constexpr uint32_t SMEM = SMEM_DATA + OVERHEAD;
+    // two accumulator sets (tiles alternate), set s at tensor-memory column 256 s; diagonal d of a
+    // set at column BN d
+    static constexpr uint32_t SET_COLS = 256;
     static constexpr uint32_t TMEM_COLS = 512;
-    static_assert(R1_COL + (uint32_t)(SPLIT ? DIAG - R0_DIAG : DIAG) * MM_BN <= TMEM_COLS, "tensor memory");
+    static_assert(DIAG * BN <= (int)SET_COLS, "tensor memory");
+    static_assert(NSLOT >= 2, "shared memory");
 };
 
 struct MmParams {
     uint32_t M, N, K;       // the update covers C[cy + m][cx + n], m < M, n < N; K <= 512 / L
     int ax, ay, bx, by;     // TMA coordinates of A (k, m) and of B^T (k, n) at the origin
     int cx, cy;             // TMA coordinates of the update region in C
-    uint32_t ntn, items;    // tiles per tile row, tiles in all
+    uint32_t ntn, items;    // tiles per tile row (BN columns each), tiles in all
     Fp fp;
     uint64_t big;           // a multiple of p above 2^58, added before the Barrett reduction
     uint32_t rd[7];         // 256^d mod p
@@ -133,6 +141,12 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t sr
                  "r"(src), "r"(x), "r"(y)
                  : "memory");
 }
+// bring a box of a tensor into L2 (no shared memory, no completion to wait for)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
@@ -160,15 +174,24 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// 16 consecutive 32-bit columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+// N consecutive 32-bit columns (N = 8 or 16) of this thread's tensor-memory lane
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[N]) {
+    if constexpr (N == 16) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+              "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    } else {
+        static_assert(N == 8, "8 or 16 columns");
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(taddr));
+    }
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 
 // Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle: rows of 128 bytes,
 // 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1, layout type 2.
@@ -182,41 +205,45 @@ __device__ __forceinline__ uint64_t sdesc_of(uint32_t lo) { return ((uint64_t)SD
 
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9,
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MM_BN >> 3) << 17) |
-                           ((uint32_t)(MM_BM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MM_BM >> 4) << 24);
+}
 
 __device__ __forceinline__ int acc_int(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
-
-// region of diagonal d and its first tensor-memory column within the region
-template <int L>
-__host__ __device__ constexpr int region_of(int d) { return MmCfg<L>::SPLIT ? (d < MmCfg<L>::R0_DIAG ? 0 : 1) : 0; }
-template <int L>
-__host__ __device__ constexpr uint32_t dcol(int d) {
-    return MmCfg<L>::SPLIT ? (d < MmCfg<L>::R0_DIAG ? (uint32_t)d * MM_BN : MmCfg<L>::R1_COL + (uint32_t)(d - MmCfg<L>::R0_DIAG) * MM_BN)
-                           : (uint32_t)d * MM_BN;
+// The same for |x| <= 2^22 without the conversion unit: x + 1.5 2^23 lies in [2^23, 2^24], where
+// FP32 steps by 1, so the sum is exact and its bit pattern minus that of 1.5 2^23 is x (the
+// classic round-by-adding-a-magic-constant conversion; 2^24 itself continues the pattern).
+__device__ __forceinline__ int acc_int_small(uint32_t bits) {
+    return __float_as_int(__fadd_rn(__uint_as_float(bits), 12582912.0f)) - 0x4B400000;
 }
-// is (i, j) the first digit pair of its diagonal in the issue order (i outer, j inner)?
+// Diagonal d sums min(d + 1, 2L - 1 - d) digit products per k, so |D_d| <= that count x (512 / L)
+// x 2^14 at the largest K of a launch; where this is at most 2^22 (diagonals 0, 1, 5, 6 for L = 4;
+// 0, 2 for L = 2) the conversion above is exact.
 template <int L>
-__host__ __device__ constexpr bool first_pair(int i, int j) { return i == 0 || j == L - 1; }
+__host__ __device__ constexpr bool small_diag(int d) {
+    return (long long)(d + 1 < 2 * L - 1 - d ? d + 1 : 2 * L - 1 - d) * (512 / L) * 16384 <= (1ll << 22);
+}
 
 template <int L>
 __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CUtensorMap ta,
                                                      const __grid_constant__ CUtensorMap tb,
                                                      const __grid_constant__ CUtensorMap tc, const MmParams P) {
     using Cfg = MmCfg<L>;
+    constexpr int BN = Cfg::BN, CPT = Cfg::CPT;
     extern __shared__ unsigned char mm_smem_raw[];
     const uint32_t raw = smem_u32(mm_smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned
     unsigned char *gbase = mm_smem_raw + (base - raw);
-    // layout: A | B (per K block: all digits) | C (two 32-column halves) | barriers
-    const uint32_t sA = base, sB = base + Cfg::A_BYTES, sC = sB + Cfg::B_BYTES;
+    // layout: A (all digits and K blocks of the row tile) | C tiles | ring of B^T slots | barriers
+    const uint32_t sA = base, sC = base + Cfg::A_BYTES, sB = sC + Cfg::C_BYTES;
     const uint32_t bars = base + Cfg::SMEM_DATA;
-    const uint32_t a_full = bars, a_empty = bars + 8, c_full = bars + 16, c_empty = bars + 24;
-    auto r_full = [&](int r) { return bars + 32 + 8u * r; };
-    auto r_empty = [&](int r) { return bars + 48 + 8u * r; };
-    auto b_full = [&](int kb) { return bars + 64 + 8u * kb; };
-    auto b_empty = [&](int kb) { return bars + 96 + 8u * kb; };
-    const uint32_t tslot = bars + 128;
+    const uint32_t a_full = bars, a_empty = bars + 8;
+    auto r_full = [&](int r) { return bars + 16 + 8u * r; };
+    auto r_empty = [&](int r) { return bars + 32 + 8u * r; };
+    auto c_full = [&](int c) { return bars + 48 + 8u * c; };
+    auto b_full = [&](int s) { return bars + 80 + 8u * s; };
+    auto b_empty = [&](int s) { return bars + 80 + 8u * Cfg::NSLOT + 8u * s; };
+    const uint32_t tslot = bars + 80 + 16u * Cfg::NSLOT;
     uint32_t *tslot_g = reinterpret_cast<uint32_t *>(gbase + (tslot - base));
     // set when a bounded wait gives up: from then on every wait returns at once and no new copy,
     // product or store is issued, but every role still runs its whole loop, so the epilogue warps
@@ -234,20 +261,24 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
     const uint32_t w0 = (uint32_t)((unsigned long long)blockIdx.x * P.items / gridDim.x);
     const uint32_t w1 = (uint32_t)((unsigned long long)(blockIdx.x + 1) * P.items / gridDim.x);
     const int nkb = (int)((P.K + MM_BK - 1) / MM_BK);
+    // epilogue thread: row r of the tile is tensor-memory lane r; warps 2..17 cover the four lane
+    // quarters four times, warp group grp taking columns CPT grp .. CPT grp + CPT - 1
+    const int quarter = warp & 3, grp = (warp - 2) >> 2;
+    const uint32_t r = (uint32_t)(32 * quarter + lane);
 
     if (threadIdx.x == 0) {
         *abort_flag = 0u;
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
-        mbar_init(c_full, 1);
-        mbar_init(c_empty, 1);
-        for (int r = 0; r < 2; ++r) {
-            mbar_init(r_full(r), 1);
-            mbar_init(r_empty(r), MM_EPI);  // one arrival per epilogue warp
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(r_full(i), 1);
+            mbar_init(r_empty(i), MM_EPI);  // one arrival per epilogue warp
         }
-        for (int kb = 0; kb < Cfg::KB; ++kb) {
-            mbar_init(b_full(kb), 1);
-            mbar_init(b_empty(kb), 1);
+        for (int c = 0; c < Cfg::NCBUF; ++c) mbar_init(c_full(c), 1);
+        static_assert(Cfg::NCBUF <= 4, "barrier space");
+        for (int s = 0; s < Cfg::NSLOT; ++s) {
+            mbar_init(b_full(s), 1);
+            mbar_init(b_empty(s), 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -259,13 +290,21 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot_g);
+    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(CPT * grp);
 
     if (warp == 0 && lane == 0) {
-        // ---- producer
+        // ---- producer.  K block kb of the it-th tile is the g-th block of the ring sequence,
+        // g = it nkb + kb, in slot g mod NSLOT, that slot's (g / NSLOT)-th use.
         int arow = -1;
-        uint32_t a_loads = 0;
+        uint32_t a_loads = 0, g = 0;
         for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
             const int mt = (int)(w / P.ntn), nt = (int)(w % P.ntn);
+            // the next tile's C goes to L2 now
+            if (w + 1 < w1 && !*abort_flag) {
+                const int mn = (int)((w + 1) / P.ntn), nn = (int)((w + 1) % P.ntn);
+                for (int h = 0; h < Cfg::C_BOXES; ++h)
+                    if ((uint32_t)nn * BN + 32u * h < P.N) tma_prefetch_2d(&tc, P.cx + nn * BN + 32 * h, P.cy + mn * MM_BM);
+            }
             if (mt != arow) {
                 if (!a_loads || wait(a_empty, (a_loads - 1) & 1u)) {
                     mbar_expect_tx(a_full, (uint32_t)(L * nkb) * Cfg::A_BLK);
@@ -277,26 +316,23 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 ++a_loads;
                 arow = mt;
             }
-            const uint32_t ph = it & 1u;
-            for (int kb = 0; kb < nkb; ++kb) {
-                if (wait(b_empty(kb), ph ^ 1u)) {
-                    mbar_expect_tx(b_full(kb), Cfg::B_KB);
-                    for (int l = 0; l < L; ++l)
-                        tma_load_3d(sB + (uint32_t)kb * Cfg::B_KB + (uint32_t)l * Cfg::B_BLK, &tb, b_full(kb),
-                                    P.bx + kb * MM_BK, P.by + nt * MM_BN, l);
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const uint32_t s = g % Cfg::NSLOT, use = g / Cfg::NSLOT;
+                if (wait(b_empty(s), (use & 1u) ^ 1u)) {
+                    // one box of all L digit planes: the slot holds digit 0's BN rows, then digit 1's...
+                    mbar_expect_tx(b_full(s), Cfg::B_BLK);
+                    tma_load_3d(sB + s * Cfg::B_BLK, &tb, b_full(s), P.bx + kb * MM_BK, P.by + nt * BN, 0);
                 }
-            }
-            // the tile's second 32-column half lies wholly past N on a ragged last tile: not moved
-            const int halves = P.N - (uint32_t)nt * MM_BN > 32u ? 2 : 1;
-            if (wait(c_empty, ph ^ 1u)) {
-                mbar_expect_tx(c_full, (uint32_t)halves * Cfg::C_HALF);
-                for (int h = 0; h < halves; ++h)
-                    tma_load_2d(sC + (uint32_t)h * Cfg::C_HALF, &tc, c_full, P.cx + nt * MM_BN + 32 * h,
-                                P.cy + mt * MM_BM);
             }
         }
     } else if (warp == 1) {
-        // ---- MMA issuer: the whole warp runs the loop (warp-uniform descriptors), lane 0 issues
+        // ---- MMA issuer: the whole warp runs the loop (warp-uniform descriptors), lane 0 issues.
+        // For each K step of 16 and each A digit i, one M=128, N=128, K=16 product of A_i with all
+        // L digits of B^T at once: its N columns are the products A_i B_j, j = 0..L-1, BN each,
+        // and its accumulator window starts at diagonal i, so A_i B_j lands on diagonal i + j.
+        // The first K step of a tile starts the diagonals: A_0's product overwrites diagonals
+        // 0..L-1, and A_i (i >= 1) opens diagonal i + L - 1 with its last digit alone (overwrite)
+        // while its other digits accumulate into diagonals the earlier digits opened.
         int arow = -1;
         uint32_t a_loads = 0;
         const uint32_t a_lo = sdesc_lo(sA), b_lo = sdesc_lo(sB);
@@ -308,112 +344,118 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 ++a_loads;
                 arow = mt;
             }
-            const uint32_t ph = it & 1u;
-            // 31-bit: region 0 (diagonals 0-3) over all of K, then region 1 (diagonals 4-6), so the
-            // epilogue drains one region while the other's products run.  16-bit: one region,
-            // alternating between tiles.
-            constexpr int NPH = Cfg::SPLIT ? 2 : 1;
+            const int set = (int)(it & 1u);
+            const bool ok = __all_sync(0xffffffffu, wait(r_empty(set), ((it >> 1) & 1u) ^ 1u));
+            tc_fence_after();
+            const uint32_t tbase = tmem + (uint32_t)set * Cfg::SET_COLS;
 #pragma unroll
-            for (int phs = 0; phs < NPH; ++phs) {
-                const int reg = Cfg::SPLIT ? phs : (int)(it & 1u);
-                const uint32_t use = Cfg::SPLIT ? it : (it >> 1);
-                const bool ok = __all_sync(0xffffffffu, wait(r_empty(reg), (use & 1u) ^ 1u));
-                tc_fence_after();
-                const uint32_t tbase = tmem + (Cfg::SPLIT ? 0u : (uint32_t)reg * Cfg::R1_COL);
+            for (int kb = 0; kb < Cfg::KB; ++kb) {
+                if (kb < nkb) {
+                    const uint32_t g = it * (uint32_t)nkb + (uint32_t)kb;
+                    const uint32_t s = g % Cfg::NSLOT;
+                    const bool have = __all_sync(0xffffffffu, wait(b_full(s), (g / Cfg::NSLOT) & 1u)) && ok;
+                    tc_fence_after();
+                    if (have && !*abort_flag && lane == 0) {
+                        // descriptor start addresses move in 16-byte units; apart from the slot's
+                        // base every offset below is a compile-time constant
+                        const uint32_t bs = b_lo + ((s * Cfg::B_BLK) >> 4);
 #pragma unroll
-                for (int kb = 0; kb < Cfg::KB; ++kb) {
-                    if (kb < nkb) {
-                        bool have = ok;
-                        if (phs == 0) {  // the K block arrives once per tile
-                            have = __all_sync(0xffffffffu, wait(b_full(kb), ph)) && ok;
-                            tc_fence_after();
-                        }
-                        if (have && !*abort_flag && lane == 0) {
-                            // descriptor start addresses move in 16-byte units; every offset below
-                            // is a compile-time constant, so each product is one add and the MMA
+                        for (int kk = 0; kk < MM_BK / 16; ++kk) {
 #pragma unroll
-                            for (int kk = 0; kk < MM_BK / 16; ++kk) {
-#pragma unroll
-                                for (int i = 0; i < L; ++i) {
-#pragma unroll
-                                    for (int j = 0; j < L; ++j) {
-                                        const int d = i + j;
-                                        if (region_of<L>(d) != phs) continue;
-                                        const bool first = kb == 0 && kk == 0 && first_pair<L>(i, j);
-                                        const uint32_t ao = ((uint32_t)(i * Cfg::KB + kb) * Cfg::A_BLK + kk * 32) >> 4;
-                                        const uint32_t bo =
-                                            ((uint32_t)kb * Cfg::B_KB + (uint32_t)j * Cfg::B_BLK + kk * 32) >> 4;
-                                        mma_bf16(tbase + dcol<L>(d), sdesc_of(a_lo + ao), sdesc_of(b_lo + bo), IDESC,
-                                                 first ? 0u : 1u);
-                                    }
+                            for (int i = 0; i < L; ++i) {
+                                const uint64_t ad = sdesc_of(a_lo + (((uint32_t)(i * Cfg::KB + kb) * Cfg::A_BLK + kk * 32) >> 4));
+                                const uint32_t bd = bs + ((kk * 32) >> 4);
+                                if (kb > 0 || kk > 0) {
+                                    mma_bf16(tbase + (uint32_t)(BN * i), ad, sdesc_of(bd), idesc(MM_MMA_N), 1u);
+                                } else if (i == 0) {
+                                    mma_bf16(tbase, ad, sdesc_of(bd), idesc(MM_MMA_N), 0u);
+                                } else {
+                                    // digits 0..L-2 of B^T (rows 0 .. (L-1) BN - 1), then digit L-1
+                                    mma_bf16(tbase + (uint32_t)(BN * i), ad, sdesc_of(bd), idesc(BN * (L - 1)), 1u);
+                                    mma_bf16(tbase + (uint32_t)(BN * (i + L - 1)), ad,
+                                             sdesc_of(bd + (((uint32_t)(L - 1) * BN * 128u) >> 4)), idesc(BN), 0u);
                                 }
                             }
                         }
-                        __syncwarp();
-                        // this K block of B^T may be refilled after its last use in the tile
-                        if (phs == NPH - 1 && lane == 0) mma_commit(b_empty(kb));
                     }
+                    __syncwarp();
+                    if (lane == 0) mma_commit(b_empty(s));  // the slot may be refilled once these are done
                 }
-                __syncwarp();
-                if (lane == 0) mma_commit(r_full(reg));  // the region's accumulators are ready
-                __syncwarp();
             }
+            __syncwarp();
+            if (lane == 0) mma_commit(r_full(set));  // the set's accumulators are ready
+            __syncwarp();
         }
     } else if (warp >= 2) {
-        // ---- epilogue: row r of the tile is tensor-memory lane r; warps 2..17 cover the four lane
-        // quarters four times, warp group g taking columns 16 g .. 16 g + 15 of the tile
-        const int quarter = warp & 3, grp = (warp - 2) >> 2;
-        const uint32_t r = (uint32_t)(32 * quarter + lane);
-        const uint32_t trow_off = ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * grp);
+        // ---- epilogue.  One thread (the storer) also moves C: it loads the C tile of a later
+        // tile into a buffer as soon as the store that last used the buffer has read it, so the
+        // producer's stream of B blocks never waits on the epilogue.
         const bool storer = warp == 2 && lane == 0;
+        auto load_c = [&](uint32_t itc) {  // C tile of the CTA's itc-th tile into buffer itc mod NCBUF
+            const uint32_t wc = w0 + itc;
+            if (wc >= w1 || *abort_flag) return;
+            const int mc = (int)(wc / P.ntn), nc = (int)(wc % P.ntn);
+            const int boxes = Cfg::C_BOXES == 2 && P.N - (uint32_t)nc * BN > 32u ? 2 : 1;
+            const uint32_t cbuf = itc % Cfg::NCBUF;
+            mbar_expect_tx(c_full(cbuf), (uint32_t)boxes * Cfg::C_BOX);
+            for (int h = 0; h < boxes; ++h)
+                tma_load_2d(sC + cbuf * Cfg::C_TILE + (uint32_t)h * Cfg::C_BOX, &tc, c_full(cbuf), P.cx + nc * BN + 32 * h,
+                            P.cy + mc * MM_BM);
+        };
+        if (storer)
+            for (uint32_t i = 0; i < (uint32_t)Cfg::NCBUF; ++i) load_c(i);
+        const uint32_t col0 = (uint32_t)(CPT * grp);                // first column in the tile
+        const uint32_t box = col0 / 32, chunk0 = (col0 % 32) / 4;  // its 32-column box, 16-byte chunk
         for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
             const int mt = (int)(w / P.ntn), nt = (int)(w % P.ntn);
-            const uint32_t ph = it & 1u;
+            const int set = (int)(it & 1u);
             // value = sum_d D_d 256^d = sum_d D_d rd[d] (mod p); |sum| < 7 2^23 2^31 < 2^57
-            long long acc[16];
+            long long acc[CPT];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0;
-            constexpr int NRG = Cfg::SPLIT ? 2 : 1;
-#pragma unroll
-            for (int rr = 0; rr < NRG; ++rr) {
-                const int reg = Cfg::SPLIT ? rr : (int)(it & 1u);
-                const uint32_t use = Cfg::SPLIT ? it : (it >> 1);
-                wait(r_full(reg), use & 1u);
-                tc_fence_after();
-                const uint32_t tb = tmem + trow_off + (Cfg::SPLIT ? 0u : (uint32_t)reg * Cfg::R1_COL);
-                const int d0 = Cfg::SPLIT ? (rr == 0 ? 0 : Cfg::R0_DIAG) : 0;
-                const int d1 = Cfg::SPLIT ? (rr == 0 ? Cfg::R0_DIAG : Cfg::DIAG) : Cfg::DIAG;
-                // one 16-column load per diagonal, the next in flight while one is summed
-                uint32_t va[16], vb[16];
-                tmem_ld16(tb + dcol<L>(d0), va);
+            for (int j = 0; j < CPT; ++j) acc[j] = 0;
+            wait(r_full(set), (it >> 1) & 1u);
+            tc_fence_after();
+            const uint32_t tb = trow + (uint32_t)set * Cfg::SET_COLS;
+            {
+                // one load per diagonal, the next in flight while one is summed
+                uint32_t va[CPT], vb[CPT];
+                tmem_ld<CPT>(tb, va);
                 tmem_wait_ld();
 #pragma unroll
                 for (int d = 0; d < Cfg::DIAG; ++d) {
-                    if (d < d0 || d >= d1) continue;
-                    const bool odd = ((d - d0) & 1) != 0;
-                    uint32_t(&cur)[16] = odd ? vb : va;
-                    uint32_t(&nxt)[16] = odd ? va : vb;
-                    if (d + 1 < d1) tmem_ld16(tb + dcol<L>(d + 1), nxt);  // in flight meanwhile
+                    uint32_t(&cur)[CPT] = (d & 1) ? vb : va;
+                    uint32_t(&nxt)[CPT] = (d & 1) ? va : vb;
+                    if (d + 1 < Cfg::DIAG) tmem_ld<CPT>(tb + (uint32_t)(BN * (d + 1)), nxt);  // in flight meanwhile
                     const long long rdd = (long long)P.rd[d];
+                    if (small_diag<L>(d)) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[j] += acc_int(cur[j]) * rdd;
-                    if (d + 1 < d1) tmem_wait_ld();
+                        for (int j = 0; j < CPT; ++j) acc[j] += acc_int_small(cur[j]) * rdd;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < CPT; ++j) acc[j] += acc_int(cur[j]) * rdd;
+                    }
+                    if (d + 1 < Cfg::DIAG) tmem_wait_ld();
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(r_empty(reg));  // the region may be overwritten
             }
-            uint32_t res[16];
+            // the set is drained: hand it back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(r_empty(set));
+            if (Cfg::NCBUF >= 2 && storer && it > 0) {
+                bulk_wait_read0();  // the previous tile's store has read its buffer: a later tile's C
+                load_c(it + Cfg::NCBUF - 1);
+            }
+            uint32_t res[CPT];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) res[j] = fp_reduce((uint64_t)(acc[j] + (long long)P.big), P.fp);
-            const bool have_c = wait(c_full, ph);
-            // columns 16 grp .. 16 grp + 15 are chunks 4 (grp & 1) .. + 3 of C half grp >> 1, row r:
-            // 128 bytes, 16-byte chunk j at chunk position j ^ (r mod 8)
-            unsigned char *crow = gbase + (sC - base) + (uint32_t)(grp >> 1) * Cfg::C_HALF + r * 128u;
+            for (int j = 0; j < CPT; ++j) res[j] = fp_reduce((uint64_t)(acc[j] + (long long)P.big), P.fp);
+            const uint32_t cb = it % Cfg::NCBUF;
+            const bool have_c = wait(c_full(cb), (it / Cfg::NCBUF) & 1u);
+            // row r of the thread's box: 128 bytes, 16-byte chunk j at chunk position j ^ (r mod 8)
+            unsigned char *crow = gbase + (sC - base) + cb * Cfg::C_TILE + box * Cfg::C_BOX + r * 128u;
             if (have_c) {
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const uint32_t j = (uint32_t)(4 * (grp & 1) + jj);
+                for (int jj = 0; jj < CPT / 4; ++jj) {
+                    const uint32_t j = chunk0 + (uint32_t)jj;
                     uint4 *q = reinterpret_cast<uint4 *>(crow + 16u * (j ^ (r & 7u)));
                     uint4 c = *q;
                     uint32_t *cw = reinterpret_cast<uint32_t *>(&c);
@@ -428,13 +470,16 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
             fence_async_smem();
             epi_sync();
             if (storer) {
-                const int halves = P.N - (uint32_t)nt * MM_BN > 32u ? 2 : 1;
+                const int boxes = Cfg::C_BOXES == 2 && P.N - (uint32_t)nt * BN > 32u ? 2 : 1;
                 if (!*abort_flag)
-                    for (int h = 0; h < halves; ++h)
-                        tma_store_2d(&tc, sC + (uint32_t)h * Cfg::C_HALF, P.cx + nt * MM_BN + 32 * h, P.cy + mt * MM_BM);
+                    for (int h = 0; h < boxes; ++h)
+                        tma_store_2d(&tc, sC + cb * Cfg::C_TILE + (uint32_t)h * Cfg::C_BOX, P.cx + nt * BN + 32 * h,
+                                     P.cy + mt * MM_BM);
                 bulk_commit();
-                bulk_wait_read0();  // the store has read the buffer: the next C tile may land there
-                mbar_arrive(c_empty);
+                if (Cfg::NCBUF == 1) {
+                    bulk_wait_read0();  // the buffer is free again: the next tile's C
+                    load_c(it + 1);
+                }
             }
         }
         if (storer) bulk_wait_all();
@@ -522,13 +567,13 @@ void encode(CUtensorMap *m, CUtensorMapDataType t, cuuint32_t rank, void *base, 
 }
 
 // digit planes [L][rows][kpad] (BF16), box of 64 K values x box_rows rows x 1 digit
-CUtensorMap digit_map(const DigitPlanes &D, uint32_t box_rows) {
+CUtensorMap digit_map(const DigitPlanes &D, uint32_t box_rows, uint32_t box_digits) {
     if (D.kpad % 8 || (reinterpret_cast<uintptr_t>(D.p) & 15))
         fail(GB_EDEVICE, "digit planes: row pitch or base not 16-byte aligned");
     CUtensorMap m;
     const cuuint64_t dims[3] = {D.K, D.rows, D.L};
     const cuuint64_t strides[2] = {2ull * D.kpad, 2ull * D.kpad * D.rows};
-    const cuuint32_t box[3] = {(cuuint32_t)MM_BK, box_rows, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)MM_BK, box_rows, box_digits};
     encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, D.p, dims, strides, box);
     return m;
 }
@@ -586,8 +631,8 @@ MmPlan::MmPlan(const DigitPlanes &A_, const DigitPlanes &B_, uint32_t *C_, uint6
     const uint32_t L = digits_for(fp.p);
     if (A->L != L || B->L != L) fail(GB_EDEVICE, "mm plan: digit count does not match p");
     if (ldc % 4 || (reinterpret_cast<uintptr_t>(C) & 15)) fail(GB_EDEVICE, "mm plan: C rows not 16-byte aligned");
-    maps->ta = digit_map(*A, MM_BM);
-    maps->tb = digit_map(*B, MM_BN);
+    maps->ta = digit_map(*A, MM_BM, 1);
+    maps->tb = digit_map(*B, MM_MMA_N / L, L);  // all digits of a tile's rows in one box
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {4ull * ldc};
     const cuuint32_t box[2] = {32u, (cuuint32_t)MM_BM};  // 128 bytes: the 128-byte swizzle span
@@ -623,7 +668,8 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
     P.by = (int)by;
     P.cx = (int)cx;
     P.cy = (int)cy;
-    P.ntn = (N + MM_BN - 1) / MM_BN;
+    const uint32_t bn = MM_MMA_N / A->L;
+    P.ntn = (N + bn - 1) / bn;
     const uint64_t items = (uint64_t)((M + MM_BM - 1) / MM_BM) * P.ntn;
     if (items >= (1ull << 31)) fail(GB_EUNSUPPORTED, "mm_update: too many tiles for one launch");
     P.items = (uint32_t)items;
