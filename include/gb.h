@@ -196,11 +196,14 @@ gb_status gb_echelon_destroy(gb_echelon *ech);
 gb_status gb_f4_step(gb_system *sys, gb_step_stats *stats);
 
 /* F4 steps until no pair remains, then the reduced Groebner basis: redundant elements dropped,
-   tails fully reduced, monic, sorted by leading monomial descending.  stats may be NULL. */
+   tails fully reduced, monic, sorted by leading monomial descending.  The basis stays in the
+   context's device arena (held by the system) until gb_basis_export copies it out or the system
+   is destroyed.  stats may be NULL. */
 gb_status gb_groebner(gb_system *sys, gb_run_stats *stats);
 
 /* The reduced basis after gb_groebner (reduced != 0), or the running basis in insertion order,
-   redundant elements included (reduced == 0). */
+   redundant elements included (reduced == 0).  Two-call pattern: with null arrays only npolys
+   and nterms are written; the terms then come from the device in one copy per array. */
 gb_status gb_basis_export(const gb_system *sys, int reduced, gb_polys_host *inout);
 /* Redundancy flags of the running basis (one byte per element; two-call pattern on *count). */
 gb_status gb_basis_redundant(const gb_system *sys, uint32_t *count, uint8_t *flags);

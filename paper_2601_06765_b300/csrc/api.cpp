@@ -77,6 +77,15 @@ void *ctx_pinned(gb_ctx *ctx, size_t bytes) {
     return p;
 }
 
+// GB_TRACE=1 in the environment: per-stage wall times of the final reduction on stderr
+bool trace_on() {
+    static const bool on = [] {
+        const char *e = std::getenv("GB_TRACE");
+        return e && *e && *e != '0';
+    }();
+    return on;
+}
+
 void ctx_sync(gb_ctx *ctx) {
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->arena.flush(ctx->stream);
@@ -479,10 +488,18 @@ gb_status gb_basis_export(const gb_system *S, int reduced, gb_polys_host *h) {
     if (reduced) {
         if (!S->finished) fail(GB_EINVAL, "the reduced basis exists after gb_groebner");
         h->npolys = (uint32_t)S->fin_off.size() - 1;
-        h->nterms = S->fin_cf.size();
+        h->nterms = S->fin_terms;
         if (h->poly_off) std::memcpy(h->poly_off, S->fin_off.data(), 4 * S->fin_off.size());
-        if (h->exps) std::memcpy(h->exps, S->fin_exps.data(), S->fin_exps.size());
-        if (h->coeffs) std::memcpy(h->coeffs, S->fin_cf.data(), 4 * S->fin_cf.size());
+        if ((h->exps || h->coeffs) && S->fin_terms) {
+            // the terms stay on the device after gb_groebner: one copy into the caller's arrays
+            Enter entered(S->ctx);
+            cudaStream_t st = S->ctx->stream;
+            if (h->exps)
+                GB_CUDA(cudaMemcpyAsync(h->exps, S->fin_exps.p, (size_t)S->fin_terms * n, cudaMemcpyDeviceToHost, st));
+            if (h->coeffs)
+                GB_CUDA(cudaMemcpyAsync(h->coeffs, S->fin_cf.p, 4ull * S->fin_terms, cudaMemcpyDeviceToHost, st));
+            GB_CUDA(cudaStreamSynchronize(st));
+        }
         return GB_OK;
     }
     gb_system *Sm = const_cast<gb_system *>(S);

@@ -657,14 +657,6 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
 
 // ---- the reduced basis ------------------------------------------------------------------------
 
-// GB_TRACE=1 in the environment: per-stage wall times of the final reduction on stderr
-static bool trace_on() {
-    static const bool on = [] {
-        const char *e = std::getenv("GB_TRACE");
-        return e && *e && *e != '0';
-    }();
-    return on;
-}
 
 void finish_batch(const std::vector<gb_system *> &Ss) {
     const size_t nj = Ss.size();
@@ -704,8 +696,9 @@ void finish_batch(const std::vector<gb_system *> &Ss) {
         gb_system *S = Ss[j];
         if (keep[j].empty()) {
             S->fin_off.assign(1, 0);
-            S->fin_exps.clear();
-            S->fin_cf.clear();
+            S->fin_exps.reset();
+            S->fin_cf.reset();
+            S->fin_terms = 0;
             continue;
         }
         SpTask t;

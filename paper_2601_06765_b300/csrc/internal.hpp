@@ -300,10 +300,12 @@ struct gb_system {
     bool unit = false;       // a constant input or element: the ideal is R
     bool finished = false;
     gb_run_stats run{};
-    // the reduced basis after gb_groebner
+    // the reduced basis after gb_groebner: element offsets on the host, the terms on the device
+    // (read by gb_basis_export straight into the caller's arrays)
     std::vector<uint32_t> fin_off;
-    std::vector<uint8_t> fin_exps;
-    std::vector<uint32_t> fin_cf;
+    gb::DBuf<uint8_t> fin_exps;  // fin_terms x n exponent bytes
+    gb::DBuf<uint32_t> fin_cf;   // fin_terms coefficients
+    uint64_t fin_terms = 0;
     // estimate of the device footprint (server admission)
     size_t footprint = 0;
 };
@@ -350,7 +352,8 @@ void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector
 void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::vector<uint32_t>> &elems);
 // a region of the context's page-locked staging area, valid until the next ctx_sync
 void *ctx_pinned(gb_ctx *ctx, size_t bytes);
-void ctx_sync(gb_ctx *ctx);                     // synchronise the stream, release deferred blocks
+void ctx_sync(gb_ctx *ctx);
+bool trace_on();  // GB_TRACE set in the environment: stage timings on stderr                     // synchronise the stream, release deferred blocks
 // run fn(i) for i in [0, n) on the context's host workers and the calling thread
 void parallel_for(gb_ctx *ctx, size_t n, const std::function<void(size_t)> &fn);
 // exclusive scan of n u32 values on the stream; out has n + 1 entries (out[n] = total)

@@ -15,6 +15,9 @@
 
 #include <cooperative_groups.h>
 
+#include <chrono>
+#include <cstdio>
+
 #include "internal.hpp"
 
 namespace gb {
@@ -1457,6 +1460,8 @@ void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::v
     Arena &ar = ctx->arena;
     cudaStream_t st = ctx->stream;
     const int nj = (int)Es.size();
+    const auto tt0 = std::chrono::steady_clock::now();
+    auto tms = [&] { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tt0).count(); };
     // element elems[j][i] becomes LM + (row i of job j's D'), compacted on the device
     uint64_t tot = 0;
     std::vector<uint64_t> roff(nj);
@@ -1468,8 +1473,9 @@ void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::v
         for (int j = 0; j < nj; ++j) {
             gb_system *S = Es[j]->mac->sys;
             S->fin_off.assign(1, 0);
-            S->fin_exps.clear();
-            S->fin_cf.clear();
+            S->fin_exps.reset();
+            S->fin_cf.reset();
+            S->fin_terms = 0;
         }
         return;
     }
@@ -1511,20 +1517,18 @@ void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::v
         ctx_sync(ctx);
         std::memcpy(hs.data(), hp, 4ull * (tot + 1));
     }
-    uint64_t bytes = 0;
-    std::vector<uint64_t> eoff(nj);
+    const double t_count = tms();
+    // each system's terms go to device buffers of its own, which it keeps
     for (int j = 0; j < nj; ++j) {
-        eoff[j] = bytes;
-        bytes += (uint64_t)(hs[roff[j] + elems[j].size()] - hs[roff[j]]) * Es[j]->mac->n;
-    }
-    DBuf<uint8_t> dex;
-    DBuf<uint32_t> dcf;
-    dex.alloc(ar, bytes, st);
-    dcf.alloc(ar, hs[tot], st);
-    for (int j = 0; j < nj; ++j) {
-        // a job's terms start at its own offset of the concatenated output
-        J[j].ocf = dcf.p + hs[roff[j]];
-        J[j].oexp = dex.p + eoff[j];
+        gb_system *S = Es[j]->mac->sys;
+        const uint32_t b = hs[roff[j]], e = hs[roff[j] + elems[j].size()];
+        S->fin_off.resize(elems[j].size() + 1);
+        for (size_t i = 0; i <= elems[j].size(); ++i) S->fin_off[i] = hs[roff[j] + i] - b;
+        S->fin_terms = e - b;
+        S->fin_cf.alloc(ar, e - b, st);
+        S->fin_exps.alloc(ar, (size_t)(e - b) * S->n, st);
+        J[j].ocf = S->fin_cf.p;
+        J[j].oexp = S->fin_exps.p;
     }
     {
         Grouped<RowsJob> G;
@@ -1532,22 +1536,10 @@ void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::v
         k_write_rows<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
         counted();
     }
-    // the terms come back through the page-locked staging area (one DMA, no pageable bounce) and
-    // are copied once into each system's result
-    const size_t cbytes = (4ull * hs[tot] + 255) & ~size_t(255);
-    char *hp = static_cast<char *>(ctx_pinned(ctx, cbytes + bytes + 16));
-    const uint32_t *allc = reinterpret_cast<const uint32_t *>(hp);
-    const uint8_t *allx = reinterpret_cast<const uint8_t *>(hp + cbytes);
-    GB_CUDA(cudaMemcpyAsync(hp, dcf.p, 4ull * hs[tot], cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaMemcpyAsync(hp + cbytes, dex.p, bytes, cudaMemcpyDeviceToHost, st));
-    ctx_sync(ctx);
-    for (int j = 0; j < nj; ++j) {
-        gb_system *S = Es[j]->mac->sys;
-        const uint32_t b = hs[roff[j]], e = hs[roff[j] + elems[j].size()], n = S->n;
-        S->fin_off.resize(elems[j].size() + 1);
-        for (size_t i = 0; i <= elems[j].size(); ++i) S->fin_off[i] = hs[roff[j] + i] - b;
-        S->fin_cf.assign(allc + b, allc + e);
-        S->fin_exps.assign(allx + eoff[j], allx + eoff[j] + (size_t)(e - b) * n);
+    if (trace_on()) {
+        ctx_sync(ctx);
+        std::fprintf(stderr, "[gb] tails: %llu rows, %u terms; count+scan %.3f ms, write %.3f ms\n",
+                     (unsigned long long)tot, hs[tot], t_count, tms() - t_count);
     }
 }
 
