@@ -110,7 +110,7 @@ def run_ours(args) -> None:
     import torch
 
     import paper_2601_06765_b300 as gb
-    from paper_2601_06765_b300 import synth
+    from paper_2601_06765_b300 import shard, synth
 
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
@@ -160,14 +160,7 @@ def run_ours(args) -> None:
         S.close()
     total_ms = sum(ms)
     nnz = sum(r["nnz_total"] for r in runs)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        c = torch.tensor([nnz], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(c)
-        nnz = float(c.item())
+    total_ms, nnz = shard.aggregate(total_ms, nnz)  # slowest rank, all ranks' nonzeros
     value = nnz / (total_ms / 1e3)
 
     # end to end through the C ABI: host arrays in, reduced basis out, copies inside the region
@@ -200,7 +193,7 @@ def run_ours(args) -> None:
                 "peak_source": f"{pk['source']} HBM copy bandwidth",
                 "traffic": profile_traffic("k_reduce_config2")}
 
-    batched = measure_batched(gb, synth, ctx) if rank == 0 and not args.no_batch else None
+    batched = measure_batched(gb, synth, ctx, rank, world) if not args.no_batch else None
     served = measure_served(gb, synth, ctx) if rank == 0 and not args.no_batch else None
     tensor = measure_tensor_core(gb, local) if rank == 0 and not args.no_batch else None
     big = measure_config3(gb, synth, local, pk) if rank == 0 and not args.no_batch else None
@@ -241,21 +234,25 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
-def _plain_vs_batched(gb, ctx, systems) -> dict:
+def _plain_vs_batched(gb, ctx, systems, rank: int = 0, world: int = 1) -> dict:
     """The same systems run one after another through gb_groebner (plain) and as one
-    gb_batch_groebner call (batched, lockstep); wall clock of each, nnz rate of each."""
-    out = {"systems": len(systems)}
+    gb_batch_groebner call (batched, lockstep); wall clock of each, nnz rate of each.  Under
+    several ranks each runs its share of the systems (no data exchange) and the numbers are the
+    slowest rank's time over all ranks' systems."""
+    from paper_2601_06765_b300 import shard
+    mine = [systems[i] for i in shard.shard([shard.system_weight(s) for s in systems], rank, world)]
+    out = {"systems": len(systems), "ranks": world}
     for mode in ("plain", "batched"):
-        hs = [gb.gb_system_create(ctx.h, s) for s in systems]
+        hs = [gb.gb_system_create(ctx.h, s) for s in mine]
         t0 = time.perf_counter()
         if mode == "plain":
             stats = [gb.gb_groebner(h) for h in hs]
         else:
-            stats = gb.gb_batch_groebner(ctx.h, hs)
-        dt = time.perf_counter() - t0
+            stats = gb.gb_batch_groebner(ctx.h, hs) if hs else []
+        dt_ms, nnz = shard.aggregate((time.perf_counter() - t0) * 1e3, sum(st["nnz_total"] for st in stats))
+        dt = dt_ms / 1e3
         for h in hs:
             gb.gb_system_destroy(h)
-        nnz = sum(st["nnz_total"] for st in stats)
         out[f"{mode}_ms"] = round(dt * 1e3, 2)
         out[f"{mode}_nnz_per_s"] = nnz / dt
         out[f"{mode}_systems_per_s"] = len(systems) / dt
@@ -267,15 +264,15 @@ def _max_degree(s: dict) -> int:
     return int(s["exps"].reshape(-1, s["n"]).sum(axis=1).max())
 
 
-def measure_batched(gb, synth, ctx) -> list:
+def measure_batched(gb, synth, ctx, rank: int = 0, world: int = 1) -> list:
     """Two batches, each run plain and batched: the n=8 dense quadratic system modulo the 128
     largest primes below 2^31, and the 256-system mixed batch without its cubic members in 8 or 9
     variables (those alone run for seconds to minutes each, beyond a bench line's budget)."""
     primes = synth.multi_prime_system(synth.largest_primes_below(2 ** 31, 128))
     mixed = [s for s in synth.mixed_batch(256) if not (_max_degree(s) == 3 and s["n"] >= 8)]
-    a = _plain_vs_batched(gb, ctx, primes)
+    a = _plain_vs_batched(gb, ctx, primes, rank, world)
     a["workload"] = "n=8 dense quadratic system modulo the 128 largest primes below 2^31"
-    b = _plain_vs_batched(gb, ctx, mixed)
+    b = _plain_vs_batched(gb, ctx, mixed, rank, world)
     b["workload"] = (f"{len(mixed)} of the 256 mixed systems (n ~ U{{5..9}}, degree 2 or 3, 10-40 terms, "
                      "p=65521): all but the cubic ones with n >= 8")
     return [a, b]
