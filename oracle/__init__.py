@@ -65,6 +65,8 @@ def _load(path: str | None = None):
     lib.or_pairs.argtypes = [P, i32p]
     lib.or_final_size.argtypes = [P, i64p]
     lib.or_final.argtypes = [P, u32p, u8p, u32p]
+    lib.or_reduce_row.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.c_int, u32p, u32p, u32p, u32p, u32p,
+                                  ctypes.c_uint32, ctypes.c_int, u32p, u32p]
     if path is None:
         _lib = lib
     return lib
@@ -245,6 +247,22 @@ class Oracle:
         for i in range(len(off) - 1):
             out.append([(tuple(int(x) for x in e[j]), int(c[j])) for j in range(off[i], off[i + 1])])
         return out
+
+
+def reduce_row(p: int, ndict: int, npivot: int, row_ptr: np.ndarray, col: np.ndarray, val: np.ndarray,
+               rcol: np.ndarray, rval: np.ndarray, nonpiv: np.ndarray) -> np.ndarray:
+    """D' of one row (Sec. 9.2): the row (rcol ascending, rval) reduced by the npivot monic pivot
+    rows that open the CSR matrix (row_ptr, col, val over ndict columns), read at the non-pivot
+    columns nonpiv -- the same loop the oracle's step runs for each of its non-pivot rows."""
+    lib = _load()
+    u32 = lambda a: np.ascontiguousarray(a, dtype=np.uint32)
+    row_ptr, col, val, rcol, rval, nonpiv = map(u32, (row_ptr, col, val, rcol, rval, nonpiv))
+    out = np.zeros(max(len(nonpiv), 1), dtype=np.uint32)
+    P = ctypes.POINTER(ctypes.c_uint32)
+    lib.or_reduce_row(p, ndict, npivot, _ptr(row_ptr, ctypes.c_uint32), _ptr(col, ctypes.c_uint32),
+                      _ptr(val, ctypes.c_uint32), _ptr(rcol, ctypes.c_uint32), _ptr(rval, ctypes.c_uint32),
+                      len(rcol), len(nonpiv), _ptr(nonpiv, ctypes.c_uint32), _ptr(out, ctypes.c_uint32))
+    return out[:len(nonpiv)]
 
 
 def groebner(system: dict, flags: int = 0, lib=None):

@@ -399,6 +399,27 @@ static void push_row(orow **rows, int *nr, int *cap, omono t, int k, int reducer
 }
 
 /* Returns 1 if a step ran, 0 if no pairs remain. */
+/* One non-pivot row of the structured elimination (Sec. 9.2): the row is reduced by the monic
+   pivot rows (piv_of_col[c]: the pivot row whose leading column is c, or -1), pivot columns in
+   ascending order from the row's leading column `start`; the result is read at the non-pivot
+   columns.  acc holds N zeros on entry and on return. */
+static void reduce_row(uint32_t p, int N, const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
+                       const int *piv_of_col, uint64_t *acc, int start, const uint32_t *rcol, const uint32_t *rval,
+                       uint32_t rlen, int nb, const uint32_t *nonpiv, uint32_t *out) {
+    for (uint32_t q = 0; q < rlen; ++q) acc[rcol[q]] = rval[q];
+    for (int c = start; c < N; ++c) {
+        uint32_t f = (uint32_t)(acc[c] % p);
+        acc[c] = f;
+        int pr = piv_of_col[c];
+        if (pr < 0 || f == 0) continue;
+        uint32_t mf = p - f; /* v <- v - f * pivot row */
+        for (uint32_t q = row_ptr[pr]; q < row_ptr[pr + 1]; ++q)
+            acc[col[q]] = (acc[col[q]] + (uint64_t)mf * val[q]) % p;
+    }
+    for (int j = 0; j < nb; ++j) out[j] = (uint32_t)(acc[nonpiv[j]] % p);
+    memset(acc, 0, sizeof(uint64_t) * (size_t)N);
+}
+
 int or_step(osys *S) {
     int n = S->n;
     uint32_t p = S->p;
@@ -532,21 +553,11 @@ int or_step(osys *S) {
         if (piv_of_col[c] < 0) { pos_of_col[c] = nb; nonpiv[nb++] = (uint32_t)c; }
     }
     uint32_t *dprime = (uint32_t *)calloc((size_t)nC * (size_t)nb + 1, sizeof(uint32_t));
-    uint64_t *acc = (uint64_t *)xrealloc(NULL, sizeof(uint64_t) * (size_t)(N ? N : 1));
+    uint64_t *acc = (uint64_t *)calloc((size_t)(N ? N : 1), sizeof(uint64_t));
     for (int i = 0; i < nC; ++i) {
         int a = nA + i;
-        memset(acc, 0, sizeof(uint64_t) * (size_t)N);
-        for (uint32_t q = row_ptr[a]; q < row_ptr[a + 1]; ++q) acc[col[q]] = val[q];
-        for (int c = rows[a].lm_col; c < N; ++c) {
-            uint32_t f = (uint32_t)(acc[c] % p);
-            acc[c] = f;
-            int pr = piv_of_col[c];
-            if (pr < 0 || f == 0) continue;
-            uint32_t mf = p - f; /* v <- v - f * pivot row */
-            for (uint32_t q = row_ptr[pr]; q < row_ptr[pr + 1]; ++q)
-                acc[col[q]] = (acc[col[q]] + (uint64_t)mf * val[q]) % p;
-        }
-        for (int j = 0; j < nb; ++j) dprime[(size_t)i * nb + j] = (uint32_t)(acc[nonpiv[j]] % p);
+        reduce_row(p, N, row_ptr, col, val, piv_of_col, acc, rows[a].lm_col, col + row_ptr[a], val + row_ptr[a],
+                   row_ptr[a + 1] - row_ptr[a], nb, nonpiv, dprime + (size_t)i * nb);
     }
     free(acc);
     free(piv_of_col);
@@ -740,6 +751,21 @@ osys *or_new(int n, uint32_t p, int m, const uint32_t *poly_off, const uint8_t *
     }
     (void)unit; /* a constant input makes every other LM redundant; R9 then yields {1} */
     return S;
+}
+
+/* D' of one non-pivot row of a Macaulay matrix given as CSR (the nA pivot rows first, each monic
+   with its leading column first; columns ascending within a row): the row (rcol, rval) reduced by
+   the pivot rows and read at the nb non-pivot columns, exactly as or_step reduces its own rows. */
+void or_reduce_row(uint32_t p, int N, int nA, const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
+                   const uint32_t *rcol, const uint32_t *rval, uint32_t rlen, int nb, const uint32_t *nonpiv,
+                   uint32_t *out) {
+    int *piv_of_col = (int *)xrealloc(NULL, sizeof(int) * (size_t)(N ? N : 1));
+    for (int c = 0; c < N; ++c) piv_of_col[c] = -1;
+    for (int a = 0; a < nA; ++a) piv_of_col[col[row_ptr[a]]] = a;
+    uint64_t *acc = (uint64_t *)calloc((size_t)(N ? N : 1), sizeof(uint64_t));
+    reduce_row(p, N, row_ptr, col, val, piv_of_col, acc, rlen ? (int)rcol[0] : N, rcol, rval, rlen, nb, nonpiv, out);
+    free(acc);
+    free(piv_of_col);
 }
 
 void or_free(osys *S) {

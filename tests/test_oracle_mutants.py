@@ -38,8 +38,8 @@ MUTANTS = {
                                    "        for (int g = 0; g < S->ng; ++g)\n            if (m_divides(&S->g[g].mon[0], m, S->n)) return g;"),
     "pivot_pair_row_largest_k": ("if (best[c] < 0 || rows[a].k < rows[best[c]].k) best[c] = a;",
                                  "if (best[c] < 0 || rows[a].k > rows[best[c]].k) best[c] = a;"),
-    "reduction_starts_one_column_late": ("for (int c = rows[a].lm_col; c < N; ++c) {",
-                                         "for (int c = rows[a].lm_col + 1; c < N; ++c) {"),
+    "reduction_starts_one_column_late": ("    for (int c = start; c < N; ++c) {",
+                                         "    for (int c = start + 1; c < N; ++c) {"),
     "tail_not_reduced": ("        opoly r = full_reduce(S, &tail, B, nB);",
                          "        opoly r = full_reduce(S, &tail, B, 0);"),
 }

@@ -4,6 +4,7 @@ the inputs, the variety by brute force, uniqueness of the reduced basis across o
 and, per F4 step, the dictionary / matrix / closure / echelon statements of Sec. 11."""
 from __future__ import annotations
 
+import numpy as np
 import pytest
 from sympy import GF
 from sympy.polys.matrices import DomainMatrix
@@ -229,6 +230,22 @@ def check_reduction_and_echelon(system, lib=None, limit=6):
         want = [[row[c] for c in nonpiv] for row, pc in zip(Rl, pivots) if pc in set(nonpiv)]
         assert d.rref.tolist() == want
         assert [nonpiv[int(j)] for j in d.rref_piv] == [pc for pc in pivots if pc in set(nonpiv)]
+
+
+@pytest.mark.parametrize("system", [synth.dense_system(4, 4, 65521, 17),
+                                    synth.dense_system(3, 3, 2147483647, 18),
+                                    synth.sparse_system(5, 5, 65521, 19, (4, 12))],
+                         ids=["n4", "n3p31", "n5sparse"])
+def test_single_row_reduction_reproduces_dprime(system):
+    """oracle.reduce_row (one non-pivot row reduced alone by the pivot rows, Sec. 9.2) gives the
+    rows of D' that the step computes and the test above pins against the library RREF; the
+    full-size GPU checks of D' rely on it."""
+    for _, d in _steps(system, limit=6):
+        for i in range(d.dprime.shape[0]):
+            a = d.nA + i
+            s, e = int(d.row_ptr[a]), int(d.row_ptr[a + 1])
+            got = oracle.reduce_row(system["p"], d.N, d.nA, d.row_ptr, d.col, d.val, d.col[s:e], d.val[s:e], d.nonpiv)
+            assert np.array_equal(got, d.dprime[i])
 
 
 def test_kernel_vectors_are_syzygies():
