@@ -417,24 +417,22 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
             tc_fence_after();
             const uint32_t tb = trow + (uint32_t)set * Cfg::SET_COLS;
             {
-                // one load per diagonal, the next in flight while one is summed
-                uint32_t va[CPT], vb[CPT];
-                tmem_ld<CPT>(tb, va);
+                // every diagonal's load in flight at once, one wait: the drain pays one tensor-memory
+                // latency instead of one per diagonal
+                uint32_t v[Cfg::DIAG][CPT];
+#pragma unroll
+                for (int d = 0; d < Cfg::DIAG; ++d) tmem_ld<CPT>(tb + (uint32_t)(BN * d), v[d]);
                 tmem_wait_ld();
 #pragma unroll
                 for (int d = 0; d < Cfg::DIAG; ++d) {
-                    uint32_t(&cur)[CPT] = (d & 1) ? vb : va;
-                    uint32_t(&nxt)[CPT] = (d & 1) ? va : vb;
-                    if (d + 1 < Cfg::DIAG) tmem_ld<CPT>(tb + (uint32_t)(BN * (d + 1)), nxt);  // in flight meanwhile
                     const long long rdd = (long long)P.rd[d];
                     if (small_diag<L>(d)) {
 #pragma unroll
-                        for (int j = 0; j < CPT; ++j) acc[j] += acc_int_small(cur[j]) * rdd;
+                        for (int j = 0; j < CPT; ++j) acc[j] += acc_int_small(v[d][j]) * rdd;
                     } else {
 #pragma unroll
-                        for (int j = 0; j < CPT; ++j) acc[j] += acc_int(cur[j]) * rdd;
+                        for (int j = 0; j < CPT; ++j) acc[j] += acc_int(v[d][j]) * rdd;
                     }
-                    if (d + 1 < Cfg::DIAG) tmem_wait_ld();
                 }
             }
             // the set is drained: hand it back
