@@ -118,7 +118,7 @@ def run_ours(args) -> None:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     system = synth.config2(0)
-    ctx = gb.Context(device=local, arena_bytes=args.arena_gb << 30)
+    ctx = gb.Context(device=local, arena_bytes=args.arena_gb << 30, graphs=not args.no_graphs)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 126 MB L2
 
     def barrier():
@@ -132,9 +132,11 @@ def run_ours(args) -> None:
         with gb.System(ctx, system) as S:
             S.groebner()
     # the reduction schedules of this workload's shape buckets, measured on this device (untimed)
-    th = gb.gb_system_create(ctx.h, system)
-    tune = gb.gb_autotune(ctx.h, [th])
-    gb.gb_system_destroy(th)
+    tune = None
+    if not args.no_tune:
+        th = gb.gb_system_create(ctx.h, system)
+        tune = gb.gb_autotune(ctx.h, [th])
+        gb.gb_system_destroy(th)
     systems = [gb.System(ctx, system) for _ in range(args.steps)]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -217,8 +219,9 @@ def run_ours(args) -> None:
                     "h2d_bytes_per_step": input_bytes(system), "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "graph_launches": graphs,
-            "autotune": {**{k: (round(v, 1) if isinstance(v, float) else v) for k, v in tune.items()},
-                         "note": "gb_autotune on this workload before the timed region; the timed runs use its table"},
+            "autotune": None if tune is None else {
+                **{k: (round(v, 1) if isinstance(v, float) else v) for k, v in tune.items()},
+                "note": "gb_autotune on this workload before the timed region; the timed runs use its table"},
             "batched": batched,
             "served": served,
             "tensor_core": tensor,
@@ -471,6 +474,10 @@ def main() -> None:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and served lines")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the RREF rounds from the host (GB_CTX_NO_GRAPHS): complete ncu launch lists")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="run the workload on the shape rules, without gb_autotune before the timed region")
     ap.add_argument("--arena-gb", type=int, default=32, help="device arena of the context (GiB)")
     ap.add_argument("--only", choices=["tensor", "config3"], default=None,
                     help="run one secondary measurement alone and print its JSON (for profiling)")
