@@ -606,24 +606,31 @@ constexpr int PT = 1024;
 template <bool SMEM>
 __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ jobs, const int *__restrict__ list) {
     extern __shared__ __align__(16) uint32_t pan[];
-    __shared__ uint32_t mult[KP], prow[KP], pslot[KP], pc[KP], red[32];
+    __shared__ uint32_t mult[KP], prow[KP], pslot[KP], pc[KP], red[32], s_row[KP];
     __shared__ uint32_t s_inv;
     const RrefJob &X = jobs[list[blockIdx.x]];
     const Fp fp = X.fp;
     const uint32_t P = X.state[1], nb = X.nb;
+    if (threadIdx.x < KP) s_row[threadIdx.x] = threadIdx.x < P ? X.panel[threadIdx.x] : 0u;
+    __syncthreads();
     auto rowp = [&](uint32_t t) -> uint32_t * {
-        return SMEM ? pan + (size_t)t * nb : X.M + (size_t)X.panel[t] * X.ldm;
+        return SMEM ? pan + (size_t)t * nb : X.M + (size_t)s_row[t] * X.ldm;
     };
-    if (SMEM) {
-        for (uint32_t t = 0; t < P; ++t) {
-            const uint32_t *src = X.M + (size_t)X.panel[t] * X.ldm;
-            for (uint32_t j = threadIdx.x; j < nb; j += PT) pan[(size_t)t * nb + j] = src[j];
+    if (SMEM) {  // all of a thread's loads in flight before its stores
+        for (uint32_t j = threadIdx.x; j < nb; j += PT) {
+            uint32_t v[KP];
+#pragma unroll
+            for (uint32_t t = 0; t < KP; ++t)
+                if (t < P) v[t] = X.M[(size_t)s_row[t] * X.ldm + j];
+#pragma unroll
+            for (uint32_t t = 0; t < KP; ++t)
+                if (t < P) pan[(size_t)t * nb + j] = v[t];
         }
         __syncthreads();
     }
     uint32_t nnew = 0;
     for (uint32_t t = 0; t < P; ++t) {
-        const uint32_t r = X.panel[t];
+        const uint32_t r = s_row[t];
         uint32_t *row = rowp(t);
         // multipliers: entries at the panel's earlier pivots, negated (those pivot rows are RREF
         // among themselves, so each multiplier is read from the unreduced row)
@@ -635,11 +642,19 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
         uint32_t c = NOLEAD;
         for (uint32_t j = threadIdx.x; j < nb; j += PT) {
             uint64_t acc = row[j];
-            if (fp.small) {  // raw products < 2^32, at most 32 of them: one reduction per entry
-                for (uint32_t k = 0; k < nnew; ++k) acc += (uint64_t)(mult[k] * rowp(pslot[k])[j]);
+            // four earlier pivot rows per iteration, their loads independent
+            if (fp.small) {  // raw products < 2^32, at most KP of them: one reduction per entry
+                for (uint32_t k0 = 0; k0 < nnew; k0 += 4) {
+#pragma unroll
+                    for (uint32_t u = 0; u < 4; ++u)
+                        if (k0 + u < nnew) acc += (uint64_t)(mult[k0 + u] * rowp(pslot[k0 + u])[j]);
+                }
             } else {
-                for (uint32_t k = 0; k < nnew; ++k)
-                    if (mult[k]) acc += fp_mul(mult[k], rowp(pslot[k])[j], fp);
+                for (uint32_t k0 = 0; k0 < nnew; k0 += 4) {
+#pragma unroll
+                    for (uint32_t u = 0; u < 4; ++u)
+                        if (k0 + u < nnew && mult[k0 + u]) acc += fp_mul(mult[k0 + u], rowp(pslot[k0 + u])[j], fp);
+                }
             }
             const uint32_t x = nnew ? fp_reduce(acc, fp) : (uint32_t)acc;
             if (nnew) row[j] = x;
@@ -650,7 +665,7 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
             if (threadIdx.x == 0) X.lead[r] = NOLEAD;
             continue;
         }
-        if (threadIdx.x == 0) s_inv = fp_inv(row[c], fp);
+        if (threadIdx.x == 0) s_inv = fp.small ? fp_inv_small(row[c], fp) : fp_inv(row[c], fp);
         __syncthreads();
         const uint32_t inv = s_inv;
         for (uint32_t j = c + threadIdx.x; j < nb; j += PT) row[j] = fp_mul(row[j], inv, fp);
@@ -659,14 +674,21 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
             mult[threadIdx.x] = v ? fp.p - v : 0u;
         }
         __syncthreads();
-        // clear column c from the earlier new rows
-        for (uint32_t k = 0; k < nnew; ++k) {
-            const uint32_t mk = mult[k];
-            if (!mk) continue;
-            uint32_t *dst = rowp(pslot[k]);
-            for (uint32_t j = c + threadIdx.x; j < nb; j += PT) {
-                const uint32_t y = row[j];
-                if (y) dst[j] = fp_reduce((uint64_t)dst[j] + (uint64_t)mk * y, fp);
+        // clear column c from the earlier new rows: per column, every earlier row at once
+        for (uint32_t j = c + threadIdx.x; j < nb; j += PT) {
+            const uint32_t y = row[j];
+            if (!y) continue;
+            for (uint32_t k0 = 0; k0 < nnew; k0 += 4) {
+#pragma unroll
+                for (uint32_t u = 0; u < 4; ++u) {
+                    const uint32_t k = k0 + u;
+                    if (k >= nnew) break;
+                    const uint32_t mk = mult[k];
+                    if (!mk) continue;
+                    uint32_t *dst = rowp(pslot[k]) + j;
+                    *dst = fp.small ? fp_add(*dst, fp_reduce32(mk * y, fp), fp)
+                                    : fp_reduce((uint64_t)*dst + (uint64_t)mk * y, fp);
+                }
             }
         }
         if (threadIdx.x == 0) {
@@ -680,9 +702,14 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
         ++nnew;
     }
     if (SMEM) {  // write the panel back (pivot rows reduced, the others now zero)
-        for (uint32_t t = 0; t < P; ++t) {
-            uint32_t *dst = X.M + (size_t)X.panel[t] * X.ldm;
-            for (uint32_t j = threadIdx.x; j < nb; j += PT) dst[j] = pan[(size_t)t * nb + j];
+        for (uint32_t j = threadIdx.x; j < nb; j += PT) {
+            uint32_t v[KP];
+#pragma unroll
+            for (uint32_t t = 0; t < KP; ++t)
+                if (t < P) v[t] = pan[(size_t)t * nb + j];
+#pragma unroll
+            for (uint32_t t = 0; t < KP; ++t)
+                if (t < P) X.M[(size_t)s_row[t] * X.ldm + j] = v[t];
         }
     }
     if (threadIdx.x < nnew) {
