@@ -114,14 +114,21 @@ __global__ void __launch_bounds__(IW * 32) k_invert_chunk_tri(const RedJob *__re
         W[r * TS + lane] = r == lane ? 1u : 0u;
     }
     __syncwarp();
+    // the sums are kept lazily in 64 bits and reduced once per entry: below 31 * 2^32 for p < 2^16
+    // (raw products of two residues), below 31 p for larger p (each product reduced)
     for (int i = 1; i < CW; ++i) {
         if (lane < i) {
-            uint32_t acc = 0;
-            for (int k = lane; k < i; ++k) {
-                const uint32_t u = U[k * TS + i];
-                if (u) acc = fp_add(acc, fp_mul(W[lane * TS + k], u, fp), fp);
+            uint64_t acc = 0;
+            if (fp.small) {
+                for (int k = lane; k < i; ++k) acc += (uint64_t)(W[lane * TS + k] * U[k * TS + i]);
+            } else {
+                for (int k = lane; k < i; ++k) {
+                    const uint32_t u = U[k * TS + i];
+                    if (u) acc += fp_mul(W[lane * TS + k], u, fp);
+                }
             }
-            W[lane * TS + i] = acc ? fp.p - acc : 0u;
+            const uint32_t sum = fp_reduce(acc, fp);
+            W[lane * TS + i] = sum ? fp.p - sum : 0u;
         }
         __syncwarp();
     }
