@@ -2,6 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#if defined(__SSE2__)
+#include <emmintrin.h>
+#endif
 #include <atomic>
 #include <condition_variable>
 #include <cstdint>
@@ -171,6 +174,28 @@ inline M16 m16(const Mono &m) {
 }
 inline bool operator==(const M16 &a, const M16 &b) { return a.lo == b.lo && a.hi == b.hi; }
 constexpr uint64_t SWAR_H = 0x8080808080808080ull, SWAR_L = 0x7F7F7F7F7F7F7F7Full;
+#if defined(__SSE2__)
+// byte-wise monomial tests with SSE2 (every x86-64 host has it): one vector per monomial
+inline __m128i v16(const M16 &a) { return _mm_set_epi64x((long long)a.hi, (long long)a.lo); }
+inline bool divides16(const M16 &a, const M16 &b) {  // a | b: every byte of a at most b's
+    const __m128i x = v16(a), y = v16(b);
+    return _mm_movemask_epi8(_mm_cmpeq_epi8(_mm_max_epu8(x, y), y)) == 0xFFFF;
+}
+inline M16 lcm16(const M16 &a, const M16 &b) {
+    const __m128i m = _mm_max_epu8(v16(a), v16(b));
+    M16 r;
+    _mm_storeu_si128(reinterpret_cast<__m128i *>(&r), m);
+    return r;
+}
+inline bool coprime16(const M16 &a, const M16 &b) {
+    return _mm_movemask_epi8(_mm_cmpeq_epi8(_mm_min_epu8(v16(a), v16(b)), _mm_setzero_si128())) == 0xFFFF;
+}
+inline uint32_t deg16(const M16 &a) {
+    const __m128i s = _mm_sad_epu8(v16(a), _mm_setzero_si128());  // two 64-bit byte sums
+    return (uint32_t)(_mm_cvtsi128_si64(s) + _mm_cvtsi128_si64(_mm_unpackhi_epi64(s, s)));
+}
+#else
+// the same with 64-bit SWAR words (exponents below 128)
 inline bool ge_all(uint64_t b, uint64_t a) { return (((b | SWAR_H) - a) & SWAR_H) == SWAR_H; }
 inline bool divides16(const M16 &a, const M16 &b) { return ge_all(b.lo, a.lo) && ge_all(b.hi, a.hi); }
 inline uint64_t max8(uint64_t a, uint64_t b) {
@@ -189,6 +214,7 @@ inline uint32_t deg16(const M16 &a) {
     s = (s & 0x0000FFFF0000FFFFull) + ((s >> 16) & 0x0000FFFF0000FFFFull);
     return (uint32_t)((s & 0xFFFFFFFFull) + (s >> 32));
 }
+#endif
 
 struct PairL {  // a critical pair with its lcm cached
     uint32_t i, j, deg, pad;
