@@ -610,11 +610,15 @@ __global__ void k_pick_panel(const RrefJob *__restrict__ jobs) {
 // reduced echelon form of each job's panel rows among themselves (block per job of `list`).
 // With SMEM the panel is copied to shared memory, reduced there and written back.
 constexpr int PT = 1024;
+constexpr uint32_t GJB = 4;  // columns of a thread handled together in the global-memory panel's sweeps
 template <bool SMEM>
 __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ jobs, const int *__restrict__ list) {
     extern __shared__ __align__(16) uint32_t pan[];
     __shared__ uint32_t mult[KP], prow[KP], pslot[KP], pc[KP], red[32], s_row[KP];
     __shared__ uint32_t s_inv;
+    // the global-memory panel batches JB columns per thread; the shared-memory one, whose rows are
+    // short, one
+    constexpr uint32_t JB = SMEM ? 1u : GJB;
     const RrefJob &X = jobs[list[blockIdx.x]];
     const Fp fp = X.fp;
     const uint32_t P = X.state[1], nb = X.nb;
@@ -646,26 +650,36 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
             mult[threadIdx.x] = v ? fp.p - v : 0u;
         }
         __syncthreads();
+        // a thread's columns JB at a time (j, j + PT, ...), and four earlier pivot rows per step:
+        // up to 4 JB independent loads in flight (the global-memory panel waits on L2 for each)
         uint32_t c = NOLEAD;
-        for (uint32_t j = threadIdx.x; j < nb; j += PT) {
-            uint64_t acc = row[j];
-            // four earlier pivot rows per iteration, their loads independent
-            if (fp.small) {  // raw products < 2^32, at most KP of them: one reduction per entry
-                for (uint32_t k0 = 0; k0 < nnew; k0 += 4) {
+        for (uint32_t j0 = threadIdx.x; j0 < nb; j0 += PT * JB) {
+            uint64_t acc[JB];
 #pragma unroll
-                    for (uint32_t u = 0; u < 4; ++u)
-                        if (k0 + u < nnew) acc += (uint64_t)(mult[k0 + u] * rowp(pslot[k0 + u])[j]);
-                }
-            } else {
-                for (uint32_t k0 = 0; k0 < nnew; k0 += 4) {
+            for (uint32_t u = 0; u < JB; ++u) acc[u] = j0 + u * PT < nb ? row[j0 + u * PT] : 0u;
+            for (uint32_t k0 = 0; k0 < nnew; k0 += 4) {
 #pragma unroll
-                    for (uint32_t u = 0; u < 4; ++u)
-                        if (k0 + u < nnew && mult[k0 + u]) acc += fp_mul(mult[k0 + u], rowp(pslot[k0 + u])[j], fp);
+                for (uint32_t v = 0; v < 4; ++v) {
+                    const uint32_t k = k0 + v;
+                    if (k >= nnew || !mult[k]) continue;
+                    const uint32_t mk = mult[k], *pk = rowp(pslot[k]);
+#pragma unroll
+                    for (uint32_t u = 0; u < JB; ++u) {
+                        const uint32_t j = j0 + u * PT;
+                        if (j >= nb) break;
+                        // raw products < 2^32 for p < 2^16 (at most KP of them), else reduced
+                        acc[u] += fp.small ? (uint64_t)(mk * pk[j]) : (uint64_t)fp_mul(mk, pk[j], fp);
+                    }
                 }
             }
-            const uint32_t x = nnew ? fp_reduce(acc, fp) : (uint32_t)acc;
-            if (nnew) row[j] = x;
-            if (x && c == NOLEAD) c = j;
+#pragma unroll
+            for (uint32_t u = 0; u < JB; ++u) {
+                const uint32_t j = j0 + u * PT;
+                if (j >= nb) break;
+                const uint32_t x = nnew ? fp_reduce(acc[u], fp) : (uint32_t)acc[u];
+                if (nnew) row[j] = x;
+                if (x && c == NOLEAD) c = j;
+            }
         }
         c = block_min(c, red);
         if (c == NOLEAD) {
@@ -675,27 +689,36 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
         if (threadIdx.x == 0) s_inv = fp.small ? fp_inv_small(row[c], fp) : fp_inv(row[c], fp);
         __syncthreads();
         const uint32_t inv = s_inv;
-        for (uint32_t j = c + threadIdx.x; j < nb; j += PT) row[j] = fp_mul(row[j], inv, fp);
+        for (uint32_t j0 = c + threadIdx.x; j0 < nb; j0 += PT * JB) {
+            uint32_t y[JB];
+#pragma unroll
+            for (uint32_t u = 0; u < JB; ++u) y[u] = j0 + u * PT < nb ? row[j0 + u * PT] : 0u;
+#pragma unroll
+            for (uint32_t u = 0; u < JB; ++u)
+                if (j0 + u * PT < nb) row[j0 + u * PT] = fp_mul(y[u], inv, fp);
+        }
         if (threadIdx.x < nnew) {
             const uint32_t v = rowp(pslot[threadIdx.x])[c];
             mult[threadIdx.x] = v ? fp.p - v : 0u;
         }
         __syncthreads();
-        // clear column c from the earlier new rows: per column, every earlier row at once
-        for (uint32_t j = c + threadIdx.x; j < nb; j += PT) {
-            const uint32_t y = row[j];
-            if (!y) continue;
-            for (uint32_t k0 = 0; k0 < nnew; k0 += 4) {
+        // clear column c from the earlier new rows: a thread's columns JB at a time, every earlier
+        // row at once
+        for (uint32_t j0 = c + threadIdx.x; j0 < nb; j0 += PT * JB) {
+            uint32_t y[JB];
 #pragma unroll
-                for (uint32_t u = 0; u < 4; ++u) {
-                    const uint32_t k = k0 + u;
-                    if (k >= nnew) break;
-                    const uint32_t mk = mult[k];
-                    if (!mk) continue;
-                    uint32_t *dst = rowp(pslot[k]) + j;
-                    *dst = fp.small ? fp_add(*dst, fp_reduce32(mk * y, fp), fp)
-                                    : fp_reduce((uint64_t)*dst + (uint64_t)mk * y, fp);
-                }
+            for (uint32_t u = 0; u < JB; ++u) y[u] = j0 + u * PT < nb ? row[j0 + u * PT] : 0u;
+            for (uint32_t k = 0; k < nnew; ++k) {
+                const uint32_t mk = mult[k];
+                if (!mk) continue;
+                uint32_t *dk = rowp(pslot[k]);
+                uint32_t d[JB];
+#pragma unroll
+                for (uint32_t u = 0; u < JB; ++u) d[u] = y[u] ? dk[j0 + u * PT] : 0u;
+#pragma unroll
+                for (uint32_t u = 0; u < JB; ++u)
+                    if (y[u]) dk[j0 + u * PT] = fp.small ? fp_add(d[u], fp_reduce32(mk * y[u], fp), fp)
+                                                         : fp_reduce((uint64_t)d[u] + (uint64_t)mk * y[u], fp);
             }
         }
         if (threadIdx.x == 0) {

@@ -64,6 +64,22 @@ def test_config3_large_step_dprime_rows_and_rref(ctx):
             if coef[k]:
                 res = (res - coef[k] * R[k]) % P31
         assert not res.any(), f"row {i} of D' outside the row space of RREF(D')"
+    # every row at once: D = D[:, piv] R, tested on random vectors mod p.  With R in RREF, a row of D
+    # equals its pivot-column entries times R exactly when it lies in the row space of R.
+    Dl = D.astype(np.int64)
+    for _ in range(3):
+        x = rng.integers(0, P31, size=D.shape[1], dtype=np.int64)
+        lhs = _matvec(Dl, x)
+        rhs = _matvec(Dl[:, piv], _matvec(R, x))
+        assert np.array_equal(lhs, rhs), "a row of D' outside the row space of RREF(D')"
+
+
+def _matvec(M: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """(M x) mod p exactly in int64: x = x0 + 2^16 x1 with 16-bit halves, so every product is below
+    2^47 and every row sum (at most 2^13 terms here) below 2^61."""
+    assert M.shape[1] < (1 << 13)
+    x0, x1 = x & 0xFFFF, x >> 16
+    return ((M @ x0) % P31 + ((M @ x1) % P31) * 65536) % P31
 
 
 def _grevlex_key(e: np.ndarray):
