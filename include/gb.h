@@ -316,7 +316,10 @@ gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, ui
    (three runs), times every step's reduction and RREF on the device, and keeps, per shape
    bucket, the schedule with the least total time.  A reduction's bucket is the prime's class
    (below 2^16 or not) and floor(log2(x + 1)) of its pivots, non-pivot rows and non-pivot columns;
-   an RREF's bucket is the class and the same of D''s rows and columns.  From then on every
+   an RREF's bucket is the class and the same of D''s rows and columns.  It also times the three
+   tiles of the prefix sums of the pipeline (4, 8 or 16 values per thread) on device arrays of
+   2^8 .. 2^24 values and keeps the fastest per floor(log2(n + 1)); every later scan of the
+   context of that size takes it.  From then on every
    single-system reduction of the context (gb_f4_step, gb_groebner, gb_reduce_macaulay) whose
    bucket the table holds takes the tuned schedule; other buckets, and the matrices of a batch,
    keep the rules.  GB_CTX_REDUCE_SPARSE, GB_CTX_REDUCE_DENSE and GB_CTX_NO_GRAPHS still take
@@ -330,7 +333,7 @@ typedef struct {
     uint32_t buckets_reduce;  /* reduction buckets in the context's table */
     uint32_t buckets_rref;    /* RREF buckets in the context's table */
     uint32_t dense_buckets;   /* reduction buckets where the tensor-core schedule won */
-    uint32_t reserved;
+    uint32_t buckets_scan;    /* prefix-sum size buckets (tile of 4, 8 or 16 values per thread) */
     double ms_wall;           /* host wall time of the tuning */
 } gb_tune_report;
 

@@ -88,7 +88,7 @@ class gb_server_stats(ctypes.Structure):
 class gb_tune_report(ctypes.Structure):
     _fields_ = [("runs", ctypes.c_uint32), ("steps", ctypes.c_uint32), ("buckets_reduce", ctypes.c_uint32),
                 ("buckets_rref", ctypes.c_uint32), ("dense_buckets", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("ms_wall", ctypes.c_double)]
+                ("buckets_scan", ctypes.c_uint32), ("ms_wall", ctypes.c_double)]
 
 
 class gb_server_opts(ctypes.Structure):

@@ -232,8 +232,9 @@ struct HostPool;
 //   reduction (TUNE_REDUCE): 0 sparse row-by-row, 1 dense blocked elimination on the tensor cores;
 //   RREF (TUNE_RREF): 0 panel updates on CUDA cores, rounds launched from the host;
 //                     1 the same rounds as one CUDA graph with the loop on the device;
-//                     2 panel updates on the tensor cores, rounds as one graph.
-constexpr uint32_t TUNE_REDUCE = 0, TUNE_RREF = 1;
+//                     2 panel updates on the tensor cores, rounds as one graph;
+//   prefix sums (TUNE_SCAN, bucket floor(log2(n + 1))): 0, 1, 2 = 4, 8, 16 values per thread.
+constexpr uint32_t TUNE_REDUCE = 0, TUNE_RREF = 1, TUNE_SCAN = 2;
 struct TuneEntry {
     uint8_t choice = 0;
     float ms[3] = {-1.f, -1.f, -1.f};  // measured total per schedule, -1 where not measured
@@ -383,7 +384,9 @@ bool trace_on();  // GB_TRACE set in the environment: stage timings on stderr   
 // run fn(i) for i in [0, n) on the context's host workers and the calling thread
 void parallel_for(gb_ctx *ctx, size_t n, const std::function<void(size_t)> &fn);
 // exclusive scan of n u32 values on the stream; out has n + 1 entries (out[n] = total)
-void exclusive_scan(Arena &ar, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t s);
+void exclusive_scan(gb_ctx *ctx, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t s);
+// the same with a given tile (ITEMS = 4, 8 or 16 values per thread), for the autotuner
+void exclusive_scan_items(gb_ctx *ctx, int items, const uint32_t *in, uint32_t *out, size_t n, cudaStream_t s);
 
 // ---- exact dense update over F_p on the tensor cores (mm.cu) --------------------------------
 // Digit planes of a matrix: [L][rows][kpad] BF16 bit patterns of the balanced base-256 digits of

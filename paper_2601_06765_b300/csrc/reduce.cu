@@ -1449,7 +1449,7 @@ void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector
         k_count_rows<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
         counted();
     }
-    exclusive_scan(ar, cnt.p, scan.p, tot, st);
+    exclusive_scan(ctx, cnt.p, scan.p, tot, st);
     char *h = static_cast<char *>(ctx_pinned(ctx, 4ull * (tot + 1) + 16ull * tot + 64));
     uint32_t *hs = reinterpret_cast<uint32_t *>(h);
     Mono *hl = reinterpret_cast<Mono *>(h + ((4ull * (tot + 1) + 15) & ~15ull));
@@ -1566,7 +1566,7 @@ void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::v
         k_count_rows<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
         counted();
     }
-    exclusive_scan(ar, cnt.p, scan.p, tot, st);
+    exclusive_scan(ctx, cnt.p, scan.p, tot, st);
     std::vector<uint32_t> hs(tot + 1);
     {
         uint32_t *hp = static_cast<uint32_t *>(ctx_pinned(ctx, 4ull * (tot + 1)));

@@ -650,15 +650,15 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         const Job *dj = reinterpret_cast<const Job *>(d2.p + o_j2);
         auto P = [&](size_t o) { return reinterpret_cast<const uint32_t *>(d2.p + o); };
         if (t_w) { k_popc<<<t_w, 256, 0, st>>>(dj, P(o_w), nj); counted(); }
-        exclusive_scan(ar, wcnt.p, wpre.p, tw, st);
+        exclusive_scan(ctx, wcnt.p, wpre.p, tw, st);
         if (t_q) { k_dict_queue<<<t_q, 256, 0, st>>>(dj, P(o_q), nj); counted(); }
         if (t_g) { k_dict_given<<<t_g, 256, 0, st>>>(dj, P(o_g), nj); counted(); }
         if (t_r) { k_piv_reducers<<<t_r, 256, 0, st>>>(dj, P(o_r), nj); counted(); }
-        exclusive_scan(ar, ispiv.p, pidx.p, tN, st);
+        exclusive_scan(ctx, ispiv.p, pidx.p, tN, st);
         if (t_N) { k_place_pivots<<<t_N, 256, 0, st>>>(dj, P(o_N), nj); counted(); }
         if (t_g) { k_place_nonpivots<<<t_g, 256, 0, st>>>(dj, P(o_g), nj); counted(); }
         if (t_rows) { k_row_len<<<t_rows, 256, 0, st>>>(dj, P(o_rows), nj); counted(); }
-        exclusive_scan(ar, lens.p, lscan.p, tr, st);
+        exclusive_scan(ctx, lens.p, lscan.p, tr, st);
         if (t_rp) { k_row_ptr<<<t_rp, 256, 0, st>>>(dj, P(o_rp), nj); counted(); }
         if (t_fill) { k_fill<<<t_fill, 32 * WPB, tab_smem, st>>>(dj, P(o_fill), nj); counted(); }
         GB_CUDA(cudaEventRecord(ctx->ev[1], st));

@@ -45,6 +45,43 @@ struct ForceGuard {
     }
 };
 
+// The prefix-sum tile per size bucket: each candidate timed on device arrays of n = 2^b values
+// (b = 8..24; a scan's cost depends on n only), best of three launches after a warm-up.
+void tune_scans(gb_ctx *ctx) {
+    constexpr int B0 = 8, B1 = 24;
+    constexpr int ITEMS[3] = {4, 8, 16};
+    cudaStream_t st = ctx->stream;
+    DBuf<uint32_t> in, out;
+    in.alloc(ctx->arena, (size_t(1) << B1) + 1, st);
+    out.alloc(ctx->arena, (size_t(1) << B1) + 1, st);
+    GB_CUDA(cudaMemsetAsync(in.p, 1, 4ull << B1, st));
+    cudaEvent_t e0, e1;
+    GB_CUDA(cudaEventCreate(&e0));
+    GB_CUDA(cudaEventCreate(&e1));
+    for (int b = B0; b <= B1; ++b) {
+        const size_t n = size_t(1) << b;
+        TuneEntry e;
+        for (int c = 0; c < 3; ++c) {
+            float best = 1e30f;
+            for (int r = 0; r < 4; ++r) {
+                GB_CUDA(cudaEventRecord(e0, st));
+                exclusive_scan_items(ctx, ITEMS[c], in.p, out.p, n, st);
+                GB_CUDA(cudaEventRecord(e1, st));
+                GB_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                GB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (r) best = std::min(best, ms);
+                ctx_sync(ctx);  // the scan's tile buffers are free again
+            }
+            e.ms[c] = best;
+            if (best < e.ms[e.choice]) e.choice = (uint8_t)c;
+        }
+        ctx->tune.table[tune_key(TUNE_SCAN, 0, (uint32_t)n, 0, 0)] = e;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
 }  // namespace
 
 void autotune(gb_ctx *ctx, const std::vector<gb_system *> &Ss, gb_tune_report *rep) {
@@ -88,6 +125,7 @@ void autotune(gb_ctx *ctx, const std::vector<gb_system *> &Ss, gb_tune_report *r
         e.choice = dense < sparse ? 1 : 0;
         ctx->tune.table[kv.first] = e;
     }
+    tune_scans(ctx);
     for (const auto &kv : rr) {
         TuneEntry e;
         for (int i = 0; i < 3; ++i) e.ms[i] = (float)kv.second[i];
@@ -104,8 +142,10 @@ void autotune(gb_ctx *ctx, const std::vector<gb_system *> &Ss, gb_tune_report *r
             if ((kv.first >> 40) == TUNE_REDUCE) {
                 ++rep->buckets_reduce;
                 rep->dense_buckets += kv.second.choice == 1;
-            } else {
+            } else if ((kv.first >> 40) == TUNE_RREF) {
                 ++rep->buckets_rref;
+            } else {
+                ++rep->buckets_scan;
             }
         }
         rep->ms_wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -123,13 +163,15 @@ void tune_save(const gb_ctx *ctx, const char *path) {
       << "# kind prime(0: p < 2^16, 1: p < 2^31) lg_a lg_b lg_c choice ms_0 ms_1 ms_2\n"
       << "# lg_x = floor(log2(x + 1)); reduce: a pivots, b non-pivot rows, c non-pivot columns,\n"
       << "#   choice 0 sparse, 1 dense (tensor cores); rref: a rows, b columns of D',\n"
-      << "#   choice 0 CUDA cores + host rounds, 1 CUDA cores + graph, 2 tensor cores + graph\n";
+      << "#   choice 0 CUDA cores + host rounds, 1 CUDA cores + graph, 2 tensor cores + graph;\n"
+      << "#   scan: a values, choice 0, 1, 2 = tiles of 4, 8, 16 values per thread\n";
     char line[160];
     for (const auto &kv : ctx->tune.table) {
         const uint64_t k = kv.first;
         const TuneEntry &e = kv.second;
+        const uint64_t kind = k >> 40;
         std::snprintf(line, sizeof line, "%s %u %u %u %u %u %.4f %.4f %.4f\n",
-                      (k >> 40) == TUNE_REDUCE ? "reduce" : "rref", (unsigned)((k >> 32) & 0xFF),
+                      kind == TUNE_REDUCE ? "reduce" : kind == TUNE_RREF ? "rref" : "scan", (unsigned)((k >> 32) & 0xFF),
                       (unsigned)((k >> 16) & 0xFF), (unsigned)((k >> 8) & 0xFF), (unsigned)(k & 0xFF),
                       (unsigned)e.choice, e.ms[0], e.ms[1], e.ms[2]);
         f << line;
@@ -153,14 +195,14 @@ void tune_load(gb_ctx *ctx, const char *path) {
         if (!(in >> kind >> cls >> a >> b >> c >> choice >> ms[0] >> ms[1] >> ms[2]))
             fail(GB_EINVAL, "gb_tune_load: malformed line " + std::to_string(no));
         std::string rest;
-        const bool red = kind == "reduce";
-        if ((!red && kind != "rref") || (in >> rest) || cls > 1 || a > 32 || b > 32 || c > 32 ||
-            choice > (red ? 1u : 2u) || (!red && c != 0))
+        const bool red = kind == "reduce", scan = kind == "scan";
+        if ((!red && !scan && kind != "rref") || (in >> rest) || cls > 1 || a > 32 || b > 32 || c > 32 ||
+            choice > (red ? 1u : 2u) || (!red && c != 0) || (scan && (b != 0 || cls != 0)))
             fail(GB_EINVAL, "gb_tune_load: malformed line " + std::to_string(no));
         TuneEntry e;
         e.choice = (uint8_t)choice;
         for (int i = 0; i < 3; ++i) e.ms[i] = ms[i];
-        const uint64_t key = ((uint64_t)(red ? TUNE_REDUCE : TUNE_RREF) << 40) | ((uint64_t)cls << 32) |
+        const uint64_t key = ((uint64_t)(red ? TUNE_REDUCE : scan ? TUNE_SCAN : TUNE_RREF) << 40) | ((uint64_t)cls << 32) |
                              ((uint64_t)a << 16) | ((uint64_t)b << 8) | c;
         add[key] = e;
     }

@@ -46,6 +46,7 @@ def test_autotune_keeps_results_and_round_trips(tmp_path):
             gb.gb_system_destroy(h)
         assert rep["runs"] == 3 and rep["steps"] > 0
         assert rep["buckets_reduce"] > 0 and rep["buckets_rref"] > 0
+        assert rep["buckets_scan"] == 17  # n = 2^8 .. 2^24
         for system in SYSTEMS:
             a, basis_a = _steps(plain, system)
             b, basis_b = _steps(tuned, system)
@@ -62,7 +63,8 @@ def test_autotune_keeps_results_and_round_trips(tmp_path):
             gb.gb_tune_save(other.h, str(f2))
         rows = [ln for ln in f1.read_text().splitlines() if not ln.startswith("#")]
         assert rows and rows == [ln for ln in f2.read_text().splitlines() if not ln.startswith("#")]
-        assert len(rows) == rep["buckets_reduce"] + rep["buckets_rref"]
+        assert len(rows) == rep["buckets_reduce"] + rep["buckets_rref"] + rep["buckets_scan"]
+        assert sum(ln.startswith("scan ") for ln in rows) == 17
 
 
 def test_loaded_table_steers_the_schedules(tmp_path):
@@ -100,6 +102,9 @@ def test_tune_rejects_bad_input(tmp_path):
         bad.write_text("rref 0 3 3 0 7 0 0 0\n")  # no schedule 7
         with pytest.raises(gb.GbError):
             gb.gb_tune_load(ctx.h, str(bad))
+        bad.write_text("scan 0 12 3 0 1 0 0 0\n")  # a scan bucket has one size
+        with pytest.raises(gb.GbError):
+            gb.gb_tune_load(ctx.h, str(bad))
         with pytest.raises(gb.GbError):
             gb.gb_tune_load(ctx.h, str(tmp_path / "missing.txt"))
         # a system that has already run a step cannot be tuned on
@@ -109,3 +114,20 @@ def test_tune_rejects_bad_input(tmp_path):
             gb.gb_autotune(ctx.h, [h])
         assert e.value.status == -1  # GB_EINVAL
         gb.gb_system_destroy(h)
+
+
+def test_scan_tiles_from_a_loaded_table_keep_results(tmp_path):
+    """Every prefix-sum tile (4, 8, 16 values per thread) gives the same plans: a table that sets
+    each size bucket to one tile in turn leaves every step of a run bit-identical."""
+    system = synth.config1(0)
+    with gb.Context(arena_bytes=1 << 30, keep_step=True) as ctx:
+        want, basis = _steps(ctx, system)
+    for choice in range(3):
+        table = tmp_path / f"scan{choice}.txt"
+        table.write_text("".join(f"scan 0 {b} 0 0 {choice} 0 0 0\n" for b in range(0, 33)))
+        with gb.Context(arena_bytes=1 << 30, keep_step=True) as ctx:
+            gb.gb_tune_load(ctx.h, str(table))
+            got, basis_got = _steps(ctx, system)
+        assert basis_got == basis
+        for (x, dx, rx), (y, dy, ry) in zip(want, got):
+            assert x["nnz"] == y["nnz"] and np.array_equal(dx, dy) and np.array_equal(rx, ry)
