@@ -198,7 +198,7 @@ def run_ours(args) -> None:
     batched = measure_batched(gb, synth, ctx, rank, world) if not args.no_batch else None
     served = measure_served(gb, synth, ctx) if rank == 0 and not args.no_batch else None
     tensor = measure_tensor_core(gb, local) if rank == 0 and not args.no_batch else None
-    big = measure_config3(gb, synth, local, pk) if rank == 0 and not args.no_batch else None
+    big = measure_config3(gb, synth, local, pk, graphs=not args.no_graphs) if rank == 0 and not args.no_batch else None
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
              for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_rref", "ms_update", "ms_pairs", "ms_select",
                        "ms_wall")}
@@ -374,7 +374,7 @@ def measure_tensor_core(gb, local: int) -> list:
     return out
 
 
-def measure_config3(gb, synth, local: int, pk: dict) -> dict:
+def measure_config3(gb, synth, local: int, pk: dict, graphs: bool = True) -> dict:
     """One F4 run of the n=13 sparse 31-bit system (the large-matrix workload) with the reduction
     chosen per matrix by the shape rules (dense tensor-core blocks for the large steps), with the
     sparse reduction only, and with the schedules gb_autotune measured on this system (its three
@@ -384,7 +384,7 @@ def measure_config3(gb, synth, local: int, pk: dict) -> dict:
     res = {"workload": "n=13, m=13 quadratics with 30 of the 105 monomials of degree <= 2, p=2^31-1, grevlex, "
                        "SplitMix64 seed 20260765; one full F4 run"}
     for mode in ("auto", "sparse", "tuned"):
-        ctx = gb.Context(device=local, arena_bytes=48 << 30, reduce="auto" if mode == "tuned" else mode)
+        ctx = gb.Context(device=local, arena_bytes=48 << 30, reduce="auto" if mode == "tuned" else mode, graphs=graphs)
         if mode == "tuned":
             th = gb.gb_system_create(ctx.h, system)
             res["autotune"] = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in gb.gb_autotune(ctx.h, [th]).items()}
@@ -491,7 +491,7 @@ def main() -> None:
         if args.only == "tensor":
             print(json.dumps({"tensor_core": measure_tensor_core(gb, 0)}))
         else:
-            print(json.dumps({"config3": measure_config3(gb, synth, 0, peaks())}))
+            print(json.dumps({"config3": measure_config3(gb, synth, 0, peaks(), graphs=not args.no_graphs)}))
     elif args.impl == "reference":
         run_reference(args)
     else:
