@@ -16,23 +16,24 @@
 // digit), which equals (A B)[m][n] mod p.  One launch covers K <= 512 / L; longer products are
 // split by the host into launches that each update C.
 //
-// Kernel: persistent, one CTA per SM, each CTA takes a contiguous run of the 128 x 64 output
-// tiles in row-major tile order.  18 warps:
-//   warp 0, lane 0   TMA producer: the digit planes of A for the CTA's current 128-row tile
-//                    (all of K, resident in shared memory while the row tile lasts), then per
-//                    output tile the digit planes of B^T, one buffer per 64-wide K block so that a
-//                    block is refilled for the next tile as soon as its products are done, and the
-//                    C tile (128-byte swizzle; mbarriers with transaction counts)
-//   warp 1           allocates the tensor memory; lane 0 issues tcgen05.mma (kind::f16, BF16
-//                    operands, FP32 accumulators, M = 128, N = 64, K = 16) for every digit pair
-//                    into the accumulator of its diagonal.  Tensor memory holds two regions: for
-//                    p >= 2^16 diagonals 0-3 and 4-6 of the same tile (7 x 64 columns), for
-//                    p < 2^16 all 3 diagonals of alternate tiles
-//   warps 2-17       epilogue (four warps per tensor-memory lane quarter, 16 columns each): drains
-//                    a region as soon as its products are done (tcgen05.ld, exact conversion,
-//                    sum_s D_s (256^s mod p)), hands it back, then one Barrett reduction,
-//                    read-modify-write of the C tile in shared memory and a TMA store
-// so that one region's products run while the other is drained.  Every wait is bounded; a wait that
+// Kernel: persistent, one CTA per SM, each CTA takes a contiguous run of the 128 x (128/L) output
+// tiles in row-major tile order.  Every product is one tcgen05.mma (kind::f16, BF16 operands, FP32
+// accumulators) of M = 128, N = 128, K = 16: one digit of A against all L digits of B^T side by
+// side (128/L rows each), its accumulator window starting at diagonal i, so that A_i B_j lands on
+// diagonal i + j.  18 warps:
+//   warp 0, lane 0   TMA producer: the digit planes of A for the CTA's current 128-row tile (all of
+//                    K, resident in shared memory while the row tile lasts), then per output tile
+//                    the K blocks of B^T (all digits in one box) through a ring of slots, and an L2
+//                    prefetch of the next tile's C (128-byte swizzle; mbarriers with transaction
+//                    counts)
+//   warp 1           allocates the tensor memory (two accumulator sets of 2L - 1 diagonals,
+//                    alternate tiles) and issues the products from lane 0
+//   warps 2-17       epilogue (four warps per tensor-memory lane quarter): drains a set as soon as
+//                    its products are done (tcgen05.ld of every diagonal, exact conversion,
+//                    sum_s D_s (256^s mod p)), hands it back, then one Barrett reduction and the
+//                    read-modify-write of the C tile in shared memory; one of its threads issues
+//                    the TMA store and loads the C tile of a later tile into the freed buffer
+// so that one set's products run while the other is drained.  Every wait is bounded; a wait that
 // gives up sets an error flag that the host turns into GB_ETIMEOUT, and the CTA still releases its
 // tensor memory.
 #include <cuda.h>
