@@ -180,20 +180,22 @@ def run_ours(args) -> None:
         d2h = off.nbytes + ex.nbytes + cf.nbytes
     e2e_value = (nnz / len(runs) * (world if world > 1 else 1)) / (statistics.median(e2e_ms) / 1e3)
 
-    # roofline of the sparse row reduction kernel (the dominant kernel, see profiles/): algorithmic
+    # roofline of the sparse row reduction (the dominant kernels, see profiles/): algorithmic
     # bytes = 8 B per modular multiply-add (col_ind + val of a pivot-row entry read); time = the
     # device time of its launches alone (CUDA events around them on the context's stream), summed
-    # over the timed runs
+    # over the timed runs.  k_reduce_rows runs the steps with more non-pivot rows than SMs, and its
+    # ncu capture gives the DRAM traffic per launch
     r0 = runs[0]
     pk = peaks()
     red_ms = sum(r["ms_reduce_kernel"] for r in runs)
     alg_bytes = 8.0 * sum(r["axpy_fma"] for r in runs)
     achieved = alg_bytes / (red_ms / 1e3) / 1e9 if red_ms > 0 else 0.0
-    roofline = {"kernel": "k_reduce (sparse row AXPY reduction, per F4 run)", "bound": "hbm",
+    roofline = {"kernel": "k_reduce_rows + k_reduce + k_reduce_cl (sparse row AXPY reduction, per F4 run)",
+                "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / pk["hbm_gbs"], 4),
                 "peak_source": f"{pk['source']} HBM copy bandwidth",
-                "traffic": profile_traffic("k_reduce_config2")}
+                "traffic": profile_traffic("k_reduce_rows_config2")}
 
     batched = measure_batched(gb, synth, ctx, rank, world) if not args.no_batch else None
     served = measure_served(gb, synth, ctx) if rank == 0 and not args.no_batch else None

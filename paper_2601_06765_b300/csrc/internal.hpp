@@ -399,6 +399,7 @@ struct DigitPlanes {
     DBuf<uint16_t> buf;
     void alloc(Arena &ar, uint32_t L, uint64_t rows, uint64_t K, cudaStream_t st);
 };
+int sm_count();  // SMs of the current device
 uint32_t digits_for(uint32_t p);
 uint32_t mm_kmax(uint32_t p);  // longest K one exact tensor-core accumulation covers
 // digit planes of the R x K matrix whose element (r, k) is src[r * rs + k * ks]

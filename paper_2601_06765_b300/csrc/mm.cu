@@ -577,6 +577,8 @@ CUtensorMap digit_map(const DigitPlanes &D, uint32_t box_rows, uint32_t box_digi
     return m;
 }
 
+}  // namespace
+
 int sm_count() {
     static int n[64] = {};
     int dev = 0;
@@ -585,8 +587,6 @@ int sm_count() {
     if (!n[dev]) GB_CUDA(cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev));
     return n[dev];
 }
-
-}  // namespace
 
 uint32_t digits_for(uint32_t p) { return p < 65536u ? 2u : 4u; }
 uint32_t mm_kmax(uint32_t p) { return 512u / digits_for(p); }

@@ -63,6 +63,7 @@ struct RedJob {
     unsigned long long *work;  // [0] pivot rows applied, [1] modular multiply-adds
     uint32_t nA, nC, N, nb;
     Fp fp;
+    uint32_t rpb, win;         // k_reduce_rows: rows per block, entries of the staging window
 };
 
 // U[chunk][j][i] for j < i: entry of pivot row chunk*32+j at pivot column pcols[chunk*32+i]
@@ -286,6 +287,148 @@ __global__ void __launch_bounds__(RT, 6) k_reduce(const RedJob *__restrict__ job
     for (uint32_t jj = threadIdx.x; jj < J.nb; jj += RT) {
         const uint32_t c = J.nonpiv[jj];
         out[jj] = c < base ? 0u : MODE == A32 ? fp_reduce32((uint32_t)acc[c - base], fp) : fp_reduce(acc[c - base], fp);
+    }
+}
+
+// ---- the same reduction with several rows per block sharing the pivot entries ------------------
+//
+// With more non-pivot rows than SMs and a dictionary short enough for the A32 accumulators of R
+// rows to sit in shared memory, one block of RB threads reduces R rows at once.  The entries of a
+// chunk's pivot rows are one contiguous CSR range: they are staged in shared memory with 16-byte
+// asynchronous copies, issued before the chunk's multipliers are formed so that the copy overlaps
+// that step (R warps form the R rows' multipliers in parallel, the other warps load the next
+// chunk's inverse triangle).  Each staged entry is then read once and applied to every row of the
+// block with a non-zero multiplier for its pivot row, so the global reads per multiply-add fall by
+// up to R.  A chunk longer than the staging window is applied window by window.
+constexpr int RB = 1024;             // threads per block
+constexpr uint32_t RMAX = 16;        // rows per block at most
+constexpr uint32_t WMIN = 4096;      // entries of the smallest staging window
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t Us[2][CW * CW];
+    __shared__ uint32_t s_pc[2][CW], s_rp[2][CW + 1];
+    __shared__ __align__(16) uint32_t s_m[CW][RMAX];  // p - f of chunk row k for block row r, at [k][r]
+    __shared__ uint32_t s_base;
+    const int jb = job_of_block(bstart, nj);
+    const RedJob &J = jobs[jb];
+    const Fp fp = J.fp;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t R = J.rpb, NS = (J.N + 3u) & ~3u, win = J.win;
+    const uint32_t i0 = (blockIdx.x - bstart[jb]) * R, nr = min(R, J.nC - i0);
+    // shared memory: R accumulator rows of NS words, then the staged columns and values
+    uint32_t *acc = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *wcol = acc + (size_t)R * NS, *wval = wcol + win + 8;
+    const uint32_t wcol_s = (uint32_t)__cvta_generic_to_shared(wcol), wval_s = (uint32_t)__cvta_generic_to_shared(wval);
+    for (uint32_t t = threadIdx.x; t < nr * NS; t += RB) acc[t] = 0;
+    for (uint32_t t = threadIdx.x; t < CW * RMAX; t += RB) s_m[t / RMAX][t % RMAX] = 0;  // rows past nr stay 0
+    if (threadIdx.x == 0) s_base = J.N;
+    __syncthreads();
+    for (uint32_t r = 0; r < nr; ++r) {
+        const uint32_t a0 = J.row_ptr[J.nA + i0 + r], b0 = J.row_ptr[J.nA + i0 + r + 1];
+        if (threadIdx.x == 0 && a0 < b0) atomicMin(&s_base, J.col[a0]);
+        for (uint32_t q = a0 + threadIdx.x; q < b0; q += RB) acc[r * NS + J.col[q]] = J.val[q];
+    }
+    __syncthreads();
+    // first chunk holding a pivot column at or right of the leftmost leading column of the rows
+    const uint32_t base = s_base;
+    uint32_t lo = 0, hi = J.nA;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (J.pcols[mid] < base) lo = mid + 1; else hi = mid;
+    }
+    const uint32_t k0 = (lo / CW) * CW;
+    // a chunk's inverse triangle, pivot columns and row pointers, by threads t0, t0 + step, ...
+    auto load_chunk = [&](uint32_t kc, uint32_t b, uint32_t t0, uint32_t step) {
+        const uint32_t cnt = min((uint32_t)CW, J.nA - kc);
+        const uint32_t *src = J.U + (size_t)(kc / CW) * CW * CW;
+        for (uint32_t t = t0; t < CW * CW; t += step) Us[b][t] = src[t];
+        for (uint32_t t = t0; t <= cnt; t += step) {
+            if (t < cnt) s_pc[b][t] = J.pcols[kc + t];
+            s_rp[b][t] = J.row_ptr[kc + t];
+        }
+    };
+    // entries [a, b) of the chunk's range into the window (a a multiple of 4); the last piece reads
+    // up to three entries past b, inside the CSR arrays' 256-byte-rounded device blocks
+    auto stage = [&](uint32_t a, uint32_t b) {
+        const uint32_t pieces = (b - a + 3) / 4;
+        for (uint32_t q = threadIdx.x; q < pieces; q += RB) {
+            cp_async16(wcol_s + 16u * q, J.col + a + 4u * q);
+            cp_async16(wval_s + 16u * q, J.val + a + 4u * q);
+        }
+        cp_async_commit();
+    };
+    if (k0 < J.nA) load_chunk(k0, 0, threadIdx.x, RB);
+    unsigned long long applied = 0, fmas = 0;
+    for (uint32_t kc = k0, buf = 0; kc < J.nA; kc += CW, buf ^= 1) {
+        const uint32_t cnt = min((uint32_t)CW, J.nA - kc);
+        __syncthreads();  // the previous chunk is applied; this chunk's tables are visible
+        const uint32_t e0 = s_rp[buf][0], e1 = s_rp[buf][cnt];
+        stage(e0 & ~3u, min(e0 + win, e1));
+        if (warp < nr) {
+            // row `warp`: the chunk's multipliers f = v_c U^{-1}, stored as p - f
+            const uint32_t x = lane < cnt ? fp_reduce32(acc[warp * NS + s_pc[buf][lane]], fp) : 0u;
+            const uint32_t *Wc = Us[buf];
+            unsigned long long s = 0;  // < 32 * 2^32
+#pragma unroll
+            for (int j = 0; j < CW; ++j) s += (unsigned long long)(__shfl_sync(0xffffffffu, x, j) * Wc[j * CW + lane]);
+            const uint32_t f = lane < cnt ? fp_reduce(s, fp) : 0u;
+            s_m[lane][warp] = f ? fp.p - f : 0u;
+            uint32_t len = f ? s_rp[buf][lane + 1] - s_rp[buf][lane] : 0u;
+#pragma unroll
+            for (int d = 16; d; d >>= 1) len += __shfl_xor_sync(0xffffffffu, len, d);
+            applied += __popc(__ballot_sync(0xffffffffu, f != 0u));
+            fmas += len;
+        } else if (kc + CW < J.nA) {
+            load_chunk(kc + CW, buf ^ 1, threadIdx.x - 32u * nr, RB - 32u * nr);
+        }
+        cp_async_wait0();
+        __syncthreads();
+        for (uint32_t w0 = e0; w0 < e1; w0 += win) {
+            const uint32_t w1 = min(w0 + win, e1), a = w0 & ~3u;
+            if (w0 != e0) {
+                stage(a, w1);
+                cp_async_wait0();
+                __syncthreads();
+            }
+            uint32_t e = w0 + threadIdx.x;
+            if (e < w1) {
+                uint32_t k = 0, khi = cnt - 1;  // the chunk row holding entry e
+                while (k < khi) {
+                    const uint32_t mid = (k + khi + 1) >> 1;
+                    if (s_rp[buf][mid] <= e) k = mid; else khi = mid - 1;
+                }
+                for (; e < w1; e += RB) {
+                    while (e >= s_rp[buf][k + 1]) ++k;
+                    const uint32_t c = wcol[e - a], v = wval[e - a];
+                    // the multipliers of four rows per shared-memory load (rows past nr hold 0)
+                    const uint4 *mk = reinterpret_cast<const uint4 *>(s_m[k]);
+                    for (uint32_t r0 = 0; r0 < nr; r0 += 4) {
+                        const uint4 m4 = mk[r0 / 4];
+                        const uint32_t mm[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+                        for (uint32_t u = 0; u < 4; ++u)
+                            if (mm[u]) atomicAdd(&acc[(r0 + u) * NS + c], fp_reduce32(mm[u] * v, fp));
+                    }
+                }
+            }
+            if (w1 < e1) __syncthreads();  // every thread is done with the window
+        }
+    }
+    __syncthreads();
+    if (warp < nr && lane == 0 && (applied || fmas)) {
+        atomicAdd(&J.work[0], applied);
+        atomicAdd(&J.work[1], fmas);
+    }
+    for (uint32_t r = 0; r < nr; ++r) {
+        uint32_t *out = J.dprime + (size_t)(i0 + r) * J.nb;
+        for (uint32_t jj = threadIdx.x; jj < J.nb; jj += RB) out[jj] = fp_reduce32(acc[r * NS + J.nonpiv[jj]], fp);
     }
 }
 
@@ -1061,6 +1204,41 @@ bool use_cluster(const RedJob &J, size_t accb, uint64_t rows) {
     return per_block <= 48 * 1024 && rows <= 160 && J.nA >= 2048;
 }
 
+// dynamic shared memory of k_reduce_rows: the device's opt-in limit less the kernel's static part
+size_t rows_dyn_smem() {
+    int dev = 0, optin = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    GB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    GB_CUDA(cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(k_reduce_rows)));
+    return (size_t)optin - fa.sharedSizeBytes;
+}
+
+// Rows per block of k_reduce_rows for an A32 matrix, or 0 when one row per block is the better
+// schedule: with no more rows than SMs one row per block already fills the GPU.  Otherwise enough
+// rows per block for about one block per SM, at most RMAX and at most what shared memory holds
+// next to a window of WMIN entries.  `rows` counts the non-pivot rows of the launch.
+uint32_t rows_per_block(const RedJob &J, uint64_t rows, size_t dyn) {
+    const uint64_t nsm = (uint64_t)sm_count(), NS = (J.N + 3u) & ~3u;
+    if (rows <= nsm || dyn < 8ull * (WMIN + 8)) return 0;
+    const uint64_t fit = (dyn - 8ull * (WMIN + 8)) / (4 * NS);
+    const uint64_t r = std::min<uint64_t>({(rows + nsm - 1) / nsm, (uint64_t)RMAX, fit});
+    return r >= 2 ? (uint32_t)r : 0u;
+}
+
+// entries of the staging window next to `rpb` accumulator rows (a multiple of 4).
+// GB_ROWS_WINDOW=n in the environment caps it at n (n >= 8): a diagnostic that makes chunks span
+// several windows.
+uint32_t rows_window(const RedJob &J, uint32_t rpb, size_t dyn) {
+    const uint64_t NS = (J.N + 3u) & ~3u;
+    uint64_t w = ((dyn - 4 * rpb * NS) / 8 - 8) & ~uint64_t(3);
+    if (const char *e = std::getenv("GB_ROWS_WINDOW")) {
+        const long cap = std::atol(e);
+        if (cap >= 8) w = std::min<uint64_t>(w, (uint64_t)cap & ~uint64_t(3));
+    }
+    return (uint32_t)w;
+}
+
 }  // namespace
 
 // the tuned schedule of a bucket, or -1 (the shape rules decide)
@@ -1141,6 +1319,7 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
     for (int j = 0; j < nj; ++j)
         if (R[j].nC && R[j].nb && !dense[j]) sparse_rows += R[j].nC;
     std::map<std::pair<int, int>, std::vector<int>> groups;  // (mode, size class or -1) -> jobs
+    const size_t rows_dyn = rows_dyn_smem();
     for (int j = 0; j < nj; ++j) {
         if (!R[j].nC || !R[j].nb || dense[j]) continue;
         const size_t accb = mode[j] == A32 ? 4 : 8;
@@ -1150,6 +1329,9 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             cls = -2;  // rows split over clusters of CS blocks (k_reduce_cl)
             sbuf[j].alloc(ar, (size_t)std::max<uint32_t>(R[j].nA, 1) * (CS + 1), st);
             R[j].split = sbuf[j].p;
+        } else if (mode[j] == A32 && (R[j].rpb = rows_per_block(R[j], sparse_rows, rows_dyn)) >= 2) {
+            cls = -3;  // several rows per block sharing the staged pivot entries (k_reduce_rows)
+            R[j].win = rows_window(R[j], R[j].rpb, rows_dyn);
         } else if (bytes <= 200 * 1024) {
             cls = 0;
             while (((size_t)1024 << cls) < bytes) ++cls;
@@ -1169,7 +1351,8 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         std::vector<std::vector<uint32_t>> per{tri, inv, spl};
         for (auto &g : groups) {
             std::vector<uint32_t> rows(nj, 0);
-            for (int j : g.second) rows[j] = R[j].nC;  // blocks, or clusters of CS blocks for class -2
+            // blocks, clusters of CS blocks for class -2, blocks of rpb rows for class -3
+            for (int j : g.second) rows[j] = g.first.second == -3 ? (R[j].nC + R[j].rpb - 1) / R[j].rpb : R[j].nC;
             per.push_back(rows);
         }
         Grouped<RedJob> G;
@@ -1204,6 +1387,13 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
         size_t gi = 3;
         for (auto &g : groups) {
             const int md = g.first.first, cls = g.first.second;
+            if (cls == -3) {
+                opt_in_smem(reinterpret_cast<const void *>(k_reduce_rows));
+                k_reduce_rows<<<G.totals[gi], RB, rows_dyn, st>>>(G.jobs, G.plans[gi], nj);
+                counted();
+                ++gi;
+                continue;
+            }
             if (cls == -2) {
                 size_t dyn = 0;
                 for (int j : g.second)
