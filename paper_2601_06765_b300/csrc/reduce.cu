@@ -314,7 +314,8 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t Us[2][CW * CW];
     __shared__ uint32_t s_pc[2][CW], s_rp[2][CW + 1];
-    __shared__ __align__(16) uint32_t s_m[CW][RMAX];  // p - f of chunk row k for block row r, at [k][r]
+    __shared__ uint32_t s_m[CW][RMAX];  // p - f of chunk row k for block row r, at [k][r]
+    __shared__ uint32_t s_mask[2][CW];  // per chunk row: the block rows with a non-zero multiplier
     __shared__ uint32_t s_base;
     const int jb = job_of_block(bstart, nj);
     const RedJob &J = jobs[jb];
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
     uint32_t *wcol = acc + (size_t)R * NS, *wval = wcol + win + 8;
     const uint32_t wcol_s = (uint32_t)__cvta_generic_to_shared(wcol), wval_s = (uint32_t)__cvta_generic_to_shared(wval);
     for (uint32_t t = threadIdx.x; t < nr * NS; t += RB) acc[t] = 0;
-    for (uint32_t t = threadIdx.x; t < CW * RMAX; t += RB) s_m[t / RMAX][t % RMAX] = 0;  // rows past nr stay 0
+    if (threadIdx.x < CW) s_mask[0][threadIdx.x] = 0;
     if (threadIdx.x == 0) s_base = J.N;
     __syncthreads();
     for (uint32_t r = 0; r < nr; ++r) {
@@ -350,7 +351,10 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
         const uint32_t *src = J.U + (size_t)(kc / CW) * CW * CW;
         for (uint32_t t = t0; t < CW * CW; t += step) Us[b][t] = src[t];
         for (uint32_t t = t0; t <= cnt; t += step) {
-            if (t < cnt) s_pc[b][t] = J.pcols[kc + t];
+            if (t < cnt) {
+                s_pc[b][t] = J.pcols[kc + t];
+                s_mask[b][t] = 0;
+            }
             s_rp[b][t] = J.row_ptr[kc + t];
         }
     };
@@ -379,7 +383,8 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
 #pragma unroll
             for (int j = 0; j < CW; ++j) s += (unsigned long long)(__shfl_sync(0xffffffffu, x, j) * Wc[j * CW + lane]);
             const uint32_t f = lane < cnt ? fp_reduce(s, fp) : 0u;
-            s_m[lane][warp] = f ? fp.p - f : 0u;
+            s_m[lane][warp] = fp.p - f;
+            if (f) atomicOr(&s_mask[buf][lane], 1u << warp);
             uint32_t len = f ? s_rp[buf][lane + 1] - s_rp[buf][lane] : 0u;
 #pragma unroll
             for (int d = 16; d; d >>= 1) len += __shfl_xor_sync(0xffffffffu, len, d);
@@ -407,14 +412,10 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
                 for (; e < w1; e += RB) {
                     while (e >= s_rp[buf][k + 1]) ++k;
                     const uint32_t c = wcol[e - a], v = wval[e - a];
-                    // the multipliers of four rows per shared-memory load (rows past nr hold 0)
-                    const uint4 *mk = reinterpret_cast<const uint4 *>(s_m[k]);
-                    for (uint32_t r0 = 0; r0 < nr; r0 += 4) {
-                        const uint4 m4 = mk[r0 / 4];
-                        const uint32_t mm[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-                        for (uint32_t u = 0; u < 4; ++u)
-                            if (mm[u]) atomicAdd(&acc[(r0 + u) * NS + c], fp_reduce32(mm[u] * v, fp));
+                    // only the block rows with a non-zero multiplier for this pivot row
+                    for (uint32_t mask = s_mask[buf][k]; mask; mask &= mask - 1u) {
+                        const uint32_t r = __ffs(mask) - 1u;
+                        atomicAdd(&acc[r * NS + c], fp_reduce32(s_m[k][r] * v, fp));
                     }
                 }
             }
