@@ -314,8 +314,9 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t Us[2][CW * CW];
     __shared__ uint32_t s_pc[2][CW], s_rp[2][CW + 1];
-    __shared__ uint32_t s_m[CW][RMAX];  // p - f of chunk row k for block row r, at [k][r]
-    __shared__ uint32_t s_mask[2][CW];  // per chunk row: the block rows with a non-zero multiplier
+    // per chunk row k: the block rows with a non-zero multiplier, as s_cnt[.][k] words
+    // (r << 16) | (p - f) in s_list[k] (p < 2^16), in no particular order
+    __shared__ uint32_t s_list[CW][RMAX], s_cnt[2][CW];
     __shared__ uint32_t s_base;
     const int jb = job_of_block(bstart, nj);
     const RedJob &J = jobs[jb];
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
     uint32_t *wcol = acc + (size_t)R * NS, *wval = wcol + win + 8;
     const uint32_t wcol_s = (uint32_t)__cvta_generic_to_shared(wcol), wval_s = (uint32_t)__cvta_generic_to_shared(wval);
     for (uint32_t t = threadIdx.x; t < nr * NS; t += RB) acc[t] = 0;
-    if (threadIdx.x < CW) s_mask[0][threadIdx.x] = 0;
+    if (threadIdx.x < CW) s_cnt[0][threadIdx.x] = 0;
     if (threadIdx.x == 0) s_base = J.N;
     __syncthreads();
     for (uint32_t r = 0; r < nr; ++r) {
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
         for (uint32_t t = t0; t <= cnt; t += step) {
             if (t < cnt) {
                 s_pc[b][t] = J.pcols[kc + t];
-                s_mask[b][t] = 0;
+                s_cnt[b][t] = 0;
             }
             s_rp[b][t] = J.row_ptr[kc + t];
         }
@@ -383,8 +384,7 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
 #pragma unroll
             for (int j = 0; j < CW; ++j) s += (unsigned long long)(__shfl_sync(0xffffffffu, x, j) * Wc[j * CW + lane]);
             const uint32_t f = lane < cnt ? fp_reduce(s, fp) : 0u;
-            s_m[lane][warp] = fp.p - f;
-            if (f) atomicOr(&s_mask[buf][lane], 1u << warp);
+            if (f) s_list[lane][atomicAdd(&s_cnt[buf][lane], 1u)] = (warp << 16) | (fp.p - f);
             uint32_t len = f ? s_rp[buf][lane + 1] - s_rp[buf][lane] : 0u;
 #pragma unroll
             for (int d = 16; d; d >>= 1) len += __shfl_xor_sync(0xffffffffu, len, d);
@@ -413,9 +413,10 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
                     while (e >= s_rp[buf][k + 1]) ++k;
                     const uint32_t c = wcol[e - a], v = wval[e - a];
                     // only the block rows with a non-zero multiplier for this pivot row
-                    for (uint32_t mask = s_mask[buf][k]; mask; mask &= mask - 1u) {
-                        const uint32_t r = __ffs(mask) - 1u;
-                        atomicAdd(&acc[r * NS + c], fp_reduce32(s_m[k][r] * v, fp));
+                    const uint32_t nk = s_cnt[buf][k];
+                    for (uint32_t j = 0; j < nk; ++j) {
+                        const uint32_t w = s_list[k][j];
+                        atomicAdd(&acc[(w >> 16) * NS + c], fp_reduce32((w & 0xFFFFu) * v, fp));
                     }
                 }
             }
