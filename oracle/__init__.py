@@ -1,6 +1,6 @@
 """THE ORACLE -- test infrastructure only.
 
-A plain CPU F4 over F_p (grevlex, x1 > ... > xn) written in C (`f4_oracle.c`) and loaded here with
+A plain CPU F4 over F_p (grevlex, or deglex with the DEGLEX flag; x1 > ... > xn) written in C (`f4_oracle.c`) and loaded here with
 ctypes.  Only tests/, the package smoke check and bench.py's CPU-baseline leg may import it; the
 product path never does.  It shares no code with the CUDA path.
 """
@@ -20,6 +20,7 @@ _lib = None
 
 ONE_PAIR = 1
 NEWEST_REDUCER = 2
+DEGLEX = 4  # the deglex term order instead of grevlex (both x1 > ... > xn)
 
 
 def build(force: bool = False) -> str:

@@ -21,7 +21,9 @@
  * Readings of points the paper leaves open (each is fixed identically, but independently, in the
  * CUDA path's host control):
  *   R1 grevlex with x1 > ... > xn: x^a > x^b iff deg a > deg b, or the degrees agree and the last
- *      nonzero entry of a - b is negative.
+ *      nonzero entry of a - b is negative.  With the flag OR_DEGLEX the other graded order of
+ *      Sec. 7.3, deglex: the same degree comparison, ties broken lexicographically (the first
+ *      nonzero entry of a - b is positive).
  *   R2 inputs are normalised: duplicate monomials merged mod p, zero terms and zero polynomials
  *      dropped, each polynomial made monic, terms sorted descending.
  *   R3 pairs are created and pruned with the Gebauer-Moeller update (Becker-Weispfenning 1993,
@@ -91,7 +93,11 @@ typedef struct {
     opoly *fin;
 } osys;
 
-enum { OR_ONE_PAIR = 1, OR_NEWEST_REDUCER = 2 };
+enum { OR_ONE_PAIR = 1, OR_NEWEST_REDUCER = 2, OR_DEGLEX = 4 };
+
+/* R1: the term order of the system being worked on, set from its flags by every entry point that
+   compares monomials (the oracle is single-threaded) */
+static int g_deglex;
 
 /* ---------------- monomials (R1) ---------------- */
 
@@ -101,10 +107,15 @@ static int m_deg(const omono *a, int n) {
     return d;
 }
 
-/* +1 if a > b, -1 if a < b, 0 if equal, in grevlex with x1 > ... > xn */
+/* +1 if a > b, -1 if a < b, 0 if equal, in grevlex (or deglex) with x1 > ... > xn */
 static int m_cmp(const omono *a, const omono *b, int n) {
     int da = m_deg(a, n), db = m_deg(b, n);
     if (da != db) return da > db ? 1 : -1;
+    if (g_deglex) {
+        for (int i = 0; i < n; ++i)
+            if (a->e[i] != b->e[i]) return a->e[i] > b->e[i] ? 1 : -1;
+        return 0;
+    }
     for (int i = n - 1; i >= 0; --i)
         if (a->e[i] != b->e[i]) return a->e[i] < b->e[i] ? 1 : -1;
     return 0;
@@ -423,6 +434,7 @@ static void reduce_row(uint32_t p, int N, const uint32_t *row_ptr, const uint32_
 int or_step(osys *S) {
     int n = S->n;
     uint32_t p = S->p;
+    g_deglex = (S->flags & OR_DEGLEX) != 0;
     if (S->np == 0) return 0;
     free_last(S);
 
@@ -687,6 +699,7 @@ static int fin_cmp(const void *x, const void *y, void *ctx) {
 
 int or_finish(osys *S) {
     int n = S->n;
+    g_deglex = (S->flags & OR_DEGLEX) != 0;
     if (S->finished) return 0;
     /* minimalise: drop g_i when another element's LM divides LM(g_i) (older wins on equality) */
     int *B = (int *)xrealloc(NULL, sizeof(int) * (size_t)(S->ng + 1));
@@ -734,6 +747,7 @@ osys *or_new(int n, uint32_t p, int m, const uint32_t *poly_off, const uint8_t *
     S->n = n;
     S->p = p;
     S->flags = flags;
+    g_deglex = (flags & OR_DEGLEX) != 0;
     int unit = 0;
     for (int i = 0; i < m; ++i) {
         int len = (int)(poly_off[i + 1] - poly_off[i]);
