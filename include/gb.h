@@ -22,8 +22,10 @@
  *   - Exports use a two-call pattern: call with NULL array pointers to learn the sizes (the size
  *     fields are filled), then call again with caller-allocated arrays of at least those sizes.
  *   - Coefficients cross the boundary as standard residues in [0, p).
- *   - Term order: grevlex with x1 > x2 > ... > xn (x^a > x^b iff deg a > deg b, or equal degrees
- *     and the last nonzero entry of a - b is negative).  Monomials are exponent vectors of n bytes.
+ *   - Term order, per system (gb_order): grevlex with x1 > x2 > ... > xn (x^a > x^b iff
+ *     deg a > deg b, or equal degrees and the last nonzero entry of a - b is negative), or deglex
+ *     (equal degrees: the first nonzero entry of a - b is positive), the two graded orders of the
+ *     monomial keys of Sec. 7.3.  Monomials are exponent vectors of n bytes.
  *   - p must be an odd prime below 2^31 (GB_EINVAL otherwise), 1 <= n <= 16.
  *   - A context and everything created from it is used by one host thread at a time, except the
  *     server, whose submit/poll calls may come from any thread.
@@ -50,7 +52,7 @@ typedef enum {
     GB_EBUSY = -7          /* server: the ticket is still running */
 } gb_status;
 
-typedef enum { GB_GREVLEX = 0 } gb_order;
+typedef enum { GB_GREVLEX = 0, GB_DEGLEX = 1 } gb_order;
 
 typedef struct gb_ctx gb_ctx;
 typedef struct gb_system gb_system;

@@ -27,6 +27,8 @@ GB_CTX_KEEP_STEP = 1
 GB_CTX_REDUCE_SPARSE = 2
 GB_CTX_REDUCE_DENSE = 4
 GB_CTX_NO_GRAPHS = 8
+GB_GREVLEX, GB_DEGLEX = 0, 1  # gb_order
+_ORDERS = {"grevlex": GB_GREVLEX, "deglex": GB_DEGLEX}
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -210,9 +212,13 @@ def _polys(system: dict):
 
 
 def gb_system_create(ctx: int, system: dict) -> int:
+    """A system from its dict; the optional key "order" is "grevlex" (the default) or "deglex"."""
+    order = system.get("order", "grevlex")
+    if order not in _ORDERS:
+        raise ValueError(f"unknown term order {order!r}")
     F, keep = _polys(system)
     h = _vp()
-    check(lib().gb_system_create(ctx, int(system["n"]), int(system["p"]), 0, ctypes.byref(F),
+    check(lib().gb_system_create(ctx, int(system["n"]), int(system["p"]), _ORDERS[order], ctypes.byref(F),
                                  ctypes.byref(h)), "gb_system_create")
     del keep
     return h.value

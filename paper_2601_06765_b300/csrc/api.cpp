@@ -300,13 +300,14 @@ gb_status gb_system_create(gb_ctx *ctx, uint32_t nvars, uint32_t p, gb_order ord
     GB_API_BEGIN
     if (!ctx || !out) fail(GB_EINVAL, "null context or out");
     *out = nullptr;
-    if (order != GB_GREVLEX) fail(GB_EUNSUPPORTED, "only grevlex is implemented");
+    if (order != GB_GREVLEX && order != GB_DEGLEX) fail(GB_EINVAL, "unknown term order");
     if (F && F->npolys && (!F->poly_off || ((!F->exps || !F->coeffs) && F->poly_off[F->npolys])))
         fail(GB_EINVAL, "null arrays in the input system");
     // host work only: the input reaches the device with the system's first step
     auto S = std::make_unique<gb_system>();
     S->ctx = ctx;
     S->stream = ctx->stream;
+    S->deglex = order == GB_DEGLEX;
     system_init(S.get(), nvars, p, F);
     *out = S.release();
     return GB_OK;

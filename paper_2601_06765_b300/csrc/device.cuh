@@ -140,26 +140,40 @@ __device__ __forceinline__ uint32_t byte_of(uint4 m, int i) {
 // of Sec. 11),
 // so it serves as MonKey, and as a bitmap index in [0, C(n + D, n)) for degrees <= D.
 //
-// tab (shared memory), rows of 2^sh entries: row 0 holds tab[d] = C(n + d - 1, n) for d in [0, D],
-// row j = 1..n-1 holds tab[(j << sh) + s] = C(s + j - 1, j) for s in [0, D] (2^sh > D).
+// Dense deglex rank (deglex: the first differing exponent decides, the larger one giving the
+// larger monomial):
+//     rank(a) = C(n + d - 1, n) + sum_{j=1}^{n-1} [C(d - S_{j-1} + n - j, n - j) - C(d - S_j + n - j, n - j)]
+// (S_0 = 0).  Within degree d, a monomial b is smaller than a iff at the first index j where they
+// differ b_j < a_j; with b_1..b_{j-1} fixed to a's, C(d - S_{j-1} + n - j, n - j) counts the
+// completions with b_j >= 0 and C(d - S_j + n - j, n - j) those with b_j >= a_j, so the difference
+// counts b_j < a_j (a hockey-stick sum).
+//
+// tab (shared memory), rows of 2^sh entries: row 0 holds tab[d] = C(n + d - 1, n) for d in [0, D];
+// row j = 1..n-1 holds, for s in [0, D] (2^sh > D), tab[(j << sh) + s] = C(s + j - 1, j) (grevlex)
+// or C(s + n - j, n - j) (deglex).
 // The prefix sums S_j come four at a time from one multiply: byte k of w * 0x01010101 is the sum of
 // bytes 0..k of w (no byte carries: every S_j <= D <= 255), and the running total is added to every
 // byte of the next word the same way.
-__device__ __forceinline__ uint32_t mono_rank(uint4 m, const uint32_t *tab, int n, int sh) {
+__device__ __forceinline__ uint32_t mono_rank(uint4 m, const uint32_t *tab, int n, int sh, bool deglex) {
     const uint32_t p0 = m.x * 0x01010101u;
     const uint32_t p1 = m.y * 0x01010101u + (p0 >> 24) * 0x01010101u;
     const uint32_t p2 = m.z * 0x01010101u + (p1 >> 24) * 0x01010101u;
     const uint32_t p3 = m.w * 0x01010101u + (p2 >> 24) * 0x01010101u;
-    uint32_t r = 0;
+    const uint32_t d = __dp4a(m.x, 0x01010101u, 0u) + __dp4a(m.y, 0x01010101u, 0u) +
+                       __dp4a(m.z, 0x01010101u, 0u) + __dp4a(m.w, 0x01010101u, 0u);
+    uint32_t r = 0, prev = 0;  // prev = S_{j-1}
 #pragma unroll
     for (int j = 1; j < 16; ++j) {
         if (j >= n) break;
         const uint32_t w = j <= 4 ? p0 : j <= 8 ? p1 : j <= 12 ? p2 : p3;  // S_j is byte j - 1
         const uint32_t sj = (w >> (8 * ((j - 1) & 3))) & 0xFFu;
-        r += tab[(j << sh) + sj];
+        if (deglex) {
+            r += tab[(j << sh) + d - prev] - tab[(j << sh) + d - sj];
+            prev = sj;
+        } else {
+            r += tab[(j << sh) + sj];
+        }
     }
-    const uint32_t d = __dp4a(m.x, 0x01010101u, 0u) + __dp4a(m.y, 0x01010101u, 0u) +
-                       __dp4a(m.z, 0x01010101u, 0u) + __dp4a(m.w, 0x01010101u, 0u);
     return r + tab[d];
 }
 

@@ -30,15 +30,19 @@ int mono_deg(const Mono &a, int n) {
     return d;
 }
 
-int mono_cmp(const Mono &a, const Mono &b, int n) {
-    // equal degrees: the last differing exponent decides, the smaller one giving the larger
-    // monomial.  With byte i = exponent of x_{i+1} (bytes >= n zero), the last differing byte is
-    // the most significant differing byte of the 128-bit little-endian word, so the words compare
-    // in reverse.
+int mono_cmp(const Mono &a, const Mono &b, int n, bool deglex) {
+    // grevlex, equal degrees: the last differing exponent decides, the smaller one giving the
+    // larger monomial.  With byte i = exponent of x_{i+1} (bytes >= n zero), the last differing
+    // byte is the most significant differing byte of the 128-bit little-endian word, so the words
+    // compare in reverse.  deglex, equal degrees: the first differing exponent decides, the larger
+    // one giving the larger monomial (bytewise lexicographic comparison).
     const M16 x = m16(a), y = m16(b);
     const uint32_t da = deg16(x), db = deg16(y);
-    (void)n;
     if (da != db) return da > db ? 1 : -1;
+    if (deglex) {
+        const int c = std::memcmp(a.e, b.e, (size_t)n);
+        return c > 0 ? 1 : c < 0 ? -1 : 0;
+    }
     if (x.hi != y.hi) return x.hi < y.hi ? 1 : -1;
     if (x.lo != y.lo) return x.lo < y.lo ? 1 : -1;
     return 0;
@@ -363,11 +367,12 @@ std::vector<RowSpec> order_rows(const gb_system *S, std::vector<std::pair<Mono, 
         if (x.second >= S->lm.size()) fail(GB_EINVAL, "row refers to a basis element that does not exist");
         rows.push_back(R{x.first, mono_mul(x.first, S->lm[x.second], n), x.second});
     }
-    std::sort(rows.begin(), rows.end(), [n](const R &a, const R &b) {
-        const int c = mono_cmp(a.lm, b.lm, n);
+    const bool dl = S->deglex;
+    std::sort(rows.begin(), rows.end(), [n, dl](const R &a, const R &b) {
+        const int c = mono_cmp(a.lm, b.lm, n, dl);
         if (c) return c > 0;
         if (a.k != b.k) return a.k < b.k;
-        return mono_cmp(a.t, b.t, n) < 0;
+        return mono_cmp(a.t, b.t, n, dl) < 0;
     });
     std::vector<RowSpec> out;
     for (size_t i = 0; i < rows.size(); ++i) {
@@ -433,7 +438,8 @@ void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F) {
             std::memcpy(m.e, F->exps + (size_t)q * n, n);
             t.emplace_back(m, F->coeffs[q] % p);
         }
-        std::sort(t.begin(), t.end(), [n](const auto &x, const auto &y) { return mono_cmp(x.first, y.first, n) > 0; });
+        const bool dl = S->deglex;
+        std::sort(t.begin(), t.end(), [n, dl](const auto &x, const auto &y) { return mono_cmp(x.first, y.first, n, dl) > 0; });
         std::vector<Mono> mon;
         std::vector<uint32_t> cf;
         for (size_t q = 0; q < t.size();) {
@@ -494,6 +500,7 @@ gb_system *system_clone_fresh(const gb_system *S) {
     auto C = std::make_unique<gb_system>();
     C->ctx = S->ctx;
     C->stream = S->stream;
+    C->deglex = S->deglex;
     system_init(C.get(), n, S->p, &F);
     return C.release();
 }
@@ -684,7 +691,7 @@ void finish_batch(const std::vector<gb_system *> &Ss) {
             if (!drop) keep[j].push_back(i);
         }
         std::sort(keep[j].begin(), keep[j].end(),
-                  [&](uint32_t a, uint32_t b) { return mono_cmp(S->lm[a], S->lm[b], n) > 0; });
+                  [&](uint32_t a, uint32_t b) { return mono_cmp(S->lm[a], S->lm[b], n, S->deglex) > 0; });
     });
     // the tails t(g) = g - LM(g), reduced by the minimal basis with the same pipeline: the closure
     // supplies reducer rows for every tail monomial a leading monomial divides, and the sparse

@@ -133,7 +133,7 @@ struct Mono {
 };
 inline bool operator==(const Mono &a, const Mono &b) { return std::memcmp(a.e, b.e, 16) == 0; }
 int mono_deg(const Mono &a, int n);
-int mono_cmp(const Mono &a, const Mono &b, int n);  // grevlex: +1 a > b, -1 a < b, 0 equal
+int mono_cmp(const Mono &a, const Mono &b, int n, bool deglex = false);  // +1 a > b, -1 a < b, 0 equal
 Mono mono_mul(const Mono &a, const Mono &b, int n);
 Mono mono_div(const Mono &b, const Mono &a, int n);
 Mono mono_lcm(const Mono &a, const Mono &b, int n);
@@ -310,6 +310,7 @@ struct gb_system {
     std::vector<gb::PairL> pairs;
     std::vector<gb::M16> lm16;     // leading monomials, SWAR form
     bool swar = true;              // every exponent so far below 128
+    bool deglex = false;           // term order: deglex, else grevlex
     // device basis: terms of element k are [off[k], off[k] + len[k]) of bmon / bcf
     gb::DBuf<uint4> bmon;
     gb::DBuf<uint32_t> bcf;

@@ -53,6 +53,7 @@ struct Job {
     uint32_t *bits;
     const uint32_t *tab;
     int n, sh, tabsz;  // table rows of 2^sh entries
+    int deglex;        // the rank table and mono_rank in deglex, else grevlex
     uint32_t W;
     // closure
     const uint32_t *nr_idx;
@@ -123,7 +124,7 @@ __device__ __forceinline__ void expand_terms(uint4 t, uint32_t off, uint32_t j0,
         uint32_t r = 0;
         if (j < len) {
             m = mono_mul(t, J.bmon[off + j]);
-            r = mono_rank(m, tab, J.n, J.sh);
+            r = mono_rank(m, tab, J.n, J.sh, J.deglex != 0);
             isnew = test_and_set(J.bits, r);
         }
         push_new(isnew, m, r, J);
@@ -143,7 +144,7 @@ __global__ void k_mark_given(const Job *__restrict__ jobs, const uint32_t *__res
         return;
     }
     const uint4 m = mono_mul(J.gt[i], J.bmon[J.boff[J.gk[i]]]);
-    const uint32_t r = mono_rank(m, tab, J.n, J.sh);
+    const uint32_t r = mono_rank(m, tab, J.n, J.sh, J.deglex != 0);
     atomicOr(&J.bits[r >> 5], 1u << (r & 31));
     J.lm_rank[i] = r;
 }
@@ -312,7 +313,7 @@ __global__ void k_fill(const Job *__restrict__ jobs, const uint32_t *__restrict_
         for (int u = 0; u < 4; ++u) {
             const uint32_t j = j0 + 32u * u;
             if (j < len) {
-                r[u] = mono_rank(mono_mul(t, J.bmon[off + j]), tab, J.n, J.sh);
+                r[u] = mono_rank(mono_mul(t, J.bmon[off + j]), tab, J.n, J.sh, J.deglex != 0);
                 v[u] = J.bcf[off + j];
             }
         }
@@ -396,7 +397,9 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         h.tab.assign((size_t)n << h.sh, 0);
         for (uint32_t d = 0; d <= h.D; ++d) h.tab[d] = (uint32_t)(d ? binom(n + d - 1, n) : 0);
         for (int i = 1; i < n; ++i)
-            for (uint32_t s = 0; s <= h.D; ++s) h.tab[((size_t)i << h.sh) + s] = (uint32_t)binom(s + i - 1, i);
+            for (uint32_t s = 0; s <= h.D; ++s)
+                h.tab[((size_t)i << h.sh) + s] =
+                    (uint32_t)(S->deglex ? binom(s + (uint32_t)(n - i), (uint32_t)(n - i)) : binom(s + i - 1, i));
         h.tabsz = (uint32_t)h.tab.size();
         h.np_index.assign(h.ng, 0xFFFFFFFFu);
         h.gt.resize(h.ng);
@@ -468,6 +471,7 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         J.n = (int)S->n;
         J.sh = (int)h.sh;
         J.tabsz = (int)h.tabsz;
+        J.deglex = S->deglex ? 1 : 0;
         J.W = h.W;
         J.nr_idx = reinterpret_cast<const uint32_t *>(dptr(h.o_nri));
         J.nr_lm = reinterpret_cast<const uint4 *>(dptr(h.o_nrl));
