@@ -389,7 +389,7 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         if (h.D > 255) fail(GB_EOVERFLOW, "step degree above 255");
         h.space = binom((uint32_t)n + h.D, (uint32_t)n);
         if (h.space >= (1ull << 32) - 64)
-            fail(GB_EUNSUPPORTED, "monomial space C(n+D, n) above 2^32 for the dense grevlex keys");
+            fail(GB_EUNSUPPORTED, "monomial space C(n+D, n) above 2^32 for the dense monomial keys");
         h.D1 = h.D + 1;
         h.sh = 0;
         while ((1u << h.sh) < h.D1) ++h.sh;
