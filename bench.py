@@ -117,7 +117,7 @@ def run_ours(args) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    system = synth.config2(0)
+    system = synth.dense_n10(0)
     ctx = gb.Context(device=local, arena_bytes=args.arena_gb << 30, graphs=not args.no_graphs)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 126 MB L2
 
@@ -195,12 +195,12 @@ def run_ours(args) -> None:
                 "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / pk["hbm_gbs"], 4),
                 "peak_source": f"{pk['source']} HBM copy bandwidth",
-                "traffic": profile_traffic("k_reduce_rows_config2")}
+                "traffic": profile_traffic("k_reduce_rows_dense_n10")}
 
     batched = measure_batched(gb, synth, ctx, rank, world) if not args.no_batch else None
     served = measure_served(gb, synth, ctx) if rank == 0 and not args.no_batch else None
     tensor = measure_tensor_core(gb, local) if rank == 0 and not args.no_batch else None
-    big = measure_config3(gb, synth, local, pk, graphs=not args.no_graphs) if rank == 0 and not args.no_batch else None
+    big = measure_sparse_n13(gb, synth, local, pk, graphs=not args.no_graphs) if rank == 0 and not args.no_batch else None
     deglex = None
     if rank == 0 and not args.no_batch:
         try:
@@ -233,7 +233,7 @@ def run_ours(args) -> None:
             "batched": batched,
             "served": served,
             "tensor_core": tensor,
-            "config3": big,
+            "sparse_n13": big,
             "deglex": deglex,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -383,13 +383,13 @@ def measure_tensor_core(gb, local: int) -> list:
     return out
 
 
-def measure_config3(gb, synth, local: int, pk: dict, graphs: bool = True) -> dict:
+def measure_sparse_n13(gb, synth, local: int, pk: dict, graphs: bool = True) -> dict:
     """One F4 run of the n=13 sparse 31-bit system (the large-matrix workload) with the reduction
     chosen per matrix by the shape rules (dense tensor-core blocks for the large steps), with the
     sparse reduction only, and with the schedules gb_autotune measured on this system (its three
     tuning runs are not in the timed run); and the symbolic preprocessing bandwidth of its largest step (algorithmic bytes: col_ind +
     val written per nonzero, row_ptr, and the dictionary monomials)."""
-    system = synth.config3(0)
+    system = synth.sparse_n13(0)
     res = {"workload": "n=13, m=13 quadratics with 30 of the 105 monomials of degree <= 2, p=2^31-1, grevlex, "
                        "SplitMix64 seed 20260765; one full F4 run"}
     for mode in ("auto", "sparse", "tuned"):
@@ -430,7 +430,7 @@ def measure_deglex(gb, synth, ctx) -> dict:
     """The same n=10 system in the deglex order: one warm-up run, then the best of three full F4
     runs to the reduced basis, timed with CUDA events on the context's stream around the run."""
     import torch
-    system = {**synth.config2(0), "order": "deglex"}
+    system = {**synth.dense_n10(0), "order": "deglex"}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
     best = None
@@ -480,7 +480,7 @@ def run_reference(args) -> None:
         return
     import oracle
     from paper_2601_06765_b300 import synth
-    system = synth.config2(0)
+    system = synth.dense_n10(0)
     # each step: a bounded sample of the workload -- the first 6 F4 steps of the run (~5 s)
     def sample():
         o = oracle.Oracle(system)
@@ -521,7 +521,7 @@ def main() -> None:
     ap.add_argument("--no-tune", action="store_true",
                     help="run the workload on the shape rules, without gb_autotune before the timed region")
     ap.add_argument("--arena-gb", type=int, default=32, help="device arena of the context (GiB)")
-    ap.add_argument("--only", choices=["tensor", "config3"], default=None,
+    ap.add_argument("--only", choices=["tensor", "sparse_n13"], default=None,
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
@@ -533,7 +533,7 @@ def main() -> None:
         if args.only == "tensor":
             print(json.dumps({"tensor_core": measure_tensor_core(gb, 0)}))
         else:
-            print(json.dumps({"config3": measure_config3(gb, synth, 0, peaks(), graphs=not args.no_graphs)}))
+            print(json.dumps({"sparse_n13": measure_sparse_n13(gb, synth, 0, peaks(), graphs=not args.no_graphs)}))
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -128,17 +128,17 @@ def sparse_system(n: int, m: int, p: int, seed: int, terms: int | tuple[int, int
 
 # ---- the five workloads ---------------------------------------------------------------------
 
-def config1(seed_index: int = 0) -> dict:
+def dense_n6(seed_index: int = 0) -> dict:
     """n=6, m=6, all 28 monomials of degree <= 2, p=65521."""
     return dense_system(6, 6, P16, BASE_SEED + seed_index)
 
 
-def config2(seed_index: int = 0) -> dict:
+def dense_n10(seed_index: int = 0) -> dict:
     """n=10, m=10, all 66 monomials of degree <= 2, p=65521."""
     return dense_system(10, 10, P16, BASE_SEED + seed_index)
 
 
-def config3(seed_index: int = 0) -> dict:
+def sparse_n13(seed_index: int = 0) -> dict:
     """n=13, m=13, 30 of the 105 monomials of degree <= 2 per polynomial, p=2^31-1."""
     return sparse_system(13, 13, P31, BASE_SEED + seed_index, 30)
 

@@ -57,7 +57,7 @@ def test_batch_equals_alone_and_oracle(ctx):
 
 def test_batch_of_one_and_of_none(ctx):
     assert gb.gb_batch_groebner(ctx.h, []) == []
-    s = synth.config1(4)
+    s = synth.dense_n6(4)
     h = gb.gb_system_create(ctx.h, s)
     try:
         gb.gb_batch_groebner(ctx.h, [h])
@@ -119,7 +119,7 @@ def test_server_admission_under_a_tight_cap(ctx):
 def test_server_poll_reports_busy_and_unknown(ctx):
     srv = gb.gb_server_create(ctx.h, 4 << 30, 2)
     try:
-        s = synth.config2(0)
+        s = synth.dense_n10(0)
         t = gb.gb_server_submit(srv, gb.gb_system_create(ctx.h, s))
         h, st = gb.gb_server_poll(srv, t)
         if h is None:

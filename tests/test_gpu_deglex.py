@@ -68,9 +68,9 @@ def test_small_systems_deglex(ctx, name, system):
     run_parity_deglex(ctx, system)
 
 
-def test_config1_deglex(ctx):
+def test_dense_n6_deglex(ctx):
     """n=6 dense quadratics mod 65521: every step and the reduced basis, in deglex."""
-    assert run_parity_deglex(ctx, synth.config1(0)) >= 5
+    assert run_parity_deglex(ctx, synth.dense_n6(0)) >= 5
 
 
 def test_dictionary_order_is_deglex_exhaustive(ctx):

@@ -32,8 +32,8 @@ def ctx():
     c.close()
 
 
-def test_config3_large_step_dprime_rows_and_rref(ctx):
-    with gb.System(ctx, synth.config3(0)) as S:
+def test_sparse_n13_large_step_dprime_rows_and_rref(ctx):
+    with gb.System(ctx, synth.sparse_n13(0)) as S:
         for _ in range(6):
             assert S.step()[0] == gb.GB_OK
         mac, ech = S.last_step()
@@ -87,8 +87,8 @@ def _grevlex_key(e: np.ndarray):
     return (int(e.sum()),) + tuple(-int(x) for x in e[::-1])
 
 
-def test_config3_reduced_basis_properties(ctx):
-    h = gb.gb_system_create(ctx.h, synth.config3(0))
+def test_sparse_n13_reduced_basis_properties(ctx):
+    h = gb.gb_system_create(ctx.h, synth.sparse_n13(0))
     gb.gb_groebner(h)
     off, ex, cf = gb.gb_basis_export(h, 13, True)
     gb.gb_system_destroy(h)

@@ -13,7 +13,7 @@ from paper_2601_06765_b300 import synth
 pytestmark = pytest.mark.gpu
 
 CASES = [
-    ("config1", synth.config1(0), "auto"),
+    ("dense_n6", synth.dense_n6(0), "auto"),
     ("sparse_n7_p31", synth.sparse_system(7, 7, 2147483647, 21, (10, 30)), "auto"),
     # forced dense: the rounds also hold the tensor-core trailing update (k_mm) of each panel
     ("dense_n6_p16_tc", synth.dense_system(6, 6, 65521, 22), "dense"),

@@ -90,20 +90,20 @@ def test_small_systems(ctx, name, system):
 
 
 @pytest.mark.parametrize("seed", range(3))
-def test_config1_dense_n6(ctx, seed):
+def test_dense_n6(ctx, seed):
     """n=6 dense quadratics mod 65521: every step and the reduced basis."""
-    assert run_parity(ctx, synth.config1(seed)) >= 5
+    assert run_parity(ctx, synth.dense_n6(seed)) >= 5
 
 
-def test_config2_dense_n10_full(ctx):
+def test_dense_n10_full(ctx):
     """The benchmark workload (n=10 dense quadratics mod 65521), every step bit-exact."""
-    assert run_parity(ctx, synth.config2(0)) == 11
+    assert run_parity(ctx, synth.dense_n10(0)) == 11
 
 
-def test_config3_sparse_n13_p31_first_steps(ctx):
+def test_sparse_n13_p31_first_steps(ctx):
     """n=13 sparse quadratics mod 2^31-1 (31-bit Montgomery path): the first steps the oracle
     finishes in seconds."""
-    run_parity(ctx, synth.config3(0), max_steps=4, final=False)
+    run_parity(ctx, synth.sparse_n13(0), max_steps=4, final=False)
 
 
 def test_mixed_batch_members(ctx):
@@ -124,7 +124,7 @@ def test_multi_prime_members(ctx):
 def test_standalone_sp_and_reduce_match_oracle_steps(ctx):
     """gb_symbolic_preprocess + gb_reduce_macaulay called directly with the oracle's pair rows of
     step k (after k-1 F4 steps on the device) reproduce the oracle's step-k matrices."""
-    system = synth.config1(1)
+    system = synth.dense_n6(1)
     o = oracle.Oracle(system)
     with gb.System(ctx, system) as S:
         for k in range(1, 6):
@@ -175,7 +175,7 @@ def test_dictionary_order_is_grevlex_exhaustive(ctx):
 
 def test_determinism(ctx):
     """the determinism theorem of Sec. 11: the same batch gives byte-identical plans on repeated runs."""
-    system = synth.config1(2)
+    system = synth.dense_n6(2)
     dumps = []
     for _ in range(2):
         with gb.System(ctx, system) as S:

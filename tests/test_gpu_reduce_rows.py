@@ -18,10 +18,10 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("window", [None, 1000, 8])
-def test_config2_steps_with_rows_kernel(window, monkeypatch):
+def test_dense_n10_steps_with_rows_kernel(window, monkeypatch):
     if window is not None:
         monkeypatch.setenv("GB_ROWS_WINDOW", str(window))
-    system = synth.config2(0)
+    system = synth.dense_n10(0)
     o = oracle.Oracle(system)
     ctx = gb.Context(arena_bytes=6 << 30, keep_step=True, reduce="sparse")
     try:

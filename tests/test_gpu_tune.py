@@ -16,7 +16,7 @@ from paper_2601_06765_b300 import synth
 
 pytestmark = pytest.mark.gpu
 
-SYSTEMS = [synth.config1(0), synth.sparse_system(7, 7, 2147483647, 31, (10, 30))]
+SYSTEMS = [synth.dense_n6(0), synth.sparse_system(7, 7, 2147483647, 31, (10, 30))]
 
 
 def _steps(ctx, system):
@@ -119,7 +119,7 @@ def test_tune_rejects_bad_input(tmp_path):
 def test_scan_tiles_from_a_loaded_table_keep_results(tmp_path):
     """Every prefix-sum tile (4, 8, 16 values per thread) gives the same plans: a table that sets
     each size bucket to one tile in turn leaves every step of a run bit-identical."""
-    system = synth.config1(0)
+    system = synth.dense_n6(0)
     with gb.Context(arena_bytes=1 << 30, keep_step=True) as ctx:
         want, basis = _steps(ctx, system)
     for choice in range(3):

@@ -55,7 +55,7 @@ def test_reduced_basis_matches_sympy_n5():
 def test_buchberger_criterion_and_membership(seed):
     """Buchberger's criterion (Sec. 2.1): every S-polynomial of the output reduces to 0; each input
     reduces to 0 modulo the output; the output is reduced and monic."""
-    s = synth.dense_system(4, 4, 65521, 300 + seed) if seed < 2 else synth.config1(0)
+    s = synth.dense_system(4, 4, 65521, 300 + seed) if seed < 2 else synth.dense_n6(0)
     G = _final_dicts(s)
     p = s["p"]
     assert R.is_reduced(G, p)
@@ -78,7 +78,7 @@ def test_variety_bruteforce(n, p):
 def test_variants_give_the_same_reduced_basis(seed):
     """The reduced basis is unique: one pair per step (Buchberger-like selection) and the newest
     instead of the oldest reducer change every intermediate matrix but not the result."""
-    s = synth.config1(seed) if seed < 3 else synth.sparse_system(5, 5, 2147483647, seed, (6, 12), 3)
+    s = synth.dense_n6(seed) if seed < 3 else synth.sparse_system(5, 5, 2147483647, seed, (6, 12), 3)
     a = oracle.groebner(s)
     assert oracle.groebner(s, oracle.ONE_PAIR) == a
     assert oracle.groebner(s, oracle.NEWEST_REDUCER) == a
@@ -117,7 +117,7 @@ def _row_poly(basis, t, k):
     return {R.mono_mul(tuple(int(x) for x in t), e): c for e, c in g.items()}
 
 
-STEP_SYSTEMS = [synth.config1(0), synth.dense_system(4, 4, 2147483647, 31),
+STEP_SYSTEMS = [synth.dense_n6(0), synth.dense_system(4, 4, 2147483647, 31),
                 synth.sparse_system(4, 4, 65521, 808, (5, 12), degree=3)]
 
 

@@ -52,7 +52,7 @@ def _run_noalloc(torch, p, m, want):
 def test_noalloc_matches_gb_reduce_macaulay_on_consecutive_calls():
     import torch
     with gb.Context(arena_bytes=1 << 30, keep_step=True) as ctx:
-        S1, m1, w1 = _matrix_after_steps(ctx, synth.config1(0), 5)                         # p = 65521
+        S1, m1, w1 = _matrix_after_steps(ctx, synth.dense_n6(0), 5)                         # p = 65521
         S2, m2, w2 = _matrix_after_steps(ctx, synth.dense_system(5, 5, 2147483647, 7), 4)  # 31-bit p
         assert w1["dprime"].size and w2["dprime"].size
         first = _run_noalloc(torch, 65521, m1, w1)
