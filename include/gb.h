@@ -48,7 +48,7 @@ typedef enum {
     GB_EOVERFLOW = -3,     /* an exponent above 255 or a monomial space too large for the keys */
     GB_ETIMEOUT = -4,      /* a bounded device wait gave up */
     GB_EDEVICE = -5,       /* a CUDA error */
-    GB_EUNSUPPORTED = -6,  /* valid but outside what this build handles */
+    GB_EUNSUPPORTED = -6,  /* valid but outside what the library handles */
     GB_EBUSY = -7          /* server: the ticket is still running */
 } gb_status;
 
