@@ -48,3 +48,14 @@ def test_null_arguments_are_rejected_without_gpu():
     assert L.gb_system_destroy(None) == -1
     assert L.gb_f4_step(None, None) == -1
     assert L.gb_macaulay_export(None, None) == -1
+
+
+def test_binding_constants_match_the_header():
+    """The enum and flag values the binding passes are the header's."""
+    src = re.sub(r"/\*.*?\*/", "", open(gb.HEADER).read(), flags=re.S)
+    vals = {k: int(v, 0) for k, v in re.findall(r"\b(GB_[A-Z0-9_]+)\s*=\s*(-?(?:0x[0-9a-fA-F]+|\d+))", src)}
+    vals.update({k: int(v.rstrip("u"), 0) for k, v in re.findall(r"#define\s+(GB_[A-Z0-9_]+)\s+(\d+u?)", src)})
+    for name in ("GB_OK", "GB_DONE", "GB_GREVLEX", "GB_DEGLEX", "GB_CTX_KEEP_STEP", "GB_CTX_REDUCE_SPARSE",
+                 "GB_CTX_REDUCE_DENSE", "GB_CTX_NO_GRAPHS"):
+        assert name in vals, name
+        assert getattr(gb, name) == vals[name], name
