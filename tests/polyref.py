@@ -143,3 +143,80 @@ def sympy_reduced_gb(system: dict) -> list[list[tuple[tuple[int, ...], int]]]:
         out.append(terms)
     out.sort(key=lambda t: grevlex(t[0][0]), reverse=True)
     return out
+
+
+def mono_deg(a) -> int:
+    return sum(a)
+
+
+def coprime(a, b) -> bool:
+    return all(x == 0 or y == 0 for x, y in zip(a, b))
+
+
+class PairModel:
+    """Critical-pair bookkeeping written from the textbook, independently of the oracle: the
+    procedure UPDATE of Becker-Weispfenning, *Groebner Bases* (1993) -- the Gebauer-Moeller
+    criteria -- and the normal selection strategy (every pair whose lcm has the least degree,
+    the "degree-driven" selection of Sec. 3.1 / Sec. 4.2).
+
+    It sees only the leading monomial of each basis element, in the order the elements are
+    inserted.  Pairs are (i, j) with i < j (basis indices).  `in_g[i]` is False once element i has
+    left G because a newer leading monomial divides its own."""
+
+    def __init__(self):
+        self.lms: list[tuple] = []
+        self.in_g: list[bool] = []
+        self.B: set[tuple[int, int]] = set()
+
+    def insert(self, h_lm: tuple) -> None:
+        """UPDATE(G_old, B_old, h): the pairs of h with G_old (visited oldest first) are kept
+        when coprime or when no other pair of h -- still waiting, or already kept -- has an lcm
+        dividing theirs; the coprime ones are then dropped (product criterion).  An old pair
+        {g1, g2} is dropped when LM(h) divides its lcm and that lcm differs from both lcm(g1, h)
+        and lcm(g2, h) (chain criterion).  Elements of G_old whose leading monomial LM(h) divides
+        leave G."""
+        h = len(self.lms)
+        g_old = [g for g in range(h) if self.in_g[g]]
+        self.lms.append(tuple(h_lm))
+        self.in_g.append(True)
+        lh = self.lms[h]
+        waiting = list(g_old)
+        kept: list[int] = []
+        while waiting:
+            g1 = waiting.pop(0)
+            l1 = lcm(lh, self.lms[g1])
+            if coprime(lh, self.lms[g1]):
+                kept.append(g1)
+                continue
+            shadowed = any(divides(lcm(lh, self.lms[g2]), l1) for g2 in waiting) or \
+                any(divides(lcm(lh, self.lms[g2]), l1) for g2 in kept)
+            if not shadowed:
+                kept.append(g1)
+        new_pairs = {(g, h) for g in kept if not coprime(lh, self.lms[g])}
+        survivors = set()
+        for g1, g2 in self.B:
+            l12 = lcm(self.lms[g1], self.lms[g2])
+            if (not divides(lh, l12) or lcm(self.lms[g1], lh) == l12
+                    or lcm(self.lms[g2], lh) == l12):
+                survivors.add((g1, g2))
+        self.B = survivors | new_pairs
+        for g in g_old:
+            if divides(lh, self.lms[g]):
+                self.in_g[g] = False
+
+    def select(self) -> tuple[int, set[tuple[int, int]]]:
+        """Normal strategy: remove and return every pair whose lcm has the least degree."""
+        d = min(mono_deg(lcm(self.lms[i], self.lms[j])) for i, j in self.B)
+        chosen = {q for q in self.B if mono_deg(lcm(self.lms[q[0]], self.lms[q[1]])) == d}
+        self.B -= chosen
+        return d, chosen
+
+    def pair_rows(self, chosen) -> set[tuple[tuple, int]]:
+        """The rows (lcm / LM(g_i), i) and (lcm / LM(g_j), j) of the chosen pairs, as a set: equal
+        rows of different pairs are one row of the matrix."""
+        rows = set()
+        for i, j in chosen:
+            L = lcm(self.lms[i], self.lms[j])
+            rows.add((mono_div(L, self.lms[i]), i))
+            rows.add((mono_div(L, self.lms[j]), j))
+        return rows

@@ -14,7 +14,8 @@ import pytest
 import oracle
 from paper_2601_06765_b300 import synth
 from tests import polyref as R
-from tests.test_oracle_pins import check_dictionary_matrix_closure, check_reduction_and_echelon
+from tests.test_oracle_pins import (PAIR_SYSTEMS, check_dictionary_matrix_closure,
+                                    check_pairs_replay, check_reduction_and_echelon)
 
 MUTANTS = {
     "axpy_sign": ("uint32_t mf = p - f; /* v <- v - f * pivot row */",
@@ -42,6 +43,20 @@ MUTANTS = {
                                          "    for (int c = start + 1; c < N; ++c) {"),
     "tail_not_reduced": ("        opoly r = full_reduce(S, &tail, B, nB);",
                          "        opoly r = full_reduce(S, &tail, B, 0);"),
+    # pair selection (normal strategy) and the Gebauer-Moeller update: these change every
+    # intermediate matrix but not the reduced basis, so only the pair replay catches them
+    "selection_takes_largest_degree": ("        if (d < dmin) dmin = d;",
+                                       "        if (d > dmin || dmin == 1 << 30) dmin = d;"),
+    "product_criterion_dropped": ("if (keepD[a] && !m_coprime(lh, &S->g[C[a]].mon[0], n)) add_pair(S, C[a], hidx);",
+                                  "if (keepD[a]) add_pair(S, C[a], hidx);"),
+    "chain_criterion_on_old_pairs_dropped": ("        if (!drop) S->pairs[w++] = S->pairs[q];",
+                                             "        (void)drop; S->pairs[w++] = S->pairs[q];"),
+    "equal_pair_rows_not_collapsed": ("if (u == 0 || rows[u - 1].k != rows[a].k || !m_eq(&rows[u - 1].t, &rows[a].t, n)) rows[u++] = rows[a];",
+                                      "rows[u++] = rows[a];"),
+    "first_loop_checks_rejected_pairs": ("                if (keepD[b] && m_divides(&L[b], &L[a], n)) keep = 0;",
+                                         "                if (m_divides(&L[b], &L[a], n)) keep = 0;"),
+    "first_loop_no_coprime_exemption": ("        if (!m_coprime(lh, &S->g[C[a]].mon[0], n)) {",
+                                        "        if (1) {"),
 }
 
 SMALL = [synth.sparse_system(3, 3, 7, 9007, (2, 4)), synth.sparse_system(3, 3, 7, 9011, (2, 4)),
@@ -56,6 +71,8 @@ def _pins_pass(lib) -> bool:
                 return False
         check_dictionary_matrix_closure(synth.dense_system(4, 4, 65521, 9), lib=lib, limit=4)
         check_reduction_and_echelon(synth.dense_system(3, 3, 65521, 10), lib=lib, limit=3)
+        for s in PAIR_SYSTEMS:
+            check_pairs_replay(s, lib=lib)
     except (AssertionError, KeyError, ValueError, IndexError, ZeroDivisionError):
         return False
     return True

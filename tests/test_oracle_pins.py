@@ -272,3 +272,74 @@ def test_kernel_vectors_are_syzygies():
             assert acc == {}
             checked += 1
     assert checked > 0  # this system's later steps have rank-deficient pair rows
+
+
+# ---- pair selection, the Gebauer-Moeller update and the pair rows --------------------------
+
+def check_pairs_replay(system, lib=None, limit=100):
+    """The oracle's critical pairs against the textbook model of tests/polyref.py
+    (Becker-Weispfenning's UPDATE, normal selection), fed only the leading monomials of the
+    oracle's basis elements in insertion order.  Before every step the two pair sets and the
+    set of elements still in G agree; the step's degree is the least lcm degree of that pair set
+    and exactly the pairs of that degree leave it; the step's pair rows (those the closure did not
+    add) are exactly the rows (lcm/LM(g_i), i), (lcm/LM(g_j), j) of the chosen pairs, each once;
+    and no two rows of a step share (t, k)."""
+    o = oracle.Oracle(system, 0, lib)
+    model = R.PairModel()
+
+    def lm_of(i):
+        return R.lm(R.terms_to_dict(o.basis_poly(i)))
+
+    def agree():
+        got = {(int(a), int(b)) for a, b in o.pairs()}
+        assert len(got) == o.npairs(), "the oracle holds a pair twice"
+        assert got == model.B
+        assert [not bool(x) for x in o.redundant()] == model.in_g
+
+    for i in range(o.basis_size()):
+        model.insert(lm_of(i))
+    agree()
+    steps = 0
+    while steps < limit and model.B:
+        ng = o.basis_size()
+        degree, chosen = model.select()
+        assert o.step()
+        d = o.dump()
+        assert d.degree == degree
+        pair_rows = [(tuple(int(x) for x in t), int(k))
+                     for t, k, red in zip(d.row_t, d.row_k, d.row_reducer) if not red]
+        assert len(pair_rows) == len(set(pair_rows)), "equal pair rows were not collapsed"
+        assert set(pair_rows) == model.pair_rows(chosen)
+        all_rows = [(bytes(t), int(k)) for t, k in zip(d.row_t, d.row_k)]
+        assert len(all_rows) == len(set(all_rows))
+        for i in range(ng, o.basis_size()):
+            model.insert(lm_of(i))
+        agree()
+        steps += 1
+    if steps < limit:
+        assert not o.step()
+    return steps
+
+
+def _coprime_shadow_system():
+    """Leading monomials x2, x1*x2, x1 (grevlex) in that input order: when x1 arrives, its pair
+    with x2 is coprime and has the same lcm x1*x2 as its pair with x1*x2, so UPDATE's first loop
+    must keep the coprime pair long enough to shadow the other (Becker-Weispfenning), and the
+    product criterion then drops it: no pair of the third input survives."""
+    return synth._pack(3, 7, [[((0, 1, 0), 1), ((0, 0, 1), 3), ((0, 0, 0), 2)],
+                              [((1, 1, 0), 1), ((0, 0, 2), 5), ((1, 0, 0), 4), ((0, 0, 0), 1)],
+                              [((1, 0, 0), 1), ((0, 0, 1), 6), ((0, 0, 0), 3)],
+                              [((0, 0, 2), 1), ((0, 1, 0), 2), ((0, 0, 1), 1)]])
+
+
+PAIR_SYSTEMS = [_coprime_shadow_system(), synth.dense_n6(0), synth.dense_n6(1), synth.dense_system(4, 4, 7, 41),
+                synth.dense_system(5, 5, 65521, 4242),
+                synth.sparse_system(4, 4, 65521, 808, (5, 12), degree=3),
+                synth.sparse_system(5, 5, 2147483647, 3, (6, 12), degree=3),
+                synth.dense_system(3, 2, 65521, 5)] + \
+    [synth.sparse_system(3, 3, 7, seed, (2, 4)) for seed in (9007, 9011, 9111, 9116)]
+
+
+@pytest.mark.parametrize("system", PAIR_SYSTEMS, ids=lambda s: f"n{s['n']}m{s['m']}p{s['p']}")
+def test_pairs_follow_the_textbook_update_and_normal_selection(system):
+    assert check_pairs_replay(system) > 0
