@@ -197,14 +197,17 @@ gb_status gb_echelon_destroy(gb_echelon *ech);
    is changed).  stats may be NULL. */
 gb_status gb_f4_step(gb_system *sys, gb_step_stats *stats);
 
-/* F4 steps until no pair remains, then the reduced Groebner basis: redundant elements dropped,
-   tails fully reduced, monic, sorted by leading monomial descending.  The basis stays in the
+/* F4 steps until no pair remains, then the reduced Groebner basis of the ideal <f1..fm> in
+   F_p[x1..xn] under the system's term order (the problem statement of Sec. 1; the reduced basis
+   and Buchberger's criterion of Sec. 2.1; the F4 loop of Sec. 2.3 and Sec. 4.2): redundant
+   elements dropped, tails fully reduced, monic, sorted by leading monomial descending.  The basis stays in the
    context's device arena (held by the system) until gb_basis_export copies it out or the system
    is destroyed.  stats may be NULL. */
 gb_status gb_groebner(gb_system *sys, gb_run_stats *stats);
 
-/* The reduced basis after gb_groebner (reduced != 0), or the running basis in insertion order,
-   redundant elements included (reduced == 0).  Two-call pattern: with null arrays only npolys
+/* The reduced basis after gb_groebner (reduced != 0; the unique reduced Groebner basis of
+   Sec. 2.1, each element monic with the leading monomial first), or the running basis in
+   insertion order, redundant elements included (reduced == 0).  Two-call pattern: with null arrays only npolys
    and nterms are written; the terms then come from the device in one copy per array. */
 gb_status gb_basis_export(const gb_system *sys, int reduced, gb_polys_host *inout);
 /* Redundancy flags of the running basis (one byte per element; two-call pattern on *count). */
@@ -236,8 +239,9 @@ typedef struct {
    gb_batch_groebner) over the admitted systems, and between iterations admits queued systems into
    free slots while their summed device footprint estimate fits under the cap.  A submitted system
    thus joins the next iteration and a finished one leaves at once.  Ownership of a submitted
-   system moves to the server until it is returned by poll.  An iteration that fails finishes all
-   of its systems with its error status. */
+   system moves to the server until it is returned by poll; submitting a system the server still
+   holds (queued, running, or finished and not yet polled) gives GB_EINVAL.  An iteration that
+   fails finishes all of its systems with its error status. */
 gb_status gb_server_create(gb_ctx *ctx, const gb_server_opts *opts, gb_server **out);
 gb_status gb_server_submit(gb_server *srv, gb_system *sys, uint64_t *ticket);
 /* GB_OK and *done = the system when finished (ownership returns to the caller, with its status in
@@ -283,24 +287,35 @@ gb_status gb_matmul_modp(gb_ctx *ctx, uint32_t p, uint32_t m, uint32_t n, uint32
 #define GB_NOALLOC_MAX_PIVOTS 16384u  /* pivot rows */
 
 /* The sparse row reduction of gb_reduce_macaulay (D' only, no echelon form), for callers that
-   cannot allocate device memory: code recorded into a CUDA graph by stream capture, or a process
-   whose device memory belongs to another allocator that must not see new allocations between its
-   own calls.  This entry point allocates nothing: it works on the caller's buffers plus one
-   scratch array of about 2.3 MB that is part of the library image (each GPU that loads the
-   library holds it until the process exits).  It has no counterpart in the paper.
+   cannot allocate device memory.  Examples: a process whose device memory is owned by another
+   allocator (a framework's caching allocator, a fixed pool sized at start-up) that must not see
+   the device's free memory change behind its back between its own calls; or a host thread with a
+   latency budget that must not take the driver's allocation path.  This entry point allocates
+   nothing: it works on the caller's buffers plus one scratch array of about 2.3 MB that is part
+   of the library image (each GPU that loads the library holds it until the process exits).  It
+   has no counterpart in the paper.
    All pointers are DEVICE pointers on the current device:
      row_ptr[npivot + nnonpivot + 1], col_ind, val: CSR of the matrix, the npivot pivot rows first
        (row i monic with leading column pivot_cols[i], pivot_cols ascending), then the non-pivot
-       rows; columns ascending within a row, values in [0, p);
+       rows; columns ascending within a row and below ndict, values in [0, p); row_ptr must be
+       non-decreasing and col_ind / val must hold row_ptr[npivot + nnonpivot] entries;
      nonpivot_cols[nb]: the columns that are no pivot's leading column, ascending;
      dprime[nnonpivot * nb] (output): the non-pivot rows reduced by the pivot rows, restricted to
        nonpivot_cols -- the D' of gb_echelon_export.
    stream: a cudaStream_t of the current device (NULL: the legacy default stream).  The call only
-   enqueues work; it returns before the work finishes.
+   enqueues work; it returns before the work finishes.  The job description reaches the device
+   as a kernel parameter, so no host memory is read after the call returns.
+   The kernels check every index that becomes an address (row pointers non-decreasing, columns
+   ascending and below ndict, each pivot row opening at its pivot column, pivot and non-pivot
+   columns below ndict).  If one fails, nothing outside dprime and the scratch array is written
+   and every entry of dprime is set to 0xFFFFFFFF, which no residue mod p < 2^31 can be: test
+   dprime[0] after the stream has finished.
    The first call on each device looks up the scratch array's device address (no allocation); make
-   that first call before any stream capture.  Every call uses the same scratch array, so calls
-   whose work overlaps on the GPU (several streams, several host threads) race: serialise them.
-   GB_EINVAL: p not an odd prime below 2^31, or a size above the limits above. */
+   that first call before any stream capture.  Every call uses the same scratch array and leaves
+   its contents there; each call clears what it needs at zero.  Calls whose work overlaps on the
+   GPU (several streams, several host threads) race on that array: serialise them.
+   GB_EINVAL: p not an odd prime below 2^31, a size above the limits above, D' above 2^31 entries,
+   or a null pointer.  GB_EDEVICE: a launch was refused. */
 gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, uint32_t nnonpivot,
                                  uint32_t nb, const uint32_t *row_ptr, const uint32_t *col_ind,
                                  const uint32_t *val, const uint32_t *pivot_cols,

@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(RT, 6) k_reduce(const RedJob *__restrict__ job
     const Fp fp = J.fp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t i = blockIdx.x - bstart[jb], row = J.nA + i;
+    if (i >= J.nC) return;  // the whole block: a job emptied after a failed input check
     const uint32_t a0 = J.row_ptr[row], b0 = J.row_ptr[row + 1];
     const uint32_t base = a0 < b0 ? J.col[a0] : J.N, width = J.N - base;
     Acc *acc = SMEM ? reinterpret_cast<Acc *>(smem_raw)
@@ -1795,15 +1796,72 @@ void replace_tails(const std::vector<gb_echelon *> &Es, const std::vector<std::v
 // ---- the sparse reduction without device allocation --------------------------------------------
 //
 // Scratch of gb_reduce_rows_noalloc: pivot-column flags (one word per dictionary column), the
-// 32 x 32 chunk triangles (one per 32 pivot rows), the two work counters of k_reduce and its
-// one-job table, carved out of one fixed array that is part of the library image.  Host code
-// reaches it only through the address cudaGetSymbolAddress returns for the current device.
+// 32 x 32 chunk triangles (one per 32 pivot rows), the two work counters of k_reduce, an error
+// word and the one-job table, carved out of one fixed array that is part of the library image.
+// Host code reaches it only through the address cudaGetSymbolAddress returns for the current
+// device.
 constexpr uint32_t NA_COLPOS = 0;
 constexpr uint32_t NA_TRI = GB_NOALLOC_MAX_DICT;
 constexpr uint32_t NA_WORK = NA_TRI + GB_NOALLOC_MAX_PIVOTS * CW;  // even: 8-byte aligned
-constexpr uint32_t NA_TABLE = NA_WORK + 4;                           // 16-byte aligned
-constexpr uint32_t NA_WORDS = NA_TABLE + (uint32_t)((sizeof(RedJob) + 15) / 4) + 8;
+constexpr uint32_t NA_ERR = NA_WORK + 4;
+constexpr uint32_t NA_TABLE = NA_WORK + 8;                           // 16-byte aligned
+// the one-job table: the job, then the block-start tables {0, blocks} of its three launches
+struct NoallocTable {
+    RedJob job;
+    uint32_t tri_start[2], inv_start[2], red_start[2];
+};
+constexpr uint32_t NA_WORDS = NA_TABLE + (uint32_t)((sizeof(NoallocTable) + 15) / 4);
 static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
+
+// The caller's indices become shared- and scratch-memory addresses in the kernels below, so they
+// are checked first, a warp per row: row pointers non-decreasing, columns strictly ascending
+// within a row and below N, each pivot row opening at its pivot column, pivot columns strictly
+// ascending, non-pivot columns below N.  Any failure sets *err.
+__global__ void k_noalloc_check(uint32_t N, uint32_t nA, uint32_t nrows, uint32_t nb,
+                                const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
+                                const uint32_t *__restrict__ pcols, const uint32_t *__restrict__ nonpiv,
+                                uint32_t *__restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    bool bad = false;
+    for (uint32_t i = warp0; i < nrows; i += nwarps) {
+        const uint32_t a = row_ptr[i], b = row_ptr[i + 1];
+        if (b < a) { bad = true; continue; }  // the same on every lane
+        if (i < nA) {
+            const uint32_t pc = pcols[i];
+            bad |= pc >= N || a == b || (a < b && col[a] != pc) || (i > 0 && pcols[i - 1] >= pc);
+        }
+        for (uint32_t q = a + lane; q < b; q += 32) {
+            const uint32_t c = col[q];
+            bad |= c >= N || (q > a && col[q - 1] >= c);
+        }
+    }
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x)
+        bad |= nonpiv[j] >= N;
+    if (bad) atomicOr(err, 1u);
+}
+
+// the table arrives as a kernel parameter; after a failed check the job is empty (no pivot rows,
+// no rows, no output columns), so the shared kernels below touch nothing
+__global__ void k_noalloc_setup(NoallocTable tb, NoallocTable *__restrict__ dst, const uint32_t *__restrict__ err) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (*err) tb.job.nA = tb.job.nC = tb.job.nb = 0;
+        *dst = tb;
+    }
+}
+
+__global__ void k_noalloc_mark(uint32_t N, uint32_t nA, const uint32_t *__restrict__ pcols, uint32_t *__restrict__ colpos) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nA && pcols[k] < N) colpos[pcols[k]] = k | 0x80000000u;
+}
+
+// after a failed check D' reads 0xFFFFFFFF everywhere: never a residue of a prime below 2^31
+__global__ void k_noalloc_poison(size_t n, uint32_t *__restrict__ dprime, const uint32_t *__restrict__ err) {
+    if (!*err) return;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        dprime[t] = 0xFFFFFFFFu;
+}
 
 namespace {
 uint32_t *noalloc_scratch_for_current_device() {
@@ -1834,35 +1892,34 @@ void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint3
         fail(GB_EINVAL, "gb_reduce_rows_noalloc: ndict above " + std::to_string(max_dict) +
                             " or npivot above " + std::to_string(GB_NOALLOC_MAX_PIVOTS));
     if (nb > N || nA > N) fail(GB_EINVAL, "gb_reduce_rows_noalloc: more pivots or non-pivot columns than columns");
+    if (nC > (1u << 31) / (nb ? nb : 1)) fail(GB_EINVAL, "gb_reduce_rows_noalloc: D' above 2^31 entries");
     if (!nC || !nb) return;
     if (!row_ptr || !col || !val || (nA && !pcols) || !nonpiv || !dprime)
         fail(GB_EINVAL, "gb_reduce_rows_noalloc: null device pointer");
     uint32_t *scr = noalloc_scratch_for_current_device();
-    uint32_t *colpos = scr + NA_COLPOS, *tri = scr + NA_TRI;
+    uint32_t *colpos = scr + NA_COLPOS, *tri = scr + NA_TRI, *err = scr + NA_ERR;
     unsigned long long *work = reinterpret_cast<unsigned long long *>(scr + NA_WORK);
     const uint32_t nchunks = (nA + CW - 1) / CW;
     // the array keeps the previous call's contents: clear what the kernels expect at zero
     GB_CUDA(cudaMemsetAsync(colpos, 0, 4ull * N, st));
     if (nchunks) GB_CUDA(cudaMemsetAsync(tri, 0, 4ull * nchunks * CW * CW, st));
-    GB_CUDA(cudaMemsetAsync(work, 0, 16, st));
-    // the one-job table: job, then the two block-start tables {0, blocks}
-    struct Table {
-        RedJob job;
-        uint32_t tri_start[2], inv_start[2], red_start[2];
-    } tb{};
+    GB_CUDA(cudaMemsetAsync(work, 0, 20, st));  // both counters and the error word
+    NoallocTable tb{};
     tb.job = RedJob{row_ptr, col, val, pcols, colpos, nonpiv, tri, dprime, nullptr, nullptr, work, nA, nC, N, nb, fp};
     tb.tri_start[1] = blocks(nA, 8);
     tb.inv_start[1] = blocks(nchunks, IW);
     tb.red_start[1] = nC;
-    static_assert(sizeof(Table) <= 4 * (NA_WORDS - NA_TABLE), "scratch too small for the job table");
-    Table *dtb = reinterpret_cast<Table *>(scr + NA_TABLE);
-    GB_CUDA(cudaMemcpyAsync(dtb, &tb, sizeof(Table), cudaMemcpyHostToDevice, st));
+    NoallocTable *dtb = reinterpret_cast<NoallocTable *>(scr + NA_TABLE);
+    const uint32_t nrows = nA + nC;
+    k_noalloc_check<<<std::min<uint32_t>(blocks(nrows, 8), 148 * 8), 256, 0, st>>>(N, nA, nrows, nb, row_ptr, col,
+                                                                                  pcols, nonpiv, err);
+    k_noalloc_setup<<<1, 32, 0, st>>>(tb, dtb, err);
+    counted(2);
     if (nA) {
-        k_mark_pivot_cols<<<blocks(nA, 256), 256, 0, st>>>(nA, pcols, colpos);
-        counted();
+        k_noalloc_mark<<<blocks(nA, 256), 256, 0, st>>>(N, nA, pcols, colpos);
         k_build_chunk_tri<<<tb.tri_start[1], 256, 0, st>>>(&dtb->job, dtb->tri_start, 1);
         k_invert_chunk_tri<<<tb.inv_start[1], IW * 32, 0, st>>>(&dtb->job, dtb->inv_start, 1);
-        counted(2);
+        counted(3);
     }
     const size_t smem = (size_t)N * (mode == A32 ? 4 : 8);
     if (mode == A32) {
@@ -1872,9 +1929,9 @@ void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint3
         opt_in_smem(reinterpret_cast<const void *>(k_reduce<M64, true>));
         k_reduce<M64, true><<<nC, RT, smem, st>>>(&dtb->job, dtb->red_start, 1);
     }
-    counted();
-    // the table's host-to-device copy came from pageable memory, so the runtime staged it before
-    // returning: this stack frame may go away while the kernels run
+    const size_t nout = (size_t)nC * nb;
+    k_noalloc_poison<<<(uint32_t)std::min<size_t>((nout + 255) / 256, 148 * 8), 256, 0, st>>>(nout, dprime, err);
+    counted(2);  // like every launch group: a refused launch fails this call
 }
 
 }  // namespace gb

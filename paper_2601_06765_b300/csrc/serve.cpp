@@ -11,6 +11,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <unordered_map>
+#include <unordered_set>
 
 #include "internal.hpp"
 
@@ -29,6 +30,7 @@ struct gb_server {
     std::deque<std::pair<uint64_t, gb_system *>> queue;
     std::unordered_map<uint64_t, std::pair<gb_system *, gb_status>> done;
     std::unordered_map<uint64_t, bool> known;
+    std::unordered_set<const gb_system *> held;  // submitted and not yet polled back
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread scheduler;
@@ -167,6 +169,10 @@ gb_status gb_server_submit(gb_server *srv, gb_system *sys, uint64_t *ticket) {
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         if (srv->stop) return GB_EINVAL;
+        if (!srv->held.insert(sys).second) {  // already queued, running or finished unpolled
+            set_last_error("gb_server_submit: this system is already held by the server");
+            return GB_EINVAL;
+        }
         *ticket = srv->next_ticket++;
         srv->known[*ticket] = true;
         srv->queue.emplace_back(*ticket, sys);
@@ -183,6 +189,7 @@ gb_status gb_server_poll(gb_server *srv, uint64_t ticket, gb_system **done, gb_s
     if (it == srv->done.end()) return GB_EBUSY;
     *done = it->second.first;
     if (result) *result = it->second.second;
+    srv->held.erase(it->second.first);
     srv->done.erase(it);
     srv->known.erase(ticket);
     return GB_OK;
