@@ -321,6 +321,37 @@ gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, ui
                                  const uint32_t *val, const uint32_t *pivot_cols,
                                  const uint32_t *nonpivot_cols, uint32_t *dprime, void *stream);
 
+/* ---- the mod-p primitives, one at a time ------------------------------------------------------ */
+
+/* Each operation applies one of the device's F_p primitives elementwise: the same functions, with
+   the same precomputed constants, that the reduction kernels use.  It exists so that each
+   primitive can be checked on its own against plain integer arithmetic. */
+typedef enum {
+    GB_MODP_REDUCE64 = 0,  /* out = (a 2^32 + b) mod p: Barrett with k = 64 (Sec. 8.3), any 64-bit x */
+    GB_MODP_REDUCE32 = 1,  /* out = a mod p: Barrett with k = 32, p < 2^16, any 32-bit a */
+    GB_MODP_MULADD = 2,    /* out = (a b + c) mod p through the 64-bit Barrett step (Sec. 8.1) */
+    GB_MODP_REDC = 3,      /* out = redc(t), t = a 2^32 + b < p 2^32: t 2^-32 mod p, in [0, 2p)
+                              (Montgomery, R = 2^32, Sec. 8.4) */
+    GB_MODP_TO_MONT = 4,   /* out = a 2^32 mod p (the Montgomery domain of Sec. 8.4), a < p */
+    GB_MODP_MONT_MUL = 5,  /* out = redc((a 2^32 mod p) b): a b mod p, in [0, 2p) -- the product of
+                              the sparse update, multiplier in Montgomery form, entry standard */
+    GB_MODP_INV = 6,       /* out = a^-1 mod p (binary extended Euclid), 0 < a < p */
+    GB_MODP_INV_SMALL = 7, /* out = a^(p-2) mod p (Fermat), p < 2^16, 0 < a < p */
+    GB_MODP_LAZY32 = 8,    /* out[i] = (c[i] + sum_j (a b mod p)) mod p over a window of `window`
+                              terms a[i*window + j] b[i*window + j], summed in 32 bits without
+                              reduction between terms (the lazy window of Rem. 8.1), p < 2^16,
+                              window < 2^16, c[i] < p */
+    GB_MODP_LAZY_MONT = 9  /* the same with 64-bit sums of GB_MODP_MONT_MUL terms (each below 2p) */
+} gb_modp_op;
+
+/* Device pointers on the current device: a, b, c [n] (b and c only where the operation reads
+   them; for the two window operations a and b hold n * window values), out [n].  stream: a
+   cudaStream_t (NULL: the legacy default stream); the call only enqueues the work.
+   GB_EINVAL: p not an odd prime below 2^31, an unknown operation, a 16-bit-only operation with a
+   larger p, a window out of range, a null pointer the operation needs. */
+gb_status gb_modp_apply(gb_modp_op op, uint32_t p, uint64_t n, uint32_t window, const uint32_t *a,
+                        const uint32_t *b, const uint32_t *c, uint32_t *out, void *stream);
+
 /* ---- autotuning ----------------------------------------------------------------------------- */
 
 /* The reduction of a Macaulay matrix has interchangeable schedules that give the same D' and

@@ -28,6 +28,9 @@ GB_CTX_REDUCE_SPARSE = 2
 GB_CTX_REDUCE_DENSE = 4
 GB_CTX_NO_GRAPHS = 8
 GB_GREVLEX, GB_DEGLEX = 0, 1  # gb_order
+# gb_modp_op
+(GB_MODP_REDUCE64, GB_MODP_REDUCE32, GB_MODP_MULADD, GB_MODP_REDC, GB_MODP_TO_MONT, GB_MODP_MONT_MUL,
+ GB_MODP_INV, GB_MODP_INV_SMALL, GB_MODP_LAZY32, GB_MODP_LAZY_MONT) = range(10)
 _ORDERS = {"grevlex": GB_GREVLEX, "deglex": GB_DEGLEX}
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -139,6 +142,7 @@ _SIGS = {
     "gb_server_destroy": [_vp],
     "gb_server_stats_get": [_vp, ctypes.POINTER(gb_server_stats)],
     "gb_reduce_rows_noalloc": [ctypes.c_uint32] * 5 + [_vp] * 7,
+    "gb_modp_apply": [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32] + [_vp] * 5,
     "gb_matmul_modp": [_vp] + [ctypes.c_uint32] * 4 + [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp,
                                                        ctypes.c_uint64, ctypes.c_int],
 }
@@ -400,6 +404,13 @@ def gb_reduce_rows_noalloc(p: int, ndict: int, npivot: int, nnonpivot: int, nb: 
     check(lib().gb_reduce_rows_noalloc(p, ndict, npivot, nnonpivot, nb, row_ptr, col_ind, val,
                                        pivot_cols, nonpivot_cols, dprime, stream or None),
           "gb_reduce_rows_noalloc")
+
+
+def gb_modp_apply(op: int, p: int, n: int, window: int, a: int, b: int | None, c: int | None, out: int,
+                  stream: int | None = None) -> None:
+    """One device F_p primitive applied elementwise (integer device addresses; b and c may be None
+    where the operation does not read them).  See include/gb.h for the operations."""
+    check(lib().gb_modp_apply(op, p, n, window, a, b or None, c or None, out, stream or None), "gb_modp_apply")
 
 
 def gb_matmul_modp(ctx: int, p: int, m: int, n: int, k: int, A: int, lda: int, B: int, ldb: int, C: int,

@@ -7,6 +7,8 @@
 #include "internal.hpp"
 
 namespace gb {
+void modp_apply(int op, uint32_t p, uint64_t n, uint32_t window, const uint32_t *a, const uint32_t *b,
+                const uint32_t *c, uint32_t *out, cudaStream_t st);
 void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint32_t nb,
                          const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
                          const uint32_t *pcols, const uint32_t *nonpiv, uint32_t *dprime,
@@ -544,6 +546,14 @@ gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, ui
     GB_API_BEGIN
     reduce_rows_noalloc(p, ndict, npivot, nnonpivot, nb, row_ptr, col_ind, val, pivot_cols, nonpivot_cols,
                         dprime, static_cast<cudaStream_t>(stream));
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_modp_apply(gb_modp_op op, uint32_t p, uint64_t n, uint32_t window, const uint32_t *a,
+                        const uint32_t *b, const uint32_t *c, uint32_t *out, void *stream) {
+    GB_API_BEGIN
+    modp_apply((int)op, p, n, window, a, b, c, out, static_cast<cudaStream_t>(stream));
     return GB_OK;
     GB_API_END
 }

@@ -86,3 +86,41 @@ def test_matmul_add_and_pitches(ctx):
 def test_matmul_rejects_bad_prime(ctx):
     with pytest.raises(gb.GbError):
         gb.gb_matmul_modp(ctx.h, 65536, 1, 1, 1, 0, 1, 0, 1, 0, 1)
+
+
+def mulmod_rows_f64(A: np.ndarray, B: np.ndarray, p: int) -> np.ndarray:
+    """(A B) mod p exactly for k <= 2^11: the products of 16-bit halves summed over k stay below
+    2^43, which float64 holds exactly, so BLAS gives the exact integer sums."""
+    A = A.astype(np.int64)
+    B = B.astype(np.int64)
+    assert A.shape[1] <= 1 << 11
+    A0, A1 = (A & 0xFFFF).astype(np.float64), (A >> 16).astype(np.float64)
+    B0, B1 = (B & 0xFFFF).astype(np.float64), (B >> 16).astype(np.float64)
+    s16, s32 = (1 << 16) % p, (1 << 32) % p
+    q = lambda X, Y: (X @ Y).astype(np.int64) % p
+    r = q(A0, B0)
+    r = (r + q(A0, B1) * s16) % p
+    r = (r + q(A1, B0) * s16) % p
+    r = (r + q(A1, B1) * s32) % p
+    return r
+
+
+@pytest.mark.parametrize("p,k", [(P16, 1024), (P31, 512)])
+def test_matmul_at_the_benchmark_shape(ctx, p, k):
+    """The shapes the benchmark times (4096 x 8192, K = 1024 at p = 65521 and K = 512 at
+    p = 2^31 - 1: 4096 output tiles of 128 x 64 or 8192 of 128 x 32 over 148 SMs, so every CTA
+    takes many tiles and both accumulator sets), checked entry by entry on 320 full rows: 256 random ones plus the first and
+    last 32 (the first and last row tiles)."""
+    import torch
+    m, n = 4096, 8192
+    rng = np.random.default_rng(p + k)
+    A = rng.integers(0, p, size=(m, k), dtype=np.int64)
+    B = rng.integers(0, p, size=(k, n), dtype=np.int64)
+    C = rng.integers(0, p, size=(m, n), dtype=np.int64)
+    dA, dB, dC = (torch.from_numpy(X.astype(np.int32)).cuda() for X in (A, B, C))
+    torch.cuda.synchronize()
+    gb.gb_matmul_modp(ctx.h, p, m, n, k, dA.data_ptr(), k, dB.data_ptr(), n, dC.data_ptr(), n, True)
+    rows = np.unique(np.concatenate([rng.choice(m, 256, replace=False), np.arange(32), np.arange(m - 32, m)]))
+    got = dC[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.int64)
+    want = (C[rows] - mulmod_rows_f64(A[rows], B, p)) % p
+    assert np.array_equal(got, want), f"{np.count_nonzero(got != want)} entries differ"
