@@ -1,14 +1,16 @@
 """Benchmark: F4 over F_p on one B300 -- Macaulay nonzeros built and reduced per second.
 
-A step is one complete F4 run (every F4 step plus the final reduction) of the dense random
-quadratic system n=10, m=10 (all 66 monomials of degree <= 2), p=65521, grevlex, seeded, through
-the C ABI (gb_groebner).  value = sum of nnz(A) over the run's Macaulay matrices / run time.
+A step is one complete F4 run (every F4 step plus the final reduction) of the sparse random
+quadratic system n=13, m=13 (30 of the 105 monomials of degree <= 2 per polynomial), p=2^31-1,
+grevlex, seeded, through the C ABI (gb_groebner): the largest single-GPU configuration.
+value = sum of nnz(A) over the run's F4-step Macaulay matrices / run time (the final tail
+reduction's matrix is not counted, in every leg, since the oracle finishes by division).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the CPU oracle (plain C F4) on the host cores for the same workload.
-Under torchrun (N > 1) each rank runs its own replica of the workload (the single system does
-not shard) and rank 0 prints the aggregate.
+--impl reference times the CPU oracle (plain C F4) on the host cores on a bounded sample of the
+same workload.  Under torchrun (N > 1) each rank runs its own replica of the workload (the single
+system does not shard) and rank 0 prints the aggregate.
 """
 from __future__ import annotations
 
@@ -27,10 +29,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "F4 Macaulay nnz built+reduced per second (n=10 dense quadratic F4 run, exact)"
+METRIC = "F4 Macaulay nnz built+reduced per second (n=13 sparse quadratic F4 run, p=2^31-1, exact)"
 UNIT = "nnz/s"
-WORKLOAD = ("n=10, m=10 dense random quadratics (all 66 monomials of degree <= 2), p=65521, "
-            "grevlex, SplitMix64 seed 20260765; one full F4 run to the reduced basis per step")
+WORKLOAD = ("n=13, m=13 sparse random quadratics (30 of the 105 monomials of degree <= 2 each), "
+            "p=2^31-1, grevlex, SplitMix64 seed 20260765; one full F4 run to the reduced basis per step")
+WORKLOAD_N10 = ("n=10, m=10 dense random quadratics (all 66 monomials of degree <= 2), p=65521, "
+                "grevlex, SplitMix64 seed 20260765; one full F4 run to the reduced basis")
+CPU_SAMPLE_STEPS = 5   # the oracle's first 5 F4 steps of the n=13 run: about 30 s on one core
+REF_SAMPLE_STEPS = 4   # the reference arm's per-step sample: the first 4 F4 steps, about 3 s
 
 
 def peaks() -> dict:
@@ -38,8 +44,9 @@ def peaks() -> dict:
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
-    return {"hbm_gbs": 6400.0, "source": "fallback"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "source": "fallback"}
 
 
 def profile_traffic(kernel_tag: str):
@@ -117,7 +124,7 @@ def run_ours(args) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    system = synth.dense_n10(0)
+    system = synth.sparse_n13(0)
     ctx = gb.Context(device=local, arena_bytes=args.arena_gb << 30, graphs=not args.no_graphs)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 126 MB L2
 
@@ -127,7 +134,6 @@ def run_ours(args) -> None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # inputs resident on the device before the timed region: one system per step
     for _ in range(args.warmup):
         with gb.System(ctx, system) as S:
             S.groebner()
@@ -137,10 +143,13 @@ def run_ours(args) -> None:
         th = gb.gb_system_create(ctx.h, system)
         tune = gb.gb_autotune(ctx.h, [th])
         gb.gb_system_destroy(th)
+    # inputs resident on the host side of the library before the timed region: one system per
+    # step (system creation copies the terms; the first step uploads them in one staged copy)
     systems = [gb.System(ctx, system) for _ in range(args.steps)]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     runs = []
+    basis_len = None
     clocks = Clocks(local)
     launches0 = gb.gb_kernel_launches()
     graphs0 = gb.gb_graph_launches()
@@ -152,23 +161,23 @@ def run_ours(args) -> None:
         runs.append(S.groebner())
         ev[i][1].record()
         torch.cuda.synchronize()
+        if basis_len is None:
+            basis_len = len(S.basis())
+        S.close()  # the reduced basis leaves the arena before the next run
     barrier()
     launches = gb.gb_kernel_launches() - launches0
     graphs = gb.gb_graph_launches() - graphs0
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
-    basis = systems[0].basis()
-    for S in systems:
-        S.close()
     total_ms = sum(ms)
-    nnz = sum(r["nnz_total"] for r in runs)
+    nnz = sum(r["nnz_steps"] for r in runs)
     total_ms, nnz = shard.aggregate(total_ms, nnz)  # slowest rank, all ranks' nonzeros
     value = nnz / (total_ms / 1e3)
 
     # end to end through the C ABI: host arrays in, reduced basis out, copies inside the region
     e2e_ms = []
     d2h = 0
-    for _ in range(max(3, min(args.steps, 5))):
+    for _ in range(3):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -180,27 +189,33 @@ def run_ours(args) -> None:
         d2h = off.nbytes + ex.nbytes + cf.nbytes
     e2e_value = (nnz / len(runs) * (world if world > 1 else 1)) / (statistics.median(e2e_ms) / 1e3)
 
-    # roofline of the sparse row reduction (the dominant kernels, see profiles/): algorithmic
-    # bytes = 8 B per modular multiply-add (col_ind + val of a pivot-row entry read); time = the
-    # device time of its launches alone (CUDA events around them on the context's stream), summed
-    # over the timed runs.  k_reduce_rows runs the steps with more non-pivot rows than SMs, and its
-    # ncu capture gives the DRAM traffic per launch
-    r0 = runs[0]
+    # roofline of the dominant kernel of this workload, the tensor-core product k_mm of the dense
+    # blocked reduction (see profiles/): algorithmic work = 2 L^2 BF16 digit-product FLOPs per
+    # mod-p multiply-add; time = CUDA events around each of its launches on the context's stream,
+    # summed over the timed runs; peak = the sustained BF16 figure (the launches run inside a
+    # run of about a second)
     pk = peaks()
-    red_ms = sum(r["ms_reduce_kernel"] for r in runs)
-    alg_bytes = 8.0 * sum(r["axpy_fma"] for r in runs)
-    achieved = alg_bytes / (red_ms / 1e3) / 1e9 if red_ms > 0 else 0.0
-    roofline = {"kernel": "k_reduce_rows + k_reduce + k_reduce_cl (sparse row AXPY reduction, per F4 run)",
-                "bound": "hbm",
-                "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / pk["hbm_gbs"], 4),
-                "peak_source": f"{pk['source']} HBM copy bandwidth",
-                "traffic": profile_traffic("k_reduce_rows_dense_n10")}
+    mm_ms = sum(r["ms_mm"] for r in runs)
+    mm_flops = sum(r["mm_flops"] for r in runs)
+    mm_launches = sum(r["mm_launches"] for r in runs)
+    achieved = mm_flops / (mm_ms / 1e3) / 1e12 if mm_ms > 0 else 0.0
+    roofline = {"kernel": "k_mm<4> (exact mod-p product on the tensor cores: dense blocked reduction "
+                          "and RREF trailing updates of the n=13 run)",
+                "bound": "tensor", "achieved": round(achieved, 1), "peak": pk["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "frac": round(achieved / pk["bf16_tflops_sustained"], 4),
+                "peak_source": f"{pk['source']} BF16 dense, sustained",
+                "launches_timed": mm_launches // max(len(runs), 1),
+                "ms_per_run": round(mm_ms / max(len(runs), 1), 2),
+                "share_of_run": round(mm_ms / sum(ms), 4) if ms else None,
+                "units": "2 L^2 = 32 BF16 digit-product FLOPs per mod-p multiply-add (L = 4 digits, p = 2^31-1)",
+                "traffic": profile_traffic("k_mm_sparse_n13")}
 
+    n10 = measure_dense_n10(gb, synth, ctx, flush, pk, args) if rank == 0 and not args.no_batch else None
     batched = measure_batched(gb, synth, ctx, rank, world) if not args.no_batch else None
     served = measure_served(gb, synth, ctx) if rank == 0 and not args.no_batch else None
     tensor = measure_tensor_core(gb, local) if rank == 0 and not args.no_batch else None
-    big = measure_sparse_n13(gb, synth, local, pk, graphs=not args.no_graphs) if rank == 0 and not args.no_batch else None
+    n13 = measure_sparse_n13(gb, synth, local, pk, runs, graphs=not args.no_graphs) \
+        if rank == 0 and not args.no_batch else None
     deglex = None
     if rank == 0 and not args.no_batch:
         try:
@@ -208,21 +223,24 @@ def run_ours(args) -> None:
         except gb.GbError as e:  # reported in the line; the main measurement stands
             deglex = {"error": str(e)}
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
-             for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_rref", "ms_update", "ms_pairs", "ms_select",
-                       "ms_wall")}
+             for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_mm", "ms_rref", "ms_update", "ms_pairs",
+                       "ms_select", "ms_finish", "ms_wall")}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(system)
     if rank == 0:
+        r0 = runs[0]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 (F_p residues, exact)",
-            "data": "synthetic (seeded SplitMix64 dense random quadratics)",
+            "data": "synthetic (seeded SplitMix64 sparse random quadratics)",
             "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
-                       "l2": "flushed before every step (512 MiB write)",
-                       "f4_steps_per_run": r0["steps"], "nnz_per_run": r0["nnz_total"],
-                       "basis_elements": len(basis), "stage_ms_per_run": stage},
+                       "l2": "flushed before every step (512 MiB write); the run's matrices exceed L2",
+                       "f4_steps_per_run": r0["steps"], "nnz_per_run": r0["nnz_steps"],
+                       "nnz_note": "sum of nnz(A) over the F4 steps; the final tail-reduction matrix "
+                                   f"({r0['nnz_total'] - r0['nnz_steps']} nnz) is not counted",
+                       "basis_elements": basis_len, "stage_ms_per_run": stage},
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": statistics.median(e2e_ms),
                     "h2d_bytes_per_step": input_bytes(system), "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -230,10 +248,11 @@ def run_ours(args) -> None:
             "autotune": None if tune is None else {
                 **{k: (round(v, 1) if isinstance(v, float) else v) for k, v in tune.items()},
                 "note": "gb_autotune on this workload before the timed region; the timed runs use its table"},
+            "dense_n10": n10,
             "batched": batched,
             "served": served,
             "tensor_core": tensor,
-            "sparse_n13": big,
+            "sparse_n13": n13,
             "deglex": deglex,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -244,6 +263,53 @@ def run_ours(args) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def measure_dense_n10(gb, synth, ctx, flush, pk: dict, args) -> dict:
+    """The n=10 dense system (p = 65521): full F4 runs timed with CUDA events after an L2 flush,
+    and the sparse row reduction that dominates it (k_reduce_rows, k_reduce, k_reduce_cl) as
+    modular multiply-adds per second and as an effective operand bandwidth (8 B per multiply-add:
+    the pivot-row entry's column and value).  The pivot rows are L2-resident (profiles/), so that
+    bandwidth is an L2-side figure, not an HBM one; the kernel is issue-bound."""
+    import torch
+    system = synth.dense_n10(0)
+    for _ in range(2):
+        with gb.System(ctx, system) as S:
+            S.groebner()
+    th = gb.gb_system_create(ctx.h, system)
+    gb.gb_autotune(ctx.h, [th])
+    gb.gb_system_destroy(th)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs, ms = [], []
+    for _ in range(max(5, args.steps)):
+        S = gb.System(ctx, system)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        runs.append(S.groebner())
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        S.close()
+    nnz = sum(r["nnz_steps"] for r in runs)
+    red_ms = sum(r["ms_reduce_kernel"] for r in runs)
+    fma = sum(r["axpy_fma"] for r in runs)
+    eff = 8.0 * fma / (red_ms / 1e3) / 1e9 if red_ms > 0 else 0.0
+    stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
+             for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_rref", "ms_update", "ms_pairs", "ms_select",
+                       "ms_finish")}
+    return {"workload": WORKLOAD_N10, "runs": len(runs), "ms_per_run": round(sum(ms) / len(ms), 3),
+            "nnz_per_run": runs[0]["nnz_steps"], "nnz_per_s": nnz / (sum(ms) / 1e3),
+            "stage_ms_per_run": stage,
+            "sparse_reduction": {
+                "kernels": "k_reduce_rows + k_reduce + k_reduce_cl",
+                "ms_per_run": round(red_ms / len(runs), 3),
+                "modp_fma_per_run": fma // len(runs),
+                "modp_fma_per_s": fma / (red_ms / 1e3) if red_ms > 0 else None,
+                "effective_operand_gbs": round(eff, 1),
+                "effective_frac_of_hbm": round(eff / pk["hbm_gbs"], 4),
+                "bound": "issue / L2 latency (operands L2-resident; profiles/k_reduce_rows_dense_n10.md)",
+                "traffic": profile_traffic("k_reduce_rows_dense_n10")}}
 
 
 def _plain_vs_batched(gb, ctx, systems, rank: int = 0, world: int = 1) -> dict:
@@ -383,21 +449,17 @@ def measure_tensor_core(gb, local: int) -> list:
     return out
 
 
-def measure_sparse_n13(gb, synth, local: int, pk: dict, graphs: bool = True) -> dict:
-    """One F4 run of the n=13 sparse 31-bit system (the large-matrix workload) with the reduction
-    chosen per matrix by the shape rules (dense tensor-core blocks for the large steps), with the
-    sparse reduction only, and with the schedules gb_autotune measured on this system (its three
-    tuning runs are not in the timed run); and the symbolic preprocessing bandwidth of its largest step (algorithmic bytes: col_ind +
-    val written per nonzero, row_ptr, and the dictionary monomials)."""
+def measure_sparse_n13(gb, synth, local: int, pk: dict, timed_runs=None, graphs: bool = True) -> dict:
+    """The headline n=13 system once more, step by step, in two fresh contexts: with the reduction
+    chosen per matrix by the shape rules (dense tensor-core blocks for the large steps), and with
+    the sparse reduction only; plus the symbolic-preprocessing bandwidth of its largest step
+    (algorithmic bytes: col_ind + val written per nonzero, row_ptr, and the dictionary monomials)
+    and the per-step stage times."""
     system = synth.sparse_n13(0)
     res = {"workload": "n=13, m=13 quadratics with 30 of the 105 monomials of degree <= 2, p=2^31-1, grevlex, "
-                       "SplitMix64 seed 20260765; one full F4 run"}
-    for mode in ("auto", "sparse", "tuned"):
-        ctx = gb.Context(device=local, arena_bytes=48 << 30, reduce="auto" if mode == "tuned" else mode, graphs=graphs)
-        if mode == "tuned":
-            th = gb.gb_system_create(ctx.h, system)
-            res["autotune"] = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in gb.gb_autotune(ctx.h, [th]).items()}
-            gb.gb_system_destroy(th)
+                       "SplitMix64 seed 20260765; one full F4 run (wall clock, step by step)"}
+    for mode in ("auto", "sparse"):
+        ctx = gb.Context(device=local, arena_bytes=48 << 30, reduce=mode, graphs=graphs)
         S = gb.System(ctx, system)
         t0 = time.perf_counter()
         steps = []
@@ -413,16 +475,22 @@ def measure_sparse_n13(gb, synth, local: int, pk: dict, graphs: bool = True) -> 
         nnz = sum(x["nnz"] for x in steps)
         res[mode] = {"ms": round(wall * 1e3, 1), "nnz_per_s": nnz / wall,
                      "ms_reduce": round(sum(x["ms_reduce"] for x in steps), 1),
-                     "ms_rref": round(sum(x["ms_rref"] for x in steps), 1)}
+                     "ms_mm": round(sum(x["ms_mm"] for x in steps), 1),
+                     "ms_rref": round(sum(x["ms_rref"] for x in steps), 1),
+                     "ms_sp": round(sum(x["ms_sp"] for x in steps), 1)}
         if mode == "auto":
             top = max(steps, key=lambda x: x["nnz"])
             alg = 8.0 * top["nnz"] + 4.0 * (top["nrows"] + 1) + 16.0 * top["ndict"]
             gbs = alg / (top["ms_sp"] / 1e3) / 1e9
-            res["sp_largest_step"] = {"step": top["step"], "nnz": top["nnz"], "ms_sp": round(top["ms_sp"], 3),
+            res["sp_largest_step"] = {"step": top["step"], "nnz": top["nnz"], "ndict": top["ndict"],
+                                      "nrows": top["nrows"], "ms_sp": round(top["ms_sp"], 3),
                                       "algorithmic_bytes": alg, "achieved_gbs": round(gbs, 1),
                                       "peak_gbs": pk["hbm_gbs"], "frac": round(gbs / pk["hbm_gbs"], 4)}
+            res["steps"] = [{k: (round(x[k], 3) if isinstance(x[k], float) else x[k])
+                             for k in ("step", "degree", "nrows", "ndict", "npivot", "nC", "nb", "rank", "nnz",
+                                       "ms_sp", "ms_reduce", "ms_mm", "ms_rref", "ms_pairs", "ms_select")}
+                            for x in steps]
     res["speedup_auto_vs_sparse"] = round(res["sparse"]["ms"] / res["auto"]["ms"], 3)
-    res["speedup_tuned_vs_auto"] = round(res["auto"]["ms"] / res["tuned"]["ms"], 3)
     return res
 
 
@@ -459,51 +527,50 @@ def measure_deglex(gb, synth, ctx) -> dict:
             "basis_elements": nb}
 
 
-def cpu_baseline(system: dict) -> dict:
-    """The oracle as it stands, single-threaded, on one full F4 run of the workload (~10-30 s)."""
+def _oracle_sample(system: dict, steps: int) -> int:
+    """The oracle as it stands on the first `steps` F4 steps of the workload: sum of nnz(A)."""
     import oracle
     o = oracle.Oracle(system)
-    t0 = time.perf_counter()
     nnz = 0
-    while o.step():
+    for _ in range(steps):
+        if not o.step():
+            break
         nnz += o.stats()["nnz"]
-    o.finish()
+    return nnz
+
+
+def cpu_baseline(system: dict) -> dict:
+    """The oracle, single-threaded, on a bounded sample of the workload: its first
+    CPU_SAMPLE_STEPS F4 steps (the later steps of the n=13 run take the oracle minutes to hours)."""
+    t0 = time.perf_counter()
+    nnz = _oracle_sample(system, CPU_SAMPLE_STEPS)
     dt = time.perf_counter() - t0
     return {"value": nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one complete F4 run of the workload ({nnz} nnz, {dt:.1f} s, final "
-                      f"reduction by division not counted in nnz)"}
+            "sample": f"the first {CPU_SAMPLE_STEPS} F4 steps of the n=13 run ({nnz} nnz of Macaulay "
+                      f"matrices, {dt:.1f} s)"}
 
 
 def run_reference(args) -> None:
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    import oracle
     from paper_2601_06765_b300 import synth
-    system = synth.dense_n10(0)
-    # each step: a bounded sample of the workload -- the first 6 F4 steps of the run (~5 s)
-    def sample():
-        o = oracle.Oracle(system)
-        nnz = 0
-        for _ in range(6):
-            if not o.step():
-                break
-            nnz += o.stats()["nnz"]
-        return nnz
+    system = synth.sparse_n13(0)
     for _ in range(args.warmup):
-        sample()
+        _oracle_sample(system, REF_SAMPLE_STEPS)
     t0 = time.perf_counter()
-    nnz = sum(sample() for _ in range(args.steps))
+    nnz = sum(_oracle_sample(system, REF_SAMPLE_STEPS) for _ in range(args.steps))
     dt = time.perf_counter() - t0
     value = nnz / dt
+    sample = f"the first {REF_SAMPLE_STEPS} F4 steps of the n=13 run per step"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 (F_p residues, exact)", "data": "synthetic (seeded SplitMix64)",
-        "config": {"workload": WORKLOAD, "parallelism": "CPU oracle, 1 thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "first 6 F4 steps of the workload per step"},
+        "config": {"workload": WORKLOAD.replace("one full F4 run to the reduced basis per step", sample),
+                   "parallelism": "CPU oracle, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -511,7 +578,7 @@ def run_reference(args) -> None:
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -520,8 +587,8 @@ def main() -> None:
                     help="launch the RREF rounds from the host (GB_CTX_NO_GRAPHS): complete ncu launch lists")
     ap.add_argument("--no-tune", action="store_true",
                     help="run the workload on the shape rules, without gb_autotune before the timed region")
-    ap.add_argument("--arena-gb", type=int, default=32, help="device arena of the context (GiB)")
-    ap.add_argument("--only", choices=["tensor", "sparse_n13"], default=None,
+    ap.add_argument("--arena-gb", type=int, default=48, help="device arena of the context (GiB)")
+    ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10"], default=None,
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
@@ -532,6 +599,11 @@ def main() -> None:
         torch.cuda.set_device(0)
         if args.only == "tensor":
             print(json.dumps({"tensor_core": measure_tensor_core(gb, 0)}))
+        elif args.only == "dense_n10":
+            ctx = gb.Context(device=0, arena_bytes=4 << 30, graphs=not args.no_graphs)
+            flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda:0")
+            print(json.dumps({"dense_n10": measure_dense_n10(gb, synth, ctx, flush, peaks(), args)}))
+            ctx.close()
         else:
             print(json.dumps({"sparse_n13": measure_sparse_n13(gb, synth, 0, peaks(), graphs=not args.no_graphs)}))
     elif args.impl == "reference":

@@ -139,6 +139,12 @@ typedef struct {
     float ms_reduce_kernel; /* device time of the row-reduction kernel launches alone (a part of
                                ms_reduce, which also covers their setup) */
     double ms_wall;    /* host wall time of the step */
+    double ms_mm;      /* device time of the tensor-core product launches (the dense blocked
+                          reduction and RREF updates), CUDA events around each launch made outside
+                          a CUDA graph; for a batch, the whole batch's */
+    double mm_flops;   /* BF16 digit-product FLOPs of those launches: 2 L^2 per mod-p multiply-add
+                          (L = 2 digits for p < 2^16, 4 otherwise) */
+    uint64_t mm_launches; /* the launches ms_mm covers */
 } gb_step_stats;
 
 typedef struct {
@@ -148,6 +154,10 @@ typedef struct {
     double ms_sp, ms_reduce, ms_rref, ms_update, ms_pairs, ms_select, ms_wall;
     double ms_reduce_kernel;
     double ms_finish;  /* wall time of the final minimalisation and tail reduction */
+    uint64_t nnz_steps; /* sum of nnz(A) over the F4 steps only (nnz_total also counts the matrix
+                           of the final tail reduction) */
+    double ms_mm, mm_flops;  /* as in gb_step_stats, summed over the run */
+    uint64_t mm_launches;
 } gb_run_stats;
 
 /* ---- context -------------------------------------------------------------------------------- */

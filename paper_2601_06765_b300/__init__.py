@@ -72,7 +72,8 @@ class gb_step_stats(ctypes.Structure):
                 ("ms_sp", ctypes.c_float), ("ms_reduce", ctypes.c_float),
                 ("ms_rref", ctypes.c_float), ("ms_update", ctypes.c_float), ("ms_pairs", ctypes.c_float),
                 ("ms_select", ctypes.c_float), ("ms_reduce_kernel", ctypes.c_float),
-                ("ms_wall", ctypes.c_double)]
+                ("ms_wall", ctypes.c_double), ("ms_mm", ctypes.c_double), ("mm_flops", ctypes.c_double),
+                ("mm_launches", ctypes.c_uint64)]
 
 
 class gb_run_stats(ctypes.Structure):
@@ -81,7 +82,9 @@ class gb_run_stats(ctypes.Structure):
                 ("ms_sp", ctypes.c_double), ("ms_reduce", ctypes.c_double), ("ms_rref", ctypes.c_double),
                 ("ms_update", ctypes.c_double), ("ms_pairs", ctypes.c_double),
                 ("ms_select", ctypes.c_double), ("ms_wall", ctypes.c_double),
-                ("ms_reduce_kernel", ctypes.c_double), ("ms_finish", ctypes.c_double)]
+                ("ms_reduce_kernel", ctypes.c_double), ("ms_finish", ctypes.c_double),
+                ("nnz_steps", ctypes.c_uint64), ("ms_mm", ctypes.c_double), ("mm_flops", ctypes.c_double),
+                ("mm_launches", ctypes.c_uint64)]
 
 
 class gb_server_stats(ctypes.Structure):

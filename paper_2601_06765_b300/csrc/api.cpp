@@ -276,6 +276,7 @@ gb_status gb_ctx_destroy(gb_ctx *ctx) {
     if (ctx->stage) cudaFreeHost(ctx->stage);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->mm_ev) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
     delete ctx;

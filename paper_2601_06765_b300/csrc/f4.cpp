@@ -642,8 +642,15 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
         st.ms_pairs = (float)ms_between(tp, t2);
         st.ms_select = (float)ms_between(t0, ts);
         st.ms_wall = ms_between(t0, t2);
+        st.ms_mm = ech->ms_mm;
+        st.mm_flops = ech->mm_flops;
+        st.mm_launches = ech->mm_launches;
         S->run.steps = S->steps;
         S->run.nnz_total += st.nnz;
+        S->run.nnz_steps += st.nnz;
+        S->run.ms_mm += st.ms_mm;
+        S->run.mm_flops += st.mm_flops;
+        S->run.mm_launches += st.mm_launches;
         S->run.axpy_rows += st.axpy_rows;
         S->run.axpy_fma += st.axpy_fma;
         S->run.ms_sp += st.ms_sp;
@@ -737,6 +744,9 @@ void finish_batch(const std::vector<gb_system *> &Ss) {
             S->run.ms_reduce += Ep[k]->ms_reduce;
             S->run.ms_reduce_kernel += Ep[k]->ms_reduce_kernel;
             S->run.nnz_total += Ms[k]->nnz;
+            S->run.ms_mm += Ep[k]->ms_mm;
+            S->run.mm_flops += Ep[k]->mm_flops;
+            S->run.mm_launches += Ep[k]->mm_launches;
             S->run.axpy_rows += Ep[k]->work[0];
             S->run.axpy_fma += Ep[k]->work[1];
         }

@@ -256,6 +256,7 @@ struct gb_ctx {
     uint32_t flags = 0;
     gb::Arena arena;
     cudaEvent_t ev[8] = {};         // stage timing of the batch in flight
+    std::vector<cudaEvent_t> mm_ev; // pairs around the tensor-core launches of one reduction
     void *stage = nullptr;          // page-locked staging of the batch in flight
     size_t stage_bytes = 0;
     size_t stage_off = 0;           // bump offset, back to 0 at every ctx_sync
@@ -296,6 +297,8 @@ struct gb_echelon {
     gb::DBuf<uint32_t> rpiv;    // rank pivot positions (ascending)
     uint64_t work[2] = {0, 0};  // pivot-row applications, mod-p multiply-adds of the reduction
     float ms_reduce = 0.f, ms_rref = 0.f, ms_reduce_kernel = 0.f;
+    double ms_mm = 0.0, mm_flops = 0.0;  // tensor-core product launches (MmTimer)
+    uint64_t mm_launches = 0;
 };
 
 struct gb_system {
@@ -409,6 +412,18 @@ void to_digits(const uint32_t *src, uint64_t rs, uint64_t ks, const DigitPlanes 
 // tensor cores (mm.cu), with A and B^T given by digit planes and C (crows x ccols, row pitch ldc,
 // 16-byte aligned, ldc a multiple of 4) by TMA.  The tensor maps are encoded once per plan; each
 // update's region ends the C tensor on the right and bottom.  err collects device error flags.
+// Device time of the tensor-core product launches of one reduction: while a reduction runs on
+// this thread, MmPlan::update records a pair of the context's events around each launch made
+// outside graph capture; the reduction reads them after its stream synchronises.
+struct MmTimer {
+    gb_ctx *ctx = nullptr;
+    size_t used = 0;  // events taken from ctx->mm_ev (two per launch)
+    double flops = 0.0;
+    uint64_t launches = 0;
+    double elapsed_ms() const;  // after the stream has synchronised
+};
+extern thread_local MmTimer *t_mm_timer;
+
 struct MmPlan {
     MmPlan(const DigitPlanes &A, const DigitPlanes &B, uint32_t *C, uint64_t ldc, uint32_t crows, uint32_t ccols,
            const Fp &fp);

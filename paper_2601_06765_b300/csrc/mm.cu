@@ -678,6 +678,21 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
     P.sub = sub ? 1 : 0;
     P.err = err;
     const unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)sm_count());
+    MmTimer *T = t_capturing ? nullptr : t_mm_timer;
+    cudaEvent_t e1 = nullptr;
+    if (T) {
+        std::vector<cudaEvent_t> &pool = T->ctx->mm_ev;
+        while (pool.size() < T->used + 2) {
+            cudaEvent_t e;
+            GB_CUDA(cudaEventCreate(&e));
+            pool.push_back(e);
+        }
+        GB_CUDA(cudaEventRecord(pool[T->used], st));
+        e1 = pool[T->used + 1];
+        T->used += 2;
+        T->flops += 2.0 * A->L * A->L * (double)M * N * K;
+        T->launches++;
+    }
     if (A->L == 2) {
         opt_in_smem(reinterpret_cast<const void *>(k_mm<2>));
         k_mm<2><<<grid, MM_THREADS, MmCfg<2>::SMEM, st>>>(maps->ta, maps->tb, maps->tc, P);
@@ -686,6 +701,19 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
         k_mm<4><<<grid, MM_THREADS, MmCfg<4>::SMEM, st>>>(maps->ta, maps->tb, maps->tc, P);
     }
     counted();
+    if (e1) GB_CUDA(cudaEventRecord(e1, st));
+}
+
+thread_local MmTimer *t_mm_timer = nullptr;
+
+double MmTimer::elapsed_ms() const {
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < used; i += 2) {
+        float x = 0.f;
+        GB_CUDA(cudaEventElapsedTime(&x, ctx->mm_ev[i], ctx->mm_ev[i + 1]));
+        ms += x;
+    }
+    return ms;
 }
 
 }  // namespace gb

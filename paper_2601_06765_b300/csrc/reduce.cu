@@ -1264,6 +1264,13 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
     Arena &ar = ctx->arena;
     cudaStream_t st = ctx->stream;
     const int nj = (int)Ms.size();
+    MmTimer mm_timer;
+    mm_timer.ctx = ctx;
+    struct TimerScope {
+        MmTimer *prev;
+        explicit TimerScope(MmTimer *t) : prev(t_mm_timer) { t_mm_timer = t; }
+        ~TimerScope() { t_mm_timer = prev; }
+    } mm_scope(&mm_timer);
     GB_CUDA(cudaEventRecord(ctx->ev[2], st));
     DBuf<unsigned long long> work;
     work.alloc(ar, 2ull * nj, st);
@@ -1598,7 +1605,11 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
     GB_CUDA(cudaEventElapsedTime(&ms_red, ctx->ev[2], ctx->ev[3]));
     GB_CUDA(cudaEventElapsedTime(&ms_kern, ctx->ev[5], ctx->ev[3]));
     GB_CUDA(cudaEventElapsedTime(&ms_rref, ctx->ev[3], ctx->ev[4]));
+    const double ms_mm = mm_timer.elapsed_ms();
     for (int j = 0; j < nj; ++j) {
+        Es[j]->ms_mm = ms_mm;
+        Es[j]->mm_flops = mm_timer.flops;
+        Es[j]->mm_launches = mm_timer.launches;
         Es[j]->work[0] = hw[2 * j];
         Es[j]->work[1] = hw[2 * j + 1];
         Es[j]->ms_reduce = ms_red;

@@ -1,4 +1,4 @@
-"""bench.py's reference arm on the CPU: the oracle timed on a bounded sample of the n=10 workload,
+"""bench.py's reference arm on the CPU: the oracle timed on a bounded sample of the n=13 workload,
 printed as one JSON line with the contract's keys; under a launcher every rank but 0 exits at once
 without work."""
 from __future__ import annotations
