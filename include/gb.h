@@ -76,7 +76,11 @@ typedef struct {
                             RREF(D');
                             GB_CTX_NO_GRAPHS: launch the rounds of the echelon form of D' one
                             by one from the host instead of as one CUDA graph whose loop runs
-                            on the device (same results). */
+                            on the device (same results);
+                            GB_CTX_SP_RANKS: symbolic preprocessing keys every term by its dense
+                            rank in a bitmap (the exact path the hash dictionary falls back to
+                            when two monomials share a hash key) instead of the hash dictionary
+                            (same results). */
     uint32_t reserved;
 } gb_ctx_opts;
 
@@ -84,6 +88,7 @@ typedef struct {
 #define GB_CTX_REDUCE_SPARSE 2u
 #define GB_CTX_REDUCE_DENSE 4u
 #define GB_CTX_NO_GRAPHS 8u
+#define GB_CTX_SP_RANKS 16u
 
 /* A polynomial system on the host: polynomial i has the terms [poly_off[i], poly_off[i+1]). */
 typedef struct {
@@ -126,7 +131,10 @@ typedef struct {
 
 typedef struct {
     uint32_t step, degree, npairs, nrows, ndict, npivot, nC, nb, rank, nbasis;
-    uint32_t closure_rounds, reserved;
+    uint32_t closure_rounds;
+    uint32_t sp_redo;    /* times the step's symbolic preprocessing ran again: its hash dictionary
+                            needed more slots, or two monomials shared a hash key (then the exact
+                            rank path built it) */
     uint64_t nnz;
     uint64_t axpy_rows;  /* pivot rows applied by the sparse reduction (eq. 8.1 row updates) */
     uint64_t axpy_fma;   /* modular multiply-adds a <- a + b c of the sparse reduction */
@@ -330,6 +338,41 @@ gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, ui
                                  uint32_t nb, const uint32_t *row_ptr, const uint32_t *col_ind,
                                  const uint32_t *val, const uint32_t *pivot_cols,
                                  const uint32_t *nonpivot_cols, uint32_t *dprime, void *stream);
+
+/* ---- kernel vectors by the block Wiedemann method ---------------------------------------------- */
+
+typedef struct {
+    uint32_t b, d, nterms;       /* block width, Hankel blocks d = ceil(r / b) + 1, sequence terms 2d */
+    uint32_t hankel_rank;        /* rank of the block Hankel matrix */
+    uint32_t free_columns;       /* its free columns: the generator vectors tried */
+    uint32_t found;              /* dimension of the span of the vectors found (rows of W) */
+    uint32_t verified;           /* rows w of W with w^T A = 0 checked on the device */
+    uint32_t reserved;
+    uint64_t spmm_products;      /* mod-p multiply-adds of the sparse products (32 lanes per entry) */
+    double ms_sequence, ms_hankel, ms_vectors, ms_total;  /* device time of the stages */
+} gb_krylov_stats;
+
+/* Relations among the rows of one step's Macaulay matrix A (r rows, N columns): vectors v with
+   v^T A = 0, i.e. sum_i v_i t_i g_{k_i} = 0 (Prop. 3.2), by the block Wiedemann method of
+   Sec. 9.3 (the Krylov alternative to elimination, Sec. 13.4): with M = A diag(delta) A^T, the
+   sequence S_i = X^T M^(i+1) Z (i < 2d, d = ceil(r / b) + 1) is computed with sparse products
+   of A and A^T with blocks of b vectors; the right kernel of the block Hankel matrix
+   H[i b + a][j b + c] = S_{i+j}[a][c] (i < d, j <= d) gives, one vector c per free column of
+   RREF(H), y(c) = sum_j M^j Z c_j in ker M; W is the reduced row echelon form of the y(c).
+   With random X, Z, delta, W spans min(b, dim ker A^T) dimensions of the left kernel.
+   mac: a matrix from gb_symbolic_preprocess or gb_system_last_step (not modified).
+   b: block width, 1..32.  X, Z: HOST arrays r x b row-major, entries in [0, p); delta: HOST N
+   entries in [1, p); all copied at the call (the caller draws them: they are the method's random
+   choices).  seq (HOST, may be NULL): 2d x b x b, the sequence S_i row-major.  W (HOST, may be
+   NULL): wcap x r, the first min(wcap, found) rows of W.  stats (may be NULL).  Runs on the
+   context's stream; returns when done.
+   GB_EINVAL: null handle or input, b out of range, an entry out of range, an empty matrix.
+   GB_ENOMEM: the arena cannot hold the block Hankel system (about 3 (d b)^2 4-byte words) and its
+   work.  GB_EUNSUPPORTED: a Hankel system above 2^34 entries.  GB_ETIMEOUT: a bounded device
+   wait gave up. */
+gb_status gb_block_wiedemann(const gb_macaulay *mac, uint32_t b, const uint32_t *X, const uint32_t *Z,
+                             const uint32_t *delta, uint32_t *seq, uint32_t *W, uint32_t wcap,
+                             gb_krylov_stats *stats);
 
 /* ---- the mod-p primitives, one at a time ------------------------------------------------------ */
 

@@ -27,6 +27,7 @@ GB_CTX_KEEP_STEP = 1
 GB_CTX_REDUCE_SPARSE = 2
 GB_CTX_REDUCE_DENSE = 4
 GB_CTX_NO_GRAPHS = 8
+GB_CTX_SP_RANKS = 16
 GB_GREVLEX, GB_DEGLEX = 0, 1  # gb_order
 # gb_modp_op
 (GB_MODP_REDUCE64, GB_MODP_REDUCE32, GB_MODP_MULADD, GB_MODP_REDC, GB_MODP_TO_MONT, GB_MODP_MONT_MUL,
@@ -67,7 +68,7 @@ class gb_echelon_host(ctypes.Structure):
 class gb_step_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint32) for f in ("step", "degree", "npairs", "nrows", "ndict", "npivot",
                                                 "nC", "nb", "rank", "nbasis", "closure_rounds",
-                                                "reserved")] + \
+                                                "sp_redo")] + \
                [("nnz", ctypes.c_uint64), ("axpy_rows", ctypes.c_uint64), ("axpy_fma", ctypes.c_uint64),
                 ("ms_sp", ctypes.c_float), ("ms_reduce", ctypes.c_float),
                 ("ms_rref", ctypes.c_float), ("ms_update", ctypes.c_float), ("ms_pairs", ctypes.c_float),
@@ -85,6 +86,13 @@ class gb_run_stats(ctypes.Structure):
                 ("ms_reduce_kernel", ctypes.c_double), ("ms_finish", ctypes.c_double),
                 ("nnz_steps", ctypes.c_uint64), ("ms_mm", ctypes.c_double), ("mm_flops", ctypes.c_double),
                 ("mm_launches", ctypes.c_uint64)]
+
+
+class gb_krylov_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint32) for f in ("b", "d", "nterms", "hankel_rank", "free_columns", "found",
+                                                "verified", "reserved")] + \
+               [("spmm_products", ctypes.c_uint64), ("ms_sequence", ctypes.c_double),
+                ("ms_hankel", ctypes.c_double), ("ms_vectors", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
 
 class gb_server_stats(ctypes.Structure):
@@ -146,6 +154,8 @@ _SIGS = {
     "gb_server_stats_get": [_vp, ctypes.POINTER(gb_server_stats)],
     "gb_reduce_rows_noalloc": [ctypes.c_uint32] * 5 + [_vp] * 7,
     "gb_modp_apply": [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32] + [_vp] * 5,
+    "gb_block_wiedemann": [_vp, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p, _u32p, ctypes.c_uint32,
+                           ctypes.POINTER(gb_krylov_stats)],
     "gb_matmul_modp": [_vp] + [ctypes.c_uint32] * 4 + [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp,
                                                        ctypes.c_uint64, ctypes.c_int],
 }
@@ -409,6 +419,29 @@ def gb_reduce_rows_noalloc(p: int, ndict: int, npivot: int, nnonpivot: int, nb: 
           "gb_reduce_rows_noalloc")
 
 
+def gb_block_wiedemann(mac: int, b: int, X: np.ndarray, Z: np.ndarray, delta: np.ndarray,
+                       want_seq: bool = True, wcap: int | None = None) -> dict:
+    """Left kernel vectors of a Macaulay matrix handle by the block Wiedemann method (Sec. 9.3):
+    X, Z (r x b) and delta (N) are the caller's random choices.  Returns the stats, the
+    sequence (2d x b x b) and W (found x r).  See include/gb.h."""
+    X = np.ascontiguousarray(X, dtype=np.uint32)
+    Z = np.ascontiguousarray(Z, dtype=np.uint32)
+    delta = np.ascontiguousarray(delta, dtype=np.uint32)
+    r = X.shape[0]
+    d = (r + b - 1) // b + 1
+    seq = np.zeros((2 * d, b, b), np.uint32) if want_seq else None
+    wcap = b if wcap is None else wcap
+    W = np.zeros((max(wcap, 1), r), np.uint32)
+    st = gb_krylov_stats()
+    check(lib().gb_block_wiedemann(mac, b, _p(X, ctypes.c_uint32), _p(Z, ctypes.c_uint32),
+                                   _p(delta, ctypes.c_uint32), _p(seq, ctypes.c_uint32) if want_seq else None,
+                                   _p(W, ctypes.c_uint32), wcap, ctypes.byref(st)), "gb_block_wiedemann")
+    out = _struct_dict(st)
+    out["seq"] = seq
+    out["W"] = W[:min(out["found"], wcap)]
+    return out
+
+
 def gb_modp_apply(op: int, p: int, n: int, window: int, a: int, b: int | None, c: int | None, out: int,
                   stream: int | None = None) -> None:
     """One device F_p primitive applied elementwise (integer device addresses; b and c may be None
@@ -435,10 +468,12 @@ class Context:
     """A library context whose device arena is a torch tensor on `device`."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 2 << 30, keep_step: bool = False,
-                 reduce: str = "auto", stream=None, graphs: bool = True):
+                 reduce: str = "auto", stream=None, graphs: bool = True, sp: str = "hash"):
         """reduce: "auto" (per matrix by shape), "sparse" or "dense" (see GB_CTX_REDUCE_*).
         stream: a torch.cuda.Stream the context runs on (default: a stream of its own).
-        graphs: False launches the echelon-form rounds one by one (GB_CTX_NO_GRAPHS)."""
+        graphs: False launches the echelon-form rounds one by one (GB_CTX_NO_GRAPHS).
+        sp: "hash" (the hash dictionary) or "ranks" (every term keyed by its dense rank,
+        GB_CTX_SP_RANKS) for symbolic preprocessing."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: this library has no CPU path")
@@ -449,6 +484,10 @@ class Context:
                                                             "dense": GB_CTX_REDUCE_DENSE}[reduce]
         if not graphs:
             flags |= GB_CTX_NO_GRAPHS
+        if sp == "ranks":
+            flags |= GB_CTX_SP_RANKS
+        elif sp != "hash":
+            raise ValueError("sp must be 'hash' or 'ranks'")
         self.stream = stream
         self.h = gb_ctx_create(device, stream.cuda_stream if stream is not None else None,
                                self.arena.data_ptr(), arena_bytes, flags)

@@ -177,6 +177,27 @@ __device__ __forceinline__ uint32_t mono_rank(uint4 m, const uint32_t *tab, int 
     return r + tab[d];
 }
 
+// Linear monomial key for the hash dictionary of symbolic preprocessing:
+//     key(a) = sum_i a_i K_i  mod 2^64,   K_i fixed odd 64-bit constants (SplitMix64 outputs).
+// It is additive, key(t m) = key(t) + key(m), so the key of a shifted term costs one 64-bit add
+// once every basis term carries its own key.  It is not injective: distinct monomials may share
+// a key, so every dictionary lookup compares the stored monomial and a mismatch sends the step to
+// the exact rank path.  For a fixed pair a != b the differences a_i - b_i are below 2^8 in
+// magnitude, so a random K gives key(a) = key(b) with probability at most 2^-56.
+static __constant__ unsigned long long MONO_KEY_K[16] = {
+    0x63cfc62a2b097593ull, 0xdc0746b419466aedull, 0x08264674f98aa19full, 0x3ca4eb47b26de7adull,
+    0xa5b384ad339cfcc3ull, 0x08f720d059892bc5ull, 0xfe6675c92d60f3dfull, 0x1d59c7b9c3a56969ull,
+    0xea5685b6014a22c9ull, 0x3935c47ec47e016dull, 0xf72314ef3d87ae57ull, 0xe2c2311ba18cfd93ull,
+    0x509d7011d7bc72c9ull, 0x4cd89b9538c27513ull, 0xa4e38806108a16a3ull, 0x5a469fb3420a4217ull};
+
+__device__ __forceinline__ unsigned long long mono_key(uint4 m) {
+    const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+    unsigned long long h = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) h += (unsigned long long)((w[i >> 2] >> (8 * (i & 3))) & 0xFFu) * MONO_KEY_K[i];
+    return h;
+}
+
 __device__ __forceinline__ uint32_t mono_deg(uint4 m) {
     return __dp4a(m.x, 0x01010101u, 0u) + __dp4a(m.y, 0x01010101u, 0u) +
            __dp4a(m.z, 0x01010101u, 0u) + __dp4a(m.w, 0x01010101u, 0u);

@@ -523,6 +523,7 @@ void make_resident(const std::vector<gb_system *> &Ss) {
         const uint64_t T = S->nterms;
         const size_t ng = S->off.size();
         S->bmon.alloc(ar, std::max<uint64_t>(T, 1024), st);
+        S->bkey.alloc(ar, std::max<uint64_t>(T, 1024), st);
         S->bcf.alloc(ar, std::max<uint64_t>(T, 1024), st);
         S->boff.alloc(ar, std::max<size_t>(ng, 64), st);
         S->blen.alloc(ar, std::max<size_t>(ng, 64), st);
@@ -538,6 +539,7 @@ void make_resident(const std::vector<gb_system *> &Ss) {
         if (T) {
             GB_CUDA(cudaMemcpyAsync(S->bmon.p, d.p + at[j].m, 16ull * T, cudaMemcpyDeviceToDevice, st));
             GB_CUDA(cudaMemcpyAsync(S->bcf.p, d.p + at[j].c, 4ull * T, cudaMemcpyDeviceToDevice, st));
+            basis_keys(S->bmon.p, S->bkey.p, T, st);
         }
         if (ng) {
             GB_CUDA(cudaMemcpyAsync(S->boff.p, d.p + at[j].o, 4ull * ng, cudaMemcpyDeviceToDevice, st));
@@ -630,6 +632,7 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
         st.rank = ech->rank;
         st.nbasis = (uint32_t)S->lm.size();
         st.closure_rounds = mac->closure_rounds;
+        st.sp_redo = mac->sp_redo;
         st.nnz = mac->nnz;
         st.axpy_rows = ech->work[0];
         st.axpy_fma = ech->work[1];

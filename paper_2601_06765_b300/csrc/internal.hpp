@@ -275,6 +275,7 @@ struct gb_macaulay {
     gb_system *sys = nullptr;
     uint32_t n = 0, degree = 0, nrows = 0, ndict = 0, nA = 0, nC = 0, nb = 0;
     uint32_t closure_rounds = 0;
+    uint32_t sp_redo = 0;  // symbolic preprocessing ran again (hash table growth or a key clash)
     uint64_t nnz = 0;
     gb::DBuf<uint32_t> row_ptr, col, val;  // CSR, val in [0, p)
     gb::DBuf<uint4> dict;                  // descending monomials
@@ -316,9 +317,11 @@ struct gb_system {
     bool deglex = false;           // term order: deglex, else grevlex
     // device basis: terms of element k are [off[k], off[k] + len[k]) of bmon / bcf
     gb::DBuf<uint4> bmon;
+    gb::DBuf<unsigned long long> bkey;  // mono_key of every basis term (the hash dictionary's keys)
     gb::DBuf<uint32_t> bcf;
     gb::DBuf<uint32_t> boff, blen;
     uint64_t nterms = 0;
+    uint32_t last_ndict = 0;  // dictionary size of the last step (sizes the next hash table)
     // the normalised input until its upload with the first step (SWAR monomials, coefficients)
     bool resident = false;
     std::vector<uint4> in_mon;
@@ -371,12 +374,22 @@ struct SpTask {
     bool closure = true;
     std::vector<uint32_t> nonred;  // non-redundant basis indices, ascending
     uint64_t cap = 0;              // frontier capacity (0: estimate)
+    uint64_t hcap = 0;             // hash-dictionary slots, a power of two (0: estimate)
+    bool ranks = false;            // dense-rank bitmap for every term instead of the hash dictionary
     std::unique_ptr<gb_macaulay> out;
 };
+// mono_key of n basis terms (after an upload of input terms)
+void basis_keys(const uint4 *mon, unsigned long long *key, uint64_t n, cudaStream_t st);
 
 // pipeline stages for many systems of one context at once (sp.cu, reduce.cu)
 void symbolic_preprocess(std::vector<SpTask> &tasks);
 std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaulay *> &Ms, bool echelon);
+// RREF of each dense matrix Es[j]->dprime (nC x nb) into Es[j]->rank / rref / rpiv (reduce.cu);
+// bounded waits of the tensor-core updates that give up are flagged in derr
+void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::vector<Fp> &fps, uint32_t *derr);
+// the block Wiedemann path of gb_block_wiedemann (krylov.cu)
+void block_wiedemann(const gb_macaulay *mac, uint32_t b, const uint32_t *X, const uint32_t *Z, const uint32_t *delta,
+                     uint32_t *seq, uint32_t *W, uint32_t wcap, gb_krylov_stats *stats);
 // append each job's echelon rows as new basis elements on the device; returns their LMs
 void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector<Mono>> &lms);
 // final reduction: element elems[j][i] of job j becomes LM + row i of its D' (writes fin_*)

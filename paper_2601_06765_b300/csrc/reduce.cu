@@ -1104,6 +1104,7 @@ struct RowsJob {
     uint4 *lm;              // leading monomials of the rows (append)
     const uint32_t *dst_off;  // absolute output offsets (append: the new elements' boff)
     uint4 *omon;            // append: basis monomials
+    unsigned long long *okey;  // append: their mono_key
     uint32_t *ocf;
     uint8_t *oexp;          // tails: n-byte exponent vectors
 };
@@ -1138,6 +1139,7 @@ __global__ void k_write_rows(const RowsJob *__restrict__ jobs, const uint32_t *_
     auto put = [&](uint32_t pos, uint4 m, uint32_t c) {
         if (J.omon) {
             J.omon[pos] = m;
+            J.okey[pos] = mono_key(m);
         } else {
             const uint32_t w[4] = {m.x, m.y, m.z, m.w};
             for (uint32_t i = 0; i < J.n; ++i) J.oexp[(size_t)pos * J.n + i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
@@ -1171,11 +1173,6 @@ __global__ void k_write_rows(const RowsJob *__restrict__ jobs, const uint32_t *_
         if (threadIdx.x == 0) base += total;
         __syncthreads();
     }
-}
-
-__global__ void k_mark_pivot_cols(uint32_t nA, const uint32_t *__restrict__ pcols, uint32_t *__restrict__ colpos) {
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nA) colpos[pcols[k]] = k | 0x80000000u;
 }
 
 // launch a grouped row kernel: `per_job` blocks per job, plan staged and uploaded with the jobs
@@ -1255,6 +1252,172 @@ static int tuned_choice(const gb_ctx *ctx, uint64_t key) {
 static int rref_schedule(const gb_ctx *ctx, uint32_t p, uint32_t nC, uint32_t nb, int nj) {
     if (ctx->tune.force_rref >= 0) return ctx->tune.force_rref;
     return nj == 1 ? tuned_choice(ctx, tune_key(TUNE_RREF, p, nC, nb, 0)) : -1;
+}
+
+// RREF of each job's dense matrix Es[j]->dprime (Es[j]->nC x Es[j]->nb, row pitch nb) over F_p
+// with fps[j] (Sec. 9.2 panel elimination): sets Es[j]->rank, rref, rpiv.  Bounded waits of the
+// tensor-core updates that give up are flagged in derr.
+void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::vector<Fp> &fps,
+                   uint32_t *derr) {
+    Arena &ar = ctx->arena;
+    cudaStream_t st = ctx->stream;
+    const int nj = (int)Es.size();
+    std::vector<uint32_t> rank(nj, 0);
+    // per-job working state, one allocation each
+    std::vector<RrefJob> X(nj);
+    std::vector<DBuf<uint32_t>> Mw(nj), lead(nj), pcol(nj), order(nj), panel(nj);
+    DBuf<uint32_t> states;  // 4 words per job, then the graph's round count; read back in one copy
+    states.alloc(ar, 4ull * nj + 4, st);
+    GB_CUDA(cudaMemsetAsync(states.p, 0, 16ull * nj + 16, st));
+    RoundGraph graph;
+    unsigned graph_nodes = 0;
+    std::vector<int> live, smem_jobs, glob_jobs, tc_jobs;
+    std::vector<DigitPlanes> FA(nj), FB(nj);
+    std::vector<std::unique_ptr<MmPlan>> plans(nj);
+    for (int j = 0; j < nj; ++j) {
+        const uint32_t nC = Es[j]->nC, nb = Es[j]->nb;
+        X[j] = RrefJob{};
+        X[j].nC = nC;
+        X[j].nb = nb;
+        X[j].fp = fps[j];
+        if (!nC || !nb) continue;
+        X[j].ldm = (nb + 3) / 4 * 4;
+        Mw[j].alloc(ar, (size_t)nC * X[j].ldm, st);
+        lead[j].alloc(ar, nC, st);
+        pcol[j].alloc(ar, nC, st);
+        order[j].alloc(ar, std::min(nC, nb), st);
+        panel[j].alloc(ar, 3 * KP, st);
+        GB_CUDA(cudaMemcpy2DAsync(Mw[j].p, 4ull * X[j].ldm, Es[j]->dprime.p, 4ull * nb, 4ull * nb, nC,
+                                  cudaMemcpyDeviceToDevice, st));
+        // large D': the trailing update of each panel on the tensor cores
+        const int sched = rref_schedule(ctx, fps[j].p, nC, nb, nj);
+        if ((ctx->flags & GB_CTX_REDUCE_DENSE) || (sched >= 0 ? sched == 2 : (uint64_t)nC * nb >= (1ull << 22))) {
+            const uint32_t L = digits_for(fps[j].p);
+            FA[j].alloc(ar, L, nC, KP, st);
+            FB[j].alloc(ar, L, nb, KP, st);
+            GB_CUDA(cudaMemsetAsync(FA[j].p, 0, FA[j].buf.bytes(), st));
+            GB_CUDA(cudaMemsetAsync(FB[j].p, 0, FB[j].buf.bytes(), st));
+            X[j].tc = 1;
+            X[j].fa = FA[j].p;
+            X[j].fb = FB[j].p;
+            X[j].fkp = FA[j].kpad;
+            plans[j] = std::make_unique<MmPlan>(FA[j], FB[j], Mw[j].p, X[j].ldm, nC, nb, fps[j]);
+            tc_jobs.push_back(j);
+        }
+        X[j].M = Mw[j].p;
+        X[j].lead = lead[j].p;
+        X[j].pcol = pcol[j].p;
+        X[j].order = order[j].p;
+        X[j].state = states.p + 4 * j;
+        X[j].panel = panel[j].p;
+        live.push_back(j);
+        (4ull * KP * nb <= 200 * 1024 ? smem_jobs : glob_jobs).push_back(j);
+    }
+    if (!live.empty()) {
+        std::vector<uint32_t> rows(nj, 0);
+        for (int j : live) rows[j] = X[j].nC;
+        Grouped<RrefJob> G;
+        G.build(ctx, X, {rows});
+        DBuf<int> lists;
+        lists.alloc(ar, (size_t)nj + 1, st);
+        {
+            std::vector<int> l(smem_jobs);
+            l.insert(l.end(), glob_jobs.begin(), glob_jobs.end());
+            int *hl = static_cast<int *>(ctx_pinned(ctx, 4ull * (l.size() + 1)));
+            std::memcpy(hl, l.data(), 4 * l.size());
+            GB_CUDA(cudaMemcpyAsync(lists.p, hl, 4 * l.size(), cudaMemcpyHostToDevice, st));
+        }
+        size_t pan_bytes = 0;
+        for (int j : smem_jobs) pan_bytes = std::max<size_t>(pan_bytes, 4ull * KP * X[j].nb);
+        if (!smem_jobs.empty()) opt_in_smem(reinterpret_cast<const void *>(k_panel_rref<true>));
+        // jobs are packed in the job table at their own index; k_pick_panel runs on all of them
+        // (a job without rows has no blocks elsewhere and its state stays zero)
+        k_leads<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
+        counted();
+        // every round turns each of its rows into a pivot row or a zero row
+        uint32_t maxrounds = 1;
+        for (int j : live) maxrounds = std::max<uint32_t>(maxrounds, (X[j].nC + KP - 1) / KP + 1);
+        // one round: each job picks its next panel, reduces it, and eliminates the panel's
+        // pivot columns from all its other rows
+        auto round = [&](cudaStream_t s) {
+            k_pick_panel<<<nj, 1024, 0, s>>>(G.jobs);
+            if (!smem_jobs.empty())
+                k_panel_rref<true><<<(unsigned)smem_jobs.size(), PT, pan_bytes, s>>>(G.jobs, lists.p);
+            if (!glob_jobs.empty())
+                k_panel_rref<false><<<(unsigned)glob_jobs.size(), PT, 0, s>>>(G.jobs, lists.p + smem_jobs.size());
+            k_eliminate<<<G.totals[0], 256, 0, s>>>(G.jobs, G.plans[0], nj);
+            counted(2 + (smem_jobs.empty() ? 0 : 1) + (glob_jobs.empty() ? 0 : 1));
+            for (int j : tc_jobs) {
+                const unsigned nt = (unsigned)(((size_t)X[j].nC + X[j].nb) * KP);
+                if (FA[j].L == 2) k_elim_digits<2><<<(nt + 255) / 256, 256, 0, s>>>(G.jobs, j);
+                else k_elim_digits<4><<<(nt + 255) / 256, 256, 0, s>>>(G.jobs, j);
+                counted();
+                plans[j]->update(0, 0, 0, 0, 0, 0, X[j].nC, X[j].nb, KP, true, derr, s);
+                k_leads_np<<<X[j].nC, 256, 0, s>>>(G.jobs, j);
+                counted();
+            }
+        };
+        int sched = -1;
+        for (int j : live) sched = std::max(sched, rref_schedule(ctx, fps[j].p, X[j].nC, X[j].nb, nj));
+        if (!(ctx->flags & GB_CTX_NO_GRAPHS) && (sched >= 0 ? sched >= 1 : maxrounds >= GRAPH_MIN_ROUNDS)) {
+            // the whole loop as one graph: the rounds repeat on the device until no job has
+            // rows left, with no host round trip between them
+            unsigned per_round = 0;
+            graph = record_round_loop(ctx, [&](cudaStream_t s, cudaGraphConditionalHandle more) {
+                round(s);
+                k_rref_more<<<1, 32, 0, s>>>(G.jobs, nj, states.p + 4 * nj, maxrounds, more);
+                counted();
+            }, per_round);
+            GB_CUDA(cudaGraphLaunch(graph.exec, st));
+            g_graph_launches.fetch_add(1, std::memory_order_relaxed);
+            graph_nodes = per_round;
+        } else {
+            uint32_t rounds = 0;
+            for (;;) {
+                const uint32_t group = rounds == 0 ? 2 : 4;
+                for (uint32_t g = 0; g < group; ++g) round(st);
+                rounds += group;
+                uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj));
+                GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
+                ctx_sync(ctx);
+                bool more = false;
+                for (int j : live) {
+                    const uint32_t *s = h + 4 * j;
+                    if (s[1] != 0 && s[3] > s[1]) more = true;
+                }
+                if (!more || rounds >= maxrounds) break;
+            }
+        }
+        // one more pick confirms that no non-zero non-pivot row is left
+        k_pick_panel<<<nj, 1024, 0, st>>>(G.jobs);
+        counted();
+        uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj + 16));
+        GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj + 16, cudaMemcpyDeviceToHost, st));
+        ctx_sync(ctx);
+        if (graph.exec) counted(graph_nodes * h[4 * nj]);  // rounds the graph ran
+        graph.reset();
+        for (int j : live) {
+            if (h[4 * j + 1] != 0) fail(GB_EDEVICE, "RREF: rows left after the last round");
+            rank[j] = h[4 * j];
+        }
+        // gather the pivot rows in order
+        std::vector<uint32_t> prow(nj, 0);
+        for (int j : live) {
+            Es[j]->rank = rank[j];
+            Es[j]->rref.alloc(ar, (size_t)rank[j] * X[j].nb, st);
+            Es[j]->rpiv.alloc(ar, rank[j], st);
+            X[j].out = Es[j]->rref.p;
+            X[j].opiv = Es[j]->rpiv.p;
+            X[j].rank = rank[j];
+            prow[j] = rank[j];
+        }
+        Grouped<RrefJob> G2;
+        G2.build(ctx, X, {prow});
+        if (G2.totals[0]) {
+            k_gather_rref<<<G2.totals[0], 256, 0, st>>>(G2.jobs, G2.plans[0], nj);
+            counted();
+        }
+    }
 }
 
 std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaulay *> &Ms, bool echelon) {
@@ -1436,163 +1599,14 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
     }
     GB_CUDA(cudaEventRecord(ctx->ev[3], st));
 
-    std::vector<uint32_t> rank(nj, 0);
     if (echelon) {
-        // per-job working state, one allocation each
-        std::vector<RrefJob> X(nj);
-        std::vector<DBuf<uint32_t>> Mw(nj), lead(nj), pcol(nj), order(nj), panel(nj);
-        DBuf<uint32_t> states;  // 4 words per job, then the graph's round count; read back in one copy
-        states.alloc(ar, 4ull * nj + 4, st);
-        GB_CUDA(cudaMemsetAsync(states.p, 0, 16ull * nj + 16, st));
-        RoundGraph graph;
-        unsigned graph_nodes = 0;
-        std::vector<int> live, smem_jobs, glob_jobs, tc_jobs;
-        std::vector<DigitPlanes> FA(nj), FB(nj);
-        std::vector<std::unique_ptr<MmPlan>> plans(nj);
+        std::vector<gb_echelon *> Ep(nj);
+        std::vector<Fp> fps(nj);
         for (int j = 0; j < nj; ++j) {
-            const uint32_t nC = R[j].nC, nb = R[j].nb;
-            X[j] = RrefJob{};
-            X[j].nC = nC;
-            X[j].nb = nb;
-            X[j].fp = R[j].fp;
-            if (!nC || !nb) continue;
-            X[j].ldm = (nb + 3) / 4 * 4;
-            Mw[j].alloc(ar, (size_t)nC * X[j].ldm, st);
-            lead[j].alloc(ar, nC, st);
-            pcol[j].alloc(ar, nC, st);
-            order[j].alloc(ar, std::min(nC, nb), st);
-            panel[j].alloc(ar, 3 * KP, st);
-            GB_CUDA(cudaMemcpy2DAsync(Mw[j].p, 4ull * X[j].ldm, Es[j]->dprime.p, 4ull * nb, 4ull * nb, nC,
-                                      cudaMemcpyDeviceToDevice, st));
-            // large D': the trailing update of each panel on the tensor cores
-            const int sched = rref_schedule(ctx, R[j].fp.p, nC, nb, nj);
-            if ((ctx->flags & GB_CTX_REDUCE_DENSE) || (sched >= 0 ? sched == 2 : (uint64_t)nC * nb >= (1ull << 22))) {
-                const uint32_t L = digits_for(R[j].fp.p);
-                FA[j].alloc(ar, L, nC, KP, st);
-                FB[j].alloc(ar, L, nb, KP, st);
-                GB_CUDA(cudaMemsetAsync(FA[j].p, 0, FA[j].buf.bytes(), st));
-                GB_CUDA(cudaMemsetAsync(FB[j].p, 0, FB[j].buf.bytes(), st));
-                X[j].tc = 1;
-                X[j].fa = FA[j].p;
-                X[j].fb = FB[j].p;
-                X[j].fkp = FA[j].kpad;
-                plans[j] = std::make_unique<MmPlan>(FA[j], FB[j], Mw[j].p, X[j].ldm, nC, nb, R[j].fp);
-                tc_jobs.push_back(j);
-            }
-            X[j].M = Mw[j].p;
-            X[j].lead = lead[j].p;
-            X[j].pcol = pcol[j].p;
-            X[j].order = order[j].p;
-            X[j].state = states.p + 4 * j;
-            X[j].panel = panel[j].p;
-            live.push_back(j);
-            (4ull * KP * nb <= 200 * 1024 ? smem_jobs : glob_jobs).push_back(j);
+            Ep[j] = Es[j].get();
+            fps[j] = R[j].fp;
         }
-        if (!live.empty()) {
-            std::vector<uint32_t> rows(nj, 0);
-            for (int j : live) rows[j] = X[j].nC;
-            Grouped<RrefJob> G;
-            G.build(ctx, X, {rows});
-            DBuf<int> lists;
-            lists.alloc(ar, (size_t)nj + 1, st);
-            {
-                std::vector<int> l(smem_jobs);
-                l.insert(l.end(), glob_jobs.begin(), glob_jobs.end());
-                int *hl = static_cast<int *>(ctx_pinned(ctx, 4ull * (l.size() + 1)));
-                std::memcpy(hl, l.data(), 4 * l.size());
-                GB_CUDA(cudaMemcpyAsync(lists.p, hl, 4 * l.size(), cudaMemcpyHostToDevice, st));
-            }
-            size_t pan_bytes = 0;
-            for (int j : smem_jobs) pan_bytes = std::max<size_t>(pan_bytes, 4ull * KP * X[j].nb);
-            if (!smem_jobs.empty()) opt_in_smem(reinterpret_cast<const void *>(k_panel_rref<true>));
-            // jobs are packed in the job table at their own index; k_pick_panel runs on all of them
-            // (a job without rows has no blocks elsewhere and its state stays zero)
-            k_leads<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
-            counted();
-            // every round turns each of its rows into a pivot row or a zero row
-            uint32_t maxrounds = 1;
-            for (int j : live) maxrounds = std::max<uint32_t>(maxrounds, (X[j].nC + KP - 1) / KP + 1);
-            // one round: each job picks its next panel, reduces it, and eliminates the panel's
-            // pivot columns from all its other rows
-            auto round = [&](cudaStream_t s) {
-                k_pick_panel<<<nj, 1024, 0, s>>>(G.jobs);
-                if (!smem_jobs.empty())
-                    k_panel_rref<true><<<(unsigned)smem_jobs.size(), PT, pan_bytes, s>>>(G.jobs, lists.p);
-                if (!glob_jobs.empty())
-                    k_panel_rref<false><<<(unsigned)glob_jobs.size(), PT, 0, s>>>(G.jobs, lists.p + smem_jobs.size());
-                k_eliminate<<<G.totals[0], 256, 0, s>>>(G.jobs, G.plans[0], nj);
-                counted(2 + (smem_jobs.empty() ? 0 : 1) + (glob_jobs.empty() ? 0 : 1));
-                for (int j : tc_jobs) {
-                    const unsigned nt = (unsigned)(((size_t)X[j].nC + X[j].nb) * KP);
-                    if (FA[j].L == 2) k_elim_digits<2><<<(nt + 255) / 256, 256, 0, s>>>(G.jobs, j);
-                    else k_elim_digits<4><<<(nt + 255) / 256, 256, 0, s>>>(G.jobs, j);
-                    counted();
-                    plans[j]->update(0, 0, 0, 0, 0, 0, X[j].nC, X[j].nb, KP, true, derr.p, s);
-                    k_leads_np<<<X[j].nC, 256, 0, s>>>(G.jobs, j);
-                    counted();
-                }
-            };
-            int sched = -1;
-            for (int j : live) sched = std::max(sched, rref_schedule(ctx, R[j].fp.p, X[j].nC, X[j].nb, nj));
-            if (!(ctx->flags & GB_CTX_NO_GRAPHS) && (sched >= 0 ? sched >= 1 : maxrounds >= GRAPH_MIN_ROUNDS)) {
-                // the whole loop as one graph: the rounds repeat on the device until no job has
-                // rows left, with no host round trip between them
-                unsigned per_round = 0;
-                graph = record_round_loop(ctx, [&](cudaStream_t s, cudaGraphConditionalHandle more) {
-                    round(s);
-                    k_rref_more<<<1, 32, 0, s>>>(G.jobs, nj, states.p + 4 * nj, maxrounds, more);
-                    counted();
-                }, per_round);
-                GB_CUDA(cudaGraphLaunch(graph.exec, st));
-                g_graph_launches.fetch_add(1, std::memory_order_relaxed);
-                graph_nodes = per_round;
-            } else {
-                uint32_t rounds = 0;
-                for (;;) {
-                    const uint32_t group = rounds == 0 ? 2 : 4;
-                    for (uint32_t g = 0; g < group; ++g) round(st);
-                    rounds += group;
-                    uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj));
-                    GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
-                    ctx_sync(ctx);
-                    bool more = false;
-                    for (int j : live) {
-                        const uint32_t *s = h + 4 * j;
-                        if (s[1] != 0 && s[3] > s[1]) more = true;
-                    }
-                    if (!more || rounds >= maxrounds) break;
-                }
-            }
-            // one more pick confirms that no non-zero non-pivot row is left
-            k_pick_panel<<<nj, 1024, 0, st>>>(G.jobs);
-            counted();
-            uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj + 16));
-            GB_CUDA(cudaMemcpyAsync(h, states.p, 16ull * nj + 16, cudaMemcpyDeviceToHost, st));
-            ctx_sync(ctx);
-            if (graph.exec) counted(graph_nodes * h[4 * nj]);  // rounds the graph ran
-            graph.reset();
-            for (int j : live) {
-                if (h[4 * j + 1] != 0) fail(GB_EDEVICE, "RREF: rows left after the last round");
-                rank[j] = h[4 * j];
-            }
-            // gather the pivot rows in order
-            std::vector<uint32_t> prow(nj, 0);
-            for (int j : live) {
-                Es[j]->rank = rank[j];
-                Es[j]->rref.alloc(ar, (size_t)rank[j] * X[j].nb, st);
-                Es[j]->rpiv.alloc(ar, rank[j], st);
-                X[j].out = Es[j]->rref.p;
-                X[j].opiv = Es[j]->rpiv.p;
-                X[j].rank = rank[j];
-                prow[j] = rank[j];
-            }
-            Grouped<RrefJob> G2;
-            G2.build(ctx, X, {prow});
-            if (G2.totals[0]) {
-                k_gather_rref<<<G2.totals[0], 256, 0, st>>>(G2.jobs, G2.plans[0], nj);
-                counted();
-            }
-        }
+        echelon_stage(ctx, Ep, fps, derr.p);
     }
     GB_CUDA(cudaEventRecord(ctx->ev[4], st));
     uint64_t *hw = static_cast<uint64_t *>(ctx_pinned(ctx, 16ull * nj + 16));
@@ -1677,6 +1691,7 @@ void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector
         const size_t ng0 = S->off.size();
         if (base + add > S->bmon.n) {
             S->bmon.grow(ar, std::max<size_t>(base + add, 2 * S->bmon.n), base, st);
+            S->bkey.grow(ar, std::max<size_t>(base + add, 2 * S->bkey.n), base, st);
             S->bcf.grow(ar, std::max<size_t>(base + add, 2 * S->bcf.n), base, st);
         }
         if (ng0 + rank > S->boff.n) {
@@ -1707,6 +1722,7 @@ void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector
         GB_CUDA(cudaMemcpyAsync(S->blen.p + ng0, d.p + at_len[j], 4ull * rank, cudaMemcpyDeviceToDevice, st));
         J[j].dst_off = S->boff.p + ng0;
         J[j].omon = S->bmon.p;
+        J[j].okey = S->bkey.p;
         J[j].ocf = S->bcf.p;
     }
     Grouped<RowsJob> G;

@@ -3,10 +3,18 @@
 // bulk frontier rounds (Sec. 7.2), for many independent jobs (systems) at once.
 //
 // Keys.  Every monomial of a job has degree <= D (its step degree), so its dense grevlex rank
-// (device.cuh) lies in [0, C(n + D, n)).  Setification + ordering of T (Sec. 5.1) is a counting
-// sort: a bitmap over the rank space (L2-resident) is marked with atomicOr, and the dictionary
-// column of a rank is the number of marked ranks above it (word popcounts + one exclusive scan).
-// The atomicOr that flips a bit is also the "new monomial" test of the closure frontier.
+// (device.cuh) lies in [0, C(n + D, n)).  Ordering of T (Sec. 5.1) is a counting sort: a bitmap
+// over the rank space (L2-resident) is marked with atomicOr, and the dictionary column of a rank
+// is the number of marked ranks above it (word popcounts + one exclusive scan).
+//
+// Setification (Sec. 5.1) and the column of every term (the join of Sec. 7.5) go through a hash
+// dictionary keyed by the additive monomial key of device.cuh: a basis term carries key(m), a row
+// key(t), so a term's key is one 64-bit add, and a slot holds the key, the monomial and (once
+// known) its column.  The insert that claims a slot is the "new monomial" test of the closure
+// frontier; the dense rank is then computed only for the N distinct monomials, not for every
+// term.  Every lookup of the fill compares the stored monomial with the term's; a mismatch (two
+// monomials sharing a key) sends the job back through the rank path, in which every term's rank
+// marks the bitmap directly and the column is read from its popcount prefix.
 //
 // Passes (each one launch for all jobs; a job's blocks are found through a prefix table):
 //   1. mark the leading monomials of the given rows (they start in Done: no reducer rows for them)
@@ -22,6 +30,8 @@
 // Scans run once over the concatenation of all jobs' arrays; a job reads its prefixes relative
 // to the first entry of its own range.
 #include <algorithm>
+#include <cstddef>
+#include <cstdlib>
 
 #include "internal.hpp"
 
@@ -40,9 +50,20 @@ struct Counters {  // device-side counters of one job, read back after each roun
     uint32_t pad;
 };
 
+// one slot of the hash dictionary: 32 bytes, so that a lookup touches one L2 sector
+struct alignas(32) HSlot {
+    unsigned long long tag;  // 0: empty, else key + 1 (0 mapped to 1)
+    uint32_t col;            // dictionary column, once the dictionary is ordered
+    uint32_t pad;
+    uint4 mon;               // the monomial, written by the thread that claimed the slot
+};
+static_assert(sizeof(HSlot) == 32 && offsetof(HSlot, col) == 8 && offsetof(HSlot, mon) == 16,
+              "the fill reads a slot as two 16-byte words: key, column, pad | monomial");
+
 struct Job {
     // basis of the job's system
     const uint4 *bmon;
+    const unsigned long long *bkey;
     const uint32_t *bcf, *boff, *blen;
     // given rows
     const uint4 *gt;
@@ -65,6 +86,11 @@ struct Job {
     uint4 *red_t;
     uint32_t *red_k, *red_rank, *lm_rank;
     Counters *cnt;
+    // hash dictionary (null htab: the rank path)
+    HSlot *htab;
+    uint32_t hmask, hshift;    // slots - 1, 64 - log2(slots)
+    unsigned long long keymask;  // all ones; fewer bits (GB_SP_KEY_MASK) force shared keys in tests
+    uint32_t *qslot, *red_slot, *lm_slot;
     // dictionary, rows and CSR (filled in once the counts are known)
     uint32_t N, nA, nrows, nq, nred, nnz;
     uint32_t *wcnt;        // this job's range of the concatenated word counts
@@ -113,6 +139,110 @@ __device__ __forceinline__ void push_new(bool isnew, uint4 m, uint32_t r, const 
     }
 }
 
+constexpr uint32_t ERR_TABLE_FULL = 64u, ERR_KEY_CLASH = 128u;
+
+__device__ __forceinline__ unsigned long long tag_of(unsigned long long key, const Job &J) {
+    const unsigned long long t = (key & J.keymask) + 1ull;
+    return t ? t : 1ull;
+}
+
+__device__ __forceinline__ uint32_t home_slot(unsigned long long tag, const Job &J) {
+    return (uint32_t)((tag * 0x9E3779B97F4A7C15ull) >> J.hshift);
+}
+
+// claim or find the slot of `tag` (linear probing from slot s, whose tag was read as `cur`; at
+// most every slot once).  isnew: this call claimed an empty slot.  A full table sets
+// ERR_TABLE_FULL and returns 0xFFFFFFFF.
+__device__ __forceinline__ uint32_t h_insert_from(unsigned long long tag, uint32_t s, unsigned long long cur,
+                                                  const Job &J, bool &isnew) {
+    isnew = false;
+    for (uint32_t probe = 0; probe <= J.hmask; ++probe) {
+        if (probe) cur = J.htab[s].tag;  // a slot only ever goes from 0 to its final tag
+        if (cur == tag) return s;
+        if (cur == 0ull) {
+            cur = atomicCAS(&J.htab[s].tag, 0ull, tag);
+            if (cur == 0ull) {
+                isnew = true;
+                return s;
+            }
+            if (cur == tag) return s;
+        }
+        s = (s + 1u) & J.hmask;
+    }
+    atomicOr(&J.cnt->err, ERR_TABLE_FULL);
+    return 0xFFFFFFFFu;
+}
+
+// the slot of a tag inserted by an earlier kernel, or 0xFFFFFFFF
+__device__ __forceinline__ uint32_t h_insert(unsigned long long tag, const Job &J, bool &isnew) {
+    const uint32_t s = home_slot(tag, J);
+    return h_insert_from(tag, s, J.htab[s].tag, J, isnew);
+}
+
+__device__ __forceinline__ uint32_t h_find(unsigned long long tag, const Job &J) {
+    uint32_t s = home_slot(tag, J);
+    for (uint32_t probe = 0; probe <= J.hmask; ++probe) {
+        const unsigned long long cur = J.htab[s].tag;
+        if (cur == tag) return s;
+        if (cur == 0ull) return 0xFFFFFFFFu;
+        s = (s + 1u) & J.hmask;
+    }
+    return 0xFFFFFFFFu;
+}
+
+// warp-aggregated append of new monomials and their slots to the job's frontier queue
+__device__ __forceinline__ void push_new_slot(bool isnew, uint4 m, uint32_t slot, const Job &J) {
+    const unsigned mask = __ballot_sync(0xffffffffu, isnew);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&J.cnt->q, (uint32_t)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (isnew) {
+        const uint32_t pos = base + __popc(mask & ((1u << lane) - 1u));
+        if (pos < J.cap) {
+            J.qmon[pos] = m;
+            J.qslot[pos] = slot;
+        }
+    }
+}
+
+// hash path of expand_terms: a term's key is key(t) + key(m_j); only a term that claims a slot
+// loads its monomial (for the slot and the frontier queue).  Four terms per lane in flight.
+__device__ __forceinline__ void expand_terms_hash(uint4 t, unsigned long long kt, uint32_t off, uint32_t j0,
+                                                  uint32_t len, const Job &J) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t jb = j0; jb < len; jb += 4 * 32) {
+        // the four terms' home slots are read together (independent loads); a term whose home
+        // slot already holds its key -- the common case -- is done
+        unsigned long long tg[4], cur[4];
+        uint32_t hs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = jb + 32u * u + lane;
+            tg[u] = j < len ? tag_of(kt + J.bkey[off + j], J) : 0ull;
+            hs[u] = home_slot(tg[u], J);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cur[u] = tg[u] ? J.htab[hs[u]].tag : 0ull;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = jb + 32u * u + lane;
+            bool isnew = false;
+            uint32_t s = 0;
+            uint4 m = make_uint4(0, 0, 0, 0);
+            if (tg[u] && cur[u] != tg[u]) {
+                s = h_insert_from(tg[u], hs[u], cur[u], J, isnew);
+                if (isnew) {
+                    m = mono_mul(t, J.bmon[off + j]);
+                    J.htab[s].mon = m;
+                }
+            }
+            push_new_slot(isnew, m, s, J);
+        }
+    }
+}
+
 // expand terms [j0, len) of t*g into the bitmap / queue; called by a whole warp
 __device__ __forceinline__ void expand_terms(uint4 t, uint32_t off, uint32_t j0, uint32_t len,
                                              const Job &J, const uint32_t *tab) {
@@ -147,6 +277,12 @@ __global__ void k_mark_given(const Job *__restrict__ jobs, const uint32_t *__res
     const uint32_t r = mono_rank(m, tab, J.n, J.sh, J.deglex != 0);
     atomicOr(&J.bits[r >> 5], 1u << (r & 31));
     J.lm_rank[i] = r;
+    if (J.htab) {  // the leading monomials start in the dictionary (Done): never frontier items
+        bool isnew = false;
+        const uint32_t s = h_insert(tag_of(mono_key(J.gt[i]) + J.bkey[J.boff[J.gk[i]]], J), J, isnew);
+        if (isnew) J.htab[s].mon = m;
+        J.lm_slot[i] = s;
+    }
 }
 
 // Pass 2: expand the given rows (warp per row)
@@ -159,7 +295,8 @@ __global__ void k_expand_given(const Job *__restrict__ jobs, const uint32_t *__r
     if (row >= J.ng) return;  // whole warp leaves together
     const uint32_t k = J.gk[row];
     const uint32_t j0 = (J.gf[row] & FLAG_TAIL) ? 1u : 0u;
-    expand_terms(J.gt[row], J.boff[k], j0, J.blen[k], J, tab);
+    if (J.htab) expand_terms_hash(J.gt[row], mono_key(J.gt[row]), J.boff[k], j0, J.blen[k], J);
+    else expand_terms(J.gt[row], J.boff[k], j0, J.blen[k], J, tab);
 }
 
 // Pass 3: one closure round over each job's frontier items [range[2j], range[2j+1]) (warp per item)
@@ -195,11 +332,28 @@ __global__ void k_closure(const Job *__restrict__ jobs, const uint32_t *__restri
         if (pos < J.cap) {
             J.red_t[pos] = t;
             J.red_k[pos] = (uint32_t)g;
-            J.red_rank[pos] = J.qrank[item];
+            if (J.htab) J.red_slot[pos] = J.qslot[item];
+            else J.red_rank[pos] = J.qrank[item];
         }
         atomicAdd(&J.cnt->red_nnz, (unsigned long long)len);
     }
-    expand_terms(t, J.boff[g], 1u, len, J, tab);
+    if (J.htab) expand_terms_hash(t, mono_key(t), J.boff[g], 1u, len, J);
+    else expand_terms(t, J.boff[g], 1u, len, J, tab);
+}
+
+// hash path, dictionary: the dense rank of every frontier monomial marks the bitmap (the given
+// rows' leading monomials were marked with their ranks in pass 1)
+__global__ void k_rank_queue(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
+    extern __shared__ uint32_t tab[];
+    const int jb = job_of_block(bstart, nj);
+    const Job &J = jobs[jb];
+    if (!J.htab) return;  // the whole block: rank-path jobs marked their bits while expanding
+    load_tab(tab, J);
+    const uint32_t i = (blockIdx.x - bstart[jb]) * blockDim.x + threadIdx.x;
+    if (i >= J.nq) return;
+    const uint32_t r = mono_rank(J.qmon[i], tab, J.n, J.sh, J.deglex != 0);
+    J.qrank[i] = r;
+    atomicOr(&J.bits[r >> 5], 1u << (r & 31));
 }
 
 // thread-per-item kernels: 256 items per block, block -> (job, local index i)
@@ -220,6 +374,7 @@ __global__ void k_dict_queue(const Job *__restrict__ jobs, const uint32_t *__res
     const uint32_t c = col_of(J, J.qrank[i]);
     if (c >= J.N) { atomicOr(&J.cnt->err, 1u); return; }
     J.dict[c] = J.qmon[i];
+    if (J.htab) J.htab[J.qslot[i]].col = c;
 }
 
 __global__ void k_dict_given(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
@@ -230,11 +385,12 @@ __global__ void k_dict_given(const Job *__restrict__ jobs, const uint32_t *__res
     J.dict[c] = mono_mul(J.gt[i], J.bmon[J.boff[J.gk[i]]]);
     J.is_piv[c] = 1u;
     J.src[c] = 0x80000000u | i;
+    if (J.htab) J.htab[J.lm_slot[i]].col = c;
 }
 
 __global__ void k_piv_reducers(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     GB_JOB_ITEM(J.nred)
-    const uint32_t c = col_of(J, J.red_rank[i]);
+    const uint32_t c = J.htab ? J.htab[J.red_slot[i]].col : col_of(J, J.red_rank[i]);
     if (c >= J.N) { atomicOr(&J.cnt->err, 4u); return; }
     J.is_piv[c] = 1u;
     J.src[c] = i;
@@ -306,6 +462,63 @@ __global__ void k_fill(const Job *__restrict__ jobs, const uint32_t *__restrict_
         if (lane == 0) atomicOr(&J.cnt->err, 32u);
         return;
     }
+    if (J.htab) {
+        // hash path: key, slot, and a comparison of the slot's monomial with the term's
+        const unsigned long long kt = mono_key(t);
+        bool clash = false;
+        for (uint32_t j0 = lane; j0 < len; j0 += 4 * 32) {
+            // every load of the four terms is issued before any is used: their keys, monomials
+            // and coefficients, then each home slot's 32 bytes (key, column, monomial) in two
+            // 16-byte reads; a key or monomial mismatch takes the probing path
+            unsigned long long tg[4];
+            uint32_t v[4], hs[4];
+            uint4 m[4], s0[4], s1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = j0 + 32u * u;
+                tg[u] = 0ull;
+                if (j < len) {
+                    tg[u] = tag_of(kt + J.bkey[off + j], J);
+                    m[u] = mono_mul(t, J.bmon[off + j]);
+                    v[u] = J.bcf[off + j];
+                }
+                hs[u] = home_slot(tg[u], J);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (tg[u]) {
+                    const uint4 *sp = reinterpret_cast<const uint4 *>(J.htab + hs[u]);
+                    s0[u] = __ldg(sp);
+                    s1[u] = __ldg(sp + 1);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = j0 + 32u * u;
+                if (j < len) {
+                    uint32_t c = 0xFFFFFFFFu;
+                    const unsigned long long t0 = ((unsigned long long)s0[u].y << 32) | s0[u].x;
+                    uint4 h = s1[u];
+                    uint32_t hc = s0[u].z;
+                    if (t0 != tg[u]) {  // not in its home slot: probe
+                        const uint32_t sl = h_find(tg[u], J);
+                        if (sl != 0xFFFFFFFFu) {
+                            h = J.htab[sl].mon;
+                            hc = J.htab[sl].col;
+                        } else {
+                            h = make_uint4(~0u, ~0u, ~0u, ~0u);
+                        }
+                    }
+                    if (h.x == m[u].x && h.y == m[u].y && h.z == m[u].z && h.w == m[u].w) c = hc;
+                    clash |= c >= J.N;
+                    J.col[s + j] = c;
+                    J.val[s + j] = v[u];
+                }
+            }
+        }
+        if (clash) atomicOr(&J.cnt->err, ERR_KEY_CLASH);
+        return;
+    }
     // four terms per lane in flight: their ranks and dictionary lookups are independent
     for (uint32_t j0 = lane; j0 < len; j0 += 4 * 32) {
         uint32_t r[4], v[4];
@@ -361,10 +574,22 @@ struct SpHost {
     size_t o_gt = 0, o_gk = 0, o_gf = 0, o_np = 0, o_tab = 0, o_nri = 0, o_nrl = 0;
     DBuf<uint32_t> bits, lm_rank, qrank, red_k, red_rank;
     DBuf<uint4> qmon, red_t;
+    // hash dictionary
+    bool hash = false;
+    uint64_t hcap = 0;
+    DBuf<HSlot> htab;
+    DBuf<uint32_t> qslot, red_slot, lm_slot;
     Counters hc{};
     uint32_t rounds = 0;
     bool overflow = false;
+    bool table_full = false;
 };
+
+uint64_t pow2_at_least(uint64_t x) {
+    uint64_t c = 1;
+    while (c < x) c <<= 1;
+    return c;
+}
 
 }  // namespace
 
@@ -378,6 +603,14 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
 
     std::vector<SpHost> H(nj);
     Stage sg;
+    // GB_SP_KEY_MASK=<mask> in the environment keeps only those bits of the hash keys, so that
+    // distinct monomials share keys: the fallback to the rank path is then exercised by tests
+    unsigned long long keymask = ~0ull;
+    if (const char *km = std::getenv("GB_SP_KEY_MASK")) keymask = std::strtoull(km, nullptr, 0);
+    // GB_SP_TABLE_SLOTS=<power of two> starts every hash dictionary that small (tests of its growth)
+    uint64_t first_slots = 0;
+    if (const char *ts = std::getenv("GB_SP_TABLE_SLOTS")) first_slots = std::strtoull(ts, nullptr, 0);
+    if (first_slots & (first_slots - 1)) first_slots = 0;
     for (int j = 0; j < nj; ++j) {
         SpTask &T = tasks[j];
         gb_system *S = T.S;
@@ -432,6 +665,19 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         h.red_k.alloc(ar, h.cap, st);
         h.red_rank.alloc(ar, h.cap, st);
         GB_CUDA(cudaMemsetAsync(h.bits.p, 0, 4ull * h.W, st));
+        // hash dictionary: at most half full at the expected size (4 x the last step's dictionary)
+        h.hash = !(ctx->flags & GB_CTX_SP_RANKS) && !T.ranks;
+        if (h.hash) {
+            h.hcap = T.hcap ? T.hcap : first_slots ? first_slots
+                            : pow2_at_least(std::min<uint64_t>(2 * h.space + 2,
+                                                               std::max<uint64_t>({1u << 14, 4ull * S->last_ndict,
+                                                                                   2ull * h.ng})));
+            h.htab.alloc(ar, h.hcap, st);
+            h.qslot.alloc(ar, h.cap, st);
+            h.red_slot.alloc(ar, h.cap, st);
+            h.lm_slot.alloc(ar, h.ng, st);
+            GB_CUDA(cudaMemsetAsync(h.htab.p, 0, sizeof(HSlot) * h.hcap, st));
+        }
     }
     std::vector<uint32_t> bm(nj), be(nj);
     int max_tab = 1;
@@ -484,6 +730,18 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         J.red_rank = h.red_rank.p;
         J.lm_rank = h.lm_rank.p;
         J.cnt = cnt.p + j;
+        J.bkey = S->bkey.p;
+        if (h.hash) {
+            J.htab = h.htab.p;
+            J.hmask = (uint32_t)(h.hcap - 1);
+            uint32_t lg = 0;
+            while ((1ull << lg) < h.hcap) ++lg;
+            J.hshift = 64u - lg;
+            J.qslot = h.qslot.p;
+            J.red_slot = h.red_slot.p;
+            J.lm_slot = h.lm_slot.p;
+            J.keymask = keymask;
+        }
     }
     std::memcpy(sg.h.data() + o_jobs, jobs.data(), sizeof(Job) * nj);
     {
@@ -514,6 +772,10 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
             SpHost &h = H[j];
             h.hc = hc[j];
             if (h.hc.q > h.cap || h.hc.red > h.cap) h.overflow = true;
+            if (h.hash && ((h.hc.err & ERR_TABLE_FULL) || 2ull * (h.hc.q + h.npiv_given) > h.hcap)) {
+                h.overflow = true;  // the table is fuller than half: again with more slots
+                h.table_full = true;
+            }
             const bool more = tasks[j].closure && !h.overflow && h.hc.q > f0[j] && jobs[j].nnr > 0;
             buf[2 * j] = f0[j];
             buf[2 * j + 1] = more ? h.hc.q : f0[j];
@@ -538,13 +800,21 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
     std::vector<int> retry_of;
     for (int j = 0; j < nj; ++j) {
         if (!H[j].overflow) continue;
-        if (H[j].cap >= H[j].space) fail(GB_EDEVICE, "frontier queue overflow beyond the monomial space");
         SpTask t;
         t.S = tasks[j].S;
         t.rows = tasks[j].rows;
         t.closure = tasks[j].closure;
         t.nonred = tasks[j].nonred;
-        t.cap = std::min<uint64_t>(H[j].space, 4ull * std::max<uint64_t>(H[j].hc.q, H[j].hc.red));
+        t.ranks = tasks[j].ranks;
+        const bool queue_full = H[j].hc.q > H[j].cap || H[j].hc.red > H[j].cap;
+        if (queue_full && H[j].cap >= H[j].space) fail(GB_EDEVICE, "frontier queue overflow beyond the monomial space");
+        t.cap = queue_full ? std::min<uint64_t>(H[j].space, 4ull * std::max<uint64_t>(H[j].hc.q, H[j].hc.red))
+                           : H[j].cap;
+        if (H[j].table_full) {
+            const uint64_t want = pow2_at_least(4ull * (H[j].hc.q + H[j].npiv_given) + 4);
+            t.hcap = std::max<uint64_t>(want, 4 * H[j].hcap);
+            if (H[j].hcap > 2 * H[j].space + 2) t.ranks = true;  // cannot grow further: exact path
+        }
         retry.push_back(std::move(t));
         retry_of.push_back(j);
     }
@@ -653,6 +923,7 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         s2.upload(ctx, d2);
         const Job *dj = reinterpret_cast<const Job *>(d2.p + o_j2);
         auto P = [&](size_t o) { return reinterpret_cast<const uint32_t *>(d2.p + o); };
+        if (t_q) { k_rank_queue<<<t_q, 256, tab_smem, st>>>(dj, P(o_q), nj); counted(); }
         if (t_w) { k_popc<<<t_w, 256, 0, st>>>(dj, P(o_w), nj); counted(); }
         exclusive_scan(ctx, wcnt.p, wpre.p, tw, st);
         if (t_q) { k_dict_queue<<<t_q, 256, 0, st>>>(dj, P(o_q), nj); counted(); }
@@ -679,6 +950,19 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         for (int j : live) {
             const Job &J = jobs[j];
             const uint32_t *c = hchk + 4 * j;
+            if (c[3] == ERR_KEY_CLASH) {
+                // two monomials of this step share a hash key: the exact rank path builds it again
+                SpTask t;
+                t.S = tasks[j].S;
+                t.rows = tasks[j].rows;
+                t.closure = tasks[j].closure;
+                t.nonred = tasks[j].nonred;
+                t.ranks = true;
+                tasks[j].out.reset();
+                retry.push_back(std::move(t));
+                retry_of.push_back(j);
+                continue;
+            }
             if (c[0] != J.N || c[1] != J.nA || c[2] != J.nnz || c[3])
                 fail(GB_EDEVICE, "symbolic preprocessing: device counts disagree with the plan: columns " +
                                      std::to_string(c[0]) + "/" + std::to_string(J.N) + ", pivots " +
@@ -686,12 +970,29 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
                                      std::to_string(c[2]) + "/" + std::to_string(J.nnz) + ", flags " +
                                      std::to_string(c[3]));
             tasks[j].out->ms_sp = ms;
+            tasks[j].S->last_ndict = J.N;
         }
     }
     if (!retry.empty()) {
         symbolic_preprocess(retry);
-        for (size_t i = 0; i < retry.size(); ++i) tasks[retry_of[i]].out = std::move(retry[i].out);
+        for (size_t i = 0; i < retry.size(); ++i) {
+            tasks[retry_of[i]].out = std::move(retry[i].out);
+            tasks[retry_of[i]].out->sp_redo += 1;
+        }
     }
+}
+
+namespace {
+__global__ void k_basis_keys(const uint4 *__restrict__ mon, unsigned long long *__restrict__ key, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        key[i] = mono_key(mon[i]);
+}
+}  // namespace
+
+void basis_keys(const uint4 *mon, unsigned long long *key, uint64_t n, cudaStream_t st) {
+    if (!n) return;
+    k_basis_keys<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 148 * 8), 256, 0, st>>>(mon, key, n);
+    counted();
 }
 
 }  // namespace gb
