@@ -216,12 +216,16 @@ def run_ours(args) -> None:
     tensor = measure_tensor_core(gb, local) if rank == 0 and not args.no_batch else None
     n13 = measure_sparse_n13(gb, synth, local, pk, runs, graphs=not args.no_graphs) \
         if rank == 0 and not args.no_batch else None
-    deglex = None
+    deglex = wied = None
     if rank == 0 and not args.no_batch:
         try:
             deglex = measure_deglex(gb, synth, ctx)
         except gb.GbError as e:  # reported in the line; the main measurement stands
             deglex = {"error": str(e)}
+        try:
+            wied = measure_wiedemann(gb, synth, local, pk)
+        except gb.GbError as e:
+            wied = {"error": str(e)}
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
              for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_mm", "ms_rref", "ms_update", "ms_pairs",
                        "ms_select", "ms_finish", "ms_wall")}
@@ -254,6 +258,7 @@ def run_ours(args) -> None:
             "tensor_core": tensor,
             "sparse_n13": n13,
             "deglex": deglex,
+            "block_wiedemann": wied,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -344,15 +349,16 @@ def _max_degree(s: dict) -> int:
 
 def measure_batched(gb, synth, ctx, rank: int = 0, world: int = 1) -> list:
     """Two batches, each run plain and batched: the n=8 dense quadratic system modulo the 128
-    largest primes below 2^31, and the 256-system mixed batch without its cubic members in 8 or 9
-    variables (those alone run for seconds to minutes each, beyond a bench line's budget)."""
+    largest primes below 2^31, and the 256-system mixed batch without its 29 cubic members in 9
+    variables (each of those alone runs for 40-60 s, and one builds a matrix above 2^32 nonzeros,
+    beyond the library's 32-bit CSR offsets)."""
     primes = synth.multi_prime_system(synth.largest_primes_below(2 ** 31, 128))
-    mixed = [s for s in synth.mixed_batch(256) if not (_max_degree(s) == 3 and s["n"] >= 8)]
+    mixed = [s for s in synth.mixed_batch(256) if not (_max_degree(s) == 3 and s["n"] >= 9)]
     a = _plain_vs_batched(gb, ctx, primes, rank, world)
     a["workload"] = "n=8 dense quadratic system modulo the 128 largest primes below 2^31"
     b = _plain_vs_batched(gb, ctx, mixed, rank, world)
     b["workload"] = (f"{len(mixed)} of the 256 mixed systems (n ~ U{{5..9}}, degree 2 or 3, 10-40 terms, "
-                     "p=65521): all but the cubic ones with n >= 8")
+                     "p=65521): all but the 29 cubic ones with n = 9")
     return [a, b]
 
 
@@ -494,6 +500,71 @@ def measure_sparse_n13(gb, synth, local: int, pk: dict, timed_runs=None, graphs:
     return res
 
 
+def measure_wiedemann(gb, synth, local: int, pk: dict) -> dict:
+    """The block Wiedemann kernel-vector path (Sec. 9.3) on one F4 step's Macaulay matrix -- the
+    n=10 workload's step 6 -- with b = 32 random vectors: the block Krylov sequence (sparse
+    products with A^T and A), the exact block-Hankel solve on the device, the kernel vectors and
+    their check.  Beside it, the elimination of the same matrix (reduction + RREF of D')."""
+    import torch
+    system = synth.dense_n10(0)
+    ctx = gb.Context(device=local, arena_bytes=8 << 30, keep_step=True)
+    S = gb.System(ctx, system)
+    for _ in range(6):
+        st, stats = S.step()
+    mac, _ = gb.gb_system_last_step(S.h)
+    m = gb.gb_macaulay_export(mac)
+    r, N, nnz = len(m["row_ptr"]) - 1, m["dict_exps"].shape[0], int(m["row_ptr"][-1])
+    rng = np.random.default_rng(20260765)
+    b, p = 32, system["p"]
+    X = rng.integers(0, p, size=(r, b), dtype=np.int64).astype(np.uint32)
+    Z = rng.integers(0, p, size=(r, b), dtype=np.int64).astype(np.uint32)
+    delta = rng.integers(1, p, size=N, dtype=np.int64).astype(np.uint32)
+    gb.gb_block_wiedemann(mac, b, X, Z, delta, want_seq=False)  # warm-up
+    runs = [gb.gb_block_wiedemann(mac, b, X, Z, delta, want_seq=False) for _ in range(3)]
+    best = min(runs, key=lambda x: x["ms_total"])
+    S.close()
+    ctx.close()
+    seq_bytes = 2.0 * nnz * 8 * best["nterms"]  # every sparse product reads each entry (col, val) once
+    gbs = seq_bytes / (best["ms_sequence"] / 1e3) / 1e9
+    return {"workload": "n=10 dense quadratic system, F4 step 6 matrix: %d rows, %d columns, %d nnz; b = 32" % (r, N, nnz),
+            "nullity": stats["nC"] - stats["rank"], "found": best["found"], "verified": best["verified"],
+            "d": best["d"], "sequence_terms": best["nterms"], "hankel_rank": best["hankel_rank"],
+            "ms_total": round(best["ms_total"], 3), "ms_sequence": round(best["ms_sequence"], 3),
+            "ms_hankel": round(best["ms_hankel"], 3), "ms_vectors": round(best["ms_vectors"], 3),
+            "sequence_modp_mac_per_s": 2.0 * nnz * 32 * best["nterms"] / (best["ms_sequence"] / 1e3),
+            "sequence_matrix_gbs": round(gbs, 1), "sequence_frac_of_hbm": round(gbs / pk["hbm_gbs"], 4),
+            "elimination_ms_same_step": round(stats["ms_reduce"] + stats["ms_rref"], 3),
+            "note": "sequence bytes: each of the 2 sparse products per term reads every matrix entry "
+                    "(8 B); the 32-wide vector blocks are L2-resident"}
+
+
+def measure_sp_paths(gb, synth, local: int, pk: dict, paths=("hash", "ranks")) -> dict:
+    """The n=13 run step by step with each symbolic-preprocessing path (the hash dictionary and
+    the rank bitmap): per-step device time of the stage and its share of HBM bandwidth on the
+    algorithmic bytes (8 B per nonzero + row_ptr + 16 B per dictionary monomial)."""
+    system = synth.sparse_n13(0)
+    out = {}
+    for sp in paths:
+        ctx = gb.Context(device=local, arena_bytes=48 << 30, sp=sp)
+        for _ in range(2):  # the first run warms up; the second is reported
+            S = gb.System(ctx, system)
+            steps = []
+            while True:
+                st, stats = S.step()
+                if st != gb.GB_OK:
+                    break
+                steps.append(stats)
+            S.close()
+        ctx.close()
+        rows = []
+        for x in steps:
+            alg = 8.0 * x["nnz"] + 4.0 * (x["nrows"] + 1) + 16.0 * x["ndict"]
+            rows.append({"step": x["step"], "nnz": x["nnz"], "ndict": x["ndict"], "ms_sp": round(x["ms_sp"], 3),
+                         "frac": round(alg / (x["ms_sp"] / 1e3) / 1e9 / pk["hbm_gbs"], 4), "sp_redo": x["sp_redo"]})
+        out[sp] = {"ms_sp_total": round(sum(x["ms_sp"] for x in steps), 3), "steps": rows}
+    return out
+
+
 def measure_deglex(gb, synth, ctx) -> dict:
     """The same n=10 system in the deglex order: one warm-up run, then the best of three full F4
     runs to the reduced basis, timed with CUDA events on the context's stream around the run."""
@@ -588,7 +659,9 @@ def main() -> None:
     ap.add_argument("--no-tune", action="store_true",
                     help="run the workload on the shape rules, without gb_autotune before the timed region")
     ap.add_argument("--arena-gb", type=int, default=48, help="device arena of the context (GiB)")
-    ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10"], default=None,
+    ap.add_argument("--sp", choices=["hash", "ranks", "both"], default="both",
+                    help="--only sp_compare: the symbolic-preprocessing path(s) to run")
+    ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10", "wiedemann", "sp_compare"], default=None,
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
@@ -599,6 +672,11 @@ def main() -> None:
         torch.cuda.set_device(0)
         if args.only == "tensor":
             print(json.dumps({"tensor_core": measure_tensor_core(gb, 0)}))
+        elif args.only == "sp_compare":
+            paths = ("hash", "ranks") if args.sp == "both" else (args.sp,)
+            print(json.dumps({"sp_paths": measure_sp_paths(gb, synth, 0, peaks(), paths)}))
+        elif args.only == "wiedemann":
+            print(json.dumps({"block_wiedemann": measure_wiedemann(gb, synth, 0, peaks())}))
         elif args.only == "dense_n10":
             ctx = gb.Context(device=0, arena_bytes=4 << 30, graphs=not args.no_graphs)
             flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda:0")

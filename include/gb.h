@@ -77,10 +77,10 @@ typedef struct {
                             GB_CTX_NO_GRAPHS: launch the rounds of the echelon form of D' one
                             by one from the host instead of as one CUDA graph whose loop runs
                             on the device (same results);
-                            GB_CTX_SP_RANKS: symbolic preprocessing keys every term by its dense
-                            rank in a bitmap (the exact path the hash dictionary falls back to
-                            when two monomials share a hash key) instead of the hash dictionary
-                            (same results). */
+                            GB_CTX_SP_HASH: symbolic preprocessing setifies through a hash
+                            dictionary keyed by an additive monomial key instead of ranking every
+                            term into a bitmap; a key shared by two monomials is detected and the
+                            step rebuilt on the rank path (same results). */
     uint32_t reserved;
 } gb_ctx_opts;
 
@@ -88,7 +88,7 @@ typedef struct {
 #define GB_CTX_REDUCE_SPARSE 2u
 #define GB_CTX_REDUCE_DENSE 4u
 #define GB_CTX_NO_GRAPHS 8u
-#define GB_CTX_SP_RANKS 16u
+#define GB_CTX_SP_HASH 16u
 
 /* A polynomial system on the host: polynomial i has the terms [poly_off[i], poly_off[i+1]). */
 typedef struct {
@@ -132,9 +132,9 @@ typedef struct {
 typedef struct {
     uint32_t step, degree, npairs, nrows, ndict, npivot, nC, nb, rank, nbasis;
     uint32_t closure_rounds;
-    uint32_t sp_redo;    /* times the step's symbolic preprocessing ran again: its hash dictionary
-                            needed more slots, or two monomials shared a hash key (then the exact
-                            rank path built it) */
+    uint32_t sp_redo;    /* times the step's symbolic preprocessing ran again: its frontier queue
+                            or (GB_CTX_SP_HASH) hash dictionary needed more room, or two monomials
+                            shared a hash key (then the rank path built it) */
     uint64_t nnz;
     uint64_t axpy_rows;  /* pivot rows applied by the sparse reduction (eq. 8.1 row updates) */
     uint64_t axpy_fma;   /* modular multiply-adds a <- a + b c of the sparse reduction */

@@ -27,7 +27,7 @@ GB_CTX_KEEP_STEP = 1
 GB_CTX_REDUCE_SPARSE = 2
 GB_CTX_REDUCE_DENSE = 4
 GB_CTX_NO_GRAPHS = 8
-GB_CTX_SP_RANKS = 16
+GB_CTX_SP_HASH = 16
 GB_GREVLEX, GB_DEGLEX = 0, 1  # gb_order
 # gb_modp_op
 (GB_MODP_REDUCE64, GB_MODP_REDUCE32, GB_MODP_MULADD, GB_MODP_REDC, GB_MODP_TO_MONT, GB_MODP_MONT_MUL,
@@ -428,7 +428,7 @@ def gb_block_wiedemann(mac: int, b: int, X: np.ndarray, Z: np.ndarray, delta: np
     Z = np.ascontiguousarray(Z, dtype=np.uint32)
     delta = np.ascontiguousarray(delta, dtype=np.uint32)
     r = X.shape[0]
-    d = (r + b - 1) // b + 1
+    d = (r + max(b, 1) - 1) // max(b, 1) + 1  # b out of range is refused by the library
     seq = np.zeros((2 * d, b, b), np.uint32) if want_seq else None
     wcap = b if wcap is None else wcap
     W = np.zeros((max(wcap, 1), r), np.uint32)
@@ -468,12 +468,12 @@ class Context:
     """A library context whose device arena is a torch tensor on `device`."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 2 << 30, keep_step: bool = False,
-                 reduce: str = "auto", stream=None, graphs: bool = True, sp: str = "hash"):
+                 reduce: str = "auto", stream=None, graphs: bool = True, sp: str = "ranks"):
         """reduce: "auto" (per matrix by shape), "sparse" or "dense" (see GB_CTX_REDUCE_*).
         stream: a torch.cuda.Stream the context runs on (default: a stream of its own).
         graphs: False launches the echelon-form rounds one by one (GB_CTX_NO_GRAPHS).
-        sp: "hash" (the hash dictionary) or "ranks" (every term keyed by its dense rank,
-        GB_CTX_SP_RANKS) for symbolic preprocessing."""
+        sp: "ranks" (every term ranked into a bitmap) or "hash" (the hash dictionary,
+        GB_CTX_SP_HASH) for symbolic preprocessing."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: this library has no CPU path")
@@ -484,9 +484,9 @@ class Context:
                                                             "dense": GB_CTX_REDUCE_DENSE}[reduce]
         if not graphs:
             flags |= GB_CTX_NO_GRAPHS
-        if sp == "ranks":
-            flags |= GB_CTX_SP_RANKS
-        elif sp != "hash":
+        if sp == "hash":
+            flags |= GB_CTX_SP_HASH
+        elif sp != "ranks":
             raise ValueError("sp must be 'hash' or 'ranks'")
         self.stream = stream
         self.h = gb_ctx_create(device, stream.cuda_stream if stream is not None else None,

@@ -551,6 +551,19 @@ gb_status gb_reduce_rows_noalloc(uint32_t p, uint32_t ndict, uint32_t npivot, ui
     GB_API_END
 }
 
+gb_status gb_block_wiedemann(const gb_macaulay *mac, uint32_t b, const uint32_t *X, const uint32_t *Z,
+                             const uint32_t *delta, uint32_t *seq, uint32_t *W, uint32_t wcap,
+                             gb_krylov_stats *stats) {
+    GB_API_BEGIN
+    if (!mac || !mac->sys) fail(GB_EINVAL, "null matrix handle");
+    gb_ctx *ctx = mac->sys->ctx;
+    std::lock_guard<std::recursive_mutex> g(ctx->mu);
+    use_device(ctx);
+    block_wiedemann(mac, b, X, Z, delta, seq, W, wcap, stats);
+    return GB_OK;
+    GB_API_END
+}
+
 gb_status gb_modp_apply(gb_modp_op op, uint32_t p, uint64_t n, uint32_t window, const uint32_t *a,
                         const uint32_t *b, const uint32_t *c, uint32_t *out, void *stream) {
     GB_API_BEGIN

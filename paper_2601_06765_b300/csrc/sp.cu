@@ -261,7 +261,9 @@ __device__ __forceinline__ void expand_terms(uint4 t, uint32_t off, uint32_t j0,
     }
 }
 
-// Pass 1: leading monomials of the given rows (tail rows have none); 256 rows per block
+// Pass 1: leading monomials of the given rows (tail rows have none); 256 rows per block.
+// HASH: the hash-dictionary path (every job of a launch takes the same path)
+template <bool HASH>
 __global__ void k_mark_given(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     extern __shared__ uint32_t tab[];
     const int jb = job_of_block(bstart, nj);
@@ -277,7 +279,7 @@ __global__ void k_mark_given(const Job *__restrict__ jobs, const uint32_t *__res
     const uint32_t r = mono_rank(m, tab, J.n, J.sh, J.deglex != 0);
     atomicOr(&J.bits[r >> 5], 1u << (r & 31));
     J.lm_rank[i] = r;
-    if (J.htab) {  // the leading monomials start in the dictionary (Done): never frontier items
+    if constexpr (HASH) {  // the leading monomials start in the dictionary (Done): never frontier items
         bool isnew = false;
         const uint32_t s = h_insert(tag_of(mono_key(J.gt[i]) + J.bkey[J.boff[J.gk[i]]], J), J, isnew);
         if (isnew) J.htab[s].mon = m;
@@ -286,26 +288,28 @@ __global__ void k_mark_given(const Job *__restrict__ jobs, const uint32_t *__res
 }
 
 // Pass 2: expand the given rows (warp per row)
+template <bool HASH>
 __global__ void k_expand_given(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     extern __shared__ uint32_t tab[];
     const int jb = job_of_block(bstart, nj);
     const Job &J = jobs[jb];
-    load_tab(tab, J);
+    if constexpr (!HASH) load_tab(tab, J);  // the hash path ranks nothing here (no table in shared memory)
     const uint32_t row = (blockIdx.x - bstart[jb]) * WPB + (threadIdx.x >> 5);
     if (row >= J.ng) return;  // whole warp leaves together
     const uint32_t k = J.gk[row];
     const uint32_t j0 = (J.gf[row] & FLAG_TAIL) ? 1u : 0u;
-    if (J.htab) expand_terms_hash(J.gt[row], mono_key(J.gt[row]), J.boff[k], j0, J.blen[k], J);
+    if constexpr (HASH) expand_terms_hash(J.gt[row], mono_key(J.gt[row]), J.boff[k], j0, J.blen[k], J);
     else expand_terms(J.gt[row], J.boff[k], j0, J.blen[k], J, tab);
 }
 
 // Pass 3: one closure round over each job's frontier items [range[2j], range[2j+1]) (warp per item)
+template <bool HASH>
 __global__ void k_closure(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj,
                           const uint32_t *__restrict__ range) {
     extern __shared__ uint32_t tab[];
     const int jb = job_of_block(bstart, nj);
     const Job &J = jobs[jb];
-    load_tab(tab, J);
+    if constexpr (!HASH) load_tab(tab, J);  // the hash path ranks nothing here (no table in shared memory)
     const uint32_t item = range[2 * jb] + (blockIdx.x - bstart[jb]) * WPB + (threadIdx.x >> 5);
     if (item >= range[2 * jb + 1]) return;
     const int lane = threadIdx.x & 31;
@@ -332,12 +336,12 @@ __global__ void k_closure(const Job *__restrict__ jobs, const uint32_t *__restri
         if (pos < J.cap) {
             J.red_t[pos] = t;
             J.red_k[pos] = (uint32_t)g;
-            if (J.htab) J.red_slot[pos] = J.qslot[item];
+            if constexpr (HASH) J.red_slot[pos] = J.qslot[item];
             else J.red_rank[pos] = J.qrank[item];
         }
         atomicAdd(&J.cnt->red_nnz, (unsigned long long)len);
     }
-    if (J.htab) expand_terms_hash(t, mono_key(t), J.boff[g], 1u, len, J);
+    if constexpr (HASH) expand_terms_hash(t, mono_key(t), J.boff[g], 1u, len, J);
     else expand_terms(t, J.boff[g], 1u, len, J, tab);
 }
 
@@ -446,11 +450,12 @@ __global__ void k_row_ptr(const Job *__restrict__ jobs, const uint32_t *__restri
 }
 
 // Pass 6: fill (warp per row)
+template <bool HASH>
 __global__ void k_fill(const Job *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
     extern __shared__ uint32_t tab[];
     const int jb = job_of_block(bstart, nj);
     const Job &J = jobs[jb];
-    load_tab(tab, J);
+    if constexpr (!HASH) load_tab(tab, J);  // the hash path ranks nothing here (no table in shared memory)
     const uint32_t row = (blockIdx.x - bstart[jb]) * WPB + (threadIdx.x >> 5);
     if (row >= J.nrows) return;
     const int lane = threadIdx.x & 31;
@@ -462,19 +467,21 @@ __global__ void k_fill(const Job *__restrict__ jobs, const uint32_t *__restrict_
         if (lane == 0) atomicOr(&J.cnt->err, 32u);
         return;
     }
-    if (J.htab) {
-        // hash path: key, slot, and a comparison of the slot's monomial with the term's
+    if constexpr (HASH) {
+        // hash path: key, slot, and a comparison of the slot's monomial with the term's.  Every
+        // load of a lane's two terms is issued before any is used: their keys, monomials and
+        // coefficients, then each home slot's 32 bytes (key, column, monomial) in two 16-byte
+        // reads; a key or monomial mismatch takes the probing path.  Two terms per lane keep the
+        // kernel near 64 registers, so that eight warps per block and four blocks per SM fit.
+        constexpr int FH = 2;
         const unsigned long long kt = mono_key(t);
         bool clash = false;
-        for (uint32_t j0 = lane; j0 < len; j0 += 4 * 32) {
-            // every load of the four terms is issued before any is used: their keys, monomials
-            // and coefficients, then each home slot's 32 bytes (key, column, monomial) in two
-            // 16-byte reads; a key or monomial mismatch takes the probing path
-            unsigned long long tg[4];
-            uint32_t v[4], hs[4];
-            uint4 m[4], s0[4], s1[4];
+        for (uint32_t j0 = lane; j0 < len; j0 += FH * 32) {
+            unsigned long long tg[FH];
+            uint32_t v[FH], hs[FH];
+            uint4 m[FH], s0[FH], s1[FH];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < FH; ++u) {
                 const uint32_t j = j0 + 32u * u;
                 tg[u] = 0ull;
                 if (j < len) {
@@ -485,7 +492,7 @@ __global__ void k_fill(const Job *__restrict__ jobs, const uint32_t *__restrict_
                 hs[u] = home_slot(tg[u], J);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < FH; ++u) {
                 if (tg[u]) {
                     const uint4 *sp = reinterpret_cast<const uint4 *>(J.htab + hs[u]);
                     s0[u] = __ldg(sp);
@@ -493,7 +500,7 @@ __global__ void k_fill(const Job *__restrict__ jobs, const uint32_t *__restrict_
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < FH; ++u) {
                 const uint32_t j = j0 + 32u * u;
                 if (j < len) {
                     uint32_t c = 0xFFFFFFFFu;
@@ -666,7 +673,7 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         h.red_rank.alloc(ar, h.cap, st);
         GB_CUDA(cudaMemsetAsync(h.bits.p, 0, 4ull * h.W, st));
         // hash dictionary: at most half full at the expected size (4 x the last step's dictionary)
-        h.hash = !(ctx->flags & GB_CTX_SP_RANKS) && !T.ranks;
+        h.hash = (ctx->flags & GB_CTX_SP_HASH) && !T.ranks;
         if (h.hash) {
             h.hcap = T.hcap ? T.hcap : first_slots ? first_slots
                             : pow2_at_least(std::min<uint64_t>(2 * h.space + 2,
@@ -679,6 +686,10 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
             GB_CUDA(cudaMemsetAsync(h.htab.p, 0, sizeof(HSlot) * h.hcap, st));
         }
     }
+    // every job of one call takes the same path, so that each launch is one kernel instantiation
+    const bool hash = H[0].hash;
+    for (int j = 1; j < nj; ++j)
+        if (H[j].hash != hash) fail(GB_EDEVICE, "symbolic preprocessing: jobs of one call on different key paths");
     std::vector<uint32_t> bm(nj), be(nj);
     int max_tab = 1;
     for (int j = 0; j < nj; ++j) {
@@ -752,9 +763,11 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
     const Job *djobs = reinterpret_cast<const Job *>(dptr(o_jobs));
     const size_t tab_smem = 4ull * max_tab;
     if (tbm) {
-        k_mark_given<<<tbm, 256, tab_smem, st>>>(djobs, reinterpret_cast<const uint32_t *>(dptr(o_bm)), nj);
+        if (hash) k_mark_given<true><<<tbm, 256, tab_smem, st>>>(djobs, reinterpret_cast<const uint32_t *>(dptr(o_bm)), nj);
+        else k_mark_given<false><<<tbm, 256, tab_smem, st>>>(djobs, reinterpret_cast<const uint32_t *>(dptr(o_bm)), nj);
         counted();
-        k_expand_given<<<tbe, 32 * WPB, tab_smem, st>>>(djobs, reinterpret_cast<const uint32_t *>(dptr(o_be)), nj);
+        if (hash) k_expand_given<true><<<tbe, 32 * WPB, 0, st>>>(djobs, reinterpret_cast<const uint32_t *>(dptr(o_be)), nj);
+        else k_expand_given<false><<<tbe, 32 * WPB, tab_smem, st>>>(djobs, reinterpret_cast<const uint32_t *>(dptr(o_be)), nj);
         counted();
     }
 
@@ -791,7 +804,8 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         uint32_t *hb = reinterpret_cast<uint32_t *>(hc);  // the counters have been consumed
         std::memcpy(hb, buf.data(), 4 * buf.size());
         GB_CUDA(cudaMemcpyAsync(dround.p, hb, 4 * buf.size(), cudaMemcpyHostToDevice, st));
-        k_closure<<<total, 32 * WPB, tab_smem, st>>>(djobs, dround.p + 2 * nj, nj, dround.p);
+        if (hash) k_closure<true><<<total, 32 * WPB, 0, st>>>(djobs, dround.p + 2 * nj, nj, dround.p);
+        else k_closure<false><<<total, 32 * WPB, tab_smem, st>>>(djobs, dround.p + 2 * nj, nj, dround.p);
         counted();
     }
 
@@ -935,7 +949,11 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         if (t_rows) { k_row_len<<<t_rows, 256, 0, st>>>(dj, P(o_rows), nj); counted(); }
         exclusive_scan(ctx, lens.p, lscan.p, tr, st);
         if (t_rp) { k_row_ptr<<<t_rp, 256, 0, st>>>(dj, P(o_rp), nj); counted(); }
-        if (t_fill) { k_fill<<<t_fill, 32 * WPB, tab_smem, st>>>(dj, P(o_fill), nj); counted(); }
+        if (t_fill) {
+            if (hash) k_fill<true><<<t_fill, 32 * WPB, 0, st>>>(dj, P(o_fill), nj);
+            else k_fill<false><<<t_fill, 32 * WPB, tab_smem, st>>>(dj, P(o_fill), nj);
+            counted();
+        }
         GB_CUDA(cudaEventRecord(ctx->ev[1], st));
         // consistency of every plan with the host's counts (one small read-back)
         DBuf<uint32_t> chk;
@@ -973,11 +991,21 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
             tasks[j].S->last_ndict = J.N;
         }
     }
-    if (!retry.empty()) {
-        symbolic_preprocess(retry);
+    // again, with more room or on the rank path: one call per path
+    for (int ranks = 0; ranks < 2; ++ranks) {
+        std::vector<SpTask> again;
+        std::vector<int> again_of;
         for (size_t i = 0; i < retry.size(); ++i) {
-            tasks[retry_of[i]].out = std::move(retry[i].out);
-            tasks[retry_of[i]].out->sp_redo += 1;
+            const bool on_ranks = retry[i].ranks || !(ctx->flags & GB_CTX_SP_HASH);
+            if (on_ranks != (ranks == 1)) continue;
+            again.push_back(std::move(retry[i]));
+            again_of.push_back(retry_of[i]);
+        }
+        if (again.empty()) continue;
+        symbolic_preprocess(again);
+        for (size_t i = 0; i < again.size(); ++i) {
+            tasks[again_of[i]].out = std::move(again[i].out);
+            tasks[again_of[i]].out->sp_redo += 1;
         }
     }
 }

@@ -134,3 +134,27 @@ def test_server_poll_reports_busy_and_unknown(ctx):
             gb.gb_server_poll(srv, 987654321)
     finally:
         gb.gb_server_destroy(srv)
+
+
+def test_cubic_n8_member_in_a_batch():
+    """A cubic member with eight variables (mixed batch index 47; its steps reach degree 19 and
+    10^8 nonzeros): its first five F4 steps equal the oracle's step for step, and its reduced
+    basis is the same alone and inside a batch with two small members."""
+    from tests.test_gpu_parity import run_parity
+    mixed = synth.mixed_batch(256)
+    cubic = mixed[47]
+    assert cubic["n"] == 8 and int(cubic["exps"].reshape(-1, 8).sum(axis=1).max()) == 3
+    with gb.Context(arena_bytes=16 << 30, keep_step=True) as c:
+        assert run_parity(c, cubic, max_steps=5, final=False) == 5
+    with gb.Context(arena_bytes=16 << 30) as c:
+        alone = _alone(c, cubic)
+        systems = [cubic, mixed[1], mixed[3]]
+        handles = [gb.gb_system_create(c.h, s) for s in systems]
+        try:
+            gb.gb_batch_groebner(c.h, handles)
+            assert gb.basis_terms(*gb.gb_basis_export(handles[0], 8, True)) == alone
+            for h, s in zip(handles[1:], systems[1:]):
+                assert gb.basis_terms(*gb.gb_basis_export(h, s["n"], True)) == oracle.groebner(s)
+        finally:
+            for h in handles:
+                gb.gb_system_destroy(h)

@@ -16,14 +16,14 @@ from paper_2601_06765_b300 import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=["sparse", "dense", "sparse-ranks"])
+@pytest.fixture(scope="module", params=["sparse", "dense", "sparse-hash"])
 def ctx(request):
     """Every case runs with each reduction schedule forced: the sparse row-by-row reduction and
     the dense blocked elimination on the tensor cores must both reproduce the unique D'.  The
-    symbolic preprocessing runs through the hash dictionary, and once more (sparse-ranks) through
-    the exact rank path the hash dictionary falls back to: both must build the same T and Pi."""
+    symbolic preprocessing ranks every term into a bitmap, and once more (sparse-hash) goes
+    through the hash dictionary: both must build the same T and Pi."""
     reduce, _, sp = request.param.partition("-")
-    c = gb.Context(arena_bytes=6 << 30, keep_step=True, reduce=reduce, sp=sp or "hash")
+    c = gb.Context(arena_bytes=6 << 30, keep_step=True, reduce=reduce, sp=sp or "ranks")
     yield c
     c.close()
 

@@ -1,6 +1,7 @@
-"""The hash dictionary of symbolic preprocessing and its two exits, against the oracle bit for bit.
+"""The hash dictionary of symbolic preprocessing (GB_CTX_SP_HASH) and its two exits, against the
+oracle bit for bit.
 
-The fast path keys every term by an additive 64-bit monomial key and checks every lookup against
+The hash path keys every term by an additive 64-bit monomial key and checks every lookup against
 the stored monomial.  Two monomials sharing a key (forced here by keeping only a few key bits,
 GB_SP_KEY_MASK) must send the step through the exact rank path, and a table that fills up (forced
 by starting it with 64 slots, GB_SP_TABLE_SLOTS) must grow; either way every dictionary, CSR plan,
@@ -22,7 +23,7 @@ SYSTEMS = [("dense_n6", synth.dense_n6(0)),
 
 
 def _redo_counts(system, **ctx_kw):
-    with gb.Context(arena_bytes=2 << 30, **ctx_kw) as ctx, gb.System(ctx, system) as S:
+    with gb.Context(arena_bytes=2 << 30, sp="hash", **ctx_kw) as ctx, gb.System(ctx, system) as S:
         out = []
         while True:
             st, stats = S.step()
@@ -43,7 +44,7 @@ def test_shared_keys_fall_back_to_the_rank_path(monkeypatch, mask, name, system)
     monkeypatch.setenv("GB_SP_KEY_MASK", mask)
     redo = _redo_counts(system)
     assert any(r > 0 for r in redo)  # the clash was seen and the step built again
-    with gb.Context(arena_bytes=2 << 30, keep_step=True) as ctx:
+    with gb.Context(arena_bytes=2 << 30, keep_step=True, sp="hash") as ctx:
         assert run_parity(ctx, system) > 0
 
 
@@ -52,7 +53,7 @@ def test_a_full_table_grows(monkeypatch, name, system):
     monkeypatch.setenv("GB_SP_TABLE_SLOTS", "64")
     redo = _redo_counts(system)
     assert any(r > 0 for r in redo)
-    with gb.Context(arena_bytes=2 << 30, keep_step=True) as ctx:
+    with gb.Context(arena_bytes=2 << 30, keep_step=True, sp="hash") as ctx:
         assert run_parity(ctx, system) > 0
 
 
