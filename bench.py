@@ -35,6 +35,7 @@ WORKLOAD = ("n=13, m=13 sparse random quadratics (30 of the 105 monomials of deg
             "p=2^31-1, grevlex, SplitMix64 seed 20260765; one full F4 run to the reduced basis per step")
 WORKLOAD_N10 = ("n=10, m=10 dense random quadratics (all 66 monomials of degree <= 2), p=65521, "
                 "grevlex, SplitMix64 seed 20260765; one full F4 run to the reduced basis")
+SERVE_FINISH_MIN = 1    # final reductions of served systems as soon as they are ready
 CPU_SAMPLE_STEPS = 5   # the oracle's first 5 F4 steps of the n=13 run: about 30 s on one core
 REF_SAMPLE_STEPS = 4   # the reference arm's per-step sample: the first 4 F4 steps, about 3 s
 
@@ -362,55 +363,85 @@ def measure_batched(gb, synth, ctx, rank: int = 0, world: int = 1) -> list:
     return [a, b]
 
 
-def measure_served(gb, synth, ctx, count: int = 300, slots: int = 64,
-                   loads=(0.5, 0.8, 0.95)) -> dict:
-    """Poisson streams of served requests (n ~ U{5..11}, 20-66 terms, p = 65521 or 2^31-1) through
-    gb_server_* at fractions of the batched saturation rate; latency = completion - arrival.  The
-    plain rate is the same requests run one at a time through gb_groebner."""
+def _serve(gb, ctx, reqs, arrivals, slots: int, finish_min: int = 0) -> dict:
+    """Submit each request at its arrival time (seconds from the start; all at 0 for a standing
+    queue), poll until every one is back; latency = completion - arrival."""
     import numpy as _np
+    count = len(reqs)
+    srv = gb.gb_server_create(ctx.h, 150 << 30, slots, finish_min)
+    pending, lat, done_at = {}, [], []
+    start = time.perf_counter()
+    nxt = 0
+    while nxt < count or pending:
+        now = time.perf_counter() - start
+        while nxt < count and arrivals[nxt] <= now:
+            pending[gb.gb_server_submit(srv, gb.gb_system_create(ctx.h, reqs[nxt]))] = arrivals[nxt]
+            nxt += 1
+        for t in list(pending):
+            h, st = gb.gb_server_poll(srv, t)
+            if h is not None:
+                fin = time.perf_counter() - start
+                lat.append(fin - pending.pop(t))
+                done_at.append(fin)
+                gb.gb_system_destroy(h)
+        time.sleep(0.0005)
+    wall = time.perf_counter() - start
+    stats = gb.gb_server_stats_get(srv)
+    gb.gb_server_destroy(srv)
+    lat_ms = _np.array(lat) * 1e3
+    done_at = _np.sort(_np.array(done_at))
+    # throughput while the stream is on: completions between the 10th and 90th percentile of the
+    # completion times, free of the start-up and of the drain after the last arrival
+    lo, hi = done_at[int(0.1 * count)], done_at[int(0.9 * count) - 1]
+    steady = (int(0.9 * count) - 1 - int(0.1 * count)) / (hi - lo) if hi > lo else None
+    return {"systems_per_s": round(count / wall, 2), "steady_systems_per_s": round(steady, 2) if steady else None,
+            "p50_ms": round(float(_np.percentile(lat_ms, 50)), 2), "p99_ms": round(float(_np.percentile(lat_ms, 99)), 2),
+            "iterations": stats["iterations"],
+            "mean_systems_per_iteration": round(stats["system_steps"] / max(stats["iterations"], 1), 1),
+            "busy_frac": round(stats["busy_ms"] / 1e3 / wall, 3),
+            "finish_passes": stats["finish_passes"],
+            "finish_share_of_busy": round(stats["finish_ms"] / max(stats["busy_ms"], 1e-9), 3)}
+
+
+def measure_served(gb, synth, ctx, count: int = 2000, slots: int = 64,
+                   loads=(0.5, 0.8, 0.95), finish_min: int = SERVE_FINISH_MIN, variants=()) -> dict:
+    """Poisson streams of served requests (n ~ U{5..11}, 20-66 terms, p = 65521 or 2^31-1) through
+    gb_server_*.  Saturation is the server's own throughput with every request queued at once (a
+    standing queue: continuous admission into free slots, no idle slot); the streams then arrive
+    at 0.5, 0.8 and 0.95 of it.  The plain rate is requests run one at a time through
+    gb_groebner (the first 500), and the lockstep rate a batch of `slots` requests started
+    together (the best case of lockstep batching, for reference)."""
     reqs = [synth.served_request(i) for i in range(count)]
-    # plain: one system at a time
     t0 = time.perf_counter()
-    for s in reqs:
+    nplain = min(count, 500)
+    for s in reqs[:nplain]:
         h = gb.gb_system_create(ctx.h, s)
         gb.gb_groebner(h)
         gb.gb_system_destroy(h)
-    plain = count / (time.perf_counter() - t0)
-    # saturation: a lockstep batch of as many requests as the server has slots
+    plain = nplain / (time.perf_counter() - t0)
     hs = [gb.gb_system_create(ctx.h, s) for s in reqs[:slots]]
     t0 = time.perf_counter()
     gb.gb_batch_groebner(ctx.h, hs)
-    sat = len(hs) / (time.perf_counter() - t0)
+    lockstep = len(hs) / (time.perf_counter() - t0)
     for h in hs:
         gb.gb_system_destroy(h)
+    tried = {}
+    for fm in variants:  # saturation under other final-reduction policies, for comparison
+        tried[fm] = _serve(gb, ctx, reqs, [0.0] * count, slots, fm)
+    sat_run = _serve(gb, ctx, reqs, [0.0] * count, slots, finish_min)
+    sat = sat_run["steady_systems_per_s"] or sat_run["systems_per_s"]
     runs = []
     for load in loads:
         rate = load * sat
-        arrivals = synth.poisson_arrivals(count, rate)
-        srv = gb.gb_server_create(ctx.h, 150 << 30, slots)
-        pending, lat = {}, []
-        start = time.perf_counter()
-        nxt = 0
-        while nxt < count or pending:
-            now = time.perf_counter() - start
-            while nxt < count and arrivals[nxt] <= now:
-                pending[gb.gb_server_submit(srv, gb.gb_system_create(ctx.h, reqs[nxt]))] = arrivals[nxt]
-                nxt += 1
-            for t in list(pending):
-                h, st = gb.gb_server_poll(srv, t)
-                if h is not None:
-                    lat.append(time.perf_counter() - start - pending.pop(t))
-                    gb.gb_system_destroy(h)
-            time.sleep(0.0005)
-        wall = time.perf_counter() - start
-        gb.gb_server_destroy(srv)
-        lat_ms = _np.array(lat) * 1e3
-        runs.append({"load": load, "rate_per_s": round(rate, 2), "systems_per_s": round(count / wall, 2),
-                     "p50_ms": round(float(_np.percentile(lat_ms, 50)), 2),
-                     "p99_ms": round(float(_np.percentile(lat_ms, 99)), 2)})
-    return {"workload": f"{count} Poisson requests per load, n ~ U{{5..11}}, 20-66 terms, "
-                        "p in {65521, 2^31-1}",
-            "plain_systems_per_s": round(plain, 2), "saturation_systems_per_s": round(sat, 2),
+        r = _serve(gb, ctx, reqs, synth.poisson_arrivals(count, rate), slots, finish_min)
+        r.update({"load": load, "offered_per_s": round(rate, 2),
+                  "delivered_over_offered": round((r["steady_systems_per_s"] or r["systems_per_s"]) / rate, 3)})
+        runs.append(r)
+    return {"workload": f"{count} Poisson requests per load, n ~ U{{5..11}}, 20-66 terms, p in {{65521, 2^31-1}}",
+            "plain_systems_per_s": round(plain, 2), "lockstep_batch_systems_per_s": round(lockstep, 2),
+            "saturation_systems_per_s": round(sat, 2), "saturation_run": sat_run,
+            "finish_min": finish_min,
+            "saturation_other_finish_min": {str(k): v["steady_systems_per_s"] for k, v in tried.items()},
             "hbm_cap_bytes": 150 << 30, "slots": slots, "loads": runs}
 
 
@@ -661,7 +692,9 @@ def main() -> None:
     ap.add_argument("--arena-gb", type=int, default=48, help="device arena of the context (GiB)")
     ap.add_argument("--sp", choices=["hash", "ranks", "both"], default="both",
                     help="--only sp_compare: the symbolic-preprocessing path(s) to run")
-    ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10", "wiedemann", "sp_compare"], default=None,
+    ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10", "wiedemann", "sp_compare", "served",
+                                       "headline"],
+                    default=None,
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
@@ -675,10 +708,27 @@ def main() -> None:
         elif args.only == "sp_compare":
             paths = ("hash", "ranks") if args.sp == "both" else (args.sp,)
             print(json.dumps({"sp_paths": measure_sp_paths(gb, synth, 0, peaks(), paths)}))
+        elif args.only == "headline":
+            # one run of the headline workload as the timed steps run it (tuned context), for the
+            # per-kernel launch list
+            system = synth.sparse_n13(0)
+            ctx = gb.Context(device=0, arena_bytes=args.arena_gb << 30, graphs=not args.no_graphs)
+            if not args.no_tune:
+                th = gb.gb_system_create(ctx.h, system)
+                gb.gb_autotune(ctx.h, [th])
+                gb.gb_system_destroy(th)
+            with gb.System(ctx, system) as S:
+                r = S.groebner()
+            print(json.dumps({"headline_run": {k: r[k] for k in ("steps", "nnz_steps", "ms_wall", "ms_mm")}}))
+            ctx.close()
+        elif args.only == "served":
+            ctx = gb.Context(device=0, arena_bytes=args.arena_gb << 30)
+            print(json.dumps({"served": measure_served(gb, synth, ctx, variants=(8, 16))}))
+            ctx.close()
         elif args.only == "wiedemann":
             print(json.dumps({"block_wiedemann": measure_wiedemann(gb, synth, 0, peaks())}))
         elif args.only == "dense_n10":
-            ctx = gb.Context(device=0, arena_bytes=4 << 30, graphs=not args.no_graphs)
+            ctx = gb.Context(device=0, arena_bytes=min(args.arena_gb, 4) << 30, graphs=not args.no_graphs)
             flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda:0")
             print(json.dumps({"dense_n10": measure_dense_n10(gb, synth, ctx, flush, peaks(), args)}))
             ctx.close()

@@ -250,7 +250,10 @@ gb_status gb_batch_groebner(gb_ctx *ctx, uint32_t count, gb_system *const *syste
 typedef struct {
     size_t hbm_cap_bytes;  /* admission cap on the summed device footprint of admitted systems */
     uint32_t max_slots;    /* systems running at once (0: 64) */
-    uint32_t reserved;
+    uint32_t finish_min;   /* systems out of pairs wait for their final reduction until at least
+                              this many are ready, for at most 4 iterations, or until no other
+                              system takes a step (0 or 1: at once); one final-reduction pass then
+                              serves them all */
 } gb_server_opts;
 
 /* A continuous-batching server: one scheduler thread runs lockstep iterations (as in
@@ -274,6 +277,8 @@ typedef struct {
     double busy_ms;         /* wall time inside iterations */
     uint32_t max_running;   /* most systems in one iteration */
     uint32_t queued;        /* systems waiting for admission now */
+    uint64_t finish_passes; /* final-reduction passes run */
+    double finish_ms;       /* wall time inside them (a part of busy_ms) */
 } gb_server_stats;
 
 /* Counters of the server since its creation. */

@@ -16,7 +16,8 @@
 #include "internal.hpp"
 
 namespace gb {
-void advance(const std::vector<gb_system *> &Ss);
+void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *stats);
+void finish_batch(const std::vector<gb_system *> &Ss);
 void groebner_batch(const std::vector<gb_system *> &Ss);
 }  // namespace gb
 
@@ -42,6 +43,7 @@ namespace {
 struct Running {
     uint64_t ticket;
     gb_system *sys;
+    uint32_t waited = 0;  // iterations spent out of pairs, waiting for the final reduction
 };
 
 // take queued systems while a slot is free and the footprint fits (a system larger than the whole
@@ -70,14 +72,40 @@ void scheduler_loop(gb_server *srv) {
             }
             admit(srv, run, bytes);
         }
-        std::vector<gb_system *> Ss;
-        for (auto &r : run) Ss.push_back(r.sys);
+        // one lockstep iteration: a step for every system with pairs left, and the final reduction
+        // of the systems out of pairs -- now, or (finish_min > 1) once enough of them are ready
+        std::vector<gb_system *> Ss, step, fin;
+        for (auto &r : run) {
+            Ss.push_back(r.sys);
+            if (r.sys->finished) continue;
+            if (!r.sys->pairs.empty()) step.push_back(r.sys);
+        }
+        {
+            size_t ready = 0;
+            bool due = step.empty();
+            for (auto &r : run)
+                if (!r.sys->finished && r.sys->pairs.empty()) {
+                    ++ready;
+                    due = due || r.waited >= 4;
+                }
+            due = due || ready >= std::max<uint32_t>(srv->opts.finish_min, 1);
+            for (auto &r : run)
+                if (!r.sys->finished && r.sys->pairs.empty()) {
+                    if (due) fin.push_back(r.sys);
+                    else ++r.waited;
+                }
+        }
         gb_status st = GB_OK;
+        double fin_ms = 0.0;
         const auto t0 = std::chrono::steady_clock::now();
         try {
             std::lock_guard<std::recursive_mutex> g(srv->ctx->mu);
             GB_CUDA(cudaSetDevice(srv->ctx->device));
-            advance(Ss);
+            if (!fin.empty()) {
+                finish_batch(fin);
+                fin_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            }
+            if (!step.empty()) f4_steps(step, nullptr);
         } catch (const gb::Error &e) {
             set_last_error(e.what());
             st = e.st;
@@ -94,6 +122,8 @@ void scheduler_loop(gb_server *srv) {
         srv->stats.iterations++;
         srv->stats.system_steps += Ss.size();
         srv->stats.busy_ms += ms;
+        srv->stats.finish_ms += fin_ms;
+        if (!fin.empty()) srv->stats.finish_passes++;
         srv->stats.max_running = std::max<uint32_t>(srv->stats.max_running, (uint32_t)Ss.size());
         size_t w = 0;
         for (auto &r : run) {
