@@ -50,6 +50,15 @@ def peaks() -> dict:
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "source": "fallback"}
 
 
+def profile_value(kernel_tag: str, key: str):
+    """A number recorded as `key: value` in a committed ncu summary, if present."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", open(path).read())
+    return float(m.group(1)) if m else None
+
+
 def profile_traffic(kernel_tag: str):
     """Per-launch DRAM bytes of a kernel from a committed ncu summary, if one exists."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
@@ -301,6 +310,16 @@ def measure_dense_n10(gb, synth, ctx, flush, pk: dict, args) -> dict:
     red_ms = sum(r["ms_reduce_kernel"] for r in runs)
     fma = sum(r["axpy_fma"] for r in runs)
     eff = 8.0 * fma / (red_ms / 1e3) / 1e9 if red_ms > 0 else 0.0
+    # issue-bound rate of the multi-row kernel: every scheduler issuing one warp instruction per
+    # clock at the measured maximum SM clock, at the instructions per multiply-add ncu counted
+    ipf = profile_value("k_reduce_rows_dense_n10", "warp_instructions_per_32_fma")
+    sm_mhz = 2032.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            sm_mhz = float(json.load(f).get("sm_max_mhz", sm_mhz))
+    issue_peak = 148 * 4 * sm_mhz * 1e6 * 32.0 / ipf if ipf else None
+    fma_rate = fma / (red_ms / 1e3) if red_ms > 0 else None
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
              for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_rref", "ms_update", "ms_pairs", "ms_select",
                        "ms_finish")}
@@ -314,6 +333,11 @@ def measure_dense_n10(gb, synth, ctx, flush, pk: dict, args) -> dict:
                 "modp_fma_per_s": fma / (red_ms / 1e3) if red_ms > 0 else None,
                 "effective_operand_gbs": round(eff, 1),
                 "effective_frac_of_hbm": round(eff / pk["hbm_gbs"], 4),
+                "issue_roofline": None if not issue_peak else {
+                    "bound": "alu", "unit": "modular multiply-adds/s", "achieved": fma_rate,
+                    "peak": issue_peak, "frac": round(fma_rate / issue_peak, 4),
+                    "peak_source": f"148 SMs x 4 schedulers x {sm_mhz:.0f} MHz, {ipf} warp instructions "
+                                   "per 32 multiply-adds (ncu, profiles/k_reduce_rows_dense_n10.md)"},
                 "bound": "issue / L2 latency (operands L2-resident; profiles/k_reduce_rows_dense_n10.md)",
                 "traffic": profile_traffic("k_reduce_rows_dense_n10")}}
 
