@@ -36,6 +36,7 @@ WORKLOAD = ("n=13, m=13 sparse random quadratics (30 of the 105 monomials of deg
 WORKLOAD_N10 = ("n=10, m=10 dense random quadratics (all 66 monomials of degree <= 2), p=65521, "
                 "grevlex, SplitMix64 seed 20260765; one full F4 run to the reduced basis")
 SERVE_FINISH_MIN = 1    # final reductions of served systems as soon as they are ready
+SERVE_ADMIT_MIN = 1     # served systems admitted into any free slot
 CPU_SAMPLE_STEPS = 5   # the oracle's first 5 F4 steps of the n=13 run: about 30 s on one core
 REF_SAMPLE_STEPS = 4   # the reference arm's per-step sample: the first 4 F4 steps, about 3 s
 
@@ -220,22 +221,21 @@ def run_ours(args) -> None:
                 "units": "2 L^2 = 32 BF16 digit-product FLOPs per mod-p multiply-add (L = 4 digits, p = 2^31-1)",
                 "traffic": profile_traffic("k_mm_sparse_n13")}
 
-    n10 = measure_dense_n10(gb, synth, ctx, flush, pk, args) if rank == 0 and not args.no_batch else None
-    batched = measure_batched(gb, synth, ctx, rank, world) if not args.no_batch else None
-    served = measure_served(gb, synth, ctx) if rank == 0 and not args.no_batch else None
-    tensor = measure_tensor_core(gb, local) if rank == 0 and not args.no_batch else None
-    n13 = measure_sparse_n13(gb, synth, local, pk, runs, graphs=not args.no_graphs) \
-        if rank == 0 and not args.no_batch else None
-    deglex = wied = None
-    if rank == 0 and not args.no_batch:
+    def guarded(fn, *a, **kw):
+        """A secondary measurement: an error is reported in the line; the headline stands."""
         try:
-            deglex = measure_deglex(gb, synth, ctx)
-        except gb.GbError as e:  # reported in the line; the main measurement stands
-            deglex = {"error": str(e)}
-        try:
-            wied = measure_wiedemann(gb, synth, local, pk)
-        except gb.GbError as e:
-            wied = {"error": str(e)}
+            return fn(*a, **kw)
+        except (gb.GbError, RuntimeError) as e:
+            return {"error": str(e)}
+
+    extra = rank == 0 and not args.no_batch
+    n10 = guarded(measure_dense_n10, gb, synth, ctx, flush, pk, args) if extra else None
+    batched = guarded(measure_batched, gb, synth, ctx, rank, world, local) if not args.no_batch else None
+    served = guarded(measure_served, gb, synth, ctx) if extra else None
+    tensor = guarded(measure_tensor_core, gb, local) if extra else None
+    n13 = guarded(measure_sparse_n13, gb, synth, local, pk, runs, graphs=not args.no_graphs) if extra else None
+    deglex = guarded(measure_deglex, gb, synth, ctx) if extra else None
+    wied = guarded(measure_wiedemann, gb, synth, local, pk) if extra else None
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
              for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_mm", "ms_rref", "ms_update", "ms_pairs",
                        "ms_select", "ms_finish", "ms_wall")}
@@ -342,7 +342,7 @@ def measure_dense_n10(gb, synth, ctx, flush, pk: dict, args) -> dict:
                 "traffic": profile_traffic("k_reduce_rows_dense_n10")}}
 
 
-def _plain_vs_batched(gb, ctx, systems, rank: int = 0, world: int = 1) -> dict:
+def _plain_vs_batched(gb, ctx, systems, rank: int = 0, world: int = 1, group: int | None = None) -> dict:
     """The same systems run one after another through gb_groebner (plain) and as one
     gb_batch_groebner call (batched, lockstep); wall clock of each, nnz rate of each.  Under
     several ranks each runs its share of the systems (no data exchange) and the numbers are the
@@ -352,15 +352,27 @@ def _plain_vs_batched(gb, ctx, systems, rank: int = 0, world: int = 1) -> dict:
     out = {"systems": len(systems), "ranks": world}
     for mode in ("plain", "batched"):
         hs = [gb.gb_system_create(ctx.h, s) for s in mine]
-        t0 = time.perf_counter()
-        if mode == "plain":
-            stats = [gb.gb_groebner(h) for h in hs]
-        else:
-            stats = gb.gb_batch_groebner(ctx.h, hs) if hs else []
-        dt_ms, nnz = shard.aggregate((time.perf_counter() - t0) * 1e3, sum(st["nnz_total"] for st in stats))
+        stats = []
+        if mode == "plain":  # one at a time; each leaves the arena before the next
+            el = 0.0
+            for h in hs:
+                t0 = time.perf_counter()
+                stats.append(gb.gb_groebner(h))
+                el += time.perf_counter() - t0
+                gb.gb_system_destroy(h)
+            hs = []
+        else:  # lockstep groups of `group` systems (all at once when group is None)
+            el = 0.0
+            g = group or max(len(hs), 1)
+            for a in range(0, len(hs), g):
+                t0 = time.perf_counter()
+                stats += gb.gb_batch_groebner(ctx.h, hs[a:a + g])
+                el += time.perf_counter() - t0
+                for h in hs[a:a + g]:
+                    gb.gb_system_destroy(h)
+            hs = []
+        dt_ms, nnz = shard.aggregate(el * 1e3, sum(st["nnz_total"] for st in stats))
         dt = dt_ms / 1e3
-        for h in hs:
-            gb.gb_system_destroy(h)
         out[f"{mode}_ms"] = round(dt * 1e3, 2)
         out[f"{mode}_nnz_per_s"] = nnz / dt
         out[f"{mode}_systems_per_s"] = len(systems) / dt
@@ -372,27 +384,47 @@ def _max_degree(s: dict) -> int:
     return int(s["exps"].reshape(-1, s["n"]).sum(axis=1).max())
 
 
-def measure_batched(gb, synth, ctx, rank: int = 0, world: int = 1) -> list:
-    """Two batches, each run plain and batched: the n=8 dense quadratic system modulo the 128
-    largest primes below 2^31, and the 256-system mixed batch without its 29 cubic members in 9
-    variables (each of those alone runs for 40-60 s, and one builds a matrix above 2^32 nonzeros,
-    beyond the library's 32-bit CSR offsets)."""
+def measure_batched(gb, synth, ctx, rank: int = 0, world: int = 1, local: int = 0) -> list:
+    """Three batches, each run plain (one system after another) and batched (lockstep):
+    - the n=8 dense quadratic system modulo the 128 largest primes below 2^31;
+    - the 256-system mixed batch without its 52 cubic members with n >= 8, as one lockstep batch;
+    - its 23 cubic members with n = 8, in lockstep groups of 4 in a context of their own: a lockstep
+      step allocates for all of its systems together, and one of these steps alone takes up to
+      39 GB.
+    The 29 cubic members with n = 9 take 40-60 s each, and one builds a matrix above 2^32 nonzeros,
+    beyond the library's 32-bit CSR offsets: they are not run here."""
     primes = synth.multi_prime_system(synth.largest_primes_below(2 ** 31, 128))
-    mixed = [s for s in synth.mixed_batch(256) if not (_max_degree(s) == 3 and s["n"] >= 9)]
+    mixed_all = synth.mixed_batch(256)
+    cubic = lambda s: _max_degree(s) == 3
+    mixed = [s for s in mixed_all if not (cubic(s) and s["n"] >= 8)]
+    cubic8 = [s for s in mixed_all if cubic(s) and s["n"] == 8]
     a = _plain_vs_batched(gb, ctx, primes, rank, world)
     a["workload"] = "n=8 dense quadratic system modulo the 128 largest primes below 2^31"
     b = _plain_vs_batched(gb, ctx, mixed, rank, world)
     b["workload"] = (f"{len(mixed)} of the 256 mixed systems (n ~ U{{5..9}}, degree 2 or 3, 10-40 terms, "
-                     "p=65521): all but the 29 cubic ones with n = 9")
-    return [a, b]
+                     "p=65521): all but the 52 cubic ones with n >= 8")
+    out = [a, b]
+    big = gb.Context(device=local, arena_bytes=160 << 30)
+    try:
+        c = _plain_vs_batched(gb, big, cubic8, rank, world, group=4)
+        c["workload"] = (f"the {len(cubic8)} cubic mixed-batch systems with n = 8 (10-40 terms, p=65521); "
+                         "batched in lockstep groups of 4; 160 GiB arena")
+    except gb.GbError as e:
+        c = {"workload": "the cubic mixed-batch systems with n = 8", "error": str(e)}
+    big.close()
+    out.append(c)
+    out.append({"covered": len(mixed) + len(cubic8), "of": len(mixed_all),
+                "left_out": "the 29 cubic systems with n = 9 (40-60 s each alone; one exceeds 2^32 "
+                            "nonzeros in a matrix)"})
+    return out
 
 
-def _serve(gb, ctx, reqs, arrivals, slots: int, finish_min: int = 0) -> dict:
+def _serve(gb, ctx, reqs, arrivals, slots: int, finish_min: int = 0, admit_min: int = 0) -> dict:
     """Submit each request at its arrival time (seconds from the start; all at 0 for a standing
     queue), poll until every one is back; latency = completion - arrival."""
     import numpy as _np
     count = len(reqs)
-    srv = gb.gb_server_create(ctx.h, 150 << 30, slots, finish_min)
+    srv = gb.gb_server_create(ctx.h, 150 << 30, slots, finish_min, admit_min)
     pending, lat, done_at = {}, [], []
     start = time.perf_counter()
     nxt = 0
@@ -428,7 +460,8 @@ def _serve(gb, ctx, reqs, arrivals, slots: int, finish_min: int = 0) -> dict:
 
 
 def measure_served(gb, synth, ctx, count: int = 2000, slots: int = 64,
-                   loads=(0.5, 0.8, 0.95), finish_min: int = SERVE_FINISH_MIN, variants=()) -> dict:
+                   loads=(0.5, 0.8, 0.95), finish_min: int = SERVE_FINISH_MIN,
+                   admit_min: int = SERVE_ADMIT_MIN, variants=()) -> dict:
     """Poisson streams of served requests (n ~ U{5..11}, 20-66 terms, p = 65521 or 2^31-1) through
     gb_server_*.  Saturation is the server's own throughput with every request queued at once (a
     standing queue: continuous admission into free slots, no idle slot); the streams then arrive
@@ -450,22 +483,22 @@ def measure_served(gb, synth, ctx, count: int = 2000, slots: int = 64,
     for h in hs:
         gb.gb_system_destroy(h)
     tried = {}
-    for fm in variants:  # saturation under other final-reduction policies, for comparison
-        tried[fm] = _serve(gb, ctx, reqs, [0.0] * count, slots, fm)
-    sat_run = _serve(gb, ctx, reqs, [0.0] * count, slots, finish_min)
+    for am in variants:  # saturation under other admission waves, for comparison
+        tried[am] = _serve(gb, ctx, reqs, [0.0] * count, slots, finish_min, am)
+    sat_run = _serve(gb, ctx, reqs, [0.0] * count, slots, finish_min, admit_min)
     sat = sat_run["steady_systems_per_s"] or sat_run["systems_per_s"]
     runs = []
     for load in loads:
         rate = load * sat
-        r = _serve(gb, ctx, reqs, synth.poisson_arrivals(count, rate), slots, finish_min)
+        r = _serve(gb, ctx, reqs, synth.poisson_arrivals(count, rate), slots, finish_min, admit_min)
         r.update({"load": load, "offered_per_s": round(rate, 2),
                   "delivered_over_offered": round((r["steady_systems_per_s"] or r["systems_per_s"]) / rate, 3)})
         runs.append(r)
     return {"workload": f"{count} Poisson requests per load, n ~ U{{5..11}}, 20-66 terms, p in {{65521, 2^31-1}}",
             "plain_systems_per_s": round(plain, 2), "lockstep_batch_systems_per_s": round(lockstep, 2),
             "saturation_systems_per_s": round(sat, 2), "saturation_run": sat_run,
-            "finish_min": finish_min,
-            "saturation_other_finish_min": {str(k): v["steady_systems_per_s"] for k, v in tried.items()},
+            "finish_min": finish_min, "admit_min": admit_min,
+            "saturation_other_admit_min": {str(k): v["steady_systems_per_s"] for k, v in tried.items()},
             "hbm_cap_bytes": 150 << 30, "slots": slots, "loads": runs}
 
 
@@ -747,7 +780,7 @@ def main() -> None:
             ctx.close()
         elif args.only == "served":
             ctx = gb.Context(device=0, arena_bytes=args.arena_gb << 30)
-            print(json.dumps({"served": measure_served(gb, synth, ctx, variants=(8, 16))}))
+            print(json.dumps({"served": measure_served(gb, synth, ctx, variants=(16, 32, 48))}))
             ctx.close()
         elif args.only == "wiedemann":
             print(json.dumps({"block_wiedemann": measure_wiedemann(gb, synth, 0, peaks())}))

@@ -254,6 +254,10 @@ typedef struct {
                               this many are ready, for at most 4 iterations, or until no other
                               system takes a step (0 or 1: at once); one final-reduction pass then
                               serves them all */
+    uint32_t admit_min;    /* queued systems are admitted only while at least this many slots are
+                              free, or when nothing runs (0 or 1: into any free slot), so that they
+                              join in waves and take their steps in phase */
+    uint32_t reserved;
 } gb_server_opts;
 
 /* A continuous-batching server: one scheduler thread runs lockstep iterations (as in

@@ -110,7 +110,7 @@ class gb_tune_report(ctypes.Structure):
 
 class gb_server_opts(ctypes.Structure):
     _fields_ = [("hbm_cap_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_uint32),
-                ("finish_min", ctypes.c_uint32)]
+                ("finish_min", ctypes.c_uint32), ("admit_min", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 def _struct_dict(s) -> dict:
@@ -376,8 +376,9 @@ def gb_tune_load(ctx: int, path: str) -> None:
     check(lib().gb_tune_load(ctx, os.fsencode(path)), "gb_tune_load")
 
 
-def gb_server_create(ctx: int, hbm_cap_bytes: int, max_slots: int = 0, finish_min: int = 0) -> int:
-    o = gb_server_opts(hbm_cap_bytes, max_slots, finish_min)
+def gb_server_create(ctx: int, hbm_cap_bytes: int, max_slots: int = 0, finish_min: int = 0,
+                     admit_min: int = 0) -> int:
+    o = gb_server_opts(hbm_cap_bytes, max_slots, finish_min, admit_min, 0)
     h = _vp()
     check(lib().gb_server_create(ctx, ctypes.byref(o), ctypes.byref(h)), "gb_server_create")
     return h.value

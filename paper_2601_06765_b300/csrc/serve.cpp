@@ -49,6 +49,8 @@ struct Running {
 // take queued systems while a slot is free and the footprint fits (a system larger than the whole
 // cap is still admitted when nothing else runs); called with srv->mu held
 void admit(gb_server *srv, std::vector<Running> &run, size_t &bytes) {
+    const size_t wave = std::max<uint32_t>(srv->opts.admit_min, 1);
+    if (!run.empty() && srv->opts.max_slots - run.size() < std::min<size_t>(wave, srv->opts.max_slots)) return;
     while (!srv->queue.empty() && run.size() < srv->opts.max_slots) {
         gb_system *S = srv->queue.front().second;
         if (!run.empty() && bytes + S->footprint > srv->opts.hbm_cap_bytes) break;
