@@ -36,7 +36,7 @@ WORKLOAD = ("n=13, m=13 sparse random quadratics (30 of the 105 monomials of deg
 WORKLOAD_N10 = ("n=10, m=10 dense random quadratics (all 66 monomials of degree <= 2), p=65521, "
                 "grevlex, SplitMix64 seed 20260765; one full F4 run to the reduced basis")
 SERVE_FINISH_MIN = 1    # final reductions of served systems as soon as they are ready
-SERVE_ADMIT_MIN = 1     # served systems admitted into any free slot
+SERVE_ADMIT_MIN = 48    # served systems admitted in waves, once 48 of the 64 slots are free
 CPU_SAMPLE_STEPS = 5   # the oracle's first 5 F4 steps of the n=13 run: about 30 s on one core
 REF_SAMPLE_STEPS = 4   # the reference arm's per-step sample: the first 4 F4 steps, about 3 s
 
@@ -780,7 +780,7 @@ def main() -> None:
             ctx.close()
         elif args.only == "served":
             ctx = gb.Context(device=0, arena_bytes=args.arena_gb << 30)
-            print(json.dumps({"served": measure_served(gb, synth, ctx, variants=(16, 32, 48))}))
+            print(json.dumps({"served": measure_served(gb, synth, ctx, variants=(1, 32, 56, 64))}))
             ctx.close()
         elif args.only == "wiedemann":
             print(json.dumps({"block_wiedemann": measure_wiedemann(gb, synth, 0, peaks())}))

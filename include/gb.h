@@ -80,7 +80,11 @@ typedef struct {
                             GB_CTX_SP_HASH: symbolic preprocessing setifies through a hash
                             dictionary keyed by an additive monomial key instead of ranking every
                             term into a bitmap; a key shared by two monomials is detected and the
-                            step rebuilt on the rank path (same results). */
+                            step rebuilt on the rank path (same results);
+                            GB_CTX_SKETCH: the echelon form of a tall D' (at least 2048 rows)
+                            through a random sketch first: RREF(R D') for a random R of 512 rows,
+                            checked exactly against D', the full echelon form when the check fails
+                            (same results). */
     uint32_t reserved;
 } gb_ctx_opts;
 
@@ -89,6 +93,7 @@ typedef struct {
 #define GB_CTX_REDUCE_DENSE 4u
 #define GB_CTX_NO_GRAPHS 8u
 #define GB_CTX_SP_HASH 16u
+#define GB_CTX_SKETCH 32u
 
 /* A polynomial system on the host: polynomial i has the terms [poly_off[i], poly_off[i+1]). */
 typedef struct {
@@ -153,6 +158,8 @@ typedef struct {
     double mm_flops;   /* BF16 digit-product FLOPs of those launches: 2 L^2 per mod-p multiply-add
                           (L = 2 digits for p < 2^16, 4 otherwise) */
     uint64_t mm_launches; /* the launches ms_mm covers */
+    uint32_t rref_sketched; /* 1: RREF(D') came from a random sketch, checked exactly */
+    uint32_t reserved;
 } gb_step_stats;
 
 typedef struct {
@@ -242,8 +249,11 @@ gb_status gb_system_last_step(const gb_system *sys, const gb_macaulay **mac,
    one F4 step of every system with pairs left (each pipeline kernel is launched once for all of
    their matrices) and builds the reduced basis of every system without pairs; per-system host
    control runs on the context's worker threads.  The results are those of gb_groebner on each
-   system alone.  A failing iteration fails the whole call (the systems are left unusable).
-   per_system may be NULL. */
+   system alone.  Each stage of an iteration allocates for all of its systems together, so the
+   arena must hold the batch's steps side by side: a batch of large systems is split by the caller
+   (or goes through the server, which admits by estimated footprint); GB_ENOMEM otherwise.  A
+   failing iteration fails the whole call (the systems are left unusable).  per_system may be
+   NULL. */
 gb_status gb_batch_groebner(gb_ctx *ctx, uint32_t count, gb_system *const *systems,
                             gb_run_stats *per_system);
 

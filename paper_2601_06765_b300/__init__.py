@@ -28,6 +28,7 @@ GB_CTX_REDUCE_SPARSE = 2
 GB_CTX_REDUCE_DENSE = 4
 GB_CTX_NO_GRAPHS = 8
 GB_CTX_SP_HASH = 16
+GB_CTX_SKETCH = 32
 GB_GREVLEX, GB_DEGLEX = 0, 1  # gb_order
 # gb_modp_op
 (GB_MODP_REDUCE64, GB_MODP_REDUCE32, GB_MODP_MULADD, GB_MODP_REDC, GB_MODP_TO_MONT, GB_MODP_MONT_MUL,
@@ -74,7 +75,7 @@ class gb_step_stats(ctypes.Structure):
                 ("ms_rref", ctypes.c_float), ("ms_update", ctypes.c_float), ("ms_pairs", ctypes.c_float),
                 ("ms_select", ctypes.c_float), ("ms_reduce_kernel", ctypes.c_float),
                 ("ms_wall", ctypes.c_double), ("ms_mm", ctypes.c_double), ("mm_flops", ctypes.c_double),
-                ("mm_launches", ctypes.c_uint64)]
+                ("mm_launches", ctypes.c_uint64), ("rref_sketched", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class gb_run_stats(ctypes.Structure):
@@ -470,12 +471,14 @@ class Context:
     """A library context whose device arena is a torch tensor on `device`."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 2 << 30, keep_step: bool = False,
-                 reduce: str = "auto", stream=None, graphs: bool = True, sp: str = "ranks"):
+                 reduce: str = "auto", stream=None, graphs: bool = True, sp: str = "ranks",
+                 sketch: bool = False):
         """reduce: "auto" (per matrix by shape), "sparse" or "dense" (see GB_CTX_REDUCE_*).
         stream: a torch.cuda.Stream the context runs on (default: a stream of its own).
         graphs: False launches the echelon-form rounds one by one (GB_CTX_NO_GRAPHS).
         sp: "ranks" (every term ranked into a bitmap) or "hash" (the hash dictionary,
-        GB_CTX_SP_HASH) for symbolic preprocessing."""
+        GB_CTX_SP_HASH) for symbolic preprocessing.
+        sketch: True echelonises tall D' through a random sketch first (GB_CTX_SKETCH)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: this library has no CPU path")
@@ -486,6 +489,8 @@ class Context:
                                                             "dense": GB_CTX_REDUCE_DENSE}[reduce]
         if not graphs:
             flags |= GB_CTX_NO_GRAPHS
+        if sketch:
+            flags |= GB_CTX_SKETCH
         if sp == "hash":
             flags |= GB_CTX_SP_HASH
         elif sp != "ranks":

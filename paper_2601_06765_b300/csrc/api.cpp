@@ -585,31 +585,10 @@ gb_status gb_matmul_modp(gb_ctx *ctx, uint32_t p, uint32_t m, uint32_t n, uint32
     Enter entered(ctx);
     Arena &ar = ctx->arena;
     cudaStream_t st = ctx->stream;
-    const Fp fp = make_fp(p);
-    const uint32_t L = digits_for(p);
-    DigitPlanes DA, DB;
-    DA.alloc(ar, L, m, k, st);
-    DB.alloc(ar, L, n, k, st);
-    to_digits(A, lda, 1, DA, p, st);
-    to_digits(B, 1, ldb, DB, p, st);  // B^T: row j holds column j of B
     DBuf<uint32_t> err;
     err.alloc(ar, 1, st);
     GB_CUDA(cudaMemsetAsync(err.p, 0, 4, st));
-    // the kernel moves C tiles by TMA: rows must start on 16-byte boundaries, else C is staged
-    DBuf<uint32_t> Cs;
-    uint32_t *Cw = C;
-    uint64_t ldw = ldc;
-    if (ldc % 4 || (reinterpret_cast<uintptr_t>(C) & 15)) {
-        ldw = (n + 3) / 4 * 4;
-        Cs.alloc(ar, (size_t)m * ldw, st);
-        Cw = Cs.p;
-        GB_CUDA(cudaMemcpy2DAsync(Cw, 4 * ldw, C, 4 * ldc, 4ull * n, m, cudaMemcpyDeviceToDevice, st));
-    }
-    const uint32_t kmax = mm_kmax(p);
-    const MmPlan plan(DA, DB, Cw, ldw, m, n, fp);
-    for (uint32_t k0 = 0; k0 < k; k0 += kmax)
-        plan.update(k0, 0, k0, 0, 0, 0, m, n, std::min(kmax, k - k0), subtract != 0, err.p, st);
-    if (Cw != C) GB_CUDA(cudaMemcpy2DAsync(C, 4 * ldc, Cw, 4 * ldw, 4ull * n, m, cudaMemcpyDeviceToDevice, st));
+    matmul_dev(ar, make_fp(p), m, n, k, A, lda, B, ldb, C, ldc, subtract != 0, err.p, st);
     uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16));
     GB_CUDA(cudaMemcpyAsync(h, err.p, 4, cudaMemcpyDeviceToHost, st));
     ctx_sync(ctx);

@@ -198,6 +198,15 @@ __device__ __forceinline__ unsigned long long mono_key(uint4 m) {
     return h;
 }
 
+// SplitMix64 (Steele, Lea, Flood 2014): counter-based pseudo-random words for the random
+// combinations of the block Wiedemann path and of the sketched echelon form
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 __device__ __forceinline__ uint32_t mono_deg(uint4 m) {
     return __dp4a(m.x, 0x01010101u, 0u) + __dp4a(m.y, 0x01010101u, 0u) +
            __dp4a(m.z, 0x01010101u, 0u) + __dp4a(m.w, 0x01010101u, 0u);

@@ -200,45 +200,44 @@ void parallel_for(gb_ctx *ctx, size_t n, const std::function<void(size_t)> &fn) 
 // beyond that the bytewise routines above are used.  Pair lcms are cached with the pair.
 
 namespace {
-struct MonoOps {
+// leading-monomial arithmetic of one system
+struct LmOps {
+    const gb_system *S;
     int n;
     bool swar;
-    bool divides(const M16 &a, const M16 &b, const Mono &ma, const Mono &mb) const {
-        return swar ? divides16(a, b) : mono_divides(ma, mb, n);
-    }
-};
-}  // namespace
-
-static void gm_update(gb_system *S, uint32_t h) {
-    const int n = (int)S->n;
-    const Mono &lh = S->lm[h];
-    const M16 lh16 = S->lm16[h];
-    const bool swar = S->swar;
-    auto lcm_of = [&](uint32_t a, uint32_t b) -> M16 {
+    explicit LmOps(const gb_system *s) : S(s), n((int)s->n), swar(s->swar) {}
+    M16 lcm(uint32_t a, uint32_t b) const {
         if (swar) return lcm16(S->lm16[a], S->lm16[b]);
         return m16(mono_lcm(S->lm[a], S->lm[b], n));
-    };
-    auto divides = [&](const M16 &a, const M16 &b) -> bool {
+    }
+    bool divides(const M16 &a, const M16 &b) const {
         if (swar) return divides16(a, b);
         Mono x, y;
         std::memcpy(x.e, &a, 16);
         std::memcpy(y.e, &b, 16);
         return mono_divides(x, y, n);
-    };
-    auto coprime = [&](uint32_t a) -> bool {
-        return swar ? coprime16(lh16, S->lm16[a]) : mono_coprime(lh, S->lm[a], n);
-    };
-    // per-thread scratch, reused across calls (the batch runs systems on several host threads)
+    }
+    bool coprime(uint32_t a, uint32_t b) const {
+        return swar ? coprime16(S->lm16[a], S->lm16[b]) : mono_coprime(S->lm[a], S->lm[b], n);
+    }
+    // the second loop of UPDATE: the waiting pair pr goes when h arrives iff LM(h) divides its
+    // lcm while lcm(LM(i), LM(h)) and lcm(LM(j), LM(h)) both differ from it
+    bool dropped_by(const PairL &pr, uint32_t h) const {
+        return divides(S->lm16[h], pr.lcm) && !(lcm(pr.i, h) == pr.lcm) && !(lcm(pr.j, h) == pr.lcm);
+    }
+};
+
+// The first loop of UPDATE for one new element h: the pairs (g, h), g in C (the elements older
+// than h that are not redundant when h arrives, oldest first), that it keeps, appended to out
+// without those of coprime leading monomials (Buchberger's product criterion).
+void new_pairs(const LmOps &o, uint32_t h, const std::vector<uint32_t> &C, std::vector<PairL> &out) {
+    // per-thread scratch, reused across calls
     struct Scratch {
-        std::vector<uint32_t> C, Ld, ord, cnt, und, slot;
+        std::vector<uint32_t> Ld, ord, cnt, und, slot;
         std::vector<M16> L, mins;
         std::vector<char> kept, cop, dom;
     };
     static thread_local Scratch z;
-    std::vector<uint32_t> &C = z.C;
-    C.clear();
-    for (uint32_t g = 0; g < h; ++g)
-        if (!S->redundant[g]) C.push_back(g);
     const size_t c = C.size();
     z.L.resize(c);
     z.Ld.resize(c);
@@ -250,10 +249,10 @@ static void gm_update(gb_system *S, uint32_t h) {
     std::vector<char> &kept = z.kept, &cop = z.cop, &dom = z.dom;
     uint32_t dmax = 0;
     for (size_t a = 0; a < c; ++a) {
-        L[a] = lcm_of(h, C[a]);
+        L[a] = o.lcm(h, C[a]);
         Ld[a] = deg16(L[a]);
         dmax = std::max(dmax, Ld[a]);
-        cop[a] = coprime(C[a]);
+        cop[a] = o.coprime(h, C[a]);
     }
     // The new pairs (h, g) are taken oldest g first: one is kept when its leading monomials are
     // coprime, or when no pair still waiting and no pair already kept has an lcm dividing its lcm.
@@ -276,7 +275,7 @@ static void gm_update(gb_system *S, uint32_t h) {
         while (e < c && Ld[ord[e]] == Ld[ord[s0]]) ++e;
         for (size_t q = s0; q < e; ++q)
             for (const M16 &m : mins)
-                if (divides(m, L[ord[q]])) {
+                if (o.divides(m, L[ord[q]])) {
                     dom[ord[q]] = 1;
                     break;
                 }
@@ -319,22 +318,117 @@ static void gm_update(gb_system *S, uint32_t h) {
     }
     for (size_t k = 0; k < cap; ++k)
         if (slot[k] != UINT32_MAX && !anyc[slot[k]]) kept[slot[k]] = 1;  // the last of its lcm
-    for (uint32_t a = 0; a < c; ++a)
-        if (cop[a]) kept[a] = 1;
-    // old pairs whose lcm LM(h) divides, with both lcm(g1, h) and lcm(g2, h) different, go
-    size_t w = 0;
-    for (size_t q = 0; q < S->pairs.size(); ++q) {
-        const PairL &pr = S->pairs[q];
-        bool drop = divides(lh16, pr.lcm);
-        if (drop) drop = !(lcm_of(pr.i, h) == pr.lcm) && !(lcm_of(pr.j, h) == pr.lcm);
-        if (!drop) S->pairs[w++] = pr;
-    }
-    S->pairs.resize(w);
-    // kept new pairs, except those with coprime leading monomials (Buchberger's product criterion)
     for (size_t a = 0; a < c; ++a)
-        if (kept[a] && !cop[a]) S->pairs.push_back(PairL{C[a], h, Ld[a], 0, L[a]});
-    for (uint32_t g = 0; g < h; ++g)
-        if (!S->redundant[g] && divides(lh16, S->lm16[g])) S->redundant[g] = 1;
+        if (kept[a] && !cop[a]) out.push_back(PairL{C[a], h, Ld[a], 0, L[a]});
+}
+}  // namespace
+
+// UPDATE (Becker and Weispfenning) for the new elements h0, h0 + 1, ..., lm.size() - 1 of each
+// system, whose leading monomials are already recorded: the same pairs, in the same order, and the
+// same redundant elements as UPDATE called on them one at a time, computed in parallel.  One at a
+// time, h_i (= h0 + i) first takes its new pairs against C_i, the older elements not yet
+// redundant; then drops the waiting pairs its leading monomial rules out; then marks redundant the
+// older elements whose leading monomial it divides.  So:
+//   - e is redundant when h_i arrives iff it was before the step, or some h_f with e < h_f, f < i
+//     has LM(h_f) | LM(e): with first(e) the least such f (k when there is none), C_i is the set
+//     of g < h_i not redundant before the step with first(g) >= i;
+//   - a pair waiting at the step's start survives iff no h_i drops it, and a new pair of h_i
+//     survives iff no later h_j drops it (the test looks at the pair and h_j only);
+//   - the survivors come in the sequential order: the waiting ones, then those of h_0, h_1, ...
+// first(), the new pairs of each h_i and the survivor tests are independent work items.
+static void update_steps(gb_ctx *ctx, const std::vector<gb_system *> &Ss, const std::vector<uint32_t> &h0) {
+    const size_t nj = Ss.size();
+    auto run = [&](size_t n, const std::function<void(size_t)> &f) {
+        if (ctx) parallel_for(ctx, n, f);
+        else for (size_t i = 0; i < n; ++i) f(i);
+    };
+    struct Sys {
+        std::vector<uint32_t> first;         // per element: the least f as above, k if none
+        std::vector<std::vector<PairL>> fresh;  // per new element: its surviving new pairs
+        std::vector<uint8_t> keep;           // per waiting pair: whether it survives
+        uint32_t k = 0;
+    };
+    std::vector<Sys> W(nj);
+    struct Item {
+        uint32_t j, a, b;  // system, range [a, b) of elements or pairs, or (a = new element, b = ~0u)
+    };
+    constexpr uint32_t CHUNK = 1024, PCHUNK = 8192;
+    std::vector<Item> items;
+    for (size_t j = 0; j < nj; ++j) {
+        const uint32_t nt = (uint32_t)Ss[j]->lm.size();
+        W[j].k = nt - h0[j];
+        W[j].first.assign(nt, W[j].k);
+        if (W[j].k)
+            for (uint32_t a = 0; a < nt; a += CHUNK) items.push_back(Item{(uint32_t)j, a, std::min(nt, a + CHUNK)});
+    }
+    run(items.size(), [&](size_t t) {
+        const Item it = items[t];
+        const gb_system *S = Ss[it.j];
+        const LmOps o(S);
+        Sys &w = W[it.j];
+        const uint32_t base = h0[it.j];
+        for (uint32_t e = it.a; e < it.b; ++e) {
+            if (S->redundant[e]) continue;
+            for (uint32_t f = e < base ? 0 : e - base + 1; f < w.k; ++f)
+                if (o.divides(S->lm16[base + f], S->lm16[e])) {
+                    w.first[e] = f;
+                    break;
+                }
+        }
+    });
+    items.clear();
+    for (size_t j = 0; j < nj; ++j) {
+        if (!W[j].k) continue;
+        W[j].fresh.resize(W[j].k);
+        W[j].keep.assign(Ss[j]->pairs.size(), 1);
+        for (uint32_t i = W[j].k; i-- > 0;) items.push_back(Item{(uint32_t)j, i, ~0u});  // largest C first
+        const uint32_t np = (uint32_t)Ss[j]->pairs.size();
+        for (uint32_t a = 0; a < np; a += PCHUNK) items.push_back(Item{(uint32_t)j, a, std::min(np, a + PCHUNK)});
+    }
+    run(items.size(), [&](size_t t) {
+        const Item it = items[t];
+        const gb_system *S = Ss[it.j];
+        const LmOps o(S);
+        Sys &w = W[it.j];
+        const uint32_t base = h0[it.j];
+        if (it.b == ~0u) {
+            const uint32_t i = it.a, h = base + i;
+            static thread_local std::vector<uint32_t> C;
+            C.clear();
+            for (uint32_t g = 0; g < h; ++g)
+                if (!S->redundant[g] && w.first[g] >= i) C.push_back(g);
+            std::vector<PairL> &out = w.fresh[i];
+            new_pairs(o, h, C, out);
+            size_t n = 0;
+            for (const PairL &pr : out) {
+                bool drop = false;
+                for (uint32_t f = i + 1; f < w.k && !drop; ++f) drop = o.dropped_by(pr, base + f);
+                if (!drop) out[n++] = pr;
+            }
+            out.resize(n);
+        } else {
+            for (uint32_t q = it.a; q < it.b; ++q) {
+                const PairL &pr = S->pairs[q];
+                for (uint32_t f = 0; f < w.k; ++f)
+                    if (o.dropped_by(pr, base + f)) {
+                        w.keep[q] = 0;
+                        break;
+                    }
+            }
+        }
+    });
+    run(nj, [&](size_t j) {
+        gb_system *S = Ss[j];
+        Sys &w = W[j];
+        if (!w.k) return;
+        size_t n = 0;
+        for (size_t q = 0; q < S->pairs.size(); ++q)
+            if (w.keep[q]) S->pairs[n++] = S->pairs[q];
+        S->pairs.resize(n);
+        for (const auto &v : w.fresh) S->pairs.insert(S->pairs.end(), v.begin(), v.end());
+        for (size_t e = 0; e < S->lm.size(); ++e)
+            if (w.first[e] < w.k) S->redundant[e] = 1;
+    });
 }
 
 // record a new leading monomial (SWAR form, and whether the fast comparisons still apply)
@@ -391,7 +485,7 @@ static void append_host_poly(gb_system *S, const Mono &lm, uint32_t len) {
     S->nterms += len;
     push_lm(S, lm);
     if (mono_deg(lm, (int)S->n) == 0) S->unit = true;
-    gm_update(S, (uint32_t)(S->lm.size() - 1));
+    update_steps(nullptr, {S}, {(uint32_t)(S->lm.size() - 1)});
 }
 
 bool is_prime32(uint32_t q) {
@@ -606,14 +700,16 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
     std::vector<std::vector<Mono>> lms;
     append_echelon(Ep, lms);
     const auto tp = Clock::now();
-    parallel_for(ctx, nj, [&](size_t j) {
+    std::vector<uint32_t> h0(nj);
+    for (size_t j = 0; j < nj; ++j) {
         gb_system *S = Ss[j];
+        h0[j] = (uint32_t)S->lm.size();
         for (const Mono &m : lms[j]) {
             push_lm(S, m);
             if (mono_deg(m, (int)S->n) == 0) S->unit = true;
-            gm_update(S, (uint32_t)(S->lm.size() - 1));
         }
-    });
+    }
+    update_steps(ctx, Ss, h0);
     const auto t2 = Clock::now();
     for (size_t j = 0; j < nj; ++j) {
         gb_system *S = Ss[j];
@@ -648,6 +744,7 @@ void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *st
         st.ms_mm = ech->ms_mm;
         st.mm_flops = ech->mm_flops;
         st.mm_launches = ech->mm_launches;
+        st.rref_sketched = ech->sketched;
         S->run.steps = S->steps;
         S->run.nnz_total += st.nnz;
         S->run.nnz_steps += st.nnz;

@@ -300,6 +300,7 @@ struct gb_echelon {
     float ms_reduce = 0.f, ms_rref = 0.f, ms_reduce_kernel = 0.f;
     double ms_mm = 0.0, mm_flops = 0.0;  // tensor-core product launches (MmTimer)
     uint64_t mm_launches = 0;
+    uint32_t sketched = 0;  // RREF(D') from a random sketch of D' (checked exactly)
 };
 
 struct gb_system {
@@ -453,6 +454,12 @@ struct MmPlan {
     struct Maps;
     Maps *maps;
 };
+
+// C <- C -/+ A B mod p on the tensor cores (A m x k, B k x n, C m x n; row pitches in elements),
+// enqueued on st; digit planes and any staging come from the arena (mm.cu)
+void matmul_dev(Arena &ar, const Fp &fp, uint32_t m, uint32_t n, uint32_t k, const uint32_t *A, uint64_t lda,
+                const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc, bool subtract, uint32_t *err,
+                cudaStream_t st);
 
 // ---- dense blocked reduction of the non-pivot rows (dense.cu) --------------------------------
 struct DenseJob {

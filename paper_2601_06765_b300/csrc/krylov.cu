@@ -120,14 +120,6 @@ __global__ void k_hankel(const unsigned long long *__restrict__ S, uint32_t d, u
     }
 }
 
-// SplitMix64 (Steele, Lea, Flood 2014): the coefficients of the random combinations below
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
-    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 // 32 random combinations (batch t) of all nf kernel vectors of H: R[i][l] = coefficient of
 // kernel vector i in combination l; C[F[i]][l] = R[i][l] and C[P_k][l] = -sum_i RREF[k][F[i]] R[i][l]
 __global__ void k_combination_coeffs(uint32_t nf, uint32_t t, uint32_t p, uint32_t *__restrict__ R) {

@@ -706,6 +706,33 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
 
 thread_local MmTimer *t_mm_timer = nullptr;
 
+void matmul_dev(Arena &ar, const Fp &fp, uint32_t m, uint32_t n, uint32_t k, const uint32_t *A, uint64_t lda,
+                const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc, bool subtract, uint32_t *err,
+                cudaStream_t st) {
+    if (!m || !n || !k) return;
+    const uint32_t L = digits_for(fp.p);
+    DigitPlanes DA, DB;
+    DA.alloc(ar, L, m, k, st);
+    DB.alloc(ar, L, n, k, st);
+    to_digits(A, lda, 1, DA, fp.p, st);
+    to_digits(B, 1, ldb, DB, fp.p, st);  // B^T: row j holds column j of B
+    // the kernel moves C tiles by TMA: rows must start on 16-byte boundaries, else C is staged
+    DBuf<uint32_t> Cs;
+    uint32_t *Cw = C;
+    uint64_t ldw = ldc;
+    if (ldc % 4 || (reinterpret_cast<uintptr_t>(C) & 15)) {
+        ldw = (n + 3) / 4 * 4;
+        Cs.alloc(ar, (size_t)m * ldw, st);
+        Cw = Cs.p;
+        GB_CUDA(cudaMemcpy2DAsync(Cw, 4 * ldw, C, 4 * ldc, 4ull * n, m, cudaMemcpyDeviceToDevice, st));
+    }
+    const uint32_t kmax = mm_kmax(fp.p);
+    const MmPlan plan(DA, DB, Cw, ldw, m, n, fp);
+    for (uint32_t k0 = 0; k0 < k; k0 += kmax)
+        plan.update(k0, 0, k0, 0, 0, 0, m, n, std::min(kmax, k - k0), subtract, err, st);
+    if (Cw != C) GB_CUDA(cudaMemcpy2DAsync(C, 4 * ldc, Cw, 4 * ldw, 4ull * n, m, cudaMemcpyDeviceToDevice, st));
+}
+
 double MmTimer::elapsed_ms() const {
     double ms = 0.0;
     for (size_t i = 0; i + 1 < used; i += 2) {

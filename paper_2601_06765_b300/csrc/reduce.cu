@@ -900,6 +900,108 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
     }
 }
 
+// The same panel solve with the panel's columns spread over a cluster of PCS blocks: block q holds
+// the columns [q S, (q + 1) S) of all panel rows in its shared memory (S = ceil(nb / PCS)).  The
+// rows are taken in order (Gauss-Jordan): per row, every block finds its first non-zero column,
+// one cluster barrier makes these visible and every block takes their minimum c (the row is zero
+// when there is none); the block owning column c writes column c of every panel row and the
+// inverse of the pivot entry into every block's shared memory (distributed shared memory); after
+// a second barrier every block scales the row by the inverse and subtracts its multiple from
+// every other panel row on its own columns.  Per pivot that is two cluster barriers and one sweep
+// of a block's share of the panel, against one block's sweeps of whole rows in k_panel_rref.
+// Eliminating each pivot column from all other panel rows at once (instead of reducing a row by
+// the earlier pivots when its turn comes) gives the same pivots and the same reduced rows: a
+// row's reduction modulo the span of the earlier pivot rows, with zeros at their pivot columns,
+// is unique, and so is the reduced echelon form of the panel's pivot rows.
+constexpr int PCS = 8;      // blocks per cluster
+constexpr int PCT = 1024;   // threads per block
+constexpr uint32_t PANEL_CLUSTER_MAX_NB = PCS * 3200;  // 4 KP S bytes of shared memory per block
+constexpr uint32_t PANEL_CLUSTER_MIN_NB = 1024;         // narrower panels: one block (k_panel_rref)
+__global__ void __cluster_dims__(PCS, 1, 1) __launch_bounds__(PCT)
+    k_panel_rref_cl(const RrefJob *__restrict__ jobs, const int *__restrict__ list) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) uint32_t slab[];  // KP rows of S columns
+    __shared__ uint32_t s_min[2];       // this block's first non-zero column of the row, by parity
+    __shared__ uint32_t s_col[KP + 1];  // column c of the panel rows, then the pivot's inverse
+    __shared__ uint32_t red[32], s_row[KP], s_c;
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t q = cl.block_rank();
+    const RrefJob &X = jobs[list[blockIdx.x / PCS]];
+    const Fp fp = X.fp;
+    const uint32_t P = X.state[1], nb = X.nb, S = (nb + PCS - 1) / PCS;
+    const uint32_t c0 = min(nb, q * S), w = min(nb, c0 + S) - c0;
+    if (threadIdx.x < KP) s_row[threadIdx.x] = threadIdx.x < P ? X.panel[threadIdx.x] : 0u;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < w; j += PCT)  // eight rows' loads in flight before their stores
+        for (uint32_t t0 = 0; t0 < P; t0 += 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (uint32_t t = 0; t < 8; ++t)
+                if (t0 + t < P) v[t] = X.M[(size_t)s_row[t0 + t] * X.ldm + c0 + j];
+#pragma unroll
+            for (uint32_t t = 0; t < 8; ++t)
+                if (t0 + t < P) slab[(size_t)(t0 + t) * S + j] = v[t];
+        }
+    __syncthreads();
+    uint32_t nnew = 0;
+    for (uint32_t t = 0; t < P; ++t) {
+        const uint32_t par = t & 1u;
+        uint32_t *row = slab + (size_t)t * S;
+        uint32_t c = NOLEAD;
+        for (uint32_t j = threadIdx.x; j < w; j += PCT)
+            if (row[j]) { c = c0 + j; break; }
+        c = block_min(c, red);
+        if (threadIdx.x == 0) s_min[par] = c;
+        cl.sync();
+        if (threadIdx.x < 32) {
+            uint32_t m = threadIdx.x < PCS ? *cl.map_shared_rank(&s_min[par], threadIdx.x) : NOLEAD;
+            for (int d = 16; d; d >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, d));
+            if (threadIdx.x == 0) s_c = m;
+        }
+        __syncthreads();
+        c = s_c;
+        if (c == NOLEAD) {  // the row reduced to zero (s_min is double-buffered: no second barrier)
+            if (q == 0 && threadIdx.x == 0) X.lead[s_row[t]] = NOLEAD;
+            continue;
+        }
+        if (c - c0 < w && threadIdx.x <= KP) {  // this block owns column c: publish it
+            const uint32_t u = threadIdx.x;
+            uint32_t v = 0;
+            if (u < KP) v = u < P && u != t ? slab[(size_t)u * S + (c - c0)] : 0u;
+            else v = fp.small ? fp_inv_small(row[c - c0], fp) : fp_inv(row[c - c0], fp);
+#pragma unroll
+            for (int r = 0; r < PCS; ++r) *cl.map_shared_rank(&s_col[u], r) = v;
+        }
+        cl.sync();
+        const uint32_t inv = s_col[KP];
+        for (uint32_t j = (c > c0 ? c - c0 : 0) + threadIdx.x; j < w; j += PCT) {
+            const uint32_t y = fp_mul(row[j], inv, fp);
+            row[j] = y;
+            if (!y) continue;
+            for (uint32_t u = 0; u < P; ++u) {
+                const uint32_t m = s_col[u];
+                if (m) slab[(size_t)u * S + j] = fp_sub(slab[(size_t)u * S + j], fp_mul(m, y, fp), fp);
+            }
+        }
+        if (q == 0 && threadIdx.x == 0) {
+            X.panel[KP + nnew] = s_row[t];
+            X.panel[2 * KP + nnew] = c;
+            X.order[X.state[0] + nnew] = s_row[t];
+            X.lead[s_row[t]] = c;
+            X.pcol[s_row[t]] = c;
+        }
+        ++nnew;
+        __syncthreads();
+    }
+    for (uint32_t j = threadIdx.x; j < w; j += PCT)  // the panel back (pivot rows reduced, the rest zero)
+        for (uint32_t t = 0; t < P; ++t) X.M[(size_t)s_row[t] * X.ldm + c0 + j] = slab[(size_t)t * S + j];
+    if (q == 0 && threadIdx.x == 0) {
+        X.state[2] = nnew;
+        X.state[0] += nnew;
+    }
+    cl.sync();  // no block leaves while another may still reach into its shared memory
+}
+
 // every other row: r <- r - sum_k r[pc_k] * Q_k over the panel's new pivot rows Q_k; one block per
 // row, so a row's multipliers are read before any thread writes the row
 __global__ void k_eliminate(const RrefJob *__restrict__ jobs, const uint32_t *__restrict__ bstart, int nj) {
@@ -1254,6 +1356,114 @@ static int rref_schedule(const gb_ctx *ctx, uint32_t p, uint32_t nC, uint32_t nb
     return nj == 1 ? tuned_choice(ctx, tune_key(TUNE_RREF, p, nC, nb, 0)) : -1;
 }
 
+// ---- the echelon form of a tall, low-rank D' through a random sketch ----------------------------
+//
+// RREF(D') is the canonical basis of the row space of D'.  For a random R (rs x nC), S = R D'
+// spans the same space whenever rank S = rank D', which holds with high probability once rs
+// exceeds the rank; then RREF(S) = RREF(D').  S is one product on the tensor cores, and its
+// echelon form works on rs rows instead of nC (at the n=13 workload's largest step, 512 rows
+// instead of 6864 for a rank of 429).  The result is then checked exactly: every row v of D' must
+// be sum_k v[piv_k] RREF(S)_k, i.e. D' - D'[:, piv] RREF(S) = 0 (one more product and a zero
+// test).  A sketch of nearly full rank, or a failed check, falls back to the full echelon form,
+// so the result is RREF(D') in every case.
+constexpr uint32_t SKETCH_ROWS = 512, SKETCH_MIN_ROWS = 2048;
+
+__global__ void k_sketch_rows(uint64_t n, uint32_t cols, uint32_t p, unsigned long long seed, bool rank1,
+                              uint32_t *__restrict__ R) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x)
+        R[t] = (uint32_t)(splitmix64(seed + (rank1 ? t % cols : t)) % p);
+}
+
+__global__ void k_gather_pivot_cols(const uint32_t *__restrict__ D, uint32_t nC, uint32_t nb,
+                                    const uint32_t *__restrict__ piv, uint32_t rank, uint32_t *__restrict__ A) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < (uint64_t)nC * rank;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = t / rank, k = t % rank;
+        A[t] = D[i * nb + piv[k]];
+    }
+}
+
+__global__ void k_any_nonzero(const uint32_t *__restrict__ C, uint32_t rows, uint32_t cols, uint64_t ld,
+                              uint32_t *__restrict__ flag) {
+    bool nz = false;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < (uint64_t)rows * cols;
+         t += (uint64_t)gridDim.x * blockDim.x)
+        nz |= C[(t / cols) * ld + t % cols] != 0u;
+    if (__any_sync(0xffffffffu, nz) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+static unsigned grid_of(uint64_t items) {
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + 255) / 256, 148ull * 16));
+}
+
+static uint64_t env_u64(const char *name, uint64_t fallback) {
+    const char *v = std::getenv(name);
+    return v ? std::strtoull(v, nullptr, 0) : fallback;
+}
+
+// true: E->rank, rref, rpiv hold RREF(E->dprime); false: nothing is set (the caller runs the full
+// echelon form).  GB_SKETCH_ROWS / GB_SKETCH_RANK1 in the environment are test hooks: fewer sketch
+// rows, or a sketch of rank one (whose check must fail on a matrix of larger rank).
+static bool echelon_by_sketch(gb_ctx *ctx, gb_echelon *E, const Fp &fp, uint32_t *derr) {
+    Arena &ar = ctx->arena;
+    cudaStream_t st = ctx->stream;
+    const uint32_t nC = E->nC, nb = E->nb;
+    const uint32_t rs = (uint32_t)std::min<uint64_t>(env_u64("GB_SKETCH_ROWS", SKETCH_ROWS), nC / 2);
+    const uint32_t margin = std::min<uint32_t>(32, rs / 4);
+    if (rs < 8) return false;
+    const bool rank1 = env_u64("GB_SKETCH_RANK1", 0) != 0;
+    DBuf<uint32_t> R;
+    R.alloc(ar, (size_t)rs * nC, st);
+    k_sketch_rows<<<grid_of((uint64_t)rs * nC), 256, 0, st>>>((uint64_t)rs * nC, nC, fp.p, 0x243F6A8885A308D3ull,
+                                                               rank1, R.p);
+    counted();
+    gb_echelon Es;
+    Es.nC = rs;
+    Es.nb = nb;
+    {
+        const uint64_t lds = (nb + 3) / 4 * 4;
+        DBuf<uint32_t> S;
+        S.alloc(ar, (size_t)rs * lds, st);
+        GB_CUDA(cudaMemsetAsync(S.p, 0, 4ull * rs * lds, st));
+        matmul_dev(ar, fp, rs, nb, nC, R.p, nC, E->dprime.p, nb, S.p, lds, false, derr, st);
+        R.reset();
+        Es.dprime.alloc(ar, (size_t)rs * nb, st);
+        GB_CUDA(cudaMemcpy2DAsync(Es.dprime.p, 4ull * nb, S.p, 4ull * lds, 4ull * nb, rs, cudaMemcpyDeviceToDevice, st));
+    }
+    echelon_stage(ctx, {&Es}, {fp}, derr);  // rs < SKETCH_MIN_ROWS rows: the full path
+    const uint32_t rank = Es.rank;
+    if (rank + margin > rs) return false;   // the sketch may not hold the whole row space
+    DBuf<uint32_t> flag;
+    flag.alloc(ar, 1, st);
+    GB_CUDA(cudaMemsetAsync(flag.p, 0, 4, st));
+    if (rank) {
+        const uint64_t ldc = (nb + 3) / 4 * 4;
+        DBuf<uint32_t> A, C;
+        A.alloc(ar, (size_t)nC * rank, st);
+        k_gather_pivot_cols<<<grid_of((uint64_t)nC * rank), 256, 0, st>>>(E->dprime.p, nC, nb, Es.rpiv.p, rank, A.p);
+        counted();
+        C.alloc(ar, (size_t)nC * ldc, st);
+        GB_CUDA(cudaMemcpy2DAsync(C.p, 4ull * ldc, E->dprime.p, 4ull * nb, 4ull * nb, nC, cudaMemcpyDeviceToDevice, st));
+        matmul_dev(ar, fp, nC, nb, rank, A.p, rank, Es.rref.p, nb, C.p, ldc, true, derr, st);
+        k_any_nonzero<<<grid_of((uint64_t)nC * nb), 256, 0, st>>>(C.p, nC, nb, ldc, flag.p);
+        counted();
+    } else {
+        k_any_nonzero<<<grid_of((uint64_t)nC * nb), 256, 0, st>>>(E->dprime.p, nC, nb, nb, flag.p);
+        counted();
+    }
+    uint32_t *h = static_cast<uint32_t *>(ctx_pinned(ctx, 16));
+    GB_CUDA(cudaMemcpyAsync(h, flag.p, 4, cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(h + 1, derr, 4, cudaMemcpyDeviceToHost, st));
+    ctx_sync(ctx);
+    if (h[1]) fail(GB_ETIMEOUT, "sketched echelon form: a bounded wait in the tensor-core kernel gave up");
+    if (h[0]) return false;  // some row of D' lies outside the sketch's row space
+    E->rank = rank;
+    E->rref = std::move(Es.rref);
+    E->rpiv = std::move(Es.rpiv);
+    E->sketched = 1;
+    return true;
+}
+
 // RREF of each job's dense matrix Es[j]->dprime (Es[j]->nC x Es[j]->nb, row pitch nb) over F_p
 // with fps[j] (Sec. 9.2 panel elimination): sets Es[j]->rank, rref, rpiv.  Bounded waits of the
 // tensor-core updates that give up are flagged in derr.
@@ -1263,6 +1473,15 @@ void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::
     cudaStream_t st = ctx->stream;
     const int nj = (int)Es.size();
     std::vector<uint32_t> rank(nj, 0);
+    // tall D' (many more rows than its rank, as at the large steps): a random sketch first, on
+    // request (measured: no faster than the full form once the panel solve runs on a cluster)
+    std::vector<uint8_t> done(nj, 0);
+    const uint64_t min_rows = env_u64("GB_SKETCH_MIN_ROWS", SKETCH_MIN_ROWS);
+    const uint64_t min_entries = min_rows < SKETCH_MIN_ROWS ? 0 : (1ull << 22);
+    if (ctx->flags & GB_CTX_SKETCH)
+        for (int j = 0; j < nj; ++j)
+            if (Es[j]->nC >= min_rows && Es[j]->nb && (uint64_t)Es[j]->nC * Es[j]->nb >= min_entries)
+                done[j] = echelon_by_sketch(ctx, Es[j], fps[j], derr) ? 1 : 0;
     // per-job working state, one allocation each
     std::vector<RrefJob> X(nj);
     std::vector<DBuf<uint32_t>> Mw(nj), lead(nj), pcol(nj), order(nj), panel(nj);
@@ -1271,7 +1490,10 @@ void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::
     GB_CUDA(cudaMemsetAsync(states.p, 0, 16ull * nj + 16, st));
     RoundGraph graph;
     unsigned graph_nodes = 0;
-    std::vector<int> live, smem_jobs, glob_jobs, tc_jobs;
+    std::vector<int> live, smem_jobs, cl_jobs, glob_jobs, tc_jobs;
+    // panels of rows wider than this are solved by a cluster of blocks (k_panel_rref_cl);
+    // GB_PANEL_CLUSTER_MIN_NB in the environment moves the bound (a test hook)
+    const uint64_t panel_cluster_min_nb = env_u64("GB_PANEL_CLUSTER_MIN_NB", PANEL_CLUSTER_MIN_NB);
     std::vector<DigitPlanes> FA(nj), FB(nj);
     std::vector<std::unique_ptr<MmPlan>> plans(nj);
     for (int j = 0; j < nj; ++j) {
@@ -1280,7 +1502,7 @@ void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::
         X[j].nC = nC;
         X[j].nb = nb;
         X[j].fp = fps[j];
-        if (!nC || !nb) continue;
+        if (!nC || !nb || done[j]) continue;
         X[j].ldm = (nb + 3) / 4 * 4;
         Mw[j].alloc(ar, (size_t)nC * X[j].ldm, st);
         lead[j].alloc(ar, nC, st);
@@ -1311,7 +1533,9 @@ void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::
         X[j].state = states.p + 4 * j;
         X[j].panel = panel[j].p;
         live.push_back(j);
-        (4ull * KP * nb <= 200 * 1024 ? smem_jobs : glob_jobs).push_back(j);
+        if (nb >= panel_cluster_min_nb && nb <= PANEL_CLUSTER_MAX_NB) cl_jobs.push_back(j);
+        else if (4ull * KP * nb <= 200 * 1024) smem_jobs.push_back(j);
+        else glob_jobs.push_back(j);
     }
     if (!live.empty()) {
         std::vector<uint32_t> rows(nj, 0);
@@ -1322,6 +1546,7 @@ void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::
         lists.alloc(ar, (size_t)nj + 1, st);
         {
             std::vector<int> l(smem_jobs);
+            l.insert(l.end(), cl_jobs.begin(), cl_jobs.end());
             l.insert(l.end(), glob_jobs.begin(), glob_jobs.end());
             int *hl = static_cast<int *>(ctx_pinned(ctx, 4ull * (l.size() + 1)));
             std::memcpy(hl, l.data(), 4 * l.size());
@@ -1330,6 +1555,9 @@ void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::
         size_t pan_bytes = 0;
         for (int j : smem_jobs) pan_bytes = std::max<size_t>(pan_bytes, 4ull * KP * X[j].nb);
         if (!smem_jobs.empty()) opt_in_smem(reinterpret_cast<const void *>(k_panel_rref<true>));
+        size_t cl_bytes = 0;
+        for (int j : cl_jobs) cl_bytes = std::max<size_t>(cl_bytes, 4ull * KP * ((X[j].nb + PCS - 1) / PCS));
+        if (!cl_jobs.empty()) opt_in_smem(reinterpret_cast<const void *>(k_panel_rref_cl));
         // jobs are packed in the job table at their own index; k_pick_panel runs on all of them
         // (a job without rows has no blocks elsewhere and its state stays zero)
         k_leads<<<G.totals[0], 256, 0, st>>>(G.jobs, G.plans[0], nj);
@@ -1343,10 +1571,14 @@ void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::
             k_pick_panel<<<nj, 1024, 0, s>>>(G.jobs);
             if (!smem_jobs.empty())
                 k_panel_rref<true><<<(unsigned)smem_jobs.size(), PT, pan_bytes, s>>>(G.jobs, lists.p);
+            if (!cl_jobs.empty())
+                k_panel_rref_cl<<<(unsigned)(PCS * cl_jobs.size()), PCT, cl_bytes, s>>>(G.jobs,
+                                                                                      lists.p + smem_jobs.size());
             if (!glob_jobs.empty())
-                k_panel_rref<false><<<(unsigned)glob_jobs.size(), PT, 0, s>>>(G.jobs, lists.p + smem_jobs.size());
+                k_panel_rref<false><<<(unsigned)glob_jobs.size(), PT, 0, s>>>(
+                    G.jobs, lists.p + smem_jobs.size() + cl_jobs.size());
             k_eliminate<<<G.totals[0], 256, 0, s>>>(G.jobs, G.plans[0], nj);
-            counted(2 + (smem_jobs.empty() ? 0 : 1) + (glob_jobs.empty() ? 0 : 1));
+            counted(2 + (smem_jobs.empty() ? 0 : 1) + (cl_jobs.empty() ? 0 : 1) + (glob_jobs.empty() ? 0 : 1));
             for (int j : tc_jobs) {
                 const unsigned nt = (unsigned)(((size_t)X[j].nC + X[j].nb) * KP);
                 if (FA[j].L == 2) k_elim_digits<2><<<(nt + 255) / 256, 256, 0, s>>>(G.jobs, j);
