@@ -30,7 +30,8 @@
 //                    alternate tiles) and issues the products from lane 0
 //   warps 2-17       epilogue (four warps per tensor-memory lane quarter): drains a set as soon as
 //                    its products are done (tcgen05.ld of every diagonal, exact conversion,
-//                    sum_s D_s (256^s mod p)), hands it back, then one Barrett reduction and the
+//                    sum_s D_s (256^s mod p)), zeroes it (tcgen05.st) and hands it back, so that
+//                    every product accumulates; then one Barrett reduction and the
 //                    read-modify-write of the C tile in shared memory; one of its threads issues
 //                    the TMA store and loads the C tile of a later tile into the freed buffer
 // so that one set's products run while the other is drained.  Every wait is bounded; a wait that
@@ -192,6 +193,21 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[N]) {
     }
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// zeros into N = 8 or 16 consecutive 32-bit columns of this thread's tensor-memory lane
+template <int N>
+__device__ __forceinline__ void tmem_zero(uint32_t taddr) {
+    if constexpr (N == 16) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+            "r"(0u)
+            : "memory");
+    } else {
+        static_assert(N == 8, "8 or 16 columns");
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(0u)
+                     : "memory");
+    }
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 
 // Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle: rows of 128 bytes,
@@ -292,6 +308,18 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot_g);
     const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(CPT * grp);
+    // Every product accumulates: the epilogue zeroes both accumulator sets here and each set again
+    // right after draining it, so no product has to open a diagonal by overwriting it.
+    if (warp >= 2) {
+#pragma unroll
+        for (int set = 0; set < 2; ++set)
+#pragma unroll
+            for (int d = 0; d < Cfg::DIAG; ++d) tmem_zero<CPT>(trow + (uint32_t)set * Cfg::SET_COLS + (uint32_t)(BN * d));
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0 && lane == 0) {
         // ---- producer.  K block kb of the it-th tile is the g-th block of the ring sequence,
@@ -331,9 +359,7 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
         // For each K step of 16 and each A digit i, one M=128, N=128, K=16 product of A_i with all
         // L digits of B^T at once: its N columns are the products A_i B_j, j = 0..L-1, BN each,
         // and its accumulator window starts at diagonal i, so A_i B_j lands on diagonal i + j.
-        // The first K step of a tile starts the diagonals: A_0's product overwrites diagonals
-        // 0..L-1, and A_i (i >= 1) opens diagonal i + L - 1 with its last digit alone (overwrite)
-        // while its other digits accumulate into diagonals the earlier digits opened.
+        // Every product accumulates into a set the epilogue has zeroed.
         int arow = -1;
         uint32_t a_loads = 0;
         const uint32_t a_lo = sdesc_lo(sA), b_lo = sdesc_lo(sB);
@@ -366,16 +392,7 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                             for (int i = 0; i < L; ++i) {
                                 const uint64_t ad = sdesc_of(a_lo + (((uint32_t)(i * Cfg::KB + kb) * Cfg::A_BLK + kk * 32) >> 4));
                                 const uint32_t bd = bs + ((kk * 32) >> 4);
-                                if (kb > 0 || kk > 0) {
-                                    mma_bf16(tbase + (uint32_t)(BN * i), ad, sdesc_of(bd), idesc(MM_MMA_N), 1u);
-                                } else if (i == 0) {
-                                    mma_bf16(tbase, ad, sdesc_of(bd), idesc(MM_MMA_N), 0u);
-                                } else {
-                                    // digits 0..L-2 of B^T (rows 0 .. (L-1) BN - 1), then digit L-1
-                                    mma_bf16(tbase + (uint32_t)(BN * i), ad, sdesc_of(bd), idesc(BN * (L - 1)), 1u);
-                                    mma_bf16(tbase + (uint32_t)(BN * (i + L - 1)), ad,
-                                             sdesc_of(bd + (((uint32_t)(L - 1) * BN * 128u) >> 4)), idesc(BN), 0u);
-                                }
+                                mma_bf16(tbase + (uint32_t)(BN * i), ad, sdesc_of(bd), idesc(MM_MMA_N), 1u);
                             }
                         }
                     }
@@ -425,6 +442,8 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 for (int d = 0; d < Cfg::DIAG; ++d) tmem_ld<CPT>(tb + (uint32_t)(BN * d), v[d]);
                 tmem_wait_ld();
 #pragma unroll
+                for (int d = 0; d < Cfg::DIAG; ++d) tmem_zero<CPT>(tb + (uint32_t)(BN * d));
+#pragma unroll
                 for (int d = 0; d < Cfg::DIAG; ++d) {
                     const long long rdd = (long long)P.rd[d];
                     if (small_diag<L>(d)) {
@@ -436,7 +455,8 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                     }
                 }
             }
-            // the set is drained: hand it back
+            // the set is drained and zeroed: hand it back
+            tmem_wait_st();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(r_empty(set));
