@@ -236,6 +236,7 @@ def run_ours(args) -> None:
     n13 = guarded(measure_sparse_n13, gb, synth, local, pk, runs, graphs=not args.no_graphs) if extra else None
     deglex = guarded(measure_deglex, gb, synth, ctx) if extra else None
     wied = guarded(measure_wiedemann, gb, synth, local, pk) if extra else None
+    f5 = guarded(measure_f5, gb, synth, local) if extra else None
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
              for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_mm", "ms_rref", "ms_update", "ms_pairs",
                        "ms_select", "ms_finish", "ms_wall")}
@@ -269,6 +270,7 @@ def run_ours(args) -> None:
             "sparse_n13": n13,
             "deglex": deglex,
             "block_wiedemann": wied,
+            "f5_signatures": f5,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -626,6 +628,44 @@ def measure_wiedemann(gb, synth, local: int, pk: dict) -> dict:
                     "(8 B); the 32-wide vector blocks are L2-resident"}
 
 
+def measure_f5(gb, synth, local: int, nvars: int = 7) -> dict:
+    """The signature-filtered path (gb_f5_groebner: F5 criterion on the device, degree-by-degree
+    Macaulay blocks through the same SP / reduction / RREF kernels) on the homogenised dense
+    quadratic system, with the criterion and without it (every candidate row kept), and the F4 path
+    on the same system for reference.  All three give the same reduced basis."""
+    system = synth.homogenize(synth.dense_system(nvars, nvars, synth.P16, synth.BASE_SEED + 52))
+    dmax = nvars + 2
+    ctx = gb.Context(device=local, arena_bytes=64 << 30)
+    out = {"workload": f"n={nvars} dense random quadratics (all monomials of degree <= 2), p=65521, "
+                       f"homogenised (n+1 = {nvars + 1} variables, grevlex), degrees {2}..{dmax}"}
+    for crit in (True, False):
+        runs = []
+        for rep in range(3):
+            with gb.System(ctx, system) as S:
+                t0 = time.perf_counter()
+                blocks, st = S.f5(dmax, crit)
+                runs.append((1e3 * (time.perf_counter() - t0), st, len(blocks)))
+        ms, st, nb = min(runs, key=lambda r: r[0])
+        out["criterion" if crit else "unfiltered"] = {
+            "ms": round(ms, 2), "blocks": nb, "candidate_rows": st["candidates"], "admissible_rows": st["admissible"],
+            "zero_reductions": st["zero_reductions"], "nnz": st["nnz"], "basis_elements": st["nbasis"],
+            "stage_ms": {k: round(st[k], 2) for k in ("ms_filter", "ms_sp", "ms_reduce", "ms_rref", "ms_finish")}}
+    f4 = []
+    for rep in range(3):
+        with gb.System(ctx, system) as S:
+            t0 = time.perf_counter()
+            S.groebner()
+            f4.append(1e3 * (time.perf_counter() - t0))
+    ctx.close()
+    c, u = out["criterion"], out["unfiltered"]
+    out["rows_removed_frac"] = round(1 - c["admissible_rows"] / c["candidate_rows"], 4)
+    out["speedup_criterion_vs_unfiltered"] = round(u["ms"] / c["ms"], 3)
+    out["f4_ms_same_system"] = round(min(f4), 2)
+    out["note"] = ("host wall clock per run; the blocks are whole degree-d Macaulay matrices, so the RREF of "
+                   "full-rank D' blocks dominates, and F4's pair-driven matrices are far smaller on this system")
+    return out
+
+
 def measure_sp_paths(gb, synth, local: int, pk: dict, paths=("hash", "ranks")) -> dict:
     """The n=13 run step by step with each symbolic-preprocessing path (the hash dictionary and
     the rank bitmap): per-step device time of the stage and its share of HBM bandwidth on the
@@ -749,7 +789,7 @@ def main() -> None:
     ap.add_argument("--arena-gb", type=int, default=48, help="device arena of the context (GiB)")
     ap.add_argument("--sp", choices=["hash", "ranks", "both"], default="both",
                     help="--only sp_compare: the symbolic-preprocessing path(s) to run")
-    ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10", "wiedemann", "sp_compare", "served",
+    ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10", "wiedemann", "f5", "sp_compare", "served",
                                        "headline"],
                     default=None,
                     help="run one secondary measurement alone and print its JSON (for profiling)")
@@ -784,6 +824,8 @@ def main() -> None:
             ctx.close()
         elif args.only == "wiedemann":
             print(json.dumps({"block_wiedemann": measure_wiedemann(gb, synth, 0, peaks())}))
+        elif args.only == "f5":
+            print(json.dumps({"f5_signatures": [measure_f5(gb, synth, 0, nv) for nv in (7, 8)]}))
         elif args.only == "dense_n10":
             ctx = gb.Context(device=0, arena_bytes=min(args.arena_gb, 4) << 30, graphs=not args.no_graphs)
             flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda:0")

@@ -393,6 +393,59 @@ gb_status gb_block_wiedemann(const gb_macaulay *mac, uint32_t b, const uint32_t 
                              const uint32_t *delta, uint32_t *seq, uint32_t *W, uint32_t wcap,
                              gb_krylov_stats *stats);
 
+/* ---- signature-filtered Macaulay matrices (F5 criterion) ------------------------------------------ */
+
+/* The admissibility predicate over packed signature keys, and the compaction of the survivors
+   (Sec. 14, "GPU-facing reformulation": a signature key per candidate row, the predicate evaluated
+   over row metadata in bulk, the survivors compacted by a scan).  The candidates are the
+   signatures x^a e_index, x^a running over the monomials of degree e in descending grevlex order;
+   candidate j (0 <= j < ncand) is admissible iff bit j of forbidden is clear (bit j % 32 of word
+   j / 32; forbidden is a DEVICE array of ceil(ncand / 32) words, or NULL: every candidate is
+   admissible).  The admissible candidates' packed keys (index << 40) | (e << 32) | j go to keys
+   (DEVICE, room for ncand) in increasing j, and their number to *count (HOST).  Runs on the
+   context's stream; returns when the count is on the host.
+   GB_EINVAL: null context or count, null keys with ncand > 0, index >= 2^24 or e > 255. */
+gb_status gb_sig_filter(gb_ctx *ctx, uint32_t index, uint32_t e, uint32_t ncand, const uint32_t *forbidden,
+                        uint64_t *keys, uint32_t *count);
+
+typedef struct {
+    uint32_t degree, index;      /* block (d, i): degree d, generator i (1-based, in input order) */
+    uint32_t candidates;         /* candidate rows x^a f_i: the monomials x^a of degree d - d_i */
+    uint32_t admissible;         /* those the F5 criterion keeps (all of them with GB_F5_NO_CRITERION) */
+    uint32_t rows;               /* rows of the block's matrix: the echelon rows of degree d, then the admissible candidates */
+    uint32_t ndict, npivot, nC;  /* its columns, pivot rows and other rows (0 when no candidate is admissible) */
+    uint32_t rank;               /* new basis elements: the reduced echelon rows of the non-pivot part */
+    uint32_t zero_reductions;    /* admissible rows that did not enlarge the row space */
+    float ms_filter, ms_sp, ms_reduce, ms_rref;  /* the filter (host clock, with its copies), device stages */
+} gb_f5_block;
+
+typedef struct {
+    uint32_t blocks, nbasis;     /* blocks run; elements of the reduced basis */
+    uint64_t candidates, admissible, zero_reductions;
+    uint64_t nnz;                /* nonzeros of the blocks' matrices */
+    double ms_wall, ms_filter, ms_sp, ms_reduce, ms_rref, ms_finish;
+} gb_f5_stats;
+
+#define GB_F5_NO_CRITERION 1u /* every candidate admissible: the unfiltered Macaulay matrices */
+
+/* The Groebner basis of a homogeneous system degree by degree through signature-filtered Macaulay
+   matrices (the signature regime of Thm. signature-sound, with F5's criterion as the predicate
+   Adm, position over term, e_1 < e_2 < ...).  For d from the least input degree to dmax and each
+   generator i with d_i <= d: the candidate rows x^a f_i (deg x^a = d - d_i) go through
+   gb_sig_filter with the leading monomials of the degree-(d - d_i) part of <f_1 .. f_{i-1}>
+   as the forbidden set; the admissible rows and the echelon rows of degree d found so far go
+   through symbolic preprocessing (without closure), the reduction and the RREF of D' on the
+   device, and the new elements join the basis.  Then the reduced basis of the elements whose
+   leading monomials are minimal, as gb_groebner leaves it (gb_basis_export).  It is the reduced
+   Groebner basis of the ideal when dmax reaches that basis's largest degree; for a regular
+   sequence no admissible row reduces to zero.  sys: a fresh system (no step run), grevlex, every
+   input homogeneous.  blocks (HOST, may be NULL): the first blocks_cap block records in order;
+   *nblocks (may be NULL): the number of blocks run.  stats may be NULL.
+   GB_EINVAL: a system that has run, an inhomogeneous input, dmax above 255 or below the least
+   input degree, an unknown flag.  GB_EUNSUPPORTED: deglex.  Otherwise as gb_groebner. */
+gb_status gb_f5_groebner(gb_system *sys, uint32_t dmax, uint32_t flags, gb_f5_block *blocks, uint32_t blocks_cap,
+                         uint32_t *nblocks, gb_f5_stats *stats);
+
 /* ---- the mod-p primitives, one at a time ------------------------------------------------------ */
 
 /* Each operation applies one of the device's F_p primitives elementwise: the same functions, with

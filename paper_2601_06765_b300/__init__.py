@@ -29,6 +29,7 @@ GB_CTX_REDUCE_DENSE = 4
 GB_CTX_NO_GRAPHS = 8
 GB_CTX_SP_HASH = 16
 GB_CTX_SKETCH = 32
+GB_F5_NO_CRITERION = 1
 GB_GREVLEX, GB_DEGLEX = 0, 1  # gb_order
 # gb_modp_op
 (GB_MODP_REDUCE64, GB_MODP_REDUCE32, GB_MODP_MULADD, GB_MODP_REDC, GB_MODP_TO_MONT, GB_MODP_MONT_MUL,
@@ -96,6 +97,21 @@ class gb_krylov_stats(ctypes.Structure):
                 ("ms_hankel", ctypes.c_double), ("ms_vectors", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
 
+class gb_f5_block(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_uint32), ("index", ctypes.c_uint32), ("candidates", ctypes.c_uint32),
+                ("admissible", ctypes.c_uint32), ("rows", ctypes.c_uint32), ("ndict", ctypes.c_uint32),
+                ("npivot", ctypes.c_uint32), ("nC", ctypes.c_uint32), ("rank", ctypes.c_uint32),
+                ("zero_reductions", ctypes.c_uint32), ("ms_filter", ctypes.c_float), ("ms_sp", ctypes.c_float),
+                ("ms_reduce", ctypes.c_float), ("ms_rref", ctypes.c_float)]
+
+
+class gb_f5_stats(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.c_uint32), ("nbasis", ctypes.c_uint32), ("candidates", ctypes.c_uint64),
+                ("admissible", ctypes.c_uint64), ("zero_reductions", ctypes.c_uint64), ("nnz", ctypes.c_uint64),
+                ("ms_wall", ctypes.c_double), ("ms_filter", ctypes.c_double), ("ms_sp", ctypes.c_double),
+                ("ms_reduce", ctypes.c_double), ("ms_rref", ctypes.c_double), ("ms_finish", ctypes.c_double)]
+
+
 class gb_server_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_uint64), ("system_steps", ctypes.c_uint64),
                 ("admitted", ctypes.c_uint64), ("finished", ctypes.c_uint64), ("busy_ms", ctypes.c_double),
@@ -158,6 +174,9 @@ _SIGS = {
     "gb_modp_apply": [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32] + [_vp] * 5,
     "gb_block_wiedemann": [_vp, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p, _u32p, ctypes.c_uint32,
                            ctypes.POINTER(gb_krylov_stats)],
+    "gb_sig_filter": [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _u32p],
+    "gb_f5_groebner": [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(gb_f5_block), ctypes.c_uint32, _u32p,
+                       ctypes.POINTER(gb_f5_stats)],
     "gb_matmul_modp": [_vp] + [ctypes.c_uint32] * 4 + [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _vp,
                                                        ctypes.c_uint64, ctypes.c_int],
 }
@@ -445,6 +464,27 @@ def gb_block_wiedemann(mac: int, b: int, X: np.ndarray, Z: np.ndarray, delta: np
     return out
 
 
+def gb_sig_filter(ctx: int, index: int, e: int, ncand: int, forbidden: int | None, keys: int) -> int:
+    """The F5 admissibility filter over one block of candidates (integer device addresses of the
+    forbidden bitmap, or None, and of the key output); returns the number of admissible keys.
+    See include/gb.h."""
+    count = ctypes.c_uint32(0)
+    check(lib().gb_sig_filter(ctx, index, e, ncand, forbidden or None, keys or None, ctypes.byref(count)),
+          "gb_sig_filter")
+    return count.value
+
+
+def gb_f5_groebner(sysh: int, dmax: int, criterion: bool = True, max_blocks: int = 4096) -> tuple[list, dict]:
+    """The signature-filtered (F5 criterion) Groebner basis of a homogeneous system up to degree
+    dmax: (block records, run statistics).  See include/gb.h."""
+    blocks = (gb_f5_block * max_blocks)()
+    nb = ctypes.c_uint32(0)
+    st = gb_f5_stats()
+    check(lib().gb_f5_groebner(sysh, dmax, 0 if criterion else GB_F5_NO_CRITERION, blocks, max_blocks,
+                               ctypes.byref(nb), ctypes.byref(st)), "gb_f5_groebner")
+    return [_struct_dict(blocks[i]) for i in range(min(nb.value, max_blocks))], _struct_dict(st)
+
+
 def gb_modp_apply(op: int, p: int, n: int, window: int, a: int, b: int | None, c: int | None, out: int,
                   stream: int | None = None) -> None:
     """One device F_p primitive applied elementwise (integer device addresses; b and c may be None
@@ -535,6 +575,9 @@ class System:
 
     def groebner(self) -> dict:
         return gb_groebner(self.h)
+
+    def f5(self, dmax: int, criterion: bool = True) -> tuple[list, dict]:
+        return gb_f5_groebner(self.h, dmax, criterion)
 
     def basis(self, reduced: bool = True):
         return basis_terms(*gb_basis_export(self.h, self.n, reduced))

@@ -16,11 +16,9 @@ void reduce_rows_noalloc(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC, uint3
 void f4_steps(const std::vector<gb_system *> &Ss, std::vector<gb_step_stats> *stats);
 void groebner_batch(const std::vector<gb_system *> &Ss);
 void system_init(gb_system *S, uint32_t nvars, uint32_t p, const gb_polys *F);
-void make_resident(const std::vector<gb_system *> &Ss);
 void autotune(gb_ctx *ctx, const std::vector<gb_system *> &Ss, gb_tune_report *rep);
 void tune_save(const gb_ctx *ctx, const char *path);
 void tune_load(gb_ctx *ctx, const char *path);
-std::vector<RowSpec> order_rows(const gb_system *S, std::vector<std::pair<Mono, uint32_t>> tk);
 
 static thread_local std::string t_last_error;
 std::atomic<unsigned long long> g_launches{0};
@@ -445,6 +443,31 @@ gb_status gb_f4_step(gb_system *S, gb_step_stats *stats) {
     std::vector<gb_step_stats> st;
     f4_steps({S}, &st);
     if (stats) *stats = st[0];
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_sig_filter(gb_ctx *ctx, uint32_t index, uint32_t e, uint32_t ncand, const uint32_t *forbidden,
+                        uint64_t *keys, uint32_t *count) {
+    GB_API_BEGIN
+    if (!ctx || !count || (ncand && !keys)) fail(GB_EINVAL, "null argument");
+    Enter entered(ctx);
+    *count = sig_filter(ctx, index, e, ncand, forbidden, reinterpret_cast<unsigned long long *>(keys));
+    return GB_OK;
+    GB_API_END
+}
+
+gb_status gb_f5_groebner(gb_system *S, uint32_t dmax, uint32_t flags, gb_f5_block *blocks, uint32_t blocks_cap,
+                         uint32_t *nblocks, gb_f5_stats *stats) {
+    GB_API_BEGIN
+    if (!S || (blocks_cap && !blocks)) fail(GB_EINVAL, "null argument");
+    if (flags & ~GB_F5_NO_CRITERION) fail(GB_EINVAL, "unknown flags");
+    Enter entered(S->ctx);
+    std::vector<gb_f5_block> out;
+    f5_groebner(S, dmax, flags, &out, stats);
+    const size_t k = std::min<size_t>(out.size(), blocks_cap);
+    if (k) std::memcpy(blocks, out.data(), k * sizeof(gb_f5_block));
+    if (nblocks) *nblocks = (uint32_t)out.size();
     return GB_OK;
     GB_API_END
 }

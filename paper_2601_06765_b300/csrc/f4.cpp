@@ -432,7 +432,7 @@ static void update_steps(gb_ctx *ctx, const std::vector<gb_system *> &Ss, const 
 }
 
 // record a new leading monomial (SWAR form, and whether the fast comparisons still apply)
-static void push_lm(gb_system *S, const Mono &m) {
+void push_lm(gb_system *S, const Mono &m) {
     S->lm.push_back(m);
     S->lm16.push_back(m16(m));
     for (uint32_t i = 0; i < S->n; ++i)

@@ -391,6 +391,18 @@ void echelon_stage(gb_ctx *ctx, const std::vector<gb_echelon *> &Es, const std::
 // the block Wiedemann path of gb_block_wiedemann (krylov.cu)
 void block_wiedemann(const gb_macaulay *mac, uint32_t b, const uint32_t *X, const uint32_t *Z, const uint32_t *delta,
                      uint32_t *seq, uint32_t *W, uint32_t wcap, gb_krylov_stats *stats);
+// host side of the F4 driver (f4.cpp): a new leading monomial in the host mirrors; rows (t, k) in
+// pivot order; the inputs of fresh systems onto the device; the reduced basis of finished systems
+void push_lm(gb_system *S, const Mono &m);
+std::vector<RowSpec> order_rows(const gb_system *S, std::vector<std::pair<Mono, uint32_t>> tk);
+void make_resident(const std::vector<gb_system *> &Ss);
+void finish_batch(const std::vector<gb_system *> &Ss);
+// the F5 criterion over one block of candidates (sig.cu): the admissible candidates' packed keys,
+// compacted into keys (device); returns their number
+uint32_t sig_filter(gb_ctx *ctx, uint32_t index, uint32_t e, uint32_t ncand, const uint32_t *forbidden,
+                    unsigned long long *keys);
+// gb_f5_groebner (f5.cpp)
+void f5_groebner(gb_system *S, uint32_t dmax, uint32_t flags, std::vector<gb_f5_block> *blocks, gb_f5_stats *stats);
 // append each job's echelon rows as new basis elements on the device; returns their LMs
 void append_echelon(const std::vector<gb_echelon *> &Es, std::vector<std::vector<Mono>> &lms);
 // final reduction: element elems[j][i] of job j becomes LM + row i of its D' (writes fin_*)

@@ -126,6 +126,36 @@ def sparse_system(n: int, m: int, p: int, seed: int, terms: int | tuple[int, int
     return _pack(n, p, polys)
 
 
+def homogeneous_system(n: int, m: int, p: int, seed: int, degree: int | list[int] = 2) -> dict:
+    """Every monomial of degree exactly d_i in polynomial i (d_i = `degree`, or the i-th entry of
+    a list of degrees), coefficients uniform in [1, p-1]: a homogeneous system, a regular sequence
+    with high probability when m <= n."""
+    rng = SplitMix64(seed)
+    degs = [degree] * m if isinstance(degree, int) else list(degree)
+    polys = []
+    for i in range(m):
+        mons = [e for e in monomials_upto(n, degs[i]) if sum(e) == degs[i]]
+        polys.append([(e, rng.between(1, p - 1)) for e in mons])
+    return _pack(n, p, polys)
+
+
+def homogenize(system: dict) -> dict:
+    """The system in n + 1 variables with every term of polynomial i raised to its degree by the
+    new last variable (the smallest one in grevlex): term x^a of a degree-D polynomial becomes
+    x^a h^(D - |a|)."""
+    n, p = int(system["n"]), int(system["p"])
+    polys = []
+    for i in range(int(system["m"])):
+        lo, hi = int(system["poly_off"][i]), int(system["poly_off"][i + 1])
+        exps = [tuple(int(x) for x in system["exps"][q][:n]) for q in range(lo, hi)]
+        if not exps:
+            polys.append([])
+            continue
+        top = max(sum(e) for e in exps)
+        polys.append([(e + (top - sum(e),), int(system["coeffs"][q])) for e, q in zip(exps, range(lo, hi))])
+    return _pack(n + 1, p, polys)
+
+
 # ---- the five workloads ---------------------------------------------------------------------
 
 def dense_n6(seed_index: int = 0) -> dict:
