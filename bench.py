@@ -789,7 +789,11 @@ def main() -> None:
     ap.add_argument("--arena-gb", type=int, default=48, help="device arena of the context (GiB)")
     ap.add_argument("--sp", choices=["hash", "ranks", "both"], default="both",
                     help="--only sp_compare: the symbolic-preprocessing path(s) to run")
+    ap.add_argument("--max-steps", type=int, default=0, help="--only n13_steps: stop after this many F4 steps")
+    ap.add_argument("--reduce", choices=["auto", "sparse", "dense"], default="auto",
+                    help="--only n13_steps: the reduction schedule of the context")
     ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10", "wiedemann", "f5", "sp_compare", "served",
+                                       "n13_steps",
                                        "headline"],
                     default=None,
                     help="run one secondary measurement alone and print its JSON (for profiling)")
@@ -805,6 +809,22 @@ def main() -> None:
         elif args.only == "sp_compare":
             paths = ("hash", "ranks") if args.sp == "both" else (args.sp,)
             print(json.dumps({"sp_paths": measure_sp_paths(gb, synth, 0, peaks(), paths)}))
+        elif args.only == "n13_steps":
+            # the headline system step by step in an untuned context (arena, reduction schedule,
+            # graphs and a step limit from the flags): the per-step statistics, for ncu captures of
+            # single stages on small arenas
+            ctx = gb.Context(device=0, arena_bytes=args.arena_gb << 30, reduce=args.reduce,
+                             graphs=not args.no_graphs)
+            rows = []
+            with gb.System(ctx, synth.sparse_n13(0)) as S:
+                while not args.max_steps or len(rows) < args.max_steps:
+                    st, stats = S.step()
+                    if st != gb.GB_OK:
+                        break
+                    rows.append({k: stats[k] for k in ("step", "nrows", "ndict", "nC", "nb", "rank", "nnz",
+                                                      "ms_sp", "ms_reduce", "ms_rref")})
+            print(json.dumps({"n13_steps": rows, "ms_rref": round(sum(r["ms_rref"] for r in rows), 3)}))
+            ctx.close()
         elif args.only == "headline":
             # one run of the headline workload as the timed steps run it (tuned context), for the
             # per-kernel launch list
