@@ -902,17 +902,19 @@ __global__ void __launch_bounds__(PT) k_panel_rref(const RrefJob *__restrict__ j
 
 // The same panel solve with the panel's columns spread over a cluster of PCS blocks: block q holds
 // the columns [q S, (q + 1) S) of all panel rows in its shared memory (S = ceil(nb / PCS)).  The
-// rows are taken in order (Gauss-Jordan): per row, every block finds its first non-zero column,
-// one cluster barrier makes these visible and every block takes their minimum c (the row is zero
-// when there is none); the block owning column c writes column c of every panel row and the
-// inverse of the pivot entry into every block's shared memory (distributed shared memory); after
-// a second barrier every block scales the row by the inverse and subtracts its multiple from
-// every other panel row on its own columns.  Per pivot that is two cluster barriers and one sweep
-// of a block's share of the panel, against one block's sweeps of whole rows in k_panel_rref.
-// Eliminating each pivot column from all other panel rows at once (instead of reducing a row by
-// the earlier pivots when its turn comes) gives the same pivots and the same reduced rows: a
-// row's reduction modulo the span of the earlier pivot rows, with zeros at their pivot columns,
-// is unique, and so is the reduced echelon form of the panel's pivot rows.
+// rows are taken in order (Gauss-Jordan).  Per row, every block finds its first non-zero column
+// c_q and publishes, in its own shared memory, c_q, column c_q of every panel row and the inverse
+// of the row's entry there; one cluster barrier; every block takes the least c_q (the row is zero
+// when there is none) and reads that block's column and inverse through distributed shared
+// memory; then every block scales the pivot row and subtracts its multiples from the other panel
+// rows on its own columns.  The published values are double-buffered by the row's parity: a block
+// overwrites them two rows later, after a barrier every block passes only once it has read them.
+// So a pivot costs one cluster barrier and one sweep of a block's share of the panel, against one
+// block's sweeps of whole rows in k_panel_rref.  Eliminating each pivot column from all other
+// panel rows at once (instead of reducing a row by the earlier pivots when its turn comes) gives
+// the same pivots and the same reduced rows: a row's reduction modulo the span of the earlier pivot
+// rows, with zeros at their pivot columns, is unique, and so is the reduced echelon form of the
+// panel's pivot rows.
 constexpr int PCS = 8;      // blocks per cluster
 constexpr int PCT = 1024;   // threads per block
 constexpr uint32_t PANEL_CLUSTER_MAX_NB = PCS * 3200;  // 4 KP S bytes of shared memory per block
@@ -921,9 +923,10 @@ __global__ void __cluster_dims__(PCS, 1, 1) __launch_bounds__(PCT)
     k_panel_rref_cl(const RrefJob *__restrict__ jobs, const int *__restrict__ list) {
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) uint32_t slab[];  // KP rows of S columns
-    __shared__ uint32_t s_min[2];       // this block's first non-zero column of the row, by parity
-    __shared__ uint32_t s_col[KP + 1];  // column c of the panel rows, then the pivot's inverse
-    __shared__ uint32_t red[32], s_row[KP], s_c;
+    __shared__ uint32_t s_min[2];           // this block's first non-zero column of the row, by parity
+    __shared__ uint32_t s_pub[2][KP + 1];   // that column of every panel row, then the inverse, by parity
+    __shared__ uint32_t s_col[KP + 1];      // the pivot block's published values, read for the update
+    __shared__ uint32_t red[32], s_row[KP], s_c, s_owner;
     cg::cluster_group cl = cg::this_cluster();
     const uint32_t q = cl.block_rank();
     const RrefJob &X = jobs[list[blockIdx.x / PCS]];
@@ -952,35 +955,44 @@ __global__ void __cluster_dims__(PCS, 1, 1) __launch_bounds__(PCT)
             if (row[j]) { c = c0 + j; break; }
         c = block_min(c, red);
         if (threadIdx.x == 0) s_min[par] = c;
+        if (c != NOLEAD && threadIdx.x <= KP) {  // this block's candidate pivot column and inverse
+            const uint32_t u = threadIdx.x, jc = c - c0;
+            uint32_t v;
+            if (u < KP) v = u < P && u != t ? slab[(size_t)u * S + jc] : 0u;
+            else v = fp.small ? fp_inv_small(row[jc], fp) : fp_inv(row[jc], fp);
+            s_pub[par][u] = v;
+        }
         cl.sync();
         if (threadIdx.x < 32) {
-            uint32_t m = threadIdx.x < PCS ? *cl.map_shared_rank(&s_min[par], threadIdx.x) : NOLEAD;
-            for (int d = 16; d; d >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, d));
-            if (threadIdx.x == 0) s_c = m;
+            const uint32_t m = threadIdx.x < PCS ? *cl.map_shared_rank(&s_min[par], threadIdx.x) : NOLEAD;
+            uint32_t best = m, who = threadIdx.x;
+            for (int d = 16; d; d >>= 1) {  // the least column (block column ranges are disjoint)
+                const uint32_t bo = __shfl_xor_sync(0xffffffffu, best, d), wo = __shfl_xor_sync(0xffffffffu, who, d);
+                if (bo < best) { best = bo; who = wo; }
+            }
+            if (threadIdx.x == 0) {
+                s_c = best;
+                s_owner = who;
+            }
         }
         __syncthreads();
         c = s_c;
-        if (c == NOLEAD) {  // the row reduced to zero (s_min is double-buffered: no second barrier)
+        if (c == NOLEAD) {  // the row reduced to zero
             if (q == 0 && threadIdx.x == 0) X.lead[s_row[t]] = NOLEAD;
             continue;
         }
-        if (c - c0 < w && threadIdx.x <= KP) {  // this block owns column c: publish it
-            const uint32_t u = threadIdx.x;
-            uint32_t v = 0;
-            if (u < KP) v = u < P && u != t ? slab[(size_t)u * S + (c - c0)] : 0u;
-            else v = fp.small ? fp_inv_small(row[c - c0], fp) : fp_inv(row[c - c0], fp);
-#pragma unroll
-            for (int r = 0; r < PCS; ++r) *cl.map_shared_rank(&s_col[u], r) = v;
-        }
-        cl.sync();
+        if (threadIdx.x <= KP) s_col[threadIdx.x] = *cl.map_shared_rank(&s_pub[par][threadIdx.x], s_owner);
+        __syncthreads();
         const uint32_t inv = s_col[KP];
         for (uint32_t j = (c > c0 ? c - c0 : 0) + threadIdx.x; j < w; j += PCT) {
-            const uint32_t y = fp_mul(row[j], inv, fp);
+            const uint32_t y = fp.small ? fp_reduce32(row[j] * inv, fp) : fp_mul(row[j], inv, fp);
             row[j] = y;
             if (!y) continue;
             for (uint32_t u = 0; u < P; ++u) {
                 const uint32_t m = s_col[u];
-                if (m) slab[(size_t)u * S + j] = fp_sub(slab[(size_t)u * S + j], fp_mul(m, y, fp), fp);
+                if (!m) continue;
+                uint32_t *x = slab + (size_t)u * S + j;
+                *x = fp_sub(*x, fp.small ? fp_reduce32(m * y, fp) : fp_mul(m, y, fp), fp);
             }
         }
         if (q == 0 && threadIdx.x == 0) {
@@ -1780,6 +1792,7 @@ std::vector<std::unique_ptr<gb_echelon>> reduce_rows(const std::vector<gb_macaul
             D.col = J.col;
             D.val = J.val;
             D.colpos = J.colpos;
+            D.pcols = J.pcols;
             D.Uinv = J.U;
             D.N = J.N;
             D.nA = J.nA;
