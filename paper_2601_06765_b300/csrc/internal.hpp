@@ -476,6 +476,7 @@ void matmul_dev(Arena &ar, const Fp &fp, uint32_t m, uint32_t n, uint32_t k, con
 // ---- dense blocked reduction of the non-pivot rows (dense.cu) --------------------------------
 struct DenseJob {
     const uint32_t *row_ptr, *col, *val, *colpos;  // CSR (pivot rows first) and column map
+    const uint32_t *pcols;                         // dictionary column of each pivot, ascending
     const uint32_t *Uinv;                          // 32 x 32 chunk-triangle inverses
     uint32_t N, nA, nC, nb;
     Fp fp;
