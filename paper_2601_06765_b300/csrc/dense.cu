@@ -31,33 +31,116 @@ __device__ __forceinline__ uint32_t qcol(uint32_t cp, uint32_t nAp) {
     return (cp & 0x80000000u) ? (cp & 0x7FFFFFFFu) : nAp + cp;
 }
 
-// balanced base-256 digits of a residue x as BF16 bits, digit l at dst[l * plane]
+// balanced base-256 digits of a residue x as BF16 bits, digit l in d[l]
 template <int L>
-__device__ __forceinline__ void put_digits(uint32_t x, uint32_t p, uint16_t *dst, uint64_t plane) {
+__device__ __forceinline__ void digits_bf16(uint32_t x, uint32_t p, uint16_t (&d)[L]) {
     const uint32_t T = L == 2 ? 32639u : 2139062143u;  // 127 (1 + 256 + ... + 256^{L-1})
     int v = x <= T ? (int)x : (int)(x - p);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         const int a = l + 1 < L ? (int)(((uint32_t)v & 0xFFu) ^ 0x80u) - 0x80 : v;
         if (l + 1 < L) v = (v - a) >> 8;
-        dst[(size_t)l * plane] = (uint16_t)(__float_as_uint((float)a) >> 16);
+        d[l] = (uint16_t)(__float_as_uint((float)a) >> 16);
     }
 }
 
-// pivot row i: entries right of its block go to the digit planes of W^T (row q, K index i), the
-// entries inside its own block (right of the diagonal) to the dense block Ub
+// balanced base-256 digits of a residue x as BF16 bits, digit l at dst[l * plane]
 template <int L>
-__global__ void k_scatter_pivots(DenseJob J) {
+__device__ __forceinline__ void put_digits(uint32_t x, uint32_t p, uint16_t *dst, uint64_t plane) {
+    uint16_t d[L];
+    digits_bf16<L>(x, p, d);
+#pragma unroll
+    for (int l = 0; l < L; ++l) dst[(size_t)l * plane] = d[l];
+}
+
+// pivot row i: the entries inside its own block, right of the diagonal, go to the dense block Ub.
+// They are pivot columns q in (i, j1), i.e. dictionary columns up to pcols[j1 - 1]: a prefix of
+// the row (its columns ascend), so the warp stops at the first column past it.
+__global__ void k_scatter_ub(DenseJob J) {
     const uint32_t i = blockIdx.x * DW + (threadIdx.x >> 5);
     if (i >= J.nA) return;
     const int lane = threadIdx.x & 31;
-    const uint32_t j0 = i / J.bs * J.bs, j1 = min(j0 + J.bs, J.nAp);
-    const uint64_t plane = (uint64_t)J.Np * J.wkpad;
+    const uint32_t j0 = i / J.bs * J.bs, j1 = min(j0 + J.bs, J.nA);
+    if (i + 1 >= j1) return;  // the block's last pivot: nothing right of the diagonal inside it
+    const uint32_t last = J.pcols[j1 - 1];
     uint32_t *ub = J.Ub + (size_t)(i / J.bs) * J.bs * J.bs + (size_t)(i - j0) * J.bs;
-    for (uint32_t e = J.row_ptr[i] + lane; e < J.row_ptr[i + 1]; e += 32) {
-        const uint32_t q = qcol(J.colpos[J.col[e]], J.nAp), v = J.val[e];
-        if (q >= j1) put_digits<L>(v, J.fp.p, J.WT + (size_t)q * J.wkpad + i, plane);
-        else if (q > i) ub[q - j0] = v;
+    for (uint32_t e0 = J.row_ptr[i]; e0 < J.row_ptr[i + 1]; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        const bool in = e < J.row_ptr[i + 1] && J.col[e] <= last;
+        if (in) {
+            const uint32_t q = qcol(J.colpos[J.col[e]], J.nAp);
+            if (q > i && q < j1) ub[q - j0] = J.val[e];
+        }
+        if (__ballot_sync(0xffffffffu, in) != 0xffffffffu) break;  // past the prefix
+    }
+}
+
+// W^T as digit planes, every entry written once, zeros included (no memset of the planes, no
+// scattered 2-byte writes): block (b, s) takes the 64 pivot rows [64 b, 64 b + 64) and the
+// dictionary columns [s FS, (s + 1) FS), finds each row's first entry there by binary search and
+// walks the segment in windows of FW, each row's CSR cursor advancing with the windows (a row's
+// columns ascend).  A window's entries gather in a shared tile; then, per column c of the window
+// and digit plane l, the 64 K entries of row q(c) of W^T go out as one 128-byte store of a warp.
+// Entries left of a pivot's own block end (q < j1) are written as well: the tensor-core update of
+// that block starts at column j1 and never reads them.  Rows q in [nA, nAp) (the padding columns)
+// come from no dictionary column; the caller zeroes them.
+constexpr int FW = 128;      // dictionary columns per window
+constexpr int FS = 16 * FW;  // dictionary columns per block
+constexpr int FT = 256;      // threads per block (8 warps)
+template <int L>
+__global__ void __launch_bounds__(FT) k_fill_wt(DenseJob J) {
+    __shared__ uint32_t tile[FW][65];
+    __shared__ uint32_t cur[64], fin[64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t i0 = blockIdx.x * 64, cs = blockIdx.y * FS, ce = min(cs + FS, J.N);
+    if (threadIdx.x < 64) {
+        const uint32_t i = i0 + threadIdx.x;
+        uint32_t lo = 0, hi = 0;
+        if (i < J.nA) {
+            lo = J.row_ptr[i];
+            hi = J.row_ptr[i + 1];
+            fin[threadIdx.x] = hi;
+            while (lo < hi) {  // the row's first entry at a column >= cs
+                const uint32_t mid = (lo + hi) >> 1;
+                if (J.col[mid] < cs) lo = mid + 1; else hi = mid;
+            }
+        } else {
+            fin[threadIdx.x] = 0u;
+        }
+        cur[threadIdx.x] = lo;
+    }
+    const uint64_t plane = (uint64_t)J.Np * J.wkpad;
+    for (uint32_t c0 = cs; c0 < ce; c0 += FW) {
+        for (uint32_t k = threadIdx.x; k < FW * 64; k += FT) tile[k >> 6][k & 63] = 0u;
+        __syncthreads();
+        const uint32_t cend = min(c0 + FW, ce);
+        for (uint32_t r = warp; r < 64; r += FT / 32) {
+            uint32_t a = cur[r];
+            const uint32_t e = fin[r];
+            for (;;) {
+                const uint32_t idx = a + lane;
+                const uint32_t c = idx < e ? J.col[idx] : 0xFFFFFFFFu;
+                const bool in = c < cend;
+                if (in) tile[c - c0][r] = J.val[idx];
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                a += __popc(m);
+                if (m != 0xffffffffu) break;
+            }
+            if (lane == 0) cur[r] = a;
+        }
+        __syncthreads();
+        for (uint32_t cc = warp; cc < FW; cc += FT / 32) {
+            const uint32_t c = c0 + cc;
+            if (c >= ce) break;
+            const uint32_t q = qcol(J.colpos[c], J.nAp);
+            uint16_t d0[L], d1[L];
+            digits_bf16<L>(tile[cc][2 * lane], J.fp.p, d0);
+            digits_bf16<L>(tile[cc][2 * lane + 1], J.fp.p, d1);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(J.WT + (size_t)q * J.wkpad + i0) + lane;
+#pragma unroll
+            for (int l = 0; l < L; ++l) dst[(size_t)l * (plane / 2)] = (uint32_t)d0[l] | ((uint32_t)d1[l] << 16);
+        }
+        __syncthreads();
     }
 }
 
@@ -177,7 +260,11 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
     F.alloc(ar, L, J.nC, J.bs, st);
     GB_CUDA(cudaMemsetAsync(M.p, 0, M.bytes(), st));
     GB_CUDA(cudaMemsetAsync(Ub.p, 0, Ub.bytes(), st));
-    GB_CUDA(cudaMemsetAsync(WT.p, 0, WT.buf.bytes(), st));
+    // rows [nA, nAp) of W^T (the padding columns) come from no dictionary column: zero them; the
+    // rest of the planes is written in full by k_fill_wt
+    for (uint32_t l = 0; l < L && J.nAp > J.nA; ++l)
+        GB_CUDA(cudaMemsetAsync(WT.p + (size_t)l * J.Np * WT.kpad + (size_t)J.nA * WT.kpad, 0,
+                                2ull * (J.nAp - J.nA) * WT.kpad, st));
     GB_CUDA(cudaMemsetAsync(F.p, 0, F.buf.bytes(), st));  // digits past a short last block stay finite
     J.M = M.p;
     J.Ub = Ub.p;
@@ -185,10 +272,12 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
     J.wkpad = WT.kpad;
     J.F = F.p;
     J.fkpad = F.kpad;
-    if (L == 2) k_scatter_pivots<2><<<blocks_of(J.nA, DW), DW * 32, 0, st>>>(J);
-    else k_scatter_pivots<4><<<blocks_of(J.nA, DW), DW * 32, 0, st>>>(J);
+    const dim3 wt_grid(J.nAp / 64, (J.N + FS - 1) / FS);
+    if (L == 2) k_fill_wt<2><<<wt_grid, FT, 0, st>>>(J);
+    else k_fill_wt<4><<<wt_grid, FT, 0, st>>>(J);
+    k_scatter_ub<<<blocks_of(J.nA, DW), DW * 32, 0, st>>>(J);
     k_scatter_rows<<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J);
-    counted(2);
+    counted(3);
     unsigned long long macs = 0;
     const MmPlan plan(F, WT, J.M, J.ldm, J.nC, J.Np, J.fp);
     for (uint32_t b = 0; b < nblk; ++b) {
