@@ -237,6 +237,7 @@ def run_ours(args) -> None:
     deglex = guarded(measure_deglex, gb, synth, ctx) if extra else None
     wied = guarded(measure_wiedemann, gb, synth, local, pk) if extra else None
     f5 = guarded(measure_f5, gb, synth, local) if extra else None
+    micro = guarded(measure_microbench, gb, synth, local) if extra else None
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
              for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_mm", "ms_rref", "ms_update", "ms_pairs",
                        "ms_select", "ms_finish", "ms_wall")}
@@ -271,6 +272,7 @@ def run_ours(args) -> None:
             "deglex": deglex,
             "block_wiedemann": wied,
             "f5_signatures": f5,
+            "microbench": micro,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -321,6 +323,10 @@ def measure_dense_n10(gb, synth, ctx, flush, pk: dict, args) -> dict:
         with open(path) as f:
             sm_mhz = float(json.load(f).get("sm_max_mhz", sm_mhz))
     issue_peak = 148 * 4 * sm_mhz * 1e6 * 32.0 / ipf if ipf else None
+    # the integer multiply-add pipe: 64 lanes per SM per clock (half the FP32 rate) at the IMADs
+    # per modular multiply-add ncu counted (the fmaheavy pipe of the same capture)
+    imad = profile_value("k_reduce_rows_dense_n10", "imad_per_32_fma")
+    imad_peak = 148 * 64 * sm_mhz * 1e6 * 32.0 / imad if imad else None
     fma_rate = fma / (red_ms / 1e3) if red_ms > 0 else None
     stage = {k: round(sum(r[k] for r in runs) / len(runs), 3)
              for k in ("ms_sp", "ms_reduce", "ms_reduce_kernel", "ms_rref", "ms_update", "ms_pairs", "ms_select",
@@ -340,6 +346,13 @@ def measure_dense_n10(gb, synth, ctx, flush, pk: dict, args) -> dict:
                     "peak": issue_peak, "frac": round(fma_rate / issue_peak, 4),
                     "peak_source": f"148 SMs x 4 schedulers x {sm_mhz:.0f} MHz, {ipf} warp instructions "
                                    "per 32 multiply-adds (ncu, profiles/k_reduce_rows_dense_n10.md)"},
+                "integer_pipe_roofline": None if not imad_peak else {
+                    "bound": "alu", "unit": "modular multiply-adds/s", "achieved": fma_rate,
+                    "peak": imad_peak, "frac": round(fma_rate / imad_peak, 4),
+                    "peak_source": f"148 SMs x 64 integer multiply-add lanes x {sm_mhz:.0f} MHz, {imad} IMAD "
+                                   "instructions per 32 multiply-adds (the 32-bit products of p < 2^16 summed "
+                                   "lazily; ncu fmaheavy pipe, profiles/k_reduce_rows_dense_n10.md); the issue "
+                                   "rate, not this pipe, binds"},
                 "bound": "issue / L2 latency (operands L2-resident; profiles/k_reduce_rows_dense_n10.md)",
                 "traffic": profile_traffic("k_reduce_rows_dense_n10")}}
 
@@ -666,6 +679,101 @@ def measure_f5(gb, synth, local: int, nvars: int = 7) -> dict:
     return out
 
 
+def _shift_rows(synth, n: int, deg: int, count: int, npolys: int, seed: int):
+    """count distinct monomials of degree deg drawn without replacement (all of them when count is
+    0 or too large), each paired with every polynomial index: the rows (t, k) of a key stream."""
+    mons = [e for e in synth.monomials_upto(n, deg) if sum(e) == deg]
+    if count and count < len(mons):
+        rng = synth.SplitMix64(seed)
+        idx = list(range(len(mons)))
+        for i in range(count):
+            j = i + rng.below(len(mons) - i)
+            idx[i], idx[j] = idx[j], idx[i]
+        mons = [mons[i] for i in sorted(idx[:count])]
+    t = np.array([m for m in mons for _ in range(npolys)], dtype=np.uint8).reshape(-1, n)
+    k = np.array([kk for _ in mons for kk in range(npolys)], dtype=np.uint32)
+    return t, k
+
+
+def measure_microbench(gb, synth, local: int, arena_gb: int = 16) -> dict:
+    """The microbenchmarks of Sec. 12.2 on this library's kernels.
+    - Dictionary build and row-assembly join: gb_symbolic_preprocess without closure on synthetic
+      key streams: 8 polynomials of 64 to 4096 terms (the row-length buckets), each shifted by a
+      set of monomials; the duplicate rate (1 - N / M) follows from how much the shifted supports
+      overlap, the key width from the number of variables (keys are 16-byte monomials).  DictBuild
+      (expansion, dense ranks into a bitmap, the popcount scan, the dictionary emitted: one pass
+      over the keys and none of radix sorting) in keys/s and bytes/s; RowAssemble (pivot split and
+      the fill of col_ind / val) in joins/s, one join per nonzero; the peak arena use of the call.
+    - The modular inner loop: chains of 512 multiply-adds per element kept in registers
+      (gb_modp_apply), Barrett against Montgomery, at p = 65521 and 2^31 - 1: updates/s."""
+    import torch
+    ctx = gb.Context(device=local, arena_bytes=arena_gb << 30)
+    out = {"dictionary_and_join": []}
+    configs = [  # (variables, input degree, shift degree, shifts drawn (0: all), note)
+        (8, 6, 6, 0, "every shift of degree 6"),
+        (10, 4, 8, 8000, "8000 random shifts of degree 8"),
+        (14, 3, 9, 4000, "4000 random shifts of degree 9"),
+    ]
+    for ci, (n, dg, de, cnt, note) in enumerate(configs):
+        lens = [64, 64, 256, 256, 1024, 1024, 4096, 4096]
+        avail = len(synth.monomials_upto(n, dg))
+        polys = []
+        rng = synth.SplitMix64(synth.BASE_SEED + 950 + ci)
+        mons = synth.monomials_upto(n, dg)
+        for L in lens:
+            L = min(L, avail)
+            idx = list(range(len(mons)))
+            for i in range(L):
+                j = i + rng.below(len(mons) - i)
+                idx[i], idx[j] = idx[j], idx[i]
+            polys.append([(mons[i], rng.between(1, synth.P31 - 1)) for i in idx[:L]])
+        system = synth._pack(n, synth.P31, polys)
+        t, k = _shift_rows(synth, n, de, cnt, len(polys), synth.BASE_SEED + 990 + ci)
+        best = None
+        with gb.System(ctx, system) as S:
+            for rep in range(3):
+                base = ctx.memory()[0]
+                ctx.memory_peak(reset=True)
+                mac = gb.gb_symbolic_preprocess(S.h, n, t, k, False)
+                st = gb.gb_macaulay_stats_get(mac)
+                peak = ctx.memory_peak() - base
+                gb.gb_macaulay_destroy(mac)
+                if rep and (best is None or st["ms_sp"] < best[0]["ms_sp"]):
+                    best = (st, peak)
+        st, peak = best
+        M, N = st["nnz"], st["ndict"]
+        out["dictionary_and_join"].append({
+            "stream": f"n={n} variables, 8 polynomials of {min(64, avail)}..{min(4096, avail)} terms of degree <= {dg}; {note}",
+            "rows": int(len(k)), "keys_M": int(M), "dictionary_N": int(N), "duplicate_rate": round(1 - N / M, 4),
+            "dict_ms": round(st["ms_dict"], 3), "keys_per_s": M / (st["ms_dict"] / 1e3),
+            "key_bytes_per_s": 16.0 * M / (st["ms_dict"] / 1e3), "radix_passes": 0,
+            "passes": "one over the keys (expand + mark the dense grevlex rank), one over the rank bitmap (popcount), a scan, the emit",
+            "assemble_ms": round(st["ms_assemble"], 3), "joins_per_s": M / (st["ms_assemble"] / 1e3),
+            "peak_arena_bytes": int(peak)})
+    chains = []
+    n_el, steps = 148 * 16 * 256 * 4, 512
+    rng = np.random.default_rng(20260765)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for p in (synth.P16, synth.P31):
+        A, B, C = (torch.from_numpy(rng.integers(0, p, n_el, dtype=np.int64).astype(np.int32)).cuda() for _ in range(3))
+        O = torch.empty(n_el, dtype=torch.int32, device="cuda")
+        for name, op in (("barrett", gb.GB_MODP_CHAIN_BARRETT), ("montgomery", gb.GB_MODP_CHAIN_MONT)):
+            s = torch.cuda.current_stream().cuda_stream
+            gb.gb_modp_apply(op, p, n_el, steps, A.data_ptr(), B.data_ptr(), C.data_ptr(), O.data_ptr(), s)
+            ms = []
+            for _ in range(5):
+                e0.record()
+                gb.gb_modp_apply(op, p, n_el, steps, A.data_ptr(), B.data_ptr(), C.data_ptr(), O.data_ptr(), s)
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            chains.append({"p": p, "form": name, "updates": n_el * steps, "ms": round(min(ms), 3),
+                           "updates_per_s": n_el * steps / (min(ms) / 1e3)})
+    out["modular_inner_loop"] = chains
+    ctx.close()
+    return out
+
+
 def measure_sp_paths(gb, synth, local: int, pk: dict, paths=("hash", "ranks")) -> dict:
     """The n=13 run step by step with each symbolic-preprocessing path (the hash dictionary and
     the rank bitmap): per-step device time of the stage and its share of HBM bandwidth on the
@@ -792,7 +900,8 @@ def main() -> None:
     ap.add_argument("--max-steps", type=int, default=0, help="--only n13_steps: stop after this many F4 steps")
     ap.add_argument("--reduce", choices=["auto", "sparse", "dense"], default="auto",
                     help="--only n13_steps: the reduction schedule of the context")
-    ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10", "wiedemann", "f5", "sp_compare", "served",
+    ap.add_argument("--only", choices=["tensor", "sparse_n13", "dense_n10", "wiedemann", "f5", "microbench",
+                                       "sp_compare", "served",
                                        "n13_steps",
                                        "headline"],
                     default=None,
@@ -844,6 +953,8 @@ def main() -> None:
             ctx.close()
         elif args.only == "wiedemann":
             print(json.dumps({"block_wiedemann": measure_wiedemann(gb, synth, 0, peaks())}))
+        elif args.only == "microbench":
+            print(json.dumps({"microbench": measure_microbench(gb, synth, 0, min(args.arena_gb, 16))}))
         elif args.only == "f5":
             print(json.dumps({"f5_signatures": [measure_f5(gb, synth, 0, nv) for nv in (7, 8)]}))
         elif args.only == "dense_n10":

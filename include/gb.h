@@ -209,6 +209,21 @@ gb_status gb_symbolic_preprocess(gb_system *sys, uint32_t r, const uint8_t *t_ex
 gb_status gb_macaulay_export(const gb_macaulay *mac, gb_macaulay_host *inout);
 gb_status gb_macaulay_destroy(gb_macaulay *mac);
 
+/* Sizes and stage times of one materialised plan (the per-run record of Sec. 12: N, M, nnz(A),
+   and the DictBuild / RowAssemble split of the kernel decomposition of Sec. 12).  Every nonzero is
+   one expanded term t m (t m is injective within a row), so the key volume M equals nnz.  The
+   times are device times of the symbolic-preprocessing call that built the matrix (for a batch,
+   the batch's). */
+typedef struct {
+    uint32_t nrows, ndict, npivot, closure_rounds;
+    uint64_t nnz;          /* = M, the expanded terms */
+    float ms_sp;           /* the whole stage */
+    float ms_dict;         /* DictBuild: expansion, closure rounds, dense ranks, the dictionary emitted */
+    float ms_assemble;     /* RowAssemble: pivot split, row lengths, the fill of col_ind / val */
+    uint32_t reserved;
+} gb_macaulay_stats;
+gb_status gb_macaulay_stats_get(const gb_macaulay *mac, gb_macaulay_stats *out);
+
 /* Structured elimination of Pi (Sec. 9.2): each non-pivot row is reduced by the pivot rows
    (pivot columns in ascending order) to D', zero on every pivot column, then D' is brought to its
    reduced row echelon form.  Both are unique. */
@@ -466,11 +481,17 @@ typedef enum {
                               terms a[i*window + j] b[i*window + j], summed in 32 bits without
                               reduction between terms (the lazy window of Rem. 8.1), p < 2^16,
                               window < 2^16, c[i] < p */
-    GB_MODP_LAZY_MONT = 9  /* the same with 64-bit sums of GB_MODP_MONT_MUL terms (each below 2p) */
+    GB_MODP_LAZY_MONT = 9, /* the same with 64-bit sums of GB_MODP_MONT_MUL terms (each below 2p) */
+    GB_MODP_CHAIN_BARRETT = 10, /* x <- (x b[i] + c[i]) mod p, `window` times from x = a[i], in registers:
+                                   the modular multiply-add through the 64-bit Barrett step; out = x
+                                   (the modular inner loop of the microbenchmarks of Sec. 12.2) */
+    GB_MODP_CHAIN_MONT = 11     /* the same chain with the product in Montgomery form (b[i] converted
+                                   once, redc per step, Sec. 8.4); out = x, the same residue */
 } gb_modp_op;
 
 /* Device pointers on the current device: a, b, c [n] (b and c only where the operation reads
-   them; for the two window operations a and b hold n * window values), out [n].  stream: a
+   them; for the two window operations a and b hold n * window values; the chains read a, b and c
+   [n] and run `window` >= 1 steps), out [n].  stream: a
    cudaStream_t (NULL: the legacy default stream); the call only enqueues the work.
    GB_EINVAL: p not an odd prime below 2^31, an unknown operation, a 16-bit-only operation with a
    larger p, a window out of range, a null pointer the operation needs. */

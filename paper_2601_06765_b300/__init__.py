@@ -33,7 +33,8 @@ GB_F5_NO_CRITERION = 1
 GB_GREVLEX, GB_DEGLEX = 0, 1  # gb_order
 # gb_modp_op
 (GB_MODP_REDUCE64, GB_MODP_REDUCE32, GB_MODP_MULADD, GB_MODP_REDC, GB_MODP_TO_MONT, GB_MODP_MONT_MUL,
- GB_MODP_INV, GB_MODP_INV_SMALL, GB_MODP_LAZY32, GB_MODP_LAZY_MONT) = range(10)
+ GB_MODP_INV, GB_MODP_INV_SMALL, GB_MODP_LAZY32, GB_MODP_LAZY_MONT, GB_MODP_CHAIN_BARRETT,
+ GB_MODP_CHAIN_MONT) = range(12)
 _ORDERS = {"grevlex": GB_GREVLEX, "deglex": GB_DEGLEX}
 
 _u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -97,6 +98,12 @@ class gb_krylov_stats(ctypes.Structure):
                 ("ms_hankel", ctypes.c_double), ("ms_vectors", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
 
+class gb_macaulay_stats(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_uint32), ("ndict", ctypes.c_uint32), ("npivot", ctypes.c_uint32),
+                ("closure_rounds", ctypes.c_uint32), ("nnz", ctypes.c_uint64), ("ms_sp", ctypes.c_float),
+                ("ms_dict", ctypes.c_float), ("ms_assemble", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+
+
 class gb_f5_block(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_uint32), ("index", ctypes.c_uint32), ("candidates", ctypes.c_uint32),
                 ("admissible", ctypes.c_uint32), ("rows", ctypes.c_uint32), ("ndict", ctypes.c_uint32),
@@ -153,6 +160,7 @@ _SIGS = {
     "gb_symbolic_preprocess": [_vp, ctypes.c_uint32, _u8p, _u32p, ctypes.c_int, ctypes.POINTER(_vp)],
     "gb_macaulay_export": [_vp, ctypes.POINTER(gb_macaulay_host)],
     "gb_macaulay_destroy": [_vp],
+    "gb_macaulay_stats_get": [_vp, ctypes.POINTER(gb_macaulay_stats)],
     "gb_reduce_macaulay": [_vp, ctypes.POINTER(_vp)],
     "gb_echelon_export": [_vp, ctypes.POINTER(gb_echelon_host)],
     "gb_echelon_destroy": [_vp],
@@ -462,6 +470,13 @@ def gb_block_wiedemann(mac: int, b: int, X: np.ndarray, Z: np.ndarray, delta: np
     out["seq"] = seq
     out["W"] = W[:min(out["found"], wcap)]
     return out
+
+
+def gb_macaulay_stats_get(mac: int) -> dict:
+    """Sizes and DictBuild / RowAssemble device times of a matrix handle.  See include/gb.h."""
+    st = gb_macaulay_stats()
+    check(lib().gb_macaulay_stats_get(mac, ctypes.byref(st)), "gb_macaulay_stats_get")
+    return _struct_dict(st)
 
 
 def gb_sig_filter(ctx: int, index: int, e: int, ncand: int, forbidden: int | None, keys: int) -> int:

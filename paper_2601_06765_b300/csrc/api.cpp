@@ -362,6 +362,22 @@ static void d2h(gb_system *S, void *dst, const void *src, size_t bytes) {
     if (bytes) GB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, S->stream));
 }
 
+gb_status gb_macaulay_stats_get(const gb_macaulay *M, gb_macaulay_stats *out) {
+    GB_API_BEGIN
+    if (!M || !out) fail(GB_EINVAL, "null argument");
+    *out = gb_macaulay_stats{};
+    out->nrows = M->nrows;
+    out->ndict = M->ndict;
+    out->npivot = M->nA;
+    out->closure_rounds = M->closure_rounds;
+    out->nnz = M->nnz;
+    out->ms_sp = M->ms_sp;
+    out->ms_dict = M->ms_dict;
+    out->ms_assemble = M->ms_sp - M->ms_dict;
+    return GB_OK;
+    GB_API_END
+}
+
 gb_status gb_macaulay_export(const gb_macaulay *M, gb_macaulay_host *h) {
     GB_API_BEGIN
     if (!M || !h) fail(GB_EINVAL, "null argument");

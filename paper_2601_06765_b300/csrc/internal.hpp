@@ -287,6 +287,7 @@ struct gb_macaulay {
     gb::DBuf<uint32_t> colpos;             // ndict: pivot index | 0x80000000 for a pivot column,
                                            // else the position among the non-pivot columns
     float ms_sp = 0.f;
+    float ms_dict = 0.f;  // of ms_sp: up to the finished dictionary (expansion, closure, ranks, emit)
 };
 
 // D' and RREF(D') on the device.

@@ -1,7 +1,9 @@
 // modp.cu -- gb_modp_apply: the register-level F_p primitives of device.cuh applied elementwise to
 // device arrays, so that each one can be checked on its own against plain integer arithmetic:
 // Barrett reduction (Sec. 8.3), Montgomery reduction and domain conversion (Sec. 8.4), the two
-// inverses, and the lazy accumulation windows of the sparse reduction (Rem. 8.1).  The kernels
+// inverses, the lazy accumulation windows of the sparse reduction (Rem. 8.1), and chains of
+// multiply-adds kept in registers (Barrett against Montgomery: the modular inner loop timed by the
+// microbenchmarks of Sec. 12.2).  The kernels
 // call exactly the functions the reduction kernels call, with the Fp constants of make_fp.
 #include "internal.hpp"
 
@@ -43,6 +45,24 @@ __global__ void k_modp_apply(int op, Fp fp, uint64_t n, uint32_t window, const u
             r = fp_reduce(acc, fp);
             break;
         }
+        case GB_MODP_CHAIN_BARRETT: {
+            uint32_t x = a[i];
+            const uint32_t m = b[i], d = c[i];
+            for (uint32_t j = 0; j < window; ++j) x = fp_reduce((uint64_t)x * m + d, fp);
+            r = x;
+            break;
+        }
+        case GB_MODP_CHAIN_MONT: {
+            uint32_t x = a[i];
+            const uint32_t m = fp_to_mont(b[i], fp), d = c[i];
+            for (uint32_t j = 0; j < window; ++j) {
+                uint32_t y = fp_redc((uint64_t)x * m, fp);  // x b mod p, in [0, 2p)
+                y = y >= fp.p ? y - fp.p : y;
+                x = fp_add(y, d, fp);
+            }
+            r = x;
+            break;
+        }
         default: break;
         }
         out[i] = r;
@@ -54,16 +74,17 @@ __global__ void k_modp_apply(int op, Fp fp, uint64_t n, uint32_t window, const u
 void modp_apply(int op, uint32_t p, uint64_t n, uint32_t window, const uint32_t *a, const uint32_t *b,
                 const uint32_t *c, uint32_t *out, cudaStream_t st) {
     if (p < 3 || p >= (1u << 31) || !is_prime32(p)) fail(GB_EINVAL, "p must be an odd prime below 2^31");
-    if (op < GB_MODP_REDUCE64 || op > GB_MODP_LAZY_MONT) fail(GB_EINVAL, "gb_modp_apply: unknown operation");
+    if (op < GB_MODP_REDUCE64 || op > GB_MODP_CHAIN_MONT) fail(GB_EINVAL, "gb_modp_apply: unknown operation");
     const bool small_only = op == GB_MODP_REDUCE32 || op == GB_MODP_INV_SMALL || op == GB_MODP_LAZY32;
     if (small_only && p >= 65536u) fail(GB_EINVAL, "gb_modp_apply: this operation needs p < 2^16");
     const bool windowed = op == GB_MODP_LAZY32 || op == GB_MODP_LAZY_MONT;
-    if (windowed && (window == 0 || (op == GB_MODP_LAZY32 && window >= 65536u)))
+    const bool chain = op == GB_MODP_CHAIN_BARRETT || op == GB_MODP_CHAIN_MONT;
+    if ((windowed || chain) && (window == 0 || (op == GB_MODP_LAZY32 && window >= 65536u)))
         fail(GB_EINVAL, "gb_modp_apply: window must be in [1, 2^16) for the 32-bit sum, >= 1 otherwise");
     if (!n) return;
     const bool needs_b = op == GB_MODP_REDUCE64 || op == GB_MODP_MULADD || op == GB_MODP_REDC ||
-                         op == GB_MODP_MONT_MUL || windowed;
-    const bool needs_c = op == GB_MODP_MULADD || windowed;
+                         op == GB_MODP_MONT_MUL || windowed || chain;
+    const bool needs_c = op == GB_MODP_MULADD || windowed || chain;
     if (!a || !out || (needs_b && !b) || (needs_c && !c)) fail(GB_EINVAL, "gb_modp_apply: null device pointer");
     const unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, 148ull * 16);
     k_modp_apply<<<grid, 256, 0, st>>>(op, make_fp(p), n, window, a, b, c, out);

@@ -942,6 +942,7 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         exclusive_scan(ctx, wcnt.p, wpre.p, tw, st);
         if (t_q) { k_dict_queue<<<t_q, 256, 0, st>>>(dj, P(o_q), nj); counted(); }
         if (t_g) { k_dict_given<<<t_g, 256, 0, st>>>(dj, P(o_g), nj); counted(); }
+        GB_CUDA(cudaEventRecord(ctx->ev[6], st));  // the dictionary is complete (DictBuild)
         if (t_r) { k_piv_reducers<<<t_r, 256, 0, st>>>(dj, P(o_r), nj); counted(); }
         exclusive_scan(ctx, ispiv.p, pidx.p, tN, st);
         if (t_N) { k_place_pivots<<<t_N, 256, 0, st>>>(dj, P(o_N), nj); counted(); }
@@ -963,8 +964,9 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
         uint32_t *hchk = static_cast<uint32_t *>(ctx_pinned(ctx, 16ull * nj + 16));
         GB_CUDA(cudaMemcpyAsync(hchk, chk.p, 16ull * nj, cudaMemcpyDeviceToHost, st));
         ctx_sync(ctx);
-        float ms = 0.f;
+        float ms = 0.f, ms_dict = 0.f;
         GB_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        GB_CUDA(cudaEventElapsedTime(&ms_dict, ctx->ev[0], ctx->ev[6]));
         for (int j : live) {
             const Job &J = jobs[j];
             const uint32_t *c = hchk + 4 * j;
@@ -988,6 +990,7 @@ void symbolic_preprocess(std::vector<SpTask> &tasks) {
                                      std::to_string(c[2]) + "/" + std::to_string(J.nnz) + ", flags " +
                                      std::to_string(c[3]));
             tasks[j].out->ms_sp = ms;
+            tasks[j].out->ms_dict = ms_dict;
             tasks[j].S->last_ndict = J.N;
         }
     }

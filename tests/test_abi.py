@@ -58,6 +58,6 @@ def test_binding_constants_match_the_header():
     for name in ("GB_OK", "GB_DONE", "GB_GREVLEX", "GB_DEGLEX", "GB_CTX_KEEP_STEP", "GB_CTX_REDUCE_SPARSE",
                  "GB_CTX_REDUCE_DENSE", "GB_CTX_NO_GRAPHS", "GB_CTX_SP_HASH", "GB_CTX_SKETCH", "GB_MODP_REDUCE64", "GB_MODP_REDUCE32",
                  "GB_MODP_MULADD", "GB_MODP_REDC", "GB_MODP_TO_MONT", "GB_MODP_MONT_MUL", "GB_MODP_INV",
-                 "GB_MODP_INV_SMALL", "GB_MODP_LAZY32", "GB_MODP_LAZY_MONT", "GB_F5_NO_CRITERION"):
+                 "GB_MODP_INV_SMALL", "GB_MODP_LAZY32", "GB_MODP_LAZY_MONT", "GB_MODP_CHAIN_BARRETT", "GB_MODP_CHAIN_MONT", "GB_F5_NO_CRITERION"):
         assert name in vals, name
         assert getattr(gb, name) == vals[name], name

@@ -163,3 +163,43 @@ def test_rejected_arguments():
         gb.gb_modp_apply(gb.GB_MODP_LAZY32, 65521, 1, 1 << 16, 1, 1, 1, 1)
     with pytest.raises(gb.GbError):
         gb.gb_modp_apply(42, 65521, 1, 0, 1, 1, 1, 1)
+
+
+def _chain(torch, op, p, a, b, c, steps):
+    A, B, C = _dev(torch, a), _dev(torch, b), _dev(torch, c)
+    out = torch.empty(len(a), dtype=torch.int32, device="cuda")
+    gb.gb_modp_apply(op, p, len(a), steps, A.data_ptr(), B.data_ptr(), C.data_ptr(), out.data_ptr(),
+                     torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return [int(x) for x in out.cpu().numpy().view(np.uint32)]
+
+
+def _chain_closed_form(a, b, c, w, p):
+    """x_w of x <- x b + c from x_0 = a: a b^w + c (b^w - 1) / (b - 1), or a + c w when b = 1."""
+    bw = pow(b, w, p)
+    if b % p == 1:
+        return (a + c * w) % p
+    return (a * bw + c * (bw - 1) * pow(b - 1, -1, p)) % p
+
+
+@pytest.mark.parametrize("p", [3, 251, 65521, 2147483647] + BIG_PRIMES[:4])
+@pytest.mark.parametrize("steps", [1, 7, 1000])
+def test_multiply_add_chains_against_the_geometric_sum(p, steps):
+    """The register chains of the inner-loop microbenchmark, Barrett and Montgomery, against the
+    closed form of the recurrence (and therefore against each other), including b = 0, 1, p - 1
+    and residues at the top of the range."""
+    import torch
+    rng = np.random.default_rng(p * 31 + steps)
+    n = 4096
+    a = rng.integers(0, p, n, dtype=np.uint64)
+    b = rng.integers(0, p, n, dtype=np.uint64)
+    c = rng.integers(0, p, n, dtype=np.uint64)
+    a[:6], b[:6], c[:6] = [p - 1] * 6, [0, 1, p - 1, p - 1, 1, 0], [p - 1, p - 1, p - 1, 0, 0, 0]
+    want = [_chain_closed_form(int(x), int(y), int(z), steps, p) for x, y, z in zip(a, b, c)]
+    for op in (gb.GB_MODP_CHAIN_BARRETT, gb.GB_MODP_CHAIN_MONT):
+        assert _chain(torch, op, p, a, b, c, steps) == want, op
+
+
+def test_chain_needs_a_step():
+    with pytest.raises(gb.GbError):
+        gb.gb_modp_apply(gb.GB_MODP_CHAIN_BARRETT, 65521, 1, 0, 1, 1, 1, 1)

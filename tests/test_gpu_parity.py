@@ -136,7 +136,11 @@ def test_standalone_sp_and_reduce_match_oracle_steps(ctx):
             pair = d.row_reducer == 0
             mac = gb.gb_symbolic_preprocess(S.h, S.n, d.row_t[pair], d.row_k[pair], True)
             ech = gb.gb_reduce_macaulay(mac)
-            compare_step(d, gb.gb_macaulay_export(mac), gb.gb_echelon_export(ech), f"standalone {k}")
+            mh = gb.gb_macaulay_export(mac)
+            compare_step(d, mh, gb.gb_echelon_export(ech), f"standalone {k}")
+            ms = gb.gb_macaulay_stats_get(mac)  # the per-run record: N, M = nnz, the stage split
+            assert (ms["nnz"], ms["ndict"], ms["nrows"]) == (len(mh["col"]), mh["dict_exps"].shape[0], len(mh["row_ptr"]) - 1)
+            assert 0 < ms["ms_dict"] <= ms["ms_sp"] and ms["ms_assemble"] >= 0
             gb.gb_echelon_destroy(ech)
             gb.gb_macaulay_destroy(mac)
             assert S.step()[0] == gb.GB_OK
