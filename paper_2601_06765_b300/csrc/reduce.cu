@@ -956,11 +956,12 @@ __global__ void __cluster_dims__(PCS, 1, 1) __launch_bounds__(PCT)
         c = block_min(c, red);
         if (threadIdx.x == 0) s_min[par] = c;
         if (c != NOLEAD && threadIdx.x <= KP) {  // this block's candidate pivot column and inverse
+            // (in Montgomery form for p >= 2^16: the update's products are then one redc each)
             const uint32_t u = threadIdx.x, jc = c - c0;
             uint32_t v;
             if (u < KP) v = u < P && u != t ? slab[(size_t)u * S + jc] : 0u;
             else v = fp.small ? fp_inv_small(row[jc], fp) : fp_inv(row[jc], fp);
-            s_pub[par][u] = v;
+            s_pub[par][u] = fp.small ? v : fp_to_mont(v, fp);
         }
         cl.sync();
         if (threadIdx.x < 32) {
@@ -984,15 +985,20 @@ __global__ void __cluster_dims__(PCS, 1, 1) __launch_bounds__(PCT)
         if (threadIdx.x <= KP) s_col[threadIdx.x] = *cl.map_shared_rank(&s_pub[par][threadIdx.x], s_owner);
         __syncthreads();
         const uint32_t inv = s_col[KP];
+        auto mulp = [&](uint32_t a, uint32_t b) -> uint32_t {  // a b mod p, b in the published form
+            if (fp.small) return fp_reduce32(a * b, fp);
+            const uint32_t r = fp_redc((uint64_t)a * b, fp);  // in [0, 2p)
+            return r >= fp.p ? r - fp.p : r;
+        };
         for (uint32_t j = (c > c0 ? c - c0 : 0) + threadIdx.x; j < w; j += PCT) {
-            const uint32_t y = fp.small ? fp_reduce32(row[j] * inv, fp) : fp_mul(row[j], inv, fp);
+            const uint32_t y = mulp(row[j], inv);
             row[j] = y;
             if (!y) continue;
             for (uint32_t u = 0; u < P; ++u) {
                 const uint32_t m = s_col[u];
                 if (!m) continue;
                 uint32_t *x = slab + (size_t)u * S + j;
-                *x = fp_sub(*x, fp.small ? fp_reduce32(m * y, fp) : fp_mul(m, y, fp), fp);
+                *x = fp_sub(*x, mulp(y, m), fp);
             }
         }
         if (q == 0 && threadIdx.x == 0) {
