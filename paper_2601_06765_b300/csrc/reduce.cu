@@ -43,7 +43,8 @@ inline unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t
 //
 // Accumulators are lazy (Rem. 8.1), in one of three modes:
 //   A32: p < 2^16, each product (p - f) v < 2^32 is Barrett-reduced to [0, p) and added to a 32-bit
-//        sum (exact while a column takes fewer than 2^16 updates: the host requires nA < 2^16);
+//        sum (exact while a column takes fewer than 2^16 updates: the host requires nA < 2^16;
+//        k_reduce_rows reduces each product only to [0, 2p) and takes nA < 2^15);
 //   A64: p < 2^16, the raw products are added to a 64-bit sum (no reduction per update);
 //   M64: p < 2^31, the Montgomery product redc(fR * v) in [0, 2p) is added to a 64-bit sum; only
 //        the multiplier is converted (once per pivot row), the entries stay in standard form.
@@ -298,12 +299,21 @@ __global__ void __launch_bounds__(RT, 6) k_reduce(const RedJob *__restrict__ job
 // chunk's pivot rows are one contiguous CSR range: they are staged in shared memory with 16-byte
 // asynchronous copies, issued before the chunk's multipliers are formed so that the copy overlaps
 // that step (R warps form the R rows' multipliers in parallel, the other warps load the next
-// chunk's inverse triangle).  Each staged entry is then read once and applied to every row of the
-// block with a non-zero multiplier for its pivot row, so the global reads per multiply-add fall by
-// up to R.  A chunk longer than the staging window is applied window by window.
+// chunk's inverse triangle).  The staged entries are then applied to every row of the block with
+// a non-zero multiplier for their pivot row, so the global reads per multiply-add fall by up to R:
+// each (pivot row, block row) pair with a non-zero multiplier goes to one warp, whose lanes walk
+// that pivot row's staged entries together (every lane does the same work; a lane per entry with
+// a loop over the entry's rows left lanes idle whenever the rows' counts differed).  A chunk
+// longer than the staging window is applied window by window.
 constexpr int RB = 1024;             // threads per block
 constexpr uint32_t RMAX = 16;        // rows per block at most
 constexpr uint32_t WMIN = 4096;      // entries of the smallest staging window
+// The update adds each product reduced only to [0, 2p) (Barrett with k = 32 without its final
+// correction): a column's 32-bit sum, below p + nA (2p - 1), stays exact for nA < 2^15 pivots.
+constexpr uint32_t ROWS_MAX_PIVOTS = 1u << 15;
+__device__ __forceinline__ uint32_t fp_reduce32_2p(uint32_t x, const Fp &f) {
+    return x - __umulhi(x, f.mu32) * f.p;  // x mod p, or x mod p + p
+}
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -396,6 +406,18 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
         }
         cp_async_wait0();
         __syncthreads();
+        // the chunk's (pivot row, block row) pairs with a non-zero multiplier: pair q is the
+        // (q - pre[k])-th block row of chunk row k, pre the exclusive prefix of the counts (every
+        // warp scans the 32 counts itself); a warp takes a pair and its lanes walk that pivot
+        // row's entries together, so every lane does the same work
+        const uint32_t nk_lane = lane < cnt ? s_cnt[buf][lane] : 0u;
+        uint32_t incl = nk_lane;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= (uint32_t)d) incl += y;
+        }
+        const uint32_t npairs = __shfl_sync(0xffffffffu, incl, 31), excl = incl - nk_lane;
         for (uint32_t w0 = e0; w0 < e1; w0 += win) {
             const uint32_t w1 = min(w0 + win, e1), a = w0 & ~3u;
             if (w0 != e0) {
@@ -403,23 +425,14 @@ __global__ void __launch_bounds__(RB, 1) k_reduce_rows(const RedJob *__restrict_
                 cp_async_wait0();
                 __syncthreads();
             }
-            uint32_t e = w0 + threadIdx.x;
-            if (e < w1) {
-                uint32_t k = 0, khi = cnt - 1;  // the chunk row holding entry e
-                while (k < khi) {
-                    const uint32_t mid = (k + khi + 1) >> 1;
-                    if (s_rp[buf][mid] <= e) k = mid; else khi = mid - 1;
-                }
-                for (; e < w1; e += RB) {
-                    while (e >= s_rp[buf][k + 1]) ++k;
-                    const uint32_t c = wcol[e - a], v = wval[e - a];
-                    // only the block rows with a non-zero multiplier for this pivot row
-                    const uint32_t nk = s_cnt[buf][k];
-                    for (uint32_t j = 0; j < nk; ++j) {
-                        const uint32_t w = s_list[k][j];
-                        atomicAdd(&acc[(w >> 16) * NS + c], fp_reduce32((w & 0xFFFFu) * v, fp));
-                    }
-                }
+            for (uint32_t q = warp; q < npairs; q += RB / 32) {
+                const uint32_t k = __popc(__ballot_sync(0xffffffffu, incl <= q));  // chunk row of pair q
+                const uint32_t w = s_list[k][q - __shfl_sync(0xffffffffu, excl, k)];
+                const uint32_t lo = max(s_rp[buf][k], w0), hi = min(s_rp[buf][k + 1], w1);
+                uint32_t *row = acc + (size_t)(w >> 16) * NS;
+                const uint32_t m = w & 0xFFFFu;
+                for (uint32_t e = lo + lane; e < hi; e += 32)
+                    atomicAdd(&row[wcol[e - a]], fp_reduce32_2p(m * wval[e - a], fp));
             }
             if (w1 < e1) __syncthreads();  // every thread is done with the window
         }
@@ -1340,7 +1353,7 @@ size_t rows_dyn_smem() {
 // next to a window of WMIN entries.  `rows` counts the non-pivot rows of the launch.
 uint32_t rows_per_block(const RedJob &J, uint64_t rows, size_t dyn) {
     const uint64_t nsm = (uint64_t)sm_count(), NS = (J.N + 3u) & ~3u;
-    if (rows <= nsm || dyn < 8ull * (WMIN + 8)) return 0;
+    if (rows <= nsm || dyn < 8ull * (WMIN + 8) || J.nA >= ROWS_MAX_PIVOTS) return 0;
     const uint64_t fit = (dyn - 8ull * (WMIN + 8)) / (4 * NS);
     const uint64_t r = std::min<uint64_t>({(rows + nsm - 1) / nsm, (uint64_t)RMAX, fit});
     return r >= 2 ? (uint32_t)r : 0u;
