@@ -11,9 +11,10 @@
 // (|a b| <= 2^14) is exact in FP32.  For each digit diagonal s the tensor cores accumulate
 //     D_s = sum_k sum_{i+j=s} a_i(k) b_j(k)
 // in FP32; with c_s <= L products per k, |partial sums| <= K L 2^14 <= 2^23 for K <= 512 / L,
-// so every partial sum is an integer the FP32 accumulator holds exactly (with a bit to spare).  The epilogue converts
-// each D_s to an integer and forms sum_s D_s 256^s mod p (Horner, one Barrett reduction per
-// digit), which equals (A B)[m][n] mod p.  One launch covers K <= 512 / L; longer products are
+// so every partial sum is an integer the FP32 accumulator holds exactly (with a bit to spare).  The
+// epilogue converts each D_s to an integer, pairs adjacent small diagonals in 32 bits, forms
+// C -/+ sum_s D_s (256^s mod p) in 64 bits and reduces it once (Barrett), which equals
+// (C -/+ A B)[m][n] mod p.  One launch covers K <= 512 / L; longer products are
 // split by the host into launches that each update C.
 //
 // Kernel: persistent, one CTA per SM, each CTA takes a contiguous run of the 128 x (128/L) output
@@ -89,9 +90,8 @@ struct MmParams {
     int cx, cy;             // TMA coordinates of the update region in C
     uint32_t ntn, items;    // tiles per tile row (BN columns each), tiles in all
     Fp fp;
-    uint64_t big;           // a multiple of p above 2^58, added before the Barrett reduction
-    uint32_t rd[7];         // 256^d mod p
-    int sub;                // 1: C -= A B, 0: C += A B
+    uint64_t big;           // a multiple of p above 2^62, added before the Barrett reduction
+    uint32_t rd[7];         // 256^d mod p (C += A B), or p minus it (C -= A B)
     uint32_t *err;          // bit 0: a bounded wait gave up
 };
 
@@ -232,6 +232,14 @@ __device__ __forceinline__ int acc_int(uint32_t bits) { return __float2int_rn(__
 // classic round-by-adding-a-magic-constant conversion; 2^24 itself continues the pattern).
 __device__ __forceinline__ int acc_int_small(uint32_t bits) {
     return __float_as_int(__fadd_rn(__uint_as_float(bits), 12582912.0f)) - 0x4B400000;
+}
+// D_lo + 256 D_hi for two diagonals of the small kind whose sum stays below 2^31 in magnitude,
+// from the two biased bit patterns: the bias of both, 257 times that of 1.5 2^23, comes off once
+// (wrapping 32-bit arithmetic; the true value fits, so the wrapped result is exact)
+__device__ __forceinline__ int acc_pair_small(uint32_t lo, uint32_t hi) {
+    const uint32_t a = (uint32_t)__float_as_int(__fadd_rn(__uint_as_float(lo), 12582912.0f));
+    const uint32_t b = (uint32_t)__float_as_int(__fadd_rn(__uint_as_float(hi), 12582912.0f));
+    return (int)(a + (b << 8) - 257u * 0x4B400000u);
 }
 // Diagonal d sums min(d + 1, 2L - 1 - d) digit products per k, so |D_d| <= that count x (512 / L)
 // x 2^14 at the largest K of a launch; where this is at most 2^22 (diagonals 0, 1, 5, 6 for L = 4;
@@ -427,10 +435,14 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
         for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
             const int mt = (int)(w / P.ntn), nt = (int)(w % P.ntn);
             const int set = (int)(it & 1u);
-            // value = sum_d D_d 256^d = sum_d D_d rd[d] (mod p); |sum| < 7 2^23 2^31 < 2^57
+            // value = sum_d D_d 256^d = sum_d D_d rd[d] (mod p), with rd[d] = -/+ 256^d mod p in
+            // [0, p) by the sign of the update.  Adjacent diagonals pair up in 32 bits first:
+            //   L = 4 (K <= 128): E_0 = D_0 + 256 D_1, |E_0| <= 2^21 + 2^30; E_5 = D_5 + 256 D_6,
+            //                     |E_5| <= 2^22 + 2^29; acc = E_0 rd0 + D_2 rd2 + D_3 rd3 + D_4 rd4
+            //                     + E_5 rd5, |acc| < 2^31 (2^30 + 2^29 + 2^25) < 2^62;
+            //   L = 2 (K <= 256): E_1 = D_1 + 256 D_2, |E_1| <= 2^23 + 2^30; acc = D_0 rd0 + E_1 rd1.
+            // Every product is signed 32 x 32 -> 64 bits (rd < p < 2^31).
             long long acc[CPT];
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) acc[j] = 0;
             wait(r_full(set), (it >> 1) & 1u);
             tc_fence_after();
             const uint32_t tb = trow + (uint32_t)set * Cfg::SET_COLS;
@@ -443,15 +455,24 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 tmem_wait_ld();
 #pragma unroll
                 for (int d = 0; d < Cfg::DIAG; ++d) tmem_zero<CPT>(tb + (uint32_t)(BN * d));
+                if constexpr (L == 4) {
+                    static_assert(small_diag<4>(0) && small_diag<4>(1) && small_diag<4>(5) && small_diag<4>(6),
+                                  "paired diagonals");
+                    const int r0 = (int)P.rd[0], r2 = (int)P.rd[2], r3 = (int)P.rd[3], r4 = (int)P.rd[4],
+                              r5 = (int)P.rd[5];
 #pragma unroll
-                for (int d = 0; d < Cfg::DIAG; ++d) {
-                    const long long rdd = (long long)P.rd[d];
-                    if (small_diag<L>(d)) {
+                    for (int j = 0; j < CPT; ++j)
+                        acc[j] = (long long)acc_pair_small(v[0][j], v[1][j]) * r0 +
+                                 (long long)acc_int(v[2][j]) * r2 + (long long)acc_int(v[3][j]) * r3 +
+                                 (long long)acc_int(v[4][j]) * r4 + (long long)acc_pair_small(v[5][j], v[6][j]) * r5;
+                } else {
+                    static_assert(L == 2 && small_diag<2>(0) && small_diag<2>(2), "paired diagonals");
+                    const int r0 = (int)P.rd[0], r1 = (int)P.rd[1];
 #pragma unroll
-                        for (int j = 0; j < CPT; ++j) acc[j] += acc_int_small(v[d][j]) * rdd;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < CPT; ++j) acc[j] += acc_int(v[d][j]) * rdd;
+                    for (int j = 0; j < CPT; ++j) {
+                        // E_1 = D_1 + 256 D_2: D_1 is converted exactly, D_2 through the bias
+                        const int e1 = acc_int(v[1][j]) + 256 * acc_int_small(v[2][j]);
+                        acc[j] = (long long)acc_int_small(v[0][j]) * r0 + (long long)e1 * r1;
                     }
                 }
             }
@@ -464,9 +485,6 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 bulk_wait_read0();  // the previous tile's store has read its buffer: a later tile's C
                 load_c(it + Cfg::NCBUF - 1);
             }
-            uint32_t res[CPT];
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) res[j] = fp_reduce((uint64_t)(acc[j] + (long long)P.big), P.fp);
             const uint32_t cb = it % Cfg::NCBUF;
             const bool have_c = wait(c_full(cb), (it / Cfg::NCBUF) & 1u);
             // row r of the thread's box: 128 bytes, 16-byte chunk j at chunk position j ^ (r mod 8)
@@ -478,11 +496,10 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                     uint4 *q = reinterpret_cast<uint4 *>(crow + 16u * (j ^ (r & 7u)));
                     uint4 c = *q;
                     uint32_t *cw = reinterpret_cast<uint32_t *>(&c);
+                    // C -/+ value in one Barrett reduction: c + acc + big lies in [0, 2^63)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const uint32_t x = res[4 * jj + e];
-                        cw[e] = P.sub ? (cw[e] >= x ? cw[e] - x : cw[e] + P.fp.p - x) : fp_add(cw[e], x, P.fp);
-                    }
+                    for (int e = 0; e < 4; ++e)
+                        cw[e] = fp_reduce((uint64_t)(acc[4 * jj + e] + (long long)P.big) + cw[e], P.fp);
                     *q = c;
                 }
             }
@@ -693,9 +710,9 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
     if (items >= (1ull << 31)) fail(GB_EUNSUPPORTED, "mm_update: too many tiles for one launch");
     P.items = (uint32_t)items;
     P.fp = fp;
-    P.big = ((1ull << 58) / fp.p + 1) * fp.p;
-    for (uint32_t d = 0, x = 1; d < 7; ++d, x = (uint32_t)((uint64_t)x * 256 % fp.p)) P.rd[d] = x;
-    P.sub = sub ? 1 : 0;
+    P.big = ((1ull << 62) / fp.p + 1) * fp.p;
+    for (uint32_t d = 0, x = 1; d < 7; ++d, x = (uint32_t)((uint64_t)x * 256 % fp.p))
+        P.rd[d] = sub && x ? fp.p - x : x;
     P.err = err;
     const unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)sm_count());
     MmTimer *T = t_capturing ? nullptr : t_mm_timer;
