@@ -13,7 +13,7 @@
 // in FP32; with c_s <= L products per k, |partial sums| <= K L 2^14 <= 2^23 for K <= 512 / L,
 // so every partial sum is an integer the FP32 accumulator holds exactly (with a bit to spare).  The
 // epilogue converts each D_s to an integer, pairs adjacent small diagonals in 32 bits, forms
-// C -/+ sum_s D_s (256^s mod p) in 64 bits and reduces it once (Barrett), which equals
+// sum_s D_s (256^s 2^32 mod p) in 64 bits, reduces it once (Montgomery) and adds C, which equals
 // (C -/+ A B)[m][n] mod p.  One launch covers K <= 512 / L; longer products are
 // split by the host into launches that each update C.
 //
@@ -90,8 +90,8 @@ struct MmParams {
     int cx, cy;             // TMA coordinates of the update region in C
     uint32_t ntn, items;    // tiles per tile row (BN columns each), tiles in all
     Fp fp;
-    uint64_t big;           // a multiple of p above 2^62, added before the Barrett reduction
-    uint32_t rd[7];         // 256^d mod p (C += A B), or p minus it (C -= A B)
+    uint64_t big;           // 2^31 p, which keeps the accumulated sum positive
+    uint32_t rd[7];         // (256^d mod p) 2^32 mod p (C += A B), or (p - 256^d mod p) 2^32 mod p
     uint32_t *err;          // bit 0: a bounded wait gave up
 };
 
@@ -435,13 +435,17 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
         for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
             const int mt = (int)(w / P.ntn), nt = (int)(w % P.ntn);
             const int set = (int)(it & 1u);
-            // value = sum_d D_d 256^d = sum_d D_d rd[d] (mod p), with rd[d] = -/+ 256^d mod p in
-            // [0, p) by the sign of the update.  Adjacent diagonals pair up in 32 bits first:
+            // value = sum_d D_d 256^d (mod p).  rd[d] = (-/+ 256^d) 2^32 mod p in [0, p), the sign
+            // that of the update, so acc = big + sum D_d rd[d] is -/+ value 2^32 (mod p), and one
+            // Montgomery reduction of acc (big = 2^31 p) gives -/+ value.  Adjacent diagonals pair
+            // up in 32 bits first:
             //   L = 4 (K <= 128): E_0 = D_0 + 256 D_1, |E_0| <= 2^21 + 2^30; E_5 = D_5 + 256 D_6,
-            //                     |E_5| <= 2^22 + 2^29; acc = E_0 rd0 + D_2 rd2 + D_3 rd3 + D_4 rd4
-            //                     + E_5 rd5, |acc| < 2^31 (2^30 + 2^29 + 2^25) < 2^62;
-            //   L = 2 (K <= 256): E_1 = D_1 + 256 D_2, |E_1| <= 2^23 + 2^30; acc = D_0 rd0 + E_1 rd1.
-            // Every product is signed 32 x 32 -> 64 bits (rd < p < 2^31).
+            //                     |E_5| <= 2^22 + 2^29; acc = big + E_0 rd0 + D_2 rd2 + D_3 rd3
+            //                     + D_4 rd4 + E_5 rd5, |acc - big| < p (2^30 + 2^29 + 2^25);
+            //   L = 2 (K <= 256): E_1 = D_1 + 256 D_2, |E_1| <= 2^23 + 2^30; acc = big + D_0 rd0
+            //                     + E_1 rd1, |acc - big| < p (2^30 + 2^24).
+            // So 0 < acc < 2^32 p, the range of the reduction.  Every product is signed
+            // 32 x 32 -> 64 bits (rd < p < 2^31).
             long long acc[CPT];
             wait(r_full(set), (it >> 1) & 1u);
             tc_fence_after();
@@ -460,19 +464,21 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                                   "paired diagonals");
                     const int r0 = (int)P.rd[0], r2 = (int)P.rd[2], r3 = (int)P.rd[3], r4 = (int)P.rd[4],
                               r5 = (int)P.rd[5];
+                    const long long big = (long long)P.big;
 #pragma unroll
                     for (int j = 0; j < CPT; ++j)
-                        acc[j] = (long long)acc_pair_small(v[0][j], v[1][j]) * r0 +
+                        acc[j] = big + (long long)acc_pair_small(v[0][j], v[1][j]) * r0 +
                                  (long long)acc_int(v[2][j]) * r2 + (long long)acc_int(v[3][j]) * r3 +
                                  (long long)acc_int(v[4][j]) * r4 + (long long)acc_pair_small(v[5][j], v[6][j]) * r5;
                 } else {
                     static_assert(L == 2 && small_diag<2>(0) && small_diag<2>(2), "paired diagonals");
                     const int r0 = (int)P.rd[0], r1 = (int)P.rd[1];
+                    const long long big = (long long)P.big;
 #pragma unroll
                     for (int j = 0; j < CPT; ++j) {
                         // E_1 = D_1 + 256 D_2: D_1 is converted exactly, D_2 through the bias
                         const int e1 = acc_int(v[1][j]) + 256 * acc_int_small(v[2][j]);
-                        acc[j] = (long long)acc_int_small(v[0][j]) * r0 + (long long)e1 * r1;
+                        acc[j] = big + (long long)acc_int_small(v[0][j]) * r0 + (long long)e1 * r1;
                     }
                 }
             }
@@ -496,10 +502,17 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                     uint4 *q = reinterpret_cast<uint4 *>(crow + 16u * (j ^ (r & 7u)));
                     uint4 c = *q;
                     uint32_t *cw = reinterpret_cast<uint32_t *>(&c);
-                    // C -/+ value in one Barrett reduction: c + acc + big lies in [0, 2^63)
+                    // C -/+ value: the Montgomery reduction of acc (in [0, 2p)), then two additions
+                    // mod p; each "x - p if x >= p" is min(x, x - p) in unsigned arithmetic
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        cw[e] = fp_reduce((uint64_t)(acc[4 * jj + e] + (long long)P.big) + cw[e], P.fp);
+                    for (int e = 0; e < 4; ++e) {
+                        const uint64_t t = (uint64_t)acc[4 * jj + e];
+                        const uint32_t m = (uint32_t)t * P.fp.pinv_neg;
+                        uint32_t u = (uint32_t)((t + (uint64_t)m * P.fp.p) >> 32);
+                        u = min(u, u - P.fp.p);
+                        const uint32_t sm = cw[e] + u;
+                        cw[e] = min(sm, sm - P.fp.p);
+                    }
                     *q = c;
                 }
             }
@@ -710,9 +723,11 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
     if (items >= (1ull << 31)) fail(GB_EUNSUPPORTED, "mm_update: too many tiles for one launch");
     P.items = (uint32_t)items;
     P.fp = fp;
-    P.big = ((1ull << 62) / fp.p + 1) * fp.p;
-    for (uint32_t d = 0, x = 1; d < 7; ++d, x = (uint32_t)((uint64_t)x * 256 % fp.p))
-        P.rd[d] = sub && x ? fp.p - x : x;
+    P.big = (uint64_t)fp.p << 31;
+    for (uint32_t d = 0, x = 1; d < 7; ++d, x = (uint32_t)((uint64_t)x * 256 % fp.p)) {
+        const uint32_t y = sub && x ? fp.p - x : x;     // -/+ 256^d mod p
+        P.rd[d] = (uint32_t)(((uint64_t)y << 32) % fp.p);  // in Montgomery form
+    }
     P.err = err;
     const unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)sm_count());
     MmTimer *T = t_capturing ? nullptr : t_mm_timer;
