@@ -60,7 +60,11 @@ struct MmCfg {
     static constexpr int DIAG = 2 * L - 1;             // digit diagonals
     static constexpr int BN = MM_MMA_N / L;            // columns of a C tile: 32 (L = 4), 64 (L = 2)
     static constexpr int KB = 512 / L / MM_BK;         // K blocks of the longest exact K
-    static constexpr int CPT = BN / 4;                 // columns of each epilogue thread
+    // epilogue groups taking alternate tiles, warps in each (all four lane quarters, WPG / 4 times)
+    static constexpr int EG = L == 4 ? 2 : 1;
+    static constexpr int WPG = MM_EPI / EG;
+    static constexpr int CPT = BN * 4 / WPG;           // columns of each epilogue thread
+    static constexpr int DRAIN = DIAG * CPT <= 64 ? CPT : 8;  // columns drained per tensor-memory wait
     static constexpr uint32_t A_BLK = MM_BM * 128;     // bytes of one digit x K block of A
     static constexpr uint32_t A_BYTES = L * KB * A_BLK;
     static constexpr uint32_t B_BLK = MM_MMA_N * 128;  // one K block of B^T: L digits x BN rows
@@ -153,7 +157,9 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * MM_EPI) : "memory"); }
+// the named barrier of epilogue group g, NT threads (barrier 0 is __syncthreads)
+template <int NT>
+__device__ __forceinline__ void epi_sync(int g) { asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(NT) : "memory"); }
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols) : "memory");
 }
@@ -286,9 +292,10 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
     const uint32_t w0 = (uint32_t)((unsigned long long)blockIdx.x * P.items / gridDim.x);
     const uint32_t w1 = (uint32_t)((unsigned long long)(blockIdx.x + 1) * P.items / gridDim.x);
     const int nkb = (int)((P.K + MM_BK - 1) / MM_BK);
-    // epilogue thread: row r of the tile is tensor-memory lane r; warps 2..17 cover the four lane
-    // quarters four times, warp group grp taking columns CPT grp .. CPT grp + CPT - 1
-    const int quarter = warp & 3, grp = (warp - 2) >> 2;
+    // epilogue thread: row r of the tile is tensor-memory lane r; the WPG warps of an epilogue
+    // group cover the four lane quarters WPG / 4 times, column group grp taking columns
+    // CPT grp .. CPT grp + CPT - 1
+    const int quarter = warp & 3, grp = ((warp - 2) % Cfg::WPG) >> 2;
     const uint32_t r = (uint32_t)(32 * quarter + lane);
 
     if (threadIdx.x == 0) {
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
         mbar_init(a_empty, 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(r_full(i), 1);
-            mbar_init(r_empty(i), MM_EPI);  // one arrival per epilogue warp
+            mbar_init(r_empty(i), Cfg::WPG);  // one arrival per warp of the group that drains it
         }
         for (int c = 0; c < Cfg::NCBUF; ++c) mbar_init(c_full(c), 1);
         static_assert(Cfg::NCBUF <= 4, "barrier space");
@@ -319,10 +326,15 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
     // Every product accumulates: the epilogue zeroes both accumulator sets here and each set again
     // right after draining it, so no product has to open a diagonal by overwriting it.
     if (warp >= 2) {
+        const int eg = (warp - 2) / Cfg::WPG;
 #pragma unroll
         for (int set = 0; set < 2; ++set)
+            if (Cfg::EG == 1 || set == eg)  // with two groups, group g drains (and zeroes) set g
 #pragma unroll
-            for (int d = 0; d < Cfg::DIAG; ++d) tmem_zero<CPT>(trow + (uint32_t)set * Cfg::SET_COLS + (uint32_t)(BN * d));
+                for (int d = 0; d < Cfg::DIAG; ++d)
+#pragma unroll
+                    for (int h = 0; h < CPT / Cfg::DRAIN; ++h)
+                        tmem_zero<Cfg::DRAIN>(trow + (uint32_t)set * Cfg::SET_COLS + (uint32_t)(BN * d + Cfg::DRAIN * h));
         tmem_wait_st();
     }
     tc_fence_before();
@@ -413,10 +425,14 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
             __syncwarp();
         }
     } else if (warp >= 2) {
-        // ---- epilogue.  One thread (the storer) also moves C: it loads the C tile of a later
-        // tile into a buffer as soon as the store that last used the buffer has read it, so the
-        // producer's stream of B blocks never waits on the epilogue.
-        const bool storer = warp == 2 && lane == 0;
+        // ---- epilogue.  EG groups of warps take alternate tiles (group eg the CTA's tiles
+        // it = eg mod EG), so that one group drains a set while the other is still busy with the
+        // C tile of the tile before.  In each group one thread (the storer) also moves C: it
+        // loads the C tile of the group's next tile into the group's buffer as soon as the store
+        // that last used the buffer has read it, so the producer's stream of B blocks never waits
+        // on the epilogue.
+        const int eg = (warp - 2) / Cfg::WPG;
+        const bool storer = (warp - 2) % Cfg::WPG == 0 && lane == 0;
         auto load_c = [&](uint32_t itc) {  // C tile of the CTA's itc-th tile into buffer itc mod NCBUF
             const uint32_t wc = w0 + itc;
             if (wc >= w1 || *abort_flag) return;
@@ -428,11 +444,16 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                 tma_load_2d(sC + cbuf * Cfg::C_TILE + (uint32_t)h * Cfg::C_BOX, &tc, c_full(cbuf), P.cx + nc * BN + 32 * h,
                             P.cy + mc * MM_BM);
         };
-        if (storer)
-            for (uint32_t i = 0; i < (uint32_t)Cfg::NCBUF; ++i) load_c(i);
+        if (storer) {
+            if (Cfg::EG == 1)
+                for (uint32_t i = 0; i < (uint32_t)Cfg::NCBUF; ++i) load_c(i);
+            else
+                load_c((uint32_t)eg);
+        }
         const uint32_t col0 = (uint32_t)(CPT * grp);                // first column in the tile
         const uint32_t box = col0 / 32, chunk0 = (col0 % 32) / 4;  // its 32-column box, 16-byte chunk
-        for (uint32_t w = w0, it = 0; w < w1; ++w, ++it) {
+        const Fp fp = P.fp;
+        for (uint32_t w = w0 + (uint32_t)eg, it = (uint32_t)eg; w < w1; w += Cfg::EG, it += Cfg::EG) {
             const int mt = (int)(w / P.ntn), nt = (int)(w % P.ntn);
             const int set = (int)(it & 1u);
             // value = sum_d D_d 256^d (mod p).  rd[d] = (-/+ 256^d) 2^32 mod p in [0, p), the sign
@@ -444,42 +465,45 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
             //                     + D_4 rd4 + E_5 rd5, |acc - big| < p (2^30 + 2^29 + 2^25);
             //   L = 2 (K <= 256): E_1 = D_1 + 256 D_2, |E_1| <= 2^23 + 2^30; acc = big + D_0 rd0
             //                     + E_1 rd1, |acc - big| < p (2^30 + 2^24).
-            // So 0 < acc < 2^32 p, the range of the reduction.  Every product is signed
-            // 32 x 32 -> 64 bits (rd < p < 2^31).
-            long long acc[CPT];
+            // So 0 < acc < 2^32 p, the range of the reduction, whose result u (in [0, 2p)) is
+            // brought to [0, p) by "u - p if u >= p", min(u, u - p) in unsigned arithmetic.  Every
+            // product is signed 32 x 32 -> 64 bits (rd < p < 2^31).
+            uint32_t u[CPT];
             wait(r_full(set), (it >> 1) & 1u);
             tc_fence_after();
             const uint32_t tb = trow + (uint32_t)set * Cfg::SET_COLS;
-            {
-                // every diagonal's load in flight at once, one wait: the drain pays one tensor-memory
-                // latency instead of one per diagonal
-                uint32_t v[Cfg::DIAG][CPT];
 #pragma unroll
-                for (int d = 0; d < Cfg::DIAG; ++d) tmem_ld<CPT>(tb + (uint32_t)(BN * d), v[d]);
+            for (int h = 0; h < CPT / Cfg::DRAIN; ++h) {
+                // every diagonal's load of DRAIN columns in flight at once, one wait: the drain pays
+                // one tensor-memory latency per DRAIN columns instead of one per diagonal
+                constexpr int NW = Cfg::DRAIN;
+                uint32_t v[Cfg::DIAG][NW];
+#pragma unroll
+                for (int d = 0; d < Cfg::DIAG; ++d) tmem_ld<NW>(tb + (uint32_t)(BN * d + NW * h), v[d]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int d = 0; d < Cfg::DIAG; ++d) tmem_zero<CPT>(tb + (uint32_t)(BN * d));
-                if constexpr (L == 4) {
-                    static_assert(small_diag<4>(0) && small_diag<4>(1) && small_diag<4>(5) && small_diag<4>(6),
-                                  "paired diagonals");
-                    const int r0 = (int)P.rd[0], r2 = (int)P.rd[2], r3 = (int)P.rd[3], r4 = (int)P.rd[4],
-                              r5 = (int)P.rd[5];
-                    const long long big = (long long)P.big;
+                for (int d = 0; d < Cfg::DIAG; ++d) tmem_zero<NW>(tb + (uint32_t)(BN * d + NW * h));
+                const long long big = (long long)P.big;
 #pragma unroll
-                    for (int j = 0; j < CPT; ++j)
-                        acc[j] = big + (long long)acc_pair_small(v[0][j], v[1][j]) * r0 +
-                                 (long long)acc_int(v[2][j]) * r2 + (long long)acc_int(v[3][j]) * r3 +
-                                 (long long)acc_int(v[4][j]) * r4 + (long long)acc_pair_small(v[5][j], v[6][j]) * r5;
-                } else {
-                    static_assert(L == 2 && small_diag<2>(0) && small_diag<2>(2), "paired diagonals");
-                    const int r0 = (int)P.rd[0], r1 = (int)P.rd[1];
-                    const long long big = (long long)P.big;
-#pragma unroll
-                    for (int j = 0; j < CPT; ++j) {
+                for (int j = 0; j < NW; ++j) {
+                    long long acc;
+                    if constexpr (L == 4) {
+                        static_assert(small_diag<4>(0) && small_diag<4>(1) && small_diag<4>(5) && small_diag<4>(6),
+                                      "paired diagonals");
+                        acc = big + (long long)acc_pair_small(v[0][j], v[1][j]) * (int)P.rd[0] +
+                              (long long)acc_int(v[2][j]) * (int)P.rd[2] + (long long)acc_int(v[3][j]) * (int)P.rd[3] +
+                              (long long)acc_int(v[4][j]) * (int)P.rd[4] +
+                              (long long)acc_pair_small(v[5][j], v[6][j]) * (int)P.rd[5];
+                    } else {
+                        static_assert(L == 2 && small_diag<2>(0) && small_diag<2>(2), "paired diagonals");
                         // E_1 = D_1 + 256 D_2: D_1 is converted exactly, D_2 through the bias
                         const int e1 = acc_int(v[1][j]) + 256 * acc_int_small(v[2][j]);
-                        acc[j] = big + (long long)acc_int_small(v[0][j]) * r0 + (long long)e1 * r1;
+                        acc = big + (long long)acc_int_small(v[0][j]) * (int)P.rd[0] + (long long)e1 * (int)P.rd[1];
                     }
+                    const uint64_t t = (uint64_t)acc;
+                    const uint32_t m = (uint32_t)t * fp.pinv_neg;
+                    const uint32_t x = (uint32_t)((t + (uint64_t)m * fp.p) >> 32);
+                    u[NW * h + j] = min(x, x - fp.p);
                 }
             }
             // the set is drained and zeroed: hand it back
@@ -487,7 +511,7 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(r_empty(set));
-            if (Cfg::NCBUF >= 2 && storer && it > 0) {
+            if (Cfg::EG == 1 && Cfg::NCBUF >= 2 && storer && it > 0) {
                 bulk_wait_read0();  // the previous tile's store has read its buffer: a later tile's C
                 load_c(it + Cfg::NCBUF - 1);
             }
@@ -502,22 +526,16 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                     uint4 *q = reinterpret_cast<uint4 *>(crow + 16u * (j ^ (r & 7u)));
                     uint4 c = *q;
                     uint32_t *cw = reinterpret_cast<uint32_t *>(&c);
-                    // C -/+ value: the Montgomery reduction of acc (in [0, 2p)), then two additions
-                    // mod p; each "x - p if x >= p" is min(x, x - p) in unsigned arithmetic
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const uint64_t t = (uint64_t)acc[4 * jj + e];
-                        const uint32_t m = (uint32_t)t * P.fp.pinv_neg;
-                        uint32_t u = (uint32_t)((t + (uint64_t)m * P.fp.p) >> 32);
-                        u = min(u, u - P.fp.p);
-                        const uint32_t sm = cw[e] + u;
-                        cw[e] = min(sm, sm - P.fp.p);
+                        const uint32_t s = cw[e] + u[4 * jj + e];  // C -/+ value, both in [0, p)
+                        cw[e] = min(s, s - fp.p);
                     }
                     *q = c;
                 }
             }
             fence_async_smem();
-            epi_sync();
+            epi_sync<32 * Cfg::WPG>(eg);
             if (storer) {
                 const int boxes = Cfg::C_BOXES == 2 && P.N - (uint32_t)nt * BN > 32u ? 2 : 1;
                 if (!*abort_flag)
@@ -525,9 +543,9 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                         tma_store_2d(&tc, sC + cb * Cfg::C_TILE + (uint32_t)h * Cfg::C_BOX, P.cx + nt * BN + 32 * h,
                                      P.cy + mt * MM_BM);
                 bulk_commit();
-                if (Cfg::NCBUF == 1) {
-                    bulk_wait_read0();  // the buffer is free again: the next tile's C
-                    load_c(it + 1);
+                if (Cfg::EG == 2 || Cfg::NCBUF == 1) {
+                    bulk_wait_read0();  // the buffer is free again: the group's next C tile
+                    load_c(it + Cfg::EG);
                 }
             }
         }
