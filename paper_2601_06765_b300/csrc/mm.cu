@@ -561,50 +561,79 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
 }
 
 // Digit planes: dst[l][r][k] (row pitch kpad, plane pitch rows * kpad) = BF16 bits of the l-th
-// balanced base-256 digit of the residue at src[r * rs + k * ks], for r < R, k < K.
+// balanced base-256 digit of a residue x (representative x or x - p, T as in the header).
 template <int L>
-__global__ void k_digits(const uint32_t *__restrict__ src, uint64_t rs, uint64_t ks, uint32_t R, uint32_t K,
-                         uint16_t *__restrict__ dst, uint64_t kpad, uint64_t plane, uint32_t p) {
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    for (uint32_t r = blockIdx.y; r < R; r += gridDim.y) {
-        const uint32_t x = src[(size_t)r * rs + (size_t)k * ks];
-        const uint32_t T = L == 2 ? 32639u : 2139062143u;  // 127 (1 + 256 + ... + 256^{L-1})
-        int v = x <= T ? (int)x : (int)(x - p);
+__device__ __forceinline__ void digits_of(uint32_t x, uint32_t p, uint32_t (&a)[L]) {
+    const uint32_t T = L == 2 ? 32639u : 2139062143u;  // 127 (1 + 256 + ... + 256^{L-1})
+    int v = x <= T ? (int)x : (int)(x - p);
 #pragma unroll
-        for (int l = 0; l < L; ++l) {
-            const int a = l + 1 < L ? (int)(((uint32_t)v & 0xFFu) ^ 0x80u) - 0x80 : v;
-            if (l + 1 < L) v = (v - a) >> 8;
-            dst[(size_t)l * plane + (size_t)r * kpad + k] = (uint16_t)(__float_as_uint((float)a) >> 16);
+    for (int l = 0; l < L; ++l) {
+        const int d = l + 1 < L ? (int)(((uint32_t)v & 0xFFu) ^ 0x80u) - 0x80 : v;
+        if (l + 1 < L) v = (v - d) >> 8;
+        a[l] = __float_as_uint((float)d) >> 16;
+    }
+}
+
+// the planes of 8 consecutive K values of one row: one 16-byte store per plane (dst 16-byte aligned)
+template <int L>
+__device__ __forceinline__ void put_digits8(const uint32_t (&x)[8], uint32_t p, uint16_t *dst, uint64_t plane) {
+    uint32_t w[L][4];
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+        uint32_t a[L], b[L];
+        digits_of<L>(x[i], p, a);
+        digits_of<L>(x[i + 1], p, b);
+#pragma unroll
+        for (int l = 0; l < L; ++l) w[l][i / 2] = a[l] | (b[l] << 16);
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+        *reinterpret_cast<uint4 *>(dst + (size_t)l * plane) = make_uint4(w[l][0], w[l][1], w[l][2], w[l][3]);
+}
+
+// rows of a row-major source (src[r * rs + k]): thread per (row, 8 K values), the whole padded
+// row written (zeros past K); the loads are 16-byte vectors when vec (rs % 4 == 0, src 16-byte
+// aligned)
+template <int L>
+__global__ void k_digits(const uint32_t *__restrict__ src, uint64_t rs, uint32_t R, uint32_t K,
+                         uint16_t *__restrict__ dst, uint64_t kpad, uint64_t plane, uint32_t p, int vec) {
+    const uint64_t groups = kpad / 8, total = (uint64_t)R * groups;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = (uint32_t)(t / groups), k0 = (uint32_t)(t % groups) * 8u;
+        const uint32_t *row = src + (size_t)r * rs;
+        uint32_t x[8];
+        if (vec && k0 + 8 <= K) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(row + k0), b = *reinterpret_cast<const uint4 *>(row + k0 + 4);
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = k0 + i < K ? row[k0 + i] : 0u;
         }
+        put_digits8<L>(x, p, dst + (size_t)r * kpad + k0, plane);
     }
 }
 
 // The same planes when the source is row-major in K (src[k * ks + r], the columns of B as rows of
-// B^T): 32 x 32 tiles through shared memory, so that both the reads and the writes are coalesced.
+// B^T): 64 x 64 tiles through shared memory, read along r and written along k, 8 K values (16
+// bytes per plane) a thread, a warp covering four rows' 128-byte segments.  The whole padded row
+// is written (zeros past K).
 template <int L>
 __global__ void k_digits_t(const uint32_t *__restrict__ src, uint64_t ks, uint32_t R, uint32_t K,
                            uint16_t *__restrict__ dst, uint64_t kpad, uint64_t plane, uint32_t p) {
-    __shared__ uint32_t tile[32][33];
-    const uint32_t r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-    const uint32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-    for (uint32_t kk = ty; kk < 32; kk += 8) {
-        const uint32_t k = k0 + kk, r = r0 + tx;
-        tile[kk][tx] = (k < K && r < R) ? src[(size_t)k * ks + r] : 0u;
+    __shared__ uint32_t tile[64][65];
+    const uint32_t r0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
+    for (uint32_t i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const uint32_t kk = i / 64, rr = i % 64, k = k0 + kk, r = r0 + rr;
+        tile[kk][rr] = (k < K && r < R) ? src[(size_t)k * ks + r] : 0u;
     }
     __syncthreads();
-    const uint32_t T = L == 2 ? 32639u : 2139062143u;  // 127 (1 + 256 + ... + 256^{L-1})
-    for (uint32_t rr = ty; rr < 32; rr += 8) {
-        const uint32_t r = r0 + rr, k = k0 + tx;
-        if (r >= R || k >= K) continue;
-        const uint32_t x = tile[tx][rr];
-        int v = x <= T ? (int)x : (int)(x - p);
+    for (uint32_t i = threadIdx.x; i < 64 * 8; i += blockDim.x) {
+        const uint32_t rr = i / 8, kg = i % 8, r = r0 + rr;
+        if (r >= R || k0 + 8 * kg >= kpad) continue;
+        uint32_t x[8];
 #pragma unroll
-        for (int l = 0; l < L; ++l) {
-            const int a = l + 1 < L ? (int)(((uint32_t)v & 0xFFu) ^ 0x80u) - 0x80 : v;
-            if (l + 1 < L) v = (v - a) >> 8;
-            dst[(size_t)l * plane + (size_t)r * kpad + k] = (uint16_t)(__float_as_uint((float)a) >> 16);
-        }
+        for (int j = 0; j < 8; ++j) x[j] = tile[8 * kg + j][rr];
+        put_digits8<L>(x, p, dst + (size_t)r * kpad + k0 + 8 * kg, plane);
     }
 }
 
@@ -670,19 +699,21 @@ void DigitPlanes::alloc(Arena &ar, uint32_t L_, uint64_t rows_, uint64_t K_, cud
 
 void to_digits(const uint32_t *src, uint64_t rs, uint64_t ks, const DigitPlanes &D, uint32_t p, cudaStream_t st) {
     if (!D.rows || !D.K) return;
+    const uint64_t plane = D.rows * D.kpad;
     if (rs == 1 && ks != 1) {  // K-strided source: transpose through shared memory
-        if ((D.K + 31) / 32 > 65535u) fail(GB_EUNSUPPORTED, "digit planes: K too large for one launch");
-        const dim3 grid((unsigned)((D.rows + 31) / 32), (unsigned)((D.K + 31) / 32));
-        const uint64_t plane = D.rows * D.kpad;
+        if ((D.kpad + 63) / 64 > 65535u) fail(GB_EUNSUPPORTED, "digit planes: K too large for one launch");
+        const dim3 grid((unsigned)((D.rows + 63) / 64), (unsigned)((D.kpad + 63) / 64));
         if (D.L == 2) k_digits_t<2><<<grid, 256, 0, st>>>(src, ks, (uint32_t)D.rows, (uint32_t)D.K, D.p, D.kpad, plane, p);
         else k_digits_t<4><<<grid, 256, 0, st>>>(src, ks, (uint32_t)D.rows, (uint32_t)D.K, D.p, D.kpad, plane, p);
         counted();
         return;
     }
-    const dim3 grid((unsigned)((D.K + 255) / 256), (unsigned)std::min<uint64_t>(D.rows, 65535));
-    const uint64_t plane = D.rows * D.kpad;
-    if (D.L == 2) k_digits<2><<<grid, 256, 0, st>>>(src, rs, ks, (uint32_t)D.rows, (uint32_t)D.K, D.p, D.kpad, plane, p);
-    else k_digits<4><<<grid, 256, 0, st>>>(src, rs, ks, (uint32_t)D.rows, (uint32_t)D.K, D.p, D.kpad, plane, p);
+    if (ks != 1) fail(GB_EUNSUPPORTED, "digit planes: the source must be contiguous in K or in rows");
+    const int vec = rs % 4 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    const uint64_t items = D.rows * (D.kpad / 8);
+    const unsigned grid = (unsigned)std::min<uint64_t>((items + 255) / 256, 65535u * 16u);
+    if (D.L == 2) k_digits<2><<<grid, 256, 0, st>>>(src, rs, (uint32_t)D.rows, (uint32_t)D.K, D.p, D.kpad, plane, p, vec);
+    else k_digits<4><<<grid, 256, 0, st>>>(src, rs, (uint32_t)D.rows, (uint32_t)D.K, D.p, D.kpad, plane, p, vec);
     counted();
 }
 
