@@ -8,7 +8,9 @@
 // non-pivot rows (nC x N'), the reduction is
 //     F W[:, :nA] = M[:, :nA],    D' = M[:, nAp:] - F W[:, nAp:],
 // and F is found block by block (right-looking, blocks of BS pivots):
-//     F_J = M[:, J] U_J^{-1}                  (U_J = W[J, J], CUDA cores: k_trsm_block)
+//     F_J = M[:, J] U_J^{-1}                  (U_J = W[J, J]; four digits: M[:, J] + M[:, J] X_J on
+//                                              the tensor cores, X_J = U_J^{-1} - I from k_block_inv;
+//                                              two digits: the CUDA-core solve k_trsm_block)
 //     M[:, j1:] <- M[:, j1:] - F_J W[J, j1:]  (tensor cores: mm_update)
 // D' is unique (the pivot rows have distinct leading columns), so this schedule gives the same
 // bits as the row-by-row sparse reduction.  BS = 512 / L (L digits per residue) is the longest K
@@ -215,6 +217,44 @@ __global__ void __launch_bounds__(DW * 32) k_trsm_block(DenseJob J, uint32_t j0)
     }
 }
 
+// X_b = U_b^{-1} - I for every pivot block b (U_b = W[J_b, J_b], unit upper triangular, its
+// entries right of the diagonal in Ub), as the digit planes of X_b^T: plane row b bs + n, K index
+// i holds X_b[i][n].  From X'U = I with X' = U^{-1}: X'[i][j] = -(U[i][j] + sum_{i<k<j} X'[i][k]
+// U[k][j]) for j > i, X'[i][i] = 1, 0 below.  Thread i computes row i, column by column, with
+// U_b staged in shared memory (rows padded by one word, so the U[k][j] reads of a warp, k = i + 1
+// + 2t, fall in distinct banks).  Two products (each below 2^62) are summed before each
+// reduction.  Rows and columns at or past the
+// block's pivot count jn (the padding of the last block) are zero.  Shared memory: U_b and the
+// rows of X, 2 bs (bs + 1) words.
+__global__ void k_block_inv(DenseJob J, uint16_t *__restrict__ xt, uint64_t kpad, uint64_t plane) {
+    extern __shared__ uint32_t xs[];
+    const uint32_t bs = J.bs, ld = bs + 1, b = blockIdx.x, i = threadIdx.x, j0 = b * bs;
+    const uint32_t jn = min(bs, J.nA - j0);
+    uint32_t *us = xs + (size_t)bs * ld;  // U_b, row k at us + k ld
+    const uint32_t *U = J.Ub + (size_t)b * bs * bs;
+    for (uint32_t e = i; e < bs * bs; e += blockDim.x) us[(e / bs) * ld + e % bs] = U[e];
+    __syncthreads();
+    const Fp fp = J.fp;
+    uint32_t *x = xs + (size_t)i * ld;
+    for (uint32_t j = 0; j < bs; ++j) {
+        uint32_t v = 0;
+        if (j < jn && i < j) {
+            uint32_t a = us[i * ld + j];
+            uint32_t k = i + 1;
+            for (; k + 1 < j; k += 2) {
+                const unsigned long long t =
+                    (unsigned long long)x[k] * us[k * ld + j] + (unsigned long long)x[k + 1] * us[(k + 1) * ld + j];
+                a = fp_add(a, fp_reduce(t, fp), fp);
+            }
+            if (k < j) a = fp_add(a, fp_mul(x[k], us[k * ld + j], fp), fp);
+            v = a ? fp.p - a : 0u;
+        }
+        x[j] = v;
+    }
+    // X_b^T digit planes: for each column n, the threads write consecutive K indices
+    for (uint32_t n = 0; n < bs; ++n) put_digits<4>(x[n], fp.p, xt + (size_t)(j0 + n) * kpad + i, plane);
+}
+
 __global__ void k_dense_work(DenseJob J, unsigned long long macs) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         J.work[0] += J.nA;
@@ -242,7 +282,9 @@ size_t dense_bytes(uint32_t p, uint32_t N, uint32_t nA, uint32_t nC) {
     const uint64_t L = digits_for(p), bs = mm_kmax(p);
     const uint64_t nAp = (nA + 63) / 64 * 64, Np = nAp + (N - nA), ldm = (Np + 3) / 4 * 4;
     const uint64_t nblk = (nAp + bs - 1) / bs;
-    return 2 * L * Np * nAp + 4 * nC * ldm + 4 * nblk * bs * bs + 2 * L * nC * bs + 4096;
+    // W^T planes, M, the blocks U_J, F's planes; for four digits also X_J^T's and M[:, J]'s planes
+    const uint64_t tc = L == 4 ? 2 * L * nblk * bs * bs + 2 * L * nC * bs : 0;
+    return 2 * L * Np * nAp + 4 * nC * ldm + 4 * nblk * bs * bs + 2 * L * nC * bs + tc + 4096;
 }
 
 void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaStream_t st) {
@@ -280,11 +322,43 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
     counted(3);
     unsigned long long macs = 0;
     const MmPlan plan(F, WT, J.M, J.ldm, J.nC, J.Np, J.fp);
+    // Four digits (p >= 2^16): the multipliers of a block on the tensor cores as well,
+    //     F_J = M[:, J] U_J^{-1} = M[:, J] + M[:, J] X_J,   X_J = U_J^{-1} - I,
+    // computed in place in M[:, J] from the digit planes of M[:, J] (MJ) and of X_J^T (Xt, all
+    // blocks at once by k_block_inv); then F_J's digit planes for the trailing update.  Two digits
+    // keep the CUDA-core solve (k_trsm_block).
+    DigitPlanes Xt, MJ;
+    std::unique_ptr<MmPlan> fplan;
+    if (L == 4) {
+        Xt.alloc(ar, L, (uint64_t)nblk * J.bs, J.bs, st);
+        MJ.alloc(ar, L, J.nC, J.bs, st);
+        const size_t smem = 8ull * J.bs * (J.bs + 1);
+        opt_in_smem(reinterpret_cast<const void *>(k_block_inv));
+        k_block_inv<<<nblk, J.bs, smem, st>>>(J, Xt.p, Xt.kpad, (uint64_t)Xt.rows * Xt.kpad);
+        counted();
+        fplan = std::make_unique<MmPlan>(MJ, Xt, J.M, J.ldm, J.nC, J.Np, J.fp);
+    }
+    // a view of planes P (same buffer and pitch) with only the first kb K values
+    auto view = [](const DigitPlanes &P, uint32_t kb) {
+        DigitPlanes v;
+        v.L = P.L;
+        v.rows = P.rows;
+        v.K = kb;
+        v.kpad = P.kpad;
+        v.p = P.p;
+        return v;
+    };
     for (uint32_t b = 0; b < nblk; ++b) {
         const uint32_t j0 = b * J.bs, j1 = std::min(j0 + J.bs, J.nAp);
-        if (L == 2) k_trsm_block<2><<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J, j0);
-        else k_trsm_block<4><<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J, j0);
-        counted();
+        if (L == 4) {
+            const uint32_t kb = j1 - j0;
+            to_digits(J.M + j0, J.ldm, 1, view(MJ, kb), J.fp.p, st);
+            fplan->update(0, 0, 0, j0, j0, 0, J.nC, kb, kb, false, err, st);
+            to_digits(J.M + j0, J.ldm, 1, view(F, kb), J.fp.p, st);
+        } else {
+            k_trsm_block<2><<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J, j0);
+            counted();
+        }
         // columns j1.. of M, K = the block's pivots (a multiple of 64: padding pivots are zero)
         plan.update(0, 0, j0, j1, j1, 0, J.nC, J.Np - j1, j1 - j0, true, err, st);
         macs += (unsigned long long)J.nC * (j1 - j0) * (J.Np - j1);

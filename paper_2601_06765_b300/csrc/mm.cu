@@ -742,8 +742,9 @@ MmPlan::MmPlan(const DigitPlanes &A_, const DigitPlanes &B_, uint32_t *C_, uint6
 MmPlan::~MmPlan() { delete maps; }
 
 // C[cy + m][cx + n] <- C -/+ sum_k A[ay + m][ax + k] B^T[by + n][bx + k] mod p for m < M, n < N,
-// k < K <= mm_kmax(p).  The update region must end the C tensor of the plan on the right and
-// bottom (the stores of ragged tiles are clipped there) and cx must be a multiple of 4.
+// k < K <= mm_kmax(p).  A ragged last tile of the update region (N not a multiple of the tile
+// width, M not a multiple of 128) must end the C tensor of the plan on that side, where the TMA
+// store clips it; cx must be a multiple of 4.
 void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t cx, uint32_t cy, uint32_t M,
                     uint32_t N, uint32_t K, bool sub, uint32_t *err, cudaStream_t st) const {
     if (!M || !N || !K) return;
@@ -755,7 +756,9 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
     if (K % MM_BK && ax + K != A->K && bx + K != B->K) fail(GB_EDEVICE, "mm_update: ragged K inside both planes");
     if (ax + K > A->K || bx + K > B->K || ay + M > A->rows || by + N > B->rows)
         fail(GB_EDEVICE, "mm_update: operand range outside the digit planes");
-    if (cx % 4 || cx + N != cols || cy + M != rows) fail(GB_EDEVICE, "mm_update: C region does not end the tensor");
+    const uint32_t bn = MM_MMA_N / A->L;
+    if (cx % 4 || cx + N > cols || cy + M > rows || (N % bn && cx + N != cols) || (M % MM_BM && cy + M != rows))
+        fail(GB_EDEVICE, "mm_update: a ragged C region does not end the tensor");
     MmParams P{};
     P.M = M;
     P.N = N;
@@ -766,7 +769,6 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
     P.by = (int)by;
     P.cx = (int)cx;
     P.cy = (int)cy;
-    const uint32_t bn = MM_MMA_N / A->L;
     P.ntn = (N + bn - 1) / bn;
     const uint64_t items = (uint64_t)((M + MM_BM - 1) / MM_BM) * P.ntn;
     if (items >= (1ull << 31)) fail(GB_EUNSUPPORTED, "mm_update: too many tiles for one launch");
