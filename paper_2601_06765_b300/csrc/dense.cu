@@ -325,8 +325,10 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
     // Four digits (p >= 2^16): the multipliers of a block on the tensor cores as well,
     //     F_J = M[:, J] U_J^{-1} = M[:, J] + M[:, J] X_J,   X_J = U_J^{-1} - I,
     // computed in place in M[:, J] from the digit planes of M[:, J] (MJ) and of X_J^T (Xt, all
-    // blocks at once by k_block_inv); then F_J's digit planes for the trailing update.  Two digits
-    // keep the CUDA-core solve (k_trsm_block).
+    // blocks at once by k_block_inv).  The product's epilogue also writes F_J's digit planes (the
+    // A operand of the trailing update), and the trailing update's epilogue those of the next
+    // block's columns (MJ for the next block), so that only block 0's MJ is converted apart.  Two
+    // digits keep the CUDA-core solve (k_trsm_block).
     DigitPlanes Xt, MJ;
     std::unique_ptr<MmPlan> fplan;
     if (L == 4) {
@@ -348,19 +350,20 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
         v.p = P.p;
         return v;
     };
+    if (L == 4) to_digits(J.M, J.ldm, 1, view(MJ, std::min(J.bs, J.nAp)), J.fp.p, st);
     for (uint32_t b = 0; b < nblk; ++b) {
         const uint32_t j0 = b * J.bs, j1 = std::min(j0 + J.bs, J.nAp);
+        const uint32_t next = b + 1 < nblk ? std::min(j1 + J.bs, J.nAp) - j1 : 0;  // the next block's width
         if (L == 4) {
             const uint32_t kb = j1 - j0;
-            to_digits(J.M + j0, J.ldm, 1, view(MJ, kb), J.fp.p, st);
-            fplan->update(0, 0, 0, j0, j0, 0, J.nC, kb, kb, false, err, st);
-            to_digits(J.M + j0, J.ldm, 1, view(F, kb), J.fp.p, st);
+            fplan->update(0, 0, 0, j0, j0, 0, J.nC, kb, kb, false, err, st, &F, kb);
         } else {
             k_trsm_block<2><<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J, j0);
             counted();
         }
         // columns j1.. of M, K = the block's pivots (a multiple of 64: padding pivots are zero)
-        plan.update(0, 0, j0, j1, j1, 0, J.nC, J.Np - j1, j1 - j0, true, err, st);
+        plan.update(0, 0, j0, j1, j1, 0, J.nC, J.Np - j1, j1 - j0, true, err, st, L == 4 ? &MJ : nullptr,
+                    L == 4 ? next : 0);
         macs += (unsigned long long)J.nC * (j1 - j0) * (J.Np - j1);
     }
     k_dense_work<<<1, 32, 0, st>>>(J, macs);

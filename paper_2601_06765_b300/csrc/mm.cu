@@ -97,6 +97,11 @@ struct MmParams {
     uint64_t big;           // 2^31 p, which keeps the accumulated sum positive
     uint32_t rd[7];         // (256^d mod p) 2^32 mod p (C += A B), or (p - 256^d mod p) 2^32 mod p
     uint32_t *err;          // bit 0: a bounded wait gave up
+    // optional: the digit planes of the updated entries of the region's first dig_cols columns
+    // (a multiple of 16) go to dig (row m, K index n; row pitch dig_kpad, plane pitch dig_plane)
+    uint16_t *dig;
+    uint64_t dig_kpad, dig_plane;
+    uint32_t dig_cols;
 };
 
 // ---- PTX wrappers (sm_100 family) ----------------------------------------------------------------
@@ -253,6 +258,37 @@ __device__ __forceinline__ int acc_pair_small(uint32_t lo, uint32_t hi) {
 template <int L>
 __host__ __device__ constexpr bool small_diag(int d) {
     return (long long)(d + 1 < 2 * L - 1 - d ? d + 1 : 2 * L - 1 - d) * (512 / L) * 16384 <= (1ll << 22);
+}
+
+// Digit planes: dst[l][r][k] (row pitch kpad, plane pitch rows * kpad) = BF16 bits of the l-th
+// balanced base-256 digit of a residue x (representative x or x - p, T as in the header).
+template <int L>
+__device__ __forceinline__ void digits_of(uint32_t x, uint32_t p, uint32_t (&a)[L]) {
+    const uint32_t T = L == 2 ? 32639u : 2139062143u;  // 127 (1 + 256 + ... + 256^{L-1})
+    int v = x <= T ? (int)x : (int)(x - p);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const int d = l + 1 < L ? (int)(((uint32_t)v & 0xFFu) ^ 0x80u) - 0x80 : v;
+        if (l + 1 < L) v = (v - d) >> 8;
+        a[l] = __float_as_uint((float)d) >> 16;
+    }
+}
+
+// the planes of 8 consecutive K values of one row: one 16-byte store per plane (dst 16-byte aligned)
+template <int L>
+__device__ __forceinline__ void put_digits8(const uint32_t (&x)[8], uint32_t p, uint16_t *dst, uint64_t plane) {
+    uint32_t w[L][4];
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+        uint32_t a[L], b[L];
+        digits_of<L>(x[i], p, a);
+        digits_of<L>(x[i + 1], p, b);
+#pragma unroll
+        for (int l = 0; l < L; ++l) w[l][i / 2] = a[l] | (b[l] << 16);
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+        *reinterpret_cast<uint4 *>(dst + (size_t)l * plane) = make_uint4(w[l][0], w[l][1], w[l][2], w[l][3]);
 }
 
 template <int L>
@@ -533,6 +569,20 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
                     }
                     *q = c;
                 }
+                // the digit planes of the first dig_cols columns, from the updated entries just
+                // written (a thread's CPT columns are all in or all out: dig_cols is a multiple of 16)
+                const uint32_t dc = (uint32_t)nt * BN + col0, dr = (uint32_t)mt * MM_BM + r;
+                if (dc < P.dig_cols && dr < P.M) {
+                    uint16_t *dst = P.dig + (size_t)dr * P.dig_kpad + dc;
+#pragma unroll 1
+                    for (int q8 = 0; q8 < CPT / 8; ++q8) {
+                        const uint32_t j = chunk0 + 2u * (uint32_t)q8;
+                        const uint4 a = *reinterpret_cast<const uint4 *>(crow + 16u * (j ^ (r & 7u)));
+                        const uint4 b = *reinterpret_cast<const uint4 *>(crow + 16u * ((j + 1) ^ (r & 7u)));
+                        const uint32_t x8[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                        put_digits8<L>(x8, fp.p, dst + 8 * q8, P.dig_plane);
+                    }
+                }
             }
             fence_async_smem();
             epi_sync<32 * Cfg::WPG>(eg);
@@ -558,37 +608,6 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
         tc_fence_after();
         tmem_dealloc(tmem, Cfg::TMEM_COLS);
     }
-}
-
-// Digit planes: dst[l][r][k] (row pitch kpad, plane pitch rows * kpad) = BF16 bits of the l-th
-// balanced base-256 digit of a residue x (representative x or x - p, T as in the header).
-template <int L>
-__device__ __forceinline__ void digits_of(uint32_t x, uint32_t p, uint32_t (&a)[L]) {
-    const uint32_t T = L == 2 ? 32639u : 2139062143u;  // 127 (1 + 256 + ... + 256^{L-1})
-    int v = x <= T ? (int)x : (int)(x - p);
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        const int d = l + 1 < L ? (int)(((uint32_t)v & 0xFFu) ^ 0x80u) - 0x80 : v;
-        if (l + 1 < L) v = (v - d) >> 8;
-        a[l] = __float_as_uint((float)d) >> 16;
-    }
-}
-
-// the planes of 8 consecutive K values of one row: one 16-byte store per plane (dst 16-byte aligned)
-template <int L>
-__device__ __forceinline__ void put_digits8(const uint32_t (&x)[8], uint32_t p, uint16_t *dst, uint64_t plane) {
-    uint32_t w[L][4];
-#pragma unroll
-    for (int i = 0; i < 8; i += 2) {
-        uint32_t a[L], b[L];
-        digits_of<L>(x[i], p, a);
-        digits_of<L>(x[i + 1], p, b);
-#pragma unroll
-        for (int l = 0; l < L; ++l) w[l][i / 2] = a[l] | (b[l] << 16);
-    }
-#pragma unroll
-    for (int l = 0; l < L; ++l)
-        *reinterpret_cast<uint4 *>(dst + (size_t)l * plane) = make_uint4(w[l][0], w[l][1], w[l][2], w[l][3]);
 }
 
 // rows of a row-major source (src[r * rs + k]): thread per (row, 8 K values), the whole padded
@@ -746,7 +765,8 @@ MmPlan::~MmPlan() { delete maps; }
 // width, M not a multiple of 128) must end the C tensor of the plan on that side, where the TMA
 // store clips it; cx must be a multiple of 4.
 void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t cx, uint32_t cy, uint32_t M,
-                    uint32_t N, uint32_t K, bool sub, uint32_t *err, cudaStream_t st) const {
+                    uint32_t N, uint32_t K, bool sub, uint32_t *err, cudaStream_t st, const DigitPlanes *dig,
+                    uint32_t dig_cols) const {
     if (!M || !N || !K) return;
     if (K > mm_kmax(fp.p)) fail(GB_EDEVICE, "mm_update: K above the exact accumulation bound");
     if (ax % 8 || bx % 8) fail(GB_EDEVICE, "mm_update: K offsets must be multiples of 8 (16-byte TMA rule)");
@@ -780,6 +800,14 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
         P.rd[d] = (uint32_t)(((uint64_t)y << 32) % fp.p);  // in Montgomery form
     }
     P.err = err;
+    if (dig && dig_cols) {
+        if (dig->L != A->L || dig->rows < M || dig_cols % 16 || dig_cols > N || dig_cols > dig->kpad)
+            fail(GB_EDEVICE, "mm_update: digit planes of the result do not fit");
+        P.dig = dig->p;
+        P.dig_kpad = dig->kpad;
+        P.dig_plane = dig->rows * dig->kpad;
+        P.dig_cols = dig_cols;
+    }
     const unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)sm_count());
     MmTimer *T = t_capturing ? nullptr : t_mm_timer;
     cudaEvent_t e1 = nullptr;
