@@ -210,8 +210,9 @@ def run_ours(args) -> None:
     mm_flops = sum(r["mm_flops"] for r in runs)
     mm_launches = sum(r["mm_launches"] for r in runs)
     achieved = mm_flops / (mm_ms / 1e3) / 1e12 if mm_ms > 0 else 0.0
-    roofline = {"kernel": "k_mm<4> (exact mod-p product on the tensor cores: dense blocked reduction "
-                          "and RREF trailing updates of the n=13 run)",
+    roofline = {"kernel": "k_mm<4> (exact mod-p product on the tensor cores: the dense blocked "
+                          "reduction's block multipliers and trailing updates, and the RREF trailing "
+                          "updates of the n=13 run)",
                 "bound": "tensor", "achieved": round(achieved, 1), "peak": pk["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "frac": round(achieved / pk["bf16_tflops_sustained"], 4),
                 "peak_source": f"{pk['source']} BF16 dense, sustained",
