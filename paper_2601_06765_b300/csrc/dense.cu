@@ -77,15 +77,17 @@ __global__ void k_scatter_ub(DenseJob J) {
     }
 }
 
-// W^T as digit planes, every entry written once, zeros included (no memset of the planes, no
-// scattered 2-byte writes): block (b, s) takes the 64 pivot rows [64 b, 64 b + 64) and the
-// dictionary columns [s FS, (s + 1) FS), finds each row's first entry there by binary search and
-// walks the segment in windows of FW, each row's CSR cursor advancing with the windows (a row's
-// columns ascend).  A window's entries gather in a shared tile; then, per column c of the window
-// and digit plane l, the 64 K entries of row q(c) of W^T go out as one 128-byte store of a warp.
-// Entries left of a pivot's own block end (q < j1) are written as well: the tensor-core update of
-// that block starts at column j1 and never reads them.  Rows q in [nA, nAp) (the padding columns)
-// come from no dictionary column; the caller zeroes them.
+// W^T as digit planes, every entry the update reads written once, zeros included (no memset of
+// the planes, no scattered 2-byte writes): block (b, s) takes the 64 pivot rows [64 b, 64 b + 64)
+// and the dictionary columns [s FS, (s + 1) FS), finds each row's first entry there by binary
+// search and walks the segment in windows of FW, each row's CSR cursor advancing with the windows
+// (a row's columns ascend).  A window's entries gather in a shared tile; then, per column c of the
+// window and digit plane l, the 64 K entries of row q(c) of W^T go out as one 128-byte store of a
+// warp.  Entries left of the end j1 of the pivots' own block (q < j1) are not written: the
+// tensor-core update of that block starts at column j1 and never reads them (that skips the
+// diagonal blocks and the zeros below them, about half of the pivot columns' part of the planes).
+// Rows q in [nA, nAp) (the padding columns) come from no dictionary column; the caller zeroes
+// them.
 constexpr int FW = 128;      // dictionary columns per window
 constexpr int FS = 16 * FW;  // dictionary columns per block
 constexpr int FT = 256;      // threads per block (8 warps)
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(FT) k_fill_wt(DenseJob J) {
             const uint32_t c = c0 + cc;
             if (c >= ce) break;
             const uint32_t q = qcol(J.colpos[c], J.nAp);
+            if (q < min((i0 / J.bs + 1) * J.bs, J.nAp)) continue;  // left of the block's end j1: never read
             uint16_t d0[L], d1[L];
             digits_bf16<L>(tile[cc][2 * lane], J.fp.p, d0);
             digits_bf16<L>(tile[cc][2 * lane + 1], J.fp.p, d1);
