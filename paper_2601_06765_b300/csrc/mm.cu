@@ -334,6 +334,9 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
     const int quarter = warp & 3, grp = ((warp - 2) % Cfg::WPG) >> 2;
     const uint32_t r = (uint32_t)(32 * quarter + lane);
 
+    // a launch that follows this one in the stream may start as soon as this grid's CTAs leave
+    // (programmatic dependent launch): it runs its prologue, then waits for this grid below
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (threadIdx.x == 0) {
         *abort_flag = 0u;
         mbar_init(a_full, 1);
@@ -376,6 +379,10 @@ __global__ void __launch_bounds__(MM_THREADS, 1) k_mm(const __grid_constant__ CU
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // nothing above touches global memory: under a programmatic dependent launch the prologue
+    // overlaps the previous grid, and the operands are read only once it has completed and its
+    // writes are visible (without such a launch this returns at once)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp == 0 && lane == 0) {
         // ---- producer.  K block kb of the it-th tile is the g-th block of the ring sequence,
@@ -742,6 +749,31 @@ struct MmPlan::Maps {
     CUtensorMap ta, tb, tc;
 };
 
+// One k_mm launch.  Outside stream capture it is a programmatic dependent launch: it may begin
+// (its prologue: barriers, tensor memory, the zeroing of the accumulators) while the previous
+// kernel of the stream finishes, and waits for that kernel (griddepcontrol.wait) before its first
+// global access.  Inside a capture it is an ordinary launch.
+template <int L>
+void launch_mm(unsigned grid, cudaStream_t st, const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &tc,
+               const MmParams &P) {
+    opt_in_smem(reinterpret_cast<const void *>(k_mm<L>));
+    if (t_capturing) {
+        k_mm<L><<<grid, MM_THREADS, MmCfg<L>::SMEM, st>>>(ta, tb, tc, P);
+        return;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(MM_THREADS);
+    cfg.dynamicSmemBytes = MmCfg<L>::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GB_CUDA(cudaLaunchKernelEx(&cfg, k_mm<L>, ta, tb, tc, P));
+}
+
 MmPlan::MmPlan(const DigitPlanes &A_, const DigitPlanes &B_, uint32_t *C_, uint64_t ldc_, uint32_t crows,
                uint32_t ccols, const Fp &fp_)
     : A(&A_), B(&B_), C(C_), ldc(ldc_), rows(crows), cols(ccols), fp(fp_), maps(new Maps) {
@@ -824,13 +856,8 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
         T->flops += 2.0 * A->L * A->L * (double)M * N * K;
         T->launches++;
     }
-    if (A->L == 2) {
-        opt_in_smem(reinterpret_cast<const void *>(k_mm<2>));
-        k_mm<2><<<grid, MM_THREADS, MmCfg<2>::SMEM, st>>>(maps->ta, maps->tb, maps->tc, P);
-    } else {
-        opt_in_smem(reinterpret_cast<const void *>(k_mm<4>));
-        k_mm<4><<<grid, MM_THREADS, MmCfg<4>::SMEM, st>>>(maps->ta, maps->tb, maps->tc, P);
-    }
+    if (A->L == 2) launch_mm<2>(grid, st, maps->ta, maps->tb, maps->tc, P);
+    else launch_mm<4>(grid, st, maps->ta, maps->tb, maps->tc, P);
     counted();
     if (e1) GB_CUDA(cudaEventRecord(e1, st));
 }
