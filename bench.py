@@ -202,8 +202,9 @@ def run_ours(args) -> None:
 
     # roofline of the dominant kernel of this workload, the tensor-core product k_mm of the dense
     # blocked reduction (see profiles/): algorithmic work = 2 L^2 BF16 digit-product FLOPs per
-    # mod-p multiply-add; time = CUDA events around each of its launches on the context's stream,
-    # summed over the timed runs; peak = the sustained BF16 figure (the launches run inside a
+    # mod-p multiply-add; time = CUDA events on the context's stream around each of its launches,
+    # or around each run of consecutive k_mm launches (the dense block loop, whose launches overlap
+    # one another), summed over the timed runs; peak = the sustained BF16 figure (the launches run inside a
     # run of about a second)
     pk = peaks()
     mm_ms = sum(r["ms_mm"] for r in runs)

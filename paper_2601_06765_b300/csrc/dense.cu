@@ -354,6 +354,10 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
         return v;
     };
     if (L == 4) to_digits(J.M, J.ldm, 1, view(MJ, std::min(J.bs, J.nAp)), J.fp.p, st);
+    // four digits: the block loop launches only k_mm, timed as one span (no events between the
+    // launches, so that each overlaps the one before)
+    MmTimer *T = L == 4 ? t_mm_timer : nullptr;
+    if (T) T->begin_span(st);
     for (uint32_t b = 0; b < nblk; ++b) {
         const uint32_t j0 = b * J.bs, j1 = std::min(j0 + J.bs, J.nAp);
         const uint32_t next = b + 1 < nblk ? std::min(j1 + J.bs, J.nAp) - j1 : 0;  // the next block's width
@@ -369,6 +373,7 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
                     L == 4 ? next : 0);
         macs += (unsigned long long)J.nC * (j1 - j0) * (J.Np - j1);
     }
+    if (T) T->end_span(st);
     k_dense_work<<<1, 32, 0, st>>>(J, macs);
     counted();
     // D' = M[:, nAp:]

@@ -444,9 +444,15 @@ void to_digits(const uint32_t *src, uint64_t rs, uint64_t ks, const DigitPlanes 
 // outside graph capture; the reduction reads them after its stream synchronises.
 struct MmTimer {
     gb_ctx *ctx = nullptr;
-    size_t used = 0;  // events taken from ctx->mm_ev (two per launch)
+    size_t used = 0;  // events taken from ctx->mm_ev (two per launch, or two per span)
     double flops = 0.0;
     uint64_t launches = 0;
+    // a span: one event pair around a run of consecutive k_mm launches with nothing else between
+    // them, in place of a pair per launch (events between launches would keep each launch from
+    // overlapping the one before, see launch_mm)
+    cudaEvent_t span_end = nullptr;
+    void begin_span(cudaStream_t st);
+    void end_span(cudaStream_t st);
     double elapsed_ms() const;  // after the stream has synchronised
 };
 extern thread_local MmTimer *t_mm_timer;

@@ -844,15 +844,17 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
     MmTimer *T = t_capturing ? nullptr : t_mm_timer;
     cudaEvent_t e1 = nullptr;
     if (T) {
-        std::vector<cudaEvent_t> &pool = T->ctx->mm_ev;
-        while (pool.size() < T->used + 2) {
-            cudaEvent_t e;
-            GB_CUDA(cudaEventCreate(&e));
-            pool.push_back(e);
+        if (!T->span_end) {
+            std::vector<cudaEvent_t> &pool = T->ctx->mm_ev;
+            while (pool.size() < T->used + 2) {
+                cudaEvent_t e;
+                GB_CUDA(cudaEventCreate(&e));
+                pool.push_back(e);
+            }
+            GB_CUDA(cudaEventRecord(pool[T->used], st));
+            e1 = pool[T->used + 1];
+            T->used += 2;
         }
-        GB_CUDA(cudaEventRecord(pool[T->used], st));
-        e1 = pool[T->used + 1];
-        T->used += 2;
         T->flops += 2.0 * A->L * A->L * (double)M * N * K;
         T->launches++;
     }
@@ -889,6 +891,25 @@ void matmul_dev(Arena &ar, const Fp &fp, uint32_t m, uint32_t n, uint32_t k, con
     for (uint32_t k0 = 0; k0 < k; k0 += kmax)
         plan.update(k0, 0, k0, 0, 0, 0, m, n, std::min(kmax, k - k0), subtract, err, st);
     if (Cw != C) GB_CUDA(cudaMemcpy2DAsync(C, 4 * ldc, Cw, 4 * ldw, 4ull * n, m, cudaMemcpyDeviceToDevice, st));
+}
+
+void MmTimer::begin_span(cudaStream_t st) {
+    if (t_capturing || span_end) return;
+    std::vector<cudaEvent_t> &pool = ctx->mm_ev;
+    while (pool.size() < used + 2) {
+        cudaEvent_t e;
+        GB_CUDA(cudaEventCreate(&e));
+        pool.push_back(e);
+    }
+    GB_CUDA(cudaEventRecord(pool[used], st));
+    span_end = pool[used + 1];
+    used += 2;
+}
+
+void MmTimer::end_span(cudaStream_t st) {
+    if (!span_end) return;
+    GB_CUDA(cudaEventRecord(span_end, st));
+    span_end = nullptr;
 }
 
 double MmTimer::elapsed_ms() const {
