@@ -204,8 +204,8 @@ def run_ours(args) -> None:
     # blocked reduction (see profiles/): algorithmic work = 2 L^2 BF16 digit-product FLOPs per
     # mod-p multiply-add; time = CUDA events on the context's stream around each of its launches,
     # or around each run of consecutive k_mm launches (the dense block loop, whose launches overlap
-    # one another), summed over the timed runs; peak = the sustained BF16 figure (the launches run inside a
-    # run of about a second)
+    # one another), summed over the timed runs; peak = the sustained BF16 figure (the launches run
+    # inside a run of about a second)
     pk = peaks()
     mm_ms = sum(r["ms_mm"] for r in runs)
     mm_flops = sum(r["mm_flops"] for r in runs)
