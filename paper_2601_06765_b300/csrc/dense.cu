@@ -363,14 +363,14 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
         const uint32_t next = b + 1 < nblk ? std::min(j1 + J.bs, J.nAp) - j1 : 0;  // the next block's width
         if (L == 4) {
             const uint32_t kb = j1 - j0;
-            fplan->update(0, 0, 0, j0, j0, 0, J.nC, kb, kb, false, err, st, &F, kb);
+            fplan->update(0, 0, 0, j0, j0, 0, J.nC, kb, kb, false, err, st, &F, kb, true);
         } else {
             k_trsm_block<2><<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J, j0);
             counted();
         }
         // columns j1.. of M, K = the block's pivots (a multiple of 64: padding pivots are zero)
         plan.update(0, 0, j0, j1, j1, 0, J.nC, J.Np - j1, j1 - j0, true, err, st, L == 4 ? &MJ : nullptr,
-                    L == 4 ? next : 0);
+                    L == 4 ? next : 0, L == 4);
         macs += (unsigned long long)J.nC * (j1 - j0) * (J.Np - j1);
     }
     if (T) T->end_span(st);

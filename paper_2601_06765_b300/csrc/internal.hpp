@@ -464,10 +464,11 @@ struct MmPlan {
     MmPlan(const MmPlan &) = delete;
     MmPlan &operator=(const MmPlan &) = delete;
     // dig (optional): the digit planes of the updated region's first dig_cols columns are also
-    // written there (row m, K index n), dig_cols a multiple of 16
+    // written there (row m, K index n), dig_cols a multiple of 16.  pdl: a programmatic dependent
+    // launch (for a run of consecutive k_mm launches; see launch_mm in mm.cu)
     void update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t cx, uint32_t cy, uint32_t M, uint32_t N,
                 uint32_t K, bool sub, uint32_t *err, cudaStream_t st, const DigitPlanes *dig = nullptr,
-                uint32_t dig_cols = 0) const;
+                uint32_t dig_cols = 0, bool pdl = false) const;
     const DigitPlanes *A, *B;
     uint32_t *C;
     uint64_t ldc;

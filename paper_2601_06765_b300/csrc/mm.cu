@@ -749,15 +749,15 @@ struct MmPlan::Maps {
     CUtensorMap ta, tb, tc;
 };
 
-// One k_mm launch.  Outside stream capture it is a programmatic dependent launch: it may begin
-// (its prologue: barriers, tensor memory, the zeroing of the accumulators) while the previous
-// kernel of the stream finishes, and waits for that kernel (griddepcontrol.wait) before its first
-// global access.  Inside a capture it is an ordinary launch.
+// One k_mm launch.  With pdl (and outside stream capture) it is a programmatic dependent launch:
+// it may begin (its prologue: barriers, tensor memory, the zeroing of the accumulators) while the
+// previous kernel of the stream finishes, and waits for that kernel (griddepcontrol.wait) before
+// its first global access.  Otherwise it is an ordinary launch.
 template <int L>
 void launch_mm(unsigned grid, cudaStream_t st, const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &tc,
-               const MmParams &P) {
+               const MmParams &P, bool pdl) {
     opt_in_smem(reinterpret_cast<const void *>(k_mm<L>));
-    if (t_capturing) {
+    if (!pdl || t_capturing) {
         k_mm<L><<<grid, MM_THREADS, MmCfg<L>::SMEM, st>>>(ta, tb, tc, P);
         return;
     }
@@ -798,7 +798,7 @@ MmPlan::~MmPlan() { delete maps; }
 // store clips it; cx must be a multiple of 4.
 void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t cx, uint32_t cy, uint32_t M,
                     uint32_t N, uint32_t K, bool sub, uint32_t *err, cudaStream_t st, const DigitPlanes *dig,
-                    uint32_t dig_cols) const {
+                    uint32_t dig_cols, bool pdl) const {
     if (!M || !N || !K) return;
     if (K > mm_kmax(fp.p)) fail(GB_EDEVICE, "mm_update: K above the exact accumulation bound");
     if (ax % 8 || bx % 8) fail(GB_EDEVICE, "mm_update: K offsets must be multiples of 8 (16-byte TMA rule)");
@@ -858,8 +858,8 @@ void MmPlan::update(uint32_t ax, uint32_t ay, uint32_t bx, uint32_t by, uint32_t
         T->flops += 2.0 * A->L * A->L * (double)M * N * K;
         T->launches++;
     }
-    if (A->L == 2) launch_mm<2>(grid, st, maps->ta, maps->tb, maps->tc, P);
-    else launch_mm<4>(grid, st, maps->ta, maps->tb, maps->tc, P);
+    if (A->L == 2) launch_mm<2>(grid, st, maps->ta, maps->tb, maps->tc, P, pdl);
+    else launch_mm<4>(grid, st, maps->ta, maps->tb, maps->tc, P, pdl);
     counted();
     if (e1) GB_CUDA(cudaEventRecord(e1, st));
 }
@@ -889,7 +889,7 @@ void matmul_dev(Arena &ar, const Fp &fp, uint32_t m, uint32_t n, uint32_t k, con
     const uint32_t kmax = mm_kmax(fp.p);
     const MmPlan plan(DA, DB, Cw, ldw, m, n, fp);
     for (uint32_t k0 = 0; k0 < k; k0 += kmax)
-        plan.update(k0, 0, k0, 0, 0, 0, m, n, std::min(kmax, k - k0), subtract, err, st);
+        plan.update(k0, 0, k0, 0, 0, 0, m, n, std::min(kmax, k - k0), subtract, err, st, nullptr, 0, true);
     if (Cw != C) GB_CUDA(cudaMemcpy2DAsync(C, 4 * ldc, Cw, 4 * ldw, 4ull * n, m, cudaMemcpyDeviceToDevice, st));
 }
 
