@@ -5,7 +5,8 @@ a pool fixed at start-up) that must not see the library take memory between its 
 entry point works on caller-owned buffers (torch tensors here) plus a fixed scratch array inside
 the library.  Its D' must equal the one the ordinary entry point gb_reduce_macaulay computes, and
 the oracle's D' of the same F4 step, bit for bit, on consecutive calls with different matrices
-(the scratch keeps the previous call's contents).  A matrix with a column index out of range
+(the scratch keeps the previous call's contents), and when the call is recorded into a CUDA graph
+and replayed.  A matrix with a column index out of range
 must leave D' at 0xFFFFFFFF, and the next valid call must be unaffected.
 """
 from __future__ import annotations
@@ -73,6 +74,38 @@ def test_noalloc_matches_gb_reduce_macaulay_and_the_oracle_on_consecutive_calls(
         third = _run_noalloc(torch, 65521, m1, w1)
         assert np.array_equal(third, o1)
         assert torch.cuda.mem_get_info()[0] >= free_before - (8 << 20)  # torch's own copies only
+        S1.close()
+        S2.close()
+
+
+def test_noalloc_call_captured_in_a_cuda_graph_replays_exactly():
+    """The call recorded into a CUDA graph on a side stream (after a first call on the device, as
+    gb.h asks) and replayed twice, the second time after another matrix has gone through the
+    scratch: every replay gives the captured matrix's D' (the job description is a kernel
+    parameter of the graph's nodes, not a host buffer)."""
+    import torch
+    with gb.Context(arena_bytes=1 << 30, keep_step=True) as ctx:
+        S1, m1, w1, o1 = _matrix_after_steps(ctx, synth.dense_n6(0), 5)                         # p = 65521
+        S2, m2, w2, o2 = _matrix_after_steps(ctx, synth.dense_system(5, 5, 2147483647, 7), 4)  # 31-bit p
+        assert np.array_equal(_run_noalloc(torch, 65521, m1, w1), o1)  # the first call on the device
+        npiv = int(m1["npivot"])
+        rp = m1["row_ptr"]
+        nC, nb, N = len(rp) - 1 - npiv, len(w1["nonpiv"]), m1["dict_exps"].shape[0]
+        bufs = [_device_u32(torch, x) for x in (rp, m1["col"], m1["val"], m1["col"][rp[:npiv]], w1["nonpiv"])]
+        out = torch.full((nC * nb,), 7, dtype=torch.int32, device="cuda")
+        side = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            gb.gb_reduce_rows_noalloc(65521, N, npiv, nC, nb, *(b.data_ptr() for b in bufs), out.data_ptr(),
+                                      side.cuda_stream)
+        for replay in range(2):
+            out.fill_(7)
+            graph.replay()
+            torch.cuda.synchronize()
+            got = out.cpu().numpy().view(np.uint32).reshape(nC, nb)
+            assert np.array_equal(got, o1), f"replay {replay}"
+            assert np.array_equal(_run_noalloc(torch, 2147483647, m2, w2), o2)  # the scratch changes hands
         S1.close()
         S2.close()
 
