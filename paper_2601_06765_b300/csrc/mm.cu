@@ -29,15 +29,19 @@
 //                    counts)
 //   warp 1           allocates the tensor memory (two accumulator sets of 2L - 1 diagonals,
 //                    alternate tiles) and issues the products from lane 0
-//   warps 2-17       epilogue (four warps per tensor-memory lane quarter): drains a set as soon as
-//                    its products are done (tcgen05.ld of every diagonal, exact conversion,
-//                    sum_s D_s (256^s mod p)), zeroes it (tcgen05.st) and hands it back, so that
-//                    every product accumulates; then one Barrett reduction and the
-//                    read-modify-write of the C tile in shared memory; one of its threads issues
-//                    the TMA store and loads the C tile of a later tile into the freed buffer
+//   warps 2-17       epilogue, in EG groups that take alternate tiles (two groups of eight warps
+//                    for L = 4, one of sixteen for L = 2; each group covers the four tensor-memory
+//                    lane quarters, a thread 16 columns of its row): drains the tile's set as soon
+//                    as its products are done (tcgen05.ld of every diagonal, exact conversion,
+//                    sum_s D_s (256^s 2^32 mod p) and one Montgomery reduction), zeroes it
+//                    (tcgen05.st) and hands it back, so that every product accumulates; then adds
+//                    C in the read-modify-write of the group's C buffer in shared memory
+//                    (optionally also writing the digit planes of the result's first columns);
+//                    one thread of the group issues the TMA store and loads the C tile of the
+//                    group's next tile into the freed buffer
 // so that one set's products run while the other is drained.  Every wait is bounded; a wait that
 // gives up sets an error flag that the host turns into GB_ETIMEOUT, and the CTA still releases its
-// tensor memory.
+// tensor memory.  Runs of consecutive launches are programmatic dependent launches (launch_mm).
 #include <cuda.h>
 
 #include <algorithm>
