@@ -306,7 +306,7 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
     GB_CUDA(cudaMemsetAsync(M.p, 0, M.bytes(), st));
     GB_CUDA(cudaMemsetAsync(Ub.p, 0, Ub.bytes(), st));
     // rows [nA, nAp) of W^T (the padding columns) come from no dictionary column: zero them; the
-    // rest of the planes is written in full by k_fill_wt
+    // rest of the planes that the trailing updates read is written by k_fill_wt
     for (uint32_t l = 0; l < L && J.nAp > J.nA; ++l)
         GB_CUDA(cudaMemsetAsync(WT.p + (size_t)l * J.Np * WT.kpad + (size_t)J.nA * WT.kpad, 0,
                                 2ull * (J.nAp - J.nA) * WT.kpad, st));
@@ -364,6 +364,7 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
         if (L == 4) {
             const uint32_t kb = j1 - j0;
             fplan->update(0, 0, 0, j0, j0, 0, J.nC, kb, kb, false, err, st, &F, kb, true);
+            macs += (unsigned long long)J.nC * kb * kb;
         } else {
             k_trsm_block<2><<<blocks_of(J.nC, DW), DW * 32, 0, st>>>(J, j0);
             counted();
