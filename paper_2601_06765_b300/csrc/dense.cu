@@ -223,39 +223,40 @@ __global__ void __launch_bounds__(DW * 32) k_trsm_block(DenseJob J, uint32_t j0)
 // X_b = U_b^{-1} - I for every pivot block b (U_b = W[J_b, J_b], unit upper triangular, its
 // entries right of the diagonal in Ub), as the digit planes of X_b^T: plane row b bs + n, K index
 // i holds X_b[i][n].  From X'U = I with X' = U^{-1}: X'[i][j] = -(U[i][j] + sum_{i<k<j} X'[i][k]
-// U[k][j]) for j > i, X'[i][i] = 1, 0 below.  Thread i computes row i, column by column, with
-// U_b staged in shared memory (rows padded by one word, so the U[k][j] reads of a warp, k = i + 1
-// + 2t, fall in distinct banks).  Two products (each below 2^62) are summed before each
-// reduction.  Rows and columns at or past the
-// block's pivot count jn (the padding of the last block) are zero.  Shared memory: U_b and the
-// rows of X, 2 bs (bs + 1) words.
+// U[k][j]) for j > i, X'[i][i] = 1, 0 below.  Four threads (four consecutive lanes) compute row
+// i, column by column: thread q sums the terms k = i + 1 + q (mod 4), two shuffles add the four
+// shares, and the row's first thread stores X'[i][j] before the next column (one warp holds
+// eight whole rows, so a __syncwarp orders it).  U_b is staged in shared memory with rows padded
+// by one word.  Rows and columns at or past the block's pivot count jn (the padding of the last
+// block) are zero.  Shared memory: U_b and the rows of X, 2 bs (bs + 1) words; bs rows x 4
+// threads per block.
 __global__ void k_block_inv(DenseJob J, uint16_t *__restrict__ xt, uint64_t kpad, uint64_t plane) {
     extern __shared__ uint32_t xs[];
-    const uint32_t bs = J.bs, ld = bs + 1, b = blockIdx.x, i = threadIdx.x, j0 = b * bs;
+    const uint32_t bs = J.bs, ld = bs + 1, b = blockIdx.x, j0 = b * bs;
+    const uint32_t i = threadIdx.x >> 2, q = threadIdx.x & 3;
     const uint32_t jn = min(bs, J.nA - j0);
     uint32_t *us = xs + (size_t)bs * ld;  // U_b, row k at us + k ld
     const uint32_t *U = J.Ub + (size_t)b * bs * bs;
-    for (uint32_t e = i; e < bs * bs; e += blockDim.x) us[(e / bs) * ld + e % bs] = U[e];
+    for (uint32_t e = threadIdx.x; e < bs * bs; e += blockDim.x) us[(e / bs) * ld + e % bs] = U[e];
     __syncthreads();
     const Fp fp = J.fp;
     uint32_t *x = xs + (size_t)i * ld;
     for (uint32_t j = 0; j < bs; ++j) {
-        uint32_t v = 0;
-        if (j < jn && i < j) {
-            uint32_t a = us[i * ld + j];
-            uint32_t k = i + 1;
-            for (; k + 1 < j; k += 2) {
-                const unsigned long long t =
-                    (unsigned long long)x[k] * us[k * ld + j] + (unsigned long long)x[k + 1] * us[(k + 1) * ld + j];
-                a = fp_add(a, fp_reduce(t, fp), fp);
-            }
-            if (k < j) a = fp_add(a, fp_mul(x[k], us[k * ld + j], fp), fp);
-            v = a ? fp.p - a : 0u;
+        const bool live = j < jn && i < j;
+        uint32_t part = 0;
+        if (live) {
+            // at most 32 terms below p, and U[i][j] for the first share: far below 2^64
+            unsigned long long acc = q == 0 ? us[i * ld + j] : 0u;
+            for (uint32_t k = i + 1 + q; k < j; k += 4) acc += fp_mul(x[k], us[k * ld + j], fp);
+            part = fp_reduce(acc, fp);
         }
-        x[j] = v;
+        part = fp_add(part, __shfl_xor_sync(0xffffffffu, part, 1), fp);
+        part = fp_add(part, __shfl_xor_sync(0xffffffffu, part, 2), fp);
+        if (q == 0) x[j] = live && part ? fp.p - part : 0u;
+        __syncwarp();
     }
-    // X_b^T digit planes: for each column n, the threads write consecutive K indices
-    for (uint32_t n = 0; n < bs; ++n) put_digits<4>(x[n], fp.p, xt + (size_t)(j0 + n) * kpad + i, plane);
+    // X_b^T digit planes: thread q writes the columns n = q (mod 4) of its row
+    for (uint32_t n = q; n < bs; n += 4) put_digits<4>(x[n], fp.p, xt + (size_t)(j0 + n) * kpad + i, plane);
 }
 
 __global__ void k_dense_work(DenseJob J, unsigned long long macs) {
@@ -339,7 +340,7 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
         MJ.alloc(ar, L, J.nC, J.bs, st);
         const size_t smem = 8ull * J.bs * (J.bs + 1);
         opt_in_smem(reinterpret_cast<const void *>(k_block_inv));
-        k_block_inv<<<nblk, J.bs, smem, st>>>(J, Xt.p, Xt.kpad, (uint64_t)Xt.rows * Xt.kpad);
+        k_block_inv<<<nblk, 4 * J.bs, smem, st>>>(J, Xt.p, Xt.kpad, (uint64_t)Xt.rows * Xt.kpad);
         counted();
         fplan = std::make_unique<MmPlan>(MJ, Xt, J.M, J.ldm, J.nC, J.Np, J.fp);
     }
