@@ -335,7 +335,7 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
     // digits keep the CUDA-core solve (k_trsm_block).
     DigitPlanes Xt, MJ;
     std::unique_ptr<MmPlan> fplan;
-    if (L == 4) {
+    if (L == 4 && nblk) {
         Xt.alloc(ar, L, (uint64_t)nblk * J.bs, J.bs, st);
         MJ.alloc(ar, L, J.nC, J.bs, st);
         const size_t smem = 8ull * J.bs * (J.bs + 1);
@@ -354,7 +354,7 @@ void reduce_dense(DenseJob J, uint32_t *dprime, Arena &ar, uint32_t *err, cudaSt
         v.p = P.p;
         return v;
     };
-    if (L == 4) to_digits(J.M, J.ldm, 1, view(MJ, std::min(J.bs, J.nAp)), J.fp.p, st);
+    if (L == 4 && nblk) to_digits(J.M, J.ldm, 1, view(MJ, std::min(J.bs, J.nAp)), J.fp.p, st);
     // four digits: the block loop launches only k_mm, timed as one span (no events between the
     // launches, so that each overlaps the one before)
     MmTimer *T = L == 4 ? t_mm_timer : nullptr;
