@@ -359,15 +359,18 @@ def measure_dense_n10(gb, synth, ctx, flush, pk: dict, args) -> dict:
                 "traffic": profile_traffic("k_reduce_rows_dense_n10")}}
 
 
-def _plain_vs_batched(gb, ctx, systems, rank: int = 0, world: int = 1, group: int | None = None) -> dict:
+def _plain_vs_batched(gb, ctx, systems, rank: int = 0, world: int = 1, group: int | None = None,
+                      repeats: int = 1) -> dict:
     """The same systems run one after another through gb_groebner (plain) and as one
-    gb_batch_groebner call (batched, lockstep); wall clock of each, nnz rate of each.  Under
-    several ranks each runs its share of the systems (no data exchange) and the numbers are the
-    slowest rank's time over all ranks' systems."""
+    gb_batch_groebner call (batched, lockstep); wall clock of each (the median of `repeats`
+    measurements, plain and batched alternating), nnz rate of each.  Under several ranks each runs
+    its share of the systems (no data exchange) and the numbers are the slowest rank's time over
+    all ranks' systems."""
     from paper_2601_06765_b300 import shard
     mine = [systems[i] for i in shard.shard([shard.system_weight(s) for s in systems], rank, world)]
-    out = {"systems": len(systems), "ranks": world}
-    for mode in ("plain", "batched"):
+    out = {"systems": len(systems), "ranks": world, "repeats": repeats}
+    times = {"plain": [], "batched": []}
+    for mode in ("plain", "batched") * repeats:
         hs = [gb.gb_system_create(ctx.h, s) for s in mine]
         stats = []
         if mode == "plain":  # one at a time; each leaves the arena before the next
@@ -388,7 +391,9 @@ def _plain_vs_batched(gb, ctx, systems, rank: int = 0, world: int = 1, group: in
                 for h in hs[a:a + g]:
                     gb.gb_system_destroy(h)
             hs = []
-        dt_ms, nnz = shard.aggregate(el * 1e3, sum(st["nnz_total"] for st in stats))
+        times[mode].append(shard.aggregate(el * 1e3, sum(st["nnz_total"] for st in stats)))
+    for mode, ts in times.items():
+        dt_ms, nnz = sorted(ts)[len(ts) // 2]
         dt = dt_ms / 1e3
         out[f"{mode}_ms"] = round(dt * 1e3, 2)
         out[f"{mode}_nnz_per_s"] = nnz / dt
@@ -415,7 +420,7 @@ def measure_batched(gb, synth, ctx, rank: int = 0, world: int = 1, local: int = 
     cubic = lambda s: _max_degree(s) == 3
     mixed = [s for s in mixed_all if not (cubic(s) and s["n"] >= 8)]
     cubic8 = [s for s in mixed_all if cubic(s) and s["n"] == 8]
-    a = _plain_vs_batched(gb, ctx, primes, rank, world)
+    a = _plain_vs_batched(gb, ctx, primes, rank, world, repeats=3)
     a["workload"] = "n=8 dense quadratic system modulo the 128 largest primes below 2^31"
     b = _plain_vs_batched(gb, ctx, mixed, rank, world)
     b["workload"] = (f"{len(mixed)} of the 256 mixed systems (n ~ U{{5..9}}, degree 2 or 3, 10-40 terms, "
