@@ -498,6 +498,22 @@ typedef enum {
 gb_status gb_modp_apply(gb_modp_op op, uint32_t p, uint64_t n, uint32_t window, const uint32_t *a,
                         const uint32_t *b, const uint32_t *c, uint32_t *out, void *stream);
 
+/* Host only, no device or context: the critical-pair bookkeeping of the F4 loop replayed on a
+   sequence of leading monomials, to check it against a textbook model.  The pairs are those of
+   UPDATE (Becker-Weispfenning; the Gebauer-Moeller criteria, Sec. 2.1's S-pairs pruned) with the
+   selection of the pipeline (Sec. 4.2: every pair of the least lcm degree).
+   lms[nelem * n]: the leading monomials (n exponent bytes each) in insertion order, inserted in
+   ngroups groups of group_sizes[g] elements; the elements of one group are inserted together, as
+   the new elements of one F4 step are (the result is that of inserting them one at a time in
+   order).  select_before[g] (NULL: never): before group g, remove the pairs whose lcm has the
+   least degree.  Output: npairs pairs (i, j), i < j, at pairs[2 q], pairs[2 q + 1] (cap pairs at
+   most), and in_basis[nelem]: 0 for an element whose leading monomial a later one divides.
+   GB_EINVAL: n outside 1..16, sizes that do not add up, a null pointer, more than cap pairs
+   (npairs then holds the count). */
+gb_status gb_pair_update_replay(uint32_t n, uint32_t nelem, const uint8_t *lms, uint32_t ngroups,
+                                const uint32_t *group_sizes, const uint8_t *select_before, uint32_t cap,
+                                uint32_t *pairs, uint32_t *npairs, uint8_t *in_basis);
+
 /* ---- autotuning ----------------------------------------------------------------------------- */
 
 /* The reduction of a Macaulay matrix has interchangeable schedules that give the same D' and

@@ -180,6 +180,8 @@ _SIGS = {
     "gb_server_stats_get": [_vp, ctypes.POINTER(gb_server_stats)],
     "gb_reduce_rows_noalloc": [ctypes.c_uint32] * 5 + [_vp] * 7,
     "gb_modp_apply": [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32] + [_vp] * 5,
+    "gb_pair_update_replay": [ctypes.c_uint32, ctypes.c_uint32, _u8p, ctypes.c_uint32, _u32p, _u8p,
+                              ctypes.c_uint32, _u32p, _u32p, _u8p],
     "gb_block_wiedemann": [_vp, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p, _u32p, ctypes.c_uint32,
                            ctypes.POINTER(gb_krylov_stats)],
     "gb_sig_filter": [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _u32p],
@@ -505,6 +507,28 @@ def gb_modp_apply(op: int, p: int, n: int, window: int, a: int, b: int | None, c
     """One device F_p primitive applied elementwise (integer device addresses; b and c may be None
     where the operation does not read them).  See include/gb.h for the operations."""
     check(lib().gb_modp_apply(op, p, n, window, a, b or None, c or None, out, stream or None), "gb_modp_apply")
+
+
+def gb_pair_update_replay(n: int, lms: np.ndarray, group_sizes, select_before=None):
+    """The host pair bookkeeping replayed on leading monomials lms[nelem][n] (uint8), inserted in
+    groups; returns (sorted list of pairs (i, j), in_basis flags).  See include/gb.h."""
+    lms = np.ascontiguousarray(lms, dtype=np.uint8).reshape(-1, n)
+    nelem = lms.shape[0]
+    gs = np.ascontiguousarray(group_sizes, dtype=np.uint32)
+    sel = None if select_before is None else np.ascontiguousarray(select_before, dtype=np.uint8)
+    inb = np.zeros(max(nelem, 1), dtype=np.uint8)
+    npairs = ctypes.c_uint32(0)
+    cap = max(nelem * nelem, 1)
+    out = np.zeros(2 * cap, dtype=np.uint32)
+    u8 = lambda a: a.ctypes.data_as(_u8p)
+    check(lib().gb_pair_update_replay(n, nelem, u8(lms) if nelem else None, len(gs),
+                                      gs.ctypes.data_as(_u32p) if len(gs) else None,
+                                      u8(sel) if sel is not None else None, cap, out.ctypes.data_as(_u32p),
+                                      ctypes.byref(npairs), u8(inb)),
+          "gb_pair_update_replay")
+    k = npairs.value
+    pairs = sorted((int(out[2 * q]), int(out[2 * q + 1])) for q in range(k))
+    return pairs, [bool(x) for x in inb[:nelem]]
 
 
 def gb_matmul_modp(ctx: int, p: int, m: int, n: int, k: int, A: int, lda: int, B: int, ldb: int, C: int,

@@ -611,6 +611,47 @@ gb_status gb_modp_apply(gb_modp_op op, uint32_t p, uint64_t n, uint32_t window, 
     GB_API_END
 }
 
+gb_status gb_pair_update_replay(uint32_t n, uint32_t nelem, const uint8_t *lms, uint32_t ngroups,
+                                const uint32_t *group_sizes, const uint8_t *select_before, uint32_t cap,
+                                uint32_t *pairs, uint32_t *npairs, uint8_t *in_basis) {
+    GB_API_BEGIN
+    if (!n || n > 16) fail(GB_EINVAL, "n must be 1..16");
+    if ((nelem && (!lms || !in_basis)) || (ngroups && !group_sizes) || !npairs || (cap && !pairs))
+        fail(GB_EINVAL, "null pointer");
+    uint64_t total = 0;
+    for (uint32_t g = 0; g < ngroups; ++g) total += group_sizes[g];
+    if (total != nelem) fail(GB_EINVAL, "group sizes do not add up to nelem");
+    gb_system S;
+    S.n = n;
+    uint32_t e = 0;
+    for (uint32_t g = 0; g < ngroups; ++g) {
+        if (select_before && select_before[g] && !S.pairs.empty()) {  // the normal strategy
+            uint32_t d = UINT32_MAX;
+            for (const PairL &q : S.pairs) d = std::min(d, q.deg);
+            size_t w = 0;
+            for (const PairL &q : S.pairs)
+                if (q.deg != d) S.pairs[w++] = q;
+            S.pairs.resize(w);
+        }
+        const uint32_t h0 = e;
+        for (uint32_t k = 0; k < group_sizes[g]; ++k, ++e) {
+            Mono m{};
+            std::memcpy(m.e, lms + (size_t)e * n, n);
+            push_lm(&S, m);
+        }
+        if (e > h0) update_pairs_host(&S, h0);
+    }
+    *npairs = (uint32_t)S.pairs.size();
+    if (S.pairs.size() > cap) fail(GB_EINVAL, "more pairs than cap (npairs holds the count)");
+    for (size_t q = 0; q < S.pairs.size(); ++q) {
+        pairs[2 * q] = std::min(S.pairs[q].i, S.pairs[q].j);
+        pairs[2 * q + 1] = std::max(S.pairs[q].i, S.pairs[q].j);
+    }
+    for (uint32_t k = 0; k < nelem; ++k) in_basis[k] = S.redundant[k] ? 0 : 1;
+    return GB_OK;
+    GB_API_END
+}
+
 gb_status gb_matmul_modp(gb_ctx *ctx, uint32_t p, uint32_t m, uint32_t n, uint32_t k, const uint32_t *A,
                          uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
                          int subtract) {

@@ -431,6 +431,9 @@ static void update_steps(gb_ctx *ctx, const std::vector<gb_system *> &Ss, const 
     });
 }
 
+// the critical-pair update of one system for its elements h0.. (host only)
+void update_pairs_host(gb_system *S, uint32_t h0) { update_steps(nullptr, {S}, {h0}); }
+
 // record a new leading monomial (SWAR form, and whether the fast comparisons still apply)
 void push_lm(gb_system *S, const Mono &m) {
     S->lm.push_back(m);

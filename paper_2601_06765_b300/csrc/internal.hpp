@@ -395,6 +395,8 @@ void block_wiedemann(const gb_macaulay *mac, uint32_t b, const uint32_t *X, cons
 // host side of the F4 driver (f4.cpp): a new leading monomial in the host mirrors; rows (t, k) in
 // pivot order; the inputs of fresh systems onto the device; the reduced basis of finished systems
 void push_lm(gb_system *S, const Mono &m);
+// the Gebauer-Moeller update of S's pairs for its elements h0 .. lm.size() - 1, all at once (f4.cpp)
+void update_pairs_host(gb_system *S, uint32_t h0);
 std::vector<RowSpec> order_rows(const gb_system *S, std::vector<std::pair<Mono, uint32_t>> tk);
 void make_resident(const std::vector<gb_system *> &Ss);
 void finish_batch(const std::vector<gb_system *> &Ss);
